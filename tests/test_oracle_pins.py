@@ -1,0 +1,314 @@
+"""Pins of the FP64 oracle against facts fixed by the mathematics, not by the oracle itself.
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term, a wrong sign or
+index, a conjugated or transposed operand) fails at least one of them:
+
+* sphere counts from exact integer arithmetic (basis, inclusion test, k shift);
+* free-electron spectrum 0.5|k+G|^2 (kinetic term, no spurious V or projector part);
+* constant potential shifts every eigenvalue by exactly v0 (V_N(0) normalisation);
+* one s projector: eigenvalues are the roots of the rank-one secular equation (nonlocal sign,
+  D placement, |beta|^2 weights);
+* Hermiticity of the naive-DFT apply and agreement with the dense matrix (DFT signs, V_N index
+  direction, beta vs conj(beta));
+* naive DFT round trip and Parseval (normalisation of the two transforms);
+* translation of all atoms by a grid vector leaves the spectrum unchanged (relative sign of the
+  V_loc centres and the projector phase e^{-iq.R});
+* axis permutation of the atom sites in a cubic cell leaves the Gamma spectrum unchanged
+  (p-channel axis assignment);
+* V_N at low |G| equals the analytic Fourier series of the periodic Gaussian (amplitude, width,
+  image sum, structure-factor sign);
+* projector norms tend to 1 and s/p channels are orthogonal (normalisation constants);
+* Sylvester inertia count equals the number of eigenvalues below a shift.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+
+def exact_count(a, ecut, kred):
+    """Number of Miller triples with |m+kappa|^2 <= 2 Ecut (a/2pi)^2 for a cubic cell, using
+    integer arithmetic on 4(m+kappa) (kappa is a multiple of 1/4 in every config here)."""
+    R2 = 2.0 * ecut * (a / (2 * math.pi)) ** 2
+    lim16 = math.floor(16 * R2)
+    assert abs(16 * R2 - round(16 * R2)) > 1e-6  # not on a boundary
+    k4 = [int(round(4 * k)) for k in kred]
+    M = int(math.isqrt(int(R2))) + 2
+    n = 0
+    for m1 in range(-M, M + 1):
+        for m2 in range(-M, M + 1):
+            s12 = (4 * m1 + k4[0]) ** 2 + (4 * m2 + k4[1]) ** 2
+            if s12 > lim16:
+                continue
+            for m3 in range(-M, M + 1):
+                if s12 + (4 * m3 + k4[2]) ** 2 <= lim16:
+                    n += 1
+    return n
+
+
+def test_reciprocal_lattice_general():
+    rng = np.random.default_rng(3)
+    lat = np.eye(3) * 7 + rng.uniform(-1, 1, (3, 3))
+    B, vol = O.reciprocal_lattice(lat)
+    assert np.allclose(lat @ B.T, 2 * math.pi * np.eye(3), atol=1e-13)
+    assert abs(vol - np.linalg.det(lat)) < 1e-10
+
+
+@pytest.mark.parametrize("a,ecut,kred,expect", [
+    (10.0, 10.0, (0, 0, 0), 1503),
+    (20.0, 20.0, (0.25, 0.25, 0.25), 34181),
+    (20.0, 20.0, (0.25, -0.25, 0.25), 34181),
+    (8.0, 12.0, (0.25, 0.25, -0.25), None),
+    (16.0, 20.0, (0, 0, 0), None),
+])
+def test_sphere_count_exact(a, ecut, kred, expect):
+    miller = O.enumerate_sphere(W.cubic(a), ecut, kred)
+    n = exact_count(a, ecut, kred)
+    assert miller.shape[0] == n
+    if expect is not None:
+        assert n == expect
+
+
+def test_sphere_order_and_offsets():
+    s = W.config1()
+    b = O.make_basis(s.lattice, s.ecut, s.kpts[0], (24, 24, 24))
+    m = b.miller
+    key = (m[:, 2].astype(np.int64) * 1000 + m[:, 1]) * 1000 + m[:, 0]
+    assert np.all(np.diff(key) > 0)  # strictly ascending (m3, m2, m1)
+    assert np.unique(b.offset).size == b.npw
+    assert b.offset.min() >= 0 and b.offset.max() < 24 ** 3
+    # offsets decode back to the Miller triples modulo N
+    o = b.offset
+    assert np.array_equal(o % 24, m[:, 0] % 24)
+    assert np.array_equal((o // 24) % 24, m[:, 1] % 24)
+    assert np.array_equal(o // 576, m[:, 2] % 24)
+
+
+def test_default_box_rule():
+    assert O.is_smooth235(96) and O.is_smooth235(25) and not O.is_smooth235(29)
+    s = W.make_system("x", 10.0, 10.0, 1, 4, seed=1)  # max |m| = 7 -> 29 -> 30
+    assert O.system_box(s) == (30, 30, 30)
+
+
+def free_electron_levels(a, ecut, kred):
+    """Sorted 0.5 (2pi/a)^2 |m+kappa|^2 over the exact-integer sphere (cubic cell)."""
+    R2 = 2.0 * ecut * (a / (2 * math.pi)) ** 2
+    M = int(math.isqrt(int(R2))) + 2
+    r = np.arange(-M, M + 1)
+    m1, m2, m3 = np.meshgrid(r, r, r, indexing="ij")
+    s = (m1 + kred[0]) ** 2 + (m2 + kred[1]) ** 2 + (m3 + kred[2]) ** 2
+    s = np.sort(s[s <= R2].ravel())
+    return 0.5 * (2 * math.pi / a) ** 2 * s
+
+
+@pytest.mark.parametrize("kred", [(0, 0, 0), (0.25, -0.25, 0.25)])
+def test_free_electron(kred):
+    s = W.tiny_system(a=7.0, ecut=3.0, natom=2, kpts=[kred], vloc_amp=0.0, nproj_per_atom=0)
+    p = O.build_problem(s, 0, box=(16, 16, 16))
+    assert np.all(p.V == 0.0)
+    w = O.all_eigenvalues(p.dense())
+    ref = free_electron_levels(7.0, 3.0, kred)
+    assert w.size == ref.size
+    assert np.max(np.abs(w - ref)) < 1e-12
+    c = W.random_block(p.basis.npw, 3, seed=11)
+    assert np.allclose(p.apply(c), c * ref_order_kinetic(p), atol=1e-12)
+
+
+def ref_order_kinetic(p):
+    k = p.basis.kred
+    m = p.basis.miller + k
+    return 0.5 * (2 * math.pi / 7.0) ** 2 * (m ** 2).sum(1)
+
+
+def test_constant_potential_shift():
+    s = W.tiny_system(a=6.0, ecut=2.5, natom=2)
+    p = O.build_problem(s, 0, box=(15, 15, 15))
+    v0 = -0.8125
+    p0 = O.Problem(p.basis, np.zeros_like(p.V), p.beta, p.D)
+    p1 = O.Problem(p.basis, np.full_like(p.V, v0), p.beta, p.D)
+    w0 = O.all_eigenvalues(p0.dense())
+    w1 = O.all_eigenvalues(p1.dense())
+    assert np.max(np.abs(w1 - w0 - v0)) < 1e-12
+
+
+def secular_roots(t, w, D):
+    """All eigenvalues of diag(t) + D b b^H from the rank-one secular equation
+    1 + D sum_s w_s/(t_s - e) = 0 over distinct shells t_s with weights w_s = sum |b|^2
+    (Golub 1973), plus the g_s - 1 unperturbed copies in every shell of multiplicity g_s."""
+    order = np.argsort(t)
+    t = t[order]
+    w = w[order]
+    shells, mult, wt = [], [], []
+    for ti, wi in zip(t, w):
+        if shells and abs(ti - shells[-1]) < 1e-10:
+            mult[-1] += 1
+            wt[-1] += wi
+        else:
+            shells.append(ti)
+            mult.append(1)
+            wt.append(wi)
+    ts = np.array(shells)
+    ws = np.array(wt)
+
+    def f(e):
+        return 1.0 + D * np.sum(ws / (ts - e))
+
+    def bisect(lo, hi):
+        flo = f(lo)
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            fm = f(mid)
+            if (fm > 0) == (flo > 0):
+                lo, flo = mid, fm
+            else:
+                hi = mid
+        return 0.5 * (lo + hi)
+
+    roots = []
+    tot = float(ws.sum())
+    eps = 1e-13
+    if D > 0:
+        for i in range(len(ts) - 1):
+            roots.append(bisect(ts[i] + eps, ts[i + 1] - eps))
+        roots.append(bisect(ts[-1] + eps, ts[-1] + D * tot + 1.0))
+    else:
+        roots.append(bisect(ts[0] + D * tot - 1.0, ts[0] - eps))
+        for i in range(len(ts) - 1):
+            roots.append(bisect(ts[i] + eps, ts[i + 1] - eps))
+    for ti, g in zip(ts, mult):
+        roots.extend([ti] * (g - 1))
+    return np.sort(np.array(roots))
+
+
+@pytest.mark.parametrize("D", [0.7, -0.45])
+def test_rank_one_secular_equation(D):
+    s = W.tiny_system(a=6.0, ecut=2.0, natom=1, vloc_amp=0.0, nproj_per_atom=1)
+    s.D[:] = D
+    p = O.build_problem(s, 0, box=(15, 15, 15))
+    b = p.beta[:, 0]
+    w_dense = O.all_eigenvalues(p.dense())
+    roots = secular_roots(p.basis.kinetic.copy(), np.abs(b) ** 2, D)
+    assert roots.size == w_dense.size
+    assert np.max(np.abs(roots - w_dense)) < 1e-10
+
+
+@pytest.fixture(scope="module")
+def tiny_problem():
+    s = W.tiny_system(a=6.5, ecut=2.5, natom=3, kpts=[(0.25, 0.25, -0.25)])
+    return O.build_problem(s, 0, box=(16, 15, 18))
+
+
+def test_hermiticity_naive_apply(tiny_problem):
+    p = tiny_problem
+    phi = W.random_block(p.basis.npw, 1, seed=1)[0]
+    psi = W.random_block(p.basis.npw, 1, seed=2)[0]
+    hpsi = p.apply(psi[None])[0]
+    hphi = p.apply(phi[None])[0]
+    lhs = np.vdot(phi, hpsi)
+    rhs = np.conj(np.vdot(psi, hphi))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_naive_apply_matches_dense(tiny_problem):
+    p = tiny_problem
+    c = W.random_block(p.basis.npw, 4, seed=5)
+    a = p.apply(c)
+    b = O.apply_h_dense(c, p.dense())
+    assert np.max(np.abs(a - b)) < 1e-12 * np.max(np.abs(b))
+    H = p.dense()
+    assert np.max(np.abs(H - H.conj().T)) < 1e-14
+
+
+def test_dft_roundtrip_and_parseval(tiny_problem):
+    p = tiny_problem
+    c = W.random_block(p.basis.npw, 2, seed=9)
+    box = O.scatter_to_box(c, p.basis)
+    r = O.naive_inverse_dft(box)
+    back = O.gather_from_box(O.naive_forward_dft(r), p.basis)
+    assert np.max(np.abs(back - c)) < 1e-13
+    n = np.prod(p.basis.box)
+    assert np.allclose((np.abs(r) ** 2).sum(axis=(1, 2, 3)) / n, (np.abs(c) ** 2).sum(1), rtol=1e-13)
+    # the inverse transform is the library inverse FFT up to the N^3 normalisation
+    assert np.allclose(r, np.fft.ifftn(box, axes=(1, 2, 3)) * n, atol=1e-12)
+
+
+def test_time_reversal():
+    k = (0.25, -0.25, 0.25)
+    s = W.tiny_system(a=6.0, ecut=2.5, natom=2, kpts=[k, tuple(-x for x in k)])
+    w = [O.all_eigenvalues(O.build_problem(s, ik, box=(15, 15, 15)).dense()) for ik in (0, 1)]
+    assert np.max(np.abs(w[0] - w[1])) < 1e-11
+
+
+def test_translation_by_grid_vector():
+    s = W.tiny_system(a=6.0, ecut=2.5, natom=2, kpts=[(0.25, 0.25, 0.25)])
+    box = (15, 15, 15)
+    w0 = O.all_eigenvalues(O.build_problem(s, 0, box=box).dense())
+    t = np.array([2 * 6.0 / 15, -3 * 6.0 / 15, 6.0 / 15])
+    s2 = W.with_(s, pos=s.pos + t)
+    w1 = O.all_eigenvalues(O.build_problem(s2, 0, box=box).dense())
+    assert np.max(np.abs(w0 - w1)) < 1e-11
+
+    # Power of this pin: plant a flipped projector phase (centres at -R while V sits at +R);
+    # the planted operator is not translation invariant.
+    def planted(sys_):
+        p = O.build_problem(sys_, 0, box=box)
+        beta = O.projectors(sys_.lattice, p.basis, -sys_.pos, 4, sys_.proj_alpha)
+        return O.all_eigenvalues(O.Problem(p.basis, p.V, beta, p.D).dense())
+
+    assert np.max(np.abs(planted(s) - planted(s2))) > 1e-6
+
+
+def test_axis_permutation_cubic_gamma():
+    s = W.tiny_system(a=6.0, ecut=2.5, natom=2)
+    box = (15, 15, 15)
+    w0 = O.all_eigenvalues(O.build_problem(s, 0, box=box).dense())
+    perm = [1, 2, 0]
+    D2 = s.D.reshape(-1, 4)[:, [0, 1 + perm[0], 1 + perm[1], 1 + perm[2]]].ravel()
+    s2 = W.with_(s, pos=s.pos[:, perm], D=D2)
+    w1 = O.all_eigenvalues(O.build_problem(s2, 0, box=box).dense())
+    assert np.max(np.abs(w0 - w1)) < 1e-11
+
+
+def test_vloc_continuum_fourier_series():
+    a = 8.0
+    s = W.make_system("v", a, 4.0, 3, 4, seed=21)
+    box = (48, 48, 48)
+    V = O.vloc_for(s, box)
+    VN = O.vloc_fourier_grid(V)
+    _, vol = O.reciprocal_lattice(s.lattice)
+    sig = s.vloc_sigma
+    for m in [(0, 0, 0), (1, 0, 0), (0, -2, 1), (3, 1, -2), (-4, 2, 2)]:
+        G = 2 * math.pi / a * np.array(m, float)
+        ana = (s.vloc_amp * (2 * math.pi * sig ** 2) ** 1.5 / vol
+               * math.exp(-0.5 * sig ** 2 * G @ G) * np.exp(-1j * (s.pos @ G)).sum())
+        got = VN[m[2] % 48, m[1] % 48, m[0] % 48]
+        assert abs(got - ana) < 1e-12, (m, got, ana)
+
+
+def test_vloc_two_forms_agree():
+    s = W.make_system("v", 7.0, 4.0, 3, 4, seed=22)
+    box = (12, 14, 15)
+    a = O.vloc_grid(s.lattice, s.pos, s.vloc_amp, s.vloc_sigma, box)
+    b = O.vloc_grid_orthorhombic(s.lattice, s.pos, s.vloc_amp, s.vloc_sigma, box)
+    assert np.max(np.abs(a - b)) < 1e-13
+
+
+def test_projector_norms_and_orthogonality():
+    s = W.make_system("p", 8.0, 40.0, 1, 4, seed=23)
+    b = O.make_basis(s.lattice, s.ecut, (0, 0, 0), (64, 64, 64))
+    beta = O.projectors(s.lattice, b, s.pos, 4, s.proj_alpha)
+    S = beta.conj().T @ beta
+    assert np.allclose(np.diag(S).real, 1.0, atol=1e-10)
+    assert np.max(np.abs(S - np.diag(np.diag(S)))) < 1e-12
+
+
+def test_inertia_count():
+    s = W.tiny_system(a=6.0, ecut=2.0, natom=2)
+    H = O.build_problem(s, 0, box=(15, 15, 15)).dense()
+    w = O.all_eigenvalues(H)
+    for k in (0, 5, 17, w.size - 3):
+        sigma = 0.5 * (w[k] + w[k + 1]) if k + 1 < w.size else w[-1] + 1
+        assert O.count_below(H, sigma) == k + 1
