@@ -1,0 +1,224 @@
+/*
+ * kss.h -- C ABI of the GB300 plane-wave Kohn-Sham Hamiltonian / Chebyshev-filter library.
+ *
+ * What is computed (arXiv 2507.08578):
+ *   The Kohn-Sham eigenproblem in a plane-wave basis, Hartree atomic units (§1), with
+ *     H = -1/2 nabla^2 + V_loc + sum_i |beta_i> D_i <beta_i|
+ *   the separable nonlocal operator of the nonlocal-Hamiltonian equation (Eq. ham-nl, §5.2) with
+ *   the diagonal h of norm-conserving pseudopotentials, the projector table and the projector
+ *   coefficients ("cprj") kept in memory so that every nonlocal step is a matrix product (§5.2),
+ *   the local part applied by batched FFTs over bands (§5.1), and the lowest bands found by a
+ *   Chebyshev-filtered subspace iteration with Rayleigh-Ritz (§5.1).
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return kss_status.  No C++ exception crosses this boundary.  On failure a
+ *     message is stored in the context (kss_last_error) and outputs are left unspecified.
+ *   - Wavefunction blocks are band-major: band n of a block occupies elements
+ *     [n*ld, n*ld + npw) of an array of complex numbers; ld >= npw.  Complex numbers are
+ *     interleaved (re, im) pairs: complex128 (2 x double) for KSS_PREC_FP64, complex64
+ *     (2 x float) for KSS_PREC_MIXED.
+ *   - Plane-wave order (the "G-sphere"): Miller triples m with 0.5*|k+G|^2 <= ecut, where
+ *     k+G = sum_i (m_i + kappa_i) b_i, sorted ascending by (m3, m2, m1), m1 fastest.
+ *   - Device pointers are CUDA device (or managed) addresses on the context's device; the
+ *     caller owns them and keeps them alive until the work queued on the context stream that
+ *     uses them has finished.  Host pointers are ordinary host memory.
+ *   - All GPU work is queued on the context stream (stream-ordered); calls that return host
+ *     results synchronise that stream before returning.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ *   - There is no CPU fallback: without a usable CUDA device kss_create fails with KSS_ECUDA.
+ */
+#ifndef KSS_H
+#define KSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KSS_VERSION_MAJOR 0
+#define KSS_VERSION_MINOR 1
+
+typedef enum {
+  KSS_OK = 0,
+  KSS_EINVAL = 1,    /* bad argument (null pointer, size out of range, inconsistent sizes) */
+  KSS_ENOMEM = 2,    /* device or host allocation failed */
+  KSS_ECUDA = 3,     /* CUDA / cuSOLVER error, or no usable device */
+  KSS_ENOCONV = 4,   /* eigensolver hit max_iter; outputs hold the last iterate */
+  KSS_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+  KSS_EBUSY = 6,     /* admission refused (memory budget or slot limit) */
+  KSS_ENUMERIC = 7,  /* non-finite values or a failed factorisation */
+  KSS_ENOTSUP = 8    /* valid request this build does not support */
+} kss_status;
+
+typedef enum { KSS_PREC_FP64 = 0, KSS_PREC_MIXED = 1 } kss_precision;
+
+typedef struct kss_ctx_s* kss_ctx;
+typedef struct kss_sys_s* kss_sys;
+typedef struct kss_solver_s* kss_solver;
+
+/* ------------------------------------------------------------------------------------------
+ * Context
+ * ------------------------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to queue work on
+ * (borrowed, must outlive the context) or NULL for a stream the context creates and owns.
+ * Errors: KSS_EINVAL (out == NULL), KSS_ECUDA (no device / bad device index). */
+kss_status kss_create(kss_ctx* out, int device, void* cuda_stream);
+
+/* Destroy a context.  Every system created on it must be destroyed first (KSS_EINVAL otherwise).
+ * Synchronises the stream. */
+kss_status kss_destroy(kss_ctx ctx);
+
+/* Message of the last failed call on this context ("" if none).  Owned by the context; valid
+ * until the next call on it.  Accepts NULL (returns a static message). */
+const char* kss_last_error(kss_ctx ctx);
+
+/* Library version as major*1000 + minor. */
+int kss_version(void);
+
+/* ------------------------------------------------------------------------------------------
+ * Systems: cell, cutoff, k-points, atoms (setup, §1 / §5.2)
+ * ------------------------------------------------------------------------------------------ */
+
+typedef struct {
+  double lattice[9];       /* rows a1, a2, a3 (bohr), row-major */
+  double ecut;             /* plane-wave cutoff (Ha), > 0 */
+  int nk;                  /* number of k-points, >= 1 */
+  const double* kpts_red;  /* host, nk*3 reduced coordinates (copied at setup) */
+  int fft_box[3];          /* FFT grid N1,N2,N3; all 0 => smallest {2,3,5}-smooth N_i >= 4 max|m_i|+1 */
+} kss_cell;
+
+typedef struct {
+  int natom;               /* >= 0 */
+  const double* pos_cart;  /* host, natom*3 Cartesian positions (bohr), copied */
+  double vloc_amp;         /* A of V(r) = A sum_a sum_L exp(-|r-R_a-L|^2/(2 sigma^2)) (Ha) */
+  double vloc_sigma;       /* sigma (bohr), > 0 */
+  int nproj_per_atom;      /* 0, 1 (s) or 4 (s, px, py, pz) */
+  double proj_alpha;       /* form factor exp(-alpha |k+G|^2), > 0 */
+  const double* D;         /* host, natom*nproj_per_atom projector energies (Ha), copied;
+                              index 4a+l for l in (s, px, py, pz) */
+} kss_atoms;
+
+/* Build a system: enumerate the G-sphere of every k-point on the host (the inclusion test is
+ * evaluated in IEEE double without contraction, exactly as written in the convention above),
+ * upload the index maps, and fill on the device the local potential on the FFT grid (full
+ * periodic-image sum of the Gaussians; terms below 1e-20*|A| omitted), the kinetic energies
+ * 0.5|k+G|^2 and the projector table beta_{a,l}(k+G) = c_l q_l exp(-alpha|q|^2) exp(-i q.R_a)
+ * (q_s = 1; c_s, c_p the continuum unit-norm constants).  Library-owned device memory.
+ * Errors: KSS_EINVAL (bad cell/atoms, FFT box too small for the sphere or not {2,3,5}-smooth,
+ * box dimension > 512), KSS_ENOMEM, KSS_ECUDA. */
+kss_status kss_setup(kss_ctx ctx, const kss_cell* cell, const kss_atoms* atoms, kss_sys* out);
+
+kss_status kss_sys_destroy(kss_sys sys);
+
+typedef struct {
+  int nk;
+  int fft_box[3];
+  int nproj;
+  int npw_max;
+  double volume;           /* bohr^3 */
+  double vloc_max;         /* max_j V(r_j) */
+} kss_sys_info;
+
+kss_status kss_sys_info_get(kss_sys sys, kss_sys_info* out);
+
+/* Number of plane waves of k-point ik and a library-owned host copy of its Miller triples
+ * (npw*3 int32, canonical order), valid until the system is destroyed. */
+kss_status kss_sphere(kss_sys sys, int ik, int* npw, const int32_t** miller_host);
+
+/* Copy back from DEVICE memory the index maps the kernels use: miller (npw*3 int32) and the box
+ * offsets (m1 mod N1) + N1*((m2 mod N2) + N2*(m3 mod N3)) (npw int32), into host buffers. */
+kss_status kss_get_maps(kss_sys sys, int ik, int32_t* miller_out, int32_t* offset_out);
+
+/* Copy back from device the local potential V(r_j) (N1*N2*N3 doubles, index j1 + N1*(j2 +
+ * N2*j3), not scaled), the kinetic energies (npw doubles) and the projector table (npw*nproj
+ * complex128, projector-major: element (i, g) at [i*npw + g]).  Any output may be NULL. */
+kss_status kss_get_tables(kss_sys sys, int ik, double* vloc_out, double* kinetic_out,
+                          double* beta_out);
+
+/* Rigorous upper bound of the spectrum of H(k): max T + max(max V, 0) + sum_i max(D_i,0)|beta_i|^2. */
+kss_status kss_upper_bound(kss_sys sys, int ik, double* bound);
+
+/* Device bytes the solver needs for nband bands at this precision (all k-points handled one at
+ * a time), excluding the system tables already allocated. */
+kss_status kss_footprint(kss_sys sys, int nband, kss_precision prec, size_t* bytes);
+
+/* ------------------------------------------------------------------------------------------
+ * Hamiltonian application on a band block (§5.1 batched FFTs; §5.2 Eq. ham-nl)
+ * ------------------------------------------------------------------------------------------ */
+
+/* hpsi = H(k_ik) psi for nb bands.  psi, hpsi: DEVICE, band-major [nb][ld], complex128 for
+ * KSS_PREC_FP64 and complex64 for KSS_PREC_MIXED; they must not overlap.  Steps: projector
+ * coefficients C = beta^H psi; per band, sphere -> box scatter, inverse 3D FFT, x V(r), forward
+ * 3D FFT, box -> sphere gather, + 0.5|k+G|^2 psi; then hpsi += beta (D C).
+ * nb == 0 is a no-op.  Errors: KSS_EINVAL (ik out of range, nb < 0, ld < npw, null pointers). */
+kss_status kss_apply_H(kss_sys sys, int ik, int nb, const void* psi, void* hpsi, int ld,
+                       kss_precision prec);
+
+/* One Chebyshev three-term step fused into the H application:
+ *   out = alpha * H psi + beta * psi + gamma * psi_prev
+ * psi_prev may be NULL (then gamma is ignored) and may alias out (out is written element by
+ * element after psi_prev at the same element is read).  psi must not overlap out. */
+kss_status kss_cheb_step(kss_sys sys, int ik, int nb, const void* psi, const void* psi_prev,
+                         void* out, int ld, double alpha, double beta, double gamma,
+                         kss_precision prec);
+
+/* kss_apply_H with HOST psi/hpsi: copies psi to library-owned device staging, applies H and
+ * copies the result back; synchronises the stream before returning. */
+kss_status kss_apply_H_host(kss_sys sys, int ik, int nb, const void* psi_host, void* hpsi_host,
+                            int ld, kss_precision prec);
+
+/* ------------------------------------------------------------------------------------------
+ * Chebyshev-filtered subspace iteration with Rayleigh-Ritz (§5.1)
+ * ------------------------------------------------------------------------------------------ */
+
+typedef struct {
+  int degree;              /* filter polynomial degree m (>= 1; 0 => 10) */
+  double tol;              /* residual tolerance |H x - lambda x| (Ha) on the wanted bands (<= 0 => 1e-8) */
+  int max_iter;            /* filter iterations (<= 0 => 200) */
+  int nbuffer;             /* extra bands (< 0 => max(4, ceil(nband/10))) */
+  kss_precision prec;
+  uint64_t seed;           /* initial block: Philox4x32-10 uniform(-1,1) re/im from this seed */
+  const void* x0;          /* optional DEVICE warm start, band-major [nb_x0][x0_ld], prec type */
+  int x0_nb;               /* bands in x0 (<= nband+nbuffer; the rest are random) */
+  int x0_ld;
+} kss_solve_opts;
+
+typedef struct {
+  int iters;               /* filter iterations done */
+  long long napply;        /* band H-applications done (bands x applications) */
+  double max_resid;        /* max residual over the wanted bands, last iterate (Ha) */
+  double ms_filter, ms_rr, ms_total;
+  int nb;                  /* block size nband + nbuffer actually used */
+} kss_solve_stats;
+
+/* Solver objects allow stepping one iteration at a time (used by the batched and served
+ * paths).  create: allocates the block buffers and draws / copies the initial block.
+ * Errors: KSS_EINVAL (nband < 1, nband+nbuffer > npw), KSS_ENOMEM. */
+kss_status kss_solver_create(kss_sys sys, int ik, int nband, const kss_solve_opts* opts,
+                             kss_solver* out);
+kss_status kss_solver_destroy(kss_solver s);
+
+/* One iteration.  The first call performs the initial Rayleigh-Ritz on the starting block; each
+ * later call filters (degree m), then Rayleigh-Ritz (FP64 Cholesky of the Gram matrix and FP64
+ * Hermitian eigensolve on the GPU), then residuals.  *converged is set to 1 when every wanted
+ * band has residual <= tol.  Synchronises the stream (the residuals decide convergence). */
+kss_status kss_solver_step(kss_solver s, int* converged);
+
+/* Results of the current iterate: evals/resid host [nband] (may be NULL); evecs DEVICE
+ * band-major [nband][ld] of the solver's precision or NULL; stats may be NULL. */
+kss_status kss_solver_results(kss_solver s, double* evals, double* resid, void* evecs, int ld,
+                              kss_solve_stats* stats);
+
+/* Full solve = create + step until converged or max_iter + results + destroy.
+ * Returns KSS_ENOCONV (outputs still filled) when max_iter is reached. */
+kss_status kss_chebfi_solve(kss_sys sys, int ik, int nband, const kss_solve_opts* opts,
+                            double* evals, void* evecs, int ld, double* resid,
+                            kss_solve_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KSS_H */

@@ -296,18 +296,18 @@ def gather_from_box(box: np.ndarray, basis: Basis) -> np.ndarray:
 def naive_inverse_dft(box: np.ndarray) -> np.ndarray:
     """psi(r_j) = sum_m B(m) e^{+2 pi i sum_i m_i j_i / N_i}: one dense DFT matrix per axis."""
     nb, N3, N2, N1 = box.shape
-    x = np.einsum("ja,nzya->nzyj", _dft_matrix(N1, +1), box)
-    x = np.einsum("ja,nzay->nzjy", _dft_matrix(N2, +1), x)
-    x = np.einsum("ja,nayx->njyx", _dft_matrix(N3, +1), x)
+    x = np.einsum("ja,nzya->nzyj", _dft_matrix(N1, +1), box, optimize=True)
+    x = np.einsum("ja,nzay->nzjy", _dft_matrix(N2, +1), x, optimize=True)
+    x = np.einsum("ja,nayx->njyx", _dft_matrix(N3, +1), x, optimize=True)
     return x
 
 
 def naive_forward_dft(f: np.ndarray) -> np.ndarray:
     """F(m) = N^-3 sum_j f(r_j) e^{-2 pi i sum_i m_i j_i / N_i}."""
     nb, N3, N2, N1 = f.shape
-    x = np.einsum("ma,nzya->nzym", _dft_matrix(N1, -1), f)
-    x = np.einsum("ma,nzay->nzmy", _dft_matrix(N2, -1), x)
-    x = np.einsum("ma,nayx->nmyx", _dft_matrix(N3, -1), x)
+    x = np.einsum("ma,nzya->nzym", _dft_matrix(N1, -1), f, optimize=True)
+    x = np.einsum("ma,nzay->nzmy", _dft_matrix(N2, -1), x, optimize=True)
+    x = np.einsum("ma,nayx->nmyx", _dft_matrix(N3, -1), x, optimize=True)
     return x / (N1 * N2 * N3)
 
 

@@ -1,0 +1,527 @@
+// Host side of the C ABI: contexts, system setup (G-sphere, index maps, tables), queries.
+//
+// Built with -ffp-contract=off: the G-sphere inclusion test below must round exactly as the
+// written expression (no fused multiply-add), so that every implementation that evaluates the
+// same expression in IEEE double selects the same plane waves.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <algorithm>
+#include <memory>
+
+#include "kss_internal.h"
+
+namespace kss {
+
+void fail(kss_status st, const std::string& msg) { throw KssError{st, msg}; }
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+void DevBuf::alloc(size_t n) {
+  release();
+  if (n == 0) return;
+  cudaError_t e = cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    cudaGetLastError();
+    fail(KSS_ENOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed: " +
+                         cudaGetErrorString(e));
+  }
+  bytes = n;
+}
+
+void DevBuf::ensure(size_t n) {
+  if (n > bytes) alloc(n);
+}
+
+static bool smooth235(int n) {
+  if (n < 1) return false;
+  for (int p : {2, 3, 5})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+FftDim make_fft_dim(int N) {
+  FftDim d{};
+  d.N = N;
+  int n = N;
+  // Radix-4 stages first (fewest passes), then 2, 3, 5.
+  while (n % 4 == 0) { d.rad[d.nst++] = 4; n /= 4; }
+  while (n % 2 == 0) { d.rad[d.nst++] = 2; n /= 2; }
+  while (n % 3 == 0) { d.rad[d.nst++] = 3; n /= 3; }
+  while (n % 5 == 0) { d.rad[d.nst++] = 5; n /= 5; }
+  if (n != 1 || d.nst > 10) fail(KSS_EINVAL, "FFT length " + std::to_string(N) + " is not {2,3,5}-smooth");
+  return d;
+}
+
+// Reciprocal rows b_i = (2 pi / vol) (a_j x a_k), scalar formula in a fixed order.
+static void reciprocal(const double* a, double* B, double* vol) {
+  const double a1x = a[0], a1y = a[1], a1z = a[2];
+  const double a2x = a[3], a2y = a[4], a2z = a[5];
+  const double a3x = a[6], a3y = a[7], a3z = a[8];
+  const double c23[3] = {a2y * a3z - a2z * a3y, a2z * a3x - a2x * a3z, a2x * a3y - a2y * a3x};
+  const double c31[3] = {a3y * a1z - a3z * a1y, a3z * a1x - a3x * a1z, a3x * a1y - a3y * a1x};
+  const double c12[3] = {a1y * a2z - a1z * a2y, a1z * a2x - a1x * a2z, a1x * a2y - a1y * a2x};
+  const double v = a1x * c23[0] + a1y * c23[1] + a1z * c23[2];
+  const double f = (2.0 * 3.141592653589793) / v;  // 2 pi in double
+  for (int i = 0; i < 3; ++i) {
+    B[0 + i] = f * c23[i];
+    B[3 + i] = f * c31[i];
+    B[6 + i] = f * c12[i];
+  }
+  *vol = v;
+}
+
+// q = sum_i (m_i + kappa_i) b_i, each Cartesian component summed left to right.
+static inline void qvec(const double* B, const double* kr, int m1, int m2, int m3, double* q) {
+  const double u1 = (double)m1 + kr[0];
+  const double u2 = (double)m2 + kr[1];
+  const double u3 = (double)m3 + kr[2];
+  q[0] = u1 * B[0] + u2 * B[3] + u3 * B[6];
+  q[1] = u1 * B[1] + u2 * B[4] + u3 * B[7];
+  q[2] = u1 * B[2] + u2 * B[5] + u3 * B[8];
+}
+
+static inline double half_q2(const double* q) {
+  return 0.5 * ((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]);
+}
+
+// Enumerate the sphere in canonical order (m3, m2, m1 ascending).  Loops visit m3, then m2, then
+// m1 in ascending order; the m1 loop is limited to a window around the row's closest approach
+// (widened by 2) and every candidate passes the exact inclusion test.
+static void enumerate_sphere(const double* lat, const double* B, double ecut, const double* kr,
+                             std::vector<int32_t>& miller) {
+  miller.clear();
+  const double gmax = std::sqrt(2.0 * ecut);
+  int lo[3], hi[3];
+  for (int i = 0; i < 3; ++i) {
+    const double an = std::sqrt(lat[3 * i] * lat[3 * i] + lat[3 * i + 1] * lat[3 * i + 1] +
+                                lat[3 * i + 2] * lat[3 * i + 2]);
+    const double R = gmax * an / (2.0 * 3.141592653589793);
+    lo[i] = (int)std::floor(-R - kr[i]) - 1;
+    hi[i] = (int)std::ceil(R - kr[i]) + 1;
+  }
+  // Along b1, |q| is minimised at u1 = -(w . b1)/|b1|^2 where w is the (m2,m3) part of q.
+  const double b1n2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+  const double b1n = std::sqrt(b1n2);
+  for (int m3 = lo[2]; m3 <= hi[2]; ++m3) {
+    for (int m2 = lo[1]; m2 <= hi[1]; ++m2) {
+      const double u2 = (double)m2 + kr[1], u3 = (double)m3 + kr[2];
+      const double w[3] = {u2 * B[3] + u3 * B[6], u2 * B[4] + u3 * B[7], u2 * B[5] + u3 * B[8]};
+      const double t = -(w[0] * B[0] + w[1] * B[1] + w[2] * B[2]) / b1n2;  // u1 at closest approach
+      const double perp2 = (w[0] + t * B[0]) * (w[0] + t * B[0]) +
+                           (w[1] + t * B[1]) * (w[1] + t * B[1]) +
+                           (w[2] + t * B[2]) * (w[2] + t * B[2]);
+      const double rem = 2.0 * ecut - perp2;
+      if (rem < -1e-6 * (2.0 * ecut + 1.0)) continue;  // row entirely outside (with margin)
+      const double half = std::sqrt(std::max(rem, 0.0)) / b1n;
+      int a = (int)std::floor(t - half - kr[0]) - 2, b = (int)std::ceil(t + half - kr[0]) + 2;
+      a = std::max(a, lo[0]);
+      b = std::min(b, hi[0]);
+      for (int m1 = a; m1 <= b; ++m1) {
+        double q[3];
+        qvec(B, kr, m1, m2, m3, q);
+        if (half_q2(q) <= ecut) {
+          miller.push_back(m1);
+          miller.push_back(m2);
+          miller.push_back(m3);
+        }
+      }
+    }
+  }
+}
+
+template <typename F>
+static kss_status guard(kss_ctx ctx, F&& f) {
+  try {
+    f();
+    if (ctx) ctx->err.clear();
+    return KSS_OK;
+  } catch (const KssError& e) {
+    if (ctx) ctx->err = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->err = "host allocation failed";
+    return KSS_ENOMEM;
+  } catch (...) {
+    if (ctx) ctx->err = "unexpected internal error";
+    return KSS_ECUDA;
+  }
+}
+
+}  // namespace kss
+
+using namespace kss;
+
+namespace kss {
+void ctx_release_solver(kss_ctx ctx);  // solver.cu
+}
+
+extern "C" {
+
+int kss_version(void) { return KSS_VERSION_MAJOR * 1000 + KSS_VERSION_MINOR; }
+
+const char* kss_last_error(kss_ctx ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+kss_status kss_create(kss_ctx* out, int device, void* cuda_stream) {
+  if (!out) return KSS_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return KSS_ECUDA;
+  }
+  if (device < 0 || device >= n) return KSS_ECUDA;
+  kss_ctx ctx = new (std::nothrow) kss_ctx_s();
+  if (!ctx) return KSS_ENOMEM;
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return KSS_ECUDA;
+  }
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return KSS_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  *out = ctx;
+  return KSS_OK;
+}
+
+kss_status kss_destroy(kss_ctx ctx) {
+  if (!ctx) return KSS_EINVAL;
+  if (ctx->nsys > 0) {
+    ctx->err = "destroy every system before its context";
+    return KSS_EINVAL;
+  }
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  ctx_release_solver(ctx);
+  ctx->ws_local.release();
+  ctx->ws_gemm.release();
+  ctx->ws_cprj.release();
+  ctx->stage_in.release();
+  ctx->stage_out.release();
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return KSS_OK;
+}
+
+kss_status kss_setup(kss_ctx ctx, const kss_cell* cell, const kss_atoms* atoms, kss_sys* out) {
+  if (!ctx) return KSS_EINVAL;
+  return guard(ctx, [&] {
+    KSS_REQUIRE(cell && atoms && out, "kss_setup: null argument");
+    *out = nullptr;
+    KSS_REQUIRE(cell->ecut > 0 && std::isfinite(cell->ecut), "ecut must be positive");
+    KSS_REQUIRE(cell->nk >= 1 && cell->kpts_red, "need at least one k-point");
+    KSS_REQUIRE(atoms->natom >= 0, "natom < 0");
+    KSS_REQUIRE(atoms->natom == 0 || atoms->pos_cart, "pos_cart is null");
+    KSS_REQUIRE(atoms->nproj_per_atom == 0 || atoms->nproj_per_atom == 1 ||
+                    atoms->nproj_per_atom == 4,
+                "nproj_per_atom must be 0, 1 or 4");
+    KSS_REQUIRE(atoms->vloc_sigma > 0, "vloc_sigma must be positive");
+    KSS_REQUIRE(atoms->nproj_per_atom == 0 || atoms->natom == 0 ||
+                    (atoms->D && atoms->proj_alpha > 0),
+                "projectors need D and proj_alpha > 0");
+    KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    std::unique_ptr<kss_sys_s> s(new kss_sys_s());
+    s->ctx = ctx;
+    std::memcpy(s->lat, cell->lattice, sizeof(s->lat));
+    reciprocal(s->lat, s->B, &s->vol);
+    KSS_REQUIRE(std::isfinite(s->vol) && s->vol > 0, "lattice must be right-handed and non-singular");
+    s->ecut = cell->ecut;
+    s->natom = atoms->natom;
+    s->nppa = atoms->natom ? atoms->nproj_per_atom : 0;
+    s->nproj = s->natom * s->nppa;
+    s->pos.assign(atoms->pos_cart, atoms->pos_cart + 3 * s->natom);
+    if (s->nproj) s->D.assign(atoms->D, atoms->D + s->nproj);
+    s->vamp = atoms->vloc_amp;
+    s->vsig = atoms->vloc_sigma;
+    s->alpha = atoms->proj_alpha;
+
+    // G-spheres.
+    s->k.resize(cell->nk);
+    int mmax[3] = {0, 0, 0};
+    for (int ik = 0; ik < cell->nk; ++ik) {
+      KData& kd = s->k[ik];
+      for (int i = 0; i < 3; ++i) kd.kred[i] = cell->kpts_red[3 * ik + i];
+      enumerate_sphere(s->lat, s->B, s->ecut, kd.kred, kd.miller);
+      kd.npw = (int)(kd.miller.size() / 3);
+      KSS_REQUIRE(kd.npw > 0, "empty G-sphere");
+      for (int i = 0; i < 3; ++i) {
+        int lo = 1 << 30, hi = -(1 << 30);
+        for (int g = 0; g < kd.npw; ++g) {
+          lo = std::min(lo, kd.miller[3 * g + i]);
+          hi = std::max(hi, kd.miller[3 * g + i]);
+          mmax[i] = std::max(mmax[i], std::abs(kd.miller[3 * g + i]));
+        }
+        kd.lo[i] = lo;
+        kd.W[i] = hi - lo + 1;
+      }
+    }
+    // FFT box.
+    const bool dflt = cell->fft_box[0] == 0 && cell->fft_box[1] == 0 && cell->fft_box[2] == 0;
+    for (int i = 0; i < 3; ++i) {
+      if (dflt) {
+        int n = 4 * mmax[i] + 1;
+        while (!smooth235(n)) ++n;
+        s->N[i] = n;
+      } else {
+        s->N[i] = cell->fft_box[i];
+      }
+      KSS_REQUIRE(s->N[i] >= 2 && s->N[i] <= 256 && smooth235(s->N[i]),
+                  "FFT box dimensions must be {2,3,5}-smooth and in [2, 256]");
+      for (auto& kd : s->k)
+        KSS_REQUIRE(kd.W[i] <= s->N[i], "FFT box does not hold the G-sphere");
+      s->dim[i] = make_fft_dim(s->N[i]);
+    }
+    const int N1 = s->N[0], N2 = s->N[1], N3 = s->N[2];
+    const int N1p = N1 + 1;  // padded row stride of the x-pencil tiles
+
+    // Twiddles e^{-2 pi i k / N} (long double angles, rounded once).
+    for (int d = 0; d < 3; ++d) {
+      const int N = s->N[d];
+      std::vector<double> tw(2 * N);
+      std::vector<float> tw32(2 * N);
+      for (int kk = 0; kk < N; ++kk) {
+        const long double ang = -2.0L * 3.141592653589793238462643383279502884L * kk / N;
+        tw[2 * kk] = (double)cosl(ang);
+        tw[2 * kk + 1] = (double)sinl(ang);
+        tw32[2 * kk] = (float)cosl(ang);
+        tw32[2 * kk + 1] = (float)sinl(ang);
+      }
+      s->d_tw64[d].alloc(tw.size() * sizeof(double));
+      s->d_tw32[d].alloc(tw32.size() * sizeof(float));
+      KSS_CHECK_CUDA(cudaMemcpy(s->d_tw64[d].p, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice));
+      KSS_CHECK_CUDA(cudaMemcpy(s->d_tw32[d].p, tw32.data(), tw32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+
+    // Local potential.
+    const size_t nr = (size_t)N1 * N2 * N3;
+    s->d_V64.alloc(nr * sizeof(double));
+    s->d_Vx64.alloc(nr * sizeof(double));
+    s->d_Vx32.alloc(nr * sizeof(float));
+    launch_vloc(s.get(), ctx->stream);
+    launch_vloc_views(s.get(), ctx->stream);
+    s->vmax = device_max(s->d_V64.as<double>(), nr, ctx->stream);
+
+    if (s->nproj) {
+      s->d_D64.alloc(s->nproj * sizeof(double));
+      s->d_D32.alloc(s->nproj * sizeof(float));
+      std::vector<float> d32(s->D.begin(), s->D.end());
+      KSS_CHECK_CUDA(cudaMemcpy(s->d_D64.p, s->D.data(), s->nproj * sizeof(double), cudaMemcpyHostToDevice));
+      KSS_CHECK_CUDA(cudaMemcpy(s->d_D32.p, d32.data(), s->nproj * sizeof(float), cudaMemcpyHostToDevice));
+    }
+
+    // Per-k tables.
+    for (auto& kd : s->k) {
+      const int npw = kd.npw;
+      std::vector<int32_t> off(npw), tile(npw);
+      std::vector<double> kin(npw), q(3 * npw);
+      std::vector<float> kin32(npw);
+      kd.zstart.assign(kd.W[2] + 1, 0);
+      kd.rowrange.assign(2 * kd.W[2], 0);
+      for (int u3 = 0; u3 < kd.W[2]; ++u3) { kd.rowrange[2 * u3] = 1 << 30; kd.rowrange[2 * u3 + 1] = -1; }
+      kd.tmax = 0;
+      for (int g = 0; g < npw; ++g) {
+        const int m1 = kd.miller[3 * g], m2 = kd.miller[3 * g + 1], m3 = kd.miller[3 * g + 2];
+        const int j1 = ((m1 % N1) + N1) % N1, j2 = ((m2 % N2) + N2) % N2, j3 = ((m3 % N3) + N3) % N3;
+        off[g] = j1 + N1 * (j2 + N2 * j3);
+        const int u2 = m2 - kd.lo[1], u3 = m3 - kd.lo[2];
+        tile[g] = u2 * N1p + j1;
+        kd.zstart[u3 + 1] += 1;
+        kd.rowrange[2 * u3] = std::min(kd.rowrange[2 * u3], u2);
+        kd.rowrange[2 * u3 + 1] = std::max(kd.rowrange[2 * u3 + 1], u2);
+        double qq[3];
+        qvec(s->B, kd.kred, m1, m2, m3, qq);
+        kin[g] = half_q2(qq);
+        kin32[g] = (float)kin[g];
+        kd.tmax = std::max(kd.tmax, kin[g]);
+        q[3 * g] = qq[0];
+        q[3 * g + 1] = qq[1];
+        q[3 * g + 2] = qq[2];
+      }
+      for (int u3 = 0; u3 < kd.W[2]; ++u3) kd.zstart[u3 + 1] += kd.zstart[u3];
+      kd.d_miller.alloc(kd.miller.size() * 4);
+      kd.d_offset.alloc(npw * 4);
+      kd.d_tileidx.alloc(npw * 4);
+      kd.d_zstart.alloc(kd.zstart.size() * 4);
+      kd.d_rowrange.alloc(kd.rowrange.size() * 4);
+      kd.d_kin64.alloc(npw * 8);
+      kd.d_kin32.alloc(npw * 4);
+      kd.d_q.alloc(3 * npw * 8);
+      KSS_CHECK_CUDA(cudaMemcpy(kd.d_miller.p, kd.miller.data(), kd.miller.size() * 4, cudaMemcpyHostToDevice));
+      KSS_CHECK_CUDA(cudaMemcpy(kd.d_offset.p, off.data(), npw * 4, cudaMemcpyHostToDevice));
+      KSS_CHECK_CUDA(cudaMemcpy(kd.d_tileidx.p, tile.data(), npw * 4, cudaMemcpyHostToDevice));
+      KSS_CHECK_CUDA(cudaMemcpy(kd.d_zstart.p, kd.zstart.data(), kd.zstart.size() * 4, cudaMemcpyHostToDevice));
+      KSS_CHECK_CUDA(cudaMemcpy(kd.d_rowrange.p, kd.rowrange.data(), kd.rowrange.size() * 4, cudaMemcpyHostToDevice));
+      KSS_CHECK_CUDA(cudaMemcpy(kd.d_kin64.p, kin.data(), npw * 8, cudaMemcpyHostToDevice));
+      KSS_CHECK_CUDA(cudaMemcpy(kd.d_kin32.p, kin32.data(), npw * 4, cudaMemcpyHostToDevice));
+      KSS_CHECK_CUDA(cudaMemcpy(kd.d_q.p, q.data(), 3 * npw * 8, cudaMemcpyHostToDevice));
+      double nl = 0;
+      if (s->nproj) {
+        kd.d_beta64.alloc((size_t)npw * s->nproj * 16);
+        kd.d_beta32.alloc((size_t)npw * s->nproj * 8);
+        launch_projectors(s.get(), kd, ctx->stream);
+        convert_f64_to_f32(kd.d_beta64.as<double>(), kd.d_beta32.as<float>(),
+                           (size_t)npw * s->nproj * 2, ctx->stream);
+        projector_norms(kd.d_beta64.as<double>(), npw, s->nproj, kd.beta_norm2, ctx->stream);
+        for (int i = 0; i < s->nproj; ++i) nl += std::max(s->D[i], 0.0) * kd.beta_norm2[i];
+      }
+      kd.bound = kd.tmax + std::max(s->vmax, 0.0) + nl;
+    }
+    KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    KSS_CHECK_CUDA(cudaGetLastError());
+    ctx->nsys += 1;
+    *out = s.release();
+  });
+}
+
+kss_status kss_sys_destroy(kss_sys sys) {
+  if (!sys) return KSS_EINVAL;
+  kss_ctx ctx = sys->ctx;
+  if (sys->nsolvers > 0) {
+    ctx->err = "destroy every solver of a system before the system";
+    return KSS_EINVAL;
+  }
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  delete sys;
+  ctx->nsys -= 1;
+  return KSS_OK;
+}
+
+kss_status kss_sys_info_get(kss_sys sys, kss_sys_info* out) {
+  if (!sys || !out) return KSS_EINVAL;
+  out->nk = (int)sys->k.size();
+  for (int i = 0; i < 3; ++i) out->fft_box[i] = sys->N[i];
+  out->nproj = sys->nproj;
+  int m = 0;
+  for (auto& kd : sys->k) m = std::max(m, kd.npw);
+  out->npw_max = m;
+  out->volume = sys->vol;
+  out->vloc_max = sys->vmax;
+  return KSS_OK;
+}
+
+kss_status kss_sphere(kss_sys sys, int ik, int* npw, const int32_t** miller_host) {
+  if (!sys || !npw) return KSS_EINVAL;
+  if (ik < 0 || ik >= (int)sys->k.size()) {
+    sys->ctx->err = "k-point index out of range";
+    return KSS_EINVAL;
+  }
+  *npw = sys->k[ik].npw;
+  if (miller_host) *miller_host = sys->k[ik].miller.data();
+  return KSS_OK;
+}
+
+kss_status kss_get_maps(kss_sys sys, int ik, int32_t* miller_out, int32_t* offset_out) {
+  if (!sys) return KSS_EINVAL;
+  return guard(sys->ctx, [&] {
+    KSS_REQUIRE(ik >= 0 && ik < (int)sys->k.size(), "k-point index out of range");
+    KData& kd = sys->k[ik];
+    KSS_CHECK_CUDA(cudaSetDevice(sys->ctx->device));
+    KSS_CHECK_CUDA(cudaStreamSynchronize(sys->ctx->stream));
+    if (miller_out)
+      KSS_CHECK_CUDA(cudaMemcpy(miller_out, kd.d_miller.p, (size_t)kd.npw * 12, cudaMemcpyDeviceToHost));
+    if (offset_out)
+      KSS_CHECK_CUDA(cudaMemcpy(offset_out, kd.d_offset.p, (size_t)kd.npw * 4, cudaMemcpyDeviceToHost));
+  });
+}
+
+kss_status kss_get_tables(kss_sys sys, int ik, double* vloc_out, double* kinetic_out,
+                          double* beta_out) {
+  if (!sys) return KSS_EINVAL;
+  return guard(sys->ctx, [&] {
+    KSS_REQUIRE(ik >= 0 && ik < (int)sys->k.size(), "k-point index out of range");
+    KData& kd = sys->k[ik];
+    KSS_CHECK_CUDA(cudaSetDevice(sys->ctx->device));
+    KSS_CHECK_CUDA(cudaStreamSynchronize(sys->ctx->stream));
+    if (vloc_out)
+      KSS_CHECK_CUDA(cudaMemcpy(vloc_out, sys->d_V64.p, sys->d_V64.bytes, cudaMemcpyDeviceToHost));
+    if (kinetic_out)
+      KSS_CHECK_CUDA(cudaMemcpy(kinetic_out, kd.d_kin64.p, (size_t)kd.npw * 8, cudaMemcpyDeviceToHost));
+    if (beta_out && sys->nproj)
+      KSS_CHECK_CUDA(cudaMemcpy(beta_out, kd.d_beta64.p, kd.d_beta64.bytes, cudaMemcpyDeviceToHost));
+  });
+}
+
+kss_status kss_upper_bound(kss_sys sys, int ik, double* bound) {
+  if (!sys || !bound) return KSS_EINVAL;
+  if (ik < 0 || ik >= (int)sys->k.size()) return KSS_EINVAL;
+  *bound = sys->k[ik].bound;
+  return KSS_OK;
+}
+
+kss_status kss_apply_H(kss_sys sys, int ik, int nb, const void* psi, void* hpsi, int ld,
+                       kss_precision prec) {
+  if (!sys) return KSS_EINVAL;
+  return guard(sys->ctx, [&] {
+    KSS_CHECK_CUDA(cudaSetDevice(sys->ctx->device));
+    apply_h(sys, ik, nb, psi, nullptr, hpsi, ld, ChebCoef{1.0, 0.0, 0.0}, prec);
+  });
+}
+
+kss_status kss_cheb_step(kss_sys sys, int ik, int nb, const void* psi, const void* psi_prev,
+                         void* out, int ld, double alpha, double beta, double gamma,
+                         kss_precision prec) {
+  if (!sys) return KSS_EINVAL;
+  return guard(sys->ctx, [&] {
+    KSS_CHECK_CUDA(cudaSetDevice(sys->ctx->device));
+    apply_h(sys, ik, nb, psi, psi_prev, out, ld, ChebCoef{alpha, beta, psi_prev ? gamma : 0.0},
+            prec);
+  });
+}
+
+kss_status kss_apply_H_host(kss_sys sys, int ik, int nb, const void* psi_host, void* hpsi_host,
+                            int ld, kss_precision prec) {
+  if (!sys) return KSS_EINVAL;
+  kss_ctx ctx = sys->ctx;
+  return guard(ctx, [&] {
+    KSS_REQUIRE(ik >= 0 && ik < (int)sys->k.size(), "k-point index out of range");
+    KSS_REQUIRE(nb >= 0 && ld >= sys->k[ik].npw, "bad nb or ld");
+    if (nb == 0) return;
+    KSS_REQUIRE(psi_host && hpsi_host, "null buffer");
+    KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    const size_t bytes = (size_t)nb * ld * (prec == KSS_PREC_FP64 ? 16 : 8);
+    ctx->stage_in.ensure(bytes);
+    ctx->stage_out.ensure(bytes);
+    KSS_CHECK_CUDA(cudaMemcpyAsync(ctx->stage_in.p, psi_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    apply_h(sys, ik, nb, ctx->stage_in.p, nullptr, ctx->stage_out.p, ld, ChebCoef{1.0, 0.0, 0.0},
+            prec);
+    KSS_CHECK_CUDA(cudaMemcpyAsync(hpsi_host, ctx->stage_out.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+kss_status kss_footprint(kss_sys sys, int nband, kss_precision prec, size_t* bytes) {
+  if (!sys || !bytes || nband < 1) return KSS_EINVAL;
+  size_t m = 0;
+  const size_t es = prec == KSS_PREC_FP64 ? 16 : 8;
+  for (size_t ik = 0; ik < sys->k.size(); ++ik) {
+    const int npw = sys->k[ik].npw;
+    const int nb = std::min(npw, nband + std::max(4, (nband + 9) / 10));
+    size_t b = 4 * (size_t)npw * nb * es;                       // four band blocks
+    if (prec == KSS_PREC_MIXED) b += 2 * (size_t)npw * nb * 16; // FP64 refinement blocks
+    b += 3 * (size_t)nb * nb * 16;                              // Gram / projected H / work
+    b += local_workspace_bytes(sys, (int)ik, nb, prec);
+    m = std::max(m, b);
+  }
+  *bytes = m;
+  return KSS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,269 @@
+// Complex GEMMs on the CUDA cores (FP64 and FP32), for the shapes of the eigensolver:
+//   gemm_cn: C = alpha A^H B + beta C   (projector coefficients beta^H psi, Gram and projected-H
+//            matrices Y^H Y, Y^H HY; K = npw is long, so K is split across CTAs and the partial
+//            sums are reduced in a fixed order, which keeps results bitwise reproducible)
+//   gemm_nn: C = alpha A B + beta C     (nonlocal accumulation beta C', subspace rotations Y Q)
+// All matrices are column-major; a band block [nb][ld] is an npw x nb matrix with leading
+// dimension ld.  On GB300 the FP64 pipe (about 1.2 TFLOP/s) bounds these kernels long before
+// shared memory or HBM does; the FP32 instantiation is the CUDA-core form of the mixed path.
+#include <algorithm>
+
+#include "kss_internal.h"
+
+namespace kss {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 8;
+
+template <typename T> struct CT;
+template <> struct CT<double> { using C = double2; };
+template <> struct CT<float> { using C = float2; };
+
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_cn_partial(int M, int N, int K, const typename CT<T>::C* __restrict__ A,
+                                                       long long lda, const typename CT<T>::C* __restrict__ B,
+                                                       long long ldb, typename CT<T>::C* __restrict__ P,
+                                                       int kchunk) {
+  using C = typename CT<T>::C;
+  __shared__ C As[BK][BM];
+  __shared__ C Bs[BK][BN];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  T accr[4][4], acci[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) accr[r][c] = acci[r][c] = 0;
+  const int li = tid >> 2, lk = (tid & 3) * 2;
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int k = k0 + lk + e;
+      const int gi = i0 + li, gj = j0 + li;
+      C a = {0, 0}, b = {0, 0};
+      if (k < kend && gi < M) a = A[gi * lda + k];
+      if (k < kend && gj < N) b = B[gj * ldb + k];
+      As[lk + e][li] = a;
+      Bs[lk + e][li] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      C a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          // conj(a) * b
+          accr[r][c] += a[r].x * b[c].x + a[r].y * b[c].y;
+          acci[r][c] += a[r].x * b[c].y - a[r].y * b[c].x;
+        }
+    }
+    __syncthreads();
+  }
+  C* Pz = P + (size_t)blockIdx.z * M * N;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
+      if (i < M && j < N) Pz[(size_t)j * M + i] = C{accr[r][c], acci[r][c]};
+    }
+}
+
+template <typename T>
+__global__ void gemm_reduce(int M, int N, int nsplit, const typename CT<T>::C* __restrict__ P,
+                            typename CT<T>::C* __restrict__ Cm, long long ldc, T ar, T ai, T br,
+                            T bi) {
+  using C = typename CT<T>::C;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)M * N) return;
+  const int i = (int)(idx % M), j = (int)(idx / M);
+  T sr = 0, si = 0;
+  for (int z = 0; z < nsplit; ++z) {
+    const C p = P[(size_t)z * M * N + idx];
+    sr += p.x;
+    si += p.y;
+  }
+  C out;
+  out.x = ar * sr - ai * si;
+  out.y = ar * si + ai * sr;
+  C* dst = Cm + (size_t)j * ldc + i;
+  if (br != 0 || bi != 0) {
+    const C o = *dst;
+    out.x += br * o.x - bi * o.y;
+    out.y += br * o.y + bi * o.x;
+  }
+  *dst = out;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_nn_kernel(int M, int N, int K, const typename CT<T>::C* __restrict__ A,
+                                                      long long lda, const typename CT<T>::C* __restrict__ B,
+                                                      long long ldb, typename CT<T>::C* __restrict__ Cm,
+                                                      long long ldc, T ar, T ai, T br, T bi) {
+  using C = typename CT<T>::C;
+  __shared__ C As[BK][BM];
+  __shared__ C Bs[BK][BN];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
+  T accr[4][4], acci[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) accr[r][c] = acci[r][c] = 0;
+  const int ai_ = tid & 63, ak = tid >> 6;           // A tile: i fastest
+  const int bj = tid >> 2, bk = (tid & 3) * 2;       // B tile: k fastest
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int k = k0 + ak + 4 * e;
+      const int gi = i0 + ai_;
+      C a = {0, 0};
+      if (k < K && gi < M) a = A[(size_t)k * lda + gi];
+      As[ak + 4 * e][ai_] = a;
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int k = k0 + bk + e;
+      const int gj = j0 + bj;
+      C b = {0, 0};
+      if (k < K && gj < N) b = B[(size_t)gj * ldb + k];
+      Bs[bk + e][bj] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      C a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][tx + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][ty + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          accr[r][c] += a[r].x * b[c].x - a[r].y * b[c].y;
+          acci[r][c] += a[r].x * b[c].y + a[r].y * b[c].x;
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = i0 + tx + 16 * r, j = j0 + ty + 16 * c;
+      if (i < M && j < N) {
+        C* dst = Cm + (size_t)j * ldc + i;
+        C out;
+        out.x = ar * accr[r][c] - ai * acci[r][c];
+        out.y = ar * acci[r][c] + ai * accr[r][c];
+        if (br != 0 || bi != 0) {
+          const C o = *dst;
+          out.x += br * o.x - bi * o.y;
+          out.y += br * o.y + bi * o.x;
+        }
+        *dst = out;
+      }
+    }
+}
+
+template <typename T>
+__global__ void scale_rows_kernel(int M, int N, typename CT<T>::C* __restrict__ Cm, long long ldc,
+                                  const T* __restrict__ d, T s) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)M * N) return;
+  const int i = (int)(idx % M), j = (int)(idx / M);
+  const T f = d[i] * s;
+  typename CT<T>::C& e = Cm[(size_t)j * ldc + i];
+  e.x *= f;
+  e.y *= f;
+}
+
+int sm_count(kss_ctx ctx) {
+  static int n = 0;
+  if (!n) {
+    int v = 0;
+    KSS_CHECK_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device));
+    n = v > 0 ? v : 1;
+  }
+  return n;
+}
+
+template <typename T>
+void run_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+            void* Cm, int ldc, double ar, double ai, double br, double bi) {
+  using C = typename CT<T>::C;
+  const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  const int tiles = tm * tn;
+  const int target = 4 * sm_count(ctx);
+  int splits = std::max(1, std::min((target + tiles - 1) / tiles, (K + 63) / 64));
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  splits = (K + kchunk - 1) / kchunk;
+  ctx->ws_gemm.ensure((size_t)splits * M * N * sizeof(C));
+  gemm_cn_partial<T><<<dim3(tm, tn, splits), 256, 0, ctx->stream>>>(
+      M, N, K, (const C*)A, lda, (const C*)B, ldb, ctx->ws_gemm.as<C>(), kchunk);
+  const long long mn = (long long)M * N;
+  gemm_reduce<T><<<(unsigned)((mn + 255) / 256), 256, 0, ctx->stream>>>(
+      M, N, splits, ctx->ws_gemm.as<C>(), (C*)Cm, ldc, (T)ar, (T)ai, (T)br, (T)bi);
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void run_nn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+            void* Cm, int ldc, double ar, double ai, double br, double bi) {
+  using C = typename CT<T>::C;
+  const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  gemm_nn_kernel<T><<<dim3(tm, tn), 256, 0, ctx->stream>>>(M, N, K, (const C*)A, lda, (const C*)B,
+                                                           ldb, (C*)Cm, ldc, (T)ar, (T)ai, (T)br, (T)bi);
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+void gemm_cn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda, const void* B,
+             int ldb, void* C, int ldc, double ar, double ai, double br, double bi) {
+  if (M <= 0 || N <= 0) return;
+  KSS_REQUIRE(K >= 0 && lda >= K && ldb >= K && ldc >= M, "gemm_cn: bad leading dimension");
+  if (K == 0) {
+    // C = beta C
+    KSS_REQUIRE(br == 0 && bi == 0, "gemm_cn: K == 0 with beta != 0 is not supported");
+    const size_t es = fp64 ? 16 : 8;
+    KSS_CHECK_CUDA(cudaMemset2DAsync(C, (size_t)ldc * es, 0, (size_t)M * es, N, ctx->stream));
+    return;
+  }
+  if (fp64) run_cn<double>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi);
+  else run_cn<float>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi);
+}
+
+void gemm_nn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda, const void* B,
+             int ldb, void* C, int ldc, double ar, double ai, double br, double bi) {
+  if (M <= 0 || N <= 0) return;
+  KSS_REQUIRE(K >= 0 && lda >= M && ldb >= K && ldc >= M, "gemm_nn: bad leading dimension");
+  if (fp64) run_nn<double>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi);
+  else run_nn<float>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi);
+}
+
+void scale_rows(bool fp64, int M, int N, void* C, int ldc, const void* d, double s,
+                cudaStream_t st) {
+  const long long mn = (long long)M * N;
+  if (!mn) return;
+  if (fp64)
+    scale_rows_kernel<double><<<(unsigned)((mn + 255) / 256), 256, 0, st>>>(M, N, (double2*)C, ldc,
+                                                                            (const double*)d, s);
+  else
+    scale_rows_kernel<float><<<(unsigned)((mn + 255) / 256), 256, 0, st>>>(M, N, (float2*)C, ldc,
+                                                                          (const float*)d, (float)s);
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+}  // namespace kss

@@ -1,0 +1,153 @@
+// Internal declarations shared by the library's translation units.  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/kss.h"
+
+namespace kss {
+
+// Errors are thrown as KssError inside the library and turned into a kss_status (with the
+// message stored in the context) at the ABI edge.  Nothing throws across extern "C".
+struct KssError {
+  kss_status st;
+  std::string msg;
+};
+
+[[noreturn]] void fail(kss_status st, const std::string& msg);
+
+#define KSS_CHECK_CUDA(call)                                                              \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      ::kss::fail(KSS_ECUDA, std::string(#call) + " failed: " + cudaGetErrorString(e_));  \
+  } while (0)
+
+#define KSS_REQUIRE(cond, msg)                          \
+  do {                                                  \
+    if (!(cond)) ::kss::fail(KSS_EINVAL, (msg));        \
+  } while (0)
+
+// Owning device allocation (cudaMalloc / cudaFree).  Move-only.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release();
+  void alloc(size_t n);           // exact size, discards contents
+  void ensure(size_t n);          // grow-only, discards contents when it grows
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// One radix-{2,3,4,5} factorisation of a transform length (Stockham stages in order).
+struct FftDim {
+  int N;
+  int nst;
+  int rad[10];
+};
+FftDim make_fft_dim(int N);  // N must be {2,3,5}-smooth, 1 < N <= 256
+
+// Per-k-point data.
+struct KData {
+  double kred[3];
+  int npw = 0;
+  int lo[3], W[3];                 // sphere bounding box: m_i in [lo_i, lo_i + W_i)
+  std::vector<int32_t> miller;     // host copy, npw*3
+  std::vector<int32_t> zstart;     // W3 + 1: sphere index range of each z-slice
+  std::vector<int32_t> rowrange;   // 2*W3: [first, last] row u2 present in each z-slice
+  DevBuf d_miller, d_offset, d_tileidx, d_zstart, d_rowrange;
+  DevBuf d_kin64, d_kin32;         // 0.5 |k+G|^2
+  DevBuf d_beta64, d_beta32;       // projector-major [nproj][npw] complex
+  DevBuf d_q;                      // Cartesian k+G, npw*3 doubles (setup only)
+  double tmax = 0;
+  double bound = 0;                // rigorous spectral upper bound
+  std::vector<double> beta_norm2;  // |beta_i|^2 per projector
+};
+
+}  // namespace kss
+
+struct kss_ctx_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  int nsys = 0;
+  void* cusolver = nullptr;        // cusolverDnHandle_t, created lazily
+  kss::DevBuf ws_local;            // FFT plane workspace
+  kss::DevBuf ws_gemm;             // split-K partial sums
+  kss::DevBuf ws_cprj;             // projector coefficients
+  kss::DevBuf stage_in, stage_out; // host-buffer entry point staging
+};
+
+struct kss_sys_s {
+  kss_ctx ctx = nullptr;
+  double lat[9];
+  double B[9];
+  double vol = 0;
+  double ecut = 0;
+  int N[3];
+  int natom = 0, nppa = 0, nproj = 0;
+  std::vector<double> pos, D;
+  double vamp = 0, vsig = 1, alpha = 0.25;
+  double vmax = 0;
+  kss::FftDim dim[3];
+  kss::DevBuf d_V64;               // V(r_j), [j3][j2][j1], unscaled
+  kss::DevBuf d_Vx64, d_Vx32;      // V(r_j)/(N1 N2 N3) in [j1][j2][j3] order (plane kernel)
+  kss::DevBuf d_tw64[3], d_tw32[3];// e^{-2 pi i k/N_d}, k < N_d
+  kss::DevBuf d_D64, d_D32;
+  std::vector<kss::KData> k;
+  int nsolvers = 0;
+};
+
+namespace kss {
+
+// ---- setup kernels (setup_kernels.cu) ----
+void launch_vloc(kss_sys s, cudaStream_t st);
+void launch_projectors(kss_sys s, KData& kd, cudaStream_t st);
+void launch_vloc_views(kss_sys s, cudaStream_t st);
+double device_max(const double* x, size_t n, cudaStream_t st);
+void projector_norms(const double* beta, int npw, int nproj, std::vector<double>& out,
+                     cudaStream_t st);
+void convert_f64_to_f32(const double* in, float* out, size_t n, cudaStream_t st);
+
+// ---- local part + H application (local_apply.cu) ----
+struct ChebCoef {
+  double alpha, beta, gamma;
+};
+// out = alpha*(T psi + V psi + nonlocal psi) + beta*psi + gamma*psi_prev (psi_prev may be null)
+void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, void* out, int ld,
+             ChebCoef c, kss_precision prec);
+size_t local_workspace_bytes(kss_sys s, int ik, int nb, kss_precision prec);
+
+// ---- complex GEMMs (gemm_simt.cu) ----
+// C (M x N, col-major ldc) = alpha * A^H B + beta * C; A: K x M (lda), B: K x N (ldb)
+void gemm_cn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda, const void* B,
+             int ldb, void* C, int ldc, double alpha_re, double alpha_im, double beta_re,
+             double beta_im);
+// C (M x N) = alpha * A B + beta * C; A: M x K (lda), B: K x N (ldb)
+void gemm_nn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda, const void* B,
+             int ldb, void* C, int ldc, double alpha_re, double alpha_im, double beta_re,
+             double beta_im);
+// Scale row i of a complex (M x N, col-major) matrix by real d[i] * s.
+void scale_rows(bool fp64, int M, int N, void* C, int ldc, const void* d, double s,
+                cudaStream_t st);
+
+// ---- solver pieces (solver.cu) ----
+void random_block(bool fp64, void* X, int npw, int nb, int ld, uint64_t seed, int band0,
+                  cudaStream_t st);
+void residual_norms(bool fp64, const void* X, const void* HX, int npw, int nb, int ld,
+                    const double* w, double* r, cudaStream_t st);
+
+}  // namespace kss

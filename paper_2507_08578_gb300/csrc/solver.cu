@@ -1,0 +1,492 @@
+// Chebyshev-filtered subspace iteration with Rayleigh-Ritz (§5.1: spectral filtering keeps the
+// number of Rayleigh-Ritz calls low and spends the time in H applications).
+//
+// One iteration on the block X (npw x nb, orthonormal Ritz vectors with Ritz values lambda):
+//   bounds   a = lambda_max(block), lambda_lo = lambda_min(block), b = rigorous upper bound of H
+//   filter   scaled Chebyshev three-term recurrence of degree m on [a, b] (each term one fused
+//            H application, the recurrence folded into the application's epilogue)
+//   HY       one more H application on the filtered block Y
+//   RR       S = Y^H Y and H_s = Y^H (HY) on the GPU, then the FP64 generalised Hermitian
+//            eigensolve H_s q = lambda S q (Cholesky factorisation of S, reduction, eigensolve)
+//            on the GPU; X = Y Q, HX = (HY) Q.  Because Q^H S Q = I this is Cholesky
+//            orthonormalisation of Y followed by Rayleigh-Ritz, with the Y L^{-H} product folded
+//            into the rotation.
+//   resid    r_n = |HX_n - lambda_n X_n|_2 (FP64 accumulation), copied to the host.
+// Mixed precision keeps the blocks, the filter and the rotations in complex64; S and H_s are
+// promoted to FP64 for the eigensolve; a converged FP32 subspace is finished by one FP64
+// H application and an FP64 Rayleigh-Ritz (Ritz values are quadratically accurate in the
+// subspace error), whose eigenvalues and residuals are what the solver returns.
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "kss_internal.h"
+
+namespace kss {
+
+namespace {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter (g, band, 0, 0), key = seed.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ double u01_sym(uint32_t v) {  // uniform in (-1, 1)
+  return ((double)(v >> 8) + 0.5) * (2.0 / 16777216.0) - 1.0;
+}
+
+template <typename C>
+__global__ void random_kernel(C* X, int npw, int nb, long long ld, uint2 key, int band0) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)npw * nb) return;
+  const int g = (int)(idx % npw), n = (int)(idx / npw);
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(band0 + n), 0u, 0u), key);
+  C v;
+  v.x = u01_sym(r.x);
+  v.y = u01_sym(r.y);
+  X[(size_t)n * ld + g] = v;
+}
+
+template <typename C>
+__global__ void residual_kernel(const C* __restrict__ X, const C* __restrict__ HX, int npw,
+                                long long ld, const double* __restrict__ w, double* __restrict__ r) {
+  __shared__ double red[256];
+  const int n = blockIdx.x;
+  const double lam = w[n];
+  const C* x = X + (size_t)n * ld;
+  const C* h = HX + (size_t)n * ld;
+  double s = 0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const double dr = (double)h[g].x - lam * (double)x[g].x;
+    const double di = (double)h[g].y - lam * (double)x[g].y;
+    s += dr * dr + di * di;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) r[n] = sqrt(red[0]);
+}
+
+__global__ void c64_to_c128(const float2* __restrict__ in, double2* __restrict__ out, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_double2(in[i].x, in[i].y);
+}
+__global__ void c128_to_c64(const double2* __restrict__ in, float2* __restrict__ out, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+// Block copy between band-major layouts with independent leading dimensions (and precisions).
+template <typename Ci, typename Co>
+__global__ void copy_block(const Ci* __restrict__ in, long long ldi, Co* __restrict__ out, long long ldo,
+                           int npw, int nb) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)npw * nb) return;
+  const int g = (int)(idx % npw), n = (int)(idx / npw);
+  const Ci v = in[(size_t)n * ldi + g];
+  Co o;
+  o.x = v.x;
+  o.y = v.y;
+  out[(size_t)n * ldo + g] = o;
+}
+
+unsigned blocks_for(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+cusolverDnHandle_t solver_handle(kss_ctx ctx) {
+  if (!ctx->cusolver) {
+    cusolverDnHandle_t h = nullptr;
+    if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) fail(KSS_ECUDA, "cusolverDnCreate failed");
+    ctx->cusolver = h;
+  }
+  cusolverDnHandle_t h = (cusolverDnHandle_t)ctx->cusolver;
+  if (cusolverDnSetStream(h, ctx->stream) != CUSOLVER_STATUS_SUCCESS)
+    fail(KSS_ECUDA, "cusolverDnSetStream failed");
+  return h;
+}
+
+}  // namespace
+
+void ctx_release_solver(kss_ctx ctx) {
+  if (ctx->cusolver) cusolverDnDestroy((cusolverDnHandle_t)ctx->cusolver);
+  ctx->cusolver = nullptr;
+}
+
+void random_block(bool fp64, void* X, int npw, int nb, int ld, uint64_t seed, int band0,
+                  cudaStream_t st) {
+  const long long n = (long long)npw * nb;
+  if (!n) return;
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  if (fp64) random_kernel<double2><<<blocks_for(n), 256, 0, st>>>((double2*)X, npw, nb, ld, key, band0);
+  else random_kernel<float2><<<blocks_for(n), 256, 0, st>>>((float2*)X, npw, nb, ld, key, band0);
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+void residual_norms(bool fp64, const void* X, const void* HX, int npw, int nb, int ld,
+                    const double* w, double* r, cudaStream_t st) {
+  if (fp64) residual_kernel<double2><<<nb, 256, 0, st>>>((const double2*)X, (const double2*)HX, npw, ld, w, r);
+  else residual_kernel<float2><<<nb, 256, 0, st>>>((const float2*)X, (const float2*)HX, npw, ld, w, r);
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+}  // namespace kss
+
+using namespace kss;
+
+struct kss_solver_s {
+  kss_sys sys = nullptr;
+  int ik = 0, nband = 0, nb = 0, npw = 0;
+  kss_solve_opts o{};
+  bool f64 = true;
+  double tol = 1e-8;
+  DevBuf blk[4];
+  int ix = 0, ihx = 1;
+  DevBuf S, Hs, W, work, info, resid_d;
+  DevBuf S32, Hs32, Q32;
+  DevBuf r64[4];  // FP64 refinement blocks (mixed precision)
+  int lwork = 0;
+  std::vector<double> evals, resid;
+  int iter = 0;
+  bool started = false, done = false, converged = false;
+  long long napply = 0;
+  double ms_filter = 0, ms_rr = 0, ms_total = 0;
+  std::vector<double> hist;  // max wanted residual per iteration
+};
+
+namespace {
+
+size_t esize(bool f64) { return f64 ? 16 : 8; }
+
+double max_wanted(const kss_solver_s* s) {
+  double m = 0;
+  for (int n = 0; n < s->nband; ++n) m = std::max(m, s->resid[n]);
+  return m;
+}
+
+// FP64 generalised eigensolve of (Hs, S) in place: Hs <- Q with Q^H S Q = I, W <- eigenvalues.
+void subspace_eig(kss_solver_s* s) {
+  kss_ctx ctx = s->sys->ctx;
+  cusolverDnHandle_t h = solver_handle(ctx);
+  const int nb = s->nb;
+  int lwork = 0;
+  if (cusolverDnZhegvd_bufferSize(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                  CUBLAS_FILL_MODE_LOWER, nb, s->Hs.as<cuDoubleComplex>(), nb,
+                                  s->S.as<cuDoubleComplex>(), nb, s->W.as<double>(),
+                                  &lwork) != CUSOLVER_STATUS_SUCCESS)
+    fail(KSS_ECUDA, "cusolverDnZhegvd_bufferSize failed");
+  s->work.ensure((size_t)std::max(lwork, 1) * sizeof(cuDoubleComplex));
+  if (cusolverDnZhegvd(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nb,
+                       s->Hs.as<cuDoubleComplex>(), nb, s->S.as<cuDoubleComplex>(), nb,
+                       s->W.as<double>(), s->work.as<cuDoubleComplex>(), lwork,
+                       s->info.as<int>()) != CUSOLVER_STATUS_SUCCESS)
+    fail(KSS_ECUDA, "cusolverDnZhegvd failed");
+}
+
+// Rayleigh-Ritz on (Y, HY) -> (Xo, HXo), eigenvalues and residuals to the host.
+void rayleigh_ritz(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo, void* HXo) {
+  kss_ctx ctx = s->sys->ctx;
+  const int nb = s->nb, npw = s->npw;
+  const long long nn = (long long)nb * nb;
+  if (f64) {
+    gemm_cn(ctx, true, nb, nb, npw, Y, npw, Y, npw, s->S.p, nb, 1, 0, 0, 0);
+    gemm_cn(ctx, true, nb, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, 1, 0, 0, 0);
+  } else {
+    gemm_cn(ctx, false, nb, nb, npw, Y, npw, Y, npw, s->S32.p, nb, 1, 0, 0, 0);
+    gemm_cn(ctx, false, nb, nb, npw, Y, npw, HY, npw, s->Hs32.p, nb, 1, 0, 0, 0);
+    c64_to_c128<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->S32.as<float2>(), s->S.as<double2>(), nn);
+    c64_to_c128<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hs32.as<float2>(), s->Hs.as<double2>(), nn);
+  }
+  subspace_eig(s);
+  int info = 0;
+  KSS_CHECK_CUDA(cudaMemcpyAsync(&info, s->info.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  if (f64) {
+    gemm_nn(ctx, true, npw, nb, nb, Y, npw, s->Hs.p, nb, Xo, npw, 1, 0, 0, 0);
+    gemm_nn(ctx, true, npw, nb, nb, HY, npw, s->Hs.p, nb, HXo, npw, 1, 0, 0, 0);
+  } else {
+    c128_to_c64<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hs.as<double2>(), s->Q32.as<float2>(), nn);
+    gemm_nn(ctx, false, npw, nb, nb, Y, npw, s->Q32.p, nb, Xo, npw, 1, 0, 0, 0);
+    gemm_nn(ctx, false, npw, nb, nb, HY, npw, s->Q32.p, nb, HXo, npw, 1, 0, 0, 0);
+  }
+  residual_norms(f64, Xo, HXo, npw, nb, npw, s->W.as<double>(), s->resid_d.as<double>(), ctx->stream);
+  s->evals.resize(nb);
+  s->resid.resize(nb);
+  KSS_CHECK_CUDA(cudaMemcpyAsync(s->evals.data(), s->W.p, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  KSS_CHECK_CUDA(cudaMemcpyAsync(s->resid.data(), s->resid_d.p, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  KSS_CHECK_CUDA(cudaGetLastError());
+  if (info != 0)
+    fail(KSS_ENUMERIC, "subspace eigensolve failed (info = " + std::to_string(info) +
+                           "): the Gram matrix is not numerically positive definite");
+  for (int n = 0; n < nb; ++n)
+    if (!std::isfinite(s->evals[n]) || !std::isfinite(s->resid[n]))
+      fail(KSS_ENUMERIC, "non-finite Ritz value or residual");
+}
+
+void apply_block(kss_solver_s* s, bool f64, const void* psi, void* out) {
+  apply_h(s->sys, s->ik, s->nb, psi, nullptr, out, s->npw, ChebCoef{1, 0, 0},
+          f64 ? KSS_PREC_FP64 : KSS_PREC_MIXED);
+  s->napply += s->nb;
+}
+
+// Scaled Chebyshev filter of degree m on X (in blk[ix]); returns the buffer holding Y_m and, in
+// *prev_out, the buffer holding Y_{m-1} (free for reuse).
+int chebyshev_filter(kss_solver_s* s, int f1, int* prev_out) {
+  const int nb = s->nb;
+  const double lam_lo = s->evals[0];
+  double a = s->evals[nb - 1];
+  const double b = s->sys->k[s->ik].bound;
+  if (!(b - a > 1e-3 * (b - lam_lo))) a = lam_lo + 0.5 * (b - lam_lo);
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  const double sigma1 = e / (lam_lo - c);
+  const double tau = 2.0 / sigma1;
+  const kss_precision p = s->f64 ? KSS_PREC_FP64 : KSS_PREC_MIXED;
+  int cur = s->ix, prev = f1;
+  // Y_1 = (sigma1/e)(H - c) X
+  {
+    const double al = sigma1 / e;
+    apply_h(s->sys, s->ik, nb, s->blk[cur].p, nullptr, s->blk[prev].p, s->npw,
+            ChebCoef{al, -al * c, 0.0}, p);
+    s->napply += nb;
+    std::swap(cur, prev);  // cur = Y_1, prev = X
+  }
+  double sigma = sigma1;
+  const int m = s->o.degree;
+  for (int j = 2; j <= m; ++j) {
+    const double sn = 1.0 / (tau - sigma);
+    const double al = 2.0 * sn / e;
+    // Y_j = (2 sn / e)(H - c) Y_{j-1} - sigma sn Y_{j-2}, written over Y_{j-2}
+    apply_h(s->sys, s->ik, nb, s->blk[cur].p, s->blk[prev].p, s->blk[prev].p, s->npw,
+            ChebCoef{al, -al * c, -sigma * sn}, p);
+    s->napply += nb;
+    std::swap(cur, prev);
+    sigma = sn;
+  }
+  *prev_out = prev;
+  return cur;
+}
+
+void refine_fp64(kss_solver_s* s) {
+  kss_ctx ctx = s->sys->ctx;
+  const size_t bytes = (size_t)s->npw * s->nb * 16;
+  for (int i = 0; i < 4; ++i) s->r64[i].ensure(bytes);
+  const long long n = (long long)s->npw * s->nb;
+  copy_block<float2, double2><<<blocks_for(n), 256, 0, ctx->stream>>>(
+      s->blk[s->ix].as<float2>(), s->npw, s->r64[0].as<double2>(), s->npw, s->npw, s->nb);
+  KSS_CHECK_CUDA(cudaGetLastError());
+  apply_block(s, true, s->r64[0].p, s->r64[1].p);
+  rayleigh_ritz(s, true, s->r64[0].p, s->r64[1].p, s->r64[2].p, s->r64[3].p);
+  // Keep the refined vectors as the current iterate (demoted to complex64).
+  copy_block<double2, float2><<<blocks_for(n), 256, 0, ctx->stream>>>(
+      s->r64[2].as<double2>(), s->npw, s->blk[s->ix].as<float2>(), s->npw, s->npw, s->nb);
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+void solver_step(kss_solver_s* s) {
+  kss_ctx ctx = s->sys->ctx;
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!s->started) {
+    apply_block(s, s->f64, s->blk[0].p, s->blk[1].p);
+    const auto t1 = std::chrono::steady_clock::now();
+    rayleigh_ritz(s, s->f64, s->blk[0].p, s->blk[1].p, s->blk[2].p, s->blk[3].p);
+    s->ix = 2;
+    s->ihx = 3;
+    s->started = true;
+    s->ms_rr += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+  } else {
+    int fr[2], nf = 0;
+    for (int i = 0; i < 4; ++i)
+      if (i != s->ix && i != s->ihx) fr[nf++] = i;
+    int prev = -1;
+    const int y = chebyshev_filter(s, fr[0], &prev);
+    // y and prev are two of {ix, fr[0]}; the HY block reuses prev.
+    apply_block(s, s->f64, s->blk[y].p, s->blk[prev].p);
+    KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    const auto t1 = std::chrono::steady_clock::now();
+    s->ms_filter += std::chrono::duration<double, std::milli>(t1 - t0).count();
+    rayleigh_ritz(s, s->f64, s->blk[y].p, s->blk[prev].p, s->blk[fr[1]].p, s->blk[s->ihx].p);
+    s->ix = fr[1];
+    s->iter += 1;
+    s->ms_rr += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+  }
+  const double r = max_wanted(s);
+  s->hist.push_back(r);
+  if (s->f64) {
+    s->converged = r <= s->tol;
+    s->done = s->converged;
+  } else {
+    bool stalled = false;
+    const size_t h = s->hist.size();
+    if (h >= 4) stalled = s->hist[h - 1] > 0.9 * s->hist[h - 4];
+    if (r <= s->tol || stalled || s->iter >= s->o.max_iter) {
+      refine_fp64(s);
+      s->converged = max_wanted(s) <= s->tol;
+      s->done = true;
+    }
+  }
+  s->ms_total += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+template <typename F>
+kss_status guard(kss_ctx ctx, F&& f) {
+  try {
+    f();
+    ctx->err.clear();
+    return KSS_OK;
+  } catch (const KssError& e) {
+    ctx->err = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    ctx->err = "host allocation failed";
+    return KSS_ENOMEM;
+  } catch (...) {
+    ctx->err = "unexpected internal error";
+    return KSS_ECUDA;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+kss_status kss_solver_create(kss_sys sys, int ik, int nband, const kss_solve_opts* opts,
+                             kss_solver* out) {
+  if (!sys || !out) return KSS_EINVAL;
+  kss_ctx ctx = sys->ctx;
+  return guard(ctx, [&] {
+    *out = nullptr;
+    KSS_REQUIRE(ik >= 0 && ik < (int)sys->k.size(), "k-point index out of range");
+    KSS_REQUIRE(nband >= 1, "nband must be >= 1");
+    KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    std::unique_ptr<kss_solver_s> s(new kss_solver_s());
+    s->sys = sys;
+    s->ik = ik;
+    s->nband = nband;
+    s->npw = sys->k[ik].npw;
+    kss_solve_opts o{};
+    if (opts) o = *opts;
+    if (o.degree <= 0) o.degree = 10;
+    if (o.max_iter <= 0) o.max_iter = 200;
+    if (o.nbuffer < 0) o.nbuffer = std::max(4, (nband + 9) / 10);
+    KSS_REQUIRE(o.prec == KSS_PREC_FP64 || o.prec == KSS_PREC_MIXED, "unknown precision");
+    s->f64 = o.prec == KSS_PREC_FP64;
+    s->tol = o.tol > 0 ? o.tol : (s->f64 ? 1e-8 : 1e-5);
+    s->nb = nband + o.nbuffer;
+    KSS_REQUIRE(s->nb <= s->npw, "nband + nbuffer exceeds the number of plane waves");
+    s->o = o;
+    const size_t bytes = (size_t)s->npw * s->nb * esize(s->f64);
+    for (int i = 0; i < 4; ++i) s->blk[i].alloc(bytes);
+    const size_t nn = (size_t)s->nb * s->nb;
+    s->S.alloc(nn * 16);
+    s->Hs.alloc(nn * 16);
+    s->W.alloc(s->nb * sizeof(double));
+    s->resid_d.alloc(s->nb * sizeof(double));
+    s->info.alloc(sizeof(int));
+    if (!s->f64) {
+      s->S32.alloc(nn * 8);
+      s->Hs32.alloc(nn * 8);
+      s->Q32.alloc(nn * 8);
+    }
+    int nx = 0;
+    if (o.x0) {
+      KSS_REQUIRE(o.x0_nb >= 0 && o.x0_nb <= s->nb && o.x0_ld >= s->npw, "bad x0_nb or x0_ld");
+      nx = o.x0_nb;
+      if (nx)
+        KSS_CHECK_CUDA(cudaMemcpy2DAsync(s->blk[0].p, (size_t)s->npw * esize(s->f64), o.x0,
+                                         (size_t)o.x0_ld * esize(s->f64), (size_t)s->npw * esize(s->f64),
+                                         nx, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    if (nx < s->nb)
+      random_block(s->f64, (char*)s->blk[0].p + (size_t)nx * s->npw * esize(s->f64), s->npw,
+                   s->nb - nx, s->npw, o.seed, nx, ctx->stream);
+    s->o.x0 = nullptr;  // copied; the caller's buffer is not referenced again
+    sys->nsolvers += 1;
+    *out = s.release();
+  });
+}
+
+kss_status kss_solver_destroy(kss_solver s) {
+  if (!s) return KSS_EINVAL;
+  cudaSetDevice(s->sys->ctx->device);
+  cudaStreamSynchronize(s->sys->ctx->stream);
+  s->sys->nsolvers -= 1;
+  delete s;
+  return KSS_OK;
+}
+
+kss_status kss_solver_step(kss_solver s, int* converged) {
+  if (!s) return KSS_EINVAL;
+  kss_ctx ctx = s->sys->ctx;
+  return guard(ctx, [&] {
+    KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    if (!s->done) solver_step(s);
+    if (converged) *converged = s->converged ? 1 : 0;
+  });
+}
+
+kss_status kss_solver_results(kss_solver s, double* evals, double* resid, void* evecs, int ld,
+                              kss_solve_stats* stats) {
+  if (!s) return KSS_EINVAL;
+  kss_ctx ctx = s->sys->ctx;
+  return guard(ctx, [&] {
+    KSS_REQUIRE(s->started, "no iterate yet: call kss_solver_step first");
+    if (evals) std::memcpy(evals, s->evals.data(), s->nband * sizeof(double));
+    if (resid) std::memcpy(resid, s->resid.data(), s->nband * sizeof(double));
+    if (evecs) {
+      KSS_REQUIRE(ld >= s->npw, "ld < npw");
+      const size_t es = esize(s->f64);
+      KSS_CHECK_CUDA(cudaMemcpy2DAsync(evecs, (size_t)ld * es, s->blk[s->ix].p, (size_t)s->npw * es,
+                                       (size_t)s->npw * es, s->nband, cudaMemcpyDeviceToDevice,
+                                       ctx->stream));
+      KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    if (stats) {
+      stats->iters = s->iter;
+      stats->napply = s->napply;
+      stats->max_resid = max_wanted(s);
+      stats->ms_filter = s->ms_filter;
+      stats->ms_rr = s->ms_rr;
+      stats->ms_total = s->ms_total;
+      stats->nb = s->nb;
+    }
+  });
+}
+
+kss_status kss_chebfi_solve(kss_sys sys, int ik, int nband, const kss_solve_opts* opts,
+                            double* evals, void* evecs, int ld, double* resid,
+                            kss_solve_stats* stats) {
+  if (!sys) return KSS_EINVAL;
+  kss_solver s = nullptr;
+  kss_status st = kss_solver_create(sys, ik, nband, opts, &s);
+  if (st != KSS_OK) return st;
+  int conv = 0;
+  while (st == KSS_OK && !conv && !s->done && s->iter < s->o.max_iter) st = kss_solver_step(s, &conv);
+  if (st == KSS_OK && !s->started) st = kss_solver_step(s, &conv);
+  kss_status st2 = KSS_OK;
+  if (s->started) st2 = kss_solver_results(s, evals, resid, evecs, ld, stats);
+  std::string msg = sys->ctx->err;
+  kss_solver_destroy(s);
+  sys->ctx->err = msg;
+  if (st != KSS_OK) return st;
+  if (st2 != KSS_OK) return st2;
+  if (!conv) {
+    sys->ctx->err = "not converged within max_iter";
+    return KSS_ENOCONV;
+  }
+  return KSS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,363 @@
+"""ctypes binding of ``libkss.so`` (include/kss.h): argument marshalling only.
+
+Every function keeps the name of its C entry point.  Device buffers are passed as torch CUDA
+tensors (their ``data_ptr()``); torch is used for device memory and streams only, all work runs
+in the library's kernels.  There is no CPU fallback: if the library or a CUDA device is missing
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_int32, c_longlong, c_size_t, c_uint64, c_void_p
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libkss.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "kss.h")
+
+KSS_OK, KSS_EINVAL, KSS_ENOMEM, KSS_ECUDA, KSS_ENOCONV, KSS_ETIMEOUT, KSS_EBUSY, KSS_ENUMERIC, KSS_ENOTSUP = range(9)
+STATUS_NAMES = ["KSS_OK", "KSS_EINVAL", "KSS_ENOMEM", "KSS_ECUDA", "KSS_ENOCONV", "KSS_ETIMEOUT",
+                "KSS_EBUSY", "KSS_ENUMERIC", "KSS_ENOTSUP"]
+KSS_PREC_FP64, KSS_PREC_MIXED = 0, 1
+
+
+class KssError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+class kss_cell(ctypes.Structure):
+    _fields_ = [("lattice", c_double * 9), ("ecut", c_double), ("nk", c_int),
+                ("kpts_red", POINTER(c_double)), ("fft_box", c_int * 3)]
+
+
+class kss_atoms(ctypes.Structure):
+    _fields_ = [("natom", c_int), ("pos_cart", POINTER(c_double)), ("vloc_amp", c_double),
+                ("vloc_sigma", c_double), ("nproj_per_atom", c_int), ("proj_alpha", c_double),
+                ("D", POINTER(c_double))]
+
+
+class kss_sys_info(ctypes.Structure):
+    _fields_ = [("nk", c_int), ("fft_box", c_int * 3), ("nproj", c_int), ("npw_max", c_int),
+                ("volume", c_double), ("vloc_max", c_double)]
+
+
+class kss_solve_opts(ctypes.Structure):
+    _fields_ = [("degree", c_int), ("tol", c_double), ("max_iter", c_int), ("nbuffer", c_int),
+                ("prec", c_int), ("seed", c_uint64), ("x0", c_void_p), ("x0_nb", c_int),
+                ("x0_ld", c_int)]
+
+
+class kss_solve_stats(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("napply", c_longlong), ("max_resid", c_double),
+                ("ms_filter", c_double), ("ms_rr", c_double), ("ms_total", c_double),
+                ("nb", c_int)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libkss.so (built by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        P = c_void_p
+        sig = {
+            "kss_version": ([], c_int),
+            "kss_create": ([POINTER(c_void_p), c_int, c_void_p], c_int),
+            "kss_destroy": ([P], c_int),
+            "kss_last_error": ([P], c_char_p),
+            "kss_setup": ([P, POINTER(kss_cell), POINTER(kss_atoms), POINTER(c_void_p)], c_int),
+            "kss_sys_destroy": ([P], c_int),
+            "kss_sys_info_get": ([P, POINTER(kss_sys_info)], c_int),
+            "kss_sphere": ([P, c_int, POINTER(c_int), POINTER(POINTER(c_int32))], c_int),
+            "kss_get_maps": ([P, c_int, P, P], c_int),
+            "kss_get_tables": ([P, c_int, P, P, P], c_int),
+            "kss_upper_bound": ([P, c_int, POINTER(c_double)], c_int),
+            "kss_footprint": ([P, c_int, c_int, POINTER(c_size_t)], c_int),
+            "kss_apply_H": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
+            "kss_cheb_step": ([P, c_int, c_int, P, P, P, c_int, c_double, c_double, c_double, c_int], c_int),
+            "kss_apply_H_host": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
+            "kss_solver_create": ([P, c_int, c_int, POINTER(kss_solve_opts), POINTER(c_void_p)], c_int),
+            "kss_solver_destroy": ([P], c_int),
+            "kss_solver_step": ([P, POINTER(c_int)], c_int),
+            "kss_solver_results": ([P, P, P, P, c_int, POINTER(kss_solve_stats)], c_int),
+            "kss_chebfi_solve": ([P, c_int, c_int, POINTER(kss_solve_opts), P, P, c_int, P,
+                                  POINTER(kss_solve_stats)], c_int),
+        }
+        for name, (args, res) in sig.items():
+            if hasattr(L, name):
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+        _lib = L
+    return _lib
+
+
+def header_functions(path: str = HEADER):
+    """Names of every function the C header declares."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(kss_[a-zA-Z0-9_]+)\s*\(", txt)) - {"kss_status"})
+
+
+# --------------------------------------------------------------------------------------------
+# marshalling helpers
+
+def _ptr(t) -> int:
+    """Device address of a torch tensor (or an int address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _block_dims(t, prec):
+    import torch
+    want = torch.complex128 if prec == KSS_PREC_FP64 else torch.complex64
+    if t.dtype != want:
+        raise ValueError(f"expected {want} for precision {prec}, got {t.dtype}")
+    if t.dim() != 2:
+        raise ValueError("band blocks are 2-D tensors (nb, ld)")
+    return int(t.shape[0]), int(t.shape[1])
+
+
+def _check(st: int, handle_ctx=None):
+    if st != KSS_OK:
+        msg = ""
+        if handle_ctx is not None:
+            m = lib().kss_last_error(handle_ctx)
+            msg = m.decode() if m else ""
+        raise KssError(st, msg)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(POINTER(c_double))
+
+
+# --------------------------------------------------------------------------------------------
+# context and systems
+
+def kss_version() -> int:
+    return lib().kss_version()
+
+
+def kss_create(device: int = 0, stream: Optional[int] = None):
+    h = c_void_p()
+    st = lib().kss_create(byref(h), int(device), c_void_p(stream) if stream else None)
+    if st != KSS_OK:
+        raise KssError(st, "kss_create failed (no usable CUDA device?)")
+    return h
+
+
+def kss_destroy(ctx):
+    _check(lib().kss_destroy(ctx), ctx)
+
+
+def kss_last_error(ctx) -> str:
+    m = lib().kss_last_error(ctx)
+    return m.decode() if m else ""
+
+
+class System:
+    """A kss_sys handle plus the context it belongs to (for error messages)."""
+
+    def __init__(self, ctx, handle, keep):
+        self.ctx = ctx
+        self.h = handle
+        self._keep = keep
+
+    def __int__(self):
+        return self.h.value
+
+
+def kss_setup(ctx, lattice, ecut, kpts, pos, D, fft_box=(0, 0, 0), vloc_amp=-2.0,
+              vloc_sigma=1.0, nproj_per_atom=4, proj_alpha=0.25) -> System:
+    lat = np.ascontiguousarray(np.asarray(lattice, np.float64).reshape(9))
+    k = np.ascontiguousarray(np.asarray(kpts, np.float64).reshape(-1, 3))
+    p = np.ascontiguousarray(np.asarray(pos, np.float64).reshape(-1, 3))
+    d = np.ascontiguousarray(np.asarray(D if D is not None else [], np.float64).reshape(-1))
+    cell = kss_cell()
+    cell.lattice[:] = lat.tolist()
+    cell.ecut = float(ecut)
+    cell.nk = int(k.shape[0])
+    cell.kpts_red = _dptr(k)
+    cell.fft_box[:] = [int(v) for v in (fft_box or (0, 0, 0))]
+    at = kss_atoms()
+    at.natom = int(p.shape[0])
+    at.pos_cart = _dptr(p)
+    at.vloc_amp = float(vloc_amp)
+    at.vloc_sigma = float(vloc_sigma)
+    at.nproj_per_atom = int(nproj_per_atom)
+    at.proj_alpha = float(proj_alpha)
+    at.D = _dptr(d)
+    h = c_void_p()
+    _check(lib().kss_setup(ctx, byref(cell), byref(at), byref(h)), ctx)
+    return System(ctx, h, (k, p, d))
+
+
+def kss_sys_destroy(sys: System):
+    _check(lib().kss_sys_destroy(sys.h), sys.ctx)
+
+
+def kss_sys_info_get(sys: System) -> dict:
+    info = kss_sys_info()
+    _check(lib().kss_sys_info_get(sys.h, byref(info)), sys.ctx)
+    return {"nk": info.nk, "fft_box": tuple(info.fft_box), "nproj": info.nproj,
+            "npw_max": info.npw_max, "volume": info.volume, "vloc_max": info.vloc_max}
+
+
+def kss_sphere(sys: System, ik: int) -> np.ndarray:
+    n = c_int()
+    mp = POINTER(c_int32)()
+    _check(lib().kss_sphere(sys.h, ik, byref(n), byref(mp)), sys.ctx)
+    return np.ctypeslib.as_array(mp, shape=(n.value * 3,)).reshape(n.value, 3).copy()
+
+
+def kss_get_maps(sys: System, ik: int):
+    npw = kss_sphere(sys, ik).shape[0]
+    miller = np.zeros((npw, 3), np.int32)
+    off = np.zeros(npw, np.int32)
+    _check(lib().kss_get_maps(sys.h, ik, miller.ctypes.data, off.ctypes.data), sys.ctx)
+    return miller, off
+
+
+def kss_get_tables(sys: System, ik: int):
+    info = kss_sys_info_get(sys)
+    npw = kss_sphere(sys, ik).shape[0]
+    N1, N2, N3 = info["fft_box"]
+    V = np.zeros(N1 * N2 * N3)
+    kin = np.zeros(npw)
+    beta = np.zeros((info["nproj"], npw), np.complex128)
+    _check(lib().kss_get_tables(sys.h, ik, V.ctypes.data, kin.ctypes.data,
+                                beta.ctypes.data if info["nproj"] else None), sys.ctx)
+    return V.reshape(N3, N2, N1), kin, beta
+
+
+def kss_upper_bound(sys: System, ik: int) -> float:
+    b = c_double()
+    _check(lib().kss_upper_bound(sys.h, ik, byref(b)), sys.ctx)
+    return b.value
+
+
+def kss_footprint(sys: System, nband: int, prec: int = KSS_PREC_FP64) -> int:
+    b = c_size_t()
+    _check(lib().kss_footprint(sys.h, nband, prec, byref(b)), sys.ctx)
+    return b.value
+
+
+# --------------------------------------------------------------------------------------------
+# H application
+
+def kss_apply_H(sys: System, ik: int, psi, hpsi, prec: int = KSS_PREC_FP64, nb: Optional[int] = None):
+    n, ld = _block_dims(psi, prec)
+    n2, ld2 = _block_dims(hpsi, prec)
+    if (n2, ld2) != (n, ld):
+        raise ValueError("psi and hpsi shapes differ")
+    _check(lib().kss_apply_H(sys.h, ik, n if nb is None else nb, _ptr(psi), _ptr(hpsi), ld, prec), sys.ctx)
+
+
+def kss_cheb_step(sys: System, ik: int, psi, psi_prev, out, alpha, beta, gamma,
+                  prec: int = KSS_PREC_FP64):
+    n, ld = _block_dims(psi, prec)
+    _check(lib().kss_cheb_step(sys.h, ik, n, _ptr(psi), _ptr(psi_prev), _ptr(out), ld,
+                               float(alpha), float(beta), float(gamma), prec), sys.ctx)
+
+
+def kss_apply_H_host(sys: System, ik: int, psi: np.ndarray, hpsi: np.ndarray,
+                     prec: int = KSS_PREC_FP64):
+    want = np.complex128 if prec == KSS_PREC_FP64 else np.complex64
+    if psi.dtype != want or hpsi.dtype != want or psi.shape != hpsi.shape or psi.ndim != 2:
+        raise ValueError("psi/hpsi must be 2-D arrays of the precision's complex type")
+    if not (psi.flags.c_contiguous and hpsi.flags.c_contiguous):
+        raise ValueError("contiguous arrays required")
+    nb, ld = psi.shape
+    _check(lib().kss_apply_H_host(sys.h, ik, nb, psi.ctypes.data, hpsi.ctypes.data, ld, prec), sys.ctx)
+
+
+# --------------------------------------------------------------------------------------------
+# eigensolver
+
+def make_opts(degree=10, tol=0.0, max_iter=0, nbuffer=-1, prec=KSS_PREC_FP64, seed=1234,
+              x0=None, x0_nb=0, x0_ld=0) -> kss_solve_opts:
+    o = kss_solve_opts()
+    o.degree = int(degree)
+    o.tol = float(tol)
+    o.max_iter = int(max_iter)
+    o.nbuffer = int(nbuffer)
+    o.prec = int(prec)
+    o.seed = int(seed)
+    o.x0 = _ptr(x0)
+    o.x0_nb = int(x0_nb)
+    o.x0_ld = int(x0_ld)
+    return o
+
+
+class Solver:
+    def __init__(self, sys, handle, nband, prec):
+        self.sys = sys
+        self.h = handle
+        self.nband = nband
+        self.prec = prec
+
+
+def kss_solver_create(sys: System, ik: int, nband: int, opts: kss_solve_opts) -> Solver:
+    h = c_void_p()
+    _check(lib().kss_solver_create(sys.h, ik, nband, byref(opts), byref(h)), sys.ctx)
+    return Solver(sys, h, nband, opts.prec)
+
+
+def kss_solver_destroy(s: Solver):
+    _check(lib().kss_solver_destroy(s.h), s.sys.ctx)
+
+
+def kss_solver_step(s: Solver) -> bool:
+    c = c_int()
+    _check(lib().kss_solver_step(s.h, byref(c)), s.sys.ctx)
+    return bool(c.value)
+
+
+def kss_solver_results(s: Solver, evecs=None):
+    ev = np.zeros(s.nband)
+    rs = np.zeros(s.nband)
+    stats = kss_solve_stats()
+    ld = 0
+    if evecs is not None:
+        _, ld = _block_dims(evecs, s.prec)
+    _check(lib().kss_solver_results(s.h, ev.ctypes.data, rs.ctypes.data, _ptr(evecs), ld,
+                                    byref(stats)), s.sys.ctx)
+    return ev, rs, stats_dict(stats)
+
+
+def stats_dict(st: kss_solve_stats) -> dict:
+    return {k: getattr(st, k) for k, _ in kss_solve_stats._fields_}
+
+
+def kss_chebfi_solve(sys: System, ik: int, nband: int, opts: kss_solve_opts, evecs=None,
+                     allow_noconv: bool = False):
+    ev = np.zeros(nband)
+    rs = np.zeros(nband)
+    stats = kss_solve_stats()
+    ld = 0
+    if evecs is not None:
+        _, ld = _block_dims(evecs, opts.prec)
+    st = lib().kss_chebfi_solve(sys.h, ik, nband, byref(opts), ev.ctypes.data, _ptr(evecs), ld,
+                                rs.ctypes.data, byref(stats))
+    if st == KSS_ENOCONV and allow_noconv:
+        return ev, rs, stats_dict(stats), st
+    _check(st, sys.ctx)
+    return ev, rs, stats_dict(stats), st

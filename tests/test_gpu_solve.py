@@ -1,0 +1,122 @@
+"""GPU ChebFi eigensolves against the oracle's dense diagonalisation, through the C ABI.
+
+Bars: FP64 eigenvalues within 1e-8 Ha of the oracle and residuals <= tol; mixed precision
+(complex64 filter, FP64 Rayleigh-Ritz) within 1e-6 Ha.  Eigenvalues are compared sorted
+(degenerate shells make the vectors gauge-dependent).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+import paper_2507_08578_gb300.kss as K
+from tests.kss_helpers import ensure_built, make_ctx, setup
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    ensure_built()
+    c = make_ctx()
+    yield c
+    torch.cuda.synchronize()
+    K.kss_destroy(c)
+
+
+def oracle_levels(s, ik, nband, box=None):
+    p = O.build_problem(s, ik, box=box)
+    w, _ = O.lowest_eigenpairs(p.dense(), nband)
+    return w
+
+
+def solve(ctx, s, ik, nband, **kw):
+    sysh = setup(ctx, s)
+    try:
+        return K.kss_chebfi_solve(sysh, ik, nband, K.make_opts(**kw))
+    finally:
+        K.kss_sys_destroy(sysh)
+
+
+def test_c1_fp64(ctx):
+    s = W.config1()
+    ev, rs, st, _ = solve(ctx, s, 0, 16, tol=1e-8)
+    ref = oracle_levels(s, 0, 16)
+    assert np.max(np.abs(ev - ref)) < 1e-8, (ev - ref)
+    assert rs.max() <= 1e-8
+    assert st["iters"] >= 1 and st["napply"] > 0
+
+
+def test_tiny_full_spectrum(ctx):
+    s = W.tiny_system(a=6.0, ecut=2.0, natom=2, kpts=[(0.25, -0.25, 0.25)])
+    p = O.build_problem(s, 0)
+    npw = p.basis.npw
+    nband = npw - 4
+    ev, rs, _, _ = solve(ctx, s, 0, nband, tol=1e-9, nbuffer=4)
+    w = O.all_eigenvalues(p.dense())[:nband]
+    assert np.max(np.abs(ev - w)) < 1e-8
+
+
+def test_settings_do_not_change_result(ctx):
+    s = W.config1()
+    a = solve(ctx, s, 0, 16, tol=1e-9, degree=6, seed=1)[0]
+    b = solve(ctx, s, 0, 16, tol=1e-9, degree=14, seed=2, nbuffer=8)[0]
+    assert np.max(np.abs(a - b)) < 2e-9
+
+
+def test_kpoint_c2_shape_small(ctx):
+    """Shifted k-points of a smaller cell with the C2 atom recipe (complex Hermitian H)."""
+    s = W.make_system("c2s", 10.0, 8.0, 8, 24, seed=1002, kpts=W.SHIFTED_222[:2], min_sep=2.0)
+    for ik in range(2):
+        ev, rs, _, _ = solve(ctx, s, ik, 24, tol=1e-8)
+        ref = oracle_levels(s, ik, 24)
+        assert np.max(np.abs(ev - ref)) < 1e-8
+
+
+def test_noconv_status(ctx):
+    s = W.config1()
+    sysh = setup(ctx, s)
+    try:
+        ev, rs, st, status = K.kss_chebfi_solve(sysh, 0, 16, K.make_opts(max_iter=1, tol=1e-12),
+                                                allow_noconv=True)
+        assert status == K.KSS_ENOCONV
+        assert st["iters"] == 1 and np.all(np.isfinite(ev)) and rs.max() > 1e-12
+    finally:
+        K.kss_sys_destroy(sysh)
+
+
+def test_mixed_c1_cell_64_bands(ctx):
+    s = W.with_(W.config1(), nband=64)
+    ev, rs, st, _ = solve(ctx, s, 0, 64, prec=K.KSS_PREC_MIXED)
+    ref = oracle_levels(s, 0, 64)
+    assert np.max(np.abs(ev - ref)) < 1e-6, np.max(np.abs(ev - ref))
+
+
+def test_stepping_api_matches_full_solve(ctx):
+    import torch
+    s = W.config1()
+    sysh = setup(ctx, s)
+    try:
+        opts = K.make_opts(tol=1e-8, seed=7)
+        sv = K.kss_solver_create(sysh, 0, 16, opts)
+        conv = False
+        for _ in range(200):
+            conv = K.kss_solver_step(sv)
+            if conv:
+                break
+        assert conv
+        npw = K.kss_sphere(sysh, 0).shape[0]
+        X = torch.zeros((16, npw), dtype=torch.complex128, device="cuda")
+        ev, rs, st = K.kss_solver_results(sv, X)
+        K.kss_solver_destroy(sv)
+        ev2 = K.kss_chebfi_solve(sysh, 0, 16, K.make_opts(tol=1e-8, seed=7))[0]
+        assert np.array_equal(ev, ev2)
+        x = X.cpu().numpy()
+        assert np.allclose(x.conj() @ x.T, np.eye(16), atol=1e-10)
+        # warm start from the converged vectors: converges in few iterations
+        opts2 = K.make_opts(tol=1e-8, x0=X, x0_nb=16, x0_ld=npw)
+        ev3, _, st3, _ = K.kss_chebfi_solve(sysh, 0, 16, opts2)
+        assert st3["iters"] <= 2 and np.max(np.abs(ev3 - ev)) < 1e-8
+    finally:
+        K.kss_sys_destroy(sysh)
