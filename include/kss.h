@@ -108,7 +108,7 @@ typedef struct {
  * 0.5|k+G|^2 and the projector table beta_{a,l}(k+G) = c_l q_l exp(-alpha|q|^2) exp(-i q.R_a)
  * (q_s = 1; c_s, c_p the continuum unit-norm constants).  Library-owned device memory.
  * Errors: KSS_EINVAL (bad cell/atoms, FFT box too small for the sphere or not {2,3,5}-smooth,
- * box dimension > 512), KSS_ENOMEM, KSS_ECUDA. */
+ * box dimension > 256), KSS_ENOMEM, KSS_ECUDA. */
 kss_status kss_setup(kss_ctx ctx, const kss_cell* cell, const kss_atoms* atoms, kss_sys* out);
 
 kss_status kss_sys_destroy(kss_sys sys);
@@ -217,6 +217,23 @@ kss_status kss_solver_results(kss_solver s, double* evals, double* resid, void* 
 kss_status kss_chebfi_solve(kss_sys sys, int ik, int nband, const kss_solve_opts* opts,
                             double* evals, void* evecs, int ld, double* resid,
                             kss_solve_stats* stats);
+
+/* ------------------------------------------------------------------------------------------
+ * Launch accounting and per-kernel timing (measurement support; no counterpart in the paper)
+ * ------------------------------------------------------------------------------------------ */
+
+/* Reset the context's counters; enable != 0 also brackets every later kernel launch of this
+ * library with a pair of CUDA events on the context stream (small overhead per launch). */
+kss_status kss_profile_enable(kss_ctx ctx, int enable);
+
+/* Number of kernel names seen so far (entries) and launches since the last reset.  Waits for
+ * the context stream when timing is enabled. */
+kss_status kss_profile_count(kss_ctx ctx, int* nkernels, long long* launches);
+
+/* Entry i < nkernels: kernel name (library-owned, static), launches and total event-timed
+ * milliseconds since the last reset (0 when timing was off).  KSS_EINVAL past the end. */
+kss_status kss_profile_entry(kss_ctx ctx, int i, const char** name, long long* launches,
+                             double* total_ms);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,7 @@
 // dimension ld.  On GB300 the FP64 pipe (about 1.2 TFLOP/s) bounds these kernels long before
 // shared memory or HBM does; the FP32 instantiation is the CUDA-core form of the mixed path.
 #include <algorithm>
+#include <string>
 
 #include "kss_internal.h"
 
@@ -198,9 +199,14 @@ int sm_count(kss_ctx ctx) {
   return n;
 }
 
+int tag_id(const char* kernel, bool f64, const char* tag) {
+  std::string n = std::string(kernel) + (f64 ? "<f64>:" : "<f32>:") + (tag ? tag : "");
+  return prof_register(n.c_str());
+}
+
 template <typename T>
 void run_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
-            void* Cm, int ldc, double ar, double ai, double br, double bi) {
+            void* Cm, int ldc, double ar, double ai, double br, double bi, const char* tag) {
   using C = typename CT<T>::C;
   const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
   const int tiles = tm * tn;
@@ -210,19 +216,27 @@ void run_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void
   kchunk = (kchunk + BK - 1) / BK * BK;
   splits = (K + kchunk - 1) / kchunk;
   ctx->ws_gemm.ensure((size_t)splits * M * N * sizeof(C));
-  gemm_cn_partial<T><<<dim3(tm, tn, splits), 256, 0, ctx->stream>>>(
-      M, N, K, (const C*)A, lda, (const C*)B, ldb, ctx->ws_gemm.as<C>(), kchunk);
+  const bool f64 = sizeof(T) == 8;
+  {
+    ProfScope ps(ctx, tag_id("gemm_cn_partial", f64, tag));
+    gemm_cn_partial<T><<<dim3(tm, tn, splits), 256, 0, ctx->stream>>>(
+        M, N, K, (const C*)A, lda, (const C*)B, ldb, ctx->ws_gemm.as<C>(), kchunk);
+  }
   const long long mn = (long long)M * N;
-  gemm_reduce<T><<<(unsigned)((mn + 255) / 256), 256, 0, ctx->stream>>>(
-      M, N, splits, ctx->ws_gemm.as<C>(), (C*)Cm, ldc, (T)ar, (T)ai, (T)br, (T)bi);
+  {
+    ProfScope ps(ctx, tag_id("gemm_reduce", f64, tag));
+    gemm_reduce<T><<<(unsigned)((mn + 255) / 256), 256, 0, ctx->stream>>>(
+        M, N, splits, ctx->ws_gemm.as<C>(), (C*)Cm, ldc, (T)ar, (T)ai, (T)br, (T)bi);
+  }
   KSS_CHECK_CUDA(cudaGetLastError());
 }
 
 template <typename T>
 void run_nn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
-            void* Cm, int ldc, double ar, double ai, double br, double bi) {
+            void* Cm, int ldc, double ar, double ai, double br, double bi, const char* tag) {
   using C = typename CT<T>::C;
   const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  ProfScope ps(ctx, tag_id("gemm_nn", sizeof(T) == 8, tag));
   gemm_nn_kernel<T><<<dim3(tm, tn), 256, 0, ctx->stream>>>(M, N, K, (const C*)A, lda, (const C*)B,
                                                            ldb, (C*)Cm, ldc, (T)ar, (T)ai, (T)br, (T)bi);
   KSS_CHECK_CUDA(cudaGetLastError());
@@ -231,7 +245,7 @@ void run_nn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void
 }  // namespace
 
 void gemm_cn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda, const void* B,
-             int ldb, void* C, int ldc, double ar, double ai, double br, double bi) {
+             int ldb, void* C, int ldc, double ar, double ai, double br, double bi, const char* tag) {
   if (M <= 0 || N <= 0) return;
   KSS_REQUIRE(K >= 0 && lda >= K && ldb >= K && ldc >= M, "gemm_cn: bad leading dimension");
   if (K == 0) {
@@ -241,22 +255,24 @@ void gemm_cn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda
     KSS_CHECK_CUDA(cudaMemset2DAsync(C, (size_t)ldc * es, 0, (size_t)M * es, N, ctx->stream));
     return;
   }
-  if (fp64) run_cn<double>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi);
-  else run_cn<float>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi);
+  if (fp64) run_cn<double>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi, tag);
+  else run_cn<float>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi, tag);
 }
 
 void gemm_nn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda, const void* B,
-             int ldb, void* C, int ldc, double ar, double ai, double br, double bi) {
+             int ldb, void* C, int ldc, double ar, double ai, double br, double bi, const char* tag) {
   if (M <= 0 || N <= 0) return;
   KSS_REQUIRE(K >= 0 && lda >= M && ldb >= K && ldc >= M, "gemm_nn: bad leading dimension");
-  if (fp64) run_nn<double>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi);
-  else run_nn<float>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi);
+  if (fp64) run_nn<double>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi, tag);
+  else run_nn<float>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi, tag);
 }
 
-void scale_rows(bool fp64, int M, int N, void* C, int ldc, const void* d, double s,
-                cudaStream_t st) {
+void scale_rows(kss_ctx ctx, bool fp64, int M, int N, void* C, int ldc, const void* d, double s) {
   const long long mn = (long long)M * N;
   if (!mn) return;
+  cudaStream_t st = ctx->stream;
+  static const int id = prof_register("scale_rows");
+  ProfScope ps(ctx, id);
   if (fp64)
     scale_rows_kernel<double><<<(unsigned)((mn + 255) / 256), 256, 0, st>>>(M, N, (double2*)C, ldc,
                                                                             (const double*)d, s);

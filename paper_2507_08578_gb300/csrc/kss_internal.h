@@ -76,6 +76,21 @@ struct KData {
   std::vector<double> beta_norm2;  // |beta_i|^2 per projector
 };
 
+// Kernel launch accounting: every launch of the library's kernels is counted; when profiling
+// is enabled a pair of CUDA events brackets each launch on the context stream.
+struct Prof {
+  bool on = false;
+  long long launches = 0;
+  std::vector<long long> count;  // per registered kernel name
+  std::vector<double> ms;
+  std::vector<cudaEvent_t> free_ev;
+  struct Pending { cudaEvent_t a, b; int id; };
+  std::vector<Pending> pending;
+};
+int prof_register(const char* name);   // process-wide id of a kernel name
+const char* prof_name(int id);
+int prof_names();
+
 }  // namespace kss
 
 struct kss_ctx_s {
@@ -89,6 +104,8 @@ struct kss_ctx_s {
   kss::DevBuf ws_gemm;             // split-K partial sums
   kss::DevBuf ws_cprj;             // projector coefficients
   kss::DevBuf stage_in, stage_out; // host-buffer entry point staging
+  kss::Prof prof;
+  int nsm = 0;
 };
 
 struct kss_sys_s {
@@ -113,6 +130,20 @@ struct kss_sys_s {
 
 namespace kss {
 
+// RAII bracket around one kernel launch (count + optional CUDA events on ctx->stream).
+struct ProfScope {
+  kss_ctx ctx;
+  int id;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(kss_ctx c, int id_);
+  ~ProfScope();
+};
+void prof_resolve(kss_ctx ctx);  // synchronise and fold pending event pairs into totals
+void prof_release(kss_ctx ctx);
+#define KSS_PROF(ctx, name)                                   \
+  static const int kss_prof_id_ = ::kss::prof_register(name); \
+  ::kss::ProfScope kss_prof_scope_((ctx), kss_prof_id_)
+
 // ---- setup kernels (setup_kernels.cu) ----
 void launch_vloc(kss_sys s, cudaStream_t st);
 void launch_projectors(kss_sys s, KData& kd, cudaStream_t st);
@@ -135,19 +166,18 @@ size_t local_workspace_bytes(kss_sys s, int ik, int nb, kss_precision prec);
 // C (M x N, col-major ldc) = alpha * A^H B + beta * C; A: K x M (lda), B: K x N (ldb)
 void gemm_cn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda, const void* B,
              int ldb, void* C, int ldc, double alpha_re, double alpha_im, double beta_re,
-             double beta_im);
+             double beta_im, const char* tag);
 // C (M x N) = alpha * A B + beta * C; A: M x K (lda), B: K x N (ldb)
 void gemm_nn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda, const void* B,
              int ldb, void* C, int ldc, double alpha_re, double alpha_im, double beta_re,
-             double beta_im);
+             double beta_im, const char* tag);
 // Scale row i of a complex (M x N, col-major) matrix by real d[i] * s.
-void scale_rows(bool fp64, int M, int N, void* C, int ldc, const void* d, double s,
-                cudaStream_t st);
+void scale_rows(kss_ctx ctx, bool fp64, int M, int N, void* C, int ldc, const void* d, double s);
 
 // ---- solver pieces (solver.cu) ----
-void random_block(bool fp64, void* X, int npw, int nb, int ld, uint64_t seed, int band0,
-                  cudaStream_t st);
-void residual_norms(bool fp64, const void* X, const void* HX, int npw, int nb, int ld,
-                    const double* w, double* r, cudaStream_t st);
+void random_block(kss_ctx ctx, bool fp64, void* X, int npw, int nb, int ld, uint64_t seed,
+                  int band0);
+void residual_norms(kss_ctx ctx, bool fp64, const void* X, const void* HX, int npw, int nb, int ld,
+                    const double* w, double* r);
 
 }  // namespace kss

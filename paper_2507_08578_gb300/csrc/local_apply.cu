@@ -401,12 +401,24 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
   const int nc = chunk_bands(s, ik, nb, sizeof(C));
   ctx->ws_local.ensure(slab_elems(s, ik) * nc * sizeof(C));
   a.work = ctx->ws_local.as<C>();
+  static const int ida = prof_register(f64 ? "local_pass_a<f64>" : "local_pass_a<f32>");
+  static const int idb = prof_register(f64 ? "local_pass_b<f64>" : "local_pass_b<f32>");
+  static const int idc = prof_register(f64 ? "local_pass_c<f64>" : "local_pass_c<f32>");
   for (int n0 = 0; n0 < nb; n0 += nc) {
     const int m = std::min(nc, nb - n0);
     a.n0 = n0;
-    pass_a<T><<<dim3(a.W3, m), kThreads, sa, ctx->stream>>>(a);
-    pass_b<T><<<dim3(a.N1, m), kThreads, sb, ctx->stream>>>(a);
-    pass_c<T><<<dim3(a.W3, m), kThreads, sa, ctx->stream>>>(a);
+    {
+      ProfScope ps(ctx, ida);
+      pass_a<T><<<dim3(a.W3, m), kThreads, sa, ctx->stream>>>(a);
+    }
+    {
+      ProfScope ps(ctx, idb);
+      pass_b<T><<<dim3(a.N1, m), kThreads, sb, ctx->stream>>>(a);
+    }
+    {
+      ProfScope ps(ctx, idc);
+      pass_c<T><<<dim3(a.W3, m), kThreads, sa, ctx->stream>>>(a);
+    }
   }
   KSS_CHECK_CUDA(cudaGetLastError());
 }
@@ -435,9 +447,9 @@ void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, v
   if (s->nproj) {
     ctx->ws_cprj.ensure((size_t)s->nproj * nb * es);
     gemm_cn(ctx, f64, s->nproj, nb, kd.npw, f64 ? kd.d_beta64.p : kd.d_beta32.p, kd.npw, psi, ld,
-            ctx->ws_cprj.p, s->nproj, 1.0, 0.0, 0.0, 0.0);
-    scale_rows(f64, s->nproj, nb, ctx->ws_cprj.p, s->nproj, f64 ? s->d_D64.p : s->d_D32.p,
-               c.alpha, ctx->stream);
+            ctx->ws_cprj.p, s->nproj, 1.0, 0.0, 0.0, 0.0, "cprj");
+    scale_rows(ctx, f64, s->nproj, nb, ctx->ws_cprj.p, s->nproj, f64 ? s->d_D64.p : s->d_D32.p,
+               c.alpha);
   }
   if (f64)
     run_local<double>(s, ik, nb, psi, psi_prev, out, ld, c);
@@ -446,7 +458,7 @@ void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, v
   // Nonlocal, second half: out += beta (alpha D C).
   if (s->nproj)
     gemm_nn(ctx, f64, kd.npw, nb, s->nproj, f64 ? kd.d_beta64.p : kd.d_beta32.p, kd.npw,
-            ctx->ws_cprj.p, s->nproj, out, ld, 1.0, 0.0, 1.0, 0.0);
+            ctx->ws_cprj.p, s->nproj, out, ld, 1.0, 0.0, 1.0, 0.0, "nonlocal");
 }
 
 }  // namespace kss

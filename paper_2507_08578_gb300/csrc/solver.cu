@@ -126,18 +126,24 @@ void ctx_release_solver(kss_ctx ctx) {
   ctx->cusolver = nullptr;
 }
 
-void random_block(bool fp64, void* X, int npw, int nb, int ld, uint64_t seed, int band0,
-                  cudaStream_t st) {
+void random_block(kss_ctx ctx, bool fp64, void* X, int npw, int nb, int ld, uint64_t seed,
+                  int band0) {
   const long long n = (long long)npw * nb;
   if (!n) return;
+  cudaStream_t st = ctx->stream;
+  static const int id = prof_register("random_block");
+  ProfScope ps(ctx, id);
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   if (fp64) random_kernel<double2><<<blocks_for(n), 256, 0, st>>>((double2*)X, npw, nb, ld, key, band0);
   else random_kernel<float2><<<blocks_for(n), 256, 0, st>>>((float2*)X, npw, nb, ld, key, band0);
   KSS_CHECK_CUDA(cudaGetLastError());
 }
 
-void residual_norms(bool fp64, const void* X, const void* HX, int npw, int nb, int ld,
-                    const double* w, double* r, cudaStream_t st) {
+void residual_norms(kss_ctx ctx, bool fp64, const void* X, const void* HX, int npw, int nb, int ld,
+                    const double* w, double* r) {
+  cudaStream_t st = ctx->stream;
+  static const int id = prof_register("residual_norms");
+  ProfScope ps(ctx, id);
   if (fp64) residual_kernel<double2><<<nb, 256, 0, st>>>((const double2*)X, (const double2*)HX, npw, ld, w, r);
   else residual_kernel<float2><<<nb, 256, 0, st>>>((const float2*)X, (const float2*)HX, npw, ld, w, r);
   KSS_CHECK_CUDA(cudaGetLastError());
@@ -202,26 +208,37 @@ void rayleigh_ritz(kss_solver_s* s, bool f64, const void* Y, const void* HY, voi
   const int nb = s->nb, npw = s->npw;
   const long long nn = (long long)nb * nb;
   if (f64) {
-    gemm_cn(ctx, true, nb, nb, npw, Y, npw, Y, npw, s->S.p, nb, 1, 0, 0, 0);
-    gemm_cn(ctx, true, nb, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, 1, 0, 0, 0);
+    gemm_cn(ctx, true, nb, nb, npw, Y, npw, Y, npw, s->S.p, nb, 1, 0, 0, 0, "gram");
+    gemm_cn(ctx, true, nb, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, 1, 0, 0, 0, "gram");
   } else {
-    gemm_cn(ctx, false, nb, nb, npw, Y, npw, Y, npw, s->S32.p, nb, 1, 0, 0, 0);
-    gemm_cn(ctx, false, nb, nb, npw, Y, npw, HY, npw, s->Hs32.p, nb, 1, 0, 0, 0);
-    c64_to_c128<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->S32.as<float2>(), s->S.as<double2>(), nn);
-    c64_to_c128<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hs32.as<float2>(), s->Hs.as<double2>(), nn);
+    gemm_cn(ctx, false, nb, nb, npw, Y, npw, Y, npw, s->S32.p, nb, 1, 0, 0, 0, "gram");
+    gemm_cn(ctx, false, nb, nb, npw, Y, npw, HY, npw, s->Hs32.p, nb, 1, 0, 0, 0, "gram");
+    static const int idc = prof_register("convert_c64_c128");
+    {
+      ProfScope ps(ctx, idc);
+      c64_to_c128<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->S32.as<float2>(), s->S.as<double2>(), nn);
+    }
+    {
+      ProfScope ps(ctx, idc);
+      c64_to_c128<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hs32.as<float2>(), s->Hs.as<double2>(), nn);
+    }
   }
   subspace_eig(s);
   int info = 0;
   KSS_CHECK_CUDA(cudaMemcpyAsync(&info, s->info.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   if (f64) {
-    gemm_nn(ctx, true, npw, nb, nb, Y, npw, s->Hs.p, nb, Xo, npw, 1, 0, 0, 0);
-    gemm_nn(ctx, true, npw, nb, nb, HY, npw, s->Hs.p, nb, HXo, npw, 1, 0, 0, 0);
+    gemm_nn(ctx, true, npw, nb, nb, Y, npw, s->Hs.p, nb, Xo, npw, 1, 0, 0, 0, "rotate");
+    gemm_nn(ctx, true, npw, nb, nb, HY, npw, s->Hs.p, nb, HXo, npw, 1, 0, 0, 0, "rotate");
   } else {
-    c128_to_c64<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hs.as<double2>(), s->Q32.as<float2>(), nn);
-    gemm_nn(ctx, false, npw, nb, nb, Y, npw, s->Q32.p, nb, Xo, npw, 1, 0, 0, 0);
-    gemm_nn(ctx, false, npw, nb, nb, HY, npw, s->Q32.p, nb, HXo, npw, 1, 0, 0, 0);
+    {
+      static const int idq = prof_register("convert_c128_c64");
+      ProfScope ps(ctx, idq);
+      c128_to_c64<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hs.as<double2>(), s->Q32.as<float2>(), nn);
+    }
+    gemm_nn(ctx, false, npw, nb, nb, Y, npw, s->Q32.p, nb, Xo, npw, 1, 0, 0, 0, "rotate");
+    gemm_nn(ctx, false, npw, nb, nb, HY, npw, s->Q32.p, nb, HXo, npw, 1, 0, 0, 0, "rotate");
   }
-  residual_norms(f64, Xo, HXo, npw, nb, npw, s->W.as<double>(), s->resid_d.as<double>(), ctx->stream);
+  residual_norms(ctx, f64, Xo, HXo, npw, nb, npw, s->W.as<double>(), s->resid_d.as<double>());
   s->evals.resize(nb);
   s->resid.resize(nb);
   KSS_CHECK_CUDA(cudaMemcpyAsync(s->evals.data(), s->W.p, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -284,14 +301,21 @@ void refine_fp64(kss_solver_s* s) {
   const size_t bytes = (size_t)s->npw * s->nb * 16;
   for (int i = 0; i < 4; ++i) s->r64[i].ensure(bytes);
   const long long n = (long long)s->npw * s->nb;
-  copy_block<float2, double2><<<blocks_for(n), 256, 0, ctx->stream>>>(
-      s->blk[s->ix].as<float2>(), s->npw, s->r64[0].as<double2>(), s->npw, s->npw, s->nb);
+  static const int idp = prof_register("copy_block");
+  {
+    ProfScope ps(ctx, idp);
+    copy_block<float2, double2><<<blocks_for(n), 256, 0, ctx->stream>>>(
+        s->blk[s->ix].as<float2>(), s->npw, s->r64[0].as<double2>(), s->npw, s->npw, s->nb);
+  }
   KSS_CHECK_CUDA(cudaGetLastError());
   apply_block(s, true, s->r64[0].p, s->r64[1].p);
   rayleigh_ritz(s, true, s->r64[0].p, s->r64[1].p, s->r64[2].p, s->r64[3].p);
   // Keep the refined vectors as the current iterate (demoted to complex64).
-  copy_block<double2, float2><<<blocks_for(n), 256, 0, ctx->stream>>>(
-      s->r64[2].as<double2>(), s->npw, s->blk[s->ix].as<float2>(), s->npw, s->npw, s->nb);
+  {
+    ProfScope ps(ctx, idp);
+    copy_block<double2, float2><<<blocks_for(n), 256, 0, ctx->stream>>>(
+        s->r64[2].as<double2>(), s->npw, s->blk[s->ix].as<float2>(), s->npw, s->npw, s->nb);
+  }
   KSS_CHECK_CUDA(cudaGetLastError());
 }
 
@@ -410,8 +434,8 @@ kss_status kss_solver_create(kss_sys sys, int ik, int nband, const kss_solve_opt
                                          nx, cudaMemcpyDeviceToDevice, ctx->stream));
     }
     if (nx < s->nb)
-      random_block(s->f64, (char*)s->blk[0].p + (size_t)nx * s->npw * esize(s->f64), s->npw,
-                   s->nb - nx, s->npw, o.seed, nx, ctx->stream);
+      random_block(ctx, s->f64, (char*)s->blk[0].p + (size_t)nx * s->npw * esize(s->f64), s->npw,
+                   s->nb - nx, s->npw, o.seed, nx);
     s->o.x0 = nullptr;  // copied; the caller's buffer is not referenced again
     sys->nsolvers += 1;
     *out = s.release();

@@ -93,6 +93,9 @@ def lib() -> ctypes.CDLL:
             "kss_solver_results": ([P, P, P, P, c_int, POINTER(kss_solve_stats)], c_int),
             "kss_chebfi_solve": ([P, c_int, c_int, POINTER(kss_solve_opts), P, P, c_int, P,
                                   POINTER(kss_solve_stats)], c_int),
+            "kss_profile_enable": ([P, c_int], c_int),
+            "kss_profile_count": ([P, POINTER(c_int), POINTER(c_longlong)], c_int),
+            "kss_profile_entry": ([P, c_int, POINTER(c_char_p), POINTER(c_longlong), POINTER(c_double)], c_int),
         }
         for name, (args, res) in sig.items():
             if hasattr(L, name):
@@ -361,3 +364,36 @@ def kss_chebfi_solve(sys: System, ik: int, nband: int, opts: kss_solve_opts, eve
         return ev, rs, stats_dict(stats), st
     _check(st, sys.ctx)
     return ev, rs, stats_dict(stats), st
+
+
+# --------------------------------------------------------------------------------------------
+# launch accounting / per-kernel timing
+
+def kss_profile_enable(ctx, enable: bool = True):
+    _check(lib().kss_profile_enable(ctx, 1 if enable else 0), ctx)
+
+
+def kss_profile_count(ctx):
+    n = c_int()
+    l = c_longlong()
+    _check(lib().kss_profile_count(ctx, byref(n), byref(l)), ctx)
+    return n.value, l.value
+
+
+def kss_profile_entry(ctx, i: int):
+    name = c_char_p()
+    l = c_longlong()
+    ms = c_double()
+    _check(lib().kss_profile_entry(ctx, i, byref(name), byref(l), byref(ms)), ctx)
+    return name.value.decode(), l.value, ms.value
+
+
+def profile_table(ctx) -> dict:
+    """{kernel name: (launches, total_ms)} since the last kss_profile_enable."""
+    n, _ = kss_profile_count(ctx)
+    out = {}
+    for i in range(n):
+        name, l, ms = kss_profile_entry(ctx, i)
+        if l:
+            out[name] = (l, ms)
+    return out
