@@ -62,8 +62,10 @@ typedef struct kss_solver_s* kss_solver;
  * Context
  * ------------------------------------------------------------------------------------------ */
 
-/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to queue work on
- * (borrowed, must outlive the context) or NULL for a stream the context creates and owns.
+/* Create a context on CUDA device `device` that queues all its work on `cuda_stream`, a
+ * cudaStream_t of that device (borrowed: it must outlive the context).  NULL is the CUDA legacy
+ * default stream (stream 0), the stream PyTorch uses unless told otherwise, so work queued by
+ * the caller on that stream and by the library is ordered.
  * Errors: KSS_EINVAL (out == NULL), KSS_ECUDA (no device / bad device index). */
 kss_status kss_create(kss_ctx* out, int device, void* cuda_stream);
 

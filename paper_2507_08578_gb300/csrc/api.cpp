@@ -187,16 +187,8 @@ kss_status kss_create(kss_ctx* out, int device, void* cuda_stream) {
     delete ctx;
     return KSS_ECUDA;
   }
-  if (cuda_stream) {
-    ctx->stream = (cudaStream_t)cuda_stream;
-    ctx->own_stream = false;
-  } else {
-    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      delete ctx;
-      return KSS_ECUDA;
-    }
-    ctx->own_stream = true;
-  }
+  ctx->stream = (cudaStream_t)cuda_stream;  // NULL: legacy default stream
+  ctx->own_stream = false;
   *out = ctx;
   return KSS_OK;
 }

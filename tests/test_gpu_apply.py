@@ -238,3 +238,46 @@ def test_setup_rejects_bad_input(ctx):
         K.kss_setup(ctx, s.lattice, s.ecut, s.kpts, s.pos, s.D, fft_box=(29, 29, 29))  # not 2,3,5-smooth
     with pytest.raises(K.KssError):
         K.kss_setup(ctx, s.lattice, -1.0, s.kpts, s.pos, s.D)
+
+
+def test_stream_ordering_with_torch(ctx):
+    """Work queued by torch and by the library on the same stream is ordered: an asynchronous
+    pinned-host upload followed at once by kss_apply_H (no synchronisation in between), on the
+    default stream and on a user stream."""
+    import torch
+    s = W.config1()
+    p = O.build_problem(s, 0)
+    c = W.random_block(p.basis.npw, 8, seed=21)
+    ref = p.apply(c)
+    host = torch.from_numpy(c).pin_memory()
+    # default stream (the context's stream)
+    sysh = setup(ctx, s)
+    try:
+        for _ in range(3):
+            psi = torch.empty(host.shape, dtype=host.dtype, device="cuda")
+            psi.copy_(host, non_blocking=True)
+            out = torch.empty_like(psi)
+            K.kss_apply_H(sysh, 0, psi, out)
+            res = torch.empty(out.shape, dtype=out.dtype).pin_memory()
+            res.copy_(out, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            assert rel_err_rows(res.numpy(), ref) < FP64_TOL
+    finally:
+        K.kss_sys_destroy(sysh)
+    # a separate user stream with its own context
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        c2 = K.kss_create(0, st.cuda_stream)
+        sys2 = setup(c2, s)
+        try:
+            psi = torch.empty(host.shape, dtype=host.dtype, device="cuda")
+            psi.copy_(host, non_blocking=True)
+            out = torch.empty_like(psi)
+            K.kss_apply_H(sys2, 0, psi, out)
+            res = torch.empty(out.shape, dtype=out.dtype).pin_memory()
+            res.copy_(out, non_blocking=True)
+            st.synchronize()
+            assert rel_err_rows(res.numpy(), ref) < FP64_TOL
+        finally:
+            K.kss_sys_destroy(sys2)
+            K.kss_destroy(c2)
