@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--nk", type=int, default=0, help="use only the first nk k-points (profiling)")
     return ap.parse_args()
 
 
@@ -262,6 +263,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     ctx = K.kss_create(local_rank, stream.cuda_stream)
     s = workload()
     prec = K.KSS_PREC_FP64 if args.form == "fp64" else K.KSS_PREC_MIXED
+    if args.nk > 0:
+        s.kpts = s.kpts[: args.nk]
     sysh = K.kss_setup(ctx, s.lattice, s.ecut, s.kpts, s.pos, s.D, fft_box=s.fft_box)
     nk = len(s.kpts)
     solvers = []
@@ -288,11 +291,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     K.kss_profile_enable(ctx, True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     for _ in range(args.steps):
         for sv in solvers:
             K.kss_solver_step(sv)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
