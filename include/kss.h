@@ -172,6 +172,19 @@ kss_status kss_cheb_step(kss_sys sys, int ik, int nb, const void* psi, const voi
 kss_status kss_apply_H_host(kss_sys sys, int ik, int nb, const void* psi_host, void* hpsi_host,
                             int ld, kss_precision prec);
 
+/* Complex GEMM of the path (projector products, Eq. ham-nl of §5.2; Gram / projected-H /
+ * rotation products of Rayleigh-Ritz, §5.1), exposed for direct testing and reuse.
+ *   op 0: C = alpha A^H B + beta C, A is K x M (lda >= K), B is K x N (ldb >= K)
+ *   op 1: C = alpha A B + beta C,   A is M x K (lda >= M), B is K x N (ldb >= K)
+ * Column-major DEVICE matrices; C is M x N (ldc >= M) and must not overlap A or B.
+ * KSS_PREC_FP64: complex128 on the FP64 pipe.  KSS_PREC_MIXED: complex64 on the tensor cores,
+ * every FP32 value split into BF16 hi + lo, products hi*hi + hi*lo + lo*hi accumulated in FP32
+ * (relative error of order 1e-5).  Errors: KSS_EINVAL, KSS_ETIMEOUT (a bounded device wait gave
+ * up; the context stays usable). */
+kss_status kss_gemm(kss_ctx ctx, int op, int M, int N, int K, const void* A, int lda, const void* B,
+                    int ldb, void* C, int ldc, double alpha_re, double alpha_im, double beta_re,
+                    double beta_im, kss_precision prec);
+
 /* ------------------------------------------------------------------------------------------
  * Chebyshev-filtered subspace iteration with Rayleigh-Ritz (§5.1)
  * ------------------------------------------------------------------------------------------ */

@@ -208,6 +208,10 @@ kss_status kss_destroy(kss_ctx ctx) {
   ctx->ws_cprj.release();
   ctx->stage_in.release();
   ctx->stage_out.release();
+  ctx->tc_a.release();
+  ctx->tc_b.release();
+  ctx->tc_part.release();
+  ctx->tc_err.release();
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return KSS_OK;
@@ -497,6 +501,35 @@ kss_status kss_apply_H_host(kss_sys sys, int ik, int nb, const void* psi_host, v
             prec);
     KSS_CHECK_CUDA(cudaMemcpyAsync(hpsi_host, ctx->stage_out.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+kss_status kss_gemm(kss_ctx ctx, int op, int M, int N, int K, const void* A, int lda, const void* B,
+                    int ldb, void* C, int ldc, double alpha_re, double alpha_im, double beta_re,
+                    double beta_im, kss_precision prec) {
+  if (!ctx) return KSS_EINVAL;
+  return guard(ctx, [&] {
+    KSS_REQUIRE(op == 0 || op == 1, "op must be 0 (A^H B) or 1 (A B)");
+    KSS_REQUIRE(M >= 0 && N >= 0 && K >= 0, "negative size");
+    KSS_REQUIRE(prec == KSS_PREC_FP64 || prec == KSS_PREC_MIXED, "unknown precision");
+    if (M == 0 || N == 0) return;
+    KSS_REQUIRE(A && B && C, "null matrix");
+    KSS_REQUIRE(ldc >= M && (op == 0 ? (lda >= K && ldb >= K) : (lda >= M && ldb >= K)),
+                "bad leading dimension");
+    KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    if (prec == KSS_PREC_FP64) {
+      if (op == 0) gemm_cn(ctx, true, M, N, K, A, lda, B, ldb, C, ldc, alpha_re, alpha_im, beta_re, beta_im, "user");
+      else gemm_nn(ctx, true, M, N, K, A, lda, B, ldb, C, ldc, alpha_re, alpha_im, beta_re, beta_im, "user");
+    } else {
+      KSS_REQUIRE(K > 0 || (beta_re == 0 && beta_im == 0), "K == 0 with beta != 0 is not supported");
+      if (K == 0) {
+        KSS_CHECK_CUDA(cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)M * 8, N, ctx->stream));
+        return;
+      }
+      if (op == 0) tc_gemm_cn(ctx, M, N, K, A, lda, B, ldb, C, ldc, alpha_re, alpha_im, beta_re, beta_im, "user");
+      else tc_gemm_nn(ctx, M, N, K, A, lda, B, ldb, C, ldc, alpha_re, alpha_im, beta_re, beta_im, "user");
+      if (tc_error_flag(ctx, true)) fail(KSS_ETIMEOUT, "tensor-core GEMM: a bounded wait gave up");
+    }
   });
 }
 

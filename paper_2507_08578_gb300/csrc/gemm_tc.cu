@@ -1,0 +1,435 @@
+// Split-precision complex GEMMs on the 5th-generation tensor cores (tcgen05 + TMEM + TMA).
+//
+// Mixed-precision form of the projector products C = beta^H psi and H psi += beta C' (Eq. ham-nl
+// with the projectors and their coefficients in memory, §5.2) and of the subspace Gram / projected
+// H / rotation products of Rayleigh-Ritz (§5.1).
+//
+// Each complex product is written as one real GEMM D = A_tc * B_tc^T with both operands K-major
+// in BF16:
+//   * complex -> real: interleaved (re, im) pairs along K; the imaginary part comes from extra
+//     rows of one operand holding (im, -re) (for A^H B) or (im, re) / (re, -im) (for A B);
+//   * split precision: every FP32 value x = hi + lo with hi = bf16(x), lo = bf16(x - hi); the
+//     K axis is tripled so that one GEMM accumulates hi*hi + hi*lo + lo*hi in FP32 (TMEM).
+// The GEMM kernel: one CTA per 128 x 128 output tile and K split across CTAs; a TMA producer
+// thread fills a 6-stage ring of 128B-swizzled 128 x 64 BF16 tiles, one thread issues
+// tcgen05.mma (M=128, N=128, K=16) into a TMEM accumulator, and four warps read TMEM back with
+// tcgen05.ld and store FP32 partial sums.  A reduction kernel adds the K-splits in a fixed order
+// and forms the complex result.  Every mbarrier wait is bounded; on time-out the kernel raises
+// an error flag, drains its own copies, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "kss_internal.h"
+
+namespace kss {
+
+namespace {
+
+constexpr int TM = 128;   // UMMA M (rows of A_tc per tile)
+constexpr int TN = 128;   // UMMA N (rows of B_tc per tile)
+constexpr int TK = 64;    // BF16 per k-block: one 128-byte swizzle row
+constexpr int STAGES = 6;
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTileBytes = TM * TK * 2;  // 16 KB (A and B tiles are the same size)
+constexpr size_t kTcSmem = 1024 + (size_t)STAGES * 2 * kTileBytes + 256;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of the given parity to complete, at most kWaitNs; false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try(bar, parity))
+    if (globaltimer() - t0 > kWaitNs) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major, M = TM, N = TN.
+__host__ __device__ constexpr uint32_t instr_desc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               float* __restrict__ D, int Mr, int Nr, int kb_per_split, int kb_total,
+               int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = base;
+  unsigned char* sB = base + STAGES * kTileBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * kTileBytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + STAGES;
+  uint64_t* done = bars + 2 * STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  __shared__ int fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tm = blockIdx.x, tn = blockIdx.y;
+  const int kb0 = blockIdx.z * kb_per_split;
+  const int nkb = max(0, min(kb_total, kb0 + kb_per_split) - kb0);
+
+  if (tid == 0) {
+    fail = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(TN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(smem_u32(&empty[s]), ((kb / STAGES) & 1) ^ 1)) {
+        atomicExch(&fail, 1);
+        break;
+      }
+      if (*(volatile int*)&fail) break;
+      mbar_expect_tx(smem_u32(&full[s]), 2 * kTileBytes);
+      const int x = (kb0 + kb) * TK;
+      tma_load_2d(smem_u32(sA + s * kTileBytes), &tmA, x, tm * TM, smem_u32(&full[s]));
+      tma_load_2d(smem_u32(sB + s * kTileBytes), &tmB, x, tn * TN, smem_u32(&full[s]));
+      ++issued;
+    }
+    // Drain: every issued copy has landed before the CTA can leave (bounded).
+    for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
+      if (!mbar_wait(smem_u32(&full[kb % STAGES]), (kb / STAGES) & 1)) atomicExch(&fail, 1);
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = instr_desc();
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(smem_u32(&full[s]), (kb / STAGES) & 1)) {
+        atomicExch(&fail, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA + s * kTileBytes), b0 = smem_u32(sB + s * kTileBytes);
+#pragma unroll
+      for (int k = 0; k < TK / 16; ++k) {
+        const uint64_t ad = smem_desc(a0 + 32 * k), bd = smem_desc(b0 + 32 * k);
+        const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&empty[s])) : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(done)) : "memory");
+  }
+  __syncwarp();
+  // Epilogue: warp w owns TMEM lanes 32w..32w+31 (accumulator rows).
+  bool ok = mbar_wait(smem_u32(done), 0);
+  ok = __all_sync(0xffffffffu, ok);
+  if (!ok) atomicExch(&fail, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int row = tm * TM + warp * 32 + lane;
+  float* Dz = D + (size_t)blockIdx.z * Mr * Nr;
+  if (ok && nkb > 0) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < TN; c0 += 32) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < Mr) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = tn * TN + c0 + j;
+          if (col < Nr) Dz[(size_t)col * Mr + row] = __uint_as_float(r[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
+  if (tid == 0 && fail) atomicExch(err, 1);
+}
+
+// ---- operand preparation -------------------------------------------------------------------
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// K-major complex source (column c has K complex values at src + c*ld) -> BF16 rows of length
+// 3*Kp: role A = [hi | hi | lo], role B = [hi | lo | hi].  swap: use (im, -re) pairs.
+__global__ void prep_kmajor(const float2* __restrict__ src, long long ld, int K, int ncols, int Kp,
+                            __nv_bfloat16* __restrict__ dst, int row0, int roleB, int swap) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int half = Kp / 2;
+  if (idx >= (long long)ncols * half) return;
+  const int c = (int)(idx / half), k = (int)(idx - (long long)c * half);
+  float re = 0.f, im = 0.f;
+  if (k < K) {
+    const float2 v = src[(size_t)c * ld + k];
+    re = v.x;
+    im = v.y;
+  }
+  float u0 = re, u1 = im;
+  if (swap) { u0 = im; u1 = -re; }
+  __nv_bfloat16 h0, l0, h1, l1;
+  split_bf16(u0, h0, l0);
+  split_bf16(u1, h1, l1);
+  __nv_bfloat16* row = dst + (size_t)(row0 + c) * (3 * (size_t)Kp);
+  const int e = 2 * k;
+  row[e] = h0;
+  row[e + 1] = h1;
+  row[Kp + e] = roleB ? l0 : h0;
+  row[Kp + e + 1] = roleB ? l1 : h1;
+  row[2 * Kp + e] = roleB ? h0 : l0;
+  row[2 * Kp + e + 1] = roleB ? h1 : l1;
+}
+
+// M-major complex A (element (i, k) at src[k*ld + i]) -> BF16 K-major rows for C = A B:
+// row i: (re, -im) pairs, row M + i: (im, re) pairs, role A [hi | hi | lo].  32x32 smem transpose.
+__global__ void prep_mmajor(const float2* __restrict__ src, long long ld, int M, int K, int Kp,
+                            __nv_bfloat16* __restrict__ dst) {
+  __shared__ float2 t[32][33];
+  const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, i = i0 + threadIdx.x;
+    t[r][threadIdx.x] = (k < K && i < M) ? src[(size_t)k * ld + i] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int half = Kp / 2;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, k = k0 + threadIdx.x;
+    if (i >= M || k >= half) continue;
+    const float2 v = t[threadIdx.x][r];
+    __nv_bfloat16 hr, lr, hi_, li_, hmi, lmi;
+    split_bf16(v.x, hr, lr);
+    split_bf16(v.y, hi_, li_);
+    split_bf16(-v.y, hmi, lmi);
+    __nv_bfloat16* ra = dst + (size_t)i * (3 * (size_t)Kp);
+    __nv_bfloat16* rb = dst + (size_t)(M + i) * (3 * (size_t)Kp);
+    const int e = 2 * k;
+    ra[e] = hr; ra[e + 1] = hmi;
+    ra[Kp + e] = hr; ra[Kp + e + 1] = hmi;
+    ra[2 * Kp + e] = lr; ra[2 * Kp + e + 1] = lmi;
+    rb[e] = hi_; rb[e + 1] = hr;
+    rb[Kp + e] = hi_; rb[Kp + e + 1] = hr;
+    rb[2 * Kp + e] = li_; rb[2 * Kp + e + 1] = lr;
+  }
+}
+
+// C (complex, col-major ldc) = alpha * D + beta * C with D assembled from the K-split partials
+// (col-major Mr x Nr).  form 0 (A^H B): re = D(i, j), im = D(i, N + j); form 1 (A B):
+// re = D(i, j), im = D(M + i, j).
+__global__ void tc_combine(const float* __restrict__ P, int nsplit, int Mr, int Nr, int M, int N,
+                           int form, float2* __restrict__ C, long long ldc, float ar, float ai,
+                           float br, float bi) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)M * N) return;
+  const int i = (int)(idx % M), j = (int)(idx / M);
+  const size_t oR = (size_t)j * Mr + i;
+  const size_t oI = form == 0 ? (size_t)(N + j) * Mr + i : (size_t)j * Mr + (M + i);
+  float sr = 0.f, si = 0.f;
+  const size_t stride = (size_t)Mr * Nr;
+  for (int z = 0; z < nsplit; ++z) {
+    sr += P[z * stride + oR];
+    si += P[z * stride + oI];
+  }
+  float2 out;
+  out.x = ar * sr - ai * si;
+  out.y = ar * si + ai * sr;
+  float2* dst = C + (size_t)j * ldc + i;
+  if (br != 0.f || bi != 0.f) {
+    const float2 o = *dst;
+    out.x += br * o.x - bi * o.y;
+    out.y += br * o.y + bi * o.x;
+  }
+  *dst = out;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+      fail(KSS_ECUDA, "cuTensorMapEncodeTiled is not available");
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+CUtensorMap make_map(const void* base, int rows, int kt) {
+  CUtensorMap m;
+  std::memset(&m, 0, sizeof(m));
+  const cuuint64_t dims[2] = {(cuuint64_t)kt, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kt * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)TM};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                                 strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(KSS_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return m;
+}
+
+int sms(kss_ctx ctx) {
+  if (!ctx->nsm) {
+    int v = 0;
+    KSS_CHECK_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device));
+    ctx->nsm = v > 0 ? v : 1;
+  }
+  return ctx->nsm;
+}
+
+// D partials = A_tc (Mr x Kt) * B_tc (Nr x Kt)^T, then combine into complex C.
+void run_tc(kss_ctx ctx, const __nv_bfloat16* Atc, int Mr, const __nv_bfloat16* Btc, int Nr, int Kt,
+            int form, int M, int N, float2* C, int ldc, double ar, double ai, double br, double bi,
+            const char* tag) {
+  const int tmn = (Mr + TM - 1) / TM, tnn = (Nr + TN - 1) / TN;
+  const int kb_total = Kt / TK;
+  const int tiles = tmn * tnn;
+  int splits = std::max(1, std::min(kb_total, (sms(ctx) + tiles - 1) / tiles));
+  const int kps = (kb_total + splits - 1) / splits;
+  splits = (kb_total + kps - 1) / kps;
+  const size_t pbytes = (size_t)splits * Mr * Nr * sizeof(float);
+  ctx->tc_part.ensure(pbytes);
+  if (!ctx->tc_err.p) {
+    ctx->tc_err.alloc(sizeof(int));
+    KSS_CHECK_CUDA(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), ctx->stream));
+  }
+  const CUtensorMap ma = make_map(Atc, Mr, Kt), mb = make_map(Btc, Nr, Kt);
+  static bool attr = false;
+  if (!attr) {
+    KSS_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+    attr = true;
+  }
+  {
+    ProfScope ps(ctx, prof_register((std::string("tc_gemm_bf16x3:") + tag).c_str()));
+    tc_gemm_kernel<<<dim3(tmn, tnn, splits), kTcThreads, kTcSmem, ctx->stream>>>(
+        ma, mb, ctx->tc_part.as<float>(), Mr, Nr, kps, kb_total, ctx->tc_err.as<int>());
+  }
+  const long long mn = (long long)M * N;
+  {
+    ProfScope ps(ctx, prof_register((std::string("tc_combine:") + tag).c_str()));
+    tc_combine<<<(unsigned)((mn + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->tc_part.as<float>(), splits, Mr, Nr, M, N, form, C, ldc, (float)ar, (float)ai, (float)br, (float)bi);
+  }
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+int kpad(int K) { return ((2 * K + TK - 1) / TK) * TK; }
+
+}  // namespace
+
+// C (M x N) = alpha A^H B + beta C, complex64; A: K x M (lda), B: K x N (ldb).
+void tc_gemm_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+                void* C, int ldc, double ar, double ai, double br, double bi, const char* tag) {
+  if (M <= 0 || N <= 0 || K <= 0) return;
+  const int Kp = kpad(K), Kt = 3 * Kp;
+  const size_t abytes = (size_t)M * Kt * 2, bbytes = (size_t)2 * N * Kt * 2;
+  ctx->tc_a.ensure(abytes);
+  ctx->tc_b.ensure(bbytes);
+  __nv_bfloat16* Atc = ctx->tc_a.as<__nv_bfloat16>();
+  __nv_bfloat16* Btc = ctx->tc_b.as<__nv_bfloat16>();
+  {
+    ProfScope ps(ctx, prof_register("tc_prep"));
+    const long long na = (long long)M * (Kp / 2), nb = (long long)N * (Kp / 2);
+    prep_kmajor<<<(unsigned)((na + 255) / 256), 256, 0, ctx->stream>>>((const float2*)A, lda, K, M, Kp, Atc, 0, 0, 0);
+    prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, 0, 1, 0);
+    prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, N, 1, 1);
+  }
+  run_tc(ctx, Atc, M, Btc, 2 * N, Kt, 0, M, N, (float2*)C, ldc, ar, ai, br, bi, tag);
+}
+
+// C (M x N) = alpha A B + beta C, complex64; A: M x K (lda, M contiguous), B: K x N (ldb).
+void tc_gemm_nn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+                void* C, int ldc, double ar, double ai, double br, double bi, const char* tag) {
+  if (M <= 0 || N <= 0 || K <= 0) return;
+  const int Kp = kpad(K), Kt = 3 * Kp;
+  const size_t abytes = (size_t)2 * M * Kt * 2, bbytes = (size_t)N * Kt * 2;
+  ctx->tc_a.ensure(abytes);
+  ctx->tc_b.ensure(bbytes);
+  __nv_bfloat16* Atc = ctx->tc_a.as<__nv_bfloat16>();
+  __nv_bfloat16* Btc = ctx->tc_b.as<__nv_bfloat16>();
+  {
+    ProfScope ps(ctx, prof_register("tc_prep"));
+    dim3 g((M + 31) / 32, (Kp / 2 + 31) / 32);
+    prep_mmajor<<<g, dim3(32, 8), 0, ctx->stream>>>((const float2*)A, lda, M, K, Kp, Atc);
+    const long long nb = (long long)N * (Kp / 2);
+    prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, 0, 1, 0);
+  }
+  run_tc(ctx, Atc, 2 * M, Btc, N, Kt, 1, M, N, (float2*)C, ldc, ar, ai, br, bi, tag);
+}
+
+// Device-side failure flag of the tensor-core kernels (bounded waits that gave up).
+int tc_error_flag(kss_ctx ctx, bool reset) {
+  if (!ctx->tc_err.p) return 0;
+  int v = 0;
+  KSS_CHECK_CUDA(cudaMemcpyAsync(&v, ctx->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (reset && v) KSS_CHECK_CUDA(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), ctx->stream));
+  return v;
+}
+
+}  // namespace kss

@@ -104,6 +104,8 @@ struct kss_ctx_s {
   kss::DevBuf ws_gemm;             // split-K partial sums
   kss::DevBuf ws_cprj;             // projector coefficients
   kss::DevBuf stage_in, stage_out; // host-buffer entry point staging
+  kss::DevBuf tc_a, tc_b, tc_part;  // tensor-core GEMM operands (BF16 split) and partial sums
+  kss::DevBuf tc_err;               // device failure flag of the tensor-core kernels
   kss::Prof prof;
   int nsm = 0;
 };
@@ -171,6 +173,12 @@ void gemm_cn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda
 void gemm_nn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda, const void* B,
              int ldb, void* C, int ldc, double alpha_re, double alpha_im, double beta_re,
              double beta_im, const char* tag);
+// Complex64 GEMMs on the tensor cores (BF16 hi/lo split, FP32 accumulation in TMEM).
+void tc_gemm_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+                void* C, int ldc, double ar, double ai, double br, double bi, const char* tag);
+void tc_gemm_nn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+                void* C, int ldc, double ar, double ai, double br, double bi, const char* tag);
+int tc_error_flag(kss_ctx ctx, bool reset);
 // Scale row i of a complex (M x N, col-major) matrix by real d[i] * s.
 void scale_rows(kss_ctx ctx, bool fp64, int M, int N, void* C, int ldc, const void* d, double s);
 

@@ -93,6 +93,8 @@ def lib() -> ctypes.CDLL:
             "kss_solver_results": ([P, P, P, P, c_int, POINTER(kss_solve_stats)], c_int),
             "kss_chebfi_solve": ([P, c_int, c_int, POINTER(kss_solve_opts), P, P, c_int, P,
                                   POINTER(kss_solve_stats)], c_int),
+            "kss_gemm": ([P, c_int, c_int, c_int, c_int, P, c_int, P, c_int, P, c_int, c_double,
+                          c_double, c_double, c_double, c_int], c_int),
             "kss_profile_enable": ([P, c_int], c_int),
             "kss_profile_count": ([P, POINTER(c_int), POINTER(c_longlong)], c_int),
             "kss_profile_entry": ([P, c_int, POINTER(c_char_p), POINTER(c_longlong), POINTER(c_double)], c_int),
@@ -397,3 +399,18 @@ def profile_table(ctx) -> dict:
         if l:
             out[name] = (l, ms)
     return out
+
+
+def kss_gemm(ctx, op: int, A, B, C, alpha=1.0, beta=0.0, prec: int = KSS_PREC_FP64):
+    """op 0: C = alpha A^H B + beta C; op 1: C = alpha A B + beta C.  Matrices are torch tensors
+    holding column-major matrices as (ncols, ld) row-major arrays (one column per row)."""
+    ka, lda = int(A.shape[0]), int(A.shape[1])
+    kb, ldb = int(B.shape[0]), int(B.shape[1])
+    n, ldc = int(C.shape[0]), int(C.shape[1])
+    if op == 0:
+        M, K = ka, lda
+    else:
+        K, M = ka, lda
+    _check(lib().kss_gemm(ctx, op, M, n, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc,
+                          complex(alpha).real, complex(alpha).imag, complex(beta).real,
+                          complex(beta).imag, prec), ctx)
