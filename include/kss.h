@@ -172,6 +172,37 @@ kss_status kss_cheb_step(kss_sys sys, int ik, int nb, const void* psi, const voi
 kss_status kss_apply_H_host(kss_sys sys, int ik, int nb, const void* psi_host, void* hpsi_host,
                             int ld, kss_precision prec);
 
+/* Size of the static device scratch array used by kss_apply_H_noalloc (64 MiB). */
+#define KSS_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+/* kss_apply_H for callers that cannot allocate device memory.  The paper has no counterpart:
+ * this is a deployment variant of the H application above.
+ *
+ * Who needs it: code that must not call cudaMalloc/cudaFree at this point -- work recorded
+ * while a CUDA stream is being captured into a graph, a host whose device memory belongs to
+ * another allocator (a framework's caching allocator or a fixed-budget pool), or a latency-
+ * critical loop where an allocation and the device-wide synchronisation of cudaFree are not
+ * acceptable.  kss_apply_H may grow the context's workspaces; this call never allocates: it
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Same arguments, layout and result as kss_apply_H (psi, hpsi: caller-owned DEVICE band blocks
+ * [nb][ld]).  Every temporary (the FFT slab of a band chunk, the projector coefficients, the
+ * split-K partial sums) lives in one file-scope device array of KSS_NOALLOC_SCRATCH_BYTES that
+ * every GPU which loads the library holds until the process exits.  The nonlocal products run
+ * on the CUDA cores in both precisions (the tensor-core path needs operand buffers larger than
+ * the scratch), so MIXED results agree with kss_apply_H to single-precision rounding.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, once
+ * per device, with that device current); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents; nothing in it needs to start
+ * at zero (every byte read is written first by the same call).  Calls whose work overlaps on
+ * the GPU (two streams, or two contexts on one device) race on the array: order them.
+ * Errors: as kss_apply_H, plus KSS_EINVAL with a message when one band's FFT slab plus the
+ * projector coefficients and one set of partial sums exceed KSS_NOALLOC_SCRATCH_BYTES (split
+ * the band block).  Launches are not counted by kss_profile_*. */
+kss_status kss_apply_H_noalloc(kss_sys sys, int ik, int nb, const void* psi, void* hpsi, int ld,
+                               kss_precision prec);
+
 /* Complex GEMM of the path (projector products, Eq. ham-nl of §5.2; Gram / projected-H /
  * rotation products of Rayleigh-Ritz, §5.1), exposed for direct testing and reuse.
  *   op 0: C = alpha A^H B + beta C, A is K x M (lda >= K), B is K x N (ldb >= K)

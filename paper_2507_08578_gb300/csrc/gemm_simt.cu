@@ -259,6 +259,65 @@ void gemm_cn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda
   else run_cn<float>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi, tag);
 }
 
+// gemm_cn with a caller-provided partial-sum buffer (no allocation, no profiling events): the
+// K split is limited to what fits in partial_bytes.  Returns false if even one split does not fit.
+bool gemm_cn_ws(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda, const void* B,
+                int ldb, void* C, int ldc, void* partials, size_t partial_bytes) {
+  if (M <= 0 || N <= 0) return true;
+  KSS_REQUIRE(K > 0 && lda >= K && ldb >= K && ldc >= M, "gemm_cn_ws: bad size");
+  const size_t es = fp64 ? 16 : 8;
+  const size_t per = (size_t)M * N * es;
+  const int maxs = (int)std::min<size_t>(partial_bytes / per, 1 << 20);
+  if (maxs < 1) return false;
+  const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  const int tiles = tm * tn;
+  const int target = 4 * sm_count(ctx);
+  int splits = std::max(1, std::min({(target + tiles - 1) / tiles, (K + 63) / 64, maxs}));
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  splits = (K + kchunk - 1) / kchunk;
+  const long long mn = (long long)M * N;
+  if (fp64) {
+    gemm_cn_partial<double><<<dim3(tm, tn, splits), 256, 0, ctx->stream>>>(
+        M, N, K, (const double2*)A, lda, (const double2*)B, ldb, (double2*)partials, kchunk);
+    gemm_reduce<double><<<(unsigned)((mn + 255) / 256), 256, 0, ctx->stream>>>(
+        M, N, splits, (const double2*)partials, (double2*)C, ldc, 1.0, 0.0, 0.0, 0.0);
+  } else {
+    gemm_cn_partial<float><<<dim3(tm, tn, splits), 256, 0, ctx->stream>>>(
+        M, N, K, (const float2*)A, lda, (const float2*)B, ldb, (float2*)partials, kchunk);
+    gemm_reduce<float><<<(unsigned)((mn + 255) / 256), 256, 0, ctx->stream>>>(
+        M, N, splits, (const float2*)partials, (float2*)C, ldc, 1.f, 0.f, 0.f, 0.f);
+  }
+  KSS_CHECK_CUDA(cudaGetLastError());
+  return true;
+}
+
+void scale_rows_noprof(bool fp64, int M, int N, void* C, int ldc, const void* d, double s,
+                       cudaStream_t st) {
+  const long long mn = (long long)M * N;
+  if (!mn) return;
+  if (fp64)
+    scale_rows_kernel<double><<<(unsigned)((mn + 255) / 256), 256, 0, st>>>(M, N, (double2*)C, ldc,
+                                                                            (const double*)d, s);
+  else
+    scale_rows_kernel<float><<<(unsigned)((mn + 255) / 256), 256, 0, st>>>(M, N, (float2*)C, ldc,
+                                                                          (const float*)d, (float)s);
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+void gemm_nn_noprof(bool fp64, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+                    void* C, int ldc, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  if (fp64)
+    gemm_nn_kernel<double><<<dim3(tm, tn), 256, 0, st>>>(M, N, K, (const double2*)A, lda, (const double2*)B,
+                                                         ldb, (double2*)C, ldc, 1.0, 0.0, 1.0, 0.0);
+  else
+    gemm_nn_kernel<float><<<dim3(tm, tn), 256, 0, st>>>(M, N, K, (const float2*)A, lda, (const float2*)B,
+                                                        ldb, (float2*)C, ldc, 1.f, 0.f, 1.f, 0.f);
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
 void gemm_nn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda, const void* B,
              int ldb, void* C, int ldc, double ar, double ai, double br, double bi, const char* tag) {
   if (M <= 0 || N <= 0) return;

@@ -163,6 +163,16 @@ struct ChebCoef {
 void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, void* out, int ld,
              ChebCoef c, kss_precision prec);
 size_t local_workspace_bytes(kss_sys s, int ik, int nb, kss_precision prec);
+// Caller-provided workspace forms (used by the entry point that allocates nothing).
+size_t local_slab_bytes_per_band(kss_sys s, int ik, kss_precision prec);
+void local_apply_ws(kss_sys s, int ik, int nb, const void* psi, void* out, int ld,
+                    kss_precision prec, void* work, int nc);
+bool gemm_cn_ws(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda, const void* B,
+                int ldb, void* C, int ldc, void* partials, size_t partial_bytes);
+void scale_rows_noprof(bool fp64, int M, int N, void* C, int ldc, const void* d, double s,
+                       cudaStream_t st);
+void gemm_nn_noprof(bool fp64, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+                    void* C, int ldc, cudaStream_t st);
 
 // ---- complex GEMMs (gemm_simt.cu) ----
 // C (M x N, col-major ldc) = alpha * A^H B + beta * C; A: K x M (lda), B: K x N (ldb)

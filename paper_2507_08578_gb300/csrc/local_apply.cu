@@ -756,7 +756,99 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
   KSS_CHECK_CUDA(cudaGetLastError());
 }
 
+// The local passes on a caller-provided slab workspace of nc bands (no allocation, no profiling
+// events).  Same kernels and launch shapes as run_local.
+template <typename T>
+void run_local_ws(kss_sys s, int ik, int nb, const void* psi, void* out, int ld, void* work, int nc) {
+  using C = typename CT<T>::C;
+  const bool f64 = sizeof(T) == 8;
+  kss_ctx ctx = s->ctx;
+  KData& kd = s->k[ik];
+  LocalArgs<T> a{};
+  a.N1 = s->N[0];
+  a.N2 = s->N[1];
+  a.N3 = s->N[2];
+  a.N1p = a.N1 + 1;
+  a.N2p = a.N2 + 1;
+  a.N3p = a.N3 + 1;
+  a.W2 = kd.W[1];
+  a.W3 = kd.W[2];
+  a.lo2 = kd.lo[1];
+  a.lo3 = kd.lo[2];
+  a.d1 = s->dim[0];
+  a.d2 = s->dim[1];
+  a.d3 = s->dim[2];
+  a.pw1 = pencils_per_call(a.d1);
+  a.pw2 = pencils_per_call(a.d2);
+  a.pw3 = pencils_per_call(a.d3);
+  a.tw1 = (const C*)(f64 ? s->d_tw64[0].p : s->d_tw32[0].p);
+  a.tw2 = (const C*)(f64 ? s->d_tw64[1].p : s->d_tw32[1].p);
+  a.tw3 = (const C*)(f64 ? s->d_tw64[2].p : s->d_tw32[2].p);
+  a.zstart = kd.d_zstart.as<int>();
+  a.rowrange = kd.d_rowrange.as<int>();
+  a.tileidx = kd.d_tileidx.as<int>();
+  a.kin = (const T*)(f64 ? kd.d_kin64.p : kd.d_kin32.p);
+  a.Vx = (const T*)(f64 ? s->d_Vx64.p : s->d_Vx32.p);
+  a.psi = (const C*)psi;
+  a.psi_prev = nullptr;
+  a.out = (C*)out;
+  a.ld = ld;
+  a.alpha = (T)1;
+  a.beta = (T)0;
+  a.gamma = (T)0;
+  a.work = (C*)work;
+  const size_t smax = 227 * 1024;
+  RegPlan rp;
+  if (choose_split(a.N1, rp.s1) && choose_split(a.N2, rp.s2) && choose_split(a.N3, rp.s3)) {
+    const int scr_warp = std::max(rp.s1.PP * rp.s1.scr, std::max(rp.s2.PP * rp.s2.scr, rp.s3.PP * rp.s3.scr));
+    const size_t es = sizeof(C);
+    const size_t ra = es * ((size_t)a.N1 + (size_t)a.W2 * a.N1p + (size_t)kWarps * scr_warp);
+    const size_t rb = es * ((size_t)a.N2 + a.N3 + (size_t)a.W3 * a.N2p + (size_t)kWarps * scr_warp) +
+                      sizeof(int) * a.N3;
+    if (ra <= smax && rb <= smax) {
+      KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_a_r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
+      KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_b_r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb));
+      KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_c_r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
+      for (int n0 = 0; n0 < nb; n0 += nc) {
+        const int m = std::min(nc, nb - n0);
+        a.n0 = n0;
+        pass_a_r<T><<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
+        pass_b_r<T><<<dim3(a.N1, m), kThreads, rb, ctx->stream>>>(a, rp, scr_warp);
+        pass_c_r<T><<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
+      }
+      KSS_CHECK_CUDA(cudaGetLastError());
+      return;
+    }
+  }
+  const size_t sa = smem_a(a), sb = smem_b(a);
+  if (sa > smax || sb > smax)
+    fail(KSS_ENOTSUP, "FFT box too large for the shared-memory pencil tiles of this build");
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_a<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
+  for (int n0 = 0; n0 < nb; n0 += nc) {
+    const int m = std::min(nc, nb - n0);
+    a.n0 = n0;
+    pass_a<T><<<dim3(a.W3, m), kThreads, sa, ctx->stream>>>(a);
+    pass_b<T><<<dim3(a.N1, m), kThreads, sb, ctx->stream>>>(a);
+    pass_c<T><<<dim3(a.W3, m), kThreads, sa, ctx->stream>>>(a);
+  }
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
 }  // namespace
+
+size_t local_slab_bytes_per_band(kss_sys s, int ik, kss_precision prec) {
+  return slab_elems(s, ik) * (prec == KSS_PREC_FP64 ? 16 : 8);
+}
+
+void local_apply_ws(kss_sys s, int ik, int nb, const void* psi, void* out, int ld,
+                    kss_precision prec, void* work, int nc) {
+  if (prec == KSS_PREC_FP64)
+    run_local_ws<double>(s, ik, nb, psi, out, ld, work, nc);
+  else
+    run_local_ws<float>(s, ik, nb, psi, out, ld, work, nc);
+}
 
 size_t local_workspace_bytes(kss_sys s, int ik, int nb, kss_precision prec) {
   const size_t es = prec == KSS_PREC_FP64 ? 16 : 8;

@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
             "kss_apply_H": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
             "kss_cheb_step": ([P, c_int, c_int, P, P, P, c_int, c_double, c_double, c_double, c_int], c_int),
             "kss_apply_H_host": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
+            "kss_apply_H_noalloc": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
             "kss_solver_create": ([P, c_int, c_int, POINTER(kss_solve_opts), POINTER(c_void_p)], c_int),
             "kss_solver_destroy": ([P], c_int),
             "kss_solver_step": ([P, POINTER(c_int)], c_int),
@@ -274,6 +275,15 @@ def kss_apply_H(sys: System, ik: int, psi, hpsi, prec: int = KSS_PREC_FP64, nb: 
     if (n2, ld2) != (n, ld):
         raise ValueError("psi and hpsi shapes differ")
     _check(lib().kss_apply_H(sys.h, ik, n if nb is None else nb, _ptr(psi), _ptr(hpsi), ld, prec), sys.ctx)
+
+
+def kss_apply_H_noalloc(sys: System, ik: int, psi, hpsi, prec: int = KSS_PREC_FP64):
+    """kss_apply_H without any device allocation (static scratch, see include/kss.h)."""
+    n, ld = _block_dims(psi, prec)
+    n2, ld2 = _block_dims(hpsi, prec)
+    if (n2, ld2) != (n, ld):
+        raise ValueError("psi and hpsi shapes differ")
+    _check(lib().kss_apply_H_noalloc(sys.h, ik, n, _ptr(psi), _ptr(hpsi), ld, prec), sys.ctx)
 
 
 def kss_cheb_step(sys: System, ik: int, psi, psi_prev, out, alpha, beta, gamma,
