@@ -265,6 +265,68 @@ kss_status kss_chebfi_solve(kss_sys sys, int ik, int nband, const kss_solve_opts
                             kss_solve_stats* stats);
 
 /* ------------------------------------------------------------------------------------------
+ * Batched solves: many systems / k-points in lockstep (§5.1 batch processing)
+ * ------------------------------------------------------------------------------------------ */
+
+/* Solve n independent (system, k-point) units of uneven sizes together: every iteration issues
+ * the FFT passes of all units as single grouped launches and the projector products as grouped
+ * GEMMs, the whole filter (degree m + the H application on the filtered block) being one CUDA
+ * graph captured once and replayed with new coefficients; Rayleigh-Ritz (FP64 eigensolve) runs
+ * per unit with one host synchronisation per iteration.  Units stop when converged.
+ * sys[u] (same context), ik[u], nband[u]; opts is shared (precision, degree, tol, max_iter,
+ * nbuffer; unit u draws its start block with seed opts->seed + u; x0 must be NULL).
+ * evals[u], resid[u]: host arrays of nband[u] (any pointer may be NULL); stats: array of n or
+ * NULL.  Returns KSS_ENOCONV if any unit hit max_iter (results still filled); KSS_ENOTSUP if a
+ * unit's FFT lengths have no two-codelet split (125, 162, 200, 216, 243, 250). */
+kss_status kss_solve_batch(kss_ctx ctx, int n, const kss_sys* sys, const int* ik, const int* nband,
+                           const kss_solve_opts* opts, double* const* evals, double* const* resid,
+                           kss_solve_stats* stats);
+
+/* ------------------------------------------------------------------------------------------
+ * Request server: continuous batching of eigensolves as they arrive
+ * ------------------------------------------------------------------------------------------ */
+
+typedef struct {
+  long long completed, rejected, warm_hits;
+  double p50_ms, p99_ms, mean_ms;  /* latency submit -> done, over completed requests */
+  double solves_per_s;             /* completed requests / (last completion - first submit) */
+  size_t peak_bytes, in_flight_bytes;  /* admission accounting (estimated footprints) */
+} kss_server_stats;
+
+/* Start a server on the context.  Requests are admitted in arrival order while the sum of their
+ * estimated device footprints stays within hbm_budget_bytes and their k-points fit in max_slots
+ * units; each admitted request's system tables and solver blocks stay resident until it
+ * completes.  opts (shared by all requests; x0 must be NULL): precision, degree, tol, max_iter,
+ * nbuffer, seed.  A warm-start cache of up to a tenth of the budget keeps the converged
+ * subspace of finished requests; a later request with identical content starts from it.
+ * While the server runs, the context belongs to it: other calls on the context are not allowed
+ * until kss_server_stop. */
+kss_status kss_server_start(kss_ctx ctx, size_t hbm_budget_bytes, int max_slots,
+                            const kss_solve_opts* opts);
+
+/* Queue a request (cell, atoms, nband: copied).  *ticket identifies it.  KSS_EBUSY if the queue
+ * is full or the request alone exceeds the budget. */
+kss_status kss_server_submit(kss_ctx ctx, const kss_cell* cell, const kss_atoms* atoms, int nband,
+                             uint64_t* ticket);
+
+/* Drive the server from the calling thread for up to max_ms (at least one tick): each tick admits
+ * what fits, runs one lockstep iteration over every unit in flight (new units start in the same
+ * tick) and retires finished requests.  Returns early when idle.  in_flight / queued: requests
+ * on the device / waiting (may be NULL). */
+kss_status kss_server_pump(kss_ctx ctx, double max_ms, int* in_flight, int* queued);
+
+/* *done = 1 when the request finished; then evals / resid (host, nk*nband, k-point-major) and
+ * the latency are filled and the ticket is released.  Returns the request's status once done
+ * (KSS_OK, KSS_ENOCONV, or the setup error). */
+kss_status kss_server_poll(kss_ctx ctx, uint64_t ticket, int* done, double* evals, double* resid,
+                           double* latency_ms);
+
+kss_status kss_server_get_stats(kss_ctx ctx, kss_server_stats* out);
+
+/* Stop the server and free everything it holds (pending and in-flight requests are dropped). */
+kss_status kss_server_stop(kss_ctx ctx);
+
+/* ------------------------------------------------------------------------------------------
  * Launch accounting and per-kernel timing (measurement support; no counterpart in the paper)
  * ------------------------------------------------------------------------------------------ */
 

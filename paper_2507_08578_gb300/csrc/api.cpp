@@ -195,6 +195,10 @@ kss_status kss_create(kss_ctx* out, int device, void* cuda_stream) {
 
 kss_status kss_destroy(kss_ctx ctx) {
   if (!ctx) return KSS_EINVAL;
+  if (ctx->server) {
+    ctx->err = "stop the request server (kss_server_stop) before destroying its context";
+    return KSS_EINVAL;
+  }
   if (ctx->nsys > 0) {
     ctx->err = "destroy every system before its context";
     return KSS_EINVAL;

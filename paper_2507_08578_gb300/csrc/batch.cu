@@ -1,0 +1,498 @@
+// Batched Chebyshev-filtered solves: many (system, k-point) units of uneven sizes advanced in
+// lockstep, the local passes and the projector products of all units issued as single grouped
+// launches, and the whole filter of one iteration (degree m applications plus H on the filtered
+// block) captured once into a CUDA graph and replayed every iteration.  The paper's strategy of
+// "batch processing" many FFTs and products per call (§5.1), extended from bands to independent
+// problems; k-points and systems share nothing (§5.3 notes the trivial parallelism in k).
+//
+// Per iteration and unit the filter reads its coefficients and buffer roles from device tables
+// that the host rewrites before each replay; Rayleigh-Ritz (FP64 eigensolve) is then issued for
+// every unit with a single host synchronisation for the convergence decisions.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "batch.h"
+#include "local_kernels.cuh"
+
+namespace kss {
+
+namespace {
+
+using namespace lk;
+using fftr::Split;
+
+template <typename T>
+struct LocalItem {
+  LocalArgs<T> a;
+  RegPlan rp;
+  int blk_ac;  // first block of this item in the pass A / pass C launches
+  int blk_b;   // first block in the pass B launch
+};
+
+template <typename T>
+__device__ __forceinline__ int find_local(const LocalItem<T>* it, int n, int b, bool pb) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((pb ? it[mid].blk_b : it[mid].blk_ac) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, int PASS>
+__global__ void __launch_bounds__(kThreads) group_pass(const LocalItem<T>* __restrict__ items, int n,
+                                                       int scr_warp) {
+  __shared__ LocalArgs<T> sa;
+  __shared__ RegPlan srp;
+  __shared__ int s_local;
+  if (threadIdx.x == 0) {
+    const int i = find_local(items, n, blockIdx.x, PASS == 1);
+    sa = items[i].a;
+    srp = items[i].rp;
+    s_local = blockIdx.x - (PASS == 1 ? items[i].blk_b : items[i].blk_ac);
+  }
+  __syncthreads();
+  const int local = s_local;
+  if (PASS == 0) pass_a_body<T>(sa, srp, scr_warp, local % sa.W3, local / sa.W3);
+  else if (PASS == 1) pass_b_body<T>(sa, srp, scr_warp, local % sa.N1, local / sa.N1);
+  else pass_c_body<T>(sa, srp, scr_warp, local % sa.W3, local / sa.W3);
+}
+
+template <typename T>
+void fill_args(kss_sys s, int ik, LocalArgs<T>& a) {
+  using C = typename CT<T>::C;
+  const bool f64 = sizeof(T) == 8;
+  KData& kd = s->k[ik];
+  a = LocalArgs<T>{};
+  a.N1 = s->N[0];
+  a.N2 = s->N[1];
+  a.N3 = s->N[2];
+  a.N1p = a.N1 + 1;
+  a.N2p = a.N2 + 1;
+  a.N3p = a.N3 + 1;
+  a.W2 = kd.W[1];
+  a.W3 = kd.W[2];
+  a.lo2 = kd.lo[1];
+  a.lo3 = kd.lo[2];
+  a.d1 = s->dim[0];
+  a.d2 = s->dim[1];
+  a.d3 = s->dim[2];
+  a.tw1 = (const C*)(f64 ? s->d_tw64[0].p : s->d_tw32[0].p);
+  a.tw2 = (const C*)(f64 ? s->d_tw64[1].p : s->d_tw32[1].p);
+  a.tw3 = (const C*)(f64 ? s->d_tw64[2].p : s->d_tw32[2].p);
+  a.zstart = kd.d_zstart.as<int>();
+  a.rowrange = kd.d_rowrange.as<int>();
+  a.tileidx = kd.d_tileidx.as<int>();
+  a.kin = (const T*)(f64 ? kd.d_kin64.p : kd.d_kin32.p);
+  a.Vx = (const T*)(f64 ? s->d_Vx64.p : s->d_Vx32.p);
+  a.ld = kd.npw;
+  a.n0 = 0;
+}
+
+size_t al256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// BatchEngine
+// ---------------------------------------------------------------------------------------------
+
+BatchEngine::~BatchEngine() { drop_graph(); }
+
+void BatchEngine::drop_graph() {
+  if (gexec) cudaGraphExecDestroy((cudaGraphExec_t)gexec);
+  gexec = nullptr;
+}
+
+void BatchEngine::set_units(const std::vector<kss_solver_s*>& us) {
+  bool same = us.size() == units.size();
+  for (size_t i = 0; same && i < us.size(); ++i) same = us[i] == units[i];
+  if (same && prepared) return;
+  units = us;
+  prepared = false;
+  drop_graph();
+}
+
+template <typename T>
+void BatchEngine::prepare_t() {
+  using C = typename CT<T>::C;
+  const size_t es = sizeof(C);
+  const int n = (int)units.size();
+  plans.assign(n, RegPlanHost{});
+  ws_off.assign(n, {0, 0, 0});
+  size_t off = 0;
+  scr_warp = 0;
+  smem_ac = smem_b = 0;
+  blocks_ac = blocks_b = 0;
+  for (int u = 0; u < n; ++u) {
+    kss_solver_s* s = units[u];
+    kss_sys sy = s->sys;
+    const KData& kd = sy->k[s->ik];
+    RegPlan rp;
+    if (!(choose_split(sy->N[0], rp.s1) && choose_split(sy->N[1], rp.s2) && choose_split(sy->N[2], rp.s3)))
+      fail(KSS_ENOTSUP, "batched solves need FFT lengths that split into two codelets (<= 16 each)");
+    static_assert(sizeof(RegPlanHost) == sizeof(RegPlan), "plan layouts differ");
+    std::memcpy(&plans[u], &rp, sizeof(RegPlan));
+    const int sw = std::max(rp.s1.PP * rp.s1.scr, std::max(rp.s2.PP * rp.s2.scr, rp.s3.PP * rp.s3.scr));
+    scr_warp = std::max(scr_warp, sw);
+    const size_t plane = (size_t)sy->N[0] * kd.W[2] * kd.W[1] * es;
+    ws_off[u].cprj = off;
+    off += al256((size_t)std::max(sy->nproj, 1) * s->nb * es);
+    ws_off[u].part = off;
+    off += al256((size_t)16 * std::max(sy->nproj, 1) * s->nb * es);
+    ws_off[u].slab = off;
+    off += al256(plane * s->nb);
+    blocks_ac += kd.W[2] * s->nb;
+    blocks_b += sy->N[0] * s->nb;
+  }
+  for (int u = 0; u < n; ++u) {
+    kss_sys sy = units[u]->sys;
+    const KData& kd = sy->k[units[u]->ik];
+    smem_ac = std::max(smem_ac, es * ((size_t)sy->N[0] + (size_t)kd.W[1] * (sy->N[0] + 1) + (size_t)kWarps * scr_warp));
+    smem_b = std::max(smem_b, es * ((size_t)sy->N[1] + sy->N[2] + (size_t)kd.W[2] * (sy->N[1] + 1) +
+                                    (size_t)kWarps * scr_warp) + sizeof(int) * sy->N[2]);
+  }
+  if (smem_ac > 227 * 1024 || smem_b > 227 * 1024)
+    fail(KSS_ENOTSUP, "a batched unit's FFT tiles do not fit in shared memory");
+  ws.ensure(off);
+  steps = degree + 1;
+  litem_bytes = sizeof(LocalItem<T>);
+  h_local.assign((size_t)steps * n * litem_bytes, 0);
+  h_cn.assign((size_t)steps * n, GemmItem{});
+  h_nn.assign((size_t)steps * n, GemmItem{});
+  d_local.ensure(h_local.size());
+  d_cn.ensure(h_cn.size() * sizeof(GemmItem));
+  d_nn.ensure(h_nn.size() * sizeof(GemmItem));
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(group_pass<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(group_pass<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(group_pass<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
+  prepared = true;
+}
+
+// Buffer roles and coefficients of every unit for the m filter steps and the H-on-Y step.
+template <typename T>
+void BatchEngine::fill_tables_t() {
+  using C = typename CT<T>::C;
+  const bool f64 = sizeof(T) == 8;
+  const int n = (int)units.size();
+  roles.assign(n, Roles{});
+  std::vector<int> cur(n), prev(n);
+  std::vector<double> sigma(n), tau(n), e(n), c(n);
+  for (int u = 0; u < n; ++u) {
+    kss_solver_s* s = units[u];
+    int fr[2], nf = 0;
+    for (int i = 0; i < 4; ++i)
+      if (i != s->ix && i != s->ihx) fr[nf++] = i;
+    cur[u] = s->ix;
+    prev[u] = fr[0];
+    roles[u].free2 = fr[1];
+    const ChebParams cp = cheb_params(s);
+    e[u] = cp.e;
+    c[u] = cp.c;
+    sigma[u] = cp.sigma1;
+    tau[u] = 2.0 / cp.sigma1;
+  }
+  for (int j = 0; j < steps; ++j) {
+    int bac = 0, bb = 0;
+    std::vector<GemmItem> cn(n), nn(n);
+    for (int u = 0; u < n; ++u) {
+      kss_solver_s* s = units[u];
+      kss_sys sy = s->sys;
+      const KData& kd = sy->k[s->ik];
+      double al, be, ga;
+      const void* psi;
+      const void* pp;
+      void* out;
+      if (j == 0) {  // Y_1 = (sigma1/e)(H - c) X
+        al = sigma[u] / e[u];
+        be = -al * c[u];
+        ga = 0;
+        psi = s->blk[cur[u]].p;
+        pp = nullptr;
+        out = s->blk[prev[u]].p;
+        std::swap(cur[u], prev[u]);
+      } else if (j < steps - 1) {  // Y_j from Y_{j-1}, Y_{j-2}, written over Y_{j-2}
+        const double sn = 1.0 / (tau[u] - sigma[u]);
+        al = 2.0 * sn / e[u];
+        be = -al * c[u];
+        ga = -sigma[u] * sn;
+        psi = s->blk[cur[u]].p;
+        pp = s->blk[prev[u]].p;
+        out = s->blk[prev[u]].p;
+        std::swap(cur[u], prev[u]);
+        sigma[u] = sn;
+      } else {  // HY = H Y_m into the Y_{m-1} buffer
+        al = 1.0;
+        be = 0.0;
+        ga = 0.0;
+        psi = s->blk[cur[u]].p;
+        pp = nullptr;
+        out = s->blk[prev[u]].p;
+        roles[u].y = cur[u];
+        roles[u].hy = prev[u];
+      }
+      LocalItem<T> it;
+      fill_args<T>(sy, s->ik, it.a);
+      it.a.psi = (const C*)psi;
+      it.a.psi_prev = (const C*)pp;
+      it.a.out = (C*)out;
+      it.a.alpha = (T)al;
+      it.a.beta = (T)be;
+      it.a.gamma = (T)ga;
+      it.a.work = (C*)((char*)ws.p + ws_off[u].slab);
+      std::memcpy(&it.rp, &plans[u], sizeof(RegPlan));
+      it.blk_ac = bac;
+      it.blk_b = bb;
+      bac += kd.W[2] * s->nb;
+      bb += sy->N[0] * s->nb;
+      std::memcpy(&h_local[((size_t)j * n + u) * litem_bytes], &it, sizeof(it));
+      GemmItem& g = cn[u];
+      g = GemmItem{};
+      GemmItem& h = nn[u];
+      h = GemmItem{};
+      if (sy->nproj) {
+        g.M = sy->nproj;
+        g.N = s->nb;
+        g.K = kd.npw;
+        g.A = f64 ? kd.d_beta64.p : kd.d_beta32.p;
+        g.lda = kd.npw;
+        g.B = psi;
+        g.ldb = kd.npw;
+        g.C = (char*)ws.p + ws_off[u].cprj;
+        g.ldc = sy->nproj;
+        g.P = (char*)ws.p + ws_off[u].part;
+        g.d = f64 ? sy->d_D64.p : sy->d_D32.p;
+        g.s = al;
+        h.M = kd.npw;
+        h.N = s->nb;
+        h.K = sy->nproj;
+        h.A = g.A;
+        h.lda = kd.npw;
+        h.B = g.C;
+        h.ldb = sy->nproj;
+        h.C = out;
+        h.ldc = kd.npw;
+        h.ar = 1.0;
+        h.br = 1.0;
+      }
+    }
+    int b1, r1, b2, r2;
+    group_plan(ctx, cn, true, &b1, &r1);
+    group_plan(ctx, nn, false, &b2, &r2);
+    std::copy(cn.begin(), cn.end(), h_cn.begin() + (size_t)j * n);
+    std::copy(nn.begin(), nn.end(), h_nn.begin() + (size_t)j * n);
+    if (j == 0) {
+      cn_blocks = b1;
+      cn_rblocks = r1;
+      nn_blocks = b2;
+    }
+  }
+  KSS_CHECK_CUDA(cudaMemcpyAsync(d_local.p, h_local.data(), h_local.size(), cudaMemcpyHostToDevice, ctx->stream));
+  KSS_CHECK_CUDA(cudaMemcpyAsync(d_cn.p, h_cn.data(), h_cn.size() * sizeof(GemmItem), cudaMemcpyHostToDevice, ctx->stream));
+  KSS_CHECK_CUDA(cudaMemcpyAsync(d_nn.p, h_nn.data(), h_nn.size() * sizeof(GemmItem), cudaMemcpyHostToDevice, ctx->stream));
+}
+
+template <typename T>
+void BatchEngine::launch_filter_t() {
+  const bool f64 = sizeof(T) == 8;
+  const int n = (int)units.size();
+  const LocalItem<T>* dl = (const LocalItem<T>*)d_local.p;
+  for (int j = 0; j < steps; ++j) {
+    const GemmItem* cn = d_cn.as<GemmItem>() + (size_t)j * n;
+    const GemmItem* nn = d_nn.as<GemmItem>() + (size_t)j * n;
+    if (cn_blocks) group_gemm_cn(ctx, f64, cn, n, cn_blocks, cn_rblocks);
+    group_pass<T, 0><<<blocks_ac, kThreads, smem_ac, ctx->stream>>>(dl + (size_t)j * n, n, scr_warp);
+    group_pass<T, 1><<<blocks_b, kThreads, smem_b, ctx->stream>>>(dl + (size_t)j * n, n, scr_warp);
+    group_pass<T, 2><<<blocks_ac, kThreads, smem_ac, ctx->stream>>>(dl + (size_t)j * n, n, scr_warp);
+    if (nn_blocks) group_gemm_nn(ctx, f64, nn, n, nn_blocks);
+  }
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+void BatchEngine::run_filter() {
+  if (!prepared) {
+    if (f64) prepare_t<double>();
+    else prepare_t<float>();
+  }
+  if (f64) fill_tables_t<double>();
+  else fill_tables_t<float>();
+  const int per_step = 3 + (cn_blocks ? 2 : 0) + (nn_blocks ? 1 : 0);
+  if (use_graph) {
+    if (!gexec) {
+      // Capture the filter launches once for this set of units; later iterations only rewrite
+      // the device tables the kernels read.
+      const bool prof_on = ctx->prof.on;
+      ctx->prof.on = false;  // no event records inside the captured region
+      KSS_CHECK_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      try {
+        if (f64) launch_filter_t<double>();
+        else launch_filter_t<float>();
+      } catch (...) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(ctx->stream, &g);
+        if (g) cudaGraphDestroy(g);
+        ctx->prof.on = prof_on;
+        throw;
+      }
+      cudaGraph_t g = nullptr;
+      KSS_CHECK_CUDA(cudaStreamEndCapture(ctx->stream, &g));
+      cudaGraphExec_t ex = nullptr;
+      const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      ctx->prof.on = prof_on;
+      KSS_CHECK_CUDA(e);
+      gexec = ex;
+      // launches recorded during capture are not executions
+      ctx->prof.launches -= (long long)per_step * steps;
+    }
+    static const int idg = prof_register("batch_filter_graph");
+    {
+      ProfScope ps(ctx, idg);
+      KSS_CHECK_CUDA(cudaGraphLaunch((cudaGraphExec_t)gexec, ctx->stream));
+    }
+    ctx->prof.launches += (long long)per_step * steps - 1;
+  } else {
+    if (f64) launch_filter_t<double>();
+    else launch_filter_t<float>();
+  }
+}
+
+// One lockstep iteration over every unit that is not done.
+void BatchEngine::iterate(std::vector<kss_solver_s*>& all) {
+  // Units that have not started: initial Rayleigh-Ritz on their starting block.
+  std::vector<kss_solver_s*> fresh, active;
+  for (auto* s : all) {
+    if (s->done) continue;
+    (s->started ? active : fresh).push_back(s);
+  }
+  for (auto* s : fresh) {
+    apply_h(s->sys, s->ik, s->nb, s->blk[0].p, nullptr, s->blk[1].p, s->npw, ChebCoef{1, 0, 0},
+            s->f64 ? KSS_PREC_FP64 : KSS_PREC_MIXED);
+    s->napply += s->nb;
+    rr_issue(s, s->f64, s->blk[0].p, s->blk[1].p, s->blk[2].p, s->blk[3].p);
+  }
+  if (!active.empty()) {
+    set_units(active);
+    run_filter();
+    for (size_t u = 0; u < active.size(); ++u) {
+      kss_solver_s* s = active[u];
+      s->napply += (long long)s->nb * steps;
+      rr_issue(s, s->f64, s->blk[roles[u].y].p, s->blk[roles[u].hy].p, s->blk[roles[u].free2].p,
+               s->blk[s->ihx].p);
+    }
+  }
+  KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  KSS_CHECK_CUDA(cudaGetLastError());
+  for (auto* s : fresh) {
+    rr_finish(s);
+    s->ix = 2;
+    s->ihx = 3;
+    s->started = true;
+    decide(s);
+  }
+  for (size_t u = 0; u < active.size(); ++u) {
+    kss_solver_s* s = active[u];
+    rr_finish(s);
+    s->ix = roles[u].free2;
+    s->iter += 1;
+    decide(s);
+  }
+}
+
+void BatchEngine::decide(kss_solver_s* s) {
+  const double r = max_wanted(s);
+  s->hist.push_back(r);
+  if (s->f64) {
+    s->converged = r <= s->tol;
+    s->done = s->converged || s->iter >= s->o.max_iter;
+  } else {
+    bool stalled = false;
+    const size_t h = s->hist.size();
+    if (h >= 4) stalled = s->hist[h - 1] > 0.9 * s->hist[h - 4];
+    if (r <= s->tol || stalled || s->iter >= s->o.max_iter) {
+      refine_fp64(s);
+      s->converged = max_wanted(s) <= s->tol;
+      s->done = true;
+    }
+  }
+}
+
+}  // namespace kss
+
+using namespace kss;
+
+extern "C" kss_status kss_solve_batch(kss_ctx ctx, int n, const kss_sys* sys, const int* ik,
+                                      const int* nband, const kss_solve_opts* opts,
+                                      double* const* evals, double* const* resid,
+                                      kss_solve_stats* stats) {
+  if (!ctx) return KSS_EINVAL;
+  std::vector<kss_solver> made;
+  try {
+    KSS_REQUIRE(n >= 0 && (n == 0 || (sys && ik && nband)), "kss_solve_batch: bad arguments");
+    KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    kss_solve_opts o{};
+    if (opts) o = *opts;
+    KSS_REQUIRE(o.x0 == nullptr, "kss_solve_batch takes no warm start (use the server or solvers)");
+    for (int u = 0; u < n; ++u) {
+      KSS_REQUIRE(sys[u] && sys[u]->ctx == ctx, "every system must belong to this context");
+      kss_solve_opts ou = o;
+      ou.seed = o.seed + (uint64_t)u;
+      kss_solver s = nullptr;
+      const kss_status st = kss_solver_create(sys[u], ik[u], nband[u], &ou, &s);
+      if (st != KSS_OK) fail(st, ctx->err);
+      made.push_back(s);
+    }
+    BatchEngine eng;
+    eng.ctx = ctx;
+    eng.f64 = n ? made[0]->f64 : true;
+    for (auto* s : made)
+      KSS_REQUIRE(s->f64 == eng.f64 && s->o.degree == made[0]->o.degree,
+                  "batched units share precision and filter degree");
+    eng.degree = n ? made[0]->o.degree : 10;
+    std::vector<kss_solver_s*> all(made.begin(), made.end());
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+      bool any = false;
+      for (auto* s : all) any |= !s->done;
+      if (!any) break;
+      eng.iterate(all);
+    }
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    bool allconv = true;
+    for (int u = 0; u < n; ++u) {
+      kss_solver_s* s = made[u];
+      allconv &= s->converged;
+      if (evals && evals[u]) std::memcpy(evals[u], s->evals.data(), s->nband * sizeof(double));
+      if (resid && resid[u]) std::memcpy(resid[u], s->resid.data(), s->nband * sizeof(double));
+      if (stats) {
+        stats[u].iters = s->iter;
+        stats[u].napply = s->napply;
+        stats[u].max_resid = max_wanted(s);
+        stats[u].ms_filter = 0;
+        stats[u].ms_rr = 0;
+        stats[u].ms_total = ms;
+        stats[u].nb = s->nb;
+      }
+    }
+    for (auto s : made) kss_solver_destroy(s);
+    made.clear();
+    if (!allconv) {
+      ctx->err = "at least one unit did not converge within max_iter";
+      return KSS_ENOCONV;
+    }
+    ctx->err.clear();
+    return KSS_OK;
+  } catch (const KssError& e) {
+    for (auto s : made) kss_solver_destroy(s);
+    ctx->err = e.msg;
+    return e.st;
+  } catch (...) {
+    for (auto s : made) kss_solver_destroy(s);
+    ctx->err = "unexpected internal error";
+    return KSS_ECUDA;
+  }
+}

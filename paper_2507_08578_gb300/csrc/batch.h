@@ -1,0 +1,59 @@
+// Batched lockstep engine shared by kss_solve_batch (batch.cu) and the request server (server.cu).
+#pragma once
+
+#include <vector>
+
+#include "fft_reg.cuh"
+#include "kss_internal.h"
+
+namespace kss {
+
+struct RegPlanHost {  // host copy of the per-unit FFT split plan (same layout as the device one)
+  fftr::Split s1, s2, s3;
+};
+struct WsOff {
+  size_t cprj, part, slab;
+};
+struct Roles {
+  int y, hy, free2;  // buffers holding Y, H Y, and the free one that receives the rotated X
+};
+
+class BatchEngine {
+ public:
+  kss_ctx ctx = nullptr;
+  bool f64 = true;
+  int degree = 10;
+  bool use_graph = true;
+
+  ~BatchEngine();
+  // One lockstep iteration over every unit of `all` that is not done (fresh units get their
+  // initial Rayleigh-Ritz; the others one filter + Rayleigh-Ritz); one host synchronisation.
+  void iterate(std::vector<kss_solver_s*>& all);
+
+ private:
+  template <typename T> void prepare_t();
+  template <typename T> void fill_tables_t();
+  template <typename T> void launch_filter_t();
+  void set_units(const std::vector<kss_solver_s*>& us);
+  void run_filter();
+  void decide(kss_solver_s* s);
+  void drop_graph();
+
+  std::vector<kss_solver_s*> units;
+  std::vector<Roles> roles;
+  bool prepared = false;
+  std::vector<RegPlanHost> plans;
+  std::vector<WsOff> ws_off;
+  DevBuf ws, d_local, d_cn, d_nn;
+  std::vector<unsigned char> h_local;
+  std::vector<GemmItem> h_cn, h_nn;
+  size_t litem_bytes = 0;
+  int scr_warp = 0;
+  size_t smem_ac = 0, smem_b = 0;
+  int blocks_ac = 0, blocks_b = 0;
+  int cn_blocks = 0, cn_rblocks = 0, nn_blocks = 0;
+  int steps = 0;
+  void* gexec = nullptr;  // cudaGraphExec_t of the captured filter
+};
+
+}  // namespace kss

@@ -22,16 +22,16 @@ template <> struct CT<double> { using C = double2; };
 template <> struct CT<float> { using C = float2; };
 
 template <typename T>
-__global__ void __launch_bounds__(256) gemm_cn_partial(int M, int N, int K, const typename CT<T>::C* __restrict__ A,
-                                                       long long lda, const typename CT<T>::C* __restrict__ B,
-                                                       long long ldb, typename CT<T>::C* __restrict__ P,
-                                                       int kchunk) {
+__device__ __forceinline__ void cn_partial_body(int M, int N, int K, const typename CT<T>::C* __restrict__ A,
+                                                long long lda, const typename CT<T>::C* __restrict__ B,
+                                                long long ldb, typename CT<T>::C* __restrict__ P,
+                                                int kchunk, int bx, int by, int bz) {
   using C = typename CT<T>::C;
   __shared__ C As[BK][BM];
   __shared__ C Bs[BK][BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
-  const int kbeg = blockIdx.z * kchunk;
+  const int i0 = bx * BM, j0 = by * BN;
+  const int kbeg = bz * kchunk;
   const int kend = min(K, kbeg + kchunk);
   T accr[4][4], acci[4][4];
 #pragma unroll
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256) gemm_cn_partial(int M, int N, int K, cons
     }
     __syncthreads();
   }
-  C* Pz = P + (size_t)blockIdx.z * M * N;
+  C* Pz = P + (size_t)bz * M * N;
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -77,6 +77,14 @@ __global__ void __launch_bounds__(256) gemm_cn_partial(int M, int N, int K, cons
       const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
       if (i < M && j < N) Pz[(size_t)j * M + i] = C{accr[r][c], acci[r][c]};
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_cn_partial(int M, int N, int K, const typename CT<T>::C* __restrict__ A,
+                                                       long long lda, const typename CT<T>::C* __restrict__ B,
+                                                       long long ldb, typename CT<T>::C* __restrict__ P,
+                                                       int kchunk) {
+  cn_partial_body<T>(M, N, K, A, lda, B, ldb, P, kchunk, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <typename T>
@@ -106,15 +114,15 @@ __global__ void gemm_reduce(int M, int N, int nsplit, const typename CT<T>::C* _
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) gemm_nn_kernel(int M, int N, int K, const typename CT<T>::C* __restrict__ A,
-                                                      long long lda, const typename CT<T>::C* __restrict__ B,
-                                                      long long ldb, typename CT<T>::C* __restrict__ Cm,
-                                                      long long ldc, T ar, T ai, T br, T bi) {
+__device__ __forceinline__ void nn_body(int M, int N, int K, const typename CT<T>::C* __restrict__ A,
+                                        long long lda, const typename CT<T>::C* __restrict__ B,
+                                        long long ldb, typename CT<T>::C* __restrict__ Cm,
+                                        long long ldc, T ar, T ai, T br, T bi, int bx, int by) {
   using C = typename CT<T>::C;
   __shared__ C As[BK][BM];
   __shared__ C Bs[BK][BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
+  const int i0 = bx * BM, j0 = by * BN;
   T accr[4][4], acci[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -175,6 +183,70 @@ __global__ void __launch_bounds__(256) gemm_nn_kernel(int M, int N, int K, const
         *dst = out;
       }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_nn_kernel(int M, int N, int K, const typename CT<T>::C* __restrict__ A,
+                                                      long long lda, const typename CT<T>::C* __restrict__ B,
+                                                      long long ldb, typename CT<T>::C* __restrict__ Cm,
+                                                      long long ldc, T ar, T ai, T br, T bi) {
+  nn_body<T>(M, N, K, A, lda, B, ldb, Cm, ldc, ar, ai, br, bi, blockIdx.x, blockIdx.y);
+}
+
+// ---- grouped forms: one launch over many independent products (batched solves) ------------
+__device__ __forceinline__ int find_item(const GemmItem* it, int n, int b, bool reduce) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((reduce ? it[mid].rblk0 : it[mid].blk0) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gg_cn_partial(const GemmItem* __restrict__ items, int n) {
+  using C = typename CT<T>::C;
+  const int i = find_item(items, n, blockIdx.x, false);
+  const GemmItem& g = items[i];
+  const int local = blockIdx.x - g.blk0;
+  const int per = g.tm * g.tn;
+  const int bz = local / per, r = local - bz * per;
+  cn_partial_body<T>(g.M, g.N, g.K, (const C*)g.A, g.lda, (const C*)g.B, g.ldb, (C*)g.P, g.kchunk,
+                     r % g.tm, r / g.tm, bz);
+}
+
+template <typename T>
+__global__ void gg_reduce(const GemmItem* __restrict__ items, int n) {
+  using C = typename CT<T>::C;
+  const int it = find_item(items, n, blockIdx.x, true);
+  const GemmItem& g = items[it];
+  const long long idx = (long long)(blockIdx.x - g.rblk0) * blockDim.x + threadIdx.x;
+  if (idx >= (long long)g.M * g.N) return;
+  const int i = (int)(idx % g.M), j = (int)(idx / g.M);
+  T sr = 0, si = 0;
+  const C* P = (const C*)g.P;
+  for (int z = 0; z < g.splits; ++z) {
+    const C p = P[(size_t)z * g.M * g.N + idx];
+    sr += p.x;
+    si += p.y;
+  }
+  // C = s * D * (sum), the nonlocal scaling alpha * D folded in (D may be null: plain product)
+  const T f = g.d ? (T)(((const T*)g.d)[i] * (T)g.s) : (T)1;
+  C out;
+  out.x = f * sr;
+  out.y = f * si;
+  ((C*)g.C)[(size_t)j * g.ldc + i] = out;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gg_nn(const GemmItem* __restrict__ items, int n) {
+  using C = typename CT<T>::C;
+  const int i = find_item(items, n, blockIdx.x, false);
+  const GemmItem& g = items[i];
+  const int local = blockIdx.x - g.blk0;
+  nn_body<T>(g.M, g.N, g.K, (const C*)g.A, g.lda, (const C*)g.B, g.ldb, (C*)g.C, g.ldc, (T)g.ar,
+             (T)0, (T)g.br, (T)0, local % g.tm, local / g.tm);
 }
 
 template <typename T>
@@ -315,6 +387,55 @@ void gemm_nn_noprof(bool fp64, int M, int N, int K, const void* A, int lda, cons
   else
     gemm_nn_kernel<float><<<dim3(tm, tn), 256, 0, st>>>(M, N, K, (const float2*)A, lda, (const float2*)B,
                                                         ldb, (float2*)C, ldc, 1.f, 0.f, 1.f, 0.f);
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+// Fill the launch bookkeeping of grouped items (tiles, splits, block offsets) and return the
+// block counts of the partial/product and reduce launches.
+void group_plan(kss_ctx ctx, std::vector<GemmItem>& items, bool cn, int* blocks, int* rblocks) {
+  int b = 0, rb = 0;
+  for (auto& g : items) {
+    g.tm = (g.M + BM - 1) / BM;
+    g.tn = (g.N + BN - 1) / BN;
+    g.blk0 = b;
+    g.rblk0 = rb;
+    if (cn) {
+      g.splits = std::max(1, std::min(16, (g.K + 2047) / 2048));
+      g.kchunk = ((g.K + g.splits - 1) / g.splits + BK - 1) / BK * BK;
+      g.splits = (g.K + g.kchunk - 1) / g.kchunk;
+      b += g.tm * g.tn * g.splits;
+      rb += (int)(((long long)g.M * g.N + 255) / 256);
+    } else {
+      g.splits = 1;
+      b += g.tm * g.tn;
+    }
+  }
+  *blocks = b;
+  *rblocks = rb;
+}
+
+void group_gemm_cn(kss_ctx ctx, bool fp64, const GemmItem* d_items, int n, int blocks, int rblocks) {
+  if (!n || !blocks) return;
+  static const int idp = prof_register("group_gemm_cn_partial"), idr = prof_register("group_gemm_reduce");
+  {
+    ProfScope ps(ctx, idp);
+    if (fp64) gg_cn_partial<double><<<blocks, 256, 0, ctx->stream>>>(d_items, n);
+    else gg_cn_partial<float><<<blocks, 256, 0, ctx->stream>>>(d_items, n);
+  }
+  {
+    ProfScope ps(ctx, idr);
+    if (fp64) gg_reduce<double><<<rblocks, 256, 0, ctx->stream>>>(d_items, n);
+    else gg_reduce<float><<<rblocks, 256, 0, ctx->stream>>>(d_items, n);
+  }
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+void group_gemm_nn(kss_ctx ctx, bool fp64, const GemmItem* d_items, int n, int blocks) {
+  if (!n || !blocks) return;
+  static const int id = prof_register("group_gemm_nn");
+  ProfScope ps(ctx, id);
+  if (fp64) gg_nn<double><<<blocks, 256, 0, ctx->stream>>>(d_items, n);
+  else gg_nn<float><<<blocks, 256, 0, ctx->stream>>>(d_items, n);
   KSS_CHECK_CUDA(cudaGetLastError());
 }
 

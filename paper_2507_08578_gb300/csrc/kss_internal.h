@@ -108,6 +108,7 @@ struct kss_ctx_s {
   kss::DevBuf tc_err;               // device failure flag of the tensor-core kernels
   kss::Prof prof;
   int nsm = 0;
+  void* server = nullptr;          // request server (server.cu), NULL when not running
 };
 
 struct kss_sys_s {
@@ -129,6 +130,29 @@ struct kss_sys_s {
   std::vector<kss::KData> k;
   int nsolvers = 0;
 };
+
+struct kss_solver_s {
+  kss_sys sys = nullptr;
+  int ik = 0, nband = 0, nb = 0, npw = 0;
+  kss_solve_opts o{};
+  bool f64 = true;
+  double tol = 1e-8;
+  kss::DevBuf blk[4];
+  int ix = 0, ihx = 1;
+  kss::DevBuf S, Hs, W, work, info, resid_d;
+  kss::DevBuf S32, Hs32, Q32;
+  kss::DevBuf r64[4];  // FP64 refinement blocks (mixed precision)
+  int lwork = 0;
+  std::vector<double> evals, resid;
+  int iter = 0;
+  bool started = false, done = false, converged = false;
+  long long napply = 0;
+  double ms_filter = 0, ms_rr = 0, ms_total = 0;
+  std::vector<double> hist;  // max wanted residual per iteration
+  double* hpin = nullptr;    // pinned host: evals[nb], resid[nb], info (as double) for async RR
+  ~kss_solver_s();
+};
+
 
 namespace kss {
 
@@ -183,6 +207,26 @@ void gemm_cn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda
 void gemm_nn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda, const void* B,
              int ldb, void* C, int ldc, double alpha_re, double alpha_im, double beta_re,
              double beta_im, const char* tag);
+// Grouped products for batched solves: one launch over many independent (M, N, K) items.
+// Device-resident item table; group_plan fills tm/tn/splits/kchunk/blk0/rblk0.
+struct GemmItem {
+  int M, N, K;
+  const void* A;
+  long long lda;
+  const void* B;
+  long long ldb;
+  void* C;
+  long long ldc;
+  void* P;          // split-K partial sums (cn form)
+  const void* d;    // optional row scale d[i] (real, precision type), applied as s * d[i] (cn form)
+  double s;
+  double ar, br;    // nn form: C = ar * A B + br * C (real coefficients)
+  int tm, tn, splits, kchunk, blk0, rblk0;
+};
+void group_plan(kss_ctx ctx, std::vector<GemmItem>& items, bool cn, int* blocks, int* rblocks);
+void group_gemm_cn(kss_ctx ctx, bool fp64, const GemmItem* d_items, int n, int blocks, int rblocks);
+void group_gemm_nn(kss_ctx ctx, bool fp64, const GemmItem* d_items, int n, int blocks);
+
 // Complex64 GEMMs on the tensor cores (BF16 hi/lo split, FP32 accumulation in TMEM).
 void tc_gemm_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                 void* C, int ldc, double ar, double ai, double br, double bi, const char* tag);
@@ -197,5 +241,16 @@ void random_block(kss_ctx ctx, bool fp64, void* X, int npw, int nb, int ld, uint
                   int band0);
 void residual_norms(kss_ctx ctx, bool fp64, const void* X, const void* HX, int npw, int nb, int ld,
                     const double* w, double* r);
+// Solver internals shared with the batched / served engine (batch.cu).
+struct ChebParams {
+  double e, c, sigma1;
+};
+ChebParams cheb_params(const kss_solver_s* s);
+// Rayleigh-Ritz in two halves: issue (GEMMs, FP64 eigensolve, rotations, residuals, async copy of
+// eigenvalues/residuals/info to pinned host memory) and finish (after the stream is synchronised).
+void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo, void* HXo);
+void rr_finish(kss_solver_s* s);
+void refine_fp64(kss_solver_s* s);
+double max_wanted(const kss_solver_s* s);
 
 }  // namespace kss

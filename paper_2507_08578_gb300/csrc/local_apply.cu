@@ -18,20 +18,15 @@
 // The slab lives in a workspace of nc bands (chunked so that it stays L2-resident).
 #include <algorithm>
 
-#include "fft_reg.cuh"
-#include "kss_internal.h"
+#include "local_kernels.cuh"
 
 namespace kss {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+using namespace lk;
+using fftr::Split;
 constexpr int kMaxB = 4;  // butterflies per lane held in registers by one Stockham stage
-
-template <typename T> struct CT;
-template <> struct CT<double> { using C = double2; };
-template <> struct CT<float> { using C = float2; };
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
@@ -156,34 +151,6 @@ __device__ __noinline__ void warp_fft(C* x, int np, int ps, const FftDim& d, con
   }
 }
 
-template <typename T>
-struct LocalArgs {
-  using C = typename CT<T>::C;
-  int N1, N2, N3, N1p, N2p, N3p;
-  int W2, W3, lo2, lo3;
-  FftDim d1, d2, d3;
-  int pw1, pw2, pw3;  // pencils per warp call along x, y, z
-  const C* tw1;
-  const C* tw2;
-  const C* tw3;
-  const int* zstart;
-  const int* rowrange;
-  const int* tileidx;
-  const T* kin;
-  const T* Vx;
-  const C* psi;
-  const C* psi_prev;
-  C* out;
-  long long ld;
-  C* work;  // [nc][N1][W3][W2]
-  int n0;
-  T alpha, beta, gamma;
-};
-
-template <typename C>
-__device__ __forceinline__ void copy_table(C* dst, const C* src, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
-}
 
 // Pass A: scatter a z-slice of the sphere, inverse FFT along x, store slab rows.
 template <typename T>
@@ -326,303 +293,19 @@ __global__ void __launch_bounds__(kThreads) pass_c(LocalArgs<T> a) {
   }
 }
 
-// ---------------------------------------------------------------------------------------------
-// Register-codelet form of the three passes (two-level pencil FFTs, see fft_reg.cuh).
-// ---------------------------------------------------------------------------------------------
-using fftr::Split;
-using fftr::kMaxR;
-
-struct RegPlan {
-  Split s1, s2, s3;  // x, y, z
-};
-
-// Transform np (<= sp.PP) pencils with one warp.  in(p, e) returns element e of pencil p, out(p,
-// e, v) receives output element e.  s = +1 inverse, -1 forward.  scr: sp.PP * sp.scr elements.
-template <typename C, typename T, class In, class Out>
-__device__ __forceinline__ void pencil_fft(const Split& sp, int np, const C* tw, T s, C* scr,
-                                           int lane, In in, Out out) {
-  const int p = lane / sp.L, r = lane - p * sp.L;
-  const bool act = p < np;
-  C* sc = scr + p * sp.scr;
-  C v[kMaxR];
-  if (act && r < sp.B) {
-#pragma unroll
-    for (int i = 0; i < kMaxR; ++i)
-      if (i < sp.A) v[i] = in(p, r + sp.B * i);
-    fftr::rdft_rt(sp.A, v, s);
-#pragma unroll
-    for (int k = 1; k < kMaxR; ++k)
-      if (k < sp.A) {
-        C w = tw[r * k];
-        w.y = -s * w.y;
-        v[k] = fftr::mul(v[k], w);
-      }
-#pragma unroll
-    for (int k = 0; k < kMaxR; ++k)
-      if (k < sp.A) sc[k * (sp.B + 1) + r] = v[k];
-  }
-  __syncwarp();
-  if (act && r < sp.A) {
-#pragma unroll
-    for (int j = 0; j < kMaxR; ++j)
-      if (j < sp.B) v[j] = sc[r * (sp.B + 1) + j];
-    fftr::rdft_rt(sp.B, v, s);
-#pragma unroll
-    for (int k = 0; k < kMaxR; ++k)
-      if (k < sp.B) out(p, r + sp.A * k, v[k]);
-  }
-  __syncwarp();
-}
-
-// z-column: inverse FFT, x V(z), forward FFT, with the data kept in registers between the two
-// transforms.  in(p, z) / out(p, z, v) address the sphere-range part of the column; vz(p, z) is
-// the (scaled) potential.
-template <typename C, typename T, class In, class Out, class Vf>
-__device__ __forceinline__ void zcolumn(const Split& sp, int np, const C* tw, C* scr, int lane,
-                                        In in, Out out, Vf vz) {
-  const int p = lane / sp.L, r = lane - p * sp.L;
-  const bool act = p < np;
-  C* sc = scr + p * sp.scr;
-  C v[kMaxR];
-  // inverse, stage 1
-  if (act && r < sp.B) {
-#pragma unroll
-    for (int i = 0; i < kMaxR; ++i)
-      if (i < sp.A) v[i] = in(p, r + sp.B * i);
-    fftr::rdft_rt(sp.A, v, (T)1);
-#pragma unroll
-    for (int k = 1; k < kMaxR; ++k)
-      if (k < sp.A) {
-        C w = tw[r * k];
-        w.y = -w.y;
-        v[k] = fftr::mul(v[k], w);
-      }
-#pragma unroll
-    for (int k = 0; k < kMaxR; ++k)
-      if (k < sp.A) sc[k * (sp.B + 1) + r] = v[k];
-  }
-  __syncwarp();
-  if (act && r < sp.A) {
-#pragma unroll
-    for (int j = 0; j < kMaxR; ++j)
-      if (j < sp.B) v[j] = sc[r * (sp.B + 1) + j];
-  }
-  __syncwarp();
-  if (act && r < sp.A) {
-    // inverse, stage 2: v[k2] = psi(z = r + A k2); multiply by V; forward stage 1 (DFT-B)
-    fftr::rdft_rt(sp.B, v, (T)1);
-#pragma unroll
-    for (int k = 0; k < kMaxR; ++k)
-      if (k < sp.B) {
-        const T vv = vz(p, r + sp.A * k);
-        v[k].x *= vv;
-        v[k].y *= vv;
-      }
-    fftr::rdft_rt(sp.B, v, (T)-1);
-#pragma unroll
-    for (int q = 1; q < kMaxR; ++q)
-      if (q < sp.B) v[q] = fftr::mul(v[q], tw[r * q]);
-#pragma unroll
-    for (int q = 0; q < kMaxR; ++q)
-      if (q < sp.B) sc[q * (sp.A + 1) + r] = v[q];
-  }
-  __syncwarp();
-  if (act && r < sp.B) {
-#pragma unroll
-    for (int k = 0; k < kMaxR; ++k)
-      if (k < sp.A) v[k] = sc[r * (sp.A + 1) + k];
-    fftr::rdft_rt(sp.A, v, (T)-1);
-#pragma unroll
-    for (int k = 0; k < kMaxR; ++k)
-      if (k < sp.A) out(p, r + sp.B * k, v[k]);
-  }
-  __syncwarp();
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kThreads) pass_a_r(LocalArgs<T> a, RegPlan rp, int scr_warp) {
-  using C = typename CT<T>::C;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C* tw = reinterpret_cast<C*>(smraw);
-  C* tile = tw + a.N1;
-  C* scr = tile + a.W2 * a.N1p + (threadIdx.x >> 5) * scr_warp;
-  const int u3 = blockIdx.x, nl = blockIdx.y, n = a.n0 + nl;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  copy_table(tw, a.tw1, a.N1);
-  const int tsz = a.W2 * a.N1p;
-  for (int i = threadIdx.x; i < tsz; i += kThreads) tile[i] = C{0, 0};
-  __syncthreads();
-  const int g0 = a.zstart[u3], g1 = a.zstart[u3 + 1];
-  const C* ps = a.psi + n * a.ld;
-  for (int g = g0 + threadIdx.x; g < g1; g += kThreads) tile[a.tileidx[g]] = ps[g];
-  __syncthreads();
-  const int r0 = a.rowrange[2 * u3], r1 = a.rowrange[2 * u3 + 1];
-  const int nrows = r1 - r0 + 1;
-  const Split sp = rp.s1;
-  for (int r = warp * sp.PP; r < nrows; r += kWarps * sp.PP) {
-    C* rows = tile + (r0 + r) * a.N1p;
-    const int ld = a.N1p;
-    pencil_fft<C, T>(sp, min(sp.PP, nrows - r), tw, (T)1, scr, lane,
-                     [&](int p, int e) { return rows[p * ld + e]; },
-                     [&](int p, int e, C v) { rows[p * ld + e] = v; });
-  }
-  __syncthreads();
-  C* dst = a.work + ((size_t)nl * a.N1 * a.W3 + u3) * a.W2;
-  const size_t xs = (size_t)a.W3 * a.W2;
-  for (int i = threadIdx.x; i < a.N1 * a.W2; i += kThreads) {
-    const int x = i / a.W2, u2 = i - x * a.W2;
-    dst[x * xs + u2] = tile[u2 * a.N1p + x];
-  }
+  pass_a_body<T>(a, rp, scr_warp, blockIdx.x, blockIdx.y);
 }
-
 template <typename T>
 __global__ void __launch_bounds__(kThreads) pass_b_r(LocalArgs<T> a, RegPlan rp, int scr_warp) {
-  using C = typename CT<T>::C;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C* tw2 = reinterpret_cast<C*>(smraw);
-  C* tw3 = tw2 + a.N2;
-  C* Q = tw3 + a.N3;                           // W3 x N2p
-  C* scr = Q + a.W3 * a.N2p + (threadIdx.x >> 5) * scr_warp;
-  int* zmap = reinterpret_cast<int*>(Q + a.W3 * a.N2p + kWarps * scr_warp);  // N3
-  const int x = blockIdx.x, nl = blockIdx.y;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  copy_table(tw2, a.tw2, a.N2);
-  copy_table(tw3, a.tw3, a.N3);
-  for (int z = threadIdx.x; z < a.N3; z += kThreads) {
-    int u = (z - a.lo3) % a.N3;
-    if (u < 0) u += a.N3;
-    zmap[z] = u < a.W3 ? u : -1;
-  }
-  for (int i = threadIdx.x; i < a.W3 * a.N2p; i += kThreads) Q[i] = C{0, 0};
-  __syncthreads();
-  C* slab = a.work + ((size_t)nl * a.N1 + x) * a.W3 * a.W2;
-  for (int i = threadIdx.x; i < a.W3 * a.W2; i += kThreads) {
-    const int u3 = i / a.W2, u2 = i - u3 * a.W2;
-    int y = (a.lo2 + u2) % a.N2;
-    if (y < 0) y += a.N2;
-    Q[u3 * a.N2p + y] = slab[i];
-  }
-  __syncthreads();
-  const int N2p = a.N2p;
-  {
-    const Split sp = rp.s2;
-    for (int r = warp * sp.PP; r < a.W3; r += kWarps * sp.PP) {
-      C* rows = Q + r * N2p;
-      pencil_fft<C, T>(sp, min(sp.PP, a.W3 - r), tw2, (T)1, scr, lane,
-                       [&](int p, int e) { return rows[p * N2p + e]; },
-                       [&](int p, int e, C v) { rows[p * N2p + e] = v; });
-    }
-  }
-  __syncthreads();
-  {
-    const Split sp = rp.s3;
-    const T* vx = a.Vx + (size_t)x * a.N2 * a.N3;
-    const int N3 = a.N3;
-    for (int y0 = warp * sp.PP; y0 < a.N2; y0 += kWarps * sp.PP) {
-      zcolumn<C, T>(sp, min(sp.PP, a.N2 - y0), tw3, scr, lane,
-                    [&](int p, int z) {
-                      const int u = zmap[z];
-                      return u >= 0 ? Q[u * N2p + y0 + p] : C{0, 0};
-                    },
-                    [&](int p, int z, C v) {
-                      const int u = zmap[z];
-                      if (u >= 0) Q[u * N2p + y0 + p] = v;
-                    },
-                    [&](int p, int z) { return vx[(size_t)(y0 + p) * N3 + z]; });
-    }
-  }
-  __syncthreads();
-  {
-    const Split sp = rp.s2;
-    for (int r = warp * sp.PP; r < a.W3; r += kWarps * sp.PP) {
-      C* rows = Q + r * N2p;
-      pencil_fft<C, T>(sp, min(sp.PP, a.W3 - r), tw2, (T)-1, scr, lane,
-                       [&](int p, int e) { return rows[p * N2p + e]; },
-                       [&](int p, int e, C v) { rows[p * N2p + e] = v; });
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < a.W3 * a.W2; i += kThreads) {
-    const int u3 = i / a.W2, u2 = i - u3 * a.W2;
-    int y = (a.lo2 + u2) % a.N2;
-    if (y < 0) y += a.N2;
-    slab[i] = Q[u3 * a.N2p + y];
-  }
+  pass_b_body<T>(a, rp, scr_warp, blockIdx.x, blockIdx.y);
 }
-
 template <typename T>
 __global__ void __launch_bounds__(kThreads) pass_c_r(LocalArgs<T> a, RegPlan rp, int scr_warp) {
-  using C = typename CT<T>::C;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C* tw = reinterpret_cast<C*>(smraw);
-  C* tile = tw + a.N1;
-  C* scr = tile + a.W2 * a.N1p + (threadIdx.x >> 5) * scr_warp;
-  const int u3 = blockIdx.x, nl = blockIdx.y, n = a.n0 + nl;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  copy_table(tw, a.tw1, a.N1);
-  const int r0 = a.rowrange[2 * u3], r1 = a.rowrange[2 * u3 + 1];
-  const int nrows = r1 - r0 + 1;
-  const C* src = a.work + ((size_t)nl * a.N1 * a.W3 + u3) * a.W2;
-  const size_t xs = (size_t)a.W3 * a.W2;
-  for (int i = threadIdx.x; i < a.N1 * nrows; i += kThreads) {
-    const int x = i / nrows, u2 = r0 + (i - x * nrows);
-    tile[u2 * a.N1p + x] = src[x * xs + u2];
-  }
-  __syncthreads();
-  const Split sp = rp.s1;
-  for (int r = warp * sp.PP; r < nrows; r += kWarps * sp.PP) {
-    C* rows = tile + (r0 + r) * a.N1p;
-    const int ld = a.N1p;
-    pencil_fft<C, T>(sp, min(sp.PP, nrows - r), tw, (T)-1, scr, lane,
-                     [&](int p, int e) { return rows[p * ld + e]; },
-                     [&](int p, int e, C v) { rows[p * ld + e] = v; });
-  }
-  __syncthreads();
-  const int g0 = a.zstart[u3], g1 = a.zstart[u3 + 1];
-  const C* ps = a.psi + n * a.ld;
-  const C* pp = a.psi_prev ? a.psi_prev + n * a.ld : nullptr;
-  C* po = a.out + n * a.ld;
-  for (int g = g0 + threadIdx.x; g < g1; g += kThreads) {
-    const C v = tile[a.tileidx[g]];
-    const C p = ps[g];
-    const T t = a.kin[g];
-    C o;
-    o.x = a.alpha * (t * p.x + v.x) + a.beta * p.x;
-    o.y = a.alpha * (t * p.y + v.y) + a.beta * p.y;
-    if (pp) {
-      const C q = pp[g];
-      o.x += a.gamma * q.x;
-      o.y += a.gamma * q.y;
-    }
-    po[g] = o;
-  }
+  pass_c_body<T>(a, rp, scr_warp, blockIdx.x, blockIdx.y);
 }
 
-// Best two-factor split N = A*B over the codelet sizes (fewest warp instructions per pencil).
-bool choose_split(int N, Split& out) {
-  static const int S[] = {1, 2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16};
-  double best = 1e30;
-  bool ok = false;
-  for (int A : S)
-    for (int B : S) {
-      if (A * B != N) continue;
-      const int L = std::max(A, B);
-      const int PP = 32 / L;
-      auto cost = [](int n) { double c = 2.0; for (int m = n; m > 1; m >>= 1) c += n; return c; };
-      const double sc = (cost(A) + cost(B)) / PP;
-      if (sc < best) {
-        best = sc;
-        out.N = N;
-        out.A = A;
-        out.B = B;
-        out.L = L;
-        out.PP = PP;
-        out.scr = std::max(A * (B + 1), B * (A + 1));
-        ok = true;
-      }
-    }
-  return ok;
-}
 
 int pencils_per_call(const FftDim& d) {
   int rmin = 5;

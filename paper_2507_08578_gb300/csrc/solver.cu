@@ -153,35 +153,21 @@ void residual_norms(kss_ctx ctx, bool fp64, const void* X, const void* HX, int n
 
 using namespace kss;
 
-struct kss_solver_s {
-  kss_sys sys = nullptr;
-  int ik = 0, nband = 0, nb = 0, npw = 0;
-  kss_solve_opts o{};
-  bool f64 = true;
-  double tol = 1e-8;
-  DevBuf blk[4];
-  int ix = 0, ihx = 1;
-  DevBuf S, Hs, W, work, info, resid_d;
-  DevBuf S32, Hs32, Q32;
-  DevBuf r64[4];  // FP64 refinement blocks (mixed precision)
-  int lwork = 0;
-  std::vector<double> evals, resid;
-  int iter = 0;
-  bool started = false, done = false, converged = false;
-  long long napply = 0;
-  double ms_filter = 0, ms_rr = 0, ms_total = 0;
-  std::vector<double> hist;  // max wanted residual per iteration
-};
+kss_solver_s::~kss_solver_s() {
+  if (hpin) cudaFreeHost(hpin);
+}
 
-namespace {
-
-size_t esize(bool f64) { return f64 ? 16 : 8; }
-
+namespace kss {
 double max_wanted(const kss_solver_s* s) {
   double m = 0;
   for (int n = 0; n < s->nband; ++n) m = std::max(m, s->resid[n]);
   return m;
 }
+}  // namespace kss
+
+namespace {
+
+size_t esize(bool f64) { return f64 ? 16 : 8; }
 
 // FP64 generalised eigensolve of (Hs, S) in place: Hs <- Q with Q^H S Q = I, W <- eigenvalues.
 void subspace_eig(kss_solver_s* s) {
@@ -202,8 +188,13 @@ void subspace_eig(kss_solver_s* s) {
     fail(KSS_ECUDA, "cusolverDnZhegvd failed");
 }
 
-// Rayleigh-Ritz on (Y, HY) -> (Xo, HXo), eigenvalues and residuals to the host.
-void rayleigh_ritz(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo, void* HXo) {
+}  // namespace
+
+namespace kss {
+
+// Rayleigh-Ritz on (Y, HY) -> (Xo, HXo): everything is queued on the stream; eigenvalues,
+// residuals and the eigensolver status land in pinned host memory (read by rr_finish).
+void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo, void* HXo) {
   kss_ctx ctx = s->sys->ctx;
   const int nb = s->nb, npw = s->npw;
   const long long nn = (long long)nb * nb;
@@ -224,8 +215,6 @@ void rayleigh_ritz(kss_solver_s* s, bool f64, const void* Y, const void* HY, voi
     }
   }
   subspace_eig(s);
-  int info = 0;
-  KSS_CHECK_CUDA(cudaMemcpyAsync(&info, s->info.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   if (f64) {
     gemm_nn(ctx, true, npw, nb, nb, Y, npw, s->Hs.p, nb, Xo, npw, 1, 0, 0, 0, "rotate");
     gemm_nn(ctx, true, npw, nb, nb, HY, npw, s->Hs.p, nb, HXo, npw, 1, 0, 0, 0, "rotate");
@@ -239,12 +228,21 @@ void rayleigh_ritz(kss_solver_s* s, bool f64, const void* Y, const void* HY, voi
     gemm_nn(ctx, false, npw, nb, nb, HY, npw, s->Q32.p, nb, HXo, npw, 1, 0, 0, 0, "rotate");
   }
   residual_norms(ctx, f64, Xo, HXo, npw, nb, npw, s->W.as<double>(), s->resid_d.as<double>());
-  s->evals.resize(nb);
-  s->resid.resize(nb);
-  KSS_CHECK_CUDA(cudaMemcpyAsync(s->evals.data(), s->W.p, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  KSS_CHECK_CUDA(cudaMemcpyAsync(s->resid.data(), s->resid_d.p, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (!s->hpin) {
+    KSS_CHECK_CUDA(cudaMallocHost((void**)&s->hpin, (2 * (size_t)nb + 1) * sizeof(double)));
+  }
+  KSS_CHECK_CUDA(cudaMemcpyAsync(s->hpin, s->W.p, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  KSS_CHECK_CUDA(cudaMemcpyAsync(s->hpin + nb, s->resid_d.p, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  KSS_CHECK_CUDA(cudaMemcpyAsync(s->hpin + 2 * nb, s->info.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+void rr_finish(kss_solver_s* s) {
+  const int nb = s->nb;
+  int info = 0;
+  std::memcpy(&info, s->hpin + 2 * nb, sizeof(int));
+  s->evals.assign(s->hpin, s->hpin + nb);
+  s->resid.assign(s->hpin + nb, s->hpin + 2 * nb);
   if (info != 0)
     fail(KSS_ENUMERIC, "subspace eigensolve failed (info = " + std::to_string(info) +
                            "): the Gram matrix is not numerically positive definite");
@@ -253,22 +251,49 @@ void rayleigh_ritz(kss_solver_s* s, bool f64, const void* Y, const void* HY, voi
       fail(KSS_ENUMERIC, "non-finite Ritz value or residual");
 }
 
+}  // namespace kss
+
+namespace {
+
+void rayleigh_ritz(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo, void* HXo) {
+  rr_issue(s, f64, Y, HY, Xo, HXo);
+  KSS_CHECK_CUDA(cudaStreamSynchronize(s->sys->ctx->stream));
+  KSS_CHECK_CUDA(cudaGetLastError());
+  rr_finish(s);
+}
+
 void apply_block(kss_solver_s* s, bool f64, const void* psi, void* out) {
   apply_h(s->sys, s->ik, s->nb, psi, nullptr, out, s->npw, ChebCoef{1, 0, 0},
           f64 ? KSS_PREC_FP64 : KSS_PREC_MIXED);
   s->napply += s->nb;
 }
 
-// Scaled Chebyshev filter of degree m on X (in blk[ix]); returns the buffer holding Y_m and, in
-// *prev_out, the buffer holding Y_{m-1} (free for reuse).
-int chebyshev_filter(kss_solver_s* s, int f1, int* prev_out) {
+}  // namespace
+
+namespace kss {
+ChebParams cheb_params(const kss_solver_s* s) {
   const int nb = s->nb;
   const double lam_lo = s->evals[0];
   double a = s->evals[nb - 1];
   const double b = s->sys->k[s->ik].bound;
   if (!(b - a > 1e-3 * (b - lam_lo))) a = lam_lo + 0.5 * (b - lam_lo);
-  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
-  const double sigma1 = e / (lam_lo - c);
+  ChebParams p;
+  p.e = 0.5 * (b - a);
+  p.c = 0.5 * (b + a);
+  p.sigma1 = p.e / (lam_lo - p.c);
+  return p;
+}
+}  // namespace kss
+
+namespace {
+
+// Scaled Chebyshev filter of degree m on X (in blk[ix]); returns the buffer holding Y_m and, in
+// *prev_out, the buffer holding Y_{m-1} (free for reuse).
+int chebyshev_filter(kss_solver_s* s, int f1, int* prev_out) {
+  const int nb = s->nb;
+  const ChebParams cp = cheb_params(s);
+  const double e = cp.e, c = cp.c;
+  const double sigma1 = cp.sigma1;
   const double tau = 2.0 / sigma1;
   const kss_precision p = s->f64 ? KSS_PREC_FP64 : KSS_PREC_MIXED;
   int cur = s->ix, prev = f1;
@@ -296,6 +321,9 @@ int chebyshev_filter(kss_solver_s* s, int f1, int* prev_out) {
   return cur;
 }
 
+}  // namespace
+
+namespace kss {
 void refine_fp64(kss_solver_s* s) {
   kss_ctx ctx = s->sys->ctx;
   const size_t bytes = (size_t)s->npw * s->nb * 16;
@@ -318,6 +346,9 @@ void refine_fp64(kss_solver_s* s) {
   }
   KSS_CHECK_CUDA(cudaGetLastError());
 }
+}  // namespace kss
+
+namespace {
 
 void solver_step(kss_solver_s* s) {
   kss_ctx ctx = s->sys->ctx;

@@ -54,6 +54,12 @@ class kss_solve_opts(ctypes.Structure):
                 ("x0_ld", c_int)]
 
 
+class kss_server_stats(ctypes.Structure):
+    _fields_ = [("completed", c_longlong), ("rejected", c_longlong), ("warm_hits", c_longlong),
+                ("p50_ms", c_double), ("p99_ms", c_double), ("mean_ms", c_double),
+                ("solves_per_s", c_double), ("peak_bytes", c_size_t), ("in_flight_bytes", c_size_t)]
+
+
 class kss_solve_stats(ctypes.Structure):
     _fields_ = [("iters", c_int), ("napply", c_longlong), ("max_resid", c_double),
                 ("ms_filter", c_double), ("ms_rr", c_double), ("ms_total", c_double),
@@ -96,6 +102,13 @@ def lib() -> ctypes.CDLL:
                                   POINTER(kss_solve_stats)], c_int),
             "kss_gemm": ([P, c_int, c_int, c_int, c_int, P, c_int, P, c_int, P, c_int, c_double,
                           c_double, c_double, c_double, c_int], c_int),
+            "kss_solve_batch": ([P, c_int, P, P, P, POINTER(kss_solve_opts), P, P, P], c_int),
+            "kss_server_start": ([P, c_size_t, c_int, POINTER(kss_solve_opts)], c_int),
+            "kss_server_submit": ([P, POINTER(kss_cell), POINTER(kss_atoms), c_int, POINTER(c_uint64)], c_int),
+            "kss_server_pump": ([P, c_double, POINTER(c_int), POINTER(c_int)], c_int),
+            "kss_server_poll": ([P, c_uint64, POINTER(c_int), P, P, POINTER(c_double)], c_int),
+            "kss_server_get_stats": ([P, POINTER(kss_server_stats)], c_int),
+            "kss_server_stop": ([P], c_int),
             "kss_profile_enable": ([P, c_int], c_int),
             "kss_profile_count": ([P, POINTER(c_int), POINTER(c_longlong)], c_int),
             "kss_profile_entry": ([P, c_int, POINTER(c_char_p), POINTER(c_longlong), POINTER(c_double)], c_int),
@@ -424,3 +437,89 @@ def kss_gemm(ctx, op: int, A, B, C, alpha=1.0, beta=0.0, prec: int = KSS_PREC_FP
     _check(lib().kss_gemm(ctx, op, M, n, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc,
                           complex(alpha).real, complex(alpha).imag, complex(beta).real,
                           complex(beta).imag, prec), ctx)
+
+
+def kss_solve_batch(ctx, systems, iks, nbands, opts: kss_solve_opts, allow_noconv: bool = False):
+    """Solve many (system, k-point) units together; returns (evals list, resid list, stats list, status)."""
+    n = len(systems)
+    hs = (c_void_p * n)(*[s.h.value for s in systems])
+    ik = (c_int * n)(*[int(k) for k in iks])
+    nbd = (c_int * n)(*[int(b) for b in nbands])
+    ev = [np.zeros(int(b)) for b in nbands]
+    rs = [np.zeros(int(b)) for b in nbands]
+    evp = (c_void_p * n)(*[a.ctypes.data for a in ev])
+    rsp = (c_void_p * n)(*[a.ctypes.data for a in rs])
+    st = (kss_solve_stats * n)()
+    status = lib().kss_solve_batch(ctx, n, hs, ik, nbd, byref(opts), evp, rsp, st)
+    if not (status == KSS_ENOCONV and allow_noconv):
+        _check(status, ctx)
+    return ev, rs, [stats_dict(x) for x in st], status
+
+
+# --------------------------------------------------------------------------------------------
+# request server
+
+def _cell_atoms(lattice, ecut, kpts, pos, D, fft_box, vloc_amp, vloc_sigma, nproj_per_atom, proj_alpha):
+    lat = np.ascontiguousarray(np.asarray(lattice, np.float64).reshape(9))
+    k = np.ascontiguousarray(np.asarray(kpts, np.float64).reshape(-1, 3))
+    p = np.ascontiguousarray(np.asarray(pos, np.float64).reshape(-1, 3))
+    d = np.ascontiguousarray(np.asarray(D if D is not None else [], np.float64).reshape(-1))
+    cell = kss_cell()
+    cell.lattice[:] = lat.tolist()
+    cell.ecut = float(ecut)
+    cell.nk = int(k.shape[0])
+    cell.kpts_red = _dptr(k)
+    cell.fft_box[:] = [int(v) for v in (fft_box or (0, 0, 0))]
+    at = kss_atoms()
+    at.natom = int(p.shape[0])
+    at.pos_cart = _dptr(p)
+    at.vloc_amp = float(vloc_amp)
+    at.vloc_sigma = float(vloc_sigma)
+    at.nproj_per_atom = int(nproj_per_atom)
+    at.proj_alpha = float(proj_alpha)
+    at.D = _dptr(d)
+    return cell, at, (k, p, d)
+
+
+def kss_server_start(ctx, hbm_budget_bytes: int, max_slots: int, opts: kss_solve_opts):
+    _check(lib().kss_server_start(ctx, int(hbm_budget_bytes), int(max_slots), byref(opts)), ctx)
+
+
+def kss_server_submit(ctx, lattice, ecut, kpts, pos, D, nband, fft_box=(0, 0, 0), vloc_amp=-2.0,
+                      vloc_sigma=1.0, nproj_per_atom=4, proj_alpha=0.25) -> int:
+    cell, at, keep = _cell_atoms(lattice, ecut, kpts, pos, D, fft_box, vloc_amp, vloc_sigma,
+                                 nproj_per_atom, proj_alpha)
+    t = c_uint64()
+    _check(lib().kss_server_submit(ctx, byref(cell), byref(at), int(nband), byref(t)), ctx)
+    return t.value
+
+
+def kss_server_pump(ctx, max_ms: float = 0.0):
+    a = c_int()
+    q = c_int()
+    _check(lib().kss_server_pump(ctx, float(max_ms), byref(a), byref(q)), ctx)
+    return a.value, q.value
+
+
+def kss_server_poll(ctx, ticket: int, nk: int, nband: int):
+    """Returns None while running, else (status, evals (nk, nband), resid, latency_ms)."""
+    d = c_int()
+    ev = np.zeros((nk, nband))
+    rs = np.zeros((nk, nband))
+    lat = c_double()
+    st = lib().kss_server_poll(ctx, c_uint64(ticket), byref(d), ev.ctypes.data, rs.ctypes.data, byref(lat))
+    if st not in (KSS_OK, KSS_ENOCONV):
+        _check(st, ctx)
+    if not d.value:
+        return None
+    return st, ev, rs, lat.value
+
+
+def kss_server_get_stats(ctx) -> dict:
+    s = kss_server_stats()
+    _check(lib().kss_server_get_stats(ctx, byref(s)), ctx)
+    return {k: getattr(s, k) for k, _ in kss_server_stats._fields_}
+
+
+def kss_server_stop(ctx):
+    _check(lib().kss_server_stop(ctx), ctx)

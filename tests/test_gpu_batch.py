@@ -1,0 +1,148 @@
+"""Batched lockstep solves and the request server, on the GPU through the C ABI.
+
+* kss_solve_batch: units of uneven size (different cells, cutoffs, FFT boxes, band counts and
+  k-points) solved together agree with the oracle's dense eigenvalues (1e-8 Ha FP64, 1e-6 Ha
+  mixed) and with the per-system solver.
+* server: a request gives the same eigenvalues alone and in a mix of other requests (1e-8 Ha);
+  a budget that holds one request at a time still completes every request in order; a request
+  larger than the whole budget is refused with KSS_EBUSY; a repeated request warm-starts.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+import paper_2507_08578_gb300.kss as K
+from tests.kss_helpers import ensure_built, make_ctx, setup
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    ensure_built()
+    c = make_ctx()
+    yield c
+    torch.cuda.synchronize()
+    K.kss_destroy(c)
+
+
+def small_systems():
+    return [
+        W.make_system("b1", 7.0, 6.0, 3, 6, seed=11, kpts=W.SHIFTED_222[:2]),
+        W.make_system("b2", 8.5, 8.0, 5, 10, seed=12, kpts=W.SHIFTED_222[2:3]),
+        W.make_system("b3", 6.0, 10.0, 2, 4, seed=13),
+    ]
+
+
+def oracle_levels(s, ik, nband):
+    p = O.build_problem(s, ik)
+    return O.lowest_eigenpairs(p.dense(), nband)[0]
+
+
+@pytest.mark.parametrize("prec,tol", [(K.KSS_PREC_FP64, 1e-8), (K.KSS_PREC_MIXED, 1e-6)])
+def test_batch_matches_oracle_and_single(ctx, prec, tol):
+    systems = small_systems()
+    handles = [setup(ctx, s) for s in systems]
+    try:
+        units = [(h, s, ik) for h, s in zip(handles, systems) for ik in range(len(s.kpts))]
+        opts = K.make_opts(prec=prec, tol=1e-9 if prec == K.KSS_PREC_FP64 else 0.0, seed=5)
+        ev, rs, st, status = K.kss_solve_batch(ctx, [u[0] for u in units], [u[2] for u in units],
+                                               [u[1].nband for u in units], opts)
+        assert status == K.KSS_OK
+        for (h, s, ik), e, sts in zip(units, ev, st):
+            ref = oracle_levels(s, ik, s.nband)
+            assert np.max(np.abs(e - ref)) < tol, (s.name, ik, np.max(np.abs(e - ref)))
+            single = K.kss_chebfi_solve(h, ik, s.nband, opts)[0]
+            assert np.max(np.abs(e - single)) < tol
+            assert sts["iters"] >= 1
+    finally:
+        for h in handles:
+            K.kss_sys_destroy(h)
+
+
+def submit(ctx, s, nband=None):
+    return K.kss_server_submit(ctx, s.lattice, s.ecut, s.kpts, s.pos, s.D, nband or s.nband,
+                               fft_box=s.fft_box or (0, 0, 0))
+
+
+def drain(ctx, tickets, shapes, limit_s=120.0):
+    import time
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        K.kss_server_pump(ctx, 50.0)
+        for t, (nk, nb) in zip(tickets, shapes):
+            if t in out:
+                continue
+            r = K.kss_server_poll(ctx, t, nk, nb)
+            if r is not None:
+                out[t] = r
+        assert time.time() - t0 < limit_s
+    return [out[t] for t in tickets]
+
+
+def test_server_same_result_alone_and_in_mix(ctx):
+    opts = K.make_opts(tol=1e-9, seed=3)
+    target = W.make_system("t", 7.5, 7.0, 4, 8, seed=21, kpts=W.SHIFTED_222[:2])
+    others = small_systems() + [W.make_system("o", 9.0, 5.0, 6, 12, seed=22)]
+    # alone
+    K.kss_server_start(ctx, 8 << 30, 64, opts)
+    try:
+        (alone,) = drain(ctx, [submit(ctx, target)], [(2, target.nband)])
+    finally:
+        K.kss_server_stop(ctx)
+    # in a mix (fresh server: no warm start), target submitted in the middle
+    K.kss_server_start(ctx, 8 << 30, 64, opts)
+    try:
+        reqs = others[:2] + [target] + others[2:]
+        tickets = [submit(ctx, s) for s in reqs]
+        res = drain(ctx, tickets, [(len(s.kpts), s.nband) for s in reqs])
+        stats = K.kss_server_get_stats(ctx)
+    finally:
+        K.kss_server_stop(ctx)
+    mixed = res[2]
+    assert alone[0] == K.KSS_OK and mixed[0] == K.KSS_OK
+    assert np.max(np.abs(alone[1] - mixed[1])) < 1e-8
+    for ik in range(2):
+        assert np.max(np.abs(mixed[1][ik] - oracle_levels(target, ik, target.nband))) < 1e-8
+    for s, r in zip(reqs, res):
+        for ik in range(len(s.kpts)):
+            assert np.max(np.abs(r[1][ik] - oracle_levels(s, ik, s.nband))) < 1e-8
+    assert stats["completed"] == len(reqs) and stats["p99_ms"] >= stats["p50_ms"] > 0
+
+
+def test_server_admission_budget_and_busy(ctx):
+    opts = K.make_opts(tol=1e-8, seed=4, prec=K.KSS_PREC_MIXED)
+    systems = small_systems()
+    # a budget just above the largest single request: requests run one or two at a time
+    K.kss_server_start(ctx, 96 << 20, 2, opts)
+    try:
+        tickets = [submit(ctx, s) for s in systems]
+        res = drain(ctx, tickets, [(len(s.kpts), s.nband) for s in systems])
+        for s, r in zip(systems, res):
+            assert r[0] == K.KSS_OK
+            for ik in range(len(s.kpts)):
+                assert np.max(np.abs(r[1][ik] - oracle_levels(s, ik, s.nband))) < 1e-6
+        big = W.make_system("big", 20.0, 20.0, 8, 256, seed=9)
+        with pytest.raises(K.KssError) as e:
+            submit(ctx, big)
+        assert e.value.status == K.KSS_EBUSY
+    finally:
+        K.kss_server_stop(ctx)
+
+
+def test_server_warm_start(ctx):
+    opts = K.make_opts(tol=1e-9, seed=6)
+    s = W.make_system("w", 8.0, 8.0, 4, 8, seed=23, kpts=W.SHIFTED_222[:1])
+    K.kss_server_start(ctx, 4 << 30, 16, opts)
+    try:
+        (first,) = drain(ctx, [submit(ctx, s)], [(1, s.nband)])
+        (second,) = drain(ctx, [submit(ctx, s)], [(1, s.nband)])
+        stats = K.kss_server_get_stats(ctx)
+    finally:
+        K.kss_server_stop(ctx)
+    assert stats["warm_hits"] == 1
+    assert np.max(np.abs(first[1] - second[1])) < 1e-8
+    assert second[3] < first[3]  # the warm-started request finishes sooner
