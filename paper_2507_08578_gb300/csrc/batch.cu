@@ -101,7 +101,10 @@ size_t al256(size_t n) { return (n + 255) & ~(size_t)255; }
 // BatchEngine
 // ---------------------------------------------------------------------------------------------
 
-BatchEngine::~BatchEngine() { drop_graph(); }
+BatchEngine::~BatchEngine() {
+  drop_graph();
+  if (cap) cudaStreamDestroy((cudaStream_t)cap);
+}
 
 void BatchEngine::drop_graph() {
   if (gexec) cudaGraphExecDestroy((cudaGraphExec_t)gexec);
@@ -325,8 +328,17 @@ void BatchEngine::run_filter() {
     if (!gexec) {
       // Capture the filter launches once for this set of units; later iterations only rewrite
       // the device tables the kernels read.
+      // Capture on a private stream (the legacy default stream cannot be captured); the graph
+      // is then launched on the context stream, which keeps it ordered with everything else.
+      if (!cap) {
+        cudaStream_t cs = nullptr;
+        KSS_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cap = cs;
+      }
       const bool prof_on = ctx->prof.on;
       ctx->prof.on = false;  // no event records inside the captured region
+      cudaStream_t home = ctx->stream;
+      ctx->stream = (cudaStream_t)cap;
       KSS_CHECK_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
       try {
         if (f64) launch_filter_t<double>();
@@ -335,11 +347,17 @@ void BatchEngine::run_filter() {
         cudaGraph_t g = nullptr;
         cudaStreamEndCapture(ctx->stream, &g);
         if (g) cudaGraphDestroy(g);
+        ctx->stream = home;
         ctx->prof.on = prof_on;
         throw;
       }
       cudaGraph_t g = nullptr;
-      KSS_CHECK_CUDA(cudaStreamEndCapture(ctx->stream, &g));
+      const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &g);
+      ctx->stream = home;
+      if (ec != cudaSuccess) {
+        ctx->prof.on = prof_on;
+        KSS_CHECK_CUDA(ec);
+      }
       cudaGraphExec_t ex = nullptr;
       const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
       cudaGraphDestroy(g);

@@ -54,6 +54,7 @@ class BatchEngine {
   int cn_blocks = 0, cn_rblocks = 0, nn_blocks = 0;
   int steps = 0;
   void* gexec = nullptr;  // cudaGraphExec_t of the captured filter
+  void* cap = nullptr;    // cudaStream_t used only to record the graph
 };
 
 }  // namespace kss

@@ -114,7 +114,7 @@ def test_server_same_result_alone_and_in_mix(ctx):
 
 
 def test_server_admission_budget_and_busy(ctx):
-    opts = K.make_opts(tol=1e-8, seed=4, prec=K.KSS_PREC_MIXED)
+    opts = K.make_opts(seed=4, prec=K.KSS_PREC_MIXED)  # default mixed tolerance (FP32 filter)
     systems = small_systems()
     # a budget just above the largest single request: requests run one or two at a time
     K.kss_server_start(ctx, 96 << 20, 2, opts)
@@ -146,3 +146,33 @@ def test_server_warm_start(ctx):
     assert stats["warm_hits"] == 1
     assert np.max(np.abs(first[1] - second[1])) < 1e-8
     assert second[3] < first[3]  # the warm-started request finishes sooner
+
+
+def test_config4_full_batch_mixed(ctx):
+    """The full config-4 workload (48 systems, 217 (system, k) units, npw 1637-13286, boxes
+    30^3-60^3, 16-128 bands) in one mixed-precision batch: every unit converges; units small
+    enough for the oracle's dense diagonalisation (npw <= 2100, one k-point each) match it to
+    1e-6 Ha; every unit's wanted residuals are below the mixed tolerance after the FP64 finish."""
+    systems = W.config4(48)
+    handles = [setup(ctx, s) for s in systems]
+    try:
+        units = [(h, s, ik) for h, s in zip(handles, systems) for ik in range(len(s.kpts))]
+        assert len(units) == 217
+        opts = K.make_opts(prec=K.KSS_PREC_MIXED, seed=7)
+        ev, rs, st, status = K.kss_solve_batch(ctx, [u[0] for u in units], [u[2] for u in units],
+                                               [u[1].nband for u in units], opts)
+        assert status == K.KSS_OK
+        assert max(r.max() for r in rs) < 1e-5
+        checked = 0
+        for (h, s, ik), e in zip(units, ev):
+            if ik != 0:
+                continue
+            if O.enumerate_sphere(s.lattice, s.ecut, s.kpts[ik]).shape[0] > 2100:
+                continue
+            ref = oracle_levels(s, ik, s.nband)
+            assert np.max(np.abs(e - ref)) < 1e-6, (s.name, np.max(np.abs(e - ref)))
+            checked += 1
+        assert checked >= 5
+    finally:
+        for h in handles:
+            K.kss_sys_destroy(h)
