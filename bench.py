@@ -423,7 +423,7 @@ def run_c3(args):
     s = W.config3()
     ctx = K.kss_create(0, torch.cuda.current_stream().cuda_stream)
     sysh = _setup(K, ctx, s)
-    opts = K.make_opts(prec=K.KSS_PREC_MIXED, seed=11)
+    opts = K.make_opts(prec=K.KSS_PREC_MIXED, seed=11, degree=args.degree)
     for _ in range(args.warmup):
         K.kss_chebfi_solve(sysh, 0, s.nband, opts)
     clocks = Clocks(0)
@@ -432,7 +432,7 @@ def run_c3(args):
     t0 = time.perf_counter()
     napply = 0
     for i in range(args.steps):
-        ev, rs, st, _ = K.kss_chebfi_solve(sysh, 0, s.nband, K.make_opts(prec=K.KSS_PREC_MIXED, seed=20 + i))
+        ev, rs, st, _ = K.kss_chebfi_solve(sysh, 0, s.nband, K.make_opts(prec=K.KSS_PREC_MIXED, seed=20 + i, degree=args.degree))
         napply += st["napply"]
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
@@ -450,7 +450,7 @@ def run_c3(args):
                                              "GEMMs, FP64 Rayleigh-Ritz, FP64 finish"},
                       "band_applies_per_s": napply / dt, "iterations": st["iters"],
                       "max_eig_err_vs_oracle_Ha": float(np.max(np.abs(ev - ref))),
-                      "max_residual_Ha": float(rs.max()), "clocks": ck}), flush=True)
+                      "max_residual_Ha": float(rs.max()), "degree": args.degree, "clocks": ck}), flush=True)
 
 
 def run_c4(args):
@@ -464,7 +464,7 @@ def run_c4(args):
     ctx = K.kss_create(0, torch.cuda.current_stream().cuda_stream)
     handles = [_setup(K, ctx, s) for s in systems]
     units = [(h, s, ik) for h, s in zip(handles, systems) for ik in range(len(s.kpts))]
-    opts = K.make_opts(prec=K.KSS_PREC_MIXED, seed=7)
+    opts = K.make_opts(prec=K.KSS_PREC_MIXED, seed=7, degree=args.degree)
     args_b = ([u[0] for u in units], [u[2] for u in units], [u[1].nband for u in units])
     for _ in range(args.warmup):
         K.kss_solve_batch(ctx, *args_b, opts)
@@ -495,6 +495,7 @@ def run_c4(args):
                       "units_per_s": len(units) * args.steps / dt, "band_applies_per_s": napply * args.steps / dt,
                       "max_residual_Ha": float(max(r.max() for r in rs)),
                       "max_iterations": max(x["iters"] for x in st), "gpu_launches": launches,
+                      "mean_iterations": sum(x["iters"] for x in st) / len(st), "degree": args.degree,
                       "clocks": ck,
                       "kernels": {k: {"launches": v[0], "ms": round(v[1], 2)} for k, v in
                                   sorted(prof.items(), key=lambda kv: -kv[1][1])[:12]}}), flush=True)
@@ -509,7 +510,7 @@ def run_c5(args):
     B.build()
     reqs = W.config5(nreq=args.requests)
     ctx = K.kss_create(0, torch.cuda.current_stream().cuda_stream)
-    opts = K.make_opts(prec=K.KSS_PREC_MIXED, seed=5)
+    opts = K.make_opts(prec=K.KSS_PREC_MIXED, seed=5, degree=args.degree)
     K.kss_server_start(ctx, 150 << 30, 512, opts)
     tickets = {}
     done = {}
@@ -556,6 +557,7 @@ def run_c5(args):
                                              "90% C4-distribution and 10% C1-size systems, 25% repeats "
                                              "(warm start), 150 GB admission budget, mixed precision"},
                       "server_stats": stats, "all_ok": all(s_ == K.KSS_OK for s_ in statuses),
+                      "statuses": {str(k): statuses.count(k) for k in set(statuses)}, "degree": args.degree,
                       "plain_fp64_per_request_solves_per_s": fp64_rate,
                       "plain_fp64_sample": f"first {len(sample)} requests, kss_chebfi_solve FP64 one by one",
                       "clocks": ck}), flush=True)

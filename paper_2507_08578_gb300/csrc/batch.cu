@@ -14,6 +14,9 @@
 #include <cstring>
 #include <memory>
 
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
 #include "batch.h"
 #include "local_kernels.cuh"
 
@@ -95,15 +98,95 @@ void fill_args(kss_sys s, int ik, LocalArgs<T>& a) {
 
 size_t al256(size_t n) { return (n + 255) & ~(size_t)255; }
 
+// Pad block of unit u's np x np matrices: S gets the identity, H gets shift * identity (so the
+// padded eigenvalues sort after every real one); rows/columns >= nb[u] only.
+__global__ void pad_init(double2* Sb, double2* Hb, const int* __restrict__ nbs, int np, double shift) {
+  const int u = blockIdx.y;
+  const int nb = nbs[u];
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)np * np) return;
+  const int i = (int)(idx % np), j = (int)(idx / np);
+  if (i < nb && j < nb) return;
+  const size_t o = (size_t)u * np * np + idx;
+  Sb[o] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  Hb[o] = make_double2(i == j ? shift : 0.0, 0.0);
+}
+
+// Copy the leading m x m block of a complex64 matrix (ld m) into a complex128 matrix (ld np).
+__global__ void c64_to_c128_ld(const float2* __restrict__ in, int m, double2* __restrict__ out, int np) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * m) return;
+  const int i = (int)(idx % m), j = (int)(idx / m);
+  const float2 v = in[idx];
+  out[(size_t)j * np + i] = make_double2(v.x, v.y);
+}
+__global__ void c128_ld_to_c64(const double2* __restrict__ in, int np, float2* __restrict__ out, int m) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * m) return;
+  const int i = (int)(idx % m), j = (int)(idx / m);
+  const double2 v = in[(size_t)j * np + i];
+  out[idx] = make_float2((float)v.x, (float)v.y);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
 // BatchEngine
 // ---------------------------------------------------------------------------------------------
 
+void ctx_release_solver(kss_ctx ctx);               // solver.cu
+cusolverDnHandle_t solver_handle_for(kss_ctx ctx);  // solver.cu (handle bound to ctx->stream)
+
 BatchEngine::~BatchEngine() {
   drop_graph();
+  if (blas) cublasDestroy((cublasHandle_t)blas);
+  if (sparams) cusolverDnDestroyParams((cusolverDnParams_t)sparams);
   if (cap) cudaStreamDestroy((cudaStream_t)cap);
+  for (auto w : workers) {
+    cudaStreamSynchronize(w->stream);
+    ctx_release_solver(w);
+    cudaStreamDestroy(w->stream);
+    delete w;
+  }
+  for (auto e : wev) cudaEventDestroy((cudaEvent_t)e);
+  if (fork_ev) cudaEventDestroy((cudaEvent_t)fork_ev);
+}
+
+// Issue every unit's Rayleigh-Ritz on the worker streams after the work already queued on the
+// context stream, then make the context stream wait for all of them.
+void BatchEngine::rr_all(const std::vector<kss_solver_s*>& us, const std::vector<int>& y,
+                         const std::vector<int>& hy, const std::vector<int>& xo,
+                         const std::vector<int>& hxo) {
+  const int kW = 8;
+  if (workers.empty()) {
+    for (int i = 0; i < kW; ++i) {
+      kss_ctx w = new kss_ctx_s();
+      w->device = ctx->device;
+      cudaStream_t st = nullptr;
+      KSS_CHECK_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      w->stream = st;
+      workers.push_back(w);
+      cudaEvent_t e = nullptr;
+      KSS_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      wev.push_back(e);
+    }
+    cudaEvent_t f = nullptr;
+    KSS_CHECK_CUDA(cudaEventCreateWithFlags(&f, cudaEventDisableTiming));
+    fork_ev = f;
+  }
+  KSS_CHECK_CUDA(cudaEventRecord((cudaEvent_t)fork_ev, ctx->stream));
+  for (auto w : workers) KSS_CHECK_CUDA(cudaStreamWaitEvent(w->stream, (cudaEvent_t)fork_ev, 0));
+  for (size_t u = 0; u < us.size(); ++u) {
+    kss_ctx w = workers[u % workers.size()];
+    kss_solver_s* s = us[u];
+    w->prof.on = false;
+    rr_issue(s, s->f64, s->blk[y[u]].p, s->blk[hy[u]].p, s->blk[xo[u]].p, s->blk[hxo[u]].p, w);
+  }
+  for (size_t i = 0; i < workers.size(); ++i) {
+    KSS_CHECK_CUDA(cudaEventRecord((cudaEvent_t)wev[i], workers[i]->stream));
+    KSS_CHECK_CUDA(cudaStreamWaitEvent(ctx->stream, (cudaEvent_t)wev[i], 0));
+  }
+  ctx->prof.launches += 0;
 }
 
 void BatchEngine::drop_graph() {
@@ -387,11 +470,17 @@ void BatchEngine::iterate(std::vector<kss_solver_s*>& all) {
     if (s->done) continue;
     (s->started ? active : fresh).push_back(s);
   }
+  std::vector<kss_solver_s*> rr_units;
+  std::vector<int> ry, rhy, rxo, rhxo;
   for (auto* s : fresh) {
     apply_h(s->sys, s->ik, s->nb, s->blk[0].p, nullptr, s->blk[1].p, s->npw, ChebCoef{1, 0, 0},
             s->f64 ? KSS_PREC_FP64 : KSS_PREC_MIXED);
     s->napply += s->nb;
-    rr_issue(s, s->f64, s->blk[0].p, s->blk[1].p, s->blk[2].p, s->blk[3].p);
+    rr_units.push_back(s);
+    ry.push_back(0);
+    rhy.push_back(1);
+    rxo.push_back(2);
+    rhxo.push_back(3);
   }
   if (!active.empty()) {
     set_units(active);
@@ -399,14 +488,23 @@ void BatchEngine::iterate(std::vector<kss_solver_s*>& all) {
     for (size_t u = 0; u < active.size(); ++u) {
       kss_solver_s* s = active[u];
       s->napply += (long long)s->nb * steps;
-      rr_issue(s, s->f64, s->blk[roles[u].y].p, s->blk[roles[u].hy].p, s->blk[roles[u].free2].p,
-               s->blk[s->ihx].p);
+      rr_units.push_back(s);
+      ry.push_back(roles[u].y);
+      rhy.push_back(roles[u].hy);
+      rxo.push_back(roles[u].free2);
+      rhxo.push_back(s->ihx);
     }
+  }
+  if (!rr_units.empty()) {
+    bool gram64_any = false;
+    for (auto* s : rr_units) gram64_any |= s->gram64;
+    if (use_batched_rr && !gram64_any) rr_batched(rr_units, ry, rhy, rxo, rhxo);
+    else rr_all(rr_units, ry, rhy, rxo, rhxo);
   }
   KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
   KSS_CHECK_CUDA(cudaGetLastError());
   for (auto* s : fresh) {
-    rr_finish(s);
+    rr_finish_or_retry(s, s->f64, s->blk[0].p, s->blk[1].p, s->blk[2].p, s->blk[3].p);
     s->ix = 2;
     s->ihx = 3;
     s->started = true;
@@ -414,7 +512,8 @@ void BatchEngine::iterate(std::vector<kss_solver_s*>& all) {
   }
   for (size_t u = 0; u < active.size(); ++u) {
     kss_solver_s* s = active[u];
-    rr_finish(s);
+    rr_finish_or_retry(s, s->f64, s->blk[roles[u].y].p, s->blk[roles[u].hy].p, s->blk[roles[u].free2].p,
+                       s->blk[s->ihx].p);
     s->ix = roles[u].free2;
     s->iter += 1;
     decide(s);
@@ -437,6 +536,134 @@ void BatchEngine::decide(kss_solver_s* s) {
       s->done = true;
     }
   }
+}
+
+void BatchEngine::rr_batched(const std::vector<kss_solver_s*>& us, const std::vector<int>& y,
+                             const std::vector<int>& hy, const std::vector<int>& xo,
+                             const std::vector<int>& hxo) {
+  const int U = (int)us.size();
+  int np = 0;
+  for (auto* s : us) np = std::max(np, s->nb);
+  cudaStream_t st = ctx->stream;
+  if (!blas) {
+    cublasHandle_t h = nullptr;
+    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) fail(KSS_ECUDA, "cublasCreate failed");
+    blas = h;
+    cusolverDnParams_t p = nullptr;
+    if (cusolverDnCreateParams(&p) != CUSOLVER_STATUS_SUCCESS) fail(KSS_ECUDA, "cusolverDnCreateParams failed");
+    sparams = p;
+  }
+  cublasSetStream((cublasHandle_t)blas, st);
+  cusolverDnHandle_t sh = solver_handle_for(ctx);
+  const size_t mat = (size_t)np * np;
+  Sb.ensure((size_t)U * mat * sizeof(double2));
+  Hb.ensure((size_t)U * mat * sizeof(double2));
+  Wb.ensure((size_t)U * np * sizeof(double));
+  ptrs.ensure((size_t)2 * U * sizeof(void*) + (size_t)U * sizeof(int));
+  binfo.ensure((size_t)2 * U * sizeof(int));
+  double2* S = Sb.as<double2>();
+  double2* H = Hb.as<double2>();
+  // per-unit pad sizes and matrix pointer arrays
+  std::vector<void*> hp(2 * U);
+  std::vector<int> nbs(U);
+  double shift = 1.0;
+  for (int u = 0; u < U; ++u) {
+    hp[u] = S + u * mat;
+    hp[U + u] = H + u * mat;
+    nbs[u] = us[u]->nb;
+    shift = std::max(shift, std::fabs(us[u]->sys->k[us[u]->ik].bound));
+  }
+  shift = 16.0 * shift + 1.0;
+  void** dS = (void**)ptrs.p;
+  void** dH = dS + U;
+  int* dnb = (int*)(dH + U);
+  KSS_CHECK_CUDA(cudaMemcpyAsync(ptrs.p, hp.data(), 2 * U * sizeof(void*), cudaMemcpyHostToDevice, st));
+  KSS_CHECK_CUDA(cudaMemcpyAsync(dnb, nbs.data(), U * sizeof(int), cudaMemcpyHostToDevice, st));
+  {
+    dim3 g((unsigned)((mat + 255) / 256), U);
+    pad_init<<<g, 256, 0, st>>>(S, H, dnb, np, shift);
+  }
+  // Gram and projected-H matrices of every unit, into the leading nb x nb blocks
+  for (int u = 0; u < U; ++u) {
+    kss_solver_s* s = us[u];
+    const int nb = s->nb, npw = s->npw;
+    const void* Y = s->blk[y[u]].p;
+    const void* HY = s->blk[hy[u]].p;
+    if (s->f64) {
+      gemm_cn(ctx, true, nb, nb, npw, Y, npw, Y, npw, S + u * mat, np, 1, 0, 0, 0, "gram");
+      gemm_cn(ctx, true, nb, nb, npw, Y, npw, HY, npw, H + u * mat, np, 1, 0, 0, 0, "gram");
+    } else {
+      gemm_cn(ctx, false, nb, nb, npw, Y, npw, Y, npw, s->S32.p, nb, 1, 0, 0, 0, "gram");
+      gemm_cn(ctx, false, nb, nb, npw, Y, npw, HY, npw, s->Hs32.p, nb, 1, 0, 0, 0, "gram");
+      const long long nn = (long long)nb * nb;
+      c64_to_c128_ld<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(s->S32.as<float2>(), nb, S + u * mat, np);
+      c64_to_c128_ld<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(s->Hs32.as<float2>(), nb, H + u * mat, np);
+    }
+  }
+  // S = L L^H ; H <- L^{-1} H L^{-H} ; H = V W V^H ; Q = L^{-H} V
+  int* dinfo = binfo.as<int>();
+  if (cusolverDnZpotrfBatched(sh, CUBLAS_FILL_MODE_LOWER, np, (cuDoubleComplex**)dS, np, dinfo, U) !=
+      CUSOLVER_STATUS_SUCCESS)
+    fail(KSS_ECUDA, "cusolverDnZpotrfBatched failed");
+  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0);
+  cublasHandle_t bh = (cublasHandle_t)blas;
+  if (cublasZtrsmBatched(bh, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, np, np,
+                         &one, (const cuDoubleComplex* const*)dS, np, (cuDoubleComplex* const*)dH, np, U) !=
+          CUBLAS_STATUS_SUCCESS ||
+      cublasZtrsmBatched(bh, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, CUBLAS_DIAG_NON_UNIT, np, np,
+                         &one, (const cuDoubleComplex* const*)dS, np, (cuDoubleComplex* const*)dH, np, U) !=
+          CUBLAS_STATUS_SUCCESS)
+    fail(KSS_ECUDA, "cublasZtrsmBatched failed");
+  size_t dws = 0, hws = 0;
+  if (cusolverDnXsyevBatched_bufferSize(sh, (cusolverDnParams_t)sparams, CUSOLVER_EIG_MODE_VECTOR,
+                                        CUBLAS_FILL_MODE_LOWER, np, CUDA_C_64F, H, np, CUDA_R_64F,
+                                        Wb.p, CUDA_C_64F, &dws, &hws, U) != CUSOLVER_STATUS_SUCCESS)
+    fail(KSS_ECUDA, "cusolverDnXsyevBatched_bufferSize failed");
+  bwork.ensure(std::max<size_t>(dws, 16));
+  if (hwork.size() < hws) hwork.resize(hws);
+  if (cusolverDnXsyevBatched(sh, (cusolverDnParams_t)sparams, CUSOLVER_EIG_MODE_VECTOR,
+                             CUBLAS_FILL_MODE_LOWER, np, CUDA_C_64F, H, np, CUDA_R_64F, Wb.p, CUDA_C_64F,
+                             bwork.p, dws, hws ? hwork.data() : nullptr, hws, dinfo + U, U) !=
+      CUSOLVER_STATUS_SUCCESS)
+    fail(KSS_ECUDA, "cusolverDnXsyevBatched failed");
+  if (cublasZtrsmBatched(bh, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, CUBLAS_DIAG_NON_UNIT, np, np,
+                         &one, (const cuDoubleComplex* const*)dS, np, (cuDoubleComplex* const*)dH, np, U) !=
+      CUBLAS_STATUS_SUCCESS)
+    fail(KSS_ECUDA, "cublasZtrsmBatched failed");
+  // rotations, residuals and results of every unit
+  for (int u = 0; u < U; ++u) {
+    kss_solver_s* s = us[u];
+    const int nb = s->nb, npw = s->npw;
+    const void* Y = s->blk[y[u]].p;
+    const void* HY = s->blk[hy[u]].p;
+    void* Xo = s->blk[xo[u]].p;
+    void* HXo = s->blk[hxo[u]].p;
+    const double2* Q = H + u * mat;
+    if (s->f64) {
+      gemm_nn(ctx, true, npw, nb, nb, Y, npw, Q, np, Xo, npw, 1, 0, 0, 0, "rotate");
+      gemm_nn(ctx, true, npw, nb, nb, HY, npw, Q, np, HXo, npw, 1, 0, 0, 0, "rotate");
+    } else {
+      const long long nn = (long long)nb * nb;
+      c128_ld_to_c64<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Q, np, s->Q32.as<float2>(), nb);
+      gemm_nn(ctx, false, npw, nb, nb, Y, npw, s->Q32.p, nb, Xo, npw, 1, 0, 0, 0, "rotate");
+      gemm_nn(ctx, false, npw, nb, nb, HY, npw, s->Q32.p, nb, HXo, npw, 1, 0, 0, 0, "rotate");
+    }
+    const double* W = Wb.as<double>() + (size_t)u * np;
+    residual_norms(ctx, s->f64, Xo, HXo, npw, nb, npw, W, s->resid_d.as<double>());
+    if (!s->hpin) KSS_CHECK_CUDA(cudaMallocHost((void**)&s->hpin, (2 * (size_t)nb + 1) * sizeof(double)));
+    KSS_CHECK_CUDA(cudaMemcpyAsync(s->hpin, W, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KSS_CHECK_CUDA(cudaMemcpyAsync(s->hpin + nb, s->resid_d.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  binfo_h.assign(2 * U, 0);
+  KSS_CHECK_CUDA(cudaMemcpyAsync(binfo_h.data(), dinfo, 2 * U * sizeof(int), cudaMemcpyDeviceToHost, st));
+  KSS_CHECK_CUDA(cudaStreamSynchronize(st));
+  for (int u = 0; u < U; ++u) {
+    // status word read by rr_finish: a failed Cholesky reports n + i like the generalised solver
+    const int pi = binfo_h[u], ei = binfo_h[U + u];
+    const int info = pi != 0 ? us[u]->nb + pi : ei;
+    std::memcpy(us[u]->hpin + 2 * us[u]->nb, &info, sizeof(int));
+  }
+  KSS_CHECK_CUDA(cudaGetLastError());
 }
 
 }  // namespace kss

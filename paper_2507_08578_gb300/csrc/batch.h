@@ -24,6 +24,7 @@ class BatchEngine {
   bool f64 = true;
   int degree = 10;
   bool use_graph = true;
+  bool use_batched_rr = true;
 
   ~BatchEngine();
   // One lockstep iteration over every unit of `all` that is not done (fresh units get their
@@ -54,6 +55,22 @@ class BatchEngine {
   int cn_blocks = 0, cn_rblocks = 0, nn_blocks = 0;
   int steps = 0;
   void* gexec = nullptr;  // cudaGraphExec_t of the captured filter
+  // Worker contexts (own stream, cuSOLVER handle and GEMM workspace) that run the units'
+  // Rayleigh-Ritz steps concurrently.
+  std::vector<kss_ctx> workers;
+  std::vector<void*> wev;  // cudaEvent_t per worker (join)
+  void* fork_ev = nullptr;
+  void rr_all(const std::vector<kss_solver_s*>& us, const std::vector<int>& y,
+              const std::vector<int>& hy, const std::vector<int>& xo, const std::vector<int>& hxo);
+  // Batched FP64 Rayleigh-Ritz of all units: matrices padded to one size, batched Cholesky,
+  // triangular solves and Hermitian eigensolve (one call each for every unit).
+  void rr_batched(const std::vector<kss_solver_s*>& us, const std::vector<int>& y,
+                  const std::vector<int>& hy, const std::vector<int>& xo, const std::vector<int>& hxo);
+  void* blas = nullptr;      // cublasHandle_t
+  void* sparams = nullptr;   // cusolverDnParams_t
+  DevBuf Sb, Hb, Wb, ptrs, binfo, bwork, q32;
+  std::vector<char> hwork;
+  std::vector<int> binfo_h;
   void* cap = nullptr;    // cudaStream_t used only to record the graph
 };
 

@@ -21,14 +21,16 @@ template <typename T> struct CT;
 template <> struct CT<double> { using C = double2; };
 template <> struct CT<float> { using C = float2; };
 
-template <typename T>
-__device__ __forceinline__ void cn_partial_body(int M, int N, int K, const typename CT<T>::C* __restrict__ A,
-                                                long long lda, const typename CT<T>::C* __restrict__ B,
+// Inputs of type TI (complex64 or complex128), accumulation and partial sums in T.
+template <typename T, typename TI = T>
+__device__ __forceinline__ void cn_partial_body(int M, int N, int K, const typename CT<TI>::C* __restrict__ A,
+                                                long long lda, const typename CT<TI>::C* __restrict__ B,
                                                 long long ldb, typename CT<T>::C* __restrict__ P,
                                                 int kchunk, int bx, int by, int bz) {
   using C = typename CT<T>::C;
-  __shared__ C As[BK][BM];
-  __shared__ C Bs[BK][BN];
+  using CI = typename CT<TI>::C;
+  __shared__ CI As[BK][BM];
+  __shared__ CI Bs[BK][BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = bx * BM, j0 = by * BN;
   const int kbeg = bz * kchunk;
@@ -44,7 +46,7 @@ __device__ __forceinline__ void cn_partial_body(int M, int N, int K, const typen
     for (int e = 0; e < 2; ++e) {
       const int k = k0 + lk + e;
       const int gi = i0 + li, gj = j0 + li;
-      C a = {0, 0}, b = {0, 0};
+      CI a = {0, 0}, b = {0, 0};
       if (k < kend && gi < M) a = A[gi * lda + k];
       if (k < kend && gj < N) b = B[gj * ldb + k];
       As[lk + e][li] = a;
@@ -53,18 +55,26 @@ __device__ __forceinline__ void cn_partial_body(int M, int N, int K, const typen
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      C a[4], b[4];
+      T ar_[4], ai_[4], br_[4], bi_[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+      for (int r = 0; r < 4; ++r) {
+        const CI v = As[kk][ty + 16 * r];
+        ar_[r] = (T)v.x;
+        ai_[r] = (T)v.y;
+      }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+      for (int c = 0; c < 4; ++c) {
+        const CI v = Bs[kk][tx + 16 * c];
+        br_[c] = (T)v.x;
+        bi_[c] = (T)v.y;
+      }
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           // conj(a) * b
-          accr[r][c] += a[r].x * b[c].x + a[r].y * b[c].y;
-          acci[r][c] += a[r].x * b[c].y - a[r].y * b[c].x;
+          accr[r][c] += ar_[r] * br_[c] + ai_[r] * bi_[c];
+          acci[r][c] += ar_[r] * bi_[c] - ai_[r] * br_[c];
         }
     }
     __syncthreads();
@@ -85,6 +95,13 @@ __global__ void __launch_bounds__(256) gemm_cn_partial(int M, int N, int K, cons
                                                        long long ldb, typename CT<T>::C* __restrict__ P,
                                                        int kchunk) {
   cn_partial_body<T>(M, N, K, A, lda, B, ldb, P, kchunk, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// complex64 inputs, FP64 accumulation (Gram matrices of ill-conditioned complex64 blocks)
+__global__ void __launch_bounds__(256) gemm_cn_partial_f32in(int M, int N, int K, const float2* __restrict__ A,
+                                                             long long lda, const float2* __restrict__ B,
+                                                             long long ldb, double2* __restrict__ P, int kchunk) {
+  cn_partial_body<double, float>(M, N, K, A, lda, B, ldb, P, kchunk, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <typename T>
@@ -329,6 +346,33 @@ void gemm_cn(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int lda
   }
   if (fp64) run_cn<double>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi, tag);
   else run_cn<float>(ctx, M, N, K, A, lda, B, ldb, C, ldc, ar, ai, br, bi, tag);
+}
+
+// C (complex128, M x N) = A^H B for complex64 A (K x M) and B (K x N), accumulated in FP64.
+void gemm_cn_c64_acc64(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B,
+                       int ldb, void* C, int ldc, const char* tag) {
+  if (M <= 0 || N <= 0) return;
+  KSS_REQUIRE(K > 0 && lda >= K && ldb >= K && ldc >= M, "gemm_cn_c64_acc64: bad leading dimension");
+  const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  const int tiles = tm * tn;
+  const int target = 4 * sm_count(ctx);
+  int splits = std::max(1, std::min((target + tiles - 1) / tiles, (K + 63) / 64));
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  splits = (K + kchunk - 1) / kchunk;
+  ctx->ws_gemm.ensure((size_t)splits * M * N * sizeof(double2));
+  {
+    ProfScope ps(ctx, tag_id("gemm_cn_partial_c64in", true, tag));
+    gemm_cn_partial_f32in<<<dim3(tm, tn, splits), 256, 0, ctx->stream>>>(
+        M, N, K, (const float2*)A, lda, (const float2*)B, ldb, ctx->ws_gemm.as<double2>(), kchunk);
+  }
+  const long long mn = (long long)M * N;
+  {
+    ProfScope ps(ctx, tag_id("gemm_reduce", true, tag));
+    gemm_reduce<double><<<(unsigned)((mn + 255) / 256), 256, 0, ctx->stream>>>(
+        M, N, splits, ctx->ws_gemm.as<double2>(), (double2*)C, ldc, 1.0, 0.0, 0.0, 0.0);
+  }
+  KSS_CHECK_CUDA(cudaGetLastError());
 }
 
 // gemm_cn with a caller-provided partial-sum buffer (no allocation, no profiling events): the

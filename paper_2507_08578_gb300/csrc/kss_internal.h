@@ -150,6 +150,8 @@ struct kss_solver_s {
   double ms_filter = 0, ms_rr = 0, ms_total = 0;
   std::vector<double> hist;  // max wanted residual per iteration
   double* hpin = nullptr;    // pinned host: evals[nb], resid[nb], info (as double) for async RR
+  bool gram64 = false;       // mixed precision: Gram matrices accumulated in FP64 (after a failed
+                             // Cholesky of the FP32-accumulated ones)
   ~kss_solver_s();
 };
 
@@ -233,6 +235,9 @@ void tc_gemm_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const 
 void tc_gemm_nn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                 void* C, int ldc, double ar, double ai, double br, double bi, const char* tag);
 int tc_error_flag(kss_ctx ctx, bool reset);
+// C (complex128) = A^H B for complex64 A, B with FP64 accumulation.
+void gemm_cn_c64_acc64(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B,
+                       int ldb, void* C, int ldc, const char* tag);
 // Scale row i of a complex (M x N, col-major) matrix by real d[i] * s.
 void scale_rows(kss_ctx ctx, bool fp64, int M, int N, void* C, int ldc, const void* d, double s);
 
@@ -248,8 +253,10 @@ struct ChebParams {
 ChebParams cheb_params(const kss_solver_s* s);
 // Rayleigh-Ritz in two halves: issue (GEMMs, FP64 eigensolve, rotations, residuals, async copy of
 // eigenvalues/residuals/info to pinned host memory) and finish (after the stream is synchronised).
-void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo, void* HXo);
+void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo, void* HXo,
+              kss_ctx on = nullptr);  // on: queue on another (worker) context's stream
 void rr_finish(kss_solver_s* s);
+void rr_finish_or_retry(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo, void* HXo);
 void refine_fp64(kss_solver_s* s);
 double max_wanted(const kss_solver_s* s);
 

@@ -121,6 +121,8 @@ cusolverDnHandle_t solver_handle(kss_ctx ctx) {
 
 }  // namespace
 
+cusolverDnHandle_t solver_handle_for(kss_ctx ctx) { return solver_handle(ctx); }
+
 void ctx_release_solver(kss_ctx ctx) {
   if (ctx->cusolver) cusolverDnDestroy((cusolverDnHandle_t)ctx->cusolver);
   ctx->cusolver = nullptr;
@@ -170,8 +172,7 @@ namespace {
 size_t esize(bool f64) { return f64 ? 16 : 8; }
 
 // FP64 generalised eigensolve of (Hs, S) in place: Hs <- Q with Q^H S Q = I, W <- eigenvalues.
-void subspace_eig(kss_solver_s* s) {
-  kss_ctx ctx = s->sys->ctx;
+void subspace_eig(kss_solver_s* s, kss_ctx ctx) {
   cusolverDnHandle_t h = solver_handle(ctx);
   const int nb = s->nb;
   int lwork = 0;
@@ -194,13 +195,17 @@ namespace kss {
 
 // Rayleigh-Ritz on (Y, HY) -> (Xo, HXo): everything is queued on the stream; eigenvalues,
 // residuals and the eigensolver status land in pinned host memory (read by rr_finish).
-void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo, void* HXo) {
-  kss_ctx ctx = s->sys->ctx;
+void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo, void* HXo,
+              kss_ctx on) {
+  kss_ctx ctx = on ? on : s->sys->ctx;
   const int nb = s->nb, npw = s->npw;
   const long long nn = (long long)nb * nb;
   if (f64) {
     gemm_cn(ctx, true, nb, nb, npw, Y, npw, Y, npw, s->S.p, nb, 1, 0, 0, 0, "gram");
     gemm_cn(ctx, true, nb, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, 1, 0, 0, 0, "gram");
+  } else if (s->gram64) {
+    gemm_cn_c64_acc64(ctx, nb, nb, npw, Y, npw, Y, npw, s->S.p, nb, "gram");
+    gemm_cn_c64_acc64(ctx, nb, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, "gram");
   } else {
     gemm_cn(ctx, false, nb, nb, npw, Y, npw, Y, npw, s->S32.p, nb, 1, 0, 0, 0, "gram");
     gemm_cn(ctx, false, nb, nb, npw, Y, npw, HY, npw, s->Hs32.p, nb, 1, 0, 0, 0, "gram");
@@ -214,7 +219,7 @@ void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo
       c64_to_c128<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hs32.as<float2>(), s->Hs.as<double2>(), nn);
     }
   }
-  subspace_eig(s);
+  subspace_eig(s, ctx);
   if (f64) {
     gemm_nn(ctx, true, npw, nb, nb, Y, npw, s->Hs.p, nb, Xo, npw, 1, 0, 0, 0, "rotate");
     gemm_nn(ctx, true, npw, nb, nb, HY, npw, s->Hs.p, nb, HXo, npw, 1, 0, 0, 0, "rotate");
@@ -235,6 +240,22 @@ void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo
   KSS_CHECK_CUDA(cudaMemcpyAsync(s->hpin + nb, s->resid_d.p, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   KSS_CHECK_CUDA(cudaMemcpyAsync(s->hpin + 2 * nb, s->info.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+// rr_finish; in mixed precision a failed Cholesky of the FP32-accumulated Gram matrix (a
+// numerically rank-deficient filtered block) is retried once with FP64 accumulation, and the
+// solver keeps FP64 accumulation from then on.  Y and HY are untouched by the first attempt.
+void rr_finish_or_retry(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo, void* HXo) {
+  try {
+    rr_finish(s);
+  } catch (const KssError& e) {
+    if (e.st != KSS_ENUMERIC || f64 || s->gram64) throw;
+    s->gram64 = true;
+    rr_issue(s, f64, Y, HY, Xo, HXo);
+    KSS_CHECK_CUDA(cudaStreamSynchronize(s->sys->ctx->stream));
+    KSS_CHECK_CUDA(cudaGetLastError());
+    rr_finish(s);
+  }
 }
 
 void rr_finish(kss_solver_s* s) {
@@ -259,7 +280,7 @@ void rayleigh_ritz(kss_solver_s* s, bool f64, const void* Y, const void* HY, voi
   rr_issue(s, f64, Y, HY, Xo, HXo);
   KSS_CHECK_CUDA(cudaStreamSynchronize(s->sys->ctx->stream));
   KSS_CHECK_CUDA(cudaGetLastError());
-  rr_finish(s);
+  rr_finish_or_retry(s, f64, Y, HY, Xo, HXo);
 }
 
 void apply_block(kss_solver_s* s, bool f64, const void* psi, void* out) {
