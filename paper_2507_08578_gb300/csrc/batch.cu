@@ -245,7 +245,7 @@ void BatchEngine::prepare_t() {
   if (smem_ac > 227 * 1024 || smem_b > 227 * 1024)
     fail(KSS_ENOTSUP, "a batched unit's FFT tiles do not fit in shared memory");
   ws.ensure(off);
-  steps = degree + 1;
+  steps = cur_degree + 1;
   litem_bytes = sizeof(LocalItem<T>);
   h_local.assign((size_t)steps * n * litem_bytes, 0);
   h_cn.assign((size_t)steps * n, GemmItem{});
@@ -400,6 +400,15 @@ void BatchEngine::launch_filter_t() {
 }
 
 void BatchEngine::run_filter() {
+  // One degree for every unit of the iteration (the smallest effective degree among them);
+  // a change of degree changes the launch sequence and re-captures the graph.
+  int m = degree;
+  for (auto* s : units) m = std::min(m, cheb_params(s).degree);
+  if (prepared && m + 1 != steps) {
+    prepared = false;
+    drop_graph();
+  }
+  cur_degree = m;
   if (!prepared) {
     if (f64) prepare_t<double>();
     else prepare_t<float>();

@@ -54,6 +54,7 @@ class BatchEngine {
   int blocks_ac = 0, blocks_b = 0;
   int cn_blocks = 0, cn_rblocks = 0, nn_blocks = 0;
   int steps = 0;
+  int cur_degree = 10;
   void* gexec = nullptr;  // cudaGraphExec_t of the captured filter
   // Worker contexts (own stream, cuSOLVER handle and GEMM workspace) that run the units'
   // Rayleigh-Ritz steps concurrently.

@@ -249,6 +249,7 @@ void residual_norms(kss_ctx ctx, bool fp64, const void* X, const void* HX, int n
 // Solver internals shared with the batched / served engine (batch.cu).
 struct ChebParams {
   double e, c, sigma1;
+  int degree;  // effective filter degree of this iteration
 };
 ChebParams cheb_params(const kss_solver_s* s);
 // Rayleigh-Ritz in two halves: issue (GEMMs, FP64 eigensolve, rotations, residuals, async copy of

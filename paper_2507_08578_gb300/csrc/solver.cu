@@ -302,6 +302,18 @@ ChebParams cheb_params(const kss_solver_s* s) {
   p.e = 0.5 * (b - a);
   p.c = 0.5 * (b + a);
   p.sigma1 = p.e / (lam_lo - p.c);
+  p.degree = s->o.degree;
+  if (!s->f64) {
+    // The scaled filter amplifies the lowest Ritz direction by T_m(|x_lo|) relative to the top of
+    // the block, x_lo = (lambda_lo - c) / e.  A complex64 block resolves about seven digits, so in
+    // mixed precision the degree is capped to keep that ratio below 2^12 and leave the top
+    // columns about twelve significant bits.
+    const double xl = std::fabs((lam_lo - p.c) / p.e);
+    if (xl > 1.0) {
+      const int m = (int)std::floor(std::acosh(4096.0) / std::acosh(xl));
+      p.degree = std::max(2, std::min(p.degree, m));
+    }
+  }
   return p;
 }
 }  // namespace kss
@@ -327,7 +339,7 @@ int chebyshev_filter(kss_solver_s* s, int f1, int* prev_out) {
     std::swap(cur, prev);  // cur = Y_1, prev = X
   }
   double sigma = sigma1;
-  const int m = s->o.degree;
+  const int m = cp.degree;
   for (int j = 2; j <= m; ++j) {
     const double sn = 1.0 / (tau - sigma);
     const double al = 2.0 * sn / e;

@@ -120,3 +120,12 @@ def test_stepping_api_matches_full_solve(ctx):
         assert st3["iters"] <= 2 and np.max(np.abs(ev3 - ev)) < 1e-8
     finally:
         K.kss_sys_destroy(sysh)
+
+
+def test_config3_mixed_1024_bands(ctx):
+    """Config 3: the config-1 cell with 1024 bands (block = 75% of the 1503 plane waves) in mixed
+    precision, within 1e-6 Ha of the oracle's dense eigenvalues."""
+    s = W.config3()
+    ev, rs, st, _ = solve(ctx, s, 0, s.nband, prec=K.KSS_PREC_MIXED, seed=3)
+    ref = oracle_levels(s, 0, s.nband)
+    assert np.max(np.abs(ev - ref)) < 1e-6, np.max(np.abs(ev - ref))
