@@ -293,17 +293,57 @@ __global__ void __launch_bounds__(kThreads) pass_c(LocalArgs<T> a) {
   }
 }
 
-template <typename T>
+template <typename T, class Pol = RtPol>
 __global__ void __launch_bounds__(kThreads) pass_a_r(LocalArgs<T> a, RegPlan rp, int scr_warp) {
-  pass_a_body<T>(a, rp, scr_warp, blockIdx.x, blockIdx.y);
+  pass_a_body<T, Pol>(a, rp, scr_warp, blockIdx.x, blockIdx.y);
 }
-template <typename T>
+template <typename T, class Pol = RtPol>
 __global__ void __launch_bounds__(kThreads) pass_b_r(LocalArgs<T> a, RegPlan rp, int scr_warp) {
-  pass_b_body<T>(a, rp, scr_warp, blockIdx.x, blockIdx.y);
+  pass_b_body<T, Pol>(a, rp, scr_warp, blockIdx.x, blockIdx.y);
 }
-template <typename T>
+template <typename T, class Pol = RtPol>
 __global__ void __launch_bounds__(kThreads) pass_c_r(LocalArgs<T> a, RegPlan rp, int scr_warp) {
-  pass_c_body<T>(a, rp, scr_warp, blockIdx.x, blockIdx.y);
+  pass_c_body<T, Pol>(a, rp, scr_warp, blockIdx.x, blockIdx.y);
+}
+
+template <typename T>
+struct PassKernels {
+  void (*a)(LocalArgs<T>, RegPlan, int);
+  void (*b)(LocalArgs<T>, RegPlan, int);
+  void (*c)(LocalArgs<T>, RegPlan, int);
+};
+
+// Kernel instances for a plan: single precision uses the compile-time transforms when the
+// x split (passes A, C) or the common y/z split (pass B) has an instance.
+template <typename T>
+PassKernels<T> pick_kernels(const RegPlan& rp) {
+  PassKernels<T> k{pass_a_r<T, RtPol>, pass_b_r<T, RtPol>, pass_c_r<T, RtPol>};
+  if constexpr (sizeof(T) == 4) {
+    const int c1 = rp.s1.A * 32 + rp.s1.B;
+    const int c23 = (rp.s2.A == rp.s3.A && rp.s2.B == rp.s3.B) ? rp.s2.A * 32 + rp.s2.B : -1;
+    switch (c1) {
+#define KSS_CASE(x, y)                    \
+  case x * 32 + y:                        \
+    k.a = pass_a_r<T, CtPol<x, y>>;        \
+    k.c = pass_c_r<T, CtPol<x, y>>;        \
+    break;
+      KSS_SPLITS(KSS_CASE)
+#undef KSS_CASE
+      default:
+        break;
+    }
+    switch (c23) {
+#define KSS_CASE(x, y)                    \
+  case x * 32 + y:                        \
+    k.b = pass_b_r<T, CtPol<x, y>>;        \
+    break;
+      KSS_SPLITS(KSS_CASE)
+#undef KSS_CASE
+      default:
+        break;
+    }
+  }
+  return k;
 }
 
 
@@ -391,9 +431,10 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
     const size_t rb = es * ((size_t)a.N2 + a.N3 + (size_t)a.W3 * a.N2p + (size_t)kWarps * scr_warp) +
                       sizeof(int) * a.N3;
     if (ra <= smax && rb <= smax) {
-      KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_a_r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
-      KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_b_r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb));
-      KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_c_r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
+      const PassKernels<T> kk = pick_kernels<T>(rp);
+      KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
+      KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb));
+      KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
       static const int ida = prof_register(f64 ? "local_pass_a<f64>" : "local_pass_a<f32>");
       static const int idb = prof_register(f64 ? "local_pass_b<f64>" : "local_pass_b<f32>");
       static const int idc = prof_register(f64 ? "local_pass_c<f64>" : "local_pass_c<f32>");
@@ -402,15 +443,15 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
         a.n0 = n0;
         {
           ProfScope ps(ctx, ida);
-          pass_a_r<T><<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
+          kk.a<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
         }
         {
           ProfScope ps(ctx, idb);
-          pass_b_r<T><<<dim3(a.N1, m), kThreads, rb, ctx->stream>>>(a, rp, scr_warp);
+          kk.b<<<dim3(a.N1, m), kThreads, rb, ctx->stream>>>(a, rp, scr_warp);
         }
         {
           ProfScope ps(ctx, idc);
-          pass_c_r<T><<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
+          kk.c<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
         }
       }
       KSS_CHECK_CUDA(cudaGetLastError());

@@ -62,7 +62,7 @@ struct RegPlan {
 // Transform np (<= sp.PP) pencils with one warp.  in(p, e) returns element e of pencil p, out(p,
 // e, v) receives output element e.  s = +1 inverse, -1 forward.  scr: sp.PP * sp.scr elements.
 template <typename C, typename T, class In, class Out>
-__device__ __forceinline__ void pencil_fft(const Split& sp, int np, const C* tw, T s, C* scr,
+__device__ __forceinline__ void pencil_fft_rt(const Split& sp, int np, const C* tw, T s, C* scr,
                                            int lane, In in, Out out) {
   const int p = lane / sp.L, r = lane - p * sp.L;
   const bool act = p < np;
@@ -101,7 +101,7 @@ __device__ __forceinline__ void pencil_fft(const Split& sp, int np, const C* tw,
 // transforms.  in(p, z) / out(p, z, v) address the sphere-range part of the column; vz(p, z) is
 // the (scaled) potential.
 template <typename C, typename T, class In, class Out, class Vf>
-__device__ __forceinline__ void zcolumn(const Split& sp, int np, const C* tw, C* scr, int lane,
+__device__ __forceinline__ void zcolumn_rt(const Split& sp, int np, const C* tw, C* scr, int lane,
                                         In in, Out out, Vf vz) {
   const int p = lane / sp.L, r = lane - p * sp.L;
   const bool act = p < np;
@@ -162,7 +162,126 @@ __device__ __forceinline__ void zcolumn(const Split& sp, int np, const C* tw, C*
   __syncwarp();
 }
 
-template <typename T>
+// Compile-time forms of the two transforms above for the (A, B) splits the common FFT lengths
+// use: loops fully unrolled with constant shared-memory offsets and no per-element guards.
+template <int A, int B, typename C, typename T, class In, class Out>
+__device__ __forceinline__ void pencil_fft_ct(int np, int scrsz, const C* tw, T s, C* scr, int lane,
+                                              In in, Out out) {
+  constexpr int L = A > B ? A : B;
+  const int p = lane / L, r = lane - p * L;
+  const bool act = p < np;
+  C* sc = scr + p * scrsz;
+  C v[L];
+  if (act && r < B) {
+#pragma unroll
+    for (int i = 0; i < A; ++i) v[i] = in(p, r + B * i);
+    fftr::rdft<A>(v, s);
+#pragma unroll
+    for (int k = 1; k < A; ++k) {
+      C w = tw[r * k];
+      w.y = -s * w.y;
+      v[k] = fftr::mul(v[k], w);
+    }
+#pragma unroll
+    for (int k = 0; k < A; ++k) sc[k * (B + 1) + r] = v[k];
+  }
+  __syncwarp();
+  if (act && r < A) {
+#pragma unroll
+    for (int j = 0; j < B; ++j) v[j] = sc[r * (B + 1) + j];
+    fftr::rdft<B>(v, s);
+#pragma unroll
+    for (int k = 0; k < B; ++k) out(p, r + A * k, v[k]);
+  }
+  __syncwarp();
+}
+
+template <int A, int B, typename C, typename T, class In, class Out, class Vf>
+__device__ __forceinline__ void zcolumn_ct(int np, int scrsz, const C* tw, C* scr, int lane, In in,
+                                           Out out, Vf vz) {
+  constexpr int L = A > B ? A : B;
+  const int p = lane / L, r = lane - p * L;
+  const bool act = p < np;
+  C* sc = scr + p * scrsz;
+  C v[L];
+  if (act && r < B) {
+#pragma unroll
+    for (int i = 0; i < A; ++i) v[i] = in(p, r + B * i);
+    fftr::rdft<A>(v, (T)1);
+#pragma unroll
+    for (int k = 1; k < A; ++k) {
+      C w = tw[r * k];
+      w.y = -w.y;
+      v[k] = fftr::mul(v[k], w);
+    }
+#pragma unroll
+    for (int k = 0; k < A; ++k) sc[k * (B + 1) + r] = v[k];
+  }
+  __syncwarp();
+  if (act && r < A) {
+#pragma unroll
+    for (int j = 0; j < B; ++j) v[j] = sc[r * (B + 1) + j];
+  }
+  __syncwarp();
+  if (act && r < A) {
+    fftr::rdft<B>(v, (T)1);
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const T vv = vz(p, r + A * k);
+      v[k].x *= vv;
+      v[k].y *= vv;
+    }
+    fftr::rdft<B>(v, (T)-1);
+#pragma unroll
+    for (int q = 1; q < B; ++q) v[q] = fftr::mul(v[q], tw[r * q]);
+#pragma unroll
+    for (int q = 0; q < B; ++q) sc[q * (A + 1) + r] = v[q];
+  }
+  __syncwarp();
+  if (act && r < B) {
+#pragma unroll
+    for (int k = 0; k < A; ++k) v[k] = sc[r * (A + 1) + k];
+    fftr::rdft<A>(v, (T)-1);
+#pragma unroll
+    for (int k = 0; k < A; ++k) out(p, r + B * k, v[k]);
+  }
+  __syncwarp();
+}
+
+// FFT policies of the pass bodies: runtime-sized transforms (any split) or the compile-time
+// forms for one (A, B) split.  Each kernel instance uses one policy, so it gets a register
+// allocation for its own split only.
+struct RtPol {
+  template <typename C, typename T, class In, class Out>
+  static __device__ __forceinline__ void pencil(const Split& sp, int np, const C* tw, T s, C* scr,
+                                                int lane, In in, Out out) {
+    pencil_fft_rt<C, T>(sp, np, tw, s, scr, lane, in, out);
+  }
+  template <typename C, typename T, class In, class Out, class Vf>
+  static __device__ __forceinline__ void zcol(const Split& sp, int np, const C* tw, C* scr, int lane,
+                                              In in, Out out, Vf vz) {
+    zcolumn_rt<C, T>(sp, np, tw, scr, lane, in, out, vz);
+  }
+};
+template <int A, int B>
+struct CtPol {
+  template <typename C, typename T, class In, class Out>
+  static __device__ __forceinline__ void pencil(const Split& sp, int np, const C* tw, T s, C* scr,
+                                                int lane, In in, Out out) {
+    pencil_fft_ct<A, B, C, T>(np, sp.scr, tw, s, scr, lane, in, out);
+  }
+  template <typename C, typename T, class In, class Out, class Vf>
+  static __device__ __forceinline__ void zcol(const Split& sp, int np, const C* tw, C* scr, int lane,
+                                              In in, Out out, Vf vz) {
+    zcolumn_ct<A, B, C, T>(np, sp.scr, tw, scr, lane, in, out, vz);
+  }
+};
+
+// Splits with compile-time kernel instances (the FFT lengths 15..60 and 96 of the workloads).
+#define KSS_SPLITS(X) X(3, 5) X(4, 4) X(3, 6) X(4, 5) X(4, 6) X(5, 5) X(3, 9) X(5, 6) X(6, 6) \
+                      X(5, 8) X(5, 9) X(6, 8) X(5, 10) X(6, 9) X(6, 10) X(8, 12)
+
+template <typename T, class Pol = RtPol>
 __device__ __forceinline__ void pass_a_body(const LocalArgs<T>& a, const RegPlan& rp, int scr_warp,
                                             int u3, int nl) {
   using C = typename CT<T>::C;
@@ -186,7 +305,7 @@ __device__ __forceinline__ void pass_a_body(const LocalArgs<T>& a, const RegPlan
   for (int r = warp * sp.PP; r < nrows; r += kWarps * sp.PP) {
     C* rows = tile + (r0 + r) * a.N1p;
     const int ld = a.N1p;
-    pencil_fft<C, T>(sp, min(sp.PP, nrows - r), tw, (T)1, scr, lane,
+    Pol::template pencil<C, T>(sp, min(sp.PP, nrows - r), tw, (T)1, scr, lane,
                      [&](int p, int e) { return rows[p * ld + e]; },
                      [&](int p, int e, C v) { rows[p * ld + e] = v; });
   }
@@ -199,7 +318,7 @@ __device__ __forceinline__ void pass_a_body(const LocalArgs<T>& a, const RegPlan
   }
 }
 
-template <typename T>
+template <typename T, class Pol = RtPol>
 __device__ __forceinline__ void pass_b_body(const LocalArgs<T>& a, const RegPlan& rp, int scr_warp,
                                             int x, int nl) {
   using C = typename CT<T>::C;
@@ -232,7 +351,7 @@ __device__ __forceinline__ void pass_b_body(const LocalArgs<T>& a, const RegPlan
     const Split sp = rp.s2;
     for (int r = warp * sp.PP; r < a.W3; r += kWarps * sp.PP) {
       C* rows = Q + r * N2p;
-      pencil_fft<C, T>(sp, min(sp.PP, a.W3 - r), tw2, (T)1, scr, lane,
+      Pol::template pencil<C, T>(sp, min(sp.PP, a.W3 - r), tw2, (T)1, scr, lane,
                        [&](int p, int e) { return rows[p * N2p + e]; },
                        [&](int p, int e, C v) { rows[p * N2p + e] = v; });
     }
@@ -243,7 +362,7 @@ __device__ __forceinline__ void pass_b_body(const LocalArgs<T>& a, const RegPlan
     const T* vx = a.Vx + (size_t)x * a.N2 * a.N3;
     const int N3 = a.N3;
     for (int y0 = warp * sp.PP; y0 < a.N2; y0 += kWarps * sp.PP) {
-      zcolumn<C, T>(sp, min(sp.PP, a.N2 - y0), tw3, scr, lane,
+      Pol::template zcol<C, T>(sp, min(sp.PP, a.N2 - y0), tw3, scr, lane,
                     [&](int p, int z) {
                       const int u = zmap[z];
                       return u >= 0 ? Q[u * N2p + y0 + p] : C{0, 0};
@@ -260,7 +379,7 @@ __device__ __forceinline__ void pass_b_body(const LocalArgs<T>& a, const RegPlan
     const Split sp = rp.s2;
     for (int r = warp * sp.PP; r < a.W3; r += kWarps * sp.PP) {
       C* rows = Q + r * N2p;
-      pencil_fft<C, T>(sp, min(sp.PP, a.W3 - r), tw2, (T)-1, scr, lane,
+      Pol::template pencil<C, T>(sp, min(sp.PP, a.W3 - r), tw2, (T)-1, scr, lane,
                        [&](int p, int e) { return rows[p * N2p + e]; },
                        [&](int p, int e, C v) { rows[p * N2p + e] = v; });
     }
@@ -274,7 +393,7 @@ __device__ __forceinline__ void pass_b_body(const LocalArgs<T>& a, const RegPlan
   }
 }
 
-template <typename T>
+template <typename T, class Pol = RtPol>
 __device__ __forceinline__ void pass_c_body(const LocalArgs<T>& a, const RegPlan& rp, int scr_warp,
                                             int u3, int nl) {
   using C = typename CT<T>::C;
@@ -298,7 +417,7 @@ __device__ __forceinline__ void pass_c_body(const LocalArgs<T>& a, const RegPlan
   for (int r = warp * sp.PP; r < nrows; r += kWarps * sp.PP) {
     C* rows = tile + (r0 + r) * a.N1p;
     const int ld = a.N1p;
-    pencil_fft<C, T>(sp, min(sp.PP, nrows - r), tw, (T)-1, scr, lane,
+    Pol::template pencil<C, T>(sp, min(sp.PP, nrows - r), tw, (T)-1, scr, lane,
                      [&](int p, int e) { return rows[p * ld + e]; },
                      [&](int p, int e, C v) { rows[p * ld + e] = v; });
   }
