@@ -33,6 +33,7 @@ struct LocalItem {
   RegPlan rp;
   int blk_ac;  // first block of this item in the pass A / pass C launches
   int blk_b;   // first block in the pass B launch
+  int idle;    // unit past its own filter degree: its blocks return at once
 };
 
 template <typename T>
@@ -46,23 +47,58 @@ __device__ __forceinline__ int find_local(const LocalItem<T>* it, int n, int b, 
   return lo;
 }
 
-template <typename T, int PASS>
+template <typename T, int PASS, class Pol>
 __global__ void __launch_bounds__(kThreads) group_pass(const LocalItem<T>* __restrict__ items, int n,
                                                        int scr_warp) {
   __shared__ LocalArgs<T> sa;
   __shared__ RegPlan srp;
-  __shared__ int s_local;
+  __shared__ int s_local, s_idle;
   if (threadIdx.x == 0) {
     const int i = find_local(items, n, blockIdx.x, PASS == 1);
-    sa = items[i].a;
-    srp = items[i].rp;
+    s_idle = items[i].idle;
+    if (!s_idle) {
+      sa = items[i].a;
+      srp = items[i].rp;
+    }
     s_local = blockIdx.x - (PASS == 1 ? items[i].blk_b : items[i].blk_ac);
   }
   __syncthreads();
+  if (s_idle) return;
   const int local = s_local;
-  if (PASS == 0) pass_a_body<T>(sa, srp, scr_warp, local % sa.W3, local / sa.W3);
-  else if (PASS == 1) pass_b_body<T>(sa, srp, scr_warp, local % sa.N1, local / sa.N1);
-  else pass_c_body<T>(sa, srp, scr_warp, local % sa.W3, local / sa.W3);
+  if (PASS == 0) pass_a_body<T, Pol>(sa, srp, scr_warp, local % sa.W3, local / sa.W3);
+  else if (PASS == 1) pass_b_body<T, Pol>(sa, srp, scr_warp, local % sa.N1, local / sa.N1);
+  else pass_c_body<T, Pol>(sa, srp, scr_warp, local % sa.W3, local / sa.W3);
+}
+
+template <typename T>
+using GroupKernel = void (*)(const LocalItem<T>*, int, int);
+
+bool has_ct(int code) {
+  switch (code) {
+#define KSS_CASE(x, y) case x * 32 + y:
+    KSS_SPLITS(KSS_CASE)
+#undef KSS_CASE
+    return true;
+    default:
+      return false;
+  }
+}
+
+// Kernel instance of one grouped pass for a split code (-1: runtime-sized transforms).
+template <typename T, int PASS>
+GroupKernel<T> group_kernel(int code) {
+  if constexpr (sizeof(T) == 4) {
+    switch (code) {
+#define KSS_CASE(x, y) \
+  case x * 32 + y:     \
+    return group_pass<T, PASS, CtPol<x, y>>;
+      KSS_SPLITS(KSS_CASE)
+#undef KSS_CASE
+      default:
+        break;
+    }
+  }
+  return group_pass<T, PASS, RtPol>;
 }
 
 template <typename T>
@@ -235,12 +271,37 @@ void BatchEngine::prepare_t() {
     blocks_ac += kd.W[2] * s->nb;
     blocks_b += sy->N[0] * s->nb;
   }
+  // Units grouped by kernel instance (compile-time split codes in single precision).
+  std::vector<std::pair<long long, int>> key(n);
   for (int u = 0; u < n; ++u) {
+    const RegPlanHost& p = plans[u];
+    int c1 = -1, c23 = -1;
+    if (!f64) {
+      c1 = has_ct(p.s1.A * 32 + p.s1.B) ? p.s1.A * 32 + p.s1.B : -1;
+      if (p.s2.A == p.s3.A && p.s2.B == p.s3.B && has_ct(p.s2.A * 32 + p.s2.B)) c23 = p.s2.A * 32 + p.s2.B;
+    }
+    key[u] = {(long long)(c1 + 1) * 4096 + (c23 + 1), u};
+  }
+  std::stable_sort(key.begin(), key.end());
+  pos.assign(n, 0);
+  classes.clear();
+  for (int i = 0; i < n; ++i) {
+    const int u = key[i].second;
+    pos[u] = i;
+    const int c1 = (int)(key[i].first / 4096) - 1, c23 = (int)(key[i].first % 4096) - 1;
+    if (classes.empty() || classes.back().code1 != c1 || classes.back().code23 != c23)
+      classes.push_back(PassClass{c1, c23, i, 0, 0, 0, 0, 0});
+    PassClass& pc = classes.back();
     kss_sys sy = units[u]->sys;
     const KData& kd = sy->k[units[u]->ik];
-    smem_ac = std::max(smem_ac, es * ((size_t)sy->N[0] + (size_t)kd.W[1] * (sy->N[0] + 1) + (size_t)kWarps * scr_warp));
-    smem_b = std::max(smem_b, es * ((size_t)sy->N[1] + sy->N[2] + (size_t)kd.W[2] * (sy->N[1] + 1) +
-                                    (size_t)kWarps * scr_warp) + sizeof(int) * sy->N[2]);
+    pc.count += 1;
+    pc.blocks_ac += kd.W[2] * units[u]->nb;
+    pc.blocks_b += sy->N[0] * units[u]->nb;
+    pc.smem_ac = std::max(pc.smem_ac, es * ((size_t)sy->N[0] + (size_t)kd.W[1] * (sy->N[0] + 1) + (size_t)kWarps * scr_warp));
+    pc.smem_b = std::max(pc.smem_b, es * ((size_t)sy->N[1] + sy->N[2] + (size_t)kd.W[2] * (sy->N[1] + 1) +
+                                          (size_t)kWarps * scr_warp) + sizeof(int) * sy->N[2]);
+    smem_ac = std::max(smem_ac, pc.smem_ac);
+    smem_b = std::max(smem_b, pc.smem_b);
   }
   if (smem_ac > 227 * 1024 || smem_b > 227 * 1024)
     fail(KSS_ENOTSUP, "a batched unit's FFT tiles do not fit in shared memory");
@@ -253,9 +314,11 @@ void BatchEngine::prepare_t() {
   d_local.ensure(h_local.size());
   d_cn.ensure(h_cn.size() * sizeof(GemmItem));
   d_nn.ensure(h_nn.size() * sizeof(GemmItem));
-  KSS_CHECK_CUDA(cudaFuncSetAttribute(group_pass<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
-  KSS_CHECK_CUDA(cudaFuncSetAttribute(group_pass<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
-  KSS_CHECK_CUDA(cudaFuncSetAttribute(group_pass<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ac));
+  for (const PassClass& pc : classes) {
+    KSS_CHECK_CUDA(cudaFuncSetAttribute(group_kernel<T, 0>(pc.code1), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_ac));
+    KSS_CHECK_CUDA(cudaFuncSetAttribute(group_kernel<T, 1>(pc.code23), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_b));
+    KSS_CHECK_CUDA(cudaFuncSetAttribute(group_kernel<T, 2>(pc.code1), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_ac));
+  }
   prepared = true;
 }
 
@@ -268,6 +331,7 @@ void BatchEngine::fill_tables_t() {
   roles.assign(n, Roles{});
   std::vector<int> cur(n), prev(n);
   std::vector<double> sigma(n), tau(n), e(n), c(n);
+  udeg.assign(n, 0);
   for (int u = 0; u < n; ++u) {
     kss_solver_s* s = units[u];
     int fr[2], nf = 0;
@@ -277,23 +341,40 @@ void BatchEngine::fill_tables_t() {
     prev[u] = fr[0];
     roles[u].free2 = fr[1];
     const ChebParams cp = cheb_params(s);
+    udeg[u] = std::min(cp.degree, steps - 1);
     e[u] = cp.e;
     c[u] = cp.c;
     sigma[u] = cp.sigma1;
     tau[u] = 2.0 / cp.sigma1;
   }
-  for (int j = 0; j < steps; ++j) {
+  // block offsets restart for every class (each class is its own launch)
+  std::vector<int> off_ac(n), off_b(n);
+  for (const PassClass& pc : classes) {
     int bac = 0, bb = 0;
+    for (int i = pc.first; i < pc.first + pc.count; ++i) {
+      int u = 0;
+      while (pos[u] != i) ++u;
+      off_ac[u] = bac;
+      off_b[u] = bb;
+      bac += units[u]->sys->k[units[u]->ik].W[2] * units[u]->nb;
+      bb += units[u]->sys->N[0] * units[u]->nb;
+    }
+  }
+  for (int j = 0; j < steps; ++j) {
     std::vector<GemmItem> cn(n), nn(n);
     for (int u = 0; u < n; ++u) {
       kss_solver_s* s = units[u];
       kss_sys sy = s->sys;
       const KData& kd = sy->k[s->ik];
-      double al, be, ga;
-      const void* psi;
-      const void* pp;
-      void* out;
-      if (j == 0) {  // Y_1 = (sigma1/e)(H - c) X
+      double al = 0, be = 0, ga = 0;
+      const void* psi = nullptr;
+      const void* pp = nullptr;
+      void* out = nullptr;
+      const int mu = udeg[u];
+      const bool idle = j > mu;
+      if (idle) {
+        // past this unit's degree: nothing to do in this step
+      } else if (j == 0) {  // Y_1 = (sigma1/e)(H - c) X
         al = sigma[u] / e[u];
         be = -al * c[u];
         ga = 0;
@@ -301,7 +382,7 @@ void BatchEngine::fill_tables_t() {
         pp = nullptr;
         out = s->blk[prev[u]].p;
         std::swap(cur[u], prev[u]);
-      } else if (j < steps - 1) {  // Y_j from Y_{j-1}, Y_{j-2}, written over Y_{j-2}
+      } else if (j < mu) {  // Y_j from Y_{j-1}, Y_{j-2}, written over Y_{j-2}
         const double sn = 1.0 / (tau[u] - sigma[u]);
         al = 2.0 * sn / e[u];
         be = -al * c[u];
@@ -331,15 +412,15 @@ void BatchEngine::fill_tables_t() {
       it.a.gamma = (T)ga;
       it.a.work = (C*)((char*)ws.p + ws_off[u].slab);
       std::memcpy(&it.rp, &plans[u], sizeof(RegPlan));
-      it.blk_ac = bac;
-      it.blk_b = bb;
-      bac += kd.W[2] * s->nb;
-      bb += sy->N[0] * s->nb;
-      std::memcpy(&h_local[((size_t)j * n + u) * litem_bytes], &it, sizeof(it));
+      it.blk_ac = off_ac[u];
+      it.blk_b = off_b[u];
+      it.idle = idle ? 1 : 0;
+      std::memcpy(&h_local[((size_t)j * n + pos[u]) * litem_bytes], &it, sizeof(it));
       GemmItem& g = cn[u];
       g = GemmItem{};
       GemmItem& h = nn[u];
       h = GemmItem{};
+      g.idle = h.idle = idle ? 1 : 0;
       if (sy->nproj) {
         g.M = sy->nproj;
         g.N = s->nb;
@@ -391,19 +472,29 @@ void BatchEngine::launch_filter_t() {
     const GemmItem* cn = d_cn.as<GemmItem>() + (size_t)j * n;
     const GemmItem* nn = d_nn.as<GemmItem>() + (size_t)j * n;
     if (cn_blocks) group_gemm_cn(ctx, f64, cn, n, cn_blocks, cn_rblocks);
-    group_pass<T, 0><<<blocks_ac, kThreads, smem_ac, ctx->stream>>>(dl + (size_t)j * n, n, scr_warp);
-    group_pass<T, 1><<<blocks_b, kThreads, smem_b, ctx->stream>>>(dl + (size_t)j * n, n, scr_warp);
-    group_pass<T, 2><<<blocks_ac, kThreads, smem_ac, ctx->stream>>>(dl + (size_t)j * n, n, scr_warp);
+    for (const PassClass& pc : classes) {
+      const LocalItem<T>* it = dl + (size_t)j * n + pc.first;
+      group_kernel<T, 0>(pc.code1)<<<pc.blocks_ac, kThreads, pc.smem_ac, ctx->stream>>>(it, pc.count, scr_warp);
+    }
+    for (const PassClass& pc : classes) {
+      const LocalItem<T>* it = dl + (size_t)j * n + pc.first;
+      group_kernel<T, 1>(pc.code23)<<<pc.blocks_b, kThreads, pc.smem_b, ctx->stream>>>(it, pc.count, scr_warp);
+    }
+    for (const PassClass& pc : classes) {
+      const LocalItem<T>* it = dl + (size_t)j * n + pc.first;
+      group_kernel<T, 2>(pc.code1)<<<pc.blocks_ac, kThreads, pc.smem_ac, ctx->stream>>>(it, pc.count, scr_warp);
+    }
     if (nn_blocks) group_gemm_nn(ctx, f64, nn, n, nn_blocks);
   }
   KSS_CHECK_CUDA(cudaGetLastError());
 }
 
 void BatchEngine::run_filter() {
-  // One degree for every unit of the iteration (the smallest effective degree among them);
-  // a change of degree changes the launch sequence and re-captures the graph.
-  int m = degree;
-  for (auto* s : units) m = std::min(m, cheb_params(s).degree);
+  // The graph runs the largest effective degree among the units; a unit with a smaller one sits
+  // out the remaining steps (its items are marked idle).  A change of that largest degree
+  // changes the launch sequence and re-captures the graph.
+  int m = 2;
+  for (auto* s : units) m = std::max(m, cheb_params(s).degree);
   if (prepared && m + 1 != steps) {
     prepared = false;
     drop_graph();
@@ -415,7 +506,7 @@ void BatchEngine::run_filter() {
   }
   if (f64) fill_tables_t<double>();
   else fill_tables_t<float>();
-  const int per_step = 3 + (cn_blocks ? 2 : 0) + (nn_blocks ? 1 : 0);
+  const int per_step = 3 * (int)classes.size() + (cn_blocks ? 2 : 0) + (nn_blocks ? 1 : 0);
   if (use_graph) {
     if (!gexec) {
       // Capture the filter launches once for this set of units; later iterations only rewrite
@@ -496,7 +587,7 @@ void BatchEngine::iterate(std::vector<kss_solver_s*>& all) {
     run_filter();
     for (size_t u = 0; u < active.size(); ++u) {
       kss_solver_s* s = active[u];
-      s->napply += (long long)s->nb * steps;
+      s->napply += (long long)s->nb * (udeg[u] + 1);
       rr_units.push_back(s);
       ry.push_back(roles[u].y);
       rhy.push_back(roles[u].hy);
@@ -538,7 +629,7 @@ void BatchEngine::decide(kss_solver_s* s) {
   } else {
     bool stalled = false;
     const size_t h = s->hist.size();
-    if (h >= 4) stalled = s->hist[h - 1] > 0.9 * s->hist[h - 4];
+    if (h >= 4) stalled = s->hist[h - 1] > 0.9 * s->hist[h - 4] && s->hist[h - 1] < 100.0 * s->tol;
     if (r <= s->tol || stalled || s->iter >= s->o.max_iter) {
       refine_fp64(s);
       s->converged = max_wanted(s) <= s->tol;

@@ -14,6 +14,12 @@ struct RegPlanHost {  // host copy of the per-unit FFT split plan (same layout a
 struct WsOff {
   size_t cprj, part, slab;
 };
+struct PassClass {  // units whose FFT passes share one kernel instance
+  int code1, code23;  // compile-time split codes (A*32+B) or -1 for the runtime-sized form
+  int first, count;   // range in the class-ordered item table
+  int blocks_ac, blocks_b;
+  size_t smem_ac, smem_b;
+};
 struct Roles {
   int y, hy, free2;  // buffers holding Y, H Y, and the free one that receives the rotated X
 };
@@ -44,6 +50,8 @@ class BatchEngine {
   std::vector<Roles> roles;
   bool prepared = false;
   std::vector<RegPlanHost> plans;
+  std::vector<PassClass> classes;
+  std::vector<int> pos;  // position of each unit in the class-ordered item table
   std::vector<WsOff> ws_off;
   DevBuf ws, d_local, d_cn, d_nn;
   std::vector<unsigned char> h_local;
@@ -55,6 +63,7 @@ class BatchEngine {
   int cn_blocks = 0, cn_rblocks = 0, nn_blocks = 0;
   int steps = 0;
   int cur_degree = 10;
+  std::vector<int> udeg;  // effective filter degree of every unit this iteration
   void* gexec = nullptr;  // cudaGraphExec_t of the captured filter
   // Worker contexts (own stream, cuSOLVER handle and GEMM workspace) that run the units'
   // Rayleigh-Ritz steps concurrently.

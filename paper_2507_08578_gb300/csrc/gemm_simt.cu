@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(256) gg_cn_partial(const GemmItem* __restrict_
   using C = typename CT<T>::C;
   const int i = find_item(items, n, blockIdx.x, false);
   const GemmItem& g = items[i];
+  if (g.idle) return;
   const int local = blockIdx.x - g.blk0;
   const int per = g.tm * g.tn;
   const int bz = local / per, r = local - bz * per;
@@ -238,6 +239,7 @@ __global__ void gg_reduce(const GemmItem* __restrict__ items, int n) {
   using C = typename CT<T>::C;
   const int it = find_item(items, n, blockIdx.x, true);
   const GemmItem& g = items[it];
+  if (g.idle) return;
   const long long idx = (long long)(blockIdx.x - g.rblk0) * blockDim.x + threadIdx.x;
   if (idx >= (long long)g.M * g.N) return;
   const int i = (int)(idx % g.M), j = (int)(idx / g.M);
@@ -261,6 +263,7 @@ __global__ void __launch_bounds__(256) gg_nn(const GemmItem* __restrict__ items,
   using C = typename CT<T>::C;
   const int i = find_item(items, n, blockIdx.x, false);
   const GemmItem& g = items[i];
+  if (g.idle) return;
   const int local = blockIdx.x - g.blk0;
   nn_body<T>(g.M, g.N, g.K, (const C*)g.A, g.lda, (const C*)g.B, g.ldb, (C*)g.C, g.ldc, (T)g.ar,
              (T)0, (T)g.br, (T)0, local % g.tm, local / g.tm);

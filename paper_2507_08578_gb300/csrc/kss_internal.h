@@ -224,6 +224,7 @@ struct GemmItem {
   double s;
   double ar, br;    // nn form: C = ar * A B + br * C (real coefficients)
   int tm, tn, splits, kchunk, blk0, rblk0;
+  int idle;         // the item's blocks return at once (unit past its own filter degree)
 };
 void group_plan(kss_ctx ctx, std::vector<GemmItem>& items, bool cn, int* blocks, int* rblocks);
 void group_gemm_cn(kss_ctx ctx, bool fp64, const GemmItem* d_items, int n, int blocks, int rblocks);

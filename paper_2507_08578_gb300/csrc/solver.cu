@@ -418,7 +418,8 @@ void solver_step(kss_solver_s* s) {
   } else {
     bool stalled = false;
     const size_t h = s->hist.size();
-    if (h >= 4) stalled = s->hist[h - 1] > 0.9 * s->hist[h - 4];
+    // stalled at the single-precision floor: no 10% progress in three iterations near tol
+    if (h >= 4) stalled = s->hist[h - 1] > 0.9 * s->hist[h - 4] && s->hist[h - 1] < 100.0 * s->tol;
     if (r <= s->tol || stalled || s->iter >= s->o.max_iter) {
       refine_fp64(s);
       s->converged = max_wanted(s) <= s->tol;
