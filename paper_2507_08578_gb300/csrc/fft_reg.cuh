@@ -67,7 +67,26 @@ template <typename C> __device__ __forceinline__ C mul(C a, C b) {
   r.y = a.x * b.y + a.y * b.x;
   return r;
 }
-template <typename C, typename T> __device__ __forceinline__ C muli(C a, T s) { C r; r.x = -s * a.y; r.y = s * a.x; return r; }
+// multiply by s*i for s = +-1: sign flips only (no multiplication)
+template <typename C, typename T> __device__ __forceinline__ C muli(C a, T s) {
+  C r;
+  if (s > (T)0) {
+    r.x = -a.y;
+    r.y = a.x;
+  } else {
+    r.x = a.y;
+    r.y = -a.x;
+  }
+  return r;
+}
+// multiply by s*m*i for s = +-1 and a constant m > 0
+template <typename C, typename T> __device__ __forceinline__ C muli_m(C a, T s, T m) {
+  const T ms = s > (T)0 ? m : -m;
+  C r;
+  r.x = -ms * a.y;
+  r.y = ms * a.x;
+  return r;
+}
 
 __host__ __device__ constexpr int first_factor(int n) { return n % 4 == 0 && n != 4 ? 4 : n % 2 == 0 && n != 2 ? 2 : n % 3 == 0 && n != 3 ? 3 : n % 5 == 0 && n != 5 ? 5 : n; }
 
@@ -87,7 +106,7 @@ __device__ __forceinline__ void rdft_base(C* v, T s) {
     C t2;
     t2.x = v[0].x - h * t1.x;
     t2.y = v[0].y - h * t1.y;
-    const C t3 = muli(sub(v[1], v[2]), s * s3);
+    const C t3 = muli_m(sub(v[1], v[2]), s, s3);
     v[0] = add(v[0], t1);
     v[1] = add(t2, t3);
     v[2] = sub(t2, t3);
@@ -138,10 +157,17 @@ __device__ __forceinline__ void rdft_split(C* v, T s) {
       constexpr int k1 = decltype(kc)::value;
       if constexpr ((j * k1) % N != 0) {
         constexpr double wc = kcos(j * k1, N), ws = ksin(j * k1, N);
-        C w;
-        w.x = (T)wc;
-        w.y = s * (T)ws;
-        t[j][k1] = mul(t[j][k1], w);
+        if constexpr (wc == 0.0 && (ws == 1.0 || ws == -1.0)) {
+          t[j][k1] = muli(t[j][k1], ws > 0.0 ? s : -s);  // w = +-i
+        } else if constexpr (ws == 0.0 && wc == -1.0) {
+          t[j][k1].x = -t[j][k1].x;  // w = -1
+          t[j][k1].y = -t[j][k1].y;
+        } else {
+          C w;
+          w.x = (T)wc;
+          w.y = s > (T)0 ? (T)ws : -(T)ws;
+          t[j][k1] = mul(t[j][k1], w);
+        }
       }
     });
   });

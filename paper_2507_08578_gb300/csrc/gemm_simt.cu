@@ -68,13 +68,16 @@ __device__ __forceinline__ void cn_partial_body(int M, int N, int K, const typen
         br_[c] = (T)v.x;
         bi_[c] = (T)v.y;
       }
+      // conj(a) * b as four fused multiply-adds per complex product (no separate add or
+      // multiply: the FP64 pipe issues exactly one instruction per real multiply-add)
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          // conj(a) * b
-          accr[r][c] += ar_[r] * br_[c] + ai_[r] * bi_[c];
-          acci[r][c] += ar_[r] * bi_[c] - ai_[r] * br_[c];
+          accr[r][c] = fma(ar_[r], br_[c], accr[r][c]);
+          accr[r][c] = fma(ai_[r], bi_[c], accr[r][c]);
+          acci[r][c] = fma(ar_[r], bi_[c], acci[r][c]);
+          acci[r][c] = fma(-ai_[r], br_[c], acci[r][c]);
         }
     }
     __syncthreads();
@@ -176,8 +179,10 @@ __device__ __forceinline__ void nn_body(int M, int N, int K, const typename CT<T
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          accr[r][c] += a[r].x * b[c].x - a[r].y * b[c].y;
-          acci[r][c] += a[r].x * b[c].y + a[r].y * b[c].x;
+          accr[r][c] = fma(a[r].x, b[c].x, accr[r][c]);
+          accr[r][c] = fma(-a[r].y, b[c].y, accr[r][c]);
+          acci[r][c] = fma(a[r].x, b[c].y, acci[r][c]);
+          acci[r][c] = fma(a[r].y, b[c].x, acci[r][c]);
         }
     }
     __syncthreads();

@@ -77,7 +77,7 @@ __device__ __forceinline__ void pencil_fft_rt(const Split& sp, int np, const C* 
     for (int k = 1; k < kMaxR; ++k)
       if (k < sp.A) {
         C w = tw[r * k];
-        w.y = -s * w.y;
+        if (s > (T)0) w.y = -w.y;  // table holds e^{-2 pi i m/N}; conjugate for the inverse
         v[k] = fftr::mul(v[k], w);
       }
 #pragma unroll
@@ -179,7 +179,7 @@ __device__ __forceinline__ void pencil_fft_ct(int np, int scrsz, const C* tw, T 
 #pragma unroll
     for (int k = 1; k < A; ++k) {
       C w = tw[r * k];
-      w.y = -s * w.y;
+      if (s > (T)0) w.y = -w.y;  // conjugate for the inverse
       v[k] = fftr::mul(v[k], w);
     }
 #pragma unroll
