@@ -70,8 +70,44 @@ __global__ void __launch_bounds__(kThreads) group_pass(const LocalItem<T>* __res
   else pass_c_body<T, Pol>(sa, srp, scr_warp, local % sa.W3, local / sa.W3);
 }
 
+// Pass B of a class with a common compile-time y/z split, in the CTA-wide form.
+template <typename T, int A, int B>
+__global__ void __launch_bounds__(kThreads) group_passw(const LocalItem<T>* __restrict__ items, int n,
+                                                        int) {
+  __shared__ LocalArgs<T> sa;
+  __shared__ int s_local, s_idle;
+  if (threadIdx.x == 0) {
+    const int i = find_local(items, n, blockIdx.x, true);
+    s_idle = items[i].idle;
+    if (!s_idle) sa = items[i].a;
+    s_local = blockIdx.x - items[i].blk_b;
+  }
+  __syncthreads();
+  if (s_idle) return;
+  const int local = s_local;
+  pass_bw_body<T, A, B>(sa, local % sa.N1, local / sa.N1);
+}
+
 template <typename T>
 using GroupKernel = void (*)(const LocalItem<T>*, int, int);
+
+template <typename T>
+GroupKernel<T> group_kernel_w(int code) {
+  switch (code) {
+#define KSS_CASE(x, y) \
+  case x * 32 + y:     \
+    return group_passw<T, x, y>;
+    KSS_SPLITS(KSS_CASE)
+#undef KSS_CASE
+    default:
+      return nullptr;
+  }
+}
+
+size_t wide_b_smem(int code, int W3, size_t es) {
+  const int N = (code / 32) * (code % 32);
+  return es * ((size_t)N + (size_t)W3 * (N + 1) + (size_t)N * (N + 1)) + sizeof(int) * N;
+}
 
 bool has_ct(int code) {
   switch (code) {
@@ -276,10 +312,8 @@ void BatchEngine::prepare_t() {
   for (int u = 0; u < n; ++u) {
     const RegPlanHost& p = plans[u];
     int c1 = -1, c23 = -1;
-    if (!f64) {
-      c1 = has_ct(p.s1.A * 32 + p.s1.B) ? p.s1.A * 32 + p.s1.B : -1;
-      if (p.s2.A == p.s3.A && p.s2.B == p.s3.B && has_ct(p.s2.A * 32 + p.s2.B)) c23 = p.s2.A * 32 + p.s2.B;
-    }
+    c1 = has_ct(p.s1.A * 32 + p.s1.B) ? p.s1.A * 32 + p.s1.B : -1;
+    if (p.s2.A == p.s3.A && p.s2.B == p.s3.B && has_ct(p.s2.A * 32 + p.s2.B)) c23 = p.s2.A * 32 + p.s2.B;
     key[u] = {(long long)(c1 + 1) * 4096 + (c23 + 1), u};
   }
   std::stable_sort(key.begin(), key.end());
@@ -290,7 +324,7 @@ void BatchEngine::prepare_t() {
     pos[u] = i;
     const int c1 = (int)(key[i].first / 4096) - 1, c23 = (int)(key[i].first % 4096) - 1;
     if (classes.empty() || classes.back().code1 != c1 || classes.back().code23 != c23)
-      classes.push_back(PassClass{c1, c23, i, 0, 0, 0, 0, 0});
+      classes.push_back(PassClass{c1, c23, i, 0, 0, 0, 0, 0, 0, false});
     PassClass& pc = classes.back();
     kss_sys sy = units[u]->sys;
     const KData& kd = sy->k[units[u]->ik];
@@ -300,9 +334,11 @@ void BatchEngine::prepare_t() {
     pc.smem_ac = std::max(pc.smem_ac, es * ((size_t)sy->N[0] + (size_t)kd.W[1] * (sy->N[0] + 1) + (size_t)kWarps * scr_warp));
     pc.smem_b = std::max(pc.smem_b, es * ((size_t)sy->N[1] + sy->N[2] + (size_t)kd.W[2] * (sy->N[1] + 1) +
                                           (size_t)kWarps * scr_warp) + sizeof(int) * sy->N[2]);
+    if (c23 >= 0) pc.smem_bw = std::max(pc.smem_bw, wide_b_smem(c23, kd.W[2], es));
     smem_ac = std::max(smem_ac, pc.smem_ac);
     smem_b = std::max(smem_b, pc.smem_b);
   }
+  for (PassClass& pc : classes) pc.wide_b = pc.code23 >= 0 && pc.smem_bw <= 227 * 1024;
   if (smem_ac > 227 * 1024 || smem_b > 227 * 1024)
     fail(KSS_ENOTSUP, "a batched unit's FFT tiles do not fit in shared memory");
   ws.ensure(off);
@@ -316,7 +352,10 @@ void BatchEngine::prepare_t() {
   d_nn.ensure(h_nn.size() * sizeof(GemmItem));
   for (const PassClass& pc : classes) {
     KSS_CHECK_CUDA(cudaFuncSetAttribute(group_kernel<T, 0>(pc.code1), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_ac));
-    KSS_CHECK_CUDA(cudaFuncSetAttribute(group_kernel<T, 1>(pc.code23), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_b));
+    if (pc.wide_b)
+      KSS_CHECK_CUDA(cudaFuncSetAttribute(group_kernel_w<T>(pc.code23), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_bw));
+    else
+      KSS_CHECK_CUDA(cudaFuncSetAttribute(group_kernel<T, 1>(pc.code23), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_b));
     KSS_CHECK_CUDA(cudaFuncSetAttribute(group_kernel<T, 2>(pc.code1), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_ac));
   }
   prepared = true;
@@ -478,7 +517,10 @@ void BatchEngine::launch_filter_t() {
     }
     for (const PassClass& pc : classes) {
       const LocalItem<T>* it = dl + (size_t)j * n + pc.first;
-      group_kernel<T, 1>(pc.code23)<<<pc.blocks_b, kThreads, pc.smem_b, ctx->stream>>>(it, pc.count, scr_warp);
+      if (pc.wide_b)
+        group_kernel_w<T>(pc.code23)<<<pc.blocks_b, kThreads, pc.smem_bw, ctx->stream>>>(it, pc.count, scr_warp);
+      else
+        group_kernel<T, 1>(pc.code23)<<<pc.blocks_b, kThreads, pc.smem_b, ctx->stream>>>(it, pc.count, scr_warp);
     }
     for (const PassClass& pc : classes) {
       const LocalItem<T>* it = dl + (size_t)j * n + pc.first;

@@ -19,6 +19,8 @@ struct PassClass {  // units whose FFT passes share one kernel instance
   int first, count;   // range in the class-ordered item table
   int blocks_ac, blocks_b;
   size_t smem_ac, smem_b;
+  size_t smem_bw;  // shared memory of the CTA-wide pass B form
+  bool wide_b;     // pass B runs in the CTA-wide form
 };
 struct Roles {
   int y, hy, free2;  // buffers holding Y, H Y, and the free one that receives the rotated X

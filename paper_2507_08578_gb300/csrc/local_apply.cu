@@ -13,12 +13,18 @@
 //     out = alpha*(T psi + V psi) + beta*psi + gamma*psi_prev
 // Only pencils that can hold sphere data are transformed (the slab keeps W2 x W3 of the N2 x N3
 // (y, z) cross-section), so the executed FFT work is about half of the dense 3D transform.
-// Every 1D transform is a warp-level in-place Stockham FFT (radix 4/2/3/5) on contiguous
-// pencils in shared memory; twiddles come from a per-dimension table staged in shared memory.
+// Kernel forms, best first:
+//   * pass B with a common y/z length A*B that has a compile-time instance: the CTA-wide form
+//     (local_wide.cu), every transform stage spread over all lanes of the CTA;
+//   * passes A/C (and pass B otherwise) with a compile-time split: per-warp two-level register
+//     codelets (fft_reg.cuh, CtPol), else the same with runtime sizes (RtPol);
+//   * lengths that do not split into two codelets of size <= 16: warp-level Stockham FFTs
+//     (radix 4/2/3/5) on contiguous pencils in shared memory (the kernels in this file).
 // The slab lives in a workspace of nc bands (chunked so that it stays L2-resident).
 #include <algorithm>
 
 #include "local_kernels.cuh"
+#include "local_wide.h"
 
 namespace kss {
 
@@ -313,12 +319,13 @@ struct PassKernels {
   void (*c)(LocalArgs<T>, RegPlan, int);
 };
 
-// Kernel instances for a plan: single precision uses the compile-time transforms when the
-// x split (passes A, C) or the common y/z split (pass B) has an instance.
+// Kernel instances for a plan: the compile-time transforms when the x split (passes A, C) or,
+// in single precision, the common y/z split (pass B) has an instance.  (Double-precision pass B
+// with a common y/z split runs the CTA-wide form of local_wide.cu.)
 template <typename T>
 PassKernels<T> pick_kernels(const RegPlan& rp) {
   PassKernels<T> k{pass_a_r<T, RtPol>, pass_b_r<T, RtPol>, pass_c_r<T, RtPol>};
-  if constexpr (sizeof(T) == 4) {
+  {
     const int c1 = rp.s1.A * 32 + rp.s1.B;
     const int c23 = (rp.s2.A == rp.s3.A && rp.s2.B == rp.s3.B) ? rp.s2.A * 32 + rp.s2.B : -1;
     switch (c1) {
@@ -332,15 +339,17 @@ PassKernels<T> pick_kernels(const RegPlan& rp) {
       default:
         break;
     }
-    switch (c23) {
+    if constexpr (sizeof(T) == 4) {
+      switch (c23) {
 #define KSS_CASE(x, y)                    \
   case x * 32 + y:                        \
     k.b = pass_b_r<T, CtPol<x, y>>;        \
     break;
-      KSS_SPLITS(KSS_CASE)
+        KSS_SPLITS(KSS_CASE)
 #undef KSS_CASE
-      default:
-        break;
+        default:
+          break;
+      }
     }
   }
   return k;
@@ -432,6 +441,7 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
                       sizeof(int) * a.N3;
     if (ra <= smax && rb <= smax) {
       const PassKernels<T> kk = pick_kernels<T>(rp);
+      const bool wide = wide_pass_b<T>(a, rp.s2.A, rp.s2.B, 0, ctx->stream, true);
       KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
       KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb));
       KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
@@ -447,7 +457,8 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
         }
         {
           ProfScope ps(ctx, idb);
-          kk.b<<<dim3(a.N1, m), kThreads, rb, ctx->stream>>>(a, rp, scr_warp);
+          if (!wide) kk.b<<<dim3(a.N1, m), kThreads, rb, ctx->stream>>>(a, rp, scr_warp);
+          else wide_pass_b<T>(a, rp.s2.A, rp.s2.B, m, ctx->stream, false);
         }
         {
           ProfScope ps(ctx, idc);
@@ -530,15 +541,18 @@ void run_local_ws(kss_sys s, int ik, int nb, const void* psi, void* out, int ld,
     const size_t rb = es * ((size_t)a.N2 + a.N3 + (size_t)a.W3 * a.N2p + (size_t)kWarps * scr_warp) +
                       sizeof(int) * a.N3;
     if (ra <= smax && rb <= smax) {
-      KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_a_r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
-      KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_b_r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb));
-      KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_c_r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
+      const PassKernels<T> kk = pick_kernels<T>(rp);
+      const bool wide = wide_pass_b<T>(a, rp.s2.A, rp.s2.B, 0, ctx->stream, true);
+      KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
+      KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb));
+      KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
       for (int n0 = 0; n0 < nb; n0 += nc) {
         const int m = std::min(nc, nb - n0);
         a.n0 = n0;
-        pass_a_r<T><<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
-        pass_b_r<T><<<dim3(a.N1, m), kThreads, rb, ctx->stream>>>(a, rp, scr_warp);
-        pass_c_r<T><<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
+        kk.a<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
+        if (!wide) kk.b<<<dim3(a.N1, m), kThreads, rb, ctx->stream>>>(a, rp, scr_warp);
+        else wide_pass_b<T>(a, rp.s2.A, rp.s2.B, m, ctx->stream, false);
+        kk.c<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
       }
       KSS_CHECK_CUDA(cudaGetLastError());
       return;

@@ -446,6 +446,183 @@ __device__ __forceinline__ void pass_c_body(const LocalArgs<T>& a, const RegPlan
 }
 
 // Best two-factor split N = A*B over the codelet sizes (fewest warp instructions per pencil).
+// Pass B with every transform stage spread over the whole CTA.  The per-warp pencil forms above
+// give each pencil max(A, B) lanes, so a stage of size min(A, B) leaves lanes idle (for 96 = 8 x
+// 12, a third of the lanes in stage 1 and half in stage 2).  Here each stage is one loop over all
+// (pencil, sub-transform) tasks of the x-plane, and every stage works in place:
+//   inverse, stage 1: task (pencil, r < B) reads elements r + B i (i < A), DFT-A, twiddle, writes
+//                     them back; stage 2: task (pencil, k < A) reads the B contiguous elements
+//                     j + B k, DFT-B, writes back, so that position k2 + B k holds the transform
+//                     at index k + A k2 (digit-reversed order);
+//   forward,  stage 1: task (pencil, r < A) reads the B contiguous elements at positions k2 + B r
+//                     (input index r + A k2), DFT-B, twiddle, writes back; stage 2: task (pencil,
+//                     q < B) reads positions q + B m (m < A), DFT-A, writes index q + B k at
+//                     position q + B k (natural order).
+// The y rows stay in digit-reversed order through the z stages, which only need to know which y
+// a column holds (to read V).  The z columns of the whole plane live in a second buffer Z, so the
+// inverse z transform reads the sphere window rows of Q (zeros elsewhere) and the forward one
+// writes only the window rows back.  Requires N2 == N3 == A * B.
+template <typename T, int A, int B>
+struct WideB {
+  static constexpr int N = A * B;
+  static constexpr int QS = N + 1;  // row strides (padded)
+  static constexpr int ZS = N + 1;
+  static size_t smem(int W3) {
+    return sizeof(typename CT<T>::C) * ((size_t)N + (size_t)W3 * QS + (size_t)N * ZS) + sizeof(int) * N;
+  }
+};
+
+template <typename T, int A, int B>
+__device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int nl) {
+  using C = typename CT<T>::C;
+  using G = WideB<T, A, B>;
+  constexpr int N = G::N, QS = G::QS, ZS = G::ZS;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* tw = reinterpret_cast<C*>(smraw);  // e^{-2 pi i m / N}, m < N
+  C* Q = tw + N;                        // W3 rows (z in the sphere window) x N (y)
+  C* Z = Q + a.W3 * QS;                 // N columns (y position) x N (z)
+  int* zmap = reinterpret_cast<int*>(Z + N * ZS);
+  const int tid = threadIdx.x;
+  const int W3 = a.W3, W2 = a.W2;
+  copy_table(tw, a.tw2, N);
+  for (int z = tid; z < N; z += kThreads) {
+    int u = (z - a.lo3) % N;
+    if (u < 0) u += N;
+    zmap[z] = u < W3 ? u : -1;
+  }
+  for (int i = tid; i < W3 * QS; i += kThreads) Q[i] = C{0, 0};
+  __syncthreads();
+  C* slab = a.work + ((size_t)nl * a.N1 + x) * W3 * W2;
+  for (int i = tid; i < W3 * W2; i += kThreads) {
+    const int u3 = i / W2, u2 = i - u3 * W2;
+    int y = (a.lo2 + u2) % N;
+    if (y < 0) y += N;
+    Q[u3 * QS + y] = slab[i];
+  }
+  __syncthreads();
+  // ---- y, inverse ----
+  for (int t = tid; t < W3 * B; t += kThreads) {
+    const int u = t / B, r = t - u * B;
+    C* row = Q + u * QS + r;
+    C v[A];
+#pragma unroll
+    for (int i = 0; i < A; ++i) v[i] = row[B * i];
+    fftr::rdft<A>(v, (T)1);
+#pragma unroll
+    for (int k = 1; k < A; ++k) {
+      C w = tw[r * k];
+      w.y = -w.y;
+      v[k] = fftr::mul(v[k], w);
+    }
+#pragma unroll
+    for (int k = 0; k < A; ++k) row[B * k] = v[k];
+  }
+  __syncthreads();
+  for (int t = tid; t < W3 * A; t += kThreads) {
+    const int u = t / A, k = t - u * A;
+    C* row = Q + u * QS + B * k;
+    C v[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) v[j] = row[j];
+    fftr::rdft<B>(v, (T)1);
+#pragma unroll
+    for (int j = 0; j < B; ++j) row[j] = v[j];
+  }
+  __syncthreads();
+  // ---- z, inverse stage 1 (column p of the plane; only window rows are nonzero) ----
+  for (int t = tid; t < N * B; t += kThreads) {
+    const int r = t / N, p = t - r * N;
+    C v[A];
+#pragma unroll
+    for (int i = 0; i < A; ++i) {
+      const int u = zmap[r + B * i];
+      v[i] = u >= 0 ? Q[u * QS + p] : C{0, 0};
+    }
+    fftr::rdft<A>(v, (T)1);
+#pragma unroll
+    for (int k = 1; k < A; ++k) {
+      C w = tw[r * k];
+      w.y = -w.y;
+      v[k] = fftr::mul(v[k], w);
+    }
+    C* col = Z + p * ZS + r;
+#pragma unroll
+    for (int k = 0; k < A; ++k) col[B * k] = v[k];
+  }
+  __syncthreads();
+  // ---- z, inverse stage 2, x V, forward stage 1 ----
+  const T* vx = a.Vx + (size_t)x * N * N;
+  for (int t = tid; t < N * A; t += kThreads) {
+    const int p = t / A, k = t - p * A;
+    const int py = p / B;
+    const int y = py + A * (p - py * B);  // position p = k2 + B k of a y row holds y = k + A k2
+    const T* vrow = vx + (size_t)y * N + k;
+    C* col = Z + p * ZS + B * k;
+    C v[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) v[j] = col[j];
+    fftr::rdft<B>(v, (T)1);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) {
+      const T vv = vrow[A * k2];  // z = k + A k2
+      v[k2].x *= vv;
+      v[k2].y *= vv;
+    }
+    fftr::rdft<B>(v, (T)-1);
+#pragma unroll
+    for (int q = 1; q < B; ++q) v[q] = fftr::mul(v[q], tw[k * q]);
+#pragma unroll
+    for (int q = 0; q < B; ++q) col[q] = v[q];
+  }
+  __syncthreads();
+  // ---- z, forward stage 2: keep the window rows ----
+  for (int t = tid; t < N * B; t += kThreads) {
+    const int q = t / N, p = t - q * N;
+    const C* col = Z + p * ZS + q;
+    C v[A];
+#pragma unroll
+    for (int m = 0; m < A; ++m) v[m] = col[B * m];
+    fftr::rdft<A>(v, (T)-1);
+#pragma unroll
+    for (int k = 0; k < A; ++k) {
+      const int u = zmap[q + B * k];
+      if (u >= 0) Q[u * QS + p] = v[k];
+    }
+  }
+  __syncthreads();
+  // ---- y, forward ----
+  for (int t = tid; t < W3 * A; t += kThreads) {
+    const int u = t / A, r = t - u * A;
+    C* row = Q + u * QS + B * r;
+    C v[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) v[j] = row[j];
+    fftr::rdft<B>(v, (T)-1);
+#pragma unroll
+    for (int q = 1; q < B; ++q) v[q] = fftr::mul(v[q], tw[r * q]);
+#pragma unroll
+    for (int q = 0; q < B; ++q) row[q] = v[q];
+  }
+  __syncthreads();
+  for (int t = tid; t < W3 * B; t += kThreads) {
+    const int u = t / B, q = t - u * B;
+    C* row = Q + u * QS + q;
+    C v[A];
+#pragma unroll
+    for (int m = 0; m < A; ++m) v[m] = row[B * m];
+    fftr::rdft<A>(v, (T)-1);
+#pragma unroll
+    for (int k = 0; k < A; ++k) row[B * k] = v[k];
+  }
+  __syncthreads();
+  for (int i = tid; i < W3 * W2; i += kThreads) {
+    const int u3 = i / W2, u2 = i - u3 * W2;
+    int y = (a.lo2 + u2) % N;
+    if (y < 0) y += N;
+    slab[i] = Q[u3 * QS + y];
+  }
+}
+
 inline bool choose_split(int N, Split& out) {
   static const int S[] = {1, 2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16};
   double best = 1e30;
