@@ -7,6 +7,8 @@
 // dimension ld.  On GB300 the FP64 pipe (about 1.2 TFLOP/s) bounds these kernels long before
 // shared memory or HBM does; the FP32 instantiation is the CUDA-core form of the mixed path.
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "kss_internal.h"
@@ -21,7 +23,61 @@ template <typename T> struct CT;
 template <> struct CT<double> { using C = double2; };
 template <> struct CT<float> { using C = float2; };
 
-// Inputs of type TI (complex64 or complex128), accumulation and partial sums in T.
+// Complex multiply-accumulate.  FP64 uses the three-multiplication (Gauss) form with the operand
+// sums formed once per staged element: for p = x + iy (from A) and q = u + iv (from B),
+//   k1 = u (x + y),  k2 = x (v - u),  k3 = y (u + v);   Re pq = k1 - k3,  Im pq = k1 + k2,
+// so each complex term costs three fused multiply-adds instead of four (the FP64 pipe bounds
+// these GEMMs; the rounding error stays a small multiple of eps * sum |p||q|).  FP32 keeps the
+// four-multiplication form, whose error bound is tighter, for the mixed path's Gram matrices.
+template <typename T>
+struct Cmac {
+  static constexpr bool G = sizeof(T) == 8;
+  static constexpr int NS = G ? 3 : 2;  // staged values per element and accumulators per output
+  // staged values of p = x + iy (A side) and q = u + iv (B side)
+  static __device__ __forceinline__ void stage_a(T (*dst)[BK][BM], int k, int i, T x, T y) {
+    if constexpr (G) {
+      dst[0][k][i] = x + y;
+      dst[1][k][i] = x;
+      dst[2][k][i] = y;
+    } else {
+      dst[0][k][i] = x;
+      dst[1][k][i] = y;
+    }
+  }
+  static __device__ __forceinline__ void stage_b(T (*dst)[BK][BN], int k, int j, T u, T v) {
+    if constexpr (G) {
+      dst[0][k][j] = u;
+      dst[1][k][j] = v - u;
+      dst[2][k][j] = u + v;
+    } else {
+      dst[0][k][j] = u;
+      dst[1][k][j] = v;
+    }
+  }
+  static __device__ __forceinline__ void mac(T (&acc)[NS], const T (&a)[NS], const T (&b)[NS]) {
+    if constexpr (G) {
+      acc[0] = fma(a[0], b[0], acc[0]);
+      acc[1] = fma(a[1], b[1], acc[1]);
+      acc[2] = fma(a[2], b[2], acc[2]);
+    } else {
+      acc[0] = fma(a[0], b[0], acc[0]);
+      acc[0] = fma(-a[1], b[1], acc[0]);
+      acc[1] = fma(a[0], b[1], acc[1]);
+      acc[1] = fma(a[1], b[0], acc[1]);
+    }
+  }
+  static __device__ __forceinline__ T re(const T (&acc)[NS]) {
+    if constexpr (G) return acc[0] - acc[2];
+    else return acc[0];
+  }
+  static __device__ __forceinline__ T im(const T (&acc)[NS]) {
+    if constexpr (G) return acc[0] + acc[1];
+    else return acc[1];
+  }
+};
+
+// Inputs of type TI (complex64 or complex128), accumulation and partial sums in T.  The next
+// K tile is fetched into registers while the current one is multiplied.
 template <typename T, typename TI = T>
 __device__ __forceinline__ void cn_partial_body(int M, int N, int K, const typename CT<TI>::C* __restrict__ A,
                                                 long long lda, const typename CT<TI>::C* __restrict__ B,
@@ -29,56 +85,56 @@ __device__ __forceinline__ void cn_partial_body(int M, int N, int K, const typen
                                                 int kchunk, int bx, int by, int bz) {
   using C = typename CT<T>::C;
   using CI = typename CT<TI>::C;
-  __shared__ CI As[BK][BM];
-  __shared__ CI Bs[BK][BN];
+  using X = Cmac<T>;
+  constexpr int NS = X::NS;
+  __shared__ T As[NS][BK][BM];
+  __shared__ T Bs[NS][BK][BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = bx * BM, j0 = by * BN;
   const int kbeg = bz * kchunk;
   const int kend = min(K, kbeg + kchunk);
-  T accr[4][4], acci[4][4];
+  T acc[4][4][NS];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) accr[r][c] = acci[r][c] = 0;
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int q = 0; q < NS; ++q) acc[r][c][q] = 0;
   const int li = tid >> 2, lk = (tid & 3) * 2;
-  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+  const int gi = i0 + li, gj = j0 + li;
+  CI ra[2], rb[2];
+  auto fetch = [&](int k0) {
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int k = k0 + lk + e;
-      const int gi = i0 + li, gj = j0 + li;
-      CI a = {0, 0}, b = {0, 0};
-      if (k < kend && gi < M) a = A[gi * lda + k];
-      if (k < kend && gj < N) b = B[gj * ldb + k];
-      As[lk + e][li] = a;
-      Bs[lk + e][li] = b;
+      ra[e] = (k < kend && gi < M) ? A[gi * lda + k] : CI{0, 0};
+      rb[e] = (k < kend && gj < N) ? B[gj * ldb + k] : CI{0, 0};
+    }
+  };
+  if (kbeg < kend) fetch(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      X::stage_a(As, lk + e, li, (T)ra[e].x, -(T)ra[e].y);  // conj(a)
+      X::stage_b(Bs, lk + e, li, (T)rb[e].x, (T)rb[e].y);
     }
     __syncthreads();
+    if (k0 + BK < kend) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T ar_[4], ai_[4], br_[4], bi_[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const CI v = As[kk][ty + 16 * r];
-        ar_[r] = (T)v.x;
-        ai_[r] = (T)v.y;
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const CI v = Bs[kk][tx + 16 * c];
-        br_[c] = (T)v.x;
-        bi_[c] = (T)v.y;
-      }
-      // conj(a) * b as four fused multiply-adds per complex product (no separate add or
-      // multiply: the FP64 pipe issues exactly one instruction per real multiply-add)
+      T av[4][NS], bv[4][NS];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          accr[r][c] = fma(ar_[r], br_[c], accr[r][c]);
-          accr[r][c] = fma(ai_[r], bi_[c], accr[r][c]);
-          acci[r][c] = fma(ar_[r], bi_[c], acci[r][c]);
-          acci[r][c] = fma(-ai_[r], br_[c], acci[r][c]);
-        }
+        for (int q = 0; q < NS; ++q) av[r][q] = As[q][kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int q = 0; q < NS; ++q) bv[c][q] = Bs[q][kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) X::mac(acc[r][c], av[r], bv[c]);
     }
     __syncthreads();
   }
@@ -88,7 +144,7 @@ __device__ __forceinline__ void cn_partial_body(int M, int N, int K, const typen
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
-      if (i < M && j < N) Pz[(size_t)j * M + i] = C{accr[r][c], acci[r][c]};
+      if (i < M && j < N) Pz[(size_t)j * M + i] = C{X::re(acc[r][c]), X::im(acc[r][c])};
     }
 }
 
@@ -139,51 +195,55 @@ __device__ __forceinline__ void nn_body(int M, int N, int K, const typename CT<T
                                         long long ldb, typename CT<T>::C* __restrict__ Cm,
                                         long long ldc, T ar, T ai, T br, T bi, int bx, int by) {
   using C = typename CT<T>::C;
-  __shared__ C As[BK][BM];
-  __shared__ C Bs[BK][BN];
+  using X = Cmac<T>;
+  constexpr int NS = X::NS;
+  __shared__ T As[NS][BK][BM];
+  __shared__ T Bs[NS][BK][BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = bx * BM, j0 = by * BN;
-  T accr[4][4], acci[4][4];
+  T acc[4][4][NS];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) accr[r][c] = acci[r][c] = 0;
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int q = 0; q < NS; ++q) acc[r][c][q] = 0;
   const int ai_ = tid & 63, ak = tid >> 6;           // A tile: i fastest
   const int bj = tid >> 2, bk = (tid & 3) * 2;       // B tile: k fastest
+  const int gi = i0 + ai_, gj = j0 + bj;
+  C ra[2], rb[2];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int ka = k0 + ak + 4 * e, kb = k0 + bk + e;
+      ra[e] = (ka < K && gi < M) ? A[(size_t)ka * lda + gi] : C{0, 0};
+      rb[e] = (kb < K && gj < N) ? B[(size_t)gj * ldb + kb] : C{0, 0};
+    }
+  };
+  if (K > 0) fetch(0);
   for (int k0 = 0; k0 < K; k0 += BK) {
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      const int k = k0 + ak + 4 * e;
-      const int gi = i0 + ai_;
-      C a = {0, 0};
-      if (k < K && gi < M) a = A[(size_t)k * lda + gi];
-      As[ak + 4 * e][ai_] = a;
-    }
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int k = k0 + bk + e;
-      const int gj = j0 + bj;
-      C b = {0, 0};
-      if (k < K && gj < N) b = B[(size_t)gj * ldb + k];
-      Bs[bk + e][bj] = b;
+      X::stage_a(As, ak + 4 * e, ai_, ra[e].x, ra[e].y);
+      X::stage_b(Bs, bk + e, bj, rb[e].x, rb[e].y);
     }
     __syncthreads();
+    if (k0 + BK < K) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      C a[4], b[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][tx + 16 * r];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][ty + 16 * c];
+      T av[4][NS], bv[4][NS];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          accr[r][c] = fma(a[r].x, b[c].x, accr[r][c]);
-          accr[r][c] = fma(-a[r].y, b[c].y, accr[r][c]);
-          acci[r][c] = fma(a[r].x, b[c].y, acci[r][c]);
-          acci[r][c] = fma(a[r].y, b[c].x, acci[r][c]);
-        }
+        for (int q = 0; q < NS; ++q) av[r][q] = As[q][kk][tx + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int q = 0; q < NS; ++q) bv[c][q] = Bs[q][kk][ty + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) X::mac(acc[r][c], av[r], bv[c]);
     }
     __syncthreads();
   }
@@ -194,9 +254,10 @@ __device__ __forceinline__ void nn_body(int M, int N, int K, const typename CT<T
       const int i = i0 + tx + 16 * r, j = j0 + ty + 16 * c;
       if (i < M && j < N) {
         C* dst = Cm + (size_t)j * ldc + i;
+        const T sr = X::re(acc[r][c]), si = X::im(acc[r][c]);
         C out;
-        out.x = ar * accr[r][c] - ai * acci[r][c];
-        out.y = ar * acci[r][c] + ai * accr[r][c];
+        out.x = ar * sr - ai * si;
+        out.y = ar * si + ai * sr;
         if (br != 0 || bi != 0) {
           const C o = *dst;
           out.x += br * o.x - bi * o.y;
@@ -296,6 +357,53 @@ int sm_count(kss_ctx ctx) {
   return n;
 }
 
+// Resident CTAs per SM of a 256-thread kernel without dynamic shared memory.
+template <class F>
+int resident_ctas(F f) {
+  static std::mutex mu;
+  static std::map<const void*, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find((const void*)f);
+  if (it != cache.end()) return it->second;
+  int b = 0;
+  KSS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, 256, 0));
+  b = std::max(b, 1);
+  cache[(const void*)f] = b;
+  return b;
+}
+
+// Split count s of a split-K product over `tiles` output tiles: the smallest s <= smax that
+// minimises the wave-quantised time ceil(tiles * s / cap) / s (cap = resident CTAs on the GPU),
+// with at least 64 K values per split.
+int pick_splits(int tiles, int K, int cap, int smax) {
+  smax = std::max(1, std::min(smax, (K + 63) / 64));
+  int best = 1;
+  double bt = 1e300;
+  for (int s = 1; s <= smax; ++s) {
+    const double t = (double)((tiles * (long long)s + cap - 1) / cap) / s;
+    if (t < bt * (1.0 - 1e-9)) {
+      bt = t;
+      best = s;
+    }
+  }
+  return best;
+}
+
+// Splits, K chunk (a multiple of BK) and partial-sum count for a split-K launch.
+struct SplitK {
+  int splits, kchunk;
+};
+template <class F>
+SplitK plan_splitk(kss_ctx ctx, F kernel, int tiles, int K, size_t partial_bytes_each, size_t max_bytes) {
+  const int cap = sm_count(ctx) * resident_ctas(kernel);
+  const int smax = (int)std::max<size_t>(1, std::min<size_t>(128, max_bytes / partial_bytes_each));
+  int splits = pick_splits(tiles, K, cap, smax);
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  splits = (K + kchunk - 1) / kchunk;
+  return {splits, kchunk};
+}
+
 int tag_id(const char* kernel, bool f64, const char* tag) {
   std::string n = std::string(kernel) + (f64 ? "<f64>:" : "<f32>:") + (tag ? tag : "");
   return prof_register(n.c_str());
@@ -306,12 +414,8 @@ void run_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void
             void* Cm, int ldc, double ar, double ai, double br, double bi, const char* tag) {
   using C = typename CT<T>::C;
   const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
-  const int tiles = tm * tn;
-  const int target = 4 * sm_count(ctx);
-  int splits = std::max(1, std::min((target + tiles - 1) / tiles, (K + 63) / 64));
-  int kchunk = (K + splits - 1) / splits;
-  kchunk = (kchunk + BK - 1) / BK * BK;
-  splits = (K + kchunk - 1) / kchunk;
+  const SplitK sk = plan_splitk(ctx, gemm_cn_partial<T>, tm * tn, K, (size_t)M * N * sizeof(C), 512ull << 20);
+  const int splits = sk.splits, kchunk = sk.kchunk;
   ctx->ws_gemm.ensure((size_t)splits * M * N * sizeof(C));
   const bool f64 = sizeof(T) == 8;
   {
@@ -362,12 +466,9 @@ void gemm_cn_c64_acc64(kss_ctx ctx, int M, int N, int K, const void* A, int lda,
   if (M <= 0 || N <= 0) return;
   KSS_REQUIRE(K > 0 && lda >= K && ldb >= K && ldc >= M, "gemm_cn_c64_acc64: bad leading dimension");
   const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
-  const int tiles = tm * tn;
-  const int target = 4 * sm_count(ctx);
-  int splits = std::max(1, std::min((target + tiles - 1) / tiles, (K + 63) / 64));
-  int kchunk = (K + splits - 1) / splits;
-  kchunk = (kchunk + BK - 1) / BK * BK;
-  splits = (K + kchunk - 1) / kchunk;
+  const SplitK sk = plan_splitk(ctx, gemm_cn_partial_f32in, tm * tn, K, (size_t)M * N * sizeof(double2),
+                                512ull << 20);
+  const int splits = sk.splits, kchunk = sk.kchunk;
   ctx->ws_gemm.ensure((size_t)splits * M * N * sizeof(double2));
   {
     ProfScope ps(ctx, tag_id("gemm_cn_partial_c64in", true, tag));
@@ -394,12 +495,9 @@ bool gemm_cn_ws(kss_ctx ctx, bool fp64, int M, int N, int K, const void* A, int 
   const int maxs = (int)std::min<size_t>(partial_bytes / per, 1 << 20);
   if (maxs < 1) return false;
   const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
-  const int tiles = tm * tn;
-  const int target = 4 * sm_count(ctx);
-  int splits = std::max(1, std::min({(target + tiles - 1) / tiles, (K + 63) / 64, maxs}));
-  int kchunk = (K + splits - 1) / splits;
-  kchunk = (kchunk + BK - 1) / BK * BK;
-  splits = (K + kchunk - 1) / kchunk;
+  const SplitK sk = fp64 ? plan_splitk(ctx, gemm_cn_partial<double>, tm * tn, K, per, (size_t)maxs * per)
+                         : plan_splitk(ctx, gemm_cn_partial<float>, tm * tn, K, per, (size_t)maxs * per);
+  const int splits = sk.splits, kchunk = sk.kchunk;
   const long long mn = (long long)M * N;
   if (fp64) {
     gemm_cn_partial<double><<<dim3(tm, tn, splits), 256, 0, ctx->stream>>>(
