@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kThreads) group_pass(const LocalItem<T>* __res
 
 // Pass B of a class with a common compile-time y/z split, in the CTA-wide form.
 template <typename T, int A, int B>
-__global__ void __launch_bounds__(kThreads) group_passw(const LocalItem<T>* __restrict__ items, int n,
+__global__ void __launch_bounds__(kWideThreads) group_passw(const LocalItem<T>* __restrict__ items, int n,
                                                         int) {
   __shared__ LocalArgs<T> sa;
   __shared__ int s_local, s_idle;
@@ -518,7 +518,7 @@ void BatchEngine::launch_filter_t() {
     for (const PassClass& pc : classes) {
       const LocalItem<T>* it = dl + (size_t)j * n + pc.first;
       if (pc.wide_b)
-        group_kernel_w<T>(pc.code23)<<<pc.blocks_b, kThreads, pc.smem_bw, ctx->stream>>>(it, pc.count, scr_warp);
+        group_kernel_w<T>(pc.code23)<<<pc.blocks_b, kWideThreads, pc.smem_bw, ctx->stream>>>(it, pc.count, scr_warp);
       else
         group_kernel<T, 1>(pc.code23)<<<pc.blocks_b, kThreads, pc.smem_b, ctx->stream>>>(it, pc.count, scr_warp);
     }

@@ -462,6 +462,8 @@ __device__ __forceinline__ void pass_c_body(const LocalArgs<T>& a, const RegPlan
 // a column holds (to read V).  The z columns of the whole plane live in a second buffer Z, so the
 // inverse z transform reads the sphere window rows of Q (zeros elsewhere) and the forward one
 // writes only the window rows back.  Requires N2 == N3 == A * B.
+constexpr int kWideThreads = 384;  // 12 warps: 96-point stages split into whole rounds of tasks
+
 template <typename T, int A, int B>
 struct WideB {
   static constexpr int N = A * B;
@@ -472,7 +474,7 @@ struct WideB {
   }
 };
 
-template <typename T, int A, int B>
+template <typename T, int A, int B, int NT = kWideThreads>
 __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int nl) {
   using C = typename CT<T>::C;
   using G = WideB<T, A, B>;
@@ -484,16 +486,16 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   int* zmap = reinterpret_cast<int*>(Z + N * ZS);
   const int tid = threadIdx.x;
   const int W3 = a.W3, W2 = a.W2;
-  copy_table(tw, a.tw2, N);
-  for (int z = tid; z < N; z += kThreads) {
+  for (int i = tid; i < N; i += NT) tw[i] = a.tw2[i];
+  for (int z = tid; z < N; z += NT) {
     int u = (z - a.lo3) % N;
     if (u < 0) u += N;
     zmap[z] = u < W3 ? u : -1;
   }
-  for (int i = tid; i < W3 * QS; i += kThreads) Q[i] = C{0, 0};
+  for (int i = tid; i < W3 * QS; i += NT) Q[i] = C{0, 0};
   __syncthreads();
   C* slab = a.work + ((size_t)nl * a.N1 + x) * W3 * W2;
-  for (int i = tid; i < W3 * W2; i += kThreads) {
+  for (int i = tid; i < W3 * W2; i += NT) {
     const int u3 = i / W2, u2 = i - u3 * W2;
     int y = (a.lo2 + u2) % N;
     if (y < 0) y += N;
@@ -501,7 +503,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   }
   __syncthreads();
   // ---- y, inverse ----
-  for (int t = tid; t < W3 * B; t += kThreads) {
+  for (int t = tid; t < W3 * B; t += NT) {
     const int u = t / B, r = t - u * B;
     C* row = Q + u * QS + r;
     C v[A];
@@ -518,7 +520,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
     for (int k = 0; k < A; ++k) row[B * k] = v[k];
   }
   __syncthreads();
-  for (int t = tid; t < W3 * A; t += kThreads) {
+  for (int t = tid; t < W3 * A; t += NT) {
     const int u = t / A, k = t - u * A;
     C* row = Q + u * QS + B * k;
     C v[B];
@@ -530,7 +532,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   }
   __syncthreads();
   // ---- z, inverse stage 1 (column p of the plane; only window rows are nonzero) ----
-  for (int t = tid; t < N * B; t += kThreads) {
+  for (int t = tid; t < N * B; t += NT) {
     const int r = t / N, p = t - r * N;
     C v[A];
 #pragma unroll
@@ -552,7 +554,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   __syncthreads();
   // ---- z, inverse stage 2, x V, forward stage 1 ----
   const T* vx = a.Vx + (size_t)x * N * N;
-  for (int t = tid; t < N * A; t += kThreads) {
+  for (int t = tid; t < N * A; t += NT) {
     const int p = t / A, k = t - p * A;
     const int py = p / B;
     const int y = py + A * (p - py * B);  // position p = k2 + B k of a y row holds y = k + A k2
@@ -576,7 +578,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   }
   __syncthreads();
   // ---- z, forward stage 2: keep the window rows ----
-  for (int t = tid; t < N * B; t += kThreads) {
+  for (int t = tid; t < N * B; t += NT) {
     const int q = t / N, p = t - q * N;
     const C* col = Z + p * ZS + q;
     C v[A];
@@ -591,7 +593,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   }
   __syncthreads();
   // ---- y, forward ----
-  for (int t = tid; t < W3 * A; t += kThreads) {
+  for (int t = tid; t < W3 * A; t += NT) {
     const int u = t / A, r = t - u * A;
     C* row = Q + u * QS + B * r;
     C v[B];
@@ -604,7 +606,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
     for (int q = 0; q < B; ++q) row[q] = v[q];
   }
   __syncthreads();
-  for (int t = tid; t < W3 * B; t += kThreads) {
+  for (int t = tid; t < W3 * B; t += NT) {
     const int u = t / B, q = t - u * B;
     C* row = Q + u * QS + q;
     C v[A];
@@ -615,7 +617,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
     for (int k = 0; k < A; ++k) row[B * k] = v[k];
   }
   __syncthreads();
-  for (int i = tid; i < W3 * W2; i += kThreads) {
+  for (int i = tid; i < W3 * W2; i += NT) {
     const int u3 = i / W2, u2 = i - u3 * W2;
     int y = (a.lo2 + u2) % N;
     if (y < 0) y += N;

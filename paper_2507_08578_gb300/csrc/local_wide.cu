@@ -11,7 +11,7 @@ namespace {
 using namespace lk;
 
 template <typename T, int A, int B>
-__global__ void __launch_bounds__(kThreads) pass_bw(LocalArgs<T> a) {
+__global__ void __launch_bounds__(kWideThreads) pass_bw(LocalArgs<T> a) {
   pass_bw_body<T, A, B>(a, blockIdx.x, blockIdx.y);
 }
 
@@ -20,13 +20,8 @@ bool launch_one(const LocalArgs<T>& a, int nbands, cudaStream_t st, bool dry) {
   const size_t sm = WideB<T, A, B>::smem(a.W3);
   if (sm > kWideSmemMax) return false;
   if (dry) return true;
-  static bool attr_done = false;  // one attribute set per instance (the size is the maximum)
-  if (!attr_done) {
-    KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_bw<T, A, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)kWideSmemMax));
-    attr_done = true;
-  }
-  pass_bw<T, A, B><<<dim3(a.N1, nbands), kThreads, sm, st>>>(a);
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_bw<T, A, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  pass_bw<T, A, B><<<dim3(a.N1, nbands), kWideThreads, sm, st>>>(a);
   return true;
 }
 
