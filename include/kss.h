@@ -343,6 +343,46 @@ kss_status kss_profile_count(kss_ctx ctx, int* nkernels, long long* launches);
 kss_status kss_profile_entry(kss_ctx ctx, int i, const char** name, long long* launches,
                              double* total_ms);
 
+/* ------------------------------------------------------------------------------------------
+ * Autotuner of the FFT radix schedule (the batched pencil FFTs of §5.1; the schedule itself is
+ * this library's choice, the paper fixes none)
+ *
+ * The y/z transforms of one x-plane (the middle pass of the local-potential path) have several
+ * kernel schedules for a box length N: a split N = A * B into two register codelets
+ * (A, B <= 16, e.g. 96 = 8 x 12, 12 x 8, 6 x 16, 16 x 6), spread over 256 or 384 threads per
+ * CTA, or a per-warp form.  With autotuning on, the first use of a (device, precision, box,
+ * sphere window) configuration times every candidate on a scratch slab and keeps the fastest
+ * for the rest of the process.  The candidates compute the same transform and differ only in
+ * rounding order (results agree to a few ulps).  Tuning never runs inside a CUDA stream capture
+ * or in kss_apply_H_noalloc; those use the table entry if one exists, else the built-in choice.
+ * ------------------------------------------------------------------------------------------ */
+
+/* mode 1 (default): tune at first use; mode 0: built-in choice for configurations not yet in
+ * the table.  KSS_EINVAL for another mode. */
+kss_status kss_autotune_set(kss_ctx ctx, int mode);
+
+typedef struct {
+  int device, precision;  /* precision: KSS_PREC_FP64 or KSS_PREC_MIXED */
+  int N1, N, W3, W2;      /* box N1 x N x N and sphere window W2 x W3 of the configuration */
+  int A, B, threads;      /* chosen split N = A * B; threads per CTA (0: per-warp form) */
+  double ms;              /* time of one tuning launch of the chosen schedule */
+  int ncand;              /* candidates timed */
+} kss_tune_entry;
+
+/* Number of table entries (process-wide, all contexts). */
+kss_status kss_autotune_count(int* n);
+/* Entry i (insertion order); KSS_EINVAL past the end or for a NULL out. */
+kss_status kss_autotune_get(int i, kss_tune_entry* out);
+/* Insert or replace the entry for (device, precision, N1, N, W3 rounded up to a multiple of 8):
+ * pins a schedule (e.g. one read back from an earlier run, for run-to-run identical rounding).
+ * A, B, threads as in kss_tune_entry (ms, ncand, W2 ignored).  A pinned schedule without a
+ * kernel instance, or whose shared memory does not fit a configuration's window, falls back to
+ * the per-warp form at use.  KSS_EINVAL for inconsistent fields (A * B != N, threads not in
+ * {0, 256, 384}, W3 outside [1, N], unknown precision). */
+kss_status kss_autotune_put(const kss_tune_entry* e);
+/* Empty the table (later configurations are tuned again). */
+kss_status kss_autotune_clear(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,9 +1,9 @@
 // Batched Chebyshev-filtered solves: many (system, k-point) units of uneven sizes advanced in
 // lockstep, the local passes and the projector products of all units issued as single grouped
 // launches, and the whole filter of one iteration (degree m applications plus H on the filtered
-// block) captured once into a CUDA graph and replayed every iteration.  The paper's strategy of
-// "batch processing" many FFTs and products per call (§5.1), extended from bands to independent
-// problems; k-points and systems share nothing (§5.3 notes the trivial parallelism in k).
+// block) captured once into a CUDA graph and replayed every iteration.  The paper batches many
+// FFTs and products per call over bands (§5.1); here the batch extends to independent problems
+// (k-points and systems share nothing, §5.3 notes the trivial parallelism in k).
 //
 // Per iteration and unit the filter reads its coefficients and buffer roles from device tables
 // that the host rewrites before each replay; Rayleigh-Ritz (FP64 eigensolve) is then issued for
@@ -12,100 +12,27 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include "batch.h"
+#include "batch_kernels.cuh"
 #include "local_kernels.cuh"
+#include "tune.h"
 
 namespace kss {
 
 namespace {
 
 using namespace lk;
+using namespace bk;
 using fftr::Split;
 
-template <typename T>
-struct LocalItem {
-  LocalArgs<T> a;
-  RegPlan rp;
-  int blk_ac;  // first block of this item in the pass A / pass C launches
-  int blk_b;   // first block in the pass B launch
-  int idle;    // unit past its own filter degree: its blocks return at once
-};
-
-template <typename T>
-__device__ __forceinline__ int find_local(const LocalItem<T>* it, int n, int b, bool pb) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if ((pb ? it[mid].blk_b : it[mid].blk_ac) <= b) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-template <typename T, int PASS, class Pol>
-__global__ void __launch_bounds__(kThreads) group_pass(const LocalItem<T>* __restrict__ items, int n,
-                                                       int scr_warp) {
-  __shared__ LocalArgs<T> sa;
-  __shared__ RegPlan srp;
-  __shared__ int s_local, s_idle;
-  if (threadIdx.x == 0) {
-    const int i = find_local(items, n, blockIdx.x, PASS == 1);
-    s_idle = items[i].idle;
-    if (!s_idle) {
-      sa = items[i].a;
-      srp = items[i].rp;
-    }
-    s_local = blockIdx.x - (PASS == 1 ? items[i].blk_b : items[i].blk_ac);
-  }
-  __syncthreads();
-  if (s_idle) return;
-  const int local = s_local;
-  if (PASS == 0) pass_a_body<T, Pol>(sa, srp, scr_warp, local % sa.W3, local / sa.W3);
-  else if (PASS == 1) pass_b_body<T, Pol>(sa, srp, scr_warp, local % sa.N1, local / sa.N1);
-  else pass_c_body<T, Pol>(sa, srp, scr_warp, local % sa.W3, local / sa.W3);
-}
-
-// Pass B of a class with a common compile-time y/z split, in the CTA-wide form.
-template <typename T, int A, int B>
-__global__ void __launch_bounds__(kWideThreads) group_passw(const LocalItem<T>* __restrict__ items, int n,
-                                                        int) {
-  __shared__ LocalArgs<T> sa;
-  __shared__ int s_local, s_idle;
-  if (threadIdx.x == 0) {
-    const int i = find_local(items, n, blockIdx.x, true);
-    s_idle = items[i].idle;
-    if (!s_idle) sa = items[i].a;
-    s_local = blockIdx.x - items[i].blk_b;
-  }
-  __syncthreads();
-  if (s_idle) return;
-  const int local = s_local;
-  pass_bw_body<T, A, B>(sa, local % sa.N1, local / sa.N1);
-}
-
-template <typename T>
-using GroupKernel = void (*)(const LocalItem<T>*, int, int);
-
-template <typename T>
-GroupKernel<T> group_kernel_w(int code) {
-  switch (code) {
-#define KSS_CASE(x, y) \
-  case x * 32 + y:     \
-    return group_passw<T, x, y>;
-    KSS_SPLITS(KSS_CASE)
-#undef KSS_CASE
-    default:
-      return nullptr;
-  }
-}
-
-size_t wide_b_smem(int code, int W3, size_t es) {
-  const int N = (code / 32) * (code % 32);
+// Shared memory of the CTA-wide pass B for box length N and sphere window W3.
+size_t wide_b_smem(int N, int W3, size_t es) {
   return es * ((size_t)N + (size_t)W3 * (N + 1) + (size_t)N * (N + 1)) + sizeof(int) * N;
 }
 
@@ -307,14 +234,27 @@ void BatchEngine::prepare_t() {
     blocks_ac += kd.W[2] * s->nb;
     blocks_b += sy->N[0] * s->nb;
   }
-  // Units grouped by kernel instance (compile-time split codes in single precision).
+  // Units grouped by kernel instance: the x split code of passes A/C and the pass-B schedule the
+  // autotuner picks for the unit's box and window (CTA-wide split and threads, or the per-warp
+  // form with its split code).
   std::vector<std::pair<long long, int>> key(n);
+  std::vector<PassBSched> bs(n);
   for (int u = 0; u < n; ++u) {
     const RegPlanHost& p = plans[u];
     int c1 = -1, c23 = -1;
     c1 = has_ct(p.s1.A * 32 + p.s1.B) ? p.s1.A * 32 + p.s1.B : -1;
     if (p.s2.A == p.s3.A && p.s2.B == p.s3.B && has_ct(p.s2.A * 32 + p.s2.B)) c23 = p.s2.A * 32 + p.s2.B;
-    key[u] = {(long long)(c1 + 1) * 4096 + (c23 + 1), u};
+    LocalArgs<T> au;
+    fill_args<T>(units[u]->sys, units[u]->ik, au);
+    RegPlan rp;
+    std::memcpy(&rp, &p, sizeof(RegPlan));
+    bs[u] = pass_b_schedule<T>(ctx, au, rp.s2, true);
+    if (bs[u].threads && (!group_kernel_w<T>(bs[u].A, bs[u].B, bs[u].threads) ||
+                          wide_b_smem(au.N2, au.W3, es) > 227 * 1024 || au.N2 != au.N3))
+      bs[u].threads = 0;
+    const long long k2 = bs[u].threads ? 10001 + (long long)(bs[u].A * 32 + bs[u].B) * 2 + (bs[u].threads == 384)
+                                       : (long long)(c23 + 1);
+    key[u] = {(long long)(c1 + 1) * 100000 + k2, u};
   }
   std::stable_sort(key.begin(), key.end());
   pos.assign(n, 0);
@@ -322,9 +262,12 @@ void BatchEngine::prepare_t() {
   for (int i = 0; i < n; ++i) {
     const int u = key[i].second;
     pos[u] = i;
-    const int c1 = (int)(key[i].first / 4096) - 1, c23 = (int)(key[i].first % 4096) - 1;
-    if (classes.empty() || classes.back().code1 != c1 || classes.back().code23 != c23)
-      classes.push_back(PassClass{c1, c23, i, 0, 0, 0, 0, 0, 0, false});
+    const RegPlanHost& p = plans[u];
+    const int c1 = (int)(key[i].first / 100000) - 1;
+    const int c23 = (p.s2.A == p.s3.A && p.s2.B == p.s3.B && has_ct(p.s2.A * 32 + p.s2.B)) ? p.s2.A * 32 + p.s2.B : -1;
+    const PassBSched& b = bs[u];
+    if (classes.empty() || i == 0 || key[i].first != key[i - 1].first)
+      classes.push_back(PassClass{c1, b.threads ? -1 : c23, i, 0, 0, 0, 0, 0, 0, b.A, b.B, b.threads});
     PassClass& pc = classes.back();
     kss_sys sy = units[u]->sys;
     const KData& kd = sy->k[units[u]->ik];
@@ -332,13 +275,14 @@ void BatchEngine::prepare_t() {
     pc.blocks_ac += kd.W[2] * units[u]->nb;
     pc.blocks_b += sy->N[0] * units[u]->nb;
     pc.smem_ac = std::max(pc.smem_ac, es * ((size_t)sy->N[0] + (size_t)kd.W[1] * (sy->N[0] + 1) + (size_t)kWarps * scr_warp));
-    pc.smem_b = std::max(pc.smem_b, es * ((size_t)sy->N[1] + sy->N[2] + (size_t)kd.W[2] * (sy->N[1] + 1) +
-                                          (size_t)kWarps * scr_warp) + sizeof(int) * sy->N[2]);
-    if (c23 >= 0) pc.smem_bw = std::max(pc.smem_bw, wide_b_smem(c23, kd.W[2], es));
+    if (pc.wnt)
+      pc.smem_bw = std::max(pc.smem_bw, wide_b_smem(sy->N[1], kd.W[2], es));
+    else
+      pc.smem_b = std::max(pc.smem_b, es * ((size_t)sy->N[1] + sy->N[2] + (size_t)kd.W[2] * (sy->N[1] + 1) +
+                                            (size_t)kWarps * scr_warp) + sizeof(int) * sy->N[2]);
     smem_ac = std::max(smem_ac, pc.smem_ac);
-    smem_b = std::max(smem_b, pc.smem_b);
+    smem_b = std::max(smem_b, std::max(pc.smem_b, pc.smem_bw));
   }
-  for (PassClass& pc : classes) pc.wide_b = pc.code23 >= 0 && pc.smem_bw <= 227 * 1024;
   if (smem_ac > 227 * 1024 || smem_b > 227 * 1024)
     fail(KSS_ENOTSUP, "a batched unit's FFT tiles do not fit in shared memory");
   ws.ensure(off);
@@ -350,14 +294,21 @@ void BatchEngine::prepare_t() {
   d_local.ensure(h_local.size());
   d_cn.ensure(h_cn.size() * sizeof(GemmItem));
   d_nn.ensure(h_nn.size() * sizeof(GemmItem));
+  // Several classes can share a kernel instance (same x split, different pass-B schedule): each
+  // instance's dynamic shared-memory limit is the largest any of its classes launches with.
+  std::map<const void*, size_t> need;
+  auto want = [&](GroupKernel<T> k, size_t bytes) {
+    size_t& v = need[(const void*)k];
+    v = std::max(v, bytes);
+  };
   for (const PassClass& pc : classes) {
-    KSS_CHECK_CUDA(cudaFuncSetAttribute(group_kernel<T, 0>(pc.code1), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_ac));
-    if (pc.wide_b)
-      KSS_CHECK_CUDA(cudaFuncSetAttribute(group_kernel_w<T>(pc.code23), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_bw));
-    else
-      KSS_CHECK_CUDA(cudaFuncSetAttribute(group_kernel<T, 1>(pc.code23), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_b));
-    KSS_CHECK_CUDA(cudaFuncSetAttribute(group_kernel<T, 2>(pc.code1), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc.smem_ac));
+    want(group_kernel<T, 0>(pc.code1), pc.smem_ac);
+    want(group_kernel<T, 2>(pc.code1), pc.smem_ac);
+    if (pc.wnt) want(group_kernel_w<T>(pc.wa, pc.wb, pc.wnt), pc.smem_bw);
+    else want(group_kernel<T, 1>(pc.code23), pc.smem_b);
   }
+  for (const auto& kv : need)
+    KSS_CHECK_CUDA(cudaFuncSetAttribute(kv.first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kv.second));
   prepared = true;
 }
 
@@ -517,8 +468,8 @@ void BatchEngine::launch_filter_t() {
     }
     for (const PassClass& pc : classes) {
       const LocalItem<T>* it = dl + (size_t)j * n + pc.first;
-      if (pc.wide_b)
-        group_kernel_w<T>(pc.code23)<<<pc.blocks_b, kWideThreads, pc.smem_bw, ctx->stream>>>(it, pc.count, scr_warp);
+      if (pc.wnt)
+        group_kernel_w<T>(pc.wa, pc.wb, pc.wnt)<<<pc.blocks_b, pc.wnt, pc.smem_bw, ctx->stream>>>(it, pc.count, scr_warp);
       else
         group_kernel<T, 1>(pc.code23)<<<pc.blocks_b, kThreads, pc.smem_b, ctx->stream>>>(it, pc.count, scr_warp);
     }

@@ -20,7 +20,8 @@ struct PassClass {  // units whose FFT passes share one kernel instance
   int blocks_ac, blocks_b;
   size_t smem_ac, smem_b;
   size_t smem_bw;  // shared memory of the CTA-wide pass B form
-  bool wide_b;     // pass B runs in the CTA-wide form
+  int wa, wb, wnt; // pass B schedule (autotuner): CTA-wide split wa x wb at wnt threads; wnt == 0:
+                   // the per-warp form (split code code23)
 };
 struct Roles {
   int y, hy, free2;  // buffers holding Y, H Y, and the free one that receives the rotated X

@@ -109,6 +109,8 @@ struct kss_ctx_s {
   kss::Prof prof;
   int nsm = 0;
   void* server = nullptr;          // request server (server.cu), NULL when not running
+  int autotune = 1;                // 1: time FFT schedule candidates at first use (tune.cu)
+  kss::DevBuf ws_tune;             // scratch slab of the autotuner
 };
 
 struct kss_sys_s {

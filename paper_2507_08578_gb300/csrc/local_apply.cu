@@ -25,6 +25,7 @@
 
 #include "local_kernels.cuh"
 #include "local_wide.h"
+#include "tune.h"
 
 namespace kss {
 
@@ -441,10 +442,13 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
                       sizeof(int) * a.N3;
     if (ra <= smax && rb <= smax) {
       const PassKernels<T> kk = pick_kernels<T>(rp);
-      const bool wide = wide_pass_b<T>(a, rp.s2.A, rp.s2.B, 0, ctx->stream, true);
       KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
       KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb));
       KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
+      auto warp_b = [&](const LocalArgs<T>& t, int m) {
+        kk.b<<<dim3(t.N1, m), kThreads, rb, ctx->stream>>>(t, rp, scr_warp);
+      };
+      const PassBSched sb = pass_b_schedule<T>(ctx, a, rp.s2, true);
       static const int ida = prof_register(f64 ? "local_pass_a<f64>" : "local_pass_a<f32>");
       static const int idb = prof_register(f64 ? "local_pass_b<f64>" : "local_pass_b<f32>");
       static const int idc = prof_register(f64 ? "local_pass_c<f64>" : "local_pass_c<f32>");
@@ -457,8 +461,7 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
         }
         {
           ProfScope ps(ctx, idb);
-          if (!wide) kk.b<<<dim3(a.N1, m), kThreads, rb, ctx->stream>>>(a, rp, scr_warp);
-          else wide_pass_b<T>(a, rp.s2.A, rp.s2.B, m, ctx->stream, false);
+          if (!(sb.threads && wide_pass_b<T>(a, sb.A, sb.B, sb.threads, m, ctx->stream, false))) warp_b(a, m);
         }
         {
           ProfScope ps(ctx, idc);
@@ -492,7 +495,8 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
 }
 
 // The local passes on a caller-provided slab workspace of nc bands (no allocation, no profiling
-// events).  Same kernels and launch shapes as run_local.
+// events).  Same kernels as run_local; the pass-B schedule comes from the autotuner's table or
+// the built-in choice (no tuning, which would allocate a scratch slab).
 template <typename T>
 void run_local_ws(kss_sys s, int ik, int nb, const void* psi, void* out, int ld, void* work, int nc) {
   using C = typename CT<T>::C;
@@ -542,16 +546,18 @@ void run_local_ws(kss_sys s, int ik, int nb, const void* psi, void* out, int ld,
                       sizeof(int) * a.N3;
     if (ra <= smax && rb <= smax) {
       const PassKernels<T> kk = pick_kernels<T>(rp);
-      const bool wide = wide_pass_b<T>(a, rp.s2.A, rp.s2.B, 0, ctx->stream, true);
       KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
       KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb));
       KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
+      auto warp_b = [&](const LocalArgs<T>& t, int m) {
+        kk.b<<<dim3(t.N1, m), kThreads, rb, ctx->stream>>>(t, rp, scr_warp);
+      };
+      const PassBSched sb = pass_b_schedule<T>(ctx, a, rp.s2, false);  // no tuning here
       for (int n0 = 0; n0 < nb; n0 += nc) {
         const int m = std::min(nc, nb - n0);
         a.n0 = n0;
         kk.a<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
-        if (!wide) kk.b<<<dim3(a.N1, m), kThreads, rb, ctx->stream>>>(a, rp, scr_warp);
-        else wide_pass_b<T>(a, rp.s2.A, rp.s2.B, m, ctx->stream, false);
+        if (!(sb.threads && wide_pass_b<T>(a, sb.A, sb.B, sb.threads, m, ctx->stream, false))) warp_b(a, m);
         kk.c<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
       }
       KSS_CHECK_CUDA(cudaGetLastError());
@@ -575,6 +581,22 @@ void run_local_ws(kss_sys s, int ik, int nb, const void* psi, void* out, int ld,
 }
 
 }  // namespace
+
+template <typename T>
+void warp_pass_b(kss_ctx ctx, const LocalArgs<T>& a, int nbands) {
+  RegPlan rp;
+  if (!(choose_split(a.N1, rp.s1) && choose_split(a.N2, rp.s2) && choose_split(a.N3, rp.s3)))
+    fail(KSS_ENOTSUP, "FFT length without a two-codelet split");
+  const int scr_warp = std::max(rp.s1.PP * rp.s1.scr, std::max(rp.s2.PP * rp.s2.scr, rp.s3.PP * rp.s3.scr));
+  const size_t es = sizeof(typename CT<T>::C);
+  const size_t rb = es * ((size_t)a.N2 + a.N3 + (size_t)a.W3 * a.N2p + (size_t)kWarps * scr_warp) +
+                    sizeof(int) * a.N3;
+  const PassKernels<T> kk = pick_kernels<T>(rp);
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rb));
+  kk.b<<<dim3(a.N1, nbands), kThreads, rb, ctx->stream>>>(a, rp, scr_warp);
+}
+template void warp_pass_b<double>(kss_ctx, const LocalArgs<double>&, int);
+template void warp_pass_b<float>(kss_ctx, const LocalArgs<float>&, int);
 
 size_t local_slab_bytes_per_band(kss_sys s, int ik, kss_precision prec) {
   return slab_elems(s, ik) * (prec == KSS_PREC_FP64 ? 16 : 8);

@@ -281,6 +281,15 @@ struct CtPol {
 #define KSS_SPLITS(X) X(3, 5) X(4, 4) X(3, 6) X(4, 5) X(4, 6) X(5, 5) X(3, 9) X(5, 6) X(6, 6) \
                       X(5, 8) X(5, 9) X(6, 8) X(5, 10) X(6, 9) X(6, 10) X(8, 12)
 
+// Splits (A, B) with CTA-wide pass B instances: both orientations of the FFT lengths the workloads
+// use (24 .. 60 and 96) plus a second factorisation of 96, so the autotuner can choose the radix
+// schedule; one orientation for the small test lengths.
+#define KSS_WIDE_SPLITS(X)                                                                        \
+  X(3, 5) X(4, 4) X(3, 6) X(4, 5) X(5, 5) X(3, 9)                                                 \
+  X(4, 6) X(6, 4) X(3, 8) X(8, 3) X(5, 6) X(6, 5) X(3, 10) X(10, 3) X(6, 6) X(4, 9) X(9, 4)       \
+  X(5, 8) X(8, 5) X(4, 10) X(10, 4) X(5, 9) X(9, 5) X(6, 8) X(8, 6) X(5, 10) X(10, 5) X(6, 9)     \
+  X(9, 6) X(6, 10) X(10, 6) X(5, 12) X(12, 5) X(8, 12) X(12, 8) X(6, 16) X(16, 6)
+
 template <typename T, class Pol = RtPol>
 __device__ __forceinline__ void pass_a_body(const LocalArgs<T>& a, const RegPlan& rp, int scr_warp,
                                             int u3, int nl) {

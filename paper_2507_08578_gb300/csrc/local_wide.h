@@ -1,4 +1,4 @@
-// Host entry of the CTA-wide pass B instances (local_wide.cu).
+// Host entry of the CTA-wide pass B instances (local_wide_impl.cuh).
 #pragma once
 
 #include "local_kernels.cuh"
@@ -7,10 +7,21 @@ namespace kss {
 
 constexpr size_t kWideSmemMax = 227 * 1024;
 
-// Launches pass B for nbands bands (grid N1 x nbands) with the CTA-wide transform stages when a
-// compile-time instance exists for the split (A, B) of N2 == N3 and its shared memory fits.
-// Returns false (and launches nothing) otherwise.  dry = true only checks availability.
+// Launches pass B for nbands bands (grid N1 x nbands, nt = 256 or 384 threads per CTA) with the
+// CTA-wide transform stages for the split N2 == N3 == A * B.  Returns false (and launches
+// nothing) when no instance exists for (A, B, nt) or its shared memory does not fit.
+// dry = true only checks availability.
 template <typename T>
-bool wide_pass_b(const lk::LocalArgs<T>& a, int A, int B, int nbands, cudaStream_t st, bool dry);
+bool wide_pass_b(const lk::LocalArgs<T>& a, int A, int B, int nt, int nbands, cudaStream_t st, bool dry);
+
+// The (A, B) pairs with instances, in KSS_WIDE_SPLITS order.
+inline const std::vector<std::pair<int, int>>& wide_splits() {
+  static const std::vector<std::pair<int, int>> v = {
+#define KSS_PAIR(x, y) {x, y},
+      KSS_WIDE_SPLITS(KSS_PAIR)
+#undef KSS_PAIR
+  };
+  return v;
+}
 
 }  // namespace kss

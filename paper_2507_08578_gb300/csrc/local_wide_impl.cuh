@@ -1,0 +1,45 @@
+// Kernel instances of the CTA-wide pass B (local_kernels.cuh, pass_bw_body) for one precision:
+// every split of KSS_WIDE_SPLITS at 256 and 384 threads per CTA.  Included by one translation
+// unit per precision (local_wide_f32.cu, local_wide_f64.cu) so the build compiles them in parallel.
+#pragma once
+
+#include "local_kernels.cuh"
+#include "local_wide.h"
+
+namespace kss {
+namespace wide_detail {
+
+using namespace lk;
+
+template <typename T, int A, int B, int NT>
+__global__ void __launch_bounds__(NT) pass_bw(LocalArgs<T> a) {
+  pass_bw_body<T, A, B, NT>(a, blockIdx.x, blockIdx.y);
+}
+
+template <typename T, int A, int B, int NT>
+bool launch_one(const LocalArgs<T>& a, int nbands, cudaStream_t st, bool dry) {
+  const size_t sm = WideB<T, A, B>::smem(a.W3);
+  if (sm > kWideSmemMax) return false;
+  if (dry) return true;
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_bw<T, A, B, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  pass_bw<T, A, B, NT><<<dim3(a.N1, nbands), NT, sm, st>>>(a);
+  return true;
+}
+
+template <typename T>
+bool dispatch(const LocalArgs<T>& a, int A, int B, int nt, int nbands, cudaStream_t st, bool dry) {
+  if (a.N2 != a.N3 || A * B != a.N2 || (nt != 256 && nt != 384)) return false;
+  switch (A * 32 + B) {
+#define KSS_CASE(x, y)                                                       \
+  case x * 32 + y:                                                           \
+    return nt == 256 ? launch_one<T, x, y, 256>(a, nbands, st, dry)          \
+                     : launch_one<T, x, y, 384>(a, nbands, st, dry);
+    KSS_WIDE_SPLITS(KSS_CASE)
+#undef KSS_CASE
+    default:
+      return false;
+  }
+}
+
+}  // namespace wide_detail
+}  // namespace kss

@@ -69,6 +69,12 @@ class kss_solve_stats(ctypes.Structure):
 _lib = None
 
 
+class kss_tune_entry(ctypes.Structure):
+    _fields_ = [("device", c_int), ("precision", c_int), ("N1", c_int), ("N", c_int),
+                ("W3", c_int), ("W2", c_int), ("A", c_int), ("B", c_int), ("threads", c_int),
+                ("ms", c_double), ("ncand", c_int)]
+
+
 def lib() -> ctypes.CDLL:
     """Load libkss.so (built by ``build()``); raises if it is missing."""
     global _lib
@@ -421,6 +427,36 @@ def profile_table(ctx) -> dict:
         name, l, ms = kss_profile_entry(ctx, i)
         if l:
             out[name] = (l, ms)
+    return out
+
+
+# --------------------------------------------------------------------------------------------
+# autotuner of the FFT pass-B schedule
+
+def kss_autotune_set(ctx, mode: int):
+    _check(lib().kss_autotune_set(ctx, int(mode)), ctx)
+
+
+def kss_autotune_put(device: int, precision: int, N1: int, N: int, W3: int, A: int, B: int,
+                     threads: int):
+    e = kss_tune_entry(device=device, precision=precision, N1=N1, N=N, W3=W3, W2=0, A=A, B=B,
+                       threads=threads, ms=0.0, ncand=0)
+    _check(lib().kss_autotune_put(byref(e)))
+
+
+def kss_autotune_clear():
+    _check(lib().kss_autotune_clear())
+
+
+def kss_autotune_table() -> list:
+    """Every table entry as a dict (kss_autotune_count / kss_autotune_get)."""
+    n = c_int()
+    _check(lib().kss_autotune_count(byref(n)))
+    out = []
+    for i in range(n.value):
+        e = kss_tune_entry()
+        _check(lib().kss_autotune_get(i, byref(e)))
+        out.append({k: getattr(e, k) for k, _ in kss_tune_entry._fields_})
     return out
 
 
