@@ -384,6 +384,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         K.kss_solver_destroy(sv)
     K.kss_sys_destroy(sysh)
     K.kss_destroy(ctx)
+    # pass-B schedules the autotuner picked (box, window, split, threads per CTA; 0 = per-warp form)
+    sched = [f"{e['N1']}x{e['N']}^2 W3<={e['W3']}: {e['A']}x{e['B']} @{e['threads']} "
+             f"({e['ncand']} timed)" for e in K.kss_autotune_table()]
 
     if rank == 0:
         line = {
@@ -395,7 +398,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "config": {"workload": workload_name(s, nb, args.form),
                        "l2": f"inputs larger than L2: {4 * nk * npw * nb * (16 if args.form == 'fp64' else 8) / 1e9:.1f} GB of band blocks per step",
                        "parallelism": "independent replica per GPU" if world > 1 else "1 GPU",
-                       "band_applies_per_step": applies / args.steps},
+                       "band_applies_per_step": applies / args.steps,
+                       "fft_schedule": sched},
             "metric_family": "band H-applies/s & eigensolves/s at <=1e-6 Ha vs FP64 oracle; p50/p99 latency",
             "gpu_launches": launches,
             "clocks": ck,

@@ -163,6 +163,45 @@ __global__ void __launch_bounds__(256) gemm_cn_partial_f32in(int M, int N, int K
   cn_partial_body<double, float>(M, N, K, A, lda, B, ldb, P, kchunk, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// Lower-triangle form for Hermitian products C = A^H B (M x M): block t of the grid's x
+// dimension is tile (bx, by) with bx >= by (row-major over the lower triangle of tiles).
+__device__ __forceinline__ void lower_tile(int t, int& bx, int& by) {
+  int r = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  while (r * (r + 1) / 2 > t) --r;
+  bx = r;
+  by = t - r * (r + 1) / 2;
+}
+
+template <typename T, typename TI>
+__global__ void __launch_bounds__(256) gemm_cn_partial_lower(int M, int K, const typename CT<TI>::C* __restrict__ A,
+                                                             long long lda, const typename CT<TI>::C* __restrict__ B,
+                                                             long long ldb, typename CT<T>::C* __restrict__ P,
+                                                             int kchunk) {
+  int bx, by;
+  lower_tile(blockIdx.x, bx, by);
+  cn_partial_body<T, TI>(M, M, K, A, lda, B, ldb, P, kchunk, bx, by, blockIdx.z);
+}
+
+// Sum of the partials on and below the diagonal tiles; strictly upper tiles of C are set to 0.
+template <typename T>
+__global__ void gemm_reduce_lower(int M, int nsplit, const typename CT<T>::C* __restrict__ P,
+                                  typename CT<T>::C* __restrict__ Cm, long long ldc) {
+  using C = typename CT<T>::C;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)M * M) return;
+  const int i = (int)(idx % M), j = (int)(idx / M);
+  C out = {0, 0};
+  if (i / BM >= j / BN) {
+    for (int z = 0; z < nsplit; ++z) {
+      const C p = P[(size_t)z * M * M + idx];
+      out.x += p.x;
+      out.y += p.y;
+    }
+  }
+  Cm[(size_t)j * ldc + i] = out;
+}
+
 template <typename T>
 __global__ void gemm_reduce(int M, int N, int nsplit, const typename CT<T>::C* __restrict__ P,
                             typename CT<T>::C* __restrict__ Cm, long long ldc, T ar, T ai, T br,
@@ -482,6 +521,48 @@ void gemm_cn_c64_acc64(kss_ctx ctx, int M, int N, int K, const void* A, int lda,
         M, N, splits, ctx->ws_gemm.as<double2>(), (double2*)C, ldc, 1.0, 0.0, 0.0, 0.0);
   }
   KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+// Lower triangle (tiles on or below the diagonal) of a Hermitian product C = A^H B, M x M, with
+// A and B K x M of element type TI (complex64 / complex128) and accumulation in T; the strictly
+// upper tiles of C are zeroed.  For Gram matrices read through one triangle by the eigensolver.
+template <typename T, typename TI>
+void run_cn_lower(kss_ctx ctx, int M, int K, const void* A, int lda, const void* B, int ldb, void* Cm,
+                  int ldc, const char* name, const char* tag) {
+  using C = typename CT<T>::C;
+  using CI = typename CT<TI>::C;
+  const int tm = (M + BM - 1) / BM;
+  const int tiles = tm * (tm + 1) / 2;
+  const SplitK sk = plan_splitk(ctx, gemm_cn_partial_lower<T, TI>, tiles, K, (size_t)M * M * sizeof(C), 512ull << 20);
+  ctx->ws_gemm.ensure((size_t)sk.splits * M * M * sizeof(C));
+  const bool f64 = sizeof(T) == 8;
+  {
+    ProfScope ps(ctx, tag_id(name, f64, tag));
+    gemm_cn_partial_lower<T, TI><<<dim3(tiles, 1, sk.splits), 256, 0, ctx->stream>>>(
+        M, K, (const CI*)A, lda, (const CI*)B, ldb, ctx->ws_gemm.as<C>(), sk.kchunk);
+  }
+  const long long mm = (long long)M * M;
+  {
+    ProfScope ps(ctx, tag_id("gemm_reduce", f64, tag));
+    gemm_reduce_lower<T><<<(unsigned)((mm + 255) / 256), 256, 0, ctx->stream>>>(M, sk.splits, ctx->ws_gemm.as<C>(),
+                                                                              (C*)Cm, ldc);
+  }
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+void gemm_cn_lower(kss_ctx ctx, bool fp64, int M, int K, const void* A, int lda, const void* B, int ldb,
+                   void* C, int ldc, const char* tag) {
+  if (M <= 0) return;
+  KSS_REQUIRE(K > 0 && lda >= K && ldb >= K && ldc >= M, "gemm_cn_lower: bad size");
+  if (fp64) run_cn_lower<double, double>(ctx, M, K, A, lda, B, ldb, C, ldc, "gemm_cn_partial", tag);
+  else run_cn_lower<float, float>(ctx, M, K, A, lda, B, ldb, C, ldc, "gemm_cn_partial", tag);
+}
+
+void gemm_cn_c64_acc64_lower(kss_ctx ctx, int M, int K, const void* A, int lda, const void* B, int ldb,
+                             void* C, int ldc, const char* tag) {
+  if (M <= 0) return;
+  KSS_REQUIRE(K > 0 && lda >= K && ldb >= K && ldc >= M, "gemm_cn_c64_acc64_lower: bad size");
+  run_cn_lower<double, float>(ctx, M, K, A, lda, B, ldb, C, ldc, "gemm_cn_partial_c64in", tag);
 }
 
 // gemm_cn with a caller-provided partial-sum buffer (no allocation, no profiling events): the

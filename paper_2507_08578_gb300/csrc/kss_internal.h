@@ -241,6 +241,12 @@ int tc_error_flag(kss_ctx ctx, bool reset);
 // C (complex128) = A^H B for complex64 A, B with FP64 accumulation.
 void gemm_cn_c64_acc64(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B,
                        int ldb, void* C, int ldc, const char* tag);
+// Lower triangle of the Hermitian product C = A^H B (M x M; A, B: K x M), strictly upper tiles
+// zeroed: FP64 / FP32 (gemm_cn_lower) and complex64 inputs with FP64 accumulation.
+void gemm_cn_lower(kss_ctx ctx, bool fp64, int M, int K, const void* A, int lda, const void* B, int ldb,
+                   void* C, int ldc, const char* tag);
+void gemm_cn_c64_acc64_lower(kss_ctx ctx, int M, int K, const void* A, int lda, const void* B, int ldb,
+                             void* C, int ldc, const char* tag);
 // Scale row i of a complex (M x N, col-major) matrix by real d[i] * s.
 void scale_rows(kss_ctx ctx, bool fp64, int M, int N, void* C, int ldc, const void* d, double s);
 

@@ -200,15 +200,17 @@ void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo
   kss_ctx ctx = on ? on : s->sys->ctx;
   const int nb = s->nb, npw = s->npw;
   const long long nn = (long long)nb * nb;
+  // The generalised eigensolve reads the lower triangles of S and Hs only: the Gram products
+  // compute the tiles on and below the diagonal (about half the work) and zero the rest.
   if (f64) {
-    gemm_cn(ctx, true, nb, nb, npw, Y, npw, Y, npw, s->S.p, nb, 1, 0, 0, 0, "gram");
-    gemm_cn(ctx, true, nb, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, 1, 0, 0, 0, "gram");
+    gemm_cn_lower(ctx, true, nb, npw, Y, npw, Y, npw, s->S.p, nb, "gram");
+    gemm_cn_lower(ctx, true, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, "gram");
   } else if (s->gram64) {
-    gemm_cn_c64_acc64(ctx, nb, nb, npw, Y, npw, Y, npw, s->S.p, nb, "gram");
-    gemm_cn_c64_acc64(ctx, nb, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, "gram");
+    gemm_cn_c64_acc64_lower(ctx, nb, npw, Y, npw, Y, npw, s->S.p, nb, "gram");
+    gemm_cn_c64_acc64_lower(ctx, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, "gram");
   } else {
-    gemm_cn(ctx, false, nb, nb, npw, Y, npw, Y, npw, s->S32.p, nb, 1, 0, 0, 0, "gram");
-    gemm_cn(ctx, false, nb, nb, npw, Y, npw, HY, npw, s->Hs32.p, nb, 1, 0, 0, 0, "gram");
+    gemm_cn_lower(ctx, false, nb, npw, Y, npw, Y, npw, s->S32.p, nb, "gram");
+    gemm_cn_lower(ctx, false, nb, npw, Y, npw, HY, npw, s->Hs32.p, nb, "gram");
     static const int idc = prof_register("convert_c64_c128");
     {
       ProfScope ps(ctx, idc);
