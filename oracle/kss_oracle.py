@@ -22,6 +22,9 @@ Conventions (readings of the paper's plane-wave statement, §1 and §5.2):
   beta_{a,x}(G) = c_p q_x exp(-alpha |q|^2) exp(-i q.R_a) (likewise y, z), with c_s, c_p the
   continuum unit-norm constants; H_nl = sum_i |beta_i> D_i <beta_i| (Eq. ham-nl, §5.2, with
   the diagonal h of norm-conserving pseudopotentials).
+* Overlap (the generalised form, §5.2: the nonlocal part of the overlap operator has the same
+  structure as Eq. ham-nl): S = 1 + sum_i |beta_i> q_i <beta_i| with diagonal q, and the
+  eigenproblem H psi = lambda S psi, eigenvectors S-orthonormal.  q = None means S = 1.
 """
 from __future__ import annotations
 
@@ -334,6 +337,22 @@ def apply_h_naive(c: np.ndarray, basis: Basis, V: np.ndarray, beta: np.ndarray,
     return basis.kinetic[None, :] * c + apply_local_naive(c, basis, V) + apply_nonlocal(c, beta, D)
 
 
+def dense_overlap(beta: np.ndarray, Q: Optional[np.ndarray]) -> np.ndarray:
+    """S_{GG'} = delta_{GG'} + sum_i beta_i(G) q_i conj(beta_i(G'))."""
+    S = np.eye(beta.shape[0], dtype=np.complex128)
+    if Q is not None and beta.shape[1]:
+        S += (beta * np.asarray(Q, np.float64)[None, :]) @ beta.conj().T
+    return S
+
+
+def apply_overlap(c: np.ndarray, beta: np.ndarray, Q: Optional[np.ndarray]) -> np.ndarray:
+    """S psi = psi + sum_i beta_i q_i <beta_i|psi> for every band (band-major block)."""
+    c = np.asarray(c, np.complex128)
+    if Q is None or beta.shape[1] == 0:
+        return c.copy()
+    return c + apply_nonlocal(c, beta, np.asarray(Q, np.float64))
+
+
 def apply_h_dense(c: np.ndarray, H: np.ndarray) -> np.ndarray:
     return np.asarray(c, np.complex128) @ H.T
 
@@ -345,6 +364,13 @@ def apply_h_dense(c: np.ndarray, H: np.ndarray) -> np.ndarray:
 def lowest_eigenpairs(H: np.ndarray, nband: int):
     """Lowest nband eigenvalues (ascending) and eigenvectors (columns) of Hermitian H (LAPACK)."""
     w, v = scipy.linalg.eigh(H, subset_by_index=[0, nband - 1], driver="evr")
+    return w, v
+
+
+def lowest_generalized_eigenpairs(H: np.ndarray, S: np.ndarray, nband: int):
+    """Lowest nband eigenpairs of H x = lambda S x (Hermitian H, Hermitian positive definite S;
+    LAPACK): eigenvalues ascending, eigenvectors S-orthonormal columns."""
+    w, v = scipy.linalg.eigh(H, S, subset_by_index=[0, nband - 1], driver="gvx")
     return w, v
 
 
@@ -368,12 +394,25 @@ class Problem:
     V: np.ndarray
     beta: np.ndarray
     D: np.ndarray
+    Q: Optional[np.ndarray] = None  # overlap coefficients (None: S = 1)
 
     def dense(self) -> np.ndarray:
         return dense_hamiltonian(self.basis, self.V, self.beta, self.D)
 
     def apply(self, c: np.ndarray) -> np.ndarray:
         return apply_h_naive(c, self.basis, self.V, self.beta, self.D)
+
+    def dense_S(self) -> np.ndarray:
+        return dense_overlap(self.beta, self.Q)
+
+    def apply_S(self, c: np.ndarray) -> np.ndarray:
+        return apply_overlap(c, self.beta, self.Q)
+
+    def lowest(self, nband: int):
+        """Lowest nband eigenpairs of H x = lambda S x (standard when Q is None)."""
+        if self.Q is None:
+            return lowest_eigenpairs(self.dense(), nband)
+        return lowest_generalized_eigenpairs(self.dense(), self.dense_S(), nband)
 
 
 def system_box(sys_) -> Tuple[int, int, int]:
@@ -390,7 +429,9 @@ def build_problem(sys_, ik: int = 0, box=None, V: Optional[np.ndarray] = None) -
         V = vloc_for(sys_, box)
     beta = projectors(sys_.lattice, basis, sys_.pos, sys_.nproj_per_atom, sys_.proj_alpha)
     D = np.asarray(sys_.D, np.float64)[: beta.shape[1]]
-    return Problem(basis=basis, V=V, beta=beta, D=D)
+    Q = getattr(sys_, "Q", None)
+    Q = None if Q is None else np.asarray(Q, np.float64)[: beta.shape[1]]
+    return Problem(basis=basis, V=V, beta=beta, D=D, Q=Q)
 
 
 def eigenvalue_error(evals: np.ndarray, ref: np.ndarray) -> float:

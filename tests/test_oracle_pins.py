@@ -312,3 +312,112 @@ def test_inertia_count():
     for k in (0, 5, 17, w.size - 3):
         sigma = 0.5 * (w[k] + w[k + 1]) if k + 1 < w.size else w[-1] + 1
         assert O.count_below(H, sigma) == k + 1
+
+
+# ---------------------------------------------------------------------------------------------
+# Generalised form: H x = lambda S x with S = 1 + sum_i |beta_i> q_i <beta_i| (§5.2: the overlap's
+# nonlocal part has the structure of Eq. ham-nl)
+# ---------------------------------------------------------------------------------------------
+
+def gen_secular_roots(t, w, q):
+    """All eigenvalues of diag(t) x = lambda (1 + q b b^H) x (t > 0, 1 + q |b|^2 > 0).  With
+    s = b^H x != 0: (t - lambda) x = lambda q b s gives the secular equation
+    1 = lambda q sum_s w_s / (t_s - lambda) over distinct shells t_s (weights w_s = sum |b|^2);
+    a shell of multiplicity g_s keeps g_s - 1 eigenvalues at t_s.  For q > 0 one root lies in
+    (0, t_1) and one in each (t_i, t_i+1); for q < 0 one in each (t_i, t_i+1) and one above the
+    last shell."""
+    order = np.argsort(t)
+    t, w = t[order], w[order]
+    shells, mult, wt = [], [], []
+    for ti, wi in zip(t, w):
+        if shells and abs(ti - shells[-1]) < 1e-10:
+            mult[-1] += 1
+            wt[-1] += wi
+        else:
+            shells.append(ti)
+            mult.append(1)
+            wt.append(wi)
+    ts, ws = np.array(shells), np.array(wt)
+
+    def f(e):
+        return 1.0 - e * q * np.sum(ws / (ts - e))
+
+    def bisect(lo, hi):
+        flo = f(lo)
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            fm = f(mid)
+            if (fm > 0) == (flo > 0):
+                lo, flo = mid, fm
+            else:
+                hi = mid
+        return 0.5 * (lo + hi)
+
+    eps = 1e-13
+    roots = [bisect(ts[i] + eps, ts[i + 1] - eps) for i in range(len(ts) - 1)]
+    if q > 0:
+        roots.append(bisect(eps, ts[0] - eps))
+    else:
+        hi = ts[-1] + 1.0
+        while f(hi) < 0:  # f -> 1 + q sum w > 0 as e -> infinity
+            hi = ts[-1] + 2.0 * (hi - ts[-1])
+        roots.append(bisect(ts[-1] + eps, hi))
+    for ti, g in zip(ts, mult):
+        roots.extend([ti] * (g - 1))
+    return np.sort(np.array(roots))
+
+
+@pytest.mark.parametrize("q", [0.8, -0.3])
+def test_generalized_rank_one_secular_equation(q):
+    s = W.tiny_system(a=6.0, ecut=2.0, natom=1, vloc_amp=0.0, nproj_per_atom=1,
+                      kpts=[(0.25, 0.25, 0.25)])
+    s.D[:] = 0.0
+    s = W.with_(s, Q=np.array([q]))
+    p = O.build_problem(s, 0, box=(15, 15, 15))
+    b = p.beta[:, 0]
+    assert 1.0 + q * np.sum(np.abs(b) ** 2) > 0.1
+    w_gen = O.lowest_generalized_eigenpairs(p.dense(), p.dense_S(), p.basis.npw)[0]
+    roots = gen_secular_roots(p.basis.kinetic.copy(), np.abs(b) ** 2, q)
+    assert roots.size == w_gen.size
+    assert np.max(np.abs(roots - w_gen)) < 1e-10
+    # the pin discriminates: a flipped overlap sign (a plausible slip) is far off
+    wrong = O.lowest_generalized_eigenpairs(p.dense(), O.dense_overlap(p.beta, -p.Q), p.basis.npw)[0]
+    assert np.max(np.abs(roots - wrong)) > 1e-3
+
+
+@pytest.fixture(scope="module")
+def tiny_overlap_problem():
+    s = W.with_overlap(W.tiny_system(a=6.5, ecut=2.5, natom=3, kpts=[(0.25, 0.25, -0.25)]), qmax=0.6)
+    return O.build_problem(s, 0, box=(16, 15, 18))
+
+
+def test_overlap_apply_matches_dense_and_is_spd(tiny_overlap_problem):
+    p = tiny_overlap_problem
+    S = p.dense_S()
+    assert np.max(np.abs(S - S.conj().T)) < 1e-15
+    np.linalg.cholesky(S)  # positive definite
+    c = W.random_block(p.basis.npw, 3, seed=12)
+    assert np.max(np.abs(p.apply_S(c) - c @ S.T)) < 1e-13
+    # q = 0 gives S = 1, and no overlap gives the standard problem
+    p0 = O.Problem(p.basis, p.V, p.beta, p.D, None)
+    assert np.array_equal(p0.dense_S(), np.eye(p.basis.npw))
+    assert np.array_equal(p0.apply_S(c), c)
+
+
+def test_generalized_eigenpairs_invariants(tiny_overlap_problem):
+    p = tiny_overlap_problem
+    n = 12
+    w, v = p.lowest(n)
+    H, S = p.dense(), p.dense_S()
+    assert np.max(np.abs(H @ v - (S @ v) * w[None, :])) < 1e-11
+    assert np.max(np.abs(v.conj().T @ S @ v - np.eye(n))) < 1e-12
+    # textbook reduction with the Cholesky factor S = L L^H: eig(L^-1 H L^-H) are the same values
+    L = np.linalg.cholesky(S)
+    Li = np.linalg.inv(L)
+    w_red = np.linalg.eigvalsh(Li @ H @ Li.conj().T)[:n]
+    assert np.max(np.abs(w_red - w)) < 1e-11
+    # S >= 1 (q >= 0) only shrinks Rayleigh quotients towards 0, so by Courant-Fischer
+    # min(l_k, 0) <= l_k(gen) <= max(l_k, 0) for the standard eigenvalue l_k of the same index
+    ws = O.lowest_eigenpairs(H, n)[0]
+    assert np.all(w <= np.maximum(ws, 0.0) + 1e-12) and np.all(w >= np.minimum(ws, 0.0) - 1e-12)
+    assert np.any(np.abs(w - ws) > 1e-3)  # and the overlap does change them

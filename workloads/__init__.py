@@ -49,6 +49,7 @@ class System:
     nproj_per_atom: int = 4  # 4 = s, px, py, pz ; 1 = s only ; 0 = none
     proj_alpha: float = 0.25  # form factor exp(-alpha |q|^2)
     seed: int = 0
+    Q: Optional[np.ndarray] = None  # (nproj,) overlap coefficients q_i; None: S = 1
 
     @property
     def natom(self) -> int:
@@ -158,6 +159,25 @@ def config5(nreq: int = 200, rate: float = 200.0) -> List[Request]:
                             kpts=SHIFTED_222[:nk])
         reqs.append(Request(t, s))
     return reqs
+
+
+def with_overlap(s: System, qmax: float = 0.5, qmin: float = 0.0, seed: Optional[int] = None) -> System:
+    """The same system with overlap coefficients q_i ~ U[qmin, qmax] (one per projector), drawn
+    from their own generator (seed + 7777 unless given) so that the other inputs are unchanged."""
+    rng = np.random.default_rng((s.seed + 7777) if seed is None else seed)
+    return replace(s, Q=rng.uniform(qmin, qmax, size=s.nproj))
+
+
+def config1s() -> System:
+    """Config 1 with a nonlocal overlap S = 1 + sum_i |beta_i> q_i <beta_i|, q_i ~ U[0, 0.5]."""
+    return with_overlap(replace(config1(), name="C1S"))
+
+
+def config2s(nk: int = 1) -> System:
+    """The config-2 cell (96^3, 64 atoms, 256 projectors, 512 bands) with the overlap of
+    config1s, on the first nk shifted k-points."""
+    s = config2()
+    return with_overlap(replace(s, name="C2S", kpts=s.kpts[:nk]))
 
 
 def tiny_system(a: float = 6.0, ecut: float = 2.0, natom: int = 2, nband: int = 8,
