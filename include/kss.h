@@ -101,6 +101,14 @@ typedef struct {
   double proj_alpha;       /* form factor exp(-alpha |k+G|^2), > 0 */
   const double* D;         /* host, natom*nproj_per_atom projector energies (Ha), copied;
                               index 4a+l for l in (s, px, py, pz) */
+  const double* Q;         /* host, natom*nproj_per_atom overlap coefficients q_i (same index),
+                              copied, or NULL.  With Q the eigenproblem is the generalised
+                              H psi = lambda S psi, S = 1 + sum_i |beta_i> q_i <beta_i| (§5.2:
+                              the nonlocal part of the overlap has the structure of Eq. ham-nl);
+                              S must be provably positive definite: 1 + min(0, min q) * g > 0,
+                              g the Gershgorin bound of the largest eigenvalue of the projector
+                              Gram matrix beta^H beta (KSS_EINVAL otherwise).  NULL or all-zero
+                              Q: S = 1, the standard problem. */
 } kss_atoms;
 
 /* Build a system: enumerate the G-sphere of every k-point on the host (the inclusion test is
@@ -159,8 +167,15 @@ kss_status kss_footprint(kss_sys sys, int nband, kss_precision prec, size_t* byt
 kss_status kss_apply_H(kss_sys sys, int ik, int nb, const void* psi, void* hpsi, int ld,
                        kss_precision prec);
 
-/* One Chebyshev three-term step fused into the H application:
- *   out = alpha * H psi + beta * psi + gamma * psi_prev
+/* spsi = S(k_ik) psi = psi + beta (Q (beta^H psi)): the overlap of a system set up with Q
+ * (spsi = psi without it).  Same layout and rules as kss_apply_H. */
+kss_status kss_apply_S(kss_sys sys, int ik, int nb, const void* psi, void* spsi, int ld,
+                       kss_precision prec);
+
+/* One Chebyshev three-term step fused into the application of the filter operator F:
+ *   out = alpha * F psi + beta * psi + gamma * psi_prev
+ * F = H, or F = S^-1 H for a system with an overlap (S^-1 = 1 - beta W beta^H with the
+ * precomputed W = Q (1 + beta^H beta Q)^-1 per k-point).
  * psi_prev may be NULL (then gamma is ignored) and may alias out (out is written element by
  * element after psi_prev at the same element is read).  psi must not overlap out. */
 kss_status kss_cheb_step(kss_sys sys, int ik, int nb, const void* psi, const void* psi_prev,
@@ -222,7 +237,7 @@ kss_status kss_gemm(kss_ctx ctx, int op, int M, int N, int K, const void* A, int
 
 typedef struct {
   int degree;              /* filter polynomial degree m (>= 1; 0 => 10) */
-  double tol;              /* residual tolerance |H x - lambda x| (Ha) on the wanted bands (<= 0 => 1e-8) */
+  double tol;              /* residual tolerance |H x - lambda S x| (Ha) on the wanted bands (<= 0 => 1e-8) */
   int max_iter;            /* filter iterations (<= 0 => 200) */
   int nbuffer;             /* extra bands (< 0 => max(4, ceil(nband/10))) */
   kss_precision prec;
@@ -259,7 +274,10 @@ kss_status kss_solver_results(kss_solver s, double* evals, double* resid, void* 
                               kss_solve_stats* stats);
 
 /* Full solve = create + step until converged or max_iter + results + destroy.
- * Returns KSS_ENOCONV (outputs still filled) when max_iter is reached. */
+ * Returns KSS_ENOCONV (outputs still filled) when max_iter is reached.
+ * For a system with an overlap (kss_atoms.Q) the solver returns the lowest generalised
+ * eigenpairs H x = lambda S x: the filter polynomial is in S^-1 H, Rayleigh-Ritz uses the
+ * metric Y^H S Y, residuals are |H x - lambda S x|, and the eigenvectors are S-orthonormal. */
 kss_status kss_chebfi_solve(kss_sys sys, int ik, int nband, const kss_solve_opts* opts,
                             double* evals, void* evecs, int ld, double* resid,
                             kss_solve_stats* stats);
@@ -277,7 +295,8 @@ kss_status kss_chebfi_solve(kss_sys sys, int ik, int nband, const kss_solve_opts
  * nbuffer; unit u draws its start block with seed opts->seed + u; x0 must be NULL).
  * evals[u], resid[u]: host arrays of nband[u] (any pointer may be NULL); stats: array of n or
  * NULL.  Returns KSS_ENOCONV if any unit hit max_iter (results still filled); KSS_ENOTSUP if a
- * unit's FFT lengths have no two-codelet split (125, 162, 200, 216, 243, 250). */
+ * unit's FFT lengths have no two-codelet split (125, 162, 200, 216, 243, 250) or its system has
+ * an overlap (generalised problems are solved per system). */
 kss_status kss_solve_batch(kss_ctx ctx, int n, const kss_sys* sys, const int* ik, const int* nband,
                            const kss_solve_opts* opts, double* const* evals, double* const* resid,
                            kss_solve_stats* stats);
@@ -305,7 +324,7 @@ kss_status kss_server_start(kss_ctx ctx, size_t hbm_budget_bytes, int max_slots,
                             const kss_solve_opts* opts);
 
 /* Queue a request (cell, atoms, nband: copied).  *ticket identifies it.  KSS_EBUSY if the queue
- * is full or the request alone exceeds the budget. */
+ * is full or the request alone exceeds the budget; KSS_ENOTSUP for atoms with an overlap Q. */
 kss_status kss_server_submit(kss_ctx ctx, const kss_cell* cell, const kss_atoms* atoms, int nband,
                              uint64_t* ticket);
 

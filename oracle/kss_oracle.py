@@ -408,6 +408,14 @@ class Problem:
     def apply_S(self, c: np.ndarray) -> np.ndarray:
         return apply_overlap(c, self.beta, self.Q)
 
+    def apply_filter_operator(self, c: np.ndarray) -> np.ndarray:
+        """S^-1 H psi (H psi without an overlap): the operator whose polynomial the generalised
+        Chebyshev filter applies; S^-1 through a dense linear solve."""
+        h = self.apply(c)
+        if self.Q is None:
+            return h
+        return np.linalg.solve(self.dense_S(), h.T).T
+
     def lowest(self, nband: int):
         """Lowest nband eigenpairs of H x = lambda S x (standard when Q is None)."""
         if self.Q is None:

@@ -249,6 +249,14 @@ kss_status kss_setup(kss_ctx ctx, const kss_cell* cell, const kss_atoms* atoms, 
     s->nproj = s->natom * s->nppa;
     s->pos.assign(atoms->pos_cart, atoms->pos_cart + 3 * s->natom);
     if (s->nproj) s->D.assign(atoms->D, atoms->D + s->nproj);
+    if (s->nproj && atoms->Q) {
+      s->Q.assign(atoms->Q, atoms->Q + s->nproj);
+      for (double q : s->Q) {
+        KSS_REQUIRE(std::isfinite(q), "non-finite overlap coefficient");
+        s->has_S |= q != 0.0;
+      }
+      if (!s->has_S) s->Q.clear();
+    }
     s->vamp = atoms->vloc_amp;
     s->vsig = atoms->vloc_sigma;
     s->alpha = atoms->proj_alpha;
@@ -326,6 +334,13 @@ kss_status kss_setup(kss_ctx ctx, const kss_cell* cell, const kss_atoms* atoms, 
       KSS_CHECK_CUDA(cudaMemcpy(s->d_D64.p, s->D.data(), s->nproj * sizeof(double), cudaMemcpyHostToDevice));
       KSS_CHECK_CUDA(cudaMemcpy(s->d_D32.p, d32.data(), s->nproj * sizeof(float), cudaMemcpyHostToDevice));
     }
+    if (s->has_S) {
+      s->d_Q64.alloc(s->nproj * sizeof(double));
+      s->d_Q32.alloc(s->nproj * sizeof(float));
+      std::vector<float> q32(s->Q.begin(), s->Q.end());
+      KSS_CHECK_CUDA(cudaMemcpy(s->d_Q64.p, s->Q.data(), s->nproj * sizeof(double), cudaMemcpyHostToDevice));
+      KSS_CHECK_CUDA(cudaMemcpy(s->d_Q32.p, q32.data(), s->nproj * sizeof(float), cudaMemcpyHostToDevice));
+    }
 
     // Per-k tables.
     for (auto& kd : s->k) {
@@ -385,6 +400,7 @@ kss_status kss_setup(kss_ctx ctx, const kss_cell* cell, const kss_atoms* atoms, 
       kd.bound = kd.tmax + std::max(s->vmax, 0.0) + nl;
     }
     KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    overlap_setup(s.get());  // per-k W = Q (1 + G Q)^-1 and the filter bound (bound_f = bound without Q)
     KSS_CHECK_CUDA(cudaGetLastError());
     ctx->nsys += 1;
     *out = s.release();
@@ -482,8 +498,23 @@ kss_status kss_cheb_step(kss_sys sys, int ik, int nb, const void* psi, const voi
   if (!sys) return KSS_EINVAL;
   return guard(sys->ctx, [&] {
     KSS_CHECK_CUDA(cudaSetDevice(sys->ctx->device));
-    apply_h(sys, ik, nb, psi, psi_prev, out, ld, ChebCoef{alpha, beta, psi_prev ? gamma : 0.0},
-            prec);
+    apply_filter_op(sys, ik, nb, psi, psi_prev, out, ld, ChebCoef{alpha, beta, psi_prev ? gamma : 0.0},
+                    prec);
+  });
+}
+
+kss_status kss_apply_S(kss_sys sys, int ik, int nb, const void* psi, void* spsi, int ld,
+                       kss_precision prec) {
+  if (!sys) return KSS_EINVAL;
+  return guard(sys->ctx, [&] {
+    KSS_REQUIRE(ik >= 0 && ik < (int)sys->k.size(), "k-point index out of range");
+    KSS_REQUIRE(nb >= 0, "nb < 0");
+    KSS_REQUIRE(prec == KSS_PREC_FP64 || prec == KSS_PREC_MIXED, "unknown precision");
+    KSS_REQUIRE(ld >= sys->k[ik].npw, "ld < npw");
+    if (nb == 0) return;
+    KSS_REQUIRE(psi && spsi && psi != spsi, "null or overlapping psi / spsi");
+    KSS_CHECK_CUDA(cudaSetDevice(sys->ctx->device));
+    apply_s(sys->ctx, sys, ik, nb, psi, spsi, ld, prec);
   });
 }
 
@@ -547,6 +578,7 @@ kss_status kss_footprint(kss_sys sys, int nband, kss_precision prec, size_t* byt
     size_t b = 4 * (size_t)npw * nb * es;                       // four band blocks
     if (prec == KSS_PREC_MIXED) b += 2 * (size_t)npw * nb * 16; // FP64 refinement blocks
     b += 3 * (size_t)nb * nb * 16;                              // Gram / projected H / work
+    if (sys->has_S) b += 2 * (size_t)npw * nb * es;             // S Y / S X block, L psi scratch
     b += local_workspace_bytes(sys, (int)ik, nb, prec);
     m = std::max(m, b);
   }

@@ -777,6 +777,8 @@ extern "C" kss_status kss_solve_batch(kss_ctx ctx, int n, const kss_sys* sys, co
     KSS_REQUIRE(o.x0 == nullptr, "kss_solve_batch takes no warm start (use the server or solvers)");
     for (int u = 0; u < n; ++u) {
       KSS_REQUIRE(sys[u] && sys[u]->ctx == ctx, "every system must belong to this context");
+      if (sys[u]->has_S)
+        fail(KSS_ENOTSUP, "batched solves take systems without an overlap (solve generalised problems per system)");
       kss_solve_opts ou = o;
       ou.seed = o.seed + (uint64_t)u;
       kss_solver s = nullptr;

@@ -72,8 +72,11 @@ struct KData {
   DevBuf d_beta64, d_beta32;       // projector-major [nproj][npw] complex
   DevBuf d_q;                      // Cartesian k+G, npw*3 doubles (setup only)
   double tmax = 0;
-  double bound = 0;                // rigorous spectral upper bound
+  double bound = 0;                // rigorous spectral upper bound of H
+  double bound_f = 0;              // same for the filter operator (H, or S^-1 H with an overlap)
   std::vector<double> beta_norm2;  // |beta_i|^2 per projector
+  DevBuf d_G64, d_G32;             // overlap only: projector Gram matrix beta^H beta, nproj^2
+  DevBuf d_W64, d_W32;             // overlap only: W = Q (1 + G Q)^-1, so S^-1 = 1 - beta W beta^H
 };
 
 // Kernel launch accounting: every launch of the library's kernels is counted; when profiling
@@ -110,6 +113,7 @@ struct kss_ctx_s {
   int nsm = 0;
   void* server = nullptr;          // request server (server.cu), NULL when not running
   int autotune = 1;                // 1: time FFT schedule candidates at first use (tune.cu)
+  kss::DevBuf ws_sapply, ws_e, ws_f; // overlap: L psi block, E = beta^H H psi, F (nproj x nb)
   kss::DevBuf ws_tune;             // scratch slab of the autotuner
 };
 
@@ -129,6 +133,9 @@ struct kss_sys_s {
   kss::DevBuf d_Vx64, d_Vx32;      // V(r_j)/(N1 N2 N3) in [j1][j2][j3] order (plane kernel)
   kss::DevBuf d_tw64[3], d_tw32[3];// e^{-2 pi i k/N_d}, k < N_d
   kss::DevBuf d_D64, d_D32;
+  bool has_S = false;              // generalised problem: S = 1 + sum_i |beta_i> q_i <beta_i|
+  std::vector<double> Q;           // overlap coefficients (nproj), empty without an overlap
+  kss::DevBuf d_Q64, d_Q32;
   std::vector<kss::KData> k;
   int nsolvers = 0;
 };
@@ -144,6 +151,7 @@ struct kss_solver_s {
   kss::DevBuf S, Hs, W, work, info, resid_d;
   kss::DevBuf S32, Hs32, Q32;
   kss::DevBuf r64[4];  // FP64 refinement blocks (mixed precision)
+  kss::DevBuf sblk, sblk64;  // overlap only: S Y, then S X (solver precision / FP64 refinement)
   int lwork = 0;
   std::vector<double> evals, resid;
   int iter = 0;
@@ -190,6 +198,15 @@ struct ChebCoef {
 // out = alpha*(T psi + V psi + nonlocal psi) + beta*psi + gamma*psi_prev (psi_prev may be null)
 void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, void* out, int ld,
              ChebCoef c, kss_precision prec);
+// out = T psi + V psi (the local part only)
+void apply_local(kss_sys s, int ik, int nb, const void* psi, void* out, int ld, kss_precision prec);
+// ---- generalised problem with a nonlocal overlap (overlap.cu) ----
+void overlap_setup(kss_sys s);
+// out = S psi on ctx's stream (out = psi without an overlap)
+void apply_s(kss_ctx ctx, kss_sys s, int ik, int nb, const void* psi, void* out, int ld, kss_precision prec);
+// out = alpha * F psi + beta * psi + gamma * psi_prev, F = H or S^-1 H (with an overlap)
+void apply_filter_op(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, void* out, int ld,
+                     ChebCoef c, kss_precision prec);
 size_t local_workspace_bytes(kss_sys s, int ik, int nb, kss_precision prec);
 // Caller-provided workspace forms (used by the entry point that allocates nothing).
 size_t local_slab_bytes_per_band(kss_sys s, int ik, kss_precision prec);

@@ -615,6 +615,14 @@ size_t local_workspace_bytes(kss_sys s, int ik, int nb, kss_precision prec) {
   return slab_elems(s, ik) * chunk_bands(s, ik, nb, es) * es;
 }
 
+void apply_local(kss_sys s, int ik, int nb, const void* psi, void* out, int ld, kss_precision prec) {
+  if (nb == 0) return;
+  if (prec == KSS_PREC_FP64)
+    run_local<double>(s, ik, nb, psi, nullptr, out, ld, ChebCoef{1.0, 0.0, 0.0});
+  else
+    run_local<float>(s, ik, nb, psi, nullptr, out, ld, ChebCoef{1.0, 0.0, 0.0});
+}
+
 void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, void* out, int ld,
              ChebCoef c, kss_precision prec) {
   KSS_REQUIRE(ik >= 0 && ik < (int)s->k.size(), "k-point index out of range");

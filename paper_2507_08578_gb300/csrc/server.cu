@@ -303,6 +303,9 @@ kss_status kss_server_submit(kss_ctx ctx, const kss_cell* cell, const kss_atoms*
     KSS_REQUIRE(cell && atoms && ticket && nband >= 1, "kss_server_submit: bad arguments");
     KSS_REQUIRE(cell->nk >= 1 && cell->kpts_red, "need at least one k-point");
     KSS_REQUIRE(atoms->natom >= 0 && (atoms->natom == 0 || atoms->pos_cart), "bad atoms");
+    if (atoms->Q && atoms->natom && atoms->nproj_per_atom)
+      for (int i = 0; i < atoms->natom * atoms->nproj_per_atom; ++i)
+        if (atoms->Q[i] != 0.0) fail(KSS_ENOTSUP, "the server takes atoms without an overlap");
     if (s->pending.size() >= 65536) fail(KSS_EBUSY, "server queue is full");
     Request r;
     r.id = s->next_id++;

@@ -200,16 +200,25 @@ void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo
   kss_ctx ctx = on ? on : s->sys->ctx;
   const int nb = s->nb, npw = s->npw;
   const long long nn = (long long)nb * nb;
+  // With an overlap the metric is Y^H S Y (S Y kept in sb, later overwritten by S X).
+  const bool gen = s->sys->has_S;
+  DevBuf& sb = (f64 && !s->f64) ? s->sblk64 : s->sblk;
+  const void* MY = Y;
+  if (gen) {
+    sb.ensure((size_t)npw * nb * (f64 ? 16 : 8));
+    apply_s(ctx, s->sys, s->ik, nb, Y, sb.p, npw, f64 ? KSS_PREC_FP64 : KSS_PREC_MIXED);
+    MY = sb.p;
+  }
   // The generalised eigensolve reads the lower triangles of S and Hs only: the Gram products
   // compute the tiles on and below the diagonal (about half the work) and zero the rest.
   if (f64) {
-    gemm_cn_lower(ctx, true, nb, npw, Y, npw, Y, npw, s->S.p, nb, "gram");
+    gemm_cn_lower(ctx, true, nb, npw, Y, npw, MY, npw, s->S.p, nb, "gram");
     gemm_cn_lower(ctx, true, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, "gram");
   } else if (s->gram64) {
-    gemm_cn_c64_acc64_lower(ctx, nb, npw, Y, npw, Y, npw, s->S.p, nb, "gram");
+    gemm_cn_c64_acc64_lower(ctx, nb, npw, Y, npw, MY, npw, s->S.p, nb, "gram");
     gemm_cn_c64_acc64_lower(ctx, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, "gram");
   } else {
-    gemm_cn_lower(ctx, false, nb, npw, Y, npw, Y, npw, s->S32.p, nb, "gram");
+    gemm_cn_lower(ctx, false, nb, npw, Y, npw, MY, npw, s->S32.p, nb, "gram");
     gemm_cn_lower(ctx, false, nb, npw, Y, npw, HY, npw, s->Hs32.p, nb, "gram");
     static const int idc = prof_register("convert_c64_c128");
     {
@@ -234,7 +243,9 @@ void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo
     gemm_nn(ctx, false, npw, nb, nb, Y, npw, s->Q32.p, nb, Xo, npw, 1, 0, 0, 0, "rotate");
     gemm_nn(ctx, false, npw, nb, nb, HY, npw, s->Q32.p, nb, HXo, npw, 1, 0, 0, 0, "rotate");
   }
-  residual_norms(ctx, f64, Xo, HXo, npw, nb, npw, s->W.as<double>(), s->resid_d.as<double>());
+  // residuals |H x - lambda S x| (S x = x without an overlap)
+  if (gen) apply_s(ctx, s->sys, s->ik, nb, Xo, sb.p, npw, f64 ? KSS_PREC_FP64 : KSS_PREC_MIXED);
+  residual_norms(ctx, f64, gen ? sb.p : Xo, HXo, npw, nb, npw, s->W.as<double>(), s->resid_d.as<double>());
   if (!s->hpin) {
     KSS_CHECK_CUDA(cudaMallocHost((void**)&s->hpin, (2 * (size_t)nb + 1) * sizeof(double)));
   }
@@ -298,7 +309,7 @@ ChebParams cheb_params(const kss_solver_s* s) {
   const int nb = s->nb;
   const double lam_lo = s->evals[0];
   double a = s->evals[nb - 1];
-  const double b = s->sys->k[s->ik].bound;
+  const double b = s->sys->k[s->ik].bound_f;  // bound of the filter operator (H or S^-1 H)
   if (!(b - a > 1e-3 * (b - lam_lo))) a = lam_lo + 0.5 * (b - lam_lo);
   ChebParams p;
   p.e = 0.5 * (b - a);
@@ -335,8 +346,8 @@ int chebyshev_filter(kss_solver_s* s, int f1, int* prev_out) {
   // Y_1 = (sigma1/e)(H - c) X
   {
     const double al = sigma1 / e;
-    apply_h(s->sys, s->ik, nb, s->blk[cur].p, nullptr, s->blk[prev].p, s->npw,
-            ChebCoef{al, -al * c, 0.0}, p);
+    apply_filter_op(s->sys, s->ik, nb, s->blk[cur].p, nullptr, s->blk[prev].p, s->npw,
+                    ChebCoef{al, -al * c, 0.0}, p);
     s->napply += nb;
     std::swap(cur, prev);  // cur = Y_1, prev = X
   }
@@ -346,8 +357,8 @@ int chebyshev_filter(kss_solver_s* s, int f1, int* prev_out) {
     const double sn = 1.0 / (tau - sigma);
     const double al = 2.0 * sn / e;
     // Y_j = (2 sn / e)(H - c) Y_{j-1} - sigma sn Y_{j-2}, written over Y_{j-2}
-    apply_h(s->sys, s->ik, nb, s->blk[cur].p, s->blk[prev].p, s->blk[prev].p, s->npw,
-            ChebCoef{al, -al * c, -sigma * sn}, p);
+    apply_filter_op(s->sys, s->ik, nb, s->blk[cur].p, s->blk[prev].p, s->blk[prev].p, s->npw,
+                    ChebCoef{al, -al * c, -sigma * sn}, p);
     s->napply += nb;
     std::swap(cur, prev);
     sigma = sn;

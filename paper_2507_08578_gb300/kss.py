@@ -40,7 +40,7 @@ class kss_cell(ctypes.Structure):
 class kss_atoms(ctypes.Structure):
     _fields_ = [("natom", c_int), ("pos_cart", POINTER(c_double)), ("vloc_amp", c_double),
                 ("vloc_sigma", c_double), ("nproj_per_atom", c_int), ("proj_alpha", c_double),
-                ("D", POINTER(c_double))]
+                ("D", POINTER(c_double)), ("Q", POINTER(c_double))]
 
 
 class kss_sys_info(ctypes.Structure):
@@ -82,50 +82,60 @@ def lib() -> ctypes.CDLL:
         if not os.path.exists(LIB_PATH):
             raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
         L = ctypes.CDLL(LIB_PATH)
-        P = c_void_p
-        sig = {
-            "kss_version": ([], c_int),
-            "kss_create": ([POINTER(c_void_p), c_int, c_void_p], c_int),
-            "kss_destroy": ([P], c_int),
-            "kss_last_error": ([P], c_char_p),
-            "kss_setup": ([P, POINTER(kss_cell), POINTER(kss_atoms), POINTER(c_void_p)], c_int),
-            "kss_sys_destroy": ([P], c_int),
-            "kss_sys_info_get": ([P, POINTER(kss_sys_info)], c_int),
-            "kss_sphere": ([P, c_int, POINTER(c_int), POINTER(POINTER(c_int32))], c_int),
-            "kss_get_maps": ([P, c_int, P, P], c_int),
-            "kss_get_tables": ([P, c_int, P, P, P], c_int),
-            "kss_upper_bound": ([P, c_int, POINTER(c_double)], c_int),
-            "kss_footprint": ([P, c_int, c_int, POINTER(c_size_t)], c_int),
-            "kss_apply_H": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
-            "kss_cheb_step": ([P, c_int, c_int, P, P, P, c_int, c_double, c_double, c_double, c_int], c_int),
-            "kss_apply_H_host": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
-            "kss_apply_H_noalloc": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
-            "kss_solver_create": ([P, c_int, c_int, POINTER(kss_solve_opts), POINTER(c_void_p)], c_int),
-            "kss_solver_destroy": ([P], c_int),
-            "kss_solver_step": ([P, POINTER(c_int)], c_int),
-            "kss_solver_results": ([P, P, P, P, c_int, POINTER(kss_solve_stats)], c_int),
-            "kss_chebfi_solve": ([P, c_int, c_int, POINTER(kss_solve_opts), P, P, c_int, P,
-                                  POINTER(kss_solve_stats)], c_int),
-            "kss_gemm": ([P, c_int, c_int, c_int, c_int, P, c_int, P, c_int, P, c_int, c_double,
-                          c_double, c_double, c_double, c_int], c_int),
-            "kss_solve_batch": ([P, c_int, P, P, P, POINTER(kss_solve_opts), P, P, P], c_int),
-            "kss_server_start": ([P, c_size_t, c_int, POINTER(kss_solve_opts)], c_int),
-            "kss_server_submit": ([P, POINTER(kss_cell), POINTER(kss_atoms), c_int, POINTER(c_uint64)], c_int),
-            "kss_server_pump": ([P, c_double, POINTER(c_int), POINTER(c_int)], c_int),
-            "kss_server_poll": ([P, c_uint64, POINTER(c_int), P, P, POINTER(c_double)], c_int),
-            "kss_server_get_stats": ([P, POINTER(kss_server_stats)], c_int),
-            "kss_server_stop": ([P], c_int),
-            "kss_profile_enable": ([P, c_int], c_int),
-            "kss_profile_count": ([P, POINTER(c_int), POINTER(c_longlong)], c_int),
-            "kss_profile_entry": ([P, c_int, POINTER(c_char_p), POINTER(c_longlong), POINTER(c_double)], c_int),
-        }
-        for name, (args, res) in sig.items():
+        for name, (args, res) in signatures().items():
             if hasattr(L, name):
                 f = getattr(L, name)
                 f.argtypes = args
                 f.restype = res
         _lib = L
     return _lib
+
+
+def signatures() -> dict:
+    """ctypes prototype (argument types, result type) of every C entry point."""
+    P = c_void_p
+    return {
+        "kss_version": ([], c_int),
+        "kss_create": ([POINTER(c_void_p), c_int, c_void_p], c_int),
+        "kss_destroy": ([P], c_int),
+        "kss_last_error": ([P], c_char_p),
+        "kss_setup": ([P, POINTER(kss_cell), POINTER(kss_atoms), POINTER(c_void_p)], c_int),
+        "kss_sys_destroy": ([P], c_int),
+        "kss_sys_info_get": ([P, POINTER(kss_sys_info)], c_int),
+        "kss_sphere": ([P, c_int, POINTER(c_int), POINTER(POINTER(c_int32))], c_int),
+        "kss_get_maps": ([P, c_int, P, P], c_int),
+        "kss_get_tables": ([P, c_int, P, P, P], c_int),
+        "kss_upper_bound": ([P, c_int, POINTER(c_double)], c_int),
+        "kss_footprint": ([P, c_int, c_int, POINTER(c_size_t)], c_int),
+        "kss_apply_H": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
+        "kss_cheb_step": ([P, c_int, c_int, P, P, P, c_int, c_double, c_double, c_double, c_int], c_int),
+        "kss_apply_H_host": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
+        "kss_apply_H_noalloc": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
+        "kss_solver_create": ([P, c_int, c_int, POINTER(kss_solve_opts), POINTER(c_void_p)], c_int),
+        "kss_solver_destroy": ([P], c_int),
+        "kss_solver_step": ([P, POINTER(c_int)], c_int),
+        "kss_solver_results": ([P, P, P, P, c_int, POINTER(kss_solve_stats)], c_int),
+        "kss_chebfi_solve": ([P, c_int, c_int, POINTER(kss_solve_opts), P, P, c_int, P,
+                              POINTER(kss_solve_stats)], c_int),
+        "kss_gemm": ([P, c_int, c_int, c_int, c_int, P, c_int, P, c_int, P, c_int, c_double,
+                      c_double, c_double, c_double, c_int], c_int),
+        "kss_solve_batch": ([P, c_int, P, P, P, POINTER(kss_solve_opts), P, P, P], c_int),
+        "kss_server_start": ([P, c_size_t, c_int, POINTER(kss_solve_opts)], c_int),
+        "kss_server_submit": ([P, POINTER(kss_cell), POINTER(kss_atoms), c_int, POINTER(c_uint64)], c_int),
+        "kss_server_pump": ([P, c_double, POINTER(c_int), POINTER(c_int)], c_int),
+        "kss_server_poll": ([P, c_uint64, POINTER(c_int), P, P, POINTER(c_double)], c_int),
+        "kss_server_get_stats": ([P, POINTER(kss_server_stats)], c_int),
+        "kss_server_stop": ([P], c_int),
+        "kss_profile_enable": ([P, c_int], c_int),
+        "kss_profile_count": ([P, POINTER(c_int), POINTER(c_longlong)], c_int),
+        "kss_profile_entry": ([P, c_int, POINTER(c_char_p), POINTER(c_longlong), POINTER(c_double)], c_int),
+        "kss_apply_S": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
+        "kss_autotune_set": ([P, c_int], c_int),
+        "kss_autotune_count": ([POINTER(c_int)], c_int),
+        "kss_autotune_get": ([c_int, POINTER(kss_tune_entry)], c_int),
+        "kss_autotune_put": ([POINTER(kss_tune_entry)], c_int),
+        "kss_autotune_clear": ([], c_int),
+    }
 
 
 def header_functions(path: str = HEADER):
@@ -211,7 +221,9 @@ class System:
 
 
 def kss_setup(ctx, lattice, ecut, kpts, pos, D, fft_box=(0, 0, 0), vloc_amp=-2.0,
-              vloc_sigma=1.0, nproj_per_atom=4, proj_alpha=0.25) -> System:
+              vloc_sigma=1.0, nproj_per_atom=4, proj_alpha=0.25, Q=None) -> System:
+    """Q: optional overlap coefficients (one per projector): the generalised problem with
+    S = 1 + sum_i |beta_i> q_i <beta_i|."""
     lat = np.ascontiguousarray(np.asarray(lattice, np.float64).reshape(9))
     k = np.ascontiguousarray(np.asarray(kpts, np.float64).reshape(-1, 3))
     p = np.ascontiguousarray(np.asarray(pos, np.float64).reshape(-1, 3))
@@ -230,9 +242,13 @@ def kss_setup(ctx, lattice, ecut, kpts, pos, D, fft_box=(0, 0, 0), vloc_amp=-2.0
     at.nproj_per_atom = int(nproj_per_atom)
     at.proj_alpha = float(proj_alpha)
     at.D = _dptr(d)
+    q = None
+    if Q is not None:
+        q = np.ascontiguousarray(np.asarray(Q, np.float64).reshape(-1))
+        at.Q = _dptr(q)
     h = c_void_p()
     _check(lib().kss_setup(ctx, byref(cell), byref(at), byref(h)), ctx)
-    return System(ctx, h, (k, p, d))
+    return System(ctx, h, (k, p, d, q))
 
 
 def kss_sys_destroy(sys: System):
@@ -294,6 +310,15 @@ def kss_apply_H(sys: System, ik: int, psi, hpsi, prec: int = KSS_PREC_FP64, nb: 
     if (n2, ld2) != (n, ld):
         raise ValueError("psi and hpsi shapes differ")
     _check(lib().kss_apply_H(sys.h, ik, n if nb is None else nb, _ptr(psi), _ptr(hpsi), ld, prec), sys.ctx)
+
+
+def kss_apply_S(sys: System, ik: int, psi, spsi, prec: int = KSS_PREC_FP64):
+    """spsi = S psi (the overlap of a system set up with Q; a copy of psi without one)."""
+    n, ld = _block_dims(psi, prec)
+    n2, ld2 = _block_dims(spsi, prec)
+    if (n2, ld2) != (n, ld):
+        raise ValueError("psi and spsi shapes differ")
+    _check(lib().kss_apply_S(sys.h, ik, n, _ptr(psi), _ptr(spsi), ld, prec), sys.ctx)
 
 
 def kss_apply_H_noalloc(sys: System, ik: int, psi, hpsi, prec: int = KSS_PREC_FP64):

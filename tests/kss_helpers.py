@@ -21,7 +21,7 @@ def setup(ctx, s):
     return K.kss_setup(ctx, s.lattice, s.ecut, s.kpts, s.pos, s.D,
                        fft_box=s.fft_box or (0, 0, 0), vloc_amp=s.vloc_amp,
                        vloc_sigma=s.vloc_sigma, nproj_per_atom=s.nproj_per_atom,
-                       proj_alpha=s.proj_alpha)
+                       proj_alpha=s.proj_alpha, Q=getattr(s, "Q", None))
 
 
 def rel_err_rows(a, b):

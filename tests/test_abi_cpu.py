@@ -18,6 +18,12 @@ def test_exports_every_header_symbol(lib):
     assert not missing, missing
 
 
+def test_every_header_function_has_a_ctypes_prototype():
+    """A function without a prototype would pass 64-bit pointers as C ints."""
+    missing = set(K.header_functions()) - set(K.signatures())
+    assert not missing, sorted(missing)
+
+
 def test_version(lib):
     assert K.kss_version() == 1
 
