@@ -47,26 +47,35 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--nk", type=int, default=0, help="use only the first nk k-points (profiling)")
-    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c2s", "c3", "c4", "c5"], default="c2",
                     help="c2: default FP64 ChebFi iterations; c3/c4/c5: mixed-precision full solves, "
                          "batched and served forms (auxiliary lines)")
     ap.add_argument("--requests", type=int, default=60, help="c5: number of requests")
     args = ap.parse_args()
     if args.degree is None:
-        args.degree = 10 if args.workload == "c2" else 20
+        args.degree = 10 if args.workload in ("c2", "c2s") else 20
+    if args.workload == "c2s":
+        args.no_cpu_baseline = True  # the oracle applies S^-1 by a dense solve: infeasible at npw 34181
     return args
 
 
 # ------------------------------------------------------------------------------------------------
 # workload description (shared by both arms)
 
-def workload():
+def workload(name: str = "c2"):
     import workloads as W
-    s = W.config2()
-    return s
+    return W.config2s(nk=4) if name == "c2s" else W.config2()
 
 
 def workload_name(s, nb, form):
+    if s.Q is not None:
+        return (f"C2S ({form}): the C2 cell (a=20 bohr, Ecut=20 Ha, FFT 96^3, npw=34181/k, "
+                f"{s.nproj} projectors, {s.nband} bands + {nb - s.nband} buffer, {len(s.kpts)} "
+                f"shifted k-points) with the nonlocal overlap S = 1 + sum |beta> q <beta|, "
+                f"q ~ U[0,0.5]; step = one generalised ChebFi iteration (degree-10 filter in "
+                f"S^-1 H + H on the filtered block + FP64 Rayleigh-Ritz with metric Y^H S Y + "
+                f"residuals |Hx - lambda Sx|) on every k-point; a band-apply is one column of "
+                f"S^-1 H psi (filter) or H psi")
     return (f"C2 ({form}): cubic a=20 bohr, Ecut=20 Ha, FFT 96^3, npw=34181/k, 64 atoms x (s,p) = "
             f"{s.nproj} projectors, {s.nband} bands (+{nb - s.nband} buffer), "
             f"{len(s.kpts)} shifted k-points; step = one ChebFi iteration (degree-10 filter + "
@@ -260,7 +269,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # CPU baseline first (rank 0, N = 1 only), before the GPU is busy.
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s0 = workload()
+        s0 = workload(args.workload)
         p = oracle_setup(s0)
         r, n, el = oracle_rate(p, args.cpu_seconds)
         cpu = {"value": r, "unit": "band-applies/s", "cores": cores(), "kind": "oracle",
@@ -270,11 +279,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     B.build()
     stream = torch.cuda.current_stream()
     ctx = K.kss_create(local_rank, stream.cuda_stream)
-    s = workload()
+    s = workload(args.workload)
     prec = K.KSS_PREC_FP64 if args.form == "fp64" else K.KSS_PREC_MIXED
     if args.nk > 0:
         s.kpts = s.kpts[: args.nk]
-    sysh = K.kss_setup(ctx, s.lattice, s.ecut, s.kpts, s.pos, s.D, fft_box=s.fft_box)
+    sysh = K.kss_setup(ctx, s.lattice, s.ecut, s.kpts, s.pos, s.D, fft_box=s.fft_box, Q=s.Q)
     nk = len(s.kpts)
     solvers = []
     for ik in range(nk):
@@ -574,7 +583,7 @@ def run_c5(args):
 
 def main():
     args = parse()
-    if args.workload != "c2" and args.impl == "ours":
+    if args.workload not in ("c2", "c2s") and args.impl == "ours":
         {"c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload](args)
         return
     rank = int(os.environ.get("RANK", "0"))
