@@ -353,6 +353,16 @@ def apply_overlap(c: np.ndarray, beta: np.ndarray, Q: Optional[np.ndarray]) -> n
     return c + apply_nonlocal(c, beta, np.asarray(Q, np.float64))
 
 
+def density(c: np.ndarray, basis: Basis, occ, vol: float) -> np.ndarray:
+    """n(r_j) = sum_n w_n |psi_n(r_j)|^2 on the grid, shape (N3, N2, N1) (Eq. nandtau, §2: w the
+    occupancy times the k-point weight), with psi_n(r) = Omega^-1/2 sum_G c_n(G) e^{i(k+G).r}
+    (the k phase drops out of the modulus)."""
+    c = np.asarray(c, np.complex128)
+    occ = np.asarray(occ, np.float64)
+    psi_r = naive_inverse_dft(scatter_to_box(c, basis))
+    return np.einsum("n,nzyx->zyx", occ, (psi_r * psi_r.conj()).real) / vol
+
+
 def apply_h_dense(c: np.ndarray, H: np.ndarray) -> np.ndarray:
     return np.asarray(c, np.complex128) @ H.T
 

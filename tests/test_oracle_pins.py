@@ -421,3 +421,62 @@ def test_generalized_eigenpairs_invariants(tiny_overlap_problem):
     ws = O.lowest_eigenpairs(H, n)[0]
     assert np.all(w <= np.maximum(ws, 0.0) + 1e-12) and np.all(w >= np.minimum(ws, 0.0) - 1e-12)
     assert np.any(np.abs(w - ws) > 1e-3)  # and the overlap does change them
+
+
+# ---------------------------------------------------------------------------------------------
+# Density after the solve: n(r) = sum w |psi(r)|^2 (Eq. nandtau, §2)
+# ---------------------------------------------------------------------------------------------
+
+def test_density_integral_is_the_occupation(tiny_problem):
+    p = tiny_problem
+    c = W.random_block(p.basis.npw, 3, seed=31)
+    occ = np.array([2.0, 1.0, 0.5])
+    _, vol = O.reciprocal_lattice(W.tiny_system(a=6.5, ecut=2.5, natom=3).lattice)
+    n = O.density(c, p.basis, occ, vol)
+    assert np.all(n >= 0)
+    integral = n.sum() * vol / np.prod(p.basis.box)
+    assert abs(integral - float(occ @ (np.abs(c) ** 2).sum(axis=1))) < 1e-11 * integral
+
+
+def test_density_plane_waves_closed_form(tiny_problem):
+    p = tiny_problem
+    npw = p.basis.npw
+    lat = W.tiny_system(a=6.5, ecut=2.5, natom=3).lattice
+    _, vol = O.reciprocal_lattice(lat)
+    # one plane wave: uniform density w / Omega
+    c1 = np.zeros((1, npw), np.complex128)
+    c1[0, 7] = 1.0
+    n1 = O.density(c1, p.basis, [3.0], vol)
+    assert np.max(np.abs(n1 - 3.0 / vol)) < 1e-13
+    # two plane waves a e^{iG1.r} + b e^{iG2.r}: (|a|^2 + |b|^2 + 2 Re(a conj(b) e^{i(G1-G2).r})) / Omega
+    i1, i2 = 3, 40
+    a, b = 0.6 - 0.2j, -0.3 + 0.7j
+    c2 = np.zeros((1, npw), np.complex128)
+    c2[0, i1], c2[0, i2] = a, b
+    N1, N2, N3 = p.basis.box
+    j3, j2, j1 = np.meshgrid(np.arange(N3), np.arange(N2), np.arange(N1), indexing="ij")
+    dm = p.basis.miller[i1].astype(float) - p.basis.miller[i2].astype(float)
+    phase = 2 * np.pi * (dm[0] * j1 / N1 + dm[1] * j2 / N2 + dm[2] * j3 / N3)
+    expect = (abs(a) ** 2 + abs(b) ** 2 + 2 * np.real(a * np.conj(b) * np.exp(1j * phase))) / vol
+    n2 = O.density(c2, p.basis, [1.0], vol)
+    assert np.max(np.abs(n2 - expect)) < 1e-13
+    # discriminates a sign slip in the transform direction: conj(phase) differs
+    wrong = (abs(a) ** 2 + abs(b) ** 2 + 2 * np.real(a * np.conj(b) * np.exp(-1j * phase))) / vol
+    assert np.max(np.abs(n2 - wrong)) > 1e-3
+
+
+def test_density_time_reversal():
+    """k -> -k with c(-G) = conj(c(G)) gives the same density (psi_-k = conj(psi_k))."""
+    s = W.tiny_system(a=6.0, ecut=2.5, natom=2, kpts=[(0.25, 0.25, -0.25), (-0.25, -0.25, 0.25)])
+    box = (15, 15, 15)
+    b0 = O.make_basis(s.lattice, s.ecut, s.kpts[0], box)
+    b1 = O.make_basis(s.lattice, s.ecut, s.kpts[1], box)
+    c0 = W.random_block(b0.npw, 2, seed=33)
+    idx = {tuple(m): i for i, m in enumerate(b1.miller)}
+    c1 = np.zeros((2, b1.npw), np.complex128)
+    for i, m in enumerate(b0.miller):
+        c1[:, idx[tuple(-m)]] = np.conj(c0[:, i])
+    _, vol = O.reciprocal_lattice(s.lattice)
+    n0 = O.density(c0, b0, [1.0, 2.0], vol)
+    n1 = O.density(c1, b1, [1.0, 2.0], vol)
+    assert np.max(np.abs(n0 - n1)) < 1e-13 * np.max(n0)
