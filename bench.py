@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--nk", type=int, default=0, help="use only the first nk k-points (profiling)")
-    ap.add_argument("--workload", choices=["c2", "c2s", "c3", "c4", "c5"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c2s", "c3", "c4", "c5", "density"], default="c2",
                     help="c2: default FP64 ChebFi iterations; c3/c4/c5: mixed-precision full solves, "
                          "batched and served forms (auxiliary lines)")
     ap.add_argument("--requests", type=int, default=60, help="c5: number of requests")
@@ -519,6 +519,78 @@ def run_c4(args):
                                   sorted(prof.items(), key=lambda kv: -kv[1][1])[:12]}}), flush=True)
 
 
+def run_density(args):
+    """Density build after the solve (Eq. nandtau) on the C2 cell: every k-point's 512 bands
+    (random unit-norm blocks standing in for the converged ones) accumulated into n(r) on 96^3."""
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_2507_08578_gb300.kss as K
+    from paper_2507_08578_gb300 import build as B
+    B.build()
+    s = W.config2()
+    nk = len(s.kpts) if args.nk <= 0 else args.nk
+    prec = K.KSS_PREC_FP64 if args.form == "fp64" else K.KSS_PREC_MIXED
+    cdt = torch.complex128 if prec == K.KSS_PREC_FP64 else torch.complex64
+    ctx = K.kss_create(0, torch.cuda.current_stream().cuda_stream)
+    sysh = K.kss_setup(ctx, s.lattice, s.ecut, s.kpts[:nk], s.pos, s.D, fft_box=s.fft_box)
+    blocks = []
+    for ik in range(nk):
+        npw = K.kss_sphere(sysh, ik).shape[0]
+        g = torch.Generator(device="cuda").manual_seed(90 + ik)
+        x = torch.randn((s.nband, npw), dtype=cdt, device="cuda", generator=g)
+        blocks.append(x / torch.linalg.vector_norm(x, dim=1, keepdim=True))
+    occ = np.full(s.nband, 2.0 / nk)
+    rho = torch.zeros((96, 96, 96), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rho.zero_()
+        for ik in range(nk):
+            K.kss_density_accumulate(sysh, ik, blocks[ik], occ, rho, prec)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    K.kss_profile_enable(ctx, True)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    prof = K.profile_table(ctx)
+    _, launches = K.kss_profile_count(ctx)
+    K.kss_profile_enable(ctx, False)
+    total = float(rho.sum().item()) * (20.0 ** 3) / 96 ** 3
+    bands = s.nband * nk * args.steps
+    # roofline of the density pass: the y and z inverse transforms (2 of the 3 axes) per band
+    name = "density_pass<f64>" if prec == K.KSS_PREC_FP64 else "density_pass<f32>"
+    roof = None
+    if name in prof:
+        l, kms = prof[name]
+        ach = bands * 2 * 5.0 * 96 ** 3 * math.log2(96) / (kms / 1000.0) / 1e12
+        peak = FP64_PEAK_TFLOPS if prec == K.KSS_PREC_FP64 else FP32_PEAK_TFLOPS
+        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "launches": l, "avg_launch_ms": kms / l}
+    K.kss_sys_destroy(sysh)
+    K.kss_destroy(ctx)
+    print(json.dumps({"metric": "band densities/s", "value": bands / (ms / 1000.0), "unit": "bands/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+                      "ms_per_step": ms / args.steps, "higher_is_better": True,
+                      "dtype": "f64" if prec == K.KSS_PREC_FP64 else "c64 (FP64 accumulation)",
+                      "data": "synthetic",
+                      "config": {"workload": f"density n(r) = sum w |psi(r)|^2 on the C2 cell (96^3), "
+                                             f"{nk} k-points x {s.nband} bands per step, inputs resident in HBM"},
+                      "electrons": total, "gpu_launches": launches, "clocks": ck, "roofline": roof,
+                      "kernels": {k: {"launches": v[0], "ms": round(v[1], 2)} for k, v in
+                                  sorted(prof.items(), key=lambda kv: -kv[1][1])}}), flush=True)
+
+
 def run_c5(args):
     import numpy as np
     import torch
@@ -584,7 +656,7 @@ def run_c5(args):
 def main():
     args = parse()
     if args.workload not in ("c2", "c2s") and args.impl == "ours":
-        {"c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload](args)
+        {"c3": run_c3, "c4": run_c4, "c5": run_c5, "density": run_density}[args.workload](args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

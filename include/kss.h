@@ -232,6 +232,21 @@ kss_status kss_gemm(kss_ctx ctx, int op, int M, int N, int K, const void* A, int
                     double beta_im, kss_precision prec);
 
 /* ------------------------------------------------------------------------------------------
+ * Electron density after the solve (Eq. nandtau, §2)
+ * ------------------------------------------------------------------------------------------ */
+
+/* rho[j] += sum_n occ[n] |psi_n(r_j)|^2 on the FFT grid, with psi_n(r) = Omega^-1/2 sum_G
+ * psi_n(G) e^{i(k+G).r} and r_j = sum_i (j_i/N_i) a_i.  psi: DEVICE band-major [nb][ld] of the
+ * precision's type; occ: HOST, nb weights (occupancy times k-point weight; copied); rho: DEVICE
+ * real double [N3][N2][N1] (j1 fastest), accumulated, so a caller sums k-points by calling once
+ * per k-point on a zeroed rho.  Inverse FFTs per band (sphere scatter + x, y, z transforms) in the
+ * precision's arithmetic, |psi|^2 accumulated in FP64 in a fixed order (bitwise reproducible).
+ * Errors: KSS_EINVAL (ik, nb, ld, null pointers, non-finite occ), KSS_ENOTSUP (boxes with
+ * N2 != N3 or a length without a two-codelet split). */
+kss_status kss_density_accumulate(kss_sys sys, int ik, int nb, const void* psi, int ld,
+                                  const double* occ, double* rho, kss_precision prec);
+
+/* ------------------------------------------------------------------------------------------
  * Chebyshev-filtered subspace iteration with Rayleigh-Ritz (§5.1)
  * ------------------------------------------------------------------------------------------ */
 

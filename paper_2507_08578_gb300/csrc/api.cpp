@@ -189,6 +189,10 @@ kss_status kss_create(kss_ctx* out, int device, void* cuda_stream) {
   }
   ctx->stream = (cudaStream_t)cuda_stream;  // NULL: legacy default stream
   ctx->own_stream = false;
+  {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && v > 0) ctx->nsm = v;
+  }
   *out = ctx;
   return KSS_OK;
 }

@@ -114,6 +114,7 @@ struct kss_ctx_s {
   void* server = nullptr;          // request server (server.cu), NULL when not running
   int autotune = 1;                // 1: time FFT schedule candidates at first use (tune.cu)
   kss::DevBuf ws_sapply, ws_e, ws_f; // overlap: L psi block, E = beta^H H psi, F (nproj x nb)
+  kss::DevBuf ws_occ, ws_rho;      // density build: occupations, per-group partial densities
   kss::DevBuf ws_tune;             // scratch slab of the autotuner
 };
 

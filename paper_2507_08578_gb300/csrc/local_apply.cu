@@ -24,6 +24,7 @@
 #include <algorithm>
 
 #include "local_kernels.cuh"
+#include "density.h"
 #include "local_wide.h"
 #include "tune.h"
 
@@ -384,12 +385,12 @@ int chunk_bands(kss_sys s, int ik, int nb, size_t es) {
   return (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, target / per));
 }
 
+// Kernel arguments of the local passes for (system, k-point, band block).
 template <typename T>
-void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, void* out,
-               int ld, ChebCoef c) {
+LocalArgs<T> local_args(kss_sys s, int ik, const void* psi, const void* psi_prev, void* out, int ld,
+                        ChebCoef c) {
   using C = typename CT<T>::C;
   const bool f64 = sizeof(T) == 8;
-  kss_ctx ctx = s->ctx;
   KData& kd = s->k[ik];
   LocalArgs<T> a{};
   a.N1 = s->N[0];
@@ -423,6 +424,16 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
   a.alpha = (T)c.alpha;
   a.beta = (T)c.beta;
   a.gamma = (T)c.gamma;
+  return a;
+}
+
+template <typename T>
+void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, void* out,
+               int ld, ChebCoef c) {
+  using C = typename CT<T>::C;
+  const bool f64 = sizeof(T) == 8;
+  kss_ctx ctx = s->ctx;
+  LocalArgs<T> a = local_args<T>(s, ik, psi, psi_prev, out, ld, c);
   const size_t sa = smem_a(a), sb = smem_b(a);
   const size_t smax = 227 * 1024;
   if (sa > smax || sb > smax)
@@ -597,6 +608,40 @@ void warp_pass_b(kss_ctx ctx, const LocalArgs<T>& a, int nbands) {
 }
 template void warp_pass_b<double>(kss_ctx, const LocalArgs<double>&, int);
 template void warp_pass_b<float>(kss_ctx, const LocalArgs<float>&, int);
+
+template <typename T>
+void pass_a_chunks(kss_sys s, int ik, int nb, const void* psi, int ld,
+                   const std::function<void(const LocalArgs<T>&, int)>& after) {
+  using C = typename CT<T>::C;
+  kss_ctx ctx = s->ctx;
+  LocalArgs<T> a = local_args<T>(s, ik, psi, nullptr, nullptr, ld, ChebCoef{1.0, 0.0, 0.0});
+  RegPlan rp;
+  if (!(choose_split(a.N1, rp.s1) && choose_split(a.N2, rp.s2) && choose_split(a.N3, rp.s3)))
+    fail(KSS_ENOTSUP, "FFT length without a two-codelet split");
+  const int scr_warp = std::max(rp.s1.PP * rp.s1.scr, std::max(rp.s2.PP * rp.s2.scr, rp.s3.PP * rp.s3.scr));
+  const size_t ra = sizeof(C) * ((size_t)a.N1 + (size_t)a.W2 * a.N1p + (size_t)kWarps * scr_warp);
+  if (ra > 227 * 1024) fail(KSS_ENOTSUP, "FFT box too large for the shared-memory pencil tiles");
+  const PassKernels<T> kk = pick_kernels<T>(rp);
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(kk.a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ra));
+  const int nc = chunk_bands(s, ik, nb, sizeof(C));
+  ctx->ws_local.ensure(slab_elems(s, ik) * nc * sizeof(C));
+  a.work = ctx->ws_local.as<C>();
+  static const int ida = prof_register(sizeof(T) == 8 ? "local_pass_a<f64>" : "local_pass_a<f32>");
+  for (int n0 = 0; n0 < nb; n0 += nc) {
+    const int m = std::min(nc, nb - n0);
+    a.n0 = n0;
+    {
+      ProfScope ps(ctx, ida);
+      kk.a<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
+    }
+    after(a, m);
+  }
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+template void pass_a_chunks<double>(kss_sys, int, int, const void*, int,
+                                    const std::function<void(const LocalArgs<double>&, int)>&);
+template void pass_a_chunks<float>(kss_sys, int, int, const void*, int,
+                                   const std::function<void(const LocalArgs<float>&, int)>&);
 
 size_t local_slab_bytes_per_band(kss_sys s, int ik, kss_precision prec) {
   return slab_elems(s, ik) * (prec == KSS_PREC_FP64 ? 16 : 8);

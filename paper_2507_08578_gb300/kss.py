@@ -130,6 +130,7 @@ def signatures() -> dict:
         "kss_profile_count": ([P, POINTER(c_int), POINTER(c_longlong)], c_int),
         "kss_profile_entry": ([P, c_int, POINTER(c_char_p), POINTER(c_longlong), POINTER(c_double)], c_int),
         "kss_apply_S": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
+        "kss_density_accumulate": ([P, c_int, c_int, P, c_int, P, P, c_int], c_int),
         "kss_autotune_set": ([P, c_int], c_int),
         "kss_autotune_count": ([POINTER(c_int)], c_int),
         "kss_autotune_get": ([c_int, POINTER(kss_tune_entry)], c_int),
@@ -319,6 +320,15 @@ def kss_apply_S(sys: System, ik: int, psi, spsi, prec: int = KSS_PREC_FP64):
     if (n2, ld2) != (n, ld):
         raise ValueError("psi and spsi shapes differ")
     _check(lib().kss_apply_S(sys.h, ik, n, _ptr(psi), _ptr(spsi), ld, prec), sys.ctx)
+
+
+def kss_density_accumulate(sys: System, ik: int, psi, occ, rho, prec: int = KSS_PREC_FP64):
+    """rho (device float64 tensor, N3 x N2 x N1) += sum_n occ[n] |psi_n(r)|^2."""
+    n, ld = _block_dims(psi, prec)
+    o = np.ascontiguousarray(np.asarray(occ, np.float64).reshape(-1))
+    if o.size != n:
+        raise ValueError("one occupation per band")
+    _check(lib().kss_density_accumulate(sys.h, ik, n, _ptr(psi), ld, o.ctypes.data, _ptr(rho), prec), sys.ctx)
 
 
 def kss_apply_H_noalloc(sys: System, ik: int, psi, hpsi, prec: int = KSS_PREC_FP64):
