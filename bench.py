@@ -47,13 +47,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--nk", type=int, default=0, help="use only the first nk k-points (profiling)")
-    ap.add_argument("--workload", choices=["c2", "c2s", "c3", "c4", "c5", "density"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c2s", "c3", "c4", "c5", "density", "lobpcg"], default="c2",
                     help="c2: default FP64 ChebFi iterations; c3/c4/c5: mixed-precision full solves, "
                          "batched and served forms (auxiliary lines)")
     ap.add_argument("--requests", type=int, default=60, help="c5: number of requests")
     args = ap.parse_args()
     if args.degree is None:
-        args.degree = 10 if args.workload in ("c2", "c2s") else 20
+        args.degree = 10 if args.workload in ("c2", "c2s", "lobpcg") else 20
     if args.workload == "c2s":
         args.no_cpu_baseline = True  # the oracle applies S^-1 by a dense solve: infeasible at npw 34181
     return args
@@ -591,6 +591,51 @@ def run_density(args):
                                   sorted(prof.items(), key=lambda kv: -kv[1][1])}}), flush=True)
 
 
+def run_lobpcg(args):
+    """ChebFi against LOBPCG (the paper's two GPU eigensolvers) on one k-point of a config-4
+    system (a = 11.6 bohr, Ecut = 19.3 Ha, 60 atoms, 120 bands, npw 6358, box 45^3), FP64 to
+    residual 1e-8: time to solution, iterations and H-applications of each."""
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_2507_08578_gb300.kss as K
+    from paper_2507_08578_gb300 import build as B
+    B.build()
+    s = W.config4(1)[0]
+    ctx = K.kss_create(0, torch.cuda.current_stream().cuda_stream)
+    sysh = K.kss_setup(ctx, s.lattice, s.ecut, s.kpts[:1], s.pos, s.D)
+    out = {}
+    evs = {}
+    for name, fn, deg in (("chebfi", K.kss_chebfi_solve, args.degree), ("lobpcg", K.kss_lobpcg_solve, 0)):
+        opts = K.make_opts(degree=deg or 10, tol=1e-8, seed=11)
+        for _ in range(max(1, args.warmup // 3)):
+            fn(sysh, 0, s.nband, opts)
+        torch.cuda.synchronize()
+        K.kss_profile_enable(ctx, True)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ev, rs, st, _ = fn(sysh, 0, s.nband, opts)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        _, launches = K.kss_profile_count(ctx)
+        K.kss_profile_enable(ctx, False)
+        evs[name] = ev
+        out[name] = {"solves_per_s": 1.0 / dt, "s_per_solve": dt, "iterations": st["iters"],
+                     "band_applies": st["napply"], "max_residual": float(rs.max()),
+                     "gpu_launches": launches // args.steps}
+    K.kss_sys_destroy(sysh)
+    K.kss_destroy(ctx)
+    print(json.dumps({"metric": "eigensolves/s", "value": out["chebfi"]["solves_per_s"],
+                      "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "higher_is_better": True,
+                      "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "one k-point of config-4 system 0 (a=11.6 bohr, Ecut=19.3 Ha, 60 atoms, "
+                                             "240 projectors, 120 bands, npw 6358, 45^3), FP64, residual 1e-8"},
+                      "chebfi": out["chebfi"], "lobpcg": out["lobpcg"],
+                      "lobpcg_over_chebfi_time": out["lobpcg"]["s_per_solve"] / out["chebfi"]["s_per_solve"],
+                      "max_eigenvalue_difference_Ha": float(np.max(np.abs(evs["chebfi"] - evs["lobpcg"])))}),
+          flush=True)
+
+
 def run_c5(args):
     import numpy as np
     import torch
@@ -656,7 +701,8 @@ def run_c5(args):
 def main():
     args = parse()
     if args.workload not in ("c2", "c2s") and args.impl == "ours":
-        {"c3": run_c3, "c4": run_c4, "c5": run_c5, "density": run_density}[args.workload](args)
+        {"c3": run_c3, "c4": run_c4, "c5": run_c5, "density": run_density,
+         "lobpcg": run_lobpcg}[args.workload](args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -297,6 +297,17 @@ kss_status kss_chebfi_solve(kss_sys sys, int ik, int nband, const kss_solve_opts
                             double* evals, void* evecs, int ld, double* resid,
                             kss_solve_stats* stats);
 
+/* LOBPCG, the paper's second GPU eigensolver (§5.1): the lowest nband eigenpairs with the
+ * locally optimal block preconditioned conjugate gradient on one block of nband + nbuffer bands
+ * (Teter-Payne-Allan preconditioner; H applied to the preconditioned residuals only, H X and H P
+ * carried by linear combination; Rayleigh-Ritz in [X W P] by an FP64 generalised eigensolve).
+ * Same arguments and outputs as kss_chebfi_solve (opts.degree ignored; max_iter <= 0 => 500).
+ * FP64 only.  Errors: KSS_ENOTSUP (mixed precision, a system with an overlap), KSS_EINVAL
+ * (3 (nband + nbuffer) > npw), KSS_ENOCONV (outputs still filled), KSS_ENUMERIC. */
+kss_status kss_lobpcg_solve(kss_sys sys, int ik, int nband, const kss_solve_opts* opts,
+                            double* evals, void* evecs, int ld, double* resid,
+                            kss_solve_stats* stats);
+
 /* ------------------------------------------------------------------------------------------
  * Batched solves: many systems / k-points in lockstep (§5.1 batch processing)
  * ------------------------------------------------------------------------------------------ */

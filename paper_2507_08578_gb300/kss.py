@@ -131,6 +131,8 @@ def signatures() -> dict:
         "kss_profile_entry": ([P, c_int, POINTER(c_char_p), POINTER(c_longlong), POINTER(c_double)], c_int),
         "kss_apply_S": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
         "kss_density_accumulate": ([P, c_int, c_int, P, c_int, P, P, c_int], c_int),
+        "kss_lobpcg_solve": ([P, c_int, c_int, POINTER(kss_solve_opts), P, P, c_int, P,
+                              POINTER(kss_solve_stats)], c_int),
         "kss_autotune_set": ([P, c_int], c_int),
         "kss_autotune_count": ([POINTER(c_int)], c_int),
         "kss_autotune_get": ([c_int, POINTER(kss_tune_entry)], c_int),
@@ -425,6 +427,22 @@ def kss_chebfi_solve(sys: System, ik: int, nband: int, opts: kss_solve_opts, eve
     if evecs is not None:
         _, ld = _block_dims(evecs, opts.prec)
     st = lib().kss_chebfi_solve(sys.h, ik, nband, byref(opts), ev.ctypes.data, _ptr(evecs), ld,
+                                rs.ctypes.data, byref(stats))
+    if st == KSS_ENOCONV and allow_noconv:
+        return ev, rs, stats_dict(stats), st
+    _check(st, sys.ctx)
+    return ev, rs, stats_dict(stats), st
+
+
+def kss_lobpcg_solve(sys: System, ik: int, nband: int, opts: kss_solve_opts, evecs=None,
+                     allow_noconv: bool = False):
+    ev = np.zeros(nband)
+    rs = np.zeros(nband)
+    stats = kss_solve_stats()
+    ld = 0
+    if evecs is not None:
+        _, ld = _block_dims(evecs, opts.prec)
+    st = lib().kss_lobpcg_solve(sys.h, ik, nband, byref(opts), ev.ctypes.data, _ptr(evecs), ld,
                                 rs.ctypes.data, byref(stats))
     if st == KSS_ENOCONV and allow_noconv:
         return ev, rs, stats_dict(stats), st
