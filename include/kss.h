@@ -167,6 +167,14 @@ kss_status kss_footprint(kss_sys sys, int nband, kss_precision prec, size_t* byt
 kss_status kss_apply_H(kss_sys sys, int ik, int nb, const void* psi, void* hpsi, int ld,
                        kss_precision prec);
 
+/* kss_apply_H for real-space-real bands at k = 0 (psi(-G) = conj psi(G) for every band, the
+ * caller's guarantee): two bands per complex FFT (psi_a + i psi_b), then
+ * H psi_a = T psi_a + (F(G) + conj F(-G))/2 + nonlocal, H psi_b = T psi_b + (F(G) - conj F(-G))/2i
+ * + nonlocal, F the transform of V (psi_a + i psi_b) (the time-reversal economy the paper notes for
+ * Gamma, §6).  Same arguments as kss_apply_H; KSS_EINVAL if k-point ik is not Gamma. */
+kss_status kss_apply_H_gamma(kss_sys sys, int ik, int nb, const void* psi, void* hpsi, int ld,
+                             kss_precision prec);
+
 /* spsi = S(k_ik) psi = psi + beta (Q (beta^H psi)): the overlap of a system set up with Q
  * (spsi = psi without it).  Same layout and rules as kss_apply_H. */
 kss_status kss_apply_S(kss_sys sys, int ik, int nb, const void* psi, void* spsi, int ld,
@@ -260,7 +268,14 @@ typedef struct {
   const void* x0;          /* optional DEVICE warm start, band-major [nb_x0][x0_ld], prec type */
   int x0_nb;               /* bands in x0 (<= nband+nbuffer; the rest are random) */
   int x0_ld;
+  int flags;               /* KSS_SOLVE_* bits, 0 for the defaults */
 } kss_solve_opts;
+
+/* At k = 0 (Gamma) the solvers keep the bands real in real space, psi(-G) = conj psi(G) (the
+ * start block and warm starts are symmetrised, Rayleigh-Ritz rotations are real), and the
+ * ChebFi filter packs two bands per complex FFT (psi_a + i psi_b), halving the FFT work (the
+ * time-reversal economy the paper notes for Gamma, §6).  This flag turns that off. */
+#define KSS_SOLVE_NO_GAMMA_REAL 1
 
 typedef struct {
   int iters;               /* filter iterations done */
@@ -307,6 +322,22 @@ kss_status kss_chebfi_solve(kss_sys sys, int ik, int nband, const kss_solve_opts
 kss_status kss_lobpcg_solve(kss_sys sys, int ik, int nband, const kss_solve_opts* opts,
                             double* evals, void* evecs, int ld, double* resid,
                             kss_solve_stats* stats);
+
+/* RMM-DIIS refinement (§5.1: residual minimisation with direct inversion in the iterative
+ * subspace, Kresse & Furthmueller): from trial vectors (opts->x0, at least nband bands; the rest
+ * of the nband + nbuffer block is random), repeated sweeps of three per-band steps
+ * psi_(j+1) = psibar_j + lambda K R(psibar_j), psibar_j the combination of the band's trials with
+ * least residual norm (coefficients summing to one), lambda the optimal step of the first step, K
+ * the Teter-Payne-Allan preconditioner, followed by one Rayleigh-Ritz (a single Cholesky
+ * orthonormalisation) per sweep.  It converges to the eigenvectors nearest the trial vectors, so
+ * the trial block must already resolve the wanted states (e.g. a solve at a loose tolerance or a
+ * nearby system), and should cover the whole block (x0_nb = nband + nbuffer): random buffer bands
+ * slow the convergence of the top of the window to a crawl.  Same outputs as kss_chebfi_solve (stats.iters = sweeps; max_iter <= 0 => 100).
+ * FP64 only.  Errors: KSS_EINVAL (no x0 or x0_nb < nband), KSS_ENOTSUP (mixed precision, an
+ * overlap), KSS_ENOCONV (outputs still filled), KSS_ENUMERIC. */
+kss_status kss_rmmdiis_solve(kss_sys sys, int ik, int nband, const kss_solve_opts* opts,
+                             double* evals, void* evecs, int ld, double* resid,
+                             kss_solve_stats* stats);
 
 /* ------------------------------------------------------------------------------------------
  * Batched solves: many systems / k-points in lockstep (§5.1 batch processing)

@@ -8,6 +8,7 @@
 #include <new>
 #include <algorithm>
 #include <memory>
+#include <unordered_map>
 
 #include "kss_internal.h"
 
@@ -349,6 +350,24 @@ kss_status kss_setup(kss_ctx ctx, const kss_cell* cell, const kss_atoms* atoms, 
     // Per-k tables.
     for (auto& kd : s->k) {
       const int npw = kd.npw;
+      // Gamma point: the sphere is symmetric under m -> -m (q -> -q exactly); the index of -m
+      // lets real-space-real bands be packed two per complex FFT
+      kd.gamma = kd.kred[0] == 0.0 && kd.kred[1] == 0.0 && kd.kred[2] == 0.0;
+      if (kd.gamma) {
+        std::unordered_map<long long, int> at;
+        auto key = [](int a, int b, int c) {
+          return ((long long)(a + 4096) << 26) | ((long long)(b + 4096) << 13) | (long long)(c + 4096);
+        };
+        for (int g = 0; g < npw; ++g) at[key(kd.miller[3 * g], kd.miller[3 * g + 1], kd.miller[3 * g + 2])] = g;
+        std::vector<int32_t> mir(npw);
+        for (int g = 0; g < npw; ++g) {
+          auto it = at.find(key(-kd.miller[3 * g], -kd.miller[3 * g + 1], -kd.miller[3 * g + 2]));
+          KSS_REQUIRE(it != at.end(), "Gamma-point sphere not symmetric (internal)");
+          mir[g] = it->second;
+        }
+        kd.d_mirror.alloc((size_t)npw * 4);
+        KSS_CHECK_CUDA(cudaMemcpy(kd.d_mirror.p, mir.data(), (size_t)npw * 4, cudaMemcpyHostToDevice));
+      }
       std::vector<int32_t> off(npw), tile(npw);
       std::vector<double> kin(npw), q(3 * npw);
       std::vector<float> kin32(npw);
@@ -504,6 +523,19 @@ kss_status kss_cheb_step(kss_sys sys, int ik, int nb, const void* psi, const voi
     KSS_CHECK_CUDA(cudaSetDevice(sys->ctx->device));
     apply_filter_op(sys, ik, nb, psi, psi_prev, out, ld, ChebCoef{alpha, beta, psi_prev ? gamma : 0.0},
                     prec);
+  });
+}
+
+kss_status kss_apply_H_gamma(kss_sys sys, int ik, int nb, const void* psi, void* hpsi, int ld,
+                             kss_precision prec) {
+  if (!sys) return KSS_EINVAL;
+  return guard(sys->ctx, [&] {
+    KSS_REQUIRE(ik >= 0 && ik < (int)sys->k.size(), "k-point index out of range");
+    KSS_REQUIRE(sys->k[ik].gamma, "kss_apply_H_gamma needs the Gamma point");
+    KSS_CHECK_CUDA(cudaSetDevice(sys->ctx->device));
+    ChebCoef c{1.0, 0.0, 0.0};
+    c.packed = true;
+    apply_h(sys, ik, nb, psi, nullptr, hpsi, ld, c, prec);
   });
 }
 

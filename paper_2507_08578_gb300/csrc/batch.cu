@@ -781,6 +781,7 @@ extern "C" kss_status kss_solve_batch(kss_ctx ctx, int n, const kss_sys* sys, co
         fail(KSS_ENOTSUP, "batched solves take systems without an overlap (solve generalised problems per system)");
       kss_solve_opts ou = o;
       ou.seed = o.seed + (uint64_t)u;
+      ou.flags |= KSS_SOLVE_NO_GAMMA_REAL;  // the grouped passes do not pack Gamma bands
       kss_solver s = nullptr;
       const kss_status st = kss_solver_create(sys[u], ik[u], nband[u], &ou, &s);
       if (st != KSS_OK) fail(st, ctx->err);

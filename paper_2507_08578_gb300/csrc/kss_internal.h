@@ -75,6 +75,8 @@ struct KData {
   double bound = 0;                // rigorous spectral upper bound of H
   double bound_f = 0;              // same for the filter operator (H, or S^-1 H with an overlap)
   std::vector<double> beta_norm2;  // |beta_i|^2 per projector
+  bool gamma = false;              // k = 0: the sphere is symmetric under G -> -G
+  DevBuf d_mirror;                 // Gamma only: sphere index of -G for every G
   DevBuf d_G64, d_G32;             // overlap only: projector Gram matrix beta^H beta, nproj^2
   DevBuf d_W64, d_W32;             // overlap only: W = Q (1 + G Q)^-1, so S^-1 = 1 - beta W beta^H
 };
@@ -115,6 +117,7 @@ struct kss_ctx_s {
   int autotune = 1;                // 1: time FFT schedule candidates at first use (tune.cu)
   kss::DevBuf ws_sapply, ws_e, ws_f; // overlap: L psi block, E = beta^H H psi, F (nproj x nb)
   kss::DevBuf ws_occ, ws_rho;      // density build: occupations, per-group partial densities
+  kss::DevBuf ws_gpack;            // Gamma-packed raw transforms (pairs x ld)
   kss::DevBuf ws_tune;             // scratch slab of the autotuner
 };
 
@@ -153,6 +156,7 @@ struct kss_solver_s {
   kss::DevBuf S32, Hs32, Q32;
   kss::DevBuf r64[4];  // FP64 refinement blocks (mixed precision)
   kss::DevBuf sblk, sblk64;  // overlap only: S Y, then S X (solver precision / FP64 refinement)
+  kss::DevBuf Sr, Hr;        // Gamma only: real parts of the pencil for the real eigensolve
   int lwork = 0;
   std::vector<double> evals, resid;
   int iter = 0;
@@ -161,6 +165,7 @@ struct kss_solver_s {
   double ms_filter = 0, ms_rr = 0, ms_total = 0;
   std::vector<double> hist;  // max wanted residual per iteration
   double* hpin = nullptr;    // pinned host: evals[nb], resid[nb], info (as double) for async RR
+  bool gamma = false;        // Gamma point with real-space-real bands (packed FFTs, real RR)
   bool gram64 = false;       // mixed precision: Gram matrices accumulated in FP64 (after a failed
                              // Cholesky of the FP32-accumulated ones)
   ~kss_solver_s();
@@ -195,6 +200,7 @@ void convert_f64_to_f32(const double* in, float* out, size_t n, cudaStream_t st)
 // ---- local part + H application (local_apply.cu) ----
 struct ChebCoef {
   double alpha, beta, gamma;
+  bool packed = false;  // Gamma point, real-space-real bands: two bands per complex FFT
 };
 // out = alpha*(T psi + V psi + nonlocal psi) + beta*psi + gamma*psi_prev (psi_prev may be null)
 void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, void* out, int ld,

@@ -301,6 +301,42 @@ __global__ void __launch_bounds__(kThreads) pass_c(LocalArgs<T> a) {
   }
 }
 
+// Gamma point: F = FT(V psi_a) + i FT(V psi_b) for the pair (a, b) = (2p, 2p+1) of real-space-real
+// bands; the two transforms of real functions separate as
+//   V psi_a(G) = (F(G) + conj F(-G)) / 2,   V psi_b(G) = (F(G) - conj F(-G)) / (2i),
+// then out = alpha (T psi + V psi) + beta psi + gamma psi_prev (psi_prev may alias out).
+template <typename C, typename T>
+__global__ void gamma_unpack(const C* __restrict__ F, long long ld, const int* __restrict__ mirror,
+                             const C* __restrict__ psi, const C* psi_prev, C* out, const T* __restrict__ kin,
+                             int npw, int nb, T al, T be, T ga) {
+  const long long n = (long long)npw * nb;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / npw), g = (int)(i - (long long)b * npw);
+    const C* f = F + (size_t)(b >> 1) * ld;
+    const C x = f[g], y = f[mirror[g]];
+    C v;
+    if ((b & 1) == 0) {
+      v.x = (T)0.5 * (x.x + y.x);
+      v.y = (T)0.5 * (x.y - y.y);
+    } else {
+      v.x = (T)0.5 * (x.y + y.y);
+      v.y = (T)0.5 * (y.x - x.x);
+    }
+    const C p = psi[(size_t)b * ld + g];
+    const T t = kin[g];
+    C o;
+    o.x = al * (t * p.x + v.x) + be * p.x;
+    o.y = al * (t * p.y + v.y) + be * p.y;
+    if (psi_prev) {
+      const C q = psi_prev[(size_t)b * ld + g];
+      o.x += ga * q.x;
+      o.y += ga * q.y;
+    }
+    out[(size_t)b * ld + g] = o;
+  }
+}
+
 template <typename T, class Pol = RtPol>
 __global__ void __launch_bounds__(kThreads) pass_a_r(LocalArgs<T> a, RegPlan rp, int scr_warp) {
   pass_a_body<T, Pol>(a, rp, scr_warp, blockIdx.x, blockIdx.y);
@@ -463,8 +499,20 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
       static const int ida = prof_register(f64 ? "local_pass_a<f64>" : "local_pass_a<f32>");
       static const int idb = prof_register(f64 ? "local_pass_b<f64>" : "local_pass_b<f32>");
       static const int idc = prof_register(f64 ? "local_pass_c<f64>" : "local_pass_c<f32>");
-      for (int n0 = 0; n0 < nb; n0 += nc) {
-        const int m = std::min(nc, nb - n0);
+      // Gamma point with real-space-real bands: the passes run over band pairs
+      const KData& kd = s->k[ik];
+      const bool packed = c.packed && kd.gamma && nb >= 2;
+      int units = nb;
+      if (packed) {
+        units = (nb + 1) / 2;
+        ctx->ws_gpack.ensure((size_t)units * ld * sizeof(C));
+        a.packed = 1;
+        a.nbands = nb;
+        a.out = ctx->ws_gpack.as<C>();
+        a.psi_prev = nullptr;
+      }
+      for (int n0 = 0; n0 < units; n0 += nc) {
+        const int m = std::min(nc, units - n0);
         a.n0 = n0;
         {
           ProfScope ps(ctx, ida);
@@ -478,6 +526,15 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
           ProfScope ps(ctx, idc);
           kk.c<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
         }
+      }
+      if (packed) {
+        static const int idu = prof_register(f64 ? "gamma_unpack<f64>" : "gamma_unpack<f32>");
+        ProfScope ps(ctx, idu);
+        const long long n = (long long)kd.npw * nb;
+        const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 32);
+        gamma_unpack<C, T><<<blocks, 256, 0, ctx->stream>>>(
+            ctx->ws_gpack.as<C>(), ld, kd.d_mirror.as<int>(), (const C*)psi, (const C*)psi_prev, (C*)out,
+            (const T*)(f64 ? kd.d_kin64.p : kd.d_kin32.p), kd.npw, nb, (T)c.alpha, (T)c.beta, (T)c.gamma);
       }
       KSS_CHECK_CUDA(cudaGetLastError());
       return;

@@ -42,6 +42,10 @@ struct LocalArgs {
   int n0;
   T alpha, beta, gamma;
   const T* coef;  // when set: alpha, beta, gamma read from device memory (graph replays)
+  int packed;     // Gamma point: "band" n of the passes is the pair (2n, 2n+1) packed as
+                  // psi_2n + i psi_2n+1 (real-space-real bands); pass C then stores the raw
+                  // transform (no epilogue) and a separate kernel unpacks
+  int nbands;     // bands in psi (packed mode: the last pair may hold one band)
 };
 
 template <typename C>
@@ -305,8 +309,22 @@ __device__ __forceinline__ void pass_a_body(const LocalArgs<T>& a, const RegPlan
   for (int i = threadIdx.x; i < tsz; i += kThreads) tile[i] = C{0, 0};
   __syncthreads();
   const int g0 = a.zstart[u3], g1 = a.zstart[u3 + 1];
-  const C* ps = a.psi + n * a.ld;
-  for (int g = g0 + threadIdx.x; g < g1; g += kThreads) tile[a.tileidx[g]] = ps[g];
+  if (a.packed) {
+    const C* pa = a.psi + (size_t)(2 * n) * a.ld;
+    const C* pb = 2 * n + 1 < a.nbands ? pa + a.ld : nullptr;
+    for (int g = g0 + threadIdx.x; g < g1; g += kThreads) {
+      C x = pa[g];
+      if (pb) {
+        const C y = pb[g];  // x + i y
+        x.x -= y.y;
+        x.y += y.x;
+      }
+      tile[a.tileidx[g]] = x;
+    }
+  } else {
+    const C* ps = a.psi + n * a.ld;
+    for (int g = g0 + threadIdx.x; g < g1; g += kThreads) tile[a.tileidx[g]] = ps[g];
+  }
   __syncthreads();
   const int r0 = a.rowrange[2 * u3], r1 = a.rowrange[2 * u3 + 1];
   const int nrows = r1 - r0 + 1;
@@ -432,6 +450,11 @@ __device__ __forceinline__ void pass_c_body(const LocalArgs<T>& a, const RegPlan
   }
   __syncthreads();
   const int g0 = a.zstart[u3], g1 = a.zstart[u3 + 1];
+  if (a.packed) {  // raw transform of the pair; unpacked and finished by gamma_unpack
+    C* po = a.out + n * a.ld;
+    for (int g = g0 + threadIdx.x; g < g1; g += kThreads) po[g] = tile[a.tileidx[g]];
+    return;
+  }
   const C* ps = a.psi + n * a.ld;
   const C* pp = a.psi_prev ? a.psi_prev + n * a.ld : nullptr;
   const T al = a.coef ? a.coef[0] : a.alpha;
@@ -454,7 +477,6 @@ __device__ __forceinline__ void pass_c_body(const LocalArgs<T>& a, const RegPlan
   }
 }
 
-// Best two-factor split N = A*B over the codelet sizes (fewest warp instructions per pencil).
 // Pass B with every transform stage spread over the whole CTA.  The per-warp pencil forms above
 // give each pencil max(A, B) lanes, so a stage of size min(A, B) leaves lanes idle (for 96 = 8 x
 // 12, a third of the lanes in stage 1 and half in stage 2).  Here each stage is one loop over all
@@ -634,6 +656,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   }
 }
 
+// Best two-factor split N = A*B over the codelet sizes (fewest warp instructions per pencil).
 inline bool choose_split(int N, Split& out) {
   static const int S[] = {1, 2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16};
   double best = 1e30;

@@ -137,6 +137,7 @@ struct Server {
             r.warm = true;
           }
           kss_solver s = nullptr;
+          o.flags |= KSS_SOLVE_NO_GAMMA_REAL;  // the lockstep engine does not pack Gamma bands
           st = kss_solver_create(r.sys, ik, r.nband, &o, &s);
           if (st != KSS_OK) fail(st, ctx->err);
           r.solvers.push_back(s);

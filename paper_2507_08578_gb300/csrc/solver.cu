@@ -82,6 +82,39 @@ __global__ void residual_kernel(const C* __restrict__ X, const C* __restrict__ H
   if (threadIdx.x == 0) r[n] = sqrt(red[0]);
 }
 
+// Gamma point: c(G) <- (c(G) + conj c(-G)) / 2 for every band (the component at G = 0 made real);
+// the thread of the smaller index of each pair writes both.
+template <typename C>
+__global__ void gamma_symmetrize(C* X, const int* __restrict__ mirror, int npw, int nb, long long ld) {
+  const long long n = (long long)npw * nb;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / npw), g = (int)(i - (long long)b * npw);
+    const int m = mirror[g];
+    C* x = X + (size_t)b * ld;
+    if (g < m) {
+      const C p = x[g], q = x[m];
+      C r;
+      r.x = (p.x + q.x) * 0.5f;
+      r.y = (p.y - q.y) * 0.5f;
+      x[g] = r;
+      r.y = -r.y;
+      x[m] = r;
+    } else if (g == m) {
+      x[g].y = 0;
+    }
+  }
+}
+
+__global__ void real_part(const double2* __restrict__ in, double* __restrict__ out, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[i].x;
+}
+__global__ void real_to_complex(const double* __restrict__ in, double2* __restrict__ out, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_double2(in[i], 0.0);
+}
+
 __global__ void c64_to_c128(const float2* __restrict__ in, double2* __restrict__ out, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) out[i] = make_double2(in[i].x, in[i].y);
@@ -171,8 +204,37 @@ namespace {
 
 size_t esize(bool f64) { return f64 ? 16 : 8; }
 
+// Gamma point: the pencil of real-space-real blocks is real symmetric; a real eigensolve gives a
+// real rotation Q, which keeps the rotated bands real in real space (a complex eigensolver may
+// return each eigenvector with an arbitrary complex phase).
+void subspace_eig_real(kss_solver_s* s, kss_ctx ctx) {
+  cusolverDnHandle_t h = solver_handle(ctx);
+  const int nb = s->nb;
+  const long long nn = (long long)nb * nb;
+  s->Sr.ensure((size_t)nn * 8);
+  s->Hr.ensure((size_t)nn * 8);
+  real_part<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->S.as<double2>(), s->Sr.as<double>(), nn);
+  real_part<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hs.as<double2>(), s->Hr.as<double>(), nn);
+  int lwork = 0;
+  if (cusolverDnDsygvd_bufferSize(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nb,
+                                  s->Hr.as<double>(), nb, s->Sr.as<double>(), nb, s->W.as<double>(),
+                                  &lwork) != CUSOLVER_STATUS_SUCCESS)
+    fail(KSS_ECUDA, "cusolverDnDsygvd_bufferSize failed");
+  s->work.ensure((size_t)std::max(lwork, 1) * sizeof(double));
+  if (cusolverDnDsygvd(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nb,
+                       s->Hr.as<double>(), nb, s->Sr.as<double>(), nb, s->W.as<double>(), s->work.as<double>(),
+                       lwork, s->info.as<int>()) != CUSOLVER_STATUS_SUCCESS)
+    fail(KSS_ECUDA, "cusolverDnDsygvd failed");
+  real_to_complex<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hr.as<double>(), s->Hs.as<double2>(), nn);
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
 // FP64 generalised eigensolve of (Hs, S) in place: Hs <- Q with Q^H S Q = I, W <- eigenvalues.
 void subspace_eig(kss_solver_s* s, kss_ctx ctx) {
+  if (s->gamma) {
+    subspace_eig_real(s, ctx);
+    return;
+  }
   cusolverDnHandle_t h = solver_handle(ctx);
   const int nb = s->nb;
   int lwork = 0;
@@ -230,7 +292,7 @@ void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo
       c64_to_c128<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hs32.as<float2>(), s->Hs.as<double2>(), nn);
     }
   }
-  subspace_eig(s, ctx);
+  subspace_eig(s, ctx);  // real symmetric at Gamma (real-space-real blocks)
   if (f64) {
     gemm_nn(ctx, true, npw, nb, nb, Y, npw, s->Hs.p, nb, Xo, npw, 1, 0, 0, 0, "rotate");
     gemm_nn(ctx, true, npw, nb, nb, HY, npw, s->Hs.p, nb, HXo, npw, 1, 0, 0, 0, "rotate");
@@ -296,8 +358,26 @@ void rayleigh_ritz(kss_solver_s* s, bool f64, const void* Y, const void* HY, voi
   rr_finish_or_retry(s, f64, Y, HY, Xo, HXo);
 }
 
+// Gamma point: re-project X and H X onto real-space-real bands after every Rayleigh-Ritz.  The
+// packed local part returns exactly symmetric output, but the nonlocal products and the
+// recurrence carry the rounding-level asymmetry of their inputs forward and the filter amplifies
+// it (about 5x per iteration); without the projection it reaches the residual level and stalls
+// convergence.
+void gamma_fix(kss_solver_s* s, bool f64, void* X, void* HX) {
+  if (!s->gamma) return;
+  kss_ctx ctx = s->sys->ctx;
+  const long long n = (long long)s->npw * s->nb;
+  const unsigned bl = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 32);
+  const int* mir = s->sys->k[s->ik].d_mirror.as<int>();
+  for (void* b : {X, HX}) {
+    if (f64) gamma_symmetrize<double2><<<bl, 256, 0, ctx->stream>>>((double2*)b, mir, s->npw, s->nb, s->npw);
+    else gamma_symmetrize<float2><<<bl, 256, 0, ctx->stream>>>((float2*)b, mir, s->npw, s->nb, s->npw);
+  }
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
 void apply_block(kss_solver_s* s, bool f64, const void* psi, void* out) {
-  apply_h(s->sys, s->ik, s->nb, psi, nullptr, out, s->npw, ChebCoef{1, 0, 0},
+  apply_h(s->sys, s->ik, s->nb, psi, nullptr, out, s->npw, ChebCoef{1, 0, 0, s->gamma},
           f64 ? KSS_PREC_FP64 : KSS_PREC_MIXED);
   s->napply += s->nb;
 }
@@ -347,7 +427,7 @@ int chebyshev_filter(kss_solver_s* s, int f1, int* prev_out) {
   {
     const double al = sigma1 / e;
     apply_filter_op(s->sys, s->ik, nb, s->blk[cur].p, nullptr, s->blk[prev].p, s->npw,
-                    ChebCoef{al, -al * c, 0.0}, p);
+                    ChebCoef{al, -al * c, 0.0, s->gamma}, p);
     s->napply += nb;
     std::swap(cur, prev);  // cur = Y_1, prev = X
   }
@@ -358,7 +438,7 @@ int chebyshev_filter(kss_solver_s* s, int f1, int* prev_out) {
     const double al = 2.0 * sn / e;
     // Y_j = (2 sn / e)(H - c) Y_{j-1} - sigma sn Y_{j-2}, written over Y_{j-2}
     apply_filter_op(s->sys, s->ik, nb, s->blk[cur].p, s->blk[prev].p, s->blk[prev].p, s->npw,
-                    ChebCoef{al, -al * c, -sigma * sn}, p);
+                    ChebCoef{al, -al * c, -sigma * sn, s->gamma}, p);
     s->napply += nb;
     std::swap(cur, prev);
     sigma = sn;
@@ -403,6 +483,7 @@ void solver_step(kss_solver_s* s) {
     apply_block(s, s->f64, s->blk[0].p, s->blk[1].p);
     const auto t1 = std::chrono::steady_clock::now();
     rayleigh_ritz(s, s->f64, s->blk[0].p, s->blk[1].p, s->blk[2].p, s->blk[3].p);
+    gamma_fix(s, s->f64, s->blk[2].p, s->blk[3].p);
     s->ix = 2;
     s->ihx = 3;
     s->started = true;
@@ -419,6 +500,7 @@ void solver_step(kss_solver_s* s) {
     const auto t1 = std::chrono::steady_clock::now();
     s->ms_filter += std::chrono::duration<double, std::milli>(t1 - t0).count();
     rayleigh_ritz(s, s->f64, s->blk[y].p, s->blk[prev].p, s->blk[fr[1]].p, s->blk[s->ihx].p);
+    gamma_fix(s, s->f64, s->blk[fr[1]].p, s->blk[s->ihx].p);
     s->ix = fr[1];
     s->iter += 1;
     s->ms_rr += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
@@ -514,6 +596,18 @@ kss_status kss_solver_create(kss_sys sys, int ik, int nband, const kss_solve_opt
     if (nx < s->nb)
       random_block(ctx, s->f64, (char*)s->blk[0].p + (size_t)nx * s->npw * esize(s->f64), s->npw,
                    s->nb - nx, s->npw, o.seed, nx);
+    s->gamma = sys->k[ik].gamma && !sys->has_S && !(o.flags & KSS_SOLVE_NO_GAMMA_REAL);
+    if (s->gamma) {
+      const long long n = (long long)s->npw * s->nb;
+      const unsigned bl = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 32);
+      if (s->f64)
+        gamma_symmetrize<double2><<<bl, 256, 0, ctx->stream>>>(s->blk[0].as<double2>(),
+                                                               sys->k[ik].d_mirror.as<int>(), s->npw, s->nb, s->npw);
+      else
+        gamma_symmetrize<float2><<<bl, 256, 0, ctx->stream>>>(s->blk[0].as<float2>(),
+                                                              sys->k[ik].d_mirror.as<int>(), s->npw, s->nb, s->npw);
+      KSS_CHECK_CUDA(cudaGetLastError());
+    }
     s->o.x0 = nullptr;  // copied; the caller's buffer is not referenced again
     sys->nsolvers += 1;
     *out = s.release();

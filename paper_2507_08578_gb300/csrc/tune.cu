@@ -1,10 +1,10 @@
 // Autotuner of the FFT radix schedule of pass B (the y/z transforms of the local-potential path,
 // §5.1 batched FFTs).  For a box length N = N2 = N3 the candidates are the CTA-wide form with
 // every compile-time split N = A * B at 256 and 384 threads per CTA, and the per-warp form.  Each
-// candidate runs one warm-up and three timed launches on a zero-filled scratch slab of the same
-// window (CUDA events on the context's stream); the fastest is kept for the process in a table
-// keyed by device, precision, box and window.  All candidates compute the same transform; they
-// differ only in rounding order.
+// candidate runs one warm-up and three timed launches (the fastest counts) on a zero-filled
+// scratch slab of the same window and of the production chunk size (CUDA events on the context's
+// stream); the fastest candidate is kept for the process in a table keyed by device, precision,
+// box and window.  All candidates compute the same transform; they differ only in rounding order.
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -65,8 +65,10 @@ PassBSched pass_b_schedule(kss_ctx ctx, const lk::LocalArgs<T>& a, const fftr::S
         if (ab.first * ab.second == a.N2 && wide_pass_b<T>(t, ab.first, ab.second, nt, 0, nullptr, true))
           cand.push_back(PassBSched{ab.first, ab.second, nt, 0, 0});
   cand.push_back(PassBSched{s2.A, s2.B, 0, 0, 0});
-  // scratch slab: enough bands for a few waves of CTAs on every SM
-  const int nbt = std::max(1, std::min(16, (4 * std::max(ctx->nsm, 1) + a.N1 - 1) / a.N1));
+  // scratch slab of the production chunk size (the local passes keep about 64 MB of slab per
+  // launch), so that candidates are timed at the launch shape they will run at
+  const size_t per_band = (size_t)t.N1 * t.W3 * t.W2 * sizeof(C);
+  const int nbt = (int)std::max<size_t>(1, std::min<size_t>(64, (64ull << 20) / per_band));
   const size_t elems = (size_t)t.N1 * t.W3 * t.W2 * nbt;
   ctx->ws_tune.ensure(elems * sizeof(C));
   KSS_CHECK_CUDA(cudaMemsetAsync(ctx->ws_tune.p, 0, elems * sizeof(C), ctx->stream));
@@ -81,14 +83,18 @@ PassBSched pass_b_schedule(kss_ctx ctx, const lk::LocalArgs<T>& a, const fftr::S
   };
   int best = -1;
   for (size_t i = 0; i < cand.size(); ++i) {
-    launch(cand[i]);
-    KSS_CHECK_CUDA(cudaEventRecord(e0, ctx->stream));
-    for (int r = 0; r < 3; ++r) launch(cand[i]);
-    KSS_CHECK_CUDA(cudaEventRecord(e1, ctx->stream));
-    KSS_CHECK_CUDA(cudaEventSynchronize(e1));
-    float ms = 0;
-    KSS_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    cand[i].ms = ms / 3.0;
+    launch(cand[i]);  // warm-up (and shared-memory attribute)
+    double tmin = 1e300;
+    for (int r = 0; r < 3; ++r) {  // the fastest of three timed launches
+      KSS_CHECK_CUDA(cudaEventRecord(e0, ctx->stream));
+      launch(cand[i]);
+      KSS_CHECK_CUDA(cudaEventRecord(e1, ctx->stream));
+      KSS_CHECK_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      KSS_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      tmin = std::min(tmin, (double)ms);
+    }
+    cand[i].ms = tmin;
     if (best < 0 || cand[i].ms < cand[best].ms) best = (int)i;
   }
   KSS_CHECK_CUDA(cudaEventDestroy(e0));

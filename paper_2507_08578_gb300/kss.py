@@ -51,7 +51,7 @@ class kss_sys_info(ctypes.Structure):
 class kss_solve_opts(ctypes.Structure):
     _fields_ = [("degree", c_int), ("tol", c_double), ("max_iter", c_int), ("nbuffer", c_int),
                 ("prec", c_int), ("seed", c_uint64), ("x0", c_void_p), ("x0_nb", c_int),
-                ("x0_ld", c_int)]
+                ("x0_ld", c_int), ("flags", c_int)]
 
 
 class kss_server_stats(ctypes.Structure):
@@ -130,9 +130,12 @@ def signatures() -> dict:
         "kss_profile_count": ([P, POINTER(c_int), POINTER(c_longlong)], c_int),
         "kss_profile_entry": ([P, c_int, POINTER(c_char_p), POINTER(c_longlong), POINTER(c_double)], c_int),
         "kss_apply_S": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
+        "kss_apply_H_gamma": ([P, c_int, c_int, P, P, c_int, c_int], c_int),
         "kss_density_accumulate": ([P, c_int, c_int, P, c_int, P, P, c_int], c_int),
         "kss_lobpcg_solve": ([P, c_int, c_int, POINTER(kss_solve_opts), P, P, c_int, P,
                               POINTER(kss_solve_stats)], c_int),
+        "kss_rmmdiis_solve": ([P, c_int, c_int, POINTER(kss_solve_opts), P, P, c_int, P,
+                               POINTER(kss_solve_stats)], c_int),
         "kss_autotune_set": ([P, c_int], c_int),
         "kss_autotune_count": ([POINTER(c_int)], c_int),
         "kss_autotune_get": ([c_int, POINTER(kss_tune_entry)], c_int),
@@ -315,6 +318,15 @@ def kss_apply_H(sys: System, ik: int, psi, hpsi, prec: int = KSS_PREC_FP64, nb: 
     _check(lib().kss_apply_H(sys.h, ik, n if nb is None else nb, _ptr(psi), _ptr(hpsi), ld, prec), sys.ctx)
 
 
+def kss_apply_H_gamma(sys: System, ik: int, psi, hpsi, prec: int = KSS_PREC_FP64):
+    """H psi for real-space-real bands at Gamma (two bands per complex FFT)."""
+    n, ld = _block_dims(psi, prec)
+    n2, ld2 = _block_dims(hpsi, prec)
+    if (n2, ld2) != (n, ld):
+        raise ValueError("psi and hpsi shapes differ")
+    _check(lib().kss_apply_H_gamma(sys.h, ik, n, _ptr(psi), _ptr(hpsi), ld, prec), sys.ctx)
+
+
 def kss_apply_S(sys: System, ik: int, psi, spsi, prec: int = KSS_PREC_FP64):
     """spsi = S psi (the overlap of a system set up with Q; a copy of psi without one)."""
     n, ld = _block_dims(psi, prec)
@@ -363,8 +375,11 @@ def kss_apply_H_host(sys: System, ik: int, psi: np.ndarray, hpsi: np.ndarray,
 # --------------------------------------------------------------------------------------------
 # eigensolver
 
+KSS_SOLVE_NO_GAMMA_REAL = 1
+
+
 def make_opts(degree=10, tol=0.0, max_iter=0, nbuffer=-1, prec=KSS_PREC_FP64, seed=1234,
-              x0=None, x0_nb=0, x0_ld=0) -> kss_solve_opts:
+              x0=None, x0_nb=0, x0_ld=0, flags=0) -> kss_solve_opts:
     o = kss_solve_opts()
     o.degree = int(degree)
     o.tol = float(tol)
@@ -375,6 +390,7 @@ def make_opts(degree=10, tol=0.0, max_iter=0, nbuffer=-1, prec=KSS_PREC_FP64, se
     o.x0 = _ptr(x0)
     o.x0_nb = int(x0_nb)
     o.x0_ld = int(x0_ld)
+    o.flags = int(flags)
     return o
 
 
@@ -443,6 +459,22 @@ def kss_lobpcg_solve(sys: System, ik: int, nband: int, opts: kss_solve_opts, eve
     if evecs is not None:
         _, ld = _block_dims(evecs, opts.prec)
     st = lib().kss_lobpcg_solve(sys.h, ik, nband, byref(opts), ev.ctypes.data, _ptr(evecs), ld,
+                                rs.ctypes.data, byref(stats))
+    if st == KSS_ENOCONV and allow_noconv:
+        return ev, rs, stats_dict(stats), st
+    _check(st, sys.ctx)
+    return ev, rs, stats_dict(stats), st
+
+
+def kss_rmmdiis_solve(sys: System, ik: int, nband: int, opts: kss_solve_opts, evecs=None,
+                     allow_noconv: bool = False):
+    ev = np.zeros(nband)
+    rs = np.zeros(nband)
+    stats = kss_solve_stats()
+    ld = 0
+    if evecs is not None:
+        _, ld = _block_dims(evecs, opts.prec)
+    st = lib().kss_rmmdiis_solve(sys.h, ik, nband, byref(opts), ev.ctypes.data, _ptr(evecs), ld,
                                 rs.ctypes.data, byref(stats))
     if st == KSS_ENOCONV and allow_noconv:
         return ev, rs, stats_dict(stats), st

@@ -79,3 +79,40 @@ def test_lobpcg_warm_start_and_statuses(ctx):
         assert e.value.status == K.KSS_ENOTSUP
     finally:
         K.kss_sys_destroy(sysS)
+
+
+@pytest.mark.parametrize("name", ["C1", "C4.1"])
+def test_rmmdiis_refines_a_loose_solve(ctx, name):
+    """RMM-DIIS from the vectors of a loose ChebFi solve (residual 1e-3, the whole block of nband +
+    nbuffer bands) reaches 1e-8 and the oracle's eigenvalues."""
+    import torch
+    s = CASES[name]()
+    sysh = setup(ctx, s)
+    try:
+        p = O.build_problem(s, 0)
+        npw = p.basis.npw
+        nbuf = max(4, (s.nband + 9) // 10)
+        m = s.nband + nbuf
+        X0 = torch.zeros((m, npw), dtype=torch.complex128, device="cuda")  # trial vectors for the whole block
+        K.kss_chebfi_solve(sysh, 0, m, K.make_opts(tol=1e-3, seed=6), evecs=X0)
+        X = torch.zeros((s.nband, npw), dtype=torch.complex128, device="cuda")
+        ev, rs, st, _ = K.kss_rmmdiis_solve(sysh, 0, s.nband, K.make_opts(tol=1e-8, nbuffer=nbuf, x0=X0, x0_nb=m,
+                                                                          x0_ld=npw), evecs=X)
+        w, _ = p.lowest(s.nband)
+        assert np.max(np.abs(ev - w)) < 1e-8, np.max(np.abs(ev - w))
+        assert rs.max() <= 1e-8 and st["iters"] >= 1
+        x = X.cpu().numpy()
+        assert np.max(np.abs(x.conj() @ x.T - np.eye(s.nband))) < 1e-10
+    finally:
+        K.kss_sys_destroy(sysh)
+
+
+def test_rmmdiis_statuses(ctx):
+    s = W.config1()
+    sysh = setup(ctx, s)
+    try:
+        with pytest.raises(K.KssError) as e:
+            K.kss_rmmdiis_solve(sysh, 0, s.nband, K.make_opts())  # no trial vectors
+        assert e.value.status == K.KSS_EINVAL
+    finally:
+        K.kss_sys_destroy(sysh)
