@@ -210,6 +210,14 @@ def run_reference(args, rank: int):
 # ------------------------------------------------------------------------------------------------
 # GPU arm
 
+# DRAM bytes per band of the middle FFT pass on the C2 workload, from one ncu capture of the
+# production launch (dram__bytes_read.sum + dram__bytes_write.sum): pass_bw<double, 8, 12, 384>
+# moved 73.60 + 9.65 MB for a 27-band launch, pass_bw<float, 8, 12, 384> 69.93 + 7.26 MB for 54
+# bands.  Valid for that schedule only (the bench reports null traffic for any other).
+PASS_B_DRAM_PER_BAND = {"fp64": (73.595136e6 + 9.649664e6) / 27, "mixed": (69.929472e6 + 7.256832e6) / 54}
+PASS_B_SCHEDULE = "8x12 @384"
+
+
 def algorithmic_work(s, npw, nb, degree, box, applies, rr_calls):
     """Algorithmic FLOPs per kernel family over the timed region (conventional counts:
     5 N log2 N per complex 1D FFT of length N, 8 flops per complex multiply-add)."""
@@ -394,8 +402,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     K.kss_sys_destroy(sysh)
     K.kss_destroy(ctx)
     # pass-B schedules the autotuner picked (box, window, split, threads per CTA; 0 = per-warp form)
+    table = K.kss_autotune_table()
     sched = [f"{e['N1']}x{e['N']}^2 W3<={e['W3']}: {e['A']}x{e['B']} @{e['threads']} "
-             f"({e['ncand']} timed)" for e in K.kss_autotune_table()]
+             f"({e['ncand']} timed)" for e in table]
+    if roof is not None and roof["kernel"] == "local_pass_b" and args.workload == "c2" and \
+            all(f"{e['A']}x{e['B']} @{e['threads']}" == PASS_B_SCHEDULE for e in table):
+        roof["traffic"] = PASS_B_DRAM_PER_BAND[args.form] * applies / roof["launches"]
+        roof["traffic_note"] = ("DRAM bytes per launch: ncu bytes per band of this kernel and schedule x the "
+                                "bands per launch of this run")
 
     if rank == 0:
         line = {
