@@ -615,6 +615,8 @@ kss_status kss_footprint(kss_sys sys, int nband, kss_precision prec, size_t* byt
     if (prec == KSS_PREC_MIXED) b += 2 * (size_t)npw * nb * 16; // FP64 refinement blocks
     b += 3 * (size_t)nb * nb * 16;                              // Gram / projected H / work
     if (sys->has_S) b += 2 * (size_t)npw * nb * es;             // S Y / S X block, L psi scratch
+    if (prec == KSS_PREC_MIXED && sys->nproj)                   // split-BF16 projector tables
+      b += tc_split_cn_bytes(sys->nproj, npw) + tc_split_nn_bytes(npw, sys->nproj);
     b += local_workspace_bytes(sys, (int)ik, nb, prec);
     m = std::max(m, b);
   }

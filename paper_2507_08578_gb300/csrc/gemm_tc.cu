@@ -94,7 +94,8 @@ __host__ __device__ constexpr uint32_t instr_desc() {
 __global__ void __launch_bounds__(kTcThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                float* __restrict__ D, int Mr, int Nr, int kb_per_split, int kb_total,
-               int* __restrict__ err) {
+               int* __restrict__ err, float2* __restrict__ Cf, long long ldc, float ar, float ai, float br,
+               float bi) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = base;
@@ -194,7 +195,32 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < Mr) {
+      if (Cf) {
+        // Fused complex epilogue (one K-split, A B form with interleaved rows): accumulator row 2i
+        // holds Re C(i, col), row 2i+1 Im C(i, col); the pair sits in adjacent lanes of this warp.
+        float w[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) w[j] = __shfl_down_sync(0xffffffffu, __uint_as_float(r[j]), 1);
+        if (row < Mr && !(lane & 1)) {
+          const int ncol = min(32, Nr - (tn * TN + c0));
+          float2* dst0 = Cf + (size_t)(tn * TN + c0) * ldc + (row >> 1);
+          float2 q[32];
+          // all loads of the old values first (independent), then the stores
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            q[j] = (j < ncol && (br != 0.f || bi != 0.f)) ? dst0[(size_t)j * ldc] : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (j < ncol) {
+              const float v = __uint_as_float(r[j]);
+              float2 o;
+              o.x = ar * v - ai * w[j] + br * q[j].x - bi * q[j].y;
+              o.y = ar * w[j] + ai * v + br * q[j].y + bi * q[j].x;
+              dst0[(size_t)j * ldc] = o;
+            }
+          }
+        }
+      } else if (row < Mr) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = tn * TN + c0 + j;
@@ -245,7 +271,8 @@ __global__ void prep_kmajor(const float2* __restrict__ src, long long ld, int K,
 }
 
 // M-major complex A (element (i, k) at src[k*ld + i]) -> BF16 K-major rows for C = A B:
-// row i: (re, -im) pairs, row M + i: (im, re) pairs, role A [hi | hi | lo].  32x32 smem transpose.
+// row 2i: (re, -im) pairs, row 2i + 1: (im, re) pairs (so the real and imaginary parts of output
+// row i are adjacent accumulator rows), role A [hi | hi | lo].  32x32 smem transpose.
 __global__ void prep_mmajor(const float2* __restrict__ src, long long ld, int M, int K, int Kp,
                             __nv_bfloat16* __restrict__ dst) {
   __shared__ float2 t[32][33];
@@ -264,8 +291,8 @@ __global__ void prep_mmajor(const float2* __restrict__ src, long long ld, int M,
     split_bf16(v.x, hr, lr);
     split_bf16(v.y, hi_, li_);
     split_bf16(-v.y, hmi, lmi);
-    __nv_bfloat16* ra = dst + (size_t)i * (3 * (size_t)Kp);
-    __nv_bfloat16* rb = dst + (size_t)(M + i) * (3 * (size_t)Kp);
+    __nv_bfloat16* ra = dst + (size_t)(2 * i) * (3 * (size_t)Kp);
+    __nv_bfloat16* rb = dst + (size_t)(2 * i + 1) * (3 * (size_t)Kp);
     const int e = 2 * k;
     ra[e] = hr; ra[e + 1] = hmi;
     ra[Kp + e] = hr; ra[Kp + e + 1] = hmi;
@@ -278,15 +305,15 @@ __global__ void prep_mmajor(const float2* __restrict__ src, long long ld, int M,
 
 // C (complex, col-major ldc) = alpha * D + beta * C with D assembled from the K-split partials
 // (col-major Mr x Nr).  form 0 (A^H B): re = D(i, j), im = D(i, N + j); form 1 (A B):
-// re = D(i, j), im = D(M + i, j).
+// re = D(2i, j), im = D(2i + 1, j).
 __global__ void tc_combine(const float* __restrict__ P, int nsplit, int Mr, int Nr, int M, int N,
                            int form, float2* __restrict__ C, long long ldc, float ar, float ai,
                            float br, float bi) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)M * N) return;
   const int i = (int)(idx % M), j = (int)(idx / M);
-  const size_t oR = (size_t)j * Mr + i;
-  const size_t oI = form == 0 ? (size_t)(N + j) * Mr + i : (size_t)j * Mr + (M + i);
+  const size_t oR = form == 0 ? (size_t)j * Mr + i : (size_t)j * Mr + 2 * i;
+  const size_t oI = form == 0 ? (size_t)(N + j) * Mr + i : (size_t)j * Mr + (2 * i + 1);
   float sr = 0.f, si = 0.f;
   const size_t stride = (size_t)Mr * Nr;
   for (int z = 0; z < nsplit; ++z) {
@@ -353,7 +380,7 @@ void run_tc(kss_ctx ctx, const __nv_bfloat16* Atc, int Mr, const __nv_bfloat16* 
   const int kps = (kb_total + splits - 1) / splits;
   splits = (kb_total + kps - 1) / kps;
   const size_t pbytes = (size_t)splits * Mr * Nr * sizeof(float);
-  ctx->tc_part.ensure(pbytes);
+  if (!(form == 1 && splits == 1)) ctx->tc_part.ensure(pbytes);
   if (!ctx->tc_err.p) {
     ctx->tc_err.alloc(sizeof(int));
     KSS_CHECK_CUDA(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), ctx->stream));
@@ -364,10 +391,17 @@ void run_tc(kss_ctx ctx, const __nv_bfloat16* Atc, int Mr, const __nv_bfloat16* 
     KSS_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
     attr = true;
   }
+  // A B form without a K-split: the kernel writes the complex result itself (no partial sums)
+  const bool fused = form == 1 && splits == 1;
   {
     ProfScope ps(ctx, prof_register((std::string("tc_gemm_bf16x3:") + tag).c_str()));
     tc_gemm_kernel<<<dim3(tmn, tnn, splits), kTcThreads, kTcSmem, ctx->stream>>>(
-        ma, mb, ctx->tc_part.as<float>(), Mr, Nr, kps, kb_total, ctx->tc_err.as<int>());
+        ma, mb, ctx->tc_part.as<float>(), Mr, Nr, kps, kb_total, ctx->tc_err.as<int>(), fused ? C : nullptr,
+        ldc, (float)ar, (float)ai, (float)br, (float)bi);
+  }
+  if (fused) {
+    KSS_CHECK_CUDA(cudaGetLastError());
+    return;
   }
   const long long mn = (long long)M * N;
   {
@@ -420,6 +454,55 @@ void tc_gemm_nn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const 
     prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, 0, 1, 0);
   }
   run_tc(ctx, Atc, 2 * M, Btc, N, Kt, 1, M, N, (float2*)C, ldc, ar, ai, br, bi, tag);
+}
+
+// Forms with A already split (static operands such as the projector table, prepared once with
+// tc_split_* and kept): only B is prepared per call.
+size_t tc_split_cn_bytes(int M, int K) { return (size_t)M * 3 * kpad(K) * 2; }
+size_t tc_split_nn_bytes(int M, int K) { return (size_t)2 * M * 3 * kpad(K) * 2; }
+
+void tc_split_cn(kss_ctx ctx, int M, int K, const void* A, int lda, void* Atc) {
+  const int Kp = kpad(K);
+  const long long na = (long long)M * (Kp / 2);
+  prep_kmajor<<<(unsigned)((na + 255) / 256), 256, 0, ctx->stream>>>((const float2*)A, lda, K, M, Kp,
+                                                                    (__nv_bfloat16*)Atc, 0, 0, 0);
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+void tc_split_nn(kss_ctx ctx, int M, int K, const void* A, int lda, void* Atc) {
+  const int Kp = kpad(K);
+  dim3 g((M + 31) / 32, (Kp / 2 + 31) / 32);
+  prep_mmajor<<<g, dim3(32, 8), 0, ctx->stream>>>((const float2*)A, lda, M, K, Kp, (__nv_bfloat16*)Atc);
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+void tc_gemm_cn_split(kss_ctx ctx, int M, int N, int K, const void* Atc, const void* B, int ldb, void* C, int ldc,
+                      double ar, double ai, double br, double bi, const char* tag) {
+  if (M <= 0 || N <= 0 || K <= 0) return;
+  const int Kp = kpad(K), Kt = 3 * Kp;
+  ctx->tc_b.ensure((size_t)2 * N * Kt * 2);
+  __nv_bfloat16* Btc = ctx->tc_b.as<__nv_bfloat16>();
+  {
+    ProfScope ps(ctx, prof_register("tc_prep"));
+    const long long nb = (long long)N * (Kp / 2);
+    prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, 0, 1, 0);
+    prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, N, 1, 1);
+  }
+  run_tc(ctx, (const __nv_bfloat16*)Atc, M, Btc, 2 * N, Kt, 0, M, N, (float2*)C, ldc, ar, ai, br, bi, tag);
+}
+
+void tc_gemm_nn_split(kss_ctx ctx, int M, int N, int K, const void* Atc, const void* B, int ldb, void* C, int ldc,
+                      double ar, double ai, double br, double bi, const char* tag) {
+  if (M <= 0 || N <= 0 || K <= 0) return;
+  const int Kp = kpad(K), Kt = 3 * Kp;
+  ctx->tc_b.ensure((size_t)N * Kt * 2);
+  __nv_bfloat16* Btc = ctx->tc_b.as<__nv_bfloat16>();
+  {
+    ProfScope ps(ctx, prof_register("tc_prep"));
+    const long long nb = (long long)N * (Kp / 2);
+    prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, 0, 1, 0);
+  }
+  run_tc(ctx, (const __nv_bfloat16*)Atc, 2 * M, Btc, N, Kt, 1, M, N, (float2*)C, ldc, ar, ai, br, bi, tag);
 }
 
 // Device-side failure flag of the tensor-core kernels (bounded waits that gave up).

@@ -70,6 +70,7 @@ struct KData {
   DevBuf d_miller, d_offset, d_tileidx, d_zstart, d_rowrange;
   DevBuf d_kin64, d_kin32;         // 0.5 |k+G|^2
   DevBuf d_beta64, d_beta32;       // projector-major [nproj][npw] complex
+  DevBuf d_btc_cn, d_btc_nn;       // mixed: split-BF16 forms of beta for beta^H psi and beta C (lazy)
   DevBuf d_q;                      // Cartesian k+G, npw*3 doubles (setup only)
   double tmax = 0;
   double bound = 0;                // rigorous spectral upper bound of H
@@ -205,6 +206,10 @@ struct ChebCoef {
 // out = alpha*(T psi + V psi + nonlocal psi) + beta*psi + gamma*psi_prev (psi_prev may be null)
 void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, void* out, int ld,
              ChebCoef c, kss_precision prec);
+// Split-BF16 forms of a k-point's complex64 projector table for the tensor-core products
+// beta^H psi and beta C (built on first use and kept with the system).
+const void* beta_split_cn(kss_sys s, int ik);
+const void* beta_split_nn(kss_sys s, int ik);
 // out = T psi + V psi (the local part only)
 void apply_local(kss_sys s, int ik, int nb, const void* psi, void* out, int ld, kss_precision prec);
 // ---- generalised problem with a nonlocal overlap (overlap.cu) ----
@@ -262,6 +267,16 @@ void tc_gemm_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const 
 void tc_gemm_nn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                 void* C, int ldc, double ar, double ai, double br, double bi, const char* tag);
 int tc_error_flag(kss_ctx ctx, bool reset);
+// The same products with the A operand split once in advance (static operands): tc_split_cn /
+// tc_split_nn write the split form of A (tc_split_*_bytes) for tc_gemm_cn_split / tc_gemm_nn_split.
+size_t tc_split_cn_bytes(int M, int K);
+size_t tc_split_nn_bytes(int M, int K);
+void tc_split_cn(kss_ctx ctx, int M, int K, const void* A, int lda, void* Atc);
+void tc_split_nn(kss_ctx ctx, int M, int K, const void* A, int lda, void* Atc);
+void tc_gemm_cn_split(kss_ctx ctx, int M, int N, int K, const void* Atc, const void* B, int ldb, void* C, int ldc,
+                      double ar, double ai, double br, double bi, const char* tag);
+void tc_gemm_nn_split(kss_ctx ctx, int M, int N, int K, const void* Atc, const void* B, int ldb, void* C, int ldc,
+                      double ar, double ai, double br, double bi, const char* tag);
 // C (complex128) = A^H B for complex64 A, B with FP64 accumulation.
 void gemm_cn_c64_acc64(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B,
                        int ldb, void* C, int ldc, const char* tag);

@@ -717,6 +717,24 @@ size_t local_workspace_bytes(kss_sys s, int ik, int nb, kss_precision prec) {
   return slab_elems(s, ik) * chunk_bands(s, ik, nb, es) * es;
 }
 
+// Split-BF16 forms of the (static) complex64 projector table, built on first use per k-point.
+const void* beta_split_cn(kss_sys s, int ik) {
+  KData& kd = s->k[ik];
+  if (!kd.d_btc_cn.p) {
+    kd.d_btc_cn.alloc(tc_split_cn_bytes(s->nproj, kd.npw));
+    tc_split_cn(s->ctx, s->nproj, kd.npw, kd.d_beta32.p, kd.npw, kd.d_btc_cn.p);
+  }
+  return kd.d_btc_cn.p;
+}
+const void* beta_split_nn(kss_sys s, int ik) {
+  KData& kd = s->k[ik];
+  if (!kd.d_btc_nn.p) {
+    kd.d_btc_nn.alloc(tc_split_nn_bytes(kd.npw, s->nproj));
+    tc_split_nn(s->ctx, kd.npw, s->nproj, kd.d_beta32.p, kd.npw, kd.d_btc_nn.p);
+  }
+  return kd.d_btc_nn.p;
+}
+
 void apply_local(kss_sys s, int ik, int nb, const void* psi, void* out, int ld, kss_precision prec) {
   if (nb == 0) return;
   if (prec == KSS_PREC_FP64)
@@ -745,8 +763,8 @@ void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, v
       gemm_cn(ctx, true, s->nproj, nb, kd.npw, kd.d_beta64.p, kd.npw, psi, ld, ctx->ws_cprj.p,
               s->nproj, 1.0, 0.0, 0.0, 0.0, "cprj");
     else
-      tc_gemm_cn(ctx, s->nproj, nb, kd.npw, kd.d_beta32.p, kd.npw, psi, ld, ctx->ws_cprj.p, s->nproj,
-                 1.0, 0.0, 0.0, 0.0, "cprj");
+      tc_gemm_cn_split(ctx, s->nproj, nb, kd.npw, beta_split_cn(s, ik), psi, ld, ctx->ws_cprj.p, s->nproj,
+                       1.0, 0.0, 0.0, 0.0, "cprj");
     scale_rows(ctx, f64, s->nproj, nb, ctx->ws_cprj.p, s->nproj, f64 ? s->d_D64.p : s->d_D32.p,
                c.alpha);
   }
@@ -760,8 +778,8 @@ void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, v
       gemm_nn(ctx, true, kd.npw, nb, s->nproj, kd.d_beta64.p, kd.npw, ctx->ws_cprj.p, s->nproj, out,
               ld, 1.0, 0.0, 1.0, 0.0, "nonlocal");
     else
-      tc_gemm_nn(ctx, kd.npw, nb, s->nproj, kd.d_beta32.p, kd.npw, ctx->ws_cprj.p, s->nproj, out, ld,
-                 1.0, 0.0, 1.0, 0.0, "nonlocal");
+      tc_gemm_nn_split(ctx, kd.npw, nb, s->nproj, beta_split_nn(s, ik), ctx->ws_cprj.p, s->nproj, out, ld,
+                       1.0, 0.0, 1.0, 0.0, "nonlocal");
   }
 }
 

@@ -41,19 +41,23 @@ __global__ void cheb_combine(const C* __restrict__ f, long long ldf, const C* __
 
 // Projector products at the precision of the path: FP64 SIMT, or split-BF16 tensor cores for
 // complex64 (the same kernels as the H application).
-void proj_cn(kss_ctx ctx, bool f64, const KData& kd, int nproj, int nb, const void* psi, int ld,
-             void* out, const char* tag) {
+void proj_cn(kss_ctx ctx, bool f64, kss_sys s, int ik, int nb, const void* psi, int ld, void* out,
+             const char* tag) {
+  const KData& kd = s->k[ik];
+  const int nproj = s->nproj;
   if (f64)
     gemm_cn(ctx, true, nproj, nb, kd.npw, kd.d_beta64.p, kd.npw, psi, ld, out, nproj, 1, 0, 0, 0, tag);
   else
-    tc_gemm_cn(ctx, nproj, nb, kd.npw, kd.d_beta32.p, kd.npw, psi, ld, out, nproj, 1, 0, 0, 0, tag);
+    tc_gemm_cn_split(ctx, nproj, nb, kd.npw, beta_split_cn(s, ik), psi, ld, out, nproj, 1, 0, 0, 0, tag);
 }
-void proj_nn(kss_ctx ctx, bool f64, const KData& kd, int nproj, int nb, const void* coef, void* out,
-             int ld, const char* tag) {
+void proj_nn(kss_ctx ctx, bool f64, kss_sys s, int ik, int nb, const void* coef, void* out, int ld,
+             const char* tag) {
+  const KData& kd = s->k[ik];
+  const int nproj = s->nproj;
   if (f64)
     gemm_nn(ctx, true, kd.npw, nb, nproj, kd.d_beta64.p, kd.npw, coef, nproj, out, ld, 1, 0, 1, 0, tag);
   else
-    tc_gemm_nn(ctx, kd.npw, nb, nproj, kd.d_beta32.p, kd.npw, coef, nproj, out, ld, 1, 0, 1, 0, tag);
+    tc_gemm_nn_split(ctx, kd.npw, nb, nproj, beta_split_nn(s, ik), coef, nproj, out, ld, 1, 0, 1, 0, tag);
 }
 
 unsigned grid_for(long long n) {
@@ -152,9 +156,9 @@ void apply_s(kss_ctx ctx, kss_sys s, int ik, int nb, const void* psi, void* out,
                                    cudaMemcpyDeviceToDevice, ctx->stream));
   if (!s->has_S || s->nproj == 0 || nb == 0) return;
   ctx->ws_cprj.ensure((size_t)s->nproj * nb * es);
-  proj_cn(ctx, f64, kd, s->nproj, nb, psi, ld, ctx->ws_cprj.p, "overlap_cprj");
+  proj_cn(ctx, f64, s, ik, nb, psi, ld, ctx->ws_cprj.p, "overlap_cprj");
   scale_rows(ctx, f64, s->nproj, nb, ctx->ws_cprj.p, s->nproj, f64 ? s->d_Q64.p : s->d_Q32.p, 1.0);
-  proj_nn(ctx, f64, kd, s->nproj, nb, ctx->ws_cprj.p, out, ld, "overlap_nonlocal");
+  proj_nn(ctx, f64, s, ik, nb, ctx->ws_cprj.p, out, ld, "overlap_nonlocal");
 }
 
 // out = alpha * F psi + beta * psi + gamma * psi_prev with the filter operator F = H, or S^-1 H
@@ -180,19 +184,19 @@ void apply_filter_op(kss_sys s, int ik, int nb, const void* psi, const void* psi
   ctx->ws_f.ensure((size_t)np * nb * es);
   void* lpsi = ctx->ws_sapply.p;
   // D C (kept in ws_f; apply_local uses ws_cprj for nothing)
-  proj_cn(ctx, f64, kd, np, nb, psi, ld, ctx->ws_f.p, "cprj");
+  proj_cn(ctx, f64, s, ik, nb, psi, ld, ctx->ws_f.p, "cprj");
   scale_rows(ctx, f64, np, nb, ctx->ws_f.p, np, f64 ? s->d_D64.p : s->d_D32.p, 1.0);
   // L psi = T psi + V psi
   apply_local(s, ik, nb, psi, lpsi, ld, prec);
   // E = beta^H (L psi) + G (D C)
-  proj_cn(ctx, f64, kd, np, nb, lpsi, ld, ctx->ws_e.p, "overlap_cprj");
+  proj_cn(ctx, f64, s, ik, nb, lpsi, ld, ctx->ws_e.p, "overlap_cprj");
   gemm_nn(ctx, f64, np, nb, np, f64 ? kd.d_G64.p : kd.d_G32.p, np, ctx->ws_f.p, np, ctx->ws_e.p, np, 1, 0, 1, 0,
           "overlap_small");
   // F = D C - W E
   gemm_nn(ctx, f64, np, nb, np, f64 ? kd.d_W64.p : kd.d_W32.p, np, ctx->ws_e.p, np, ctx->ws_f.p, np, -1, 0, 1, 0,
           "overlap_small");
   // S^-1 H psi = L psi + beta F
-  proj_nn(ctx, f64, kd, np, nb, ctx->ws_f.p, lpsi, ld, "nonlocal");
+  proj_nn(ctx, f64, s, ik, nb, ctx->ws_f.p, lpsi, ld, "nonlocal");
   static const int idc = prof_register("cheb_combine");
   const long long n = (long long)kd.npw * nb;
   {
