@@ -255,24 +255,18 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
+    from paper_2507_08578_gb300 import multi as MR
+
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
     def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return MR.max_over_ranks(x, dist, "cuda")
 
     def sum_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return MR.sum_over_ranks(x, dist, "cuda")
 
     # CPU baseline first (rank 0, N = 1 only), before the GPU is busy.
     cpu = None
@@ -491,43 +485,69 @@ def run_c4(args):
     import workloads as W
     import paper_2507_08578_gb300.kss as K
     from paper_2507_08578_gb300 import build as B
+    from paper_2507_08578_gb300 import multi as MR
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     B.build()
     systems = W.config4(48)
-    ctx = K.kss_create(0, torch.cuda.current_stream().cuda_stream)
-    handles = [_setup(K, ctx, s) for s in systems]
-    units = [(h, s, ik) for h, s in zip(handles, systems) for ik in range(len(s.kpts))]
+    # (system, k-point) units, split across ranks by a greedy longest-processing-time assignment
+    all_units = [(j, ik) for j, s in enumerate(systems) for ik in range(len(s.kpts))]
+    costs = [MR.unit_cost(int(MR.npw_estimate(abs(np.linalg.det(systems[j].lattice)), systems[j].ecut)),
+                          systems[j].nband, args.degree) for j, _ in all_units]
+    mine = MR.lpt_partition(costs, world)[rank]
+    ctx = K.kss_create(local_rank, torch.cuda.current_stream().cuda_stream)
+    need = sorted({all_units[u][0] for u in mine})
+    handles = {j: _setup(K, ctx, systems[j]) for j in need}
+    units = [(handles[all_units[u][0]], systems[all_units[u][0]], all_units[u][1]) for u in mine]
     opts = K.make_opts(prec=K.KSS_PREC_MIXED, seed=7, degree=args.degree)
     args_b = ([u[0] for u in units], [u[2] for u in units], [u[1].nband for u in units])
     for _ in range(args.warmup):
         K.kss_solve_batch(ctx, *args_b, opts)
-    clocks = Clocks(0)
+    clocks = Clocks(local_rank)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     K.kss_profile_enable(ctx, True)
     clocks.start()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         ev, rs, st, _ = K.kss_solve_batch(ctx, *args_b, opts)
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    if dist is not None:
+        dist.barrier()
+    dt = MR.max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     ck = clocks.stop()
     prof = K.profile_table(ctx)
     _, launches = K.kss_profile_count(ctx)
     K.kss_profile_enable(ctx, False)
-    napply = sum(x["napply"] for x in st)
-    for h in handles:
+    napply = MR.sum_over_ranks(sum(x["napply"] for x in st), dist, "cuda")
+    iters = [x["iters"] for x in st]
+    max_res = MR.max_over_ranks(float(max(r.max() for r in rs)) if rs else 0.0, dist, "cuda")
+    for h in handles.values():
         K.kss_sys_destroy(h)
     K.kss_destroy(ctx)
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
     print(json.dumps({"metric": "eigensolves/s", "value": len(systems) * args.steps / dt,
-                      "unit": "systems solved/s", "n_gpus": 1, "steps": args.steps,
+                      "unit": "systems solved/s", "n_gpus": world, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
                       "higher_is_better": True, "dtype": "c64+f64", "data": "synthetic",
-                      "config": {"workload": f"C4: 48 systems, {len(units)} (system,k) units in one "
+                      "config": {"workload": f"C4: 48 systems, {len(all_units)} (system,k) units in one "
                                              "lockstep batch (grouped launches, CUDA-graph filter), "
                                              "mixed precision"},
-                      "units_per_s": len(units) * args.steps / dt, "band_applies_per_s": napply * args.steps / dt,
-                      "max_residual_Ha": float(max(r.max() for r in rs)),
-                      "max_iterations": max(x["iters"] for x in st), "gpu_launches": launches,
-                      "mean_iterations": sum(x["iters"] for x in st) / len(st), "degree": args.degree,
+                      "units_per_s": len(all_units) * args.steps / dt, "band_applies_per_s": napply * args.steps / dt,
+                      "max_residual_Ha": max_res, "scaling": "strong" if world > 1 else None,
+                      "partition": "greedy longest-processing-time over (system, k) units" if world > 1 else None,
+                      "max_iterations": max(iters), "gpu_launches": launches,
+                      "mean_iterations": sum(iters) / len(iters), "degree": args.degree,
                       "clocks": ck,
                       "kernels": {k: {"launches": v[0], "ms": round(v[1], 2)} for k, v in
                                   sorted(prof.items(), key=lambda kv: -kv[1][1])[:12]}}), flush=True)

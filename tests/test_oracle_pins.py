@@ -480,3 +480,22 @@ def test_density_time_reversal():
     n0 = O.density(c0, b0, [1.0, 2.0], vol)
     n1 = O.density(c1, b1, [1.0, 2.0], vol)
     assert np.max(np.abs(n0 - n1)) < 1e-13 * np.max(n0)
+
+
+# ---------------------------------------------------------------------------------------------
+# Stored values (tests/golden/, written by tests/golden/make_golden.py from the oracle only)
+# ---------------------------------------------------------------------------------------------
+
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    return np.array([float(l) for l in open(path) if l.strip() and not l.startswith("#")])
+
+
+def test_golden_values_reproduce():
+    w, _ = O.build_problem(W.config1(), 0).lowest(16)
+    assert np.max(np.abs(w - _golden("c1_lowest16_Ha.txt"))) < 1e-12
+    ws, _ = O.build_problem(W.config1s(), 0).lowest(16)
+    assert np.max(np.abs(ws - _golden("c1s_lowest16_Ha.txt"))) < 1e-12
+    counts = _golden("sphere_counts.txt").astype(int)
+    assert counts[0] == 1503 and np.all(counts[1:] == 34181)
