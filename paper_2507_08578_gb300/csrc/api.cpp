@@ -618,6 +618,8 @@ kss_status kss_footprint(kss_sys sys, int nband, kss_precision prec, size_t* byt
     if (prec == KSS_PREC_MIXED && sys->nproj)                   // split-BF16 projector tables
       b += tc_split_cn_bytes(sys->nproj, npw) + tc_split_nn_bytes(npw, sys->nproj);
     b += local_workspace_bytes(sys, (int)ik, nb, prec);
+    // V in the CTA-wide pass B's layout (one split per precision in use)
+    b += (size_t)sys->N[0] * sys->N[1] * sys->N[2] * (prec == KSS_PREC_FP64 ? 8 : 12);
     m = std::max(m, b);
   }
   *bytes = m;

@@ -33,7 +33,8 @@ using fftr::Split;
 
 // Shared memory of the CTA-wide pass B for box length N and sphere window W3.
 size_t wide_b_smem(int N, int W3, size_t es) {
-  return es * ((size_t)N + (size_t)W3 * (N + 1) + (size_t)N * (N + 1)) + sizeof(int) * N;
+  const size_t P = (size_t)((N + 1) | 1);  // the odd pitches of the CTA-wide form
+  return es * ((size_t)N + (size_t)W3 * P + (size_t)N * P) + sizeof(int) * N;
 }
 
 bool has_ct(int code) {
@@ -256,6 +257,9 @@ void BatchEngine::prepare_t() {
                                        : (long long)(c23 + 1);
     key[u] = {(long long)(c1 + 1) * 100000 + k2, u};
   }
+  vpi.assign(n, nullptr);
+  for (int u = 0; u < n; ++u)
+    if (bs[u].threads) vpi[u] = vpi_view(units[u]->sys, bs[u].A, bs[u].B, sizeof(T) == 8);
   std::stable_sort(key.begin(), key.end());
   pos.assign(n, 0);
   classes.clear();
@@ -394,6 +398,7 @@ void BatchEngine::fill_tables_t() {
       }
       LocalItem<T> it;
       fill_args<T>(sy, s->ik, it.a);
+      it.a.Vpi = (const T*)vpi[u];
       it.a.psi = (const C*)psi;
       it.a.psi_prev = (const C*)pp;
       it.a.out = (C*)out;

@@ -55,6 +55,7 @@ class BatchEngine {
   std::vector<RegPlanHost> plans;
   std::vector<PassClass> classes;
   std::vector<int> pos;  // position of each unit in the class-ordered item table
+  std::vector<const void*> vpi;  // per unit: V in the CTA-wide pass B's layout (null: per-warp form)
   std::vector<WsOff> ws_off;
   DevBuf ws, d_local, d_cn, d_nn;
   std::vector<unsigned char> h_local;

@@ -25,7 +25,7 @@ template <typename T, int A, int B, int NT>
 __global__ void __launch_bounds__(NT) pass_dw(LocalArgs<T> a, int m, int G, const double* __restrict__ occ,
                                               double* __restrict__ part) {
   using C = typename CT<T>::C;
-  constexpr int N = A * B, QS = N + 1, ZS = N + 1;
+  constexpr int N = A * B, QS = (N + 1) | 1, ZS = (N + 1) | 1;  // odd pitches (as the CTA-wide pass B)
   constexpr int R = (N * A + NT - 1) / NT;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* tw = reinterpret_cast<C*>(smraw);
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(NT) pass_dw(LocalArgs<T> a, int m, int G, cons
     __syncthreads();
     // y inverse (two stages, in place; leaves position k2 + B k holding y = k + A k2)
     for (int t = tid; t < W3 * B; t += NT) {
-      const int u = t / B, r = t - u * B;
+      const int r = t / W3, u = t - r * W3;  // rows fastest across lanes
       C* row = Q + u * QS + r;
       C v[A];
 #pragma unroll
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(NT) pass_dw(LocalArgs<T> a, int m, int G, cons
     }
     __syncthreads();
     for (int t = tid; t < W3 * A; t += NT) {
-      const int u = t / A, k = t - u * A;
+      const int k = t / W3, u = t - k * W3;
       C* row = Q + u * QS + B * k;
       C v[B];
 #pragma unroll
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(NT) pass_dw(LocalArgs<T> a, int m, int G, cons
     for (int r = 0; r < R; ++r) {
       const int t = tid + NT * r;
       if (t < N * A) {
-        const int p = t / A, k = t - p * A;
+        const int k = t / N, p = t - k * N;  // columns fastest across lanes
         const C* col = Z + p * ZS + B * k;
         C v[B];
 #pragma unroll
@@ -127,17 +127,26 @@ __global__ void __launch_bounds__(NT) pass_dw(LocalArgs<T> a, int m, int G, cons
       }
     }
   }
-  double* pg = part + ((size_t)g * a.N1 + x) * N * N;
+  // Through shared memory to the partial plane: the accumulators sit in column (y position) order,
+  // so stage them as [p][z] (the odd pitch ZS, in doubles: Z holds at least N ZS of them) and write
+  // the plane out row by row in natural y.
+  __syncthreads();  // the last band's reads of Z are done
+  double* st = reinterpret_cast<double*>(Z);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int t = tid + NT * r;
     if (t < N * A) {
-      const int p = t / A, k = t - p * A;
-      const int py = p / B;
-      const int y = py + A * (p - py * B);
+      const int k = t / N, p = t - k * N;  // the accumulation's task -> thread map
 #pragma unroll
-      for (int j = 0; j < B; ++j) pg[(size_t)y * N + k + A * j] += acc[r][j];
+      for (int j = 0; j < B; ++j) st[p * ZS + k + A * j] = acc[r][j];
     }
+  }
+  __syncthreads();
+  double* pg = part + ((size_t)g * a.N1 + x) * N * N;
+  for (int i = tid; i < N * N; i += NT) {
+    const int y = i / N, z = i - y * N;
+    const int k2 = y / A, k = y - k2 * A;  // y = k + A k2 sits at position k2 + B k
+    pg[i] += st[(k2 + B * k) * ZS + z];
   }
 }
 
@@ -163,7 +172,8 @@ bool launch_d(const LocalArgs<T>& a, int m, int G, const double* occ, double* pa
               int* resident) {
   using C = typename CT<T>::C;
   constexpr int N = A * B;
-  const size_t sm = sizeof(C) * ((size_t)N + (size_t)a.W3 * (N + 1) + (size_t)N * (N + 1)) + sizeof(int) * N;
+  constexpr int P = (N + 1) | 1;
+  const size_t sm = sizeof(C) * ((size_t)N + (size_t)a.W3 * P + (size_t)N * P) + sizeof(int) * N;
   if (sm > 227 * 1024) return false;
   if (resident) {
     KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_dw<T, A, B, kDensThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,

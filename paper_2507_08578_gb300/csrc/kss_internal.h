@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "../../include/kss.h"
@@ -138,6 +139,7 @@ struct kss_sys_s {
   kss::DevBuf d_Vx64, d_Vx32;      // V(r_j)/(N1 N2 N3) in [j1][j2][j3] order (plane kernel)
   kss::DevBuf d_tw64[3], d_tw32[3];// e^{-2 pi i k/N_d}, k < N_d
   kss::DevBuf d_D64, d_D32;
+  std::map<int, kss::DevBuf> vpi64, vpi32;  // V/N^3 as [x][z][p] per split code A*32+B (lazy)
   bool has_S = false;              // generalised problem: S = 1 + sum_i |beta_i> q_i <beta_i|
   std::vector<double> Q;           // overlap coefficients (nproj), empty without an overlap
   kss::DevBuf d_Q64, d_Q32;
@@ -210,6 +212,9 @@ void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, v
 // beta^H psi and beta C (built on first use and kept with the system).
 const void* beta_split_cn(kss_sys s, int ik);
 const void* beta_split_nn(kss_sys s, int ik);
+// V/N^3 of the system in the [x][z][p] layout of the CTA-wide pass B for split N2 = N3 = A*B (p the
+// digit-reversed y position k2 + B k of y = k + A k2), built on first use and kept.
+const void* vpi_view(kss_sys s, int A, int B, bool f64);
 // out = T psi + V psi (the local part only)
 void apply_local(kss_sys s, int ik, int nb, const void* psi, void* out, int ld, kss_precision prec);
 // ---- generalised problem with a nonlocal overlap (overlap.cu) ----

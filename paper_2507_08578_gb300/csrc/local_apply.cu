@@ -496,6 +496,7 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
         kk.b<<<dim3(t.N1, m), kThreads, rb, ctx->stream>>>(t, rp, scr_warp);
       };
       const PassBSched sb = pass_b_schedule<T>(ctx, a, rp.s2, true);
+      if (sb.threads) a.Vpi = (const T*)vpi_view(s, sb.A, sb.B, f64);
       static const int ida = prof_register(f64 ? "local_pass_a<f64>" : "local_pass_a<f32>");
       static const int idb = prof_register(f64 ? "local_pass_b<f64>" : "local_pass_b<f32>");
       static const int idc = prof_register(f64 ? "local_pass_c<f64>" : "local_pass_c<f32>");
@@ -620,7 +621,15 @@ void run_local_ws(kss_sys s, int ik, int nb, const void* psi, void* out, int ld,
       auto warp_b = [&](const LocalArgs<T>& t, int m) {
         kk.b<<<dim3(t.N1, m), kThreads, rb, ctx->stream>>>(t, rp, scr_warp);
       };
-      const PassBSched sb = pass_b_schedule<T>(ctx, a, rp.s2, false);  // no tuning here
+      PassBSched sb = pass_b_schedule<T>(ctx, a, rp.s2, false);  // no tuning here
+      // The CTA-wide form needs V in its split's layout; that view is built (allocated) by the
+      // first ordinary application, and without it this path takes the per-warp form.
+      if (sb.threads) {
+        auto& cache = f64 ? s->vpi64 : s->vpi32;
+        auto it = cache.find(sb.A * 32 + sb.B);
+        if (it != cache.end()) a.Vpi = (const T*)it->second.p;
+        else sb.threads = 0;
+      }
       for (int n0 = 0; n0 < nb; n0 += nc) {
         const int m = std::min(nc, nb - n0);
         a.n0 = n0;
@@ -715,6 +724,39 @@ void local_apply_ws(kss_sys s, int ik, int nb, const void* psi, void* out, int l
 size_t local_workspace_bytes(kss_sys s, int ik, int nb, kss_precision prec) {
   const size_t es = prec == KSS_PREC_FP64 ? 16 : 8;
   return slab_elems(s, ik) * chunk_bands(s, ik, nb, es) * es;
+}
+
+template <typename T>
+__global__ void vpi_gather(const T* __restrict__ vx, T* __restrict__ out, int N1, int N, int A, int B) {
+  const long long n = (long long)N1 * N * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(i % N);
+    const long long r = i / N;
+    const int z = (int)(r % N), x = (int)(r / N);
+    const int k = p / B, k2 = p - k * B;
+    const int y = k + A * k2;
+    out[i] = vx[((size_t)x * N + y) * N + z];
+  }
+}
+
+const void* vpi_view(kss_sys s, int A, int B, bool f64) {
+  const int code = A * 32 + B;
+  auto& cache = f64 ? s->vpi64 : s->vpi32;
+  auto it = cache.find(code);
+  if (it != cache.end()) return it->second.p;
+  KSS_REQUIRE(s->N[1] == s->N[2] && A * B == s->N[1], "V view: split does not match the box");
+  const int N1 = s->N[0], N = s->N[1];
+  const long long n = (long long)N1 * N * N;
+  DevBuf& d = cache[code];
+  d.alloc((size_t)n * (f64 ? 8 : 4));
+  const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 32);
+  if (f64)
+    vpi_gather<double><<<blocks, 256, 0, s->ctx->stream>>>(s->d_Vx64.as<double>(), d.as<double>(), N1, N, A, B);
+  else
+    vpi_gather<float><<<blocks, 256, 0, s->ctx->stream>>>(s->d_Vx32.as<float>(), d.as<float>(), N1, N, A, B);
+  KSS_CHECK_CUDA(cudaGetLastError());
+  return d.p;
 }
 
 // Split-BF16 forms of the (static) complex64 projector table, built on first use per k-point.

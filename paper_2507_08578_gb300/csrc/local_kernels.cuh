@@ -34,6 +34,8 @@ struct LocalArgs {
   const int* tileidx;
   const T* kin;
   const T* Vx;
+  const T* Vpi;   // CTA-wide pass B: V/N^3 as [x][z][p], p the y position of the stages' digit-reversed
+                  // order for the split in use (so the middle z stage reads it coalesced)
   const C* psi;
   const C* psi_prev;
   C* out;
@@ -498,8 +500,8 @@ constexpr int kWideThreads = 384;  // 12 warps: 96-point stages split into whole
 template <typename T, int A, int B>
 struct WideB {
   static constexpr int N = A * B;
-  static constexpr int QS = N + 1;  // row strides (padded)
-  static constexpr int ZS = N + 1;
+  static constexpr int QS = (N + 1) | 1;  // odd row / column pitches: with the index along the
+  static constexpr int ZS = (N + 1) | 1;  // pitch fastest across lanes, no shared-memory bank conflicts
   static size_t smem(int W3) {
     return sizeof(typename CT<T>::C) * ((size_t)N + (size_t)W3 * QS + (size_t)N * ZS) + sizeof(int) * N;
   }
@@ -535,7 +537,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   __syncthreads();
   // ---- y, inverse ----
   for (int t = tid; t < W3 * B; t += NT) {
-    const int u = t / B, r = t - u * B;
+    const int r = t / W3, u = t - r * W3;  // rows fastest across lanes
     C* row = Q + u * QS + r;
     C v[A];
 #pragma unroll
@@ -552,7 +554,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   }
   __syncthreads();
   for (int t = tid; t < W3 * A; t += NT) {
-    const int u = t / A, k = t - u * A;
+    const int k = t / W3, u = t - k * W3;
     C* row = Q + u * QS + B * k;
     C v[B];
 #pragma unroll
@@ -584,12 +586,11 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   }
   __syncthreads();
   // ---- z, inverse stage 2, x V, forward stage 1 ----
-  const T* vx = a.Vx + (size_t)x * N * N;
+  // columns fastest across lanes; V from the [x][z][p] view (coalesced in p)
+  const T* vp = a.Vpi + (size_t)x * N * N;
   for (int t = tid; t < N * A; t += NT) {
-    const int p = t / A, k = t - p * A;
-    const int py = p / B;
-    const int y = py + A * (p - py * B);  // position p = k2 + B k of a y row holds y = k + A k2
-    const T* vrow = vx + (size_t)y * N + k;
+    const int k = t / N, p = t - k * N;
+    const T* vrow = vp + (size_t)k * N + p;  // (z = k + A k2, p) at vrow[A k2 N]
     C* col = Z + p * ZS + B * k;
     C v[B];
 #pragma unroll
@@ -597,7 +598,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
     fftr::rdft<B>(v, (T)1);
 #pragma unroll
     for (int k2 = 0; k2 < B; ++k2) {
-      const T vv = vrow[A * k2];  // z = k + A k2
+      const T vv = vrow[(size_t)A * k2 * N];  // z = k + A k2
       v[k2].x *= vv;
       v[k2].y *= vv;
     }
@@ -625,7 +626,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   __syncthreads();
   // ---- y, forward ----
   for (int t = tid; t < W3 * A; t += NT) {
-    const int u = t / A, r = t - u * A;
+    const int r = t / W3, u = t - r * W3;
     C* row = Q + u * QS + B * r;
     C v[B];
 #pragma unroll
@@ -638,7 +639,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   }
   __syncthreads();
   for (int t = tid; t < W3 * B; t += NT) {
-    const int u = t / B, q = t - u * B;
+    const int q = t / W3, u = t - q * W3;
     C* row = Q + u * QS + q;
     C v[A];
 #pragma unroll

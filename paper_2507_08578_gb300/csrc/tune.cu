@@ -73,6 +73,7 @@ PassBSched pass_b_schedule(kss_ctx ctx, const lk::LocalArgs<T>& a, const fftr::S
   ctx->ws_tune.ensure(elems * sizeof(C));
   KSS_CHECK_CUDA(cudaMemsetAsync(ctx->ws_tune.p, 0, elems * sizeof(C), ctx->stream));
   t.work = ctx->ws_tune.as<C>();
+  t.Vpi = t.Vx;  // any N1 x N x N array: the values do not matter for timing
   t.n0 = 0;
   cudaEvent_t e0, e1;
   KSS_CHECK_CUDA(cudaEventCreate(&e0));
