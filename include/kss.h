@@ -298,6 +298,20 @@ kss_status kss_solver_destroy(kss_solver s);
  * band has residual <= tol.  Synchronises the stream (the residuals decide convergence). */
 kss_status kss_solver_step(kss_solver s, int* converged);
 
+/* One iteration on each of n solvers of the same context (e.g. the k-points of one system; §5.3
+ * notes that k-points are independent), with the same results as n calls of kss_solver_step in
+ * order.  The Rayleigh-Ritz of solver i (Gram products, the FP64 generalised eigensolve, the
+ * rotations and residuals, §5.1) runs on a helper stream of the context while the filter of
+ * solver i+1 runs on the context stream: the dense eigensolve is latency-bound and would
+ * otherwise leave the GPU mostly idle.  Solvers that have not taken their first step do it
+ * (initial Rayleigh-Ritz) in order first; solvers that are done are skipped, and a solver listed
+ * twice steps once.  converged: NULL or an int array [n] set like kss_solver_step's flag.
+ * Errors: KSS_EINVAL (n < 0, a NULL solver, solvers of different contexts), and those of
+ * kss_solver_step; as after a failed kss_solver_step, the iterates are then undefined (the
+ * filter works in place) and the solvers should be destroyed.  The stepped solvers' ms_filter
+ * and ms_rr receive equal shares of the call's wall time. */
+kss_status kss_solver_step_many(int n, kss_solver const* solvers, int* converged);
+
 /* Results of the current iterate: evals/resid host [nband] (may be NULL); evecs DEVICE
  * band-major [nband][ld] of the solver's precision or NULL; stats may be NULL. */
 kss_status kss_solver_results(kss_solver s, double* evals, double* resid, void* evecs, int ld,

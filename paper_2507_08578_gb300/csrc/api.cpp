@@ -210,6 +210,7 @@ kss_status kss_destroy(kss_ctx ctx) {
   }
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  aux_release(ctx);
   ctx_release_solver(ctx);
   prof_release(ctx);
   ctx->ws_local.release();

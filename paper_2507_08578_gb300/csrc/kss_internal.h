@@ -121,6 +121,7 @@ struct kss_ctx_s {
   kss::DevBuf ws_occ, ws_rho;      // density build: occupations, per-group partial densities
   kss::DevBuf ws_gpack;            // Gamma-packed raw transforms (pairs x ld)
   kss::DevBuf ws_tune;             // scratch slab of the autotuner
+  std::vector<kss_ctx_s*> aux;     // helper contexts on their own streams (concurrent Rayleigh-Ritz)
 };
 
 struct kss_sys_s {
@@ -186,6 +187,9 @@ struct ProfScope {
   ~ProfScope();
 };
 void prof_resolve(kss_ctx ctx);  // synchronise and fold pending event pairs into totals
+void prof_fold(kss_ctx ctx);     // add the helper contexts' counts and times into ctx's
+kss_ctx aux_ctx(kss_ctx ctx, int i);  // helper context i of ctx (created on first use)
+void aux_release(kss_ctx ctx);
 void prof_release(kss_ctx ctx);
 #define KSS_PROF(ctx, name)                                   \
   static const int kss_prof_id_ = ::kss::prof_register(name); \

@@ -95,6 +95,25 @@ void prof_resolve(kss_ctx ctx) {
   p.pending.clear();
 }
 
+void prof_fold(kss_ctx ctx) {
+  for (kss_ctx w : ctx->aux) {
+    prof_resolve(w);
+    Prof& a = w->prof;
+    if (ctx->prof.count.size() < a.count.size()) {
+      ctx->prof.count.resize(a.count.size(), 0);
+      ctx->prof.ms.resize(a.count.size(), 0.0);
+    }
+    for (size_t i = 0; i < a.count.size(); ++i) {
+      ctx->prof.count[i] += a.count[i];
+      ctx->prof.ms[i] += a.ms[i];
+    }
+    ctx->prof.launches += a.launches;
+    a.launches = 0;
+    std::fill(a.count.begin(), a.count.end(), 0);
+    std::fill(a.ms.begin(), a.ms.end(), 0.0);
+  }
+}
+
 void prof_release(kss_ctx ctx) {
   prof_resolve(ctx);
   for (auto e : ctx->prof.free_ev) cudaEventDestroy(e);
@@ -110,6 +129,7 @@ extern "C" {
 kss_status kss_profile_enable(kss_ctx ctx, int enable) {
   if (!ctx) return KSS_EINVAL;
   prof_resolve(ctx);
+  prof_fold(ctx);
   ctx->prof.on = enable != 0;
   ctx->prof.launches = 0;
   std::fill(ctx->prof.count.begin(), ctx->prof.count.end(), 0);
@@ -120,6 +140,7 @@ kss_status kss_profile_enable(kss_ctx ctx, int enable) {
 kss_status kss_profile_count(kss_ctx ctx, int* nkernels, long long* launches) {
   if (!ctx) return KSS_EINVAL;
   prof_resolve(ctx);
+  prof_fold(ctx);
   if (nkernels) *nkernels = (int)ctx->prof.count.size();
   if (launches) *launches = ctx->prof.launches;
   return KSS_OK;
@@ -129,6 +150,7 @@ kss_status kss_profile_entry(kss_ctx ctx, int i, const char** name, long long* l
                              double* total_ms) {
   if (!ctx) return KSS_EINVAL;
   prof_resolve(ctx);
+  prof_fold(ctx);
   if (i < 0 || i >= (int)ctx->prof.count.size()) return KSS_EINVAL;
   if (name) *name = prof_name(i);
   if (launches) *launches = ctx->prof.count[i];

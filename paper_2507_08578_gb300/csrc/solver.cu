@@ -161,6 +161,35 @@ void ctx_release_solver(kss_ctx ctx) {
   ctx->cusolver = nullptr;
 }
 
+// Helper contexts: same device and settings, own non-blocking stream, own workspaces and
+// eigensolver handle, so that work issued on them can run beside the context stream's.
+kss_ctx aux_ctx(kss_ctx ctx, int i) {
+  while ((int)ctx->aux.size() <= i) {
+    std::unique_ptr<kss_ctx_s> w(new kss_ctx_s());
+    w->device = ctx->device;
+    w->nsm = ctx->nsm;
+    w->autotune = ctx->autotune;
+    cudaStream_t st = nullptr;
+    KSS_CHECK_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    w->stream = st;
+    w->own_stream = true;
+    ctx->aux.push_back(w.release());
+  }
+  return ctx->aux[i];
+}
+
+void aux_release(kss_ctx ctx) {
+  prof_fold(ctx);
+  for (kss_ctx w : ctx->aux) {
+    cudaStreamSynchronize(w->stream);
+    ctx_release_solver(w);
+    prof_release(w);
+    cudaStreamDestroy(w->stream);
+    delete w;
+  }
+  ctx->aux.clear();
+}
+
 void random_block(kss_ctx ctx, bool fp64, void* X, int npw, int nb, int ld, uint64_t seed,
                   int band0) {
   const long long n = (long long)npw * nb;
@@ -476,6 +505,8 @@ void refine_fp64(kss_solver_s* s) {
 
 namespace {
 
+void after_iterate(kss_solver_s* s);
+
 void solver_step(kss_solver_s* s) {
   kss_ctx ctx = s->sys->ctx;
   const auto t0 = std::chrono::steady_clock::now();
@@ -505,6 +536,12 @@ void solver_step(kss_solver_s* s) {
     s->iter += 1;
     s->ms_rr += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
   }
+  after_iterate(s);
+  s->ms_total += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Convergence bookkeeping after a Rayleigh-Ritz (and the FP64 refinement that ends a mixed solve).
+void after_iterate(kss_solver_s* s) {
   const double r = max_wanted(s);
   s->hist.push_back(r);
   if (s->f64) {
@@ -521,7 +558,78 @@ void solver_step(kss_solver_s* s) {
       s->done = true;
     }
   }
-  s->ms_total += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// One pipelined iteration of several solvers of one context: the filter of solver u+1 is queued
+// on the context stream before the Rayleigh-Ritz of solver u is issued on a helper stream (the
+// eigensolver may block the host until its input is ready, and the queued filter keeps the GPU
+// busy meanwhile).  Every solver's blocks and the workspaces of each stream are disjoint; the
+// context stream waits for the helpers before the results are read.
+void step_many(kss_ctx ctx, const std::vector<kss_solver_s*>& us) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int n = (int)us.size();
+  constexpr int kAux = 2;
+  struct Roles { int y, prev, f1; };
+  std::vector<Roles> ro(n);
+  std::vector<cudaEvent_t> ev(n, nullptr);
+  std::vector<cudaEvent_t> jev(kAux, nullptr);
+  auto destroy = [&] {
+    for (auto e : ev) if (e) cudaEventDestroy(e);
+    for (auto e : jev) if (e) cudaEventDestroy(e);
+  };
+  try {
+    auto filter = [&](int u) {
+      kss_solver_s* s = us[u];
+      int fr[2], nf = 0;
+      for (int i = 0; i < 4; ++i)
+        if (i != s->ix && i != s->ihx) fr[nf++] = i;
+      int prev = -1;
+      const int y = chebyshev_filter(s, fr[0], &prev);
+      apply_block(s, s->f64, s->blk[y].p, s->blk[prev].p);
+      ro[u] = Roles{y, prev, fr[1]};
+      KSS_CHECK_CUDA(cudaEventCreateWithFlags(&ev[u], cudaEventDisableTiming));
+      KSS_CHECK_CUDA(cudaEventRecord(ev[u], ctx->stream));
+    };
+    auto rr = [&](int u) {
+      kss_solver_s* s = us[u];
+      kss_ctx w = aux_ctx(ctx, u % kAux);
+      w->prof.on = ctx->prof.on;
+      KSS_CHECK_CUDA(cudaStreamWaitEvent(w->stream, ev[u], 0));
+      rr_issue(s, s->f64, s->blk[ro[u].y].p, s->blk[ro[u].prev].p, s->blk[ro[u].f1].p, s->blk[s->ihx].p, w);
+    };
+    if (n > 0) filter(0);
+    for (int u = 0; u < n; ++u) {
+      if (u + 1 < n) filter(u + 1);
+      rr(u);
+    }
+    for (int i = 0; i < std::min(n, kAux); ++i) {
+      KSS_CHECK_CUDA(cudaEventCreateWithFlags(&jev[i], cudaEventDisableTiming));
+      KSS_CHECK_CUDA(cudaEventRecord(jev[i], ctx->aux[i]->stream));
+      KSS_CHECK_CUDA(cudaStreamWaitEvent(ctx->stream, jev[i], 0));
+    }
+    KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    KSS_CHECK_CUDA(cudaGetLastError());
+  } catch (...) {
+    for (kss_ctx w : ctx->aux) cudaStreamSynchronize(w->stream);
+    destroy();
+    throw;
+  }
+  destroy();
+  const double share =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() / std::max(n, 1);
+  for (int u = 0; u < n; ++u) {
+    kss_solver_s* s = us[u];
+    const auto t1 = std::chrono::steady_clock::now();
+    rr_finish_or_retry(s, s->f64, s->blk[ro[u].y].p, s->blk[ro[u].prev].p, s->blk[ro[u].f1].p, s->blk[s->ihx].p);
+    gamma_fix(s, s->f64, s->blk[ro[u].f1].p, s->blk[s->ihx].p);
+    s->ix = ro[u].f1;
+    s->iter += 1;
+    after_iterate(s);
+    const double own = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+    s->ms_filter += 0.5 * share;
+    s->ms_rr += 0.5 * share + own;
+    s->ms_total += share + own;
+  }
 }
 
 template <typename F>
@@ -630,6 +738,33 @@ kss_status kss_solver_step(kss_solver s, int* converged) {
     KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
     if (!s->done) solver_step(s);
     if (converged) *converged = s->converged ? 1 : 0;
+  });
+}
+
+kss_status kss_solver_step_many(int n, kss_solver const* solvers, int* converged) {
+  if (n < 0 || (n > 0 && !solvers)) return KSS_EINVAL;
+  if (n == 0) return KSS_OK;
+  for (int u = 0; u < n; ++u)
+    if (!solvers[u]) return KSS_EINVAL;
+  kss_ctx ctx = solvers[0]->sys->ctx;
+  for (int u = 1; u < n; ++u)
+    if (solvers[u]->sys->ctx != ctx) {
+      ctx->err = "kss_solver_step_many: the solvers belong to different contexts";
+      return KSS_EINVAL;
+    }
+  return guard(ctx, [&] {
+    KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    std::vector<kss_solver_s*> uniq, iter;
+    for (int u = 0; u < n; ++u)
+      if (std::find(uniq.begin(), uniq.end(), solvers[u]) == uniq.end()) uniq.push_back(solvers[u]);
+    for (kss_solver_s* s : uniq) {
+      if (s->done) continue;
+      if (!s->started) solver_step(s);  // the initial Rayleigh-Ritz is this call's step
+      else iter.push_back(s);
+    }
+    step_many(ctx, iter);
+    if (converged)
+      for (int u = 0; u < n; ++u) converged[u] = solvers[u]->converged ? 1 : 0;
   });
 }
 

@@ -114,6 +114,7 @@ def signatures() -> dict:
         "kss_solver_create": ([P, c_int, c_int, POINTER(kss_solve_opts), POINTER(c_void_p)], c_int),
         "kss_solver_destroy": ([P], c_int),
         "kss_solver_step": ([P, POINTER(c_int)], c_int),
+        "kss_solver_step_many": ([c_int, POINTER(P), POINTER(c_int)], c_int),
         "kss_solver_results": ([P, P, P, P, c_int, POINTER(kss_solve_stats)], c_int),
         "kss_chebfi_solve": ([P, c_int, c_int, POINTER(kss_solve_opts), P, P, c_int, P,
                               POINTER(kss_solve_stats)], c_int),
@@ -416,6 +417,19 @@ def kss_solver_step(s: Solver) -> bool:
     c = c_int()
     _check(lib().kss_solver_step(s.h, byref(c)), s.sys.ctx)
     return bool(c.value)
+
+
+def kss_solver_step_many(solvers) -> list:
+    """One iteration of every solver (same context), the Rayleigh-Ritz of one overlapping the
+    filter of the next; returns the converged flags."""
+    solvers = list(solvers)
+    n = len(solvers)
+    if n == 0:
+        return []
+    hs = (c_void_p * n)(*[sv.h.value for sv in solvers])
+    flags = (c_int * n)()
+    _check(lib().kss_solver_step_many(n, hs, flags), solvers[0].sys.ctx)
+    return [bool(f) for f in flags]
 
 
 def kss_solver_results(s: Solver, evecs=None):
