@@ -33,6 +33,16 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal); a CUDA-core FMA probe measured
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
 
 
+def bf16_peak():
+    """Dense BF16 tensor peak for a kernel timed inside a long step: the measured sustained cuBLAS
+    figure of this machine pool when the measured-peaks file is present, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "measured (sustained cuBLAS BF16)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback (sustained BF16)"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -210,12 +220,13 @@ def run_reference(args, rank: int):
 # ------------------------------------------------------------------------------------------------
 # GPU arm
 
-# DRAM bytes per band of the middle FFT pass on the C2 workload, from one ncu capture of the
-# production launch (dram__bytes_read.sum + dram__bytes_write.sum): pass_bw<double, 8, 12, 384>
-# moved 73.60 + 9.65 MB for a 27-band launch, pass_bw<float, 8, 12, 384> 69.93 + 7.26 MB for 54
-# bands.  Valid for that schedule only (the bench reports null traffic for any other).
-PASS_B_DRAM_PER_BAND = {"fp64": (73.595136e6 + 9.649664e6) / 27, "mixed": (69.929472e6 + 7.256832e6) / 54}
-PASS_B_SCHEDULE = "8x12 @384"
+# DRAM bytes per band of the middle FFT pass on the C2 workload, from one ncu capture of two
+# production launches each (dram__bytes_read.sum + dram__bytes_write.sum, mean of the two):
+# pass_bw<double, 8, 12, 384> moved 73.53 + 7.28 MB per 27-band launch, pass_bw<float, 12, 8, 384>
+# 69.94 + 6.15 MB per 54-band launch.  Valid for that kernel and schedule only (the bench reports
+# null traffic when the autotuner picked another).
+PASS_B_DRAM_PER_BAND = {"fp64": (73.533824e6 + 7.281024e6) / 27, "mixed": (69.942784e6 + 6.154112e6) / 54}
+PASS_B_SCHEDULE = {"fp64": "8x12 @384", "mixed": "12x8 @384"}
 
 
 def algorithmic_work(s, npw, nb, degree, box, applies, rr_calls):
@@ -237,7 +248,9 @@ def algorithmic_work(s, npw, nb, degree, box, applies, rr_calls):
 
 
 def family(name: str) -> str:
-    base = name.split("<")[0]
+    """Kernel family of a profile entry: the name without template arguments, with its tag
+    ("gemm_cn_partial<f64>:cprj" -> "gemm_cn_partial:cprj", "local_pass_b<f32>" -> "local_pass_b")."""
+    base = name.split("<")[0].split(":")[0]
     tag = name.split(":", 1)[1] if ":" in name else ""
     return base + (":" + tag if tag else "")
 
@@ -351,6 +364,22 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                               "FP32 CUDA-core rate from 152 SMs x 128 lanes x 2 x 2070 MHz"),
                 "launches": dl, "avg_launch_ms": dms / dl}
 
+    # ---- the projector products on the tensor cores (mixed form) ----
+    proj = None
+    tc_fams = [f for f in ("tc_gemm_bf16x3:cprj", "tc_gemm_bf16x3:nonlocal") if f in fam]
+    if args.form == "mixed" and tc_fams:
+        tl = sum(fam[f][0] for f in tc_fams)
+        tms = sum(fam[f][1] for f in tc_fams)
+        alg = len(tc_fams) * applies * 8.0 * s.nproj * npw  # conventional complex count per product
+        ach = alg / (tms / 1000.0) / 1e12
+        pk, pnote = bf16_peak()
+        proj = {"kernel": "tc_gemm_bf16x3 (cprj + nonlocal)", "bound": "tensor", "achieved": ach,
+                "peak": pk, "unit": "TFLOP/s", "frac": ach / pk, "peak_note": pnote,
+                "executed_frac": 3 * ach / pk,
+                "executed_note": "split BF16: three BF16 products (hi*hi, hi*lo, lo*hi) per "
+                                 "complex64 product, each as many flops as the conventional count",
+                "launches": tl, "avg_launch_ms": tms / tl}
+
     # ---- end to end through the public API with host buffers ----
     e2e = None
     if args.e2e_steps > 0:
@@ -403,7 +432,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     sched = [f"{e['N1']}x{e['N']}^2 W3<={e['W3']}: {e['A']}x{e['B']} @{e['threads']} "
              f"({e['ncand']} timed)" for e in table]
     if roof is not None and roof["kernel"] == "local_pass_b" and args.workload == "c2" and \
-            all(f"{e['A']}x{e['B']} @{e['threads']}" == PASS_B_SCHEDULE for e in table):
+            all(f"{e['A']}x{e['B']} @{e['threads']}" == PASS_B_SCHEDULE[args.form] for e in table):
         roof["traffic"] = PASS_B_DRAM_PER_BAND[args.form] * applies / roof["launches"]
         roof["traffic_note"] = ("DRAM bytes per launch: ncu bytes per band of this kernel and schedule x the "
                                 "bands per launch of this run")
@@ -426,6 +455,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "gpu_launches": launches,
             "clocks": ck,
             "roofline": roof,
+            "roofline_projector_gemm": proj,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "max_residual_after": float(resid),

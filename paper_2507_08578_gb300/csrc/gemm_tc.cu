@@ -6,16 +6,22 @@
 //
 // Each complex product is written as one real GEMM D = A_tc * B_tc^T with both operands K-major
 // in BF16:
-//   * complex -> real: interleaved (re, im) pairs along K; the imaginary part comes from extra
-//     rows of one operand holding (im, -re) (for A^H B) or (im, re) / (re, -im) (for A B);
-//   * split precision: every FP32 value x = hi + lo with hi = bf16(x), lo = bf16(x - hi); the
-//     K axis is tripled so that one GEMM accumulates hi*hi + hi*lo + lo*hi in FP32 (TMEM).
-// The GEMM kernel: one CTA per 128 x 128 output tile and K split across CTAs; a TMA producer
-// thread fills a 6-stage ring of 128B-swizzled 128 x 64 BF16 tiles, one thread issues
-// tcgen05.mma (M=128, N=128, K=16) into a TMEM accumulator, and four warps read TMEM back with
-// tcgen05.ld and store FP32 partial sums.  A reduction kernel adds the K-splits in a fixed order
-// and forms the complex result.  Every mbarrier wait is bounded; on time-out the kernel raises
-// an error flag, drains its own copies, frees TMEM and returns.
+//   * complex -> real: the B rows hold interleaved (re, im) pairs along K; every complex row i of
+//     A becomes two real rows, 2i giving the real and 2i + 1 the imaginary part of output row i
+//     ((re, im) and (-im, re) for A^H B; (re, -im) and (im, re) for A B), so the extra rows sit on
+//     the A side, which for the projector products is the static table prepared once;
+//   * split precision: every FP32 value x = hi + lo with hi = bf16(x), lo = bf16(x - hi); each
+//     operand row holds its hi copy followed by its lo copy, and for every k-block the kernel
+//     accumulates hi*hi + hi*lo + lo*hi in FP32 (TMEM) from the same four staged tiles.
+// The GEMM kernel: one CTA per 128 x 128 output tile (tiles with the same A rows adjacent in
+// launch order, so A is fetched from HBM once and re-read from L2) and K split across CTAs so
+// that the grid fills the SMs in as few waves as possible; a TMA producer thread fills a 3-stage
+// ring, each stage holding the hi and lo 128B-swizzled 128 x 64 BF16 tiles of both operands; one
+// thread issues tcgen05.mma (M=128, N=128, K=16; three per 16-wide slice) into a TMEM
+// accumulator, and four warps read TMEM back with tcgen05.ld and store FP32 partial sums.  A
+// reduction kernel adds the K-splits in a fixed order and forms the complex result.  Every
+// mbarrier wait is bounded; on time-out the kernel raises an error flag, drains its own copies,
+// frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -33,10 +39,11 @@ namespace {
 constexpr int TM = 128;   // UMMA M (rows of A_tc per tile)
 constexpr int TN = 128;   // UMMA N (rows of B_tc per tile)
 constexpr int TK = 64;    // BF16 per k-block: one 128-byte swizzle row
-constexpr int STAGES = 6;
+constexpr int STAGES = 3;
 constexpr int kTcThreads = 128;
 constexpr uint32_t kTileBytes = TM * TK * 2;  // 16 KB (A and B tiles are the same size)
-constexpr size_t kTcSmem = 1024 + (size_t)STAGES * 2 * kTileBytes + 256;
+constexpr uint32_t kStageBytes = 4 * kTileBytes;  // A hi, A lo, B hi, B lo
+constexpr size_t kTcSmem = 1024 + (size_t)STAGES * kStageBytes + 256;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -93,14 +100,13 @@ __host__ __device__ constexpr uint32_t instr_desc() {
 
 __global__ void __launch_bounds__(kTcThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               float* __restrict__ D, int Mr, int Nr, int kb_per_split, int kb_total,
+               float* __restrict__ D, int Mr, int Nr, int tnn, int kb_per_split, int kb_total, int kp,
                int* __restrict__ err, float2* __restrict__ Cf, long long ldc, float ar, float ai, float br,
                float bi) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = base;
-  unsigned char* sB = base + STAGES * kTileBytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * kTileBytes);
+  // stage s: A hi, A lo, B hi, B lo tiles at base + s * kStageBytes
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * kStageBytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + STAGES;
   uint64_t* done = bars + 2 * STAGES;
@@ -108,8 +114,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   __shared__ int fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tm = blockIdx.x, tn = blockIdx.y;
-  const int kb0 = blockIdx.z * kb_per_split;
+  const int tm = blockIdx.x / tnn, tn = blockIdx.x - tm * tnn;
+  const int kb0 = blockIdx.y * kb_per_split;
   const int nkb = max(0, min(kb_total, kb0 + kb_per_split) - kb0);
 
   if (tid == 0) {
@@ -140,10 +146,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         break;
       }
       if (*(volatile int*)&fail) break;
-      mbar_expect_tx(smem_u32(&full[s]), 2 * kTileBytes);
-      const int x = (kb0 + kb) * TK;
-      tma_load_2d(smem_u32(sA + s * kTileBytes), &tmA, x, tm * TM, smem_u32(&full[s]));
-      tma_load_2d(smem_u32(sB + s * kTileBytes), &tmB, x, tn * TN, smem_u32(&full[s]));
+      mbar_expect_tx(smem_u32(&full[s]), kStageBytes);
+      const int x = (kb0 + kb) * TK;  // hi copy at x, lo copy at x + kp (both multiples of 64)
+      const uint32_t st = smem_u32(base + s * kStageBytes), fb = smem_u32(&full[s]);
+      tma_load_2d(st, &tmA, x, tm * TM, fb);
+      tma_load_2d(st + kTileBytes, &tmA, x + kp, tm * TM, fb);
+      tma_load_2d(st + 2 * kTileBytes, &tmB, x, tn * TN, fb);
+      tma_load_2d(st + 3 * kTileBytes, &tmB, x + kp, tn * TN, fb);
       ++issued;
     }
     // Drain: every issued copy has landed before the CTA can leave (bounded).
@@ -159,15 +168,20 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(sA + s * kTileBytes), b0 = smem_u32(sB + s * kTileBytes);
+      const uint32_t ah = smem_u32(base + s * kStageBytes), al = ah + kTileBytes;
+      const uint32_t bh = ah + 2 * kTileBytes, bl = ah + 3 * kTileBytes;
 #pragma unroll
       for (int k = 0; k < TK / 16; ++k) {
-        const uint64_t ad = smem_desc(a0 + 32 * k), bd = smem_desc(b0 + 32 * k);
+        // hi*hi, hi*lo, lo*hi for this 16-wide slice (32 bytes into each swizzled row)
+        const uint64_t dah = smem_desc(ah + 32 * k), dal = smem_desc(al + 32 * k);
+        const uint64_t dbh = smem_desc(bh + 32 * k), dbl = smem_desc(bl + 32 * k);
         const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
         asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            "{\n .reg .pred p, q;\n setp.ne.b32 p, %6, 0;\n setp.eq.b32 q, %6, %6;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %5, p;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %3, %5, q;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %4, %2, %5, q;\n}\n" ::"r"(tmem),
+            "l"(dah), "l"(dbh), "l"(dbl), "l"(dal), "r"(idesc), "r"(acc));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&empty[s])) : "memory");
     }
@@ -180,7 +194,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   if (!ok) atomicExch(&fail, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int row = tm * TM + warp * 32 + lane;
-  float* Dz = D + (size_t)blockIdx.z * Mr * Nr;
+  float* Dz = D + (size_t)blockIdx.y * Mr * Nr;
   if (ok && nkb > 0) {
 #pragma unroll 1
     for (int c0 = 0; c0 < TN; c0 += 32) {
@@ -196,7 +210,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (Cf) {
-        // Fused complex epilogue (one K-split, A B form with interleaved rows): accumulator row 2i
+        // Fused complex epilogue (no K-split; interleaved A rows): accumulator row 2i
         // holds Re C(i, col), row 2i+1 Im C(i, col); the pair sits in adjacent lanes of this warp.
         float w[32];
 #pragma unroll
@@ -242,9 +256,10 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
 }
 
 // K-major complex source (column c has K complex values at src + c*ld) -> BF16 rows of length
-// 3*Kp: role A = [hi | hi | lo], role B = [hi | lo | hi].  swap: use (im, -re) pairs.
+// 2*Kp, [hi | lo] of interleaved pairs.  pair = 0: row c holds (re, im).  pair = 1 (the A operand
+// of A^H B): row 2c holds (re, im) and row 2c + 1 holds (-im, re).
 __global__ void prep_kmajor(const float2* __restrict__ src, long long ld, int K, int ncols, int Kp,
-                            __nv_bfloat16* __restrict__ dst, int row0, int roleB, int swap) {
+                            __nv_bfloat16* __restrict__ dst, int pair) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int half = Kp / 2;
   if (idx >= (long long)ncols * half) return;
@@ -255,24 +270,25 @@ __global__ void prep_kmajor(const float2* __restrict__ src, long long ld, int K,
     re = v.x;
     im = v.y;
   }
-  float u0 = re, u1 = im;
-  if (swap) { u0 = im; u1 = -re; }
-  __nv_bfloat16 h0, l0, h1, l1;
-  split_bf16(u0, h0, l0);
-  split_bf16(u1, h1, l1);
-  __nv_bfloat16* row = dst + (size_t)(row0 + c) * (3 * (size_t)Kp);
-  const int e = 2 * k;
-  row[e] = h0;
-  row[e + 1] = h1;
-  row[Kp + e] = roleB ? l0 : h0;
-  row[Kp + e + 1] = roleB ? l1 : h1;
-  row[2 * Kp + e] = roleB ? h0 : l0;
-  row[2 * Kp + e + 1] = roleB ? h1 : l1;
+  __nv_bfloat16 hr, lr, hi_, li_;
+  split_bf16(re, hr, lr);
+  split_bf16(im, hi_, li_);
+  const size_t rowlen = 2 * (size_t)Kp;
+  __nv_bfloat162* r0 = reinterpret_cast<__nv_bfloat162*>(dst + (size_t)(pair ? 2 * c : c) * rowlen);
+  r0[k] = __halves2bfloat162(hr, hi_);
+  r0[half + k] = __halves2bfloat162(lr, li_);
+  if (pair) {
+    __nv_bfloat16 hmi, lmi;
+    split_bf16(-im, hmi, lmi);
+    __nv_bfloat162* r1 = reinterpret_cast<__nv_bfloat162*>(dst + (size_t)(2 * c + 1) * rowlen);
+    r1[k] = __halves2bfloat162(hmi, hr);
+    r1[half + k] = __halves2bfloat162(lmi, lr);
+  }
 }
 
 // M-major complex A (element (i, k) at src[k*ld + i]) -> BF16 K-major rows for C = A B:
 // row 2i: (re, -im) pairs, row 2i + 1: (im, re) pairs (so the real and imaginary parts of output
-// row i are adjacent accumulator rows), role A [hi | hi | lo].  32x32 smem transpose.
+// row i are adjacent accumulator rows), each row [hi | lo].  32x32 smem transpose.
 __global__ void prep_mmajor(const float2* __restrict__ src, long long ld, int M, int K, int Kp,
                             __nv_bfloat16* __restrict__ dst) {
   __shared__ float2 t[32][33];
@@ -291,43 +307,38 @@ __global__ void prep_mmajor(const float2* __restrict__ src, long long ld, int M,
     split_bf16(v.x, hr, lr);
     split_bf16(v.y, hi_, li_);
     split_bf16(-v.y, hmi, lmi);
-    __nv_bfloat16* ra = dst + (size_t)(2 * i) * (3 * (size_t)Kp);
-    __nv_bfloat16* rb = dst + (size_t)(2 * i + 1) * (3 * (size_t)Kp);
-    const int e = 2 * k;
-    ra[e] = hr; ra[e + 1] = hmi;
-    ra[Kp + e] = hr; ra[Kp + e + 1] = hmi;
-    ra[2 * Kp + e] = lr; ra[2 * Kp + e + 1] = lmi;
-    rb[e] = hi_; rb[e + 1] = hr;
-    rb[Kp + e] = hi_; rb[Kp + e + 1] = hr;
-    rb[2 * Kp + e] = li_; rb[2 * Kp + e + 1] = lr;
+    __nv_bfloat162* ra = reinterpret_cast<__nv_bfloat162*>(dst + (size_t)(2 * i) * (2 * (size_t)Kp));
+    __nv_bfloat162* rb = reinterpret_cast<__nv_bfloat162*>(dst + (size_t)(2 * i + 1) * (2 * (size_t)Kp));
+    ra[k] = __halves2bfloat162(hr, hmi);
+    ra[half + k] = __halves2bfloat162(lr, lmi);
+    rb[k] = __halves2bfloat162(hi_, hr);
+    rb[half + k] = __halves2bfloat162(li_, lr);
   }
 }
 
 // C (complex, col-major ldc) = alpha * D + beta * C with D assembled from the K-split partials
-// (col-major Mr x Nr).  form 0 (A^H B): re = D(i, j), im = D(i, N + j); form 1 (A B):
-// re = D(2i, j), im = D(2i + 1, j).
+// (col-major Mr x Nr, Mr = 2M): re = D(2i, j), im = D(2i + 1, j).
 __global__ void tc_combine(const float* __restrict__ P, int nsplit, int Mr, int Nr, int M, int N,
-                           int form, float2* __restrict__ C, long long ldc, float ar, float ai,
-                           float br, float bi) {
+                           float2* __restrict__ C, long long ldc, float ar, float ai, float br, float bi) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)M * N) return;
   const int i = (int)(idx % M), j = (int)(idx / M);
-  const size_t oR = form == 0 ? (size_t)j * Mr + i : (size_t)j * Mr + 2 * i;
-  const size_t oI = form == 0 ? (size_t)(N + j) * Mr + i : (size_t)j * Mr + (2 * i + 1);
+  const size_t o = (size_t)j * Mr + 2 * i;
   float sr = 0.f, si = 0.f;
   const size_t stride = (size_t)Mr * Nr;
   for (int z = 0; z < nsplit; ++z) {
-    sr += P[z * stride + oR];
-    si += P[z * stride + oI];
+    const float2 v = *reinterpret_cast<const float2*>(P + z * stride + o);
+    sr += v.x;
+    si += v.y;
   }
   float2 out;
   out.x = ar * sr - ai * si;
   out.y = ar * si + ai * sr;
   float2* dst = C + (size_t)j * ldc + i;
   if (br != 0.f || bi != 0.f) {
-    const float2 o = *dst;
-    out.x += br * o.x - bi * o.y;
-    out.y += br * o.y + bi * o.x;
+    const float2 o2 = *dst;
+    out.x += br * o2.x - bi * o2.y;
+    out.y += br * o2.y + bi * o2.x;
   }
   *dst = out;
 }
@@ -369,35 +380,44 @@ int sms(kss_ctx ctx) {
   return ctx->nsm;
 }
 
-// D partials = A_tc (Mr x Kt) * B_tc (Nr x Kt)^T, then combine into complex C.
-void run_tc(kss_ctx ctx, const __nv_bfloat16* Atc, int Mr, const __nv_bfloat16* Btc, int Nr, int Kt,
-            int form, int M, int N, float2* C, int ldc, double ar, double ai, double br, double bi,
-            const char* tag) {
+// C (M x N complex) = alpha * A_tc (2M x 2Kp) * B_tc (N x 2Kp)^T + beta * C over the three hi/lo
+// products: written by the GEMM kernel itself without a K-split, else through partial sums.
+void run_tc(kss_ctx ctx, const __nv_bfloat16* Atc, const __nv_bfloat16* Btc, int Kp, int M, int N,
+            float2* C, int ldc, double ar, double ai, double br, double bi, const char* tag) {
+  const int Mr = 2 * M, Nr = N;
   const int tmn = (Mr + TM - 1) / TM, tnn = (Nr + TN - 1) / TN;
-  const int kb_total = Kt / TK;
-  const int tiles = tmn * tnn;
-  int splits = std::max(1, std::min(kb_total, (sms(ctx) + tiles - 1) / tiles));
-  const int kps = (kb_total + splits - 1) / splits;
+  const int kb_total = Kp / TK;
+  const long long tiles = (long long)tmn * tnn;
+  if (tiles > 0x7fffffffLL) fail(KSS_EINVAL, "tensor-core GEMM: too many output tiles");
+  // K-split plan.  One CTA fits per SM (the ring takes ~194 KB of shared memory).  With at least
+  // as many output tiles as SMs there is no split (the kernel writes the complex result itself);
+  // otherwise split K so that the grid fills the SMs in one wave, keeping at least 8 k-blocks per
+  // CTA.  Every extra split costs a CTA's fixed work (TMEM allocation, pipeline fill, epilogue)
+  // and one more set of FP32 partial sums written and read back, so more than one wave of split
+  // CTAs does not pay.
+  const int nsm = sms(ctx);
+  int splits = 1;
+  if (tiles < nsm) splits = (int)std::max(1LL, std::min<long long>(nsm / tiles, kb_total / 8));
+  int kps = (kb_total + splits - 1) / splits;
   splits = (kb_total + kps - 1) / kps;
   const size_t pbytes = (size_t)splits * Mr * Nr * sizeof(float);
-  if (!(form == 1 && splits == 1)) ctx->tc_part.ensure(pbytes);
+  if (splits > 1) ctx->tc_part.ensure(pbytes);
   if (!ctx->tc_err.p) {
     ctx->tc_err.alloc(sizeof(int));
     KSS_CHECK_CUDA(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), ctx->stream));
   }
-  const CUtensorMap ma = make_map(Atc, Mr, Kt), mb = make_map(Btc, Nr, Kt);
+  const CUtensorMap ma = make_map(Atc, Mr, 2 * Kp), mb = make_map(Btc, Nr, 2 * Kp);
   static bool attr = false;
   if (!attr) {
     KSS_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
     attr = true;
   }
-  // A B form without a K-split: the kernel writes the complex result itself (no partial sums)
-  const bool fused = form == 1 && splits == 1;
+  const bool fused = splits == 1;
   {
     ProfScope ps(ctx, prof_register((std::string("tc_gemm_bf16x3:") + tag).c_str()));
-    tc_gemm_kernel<<<dim3(tmn, tnn, splits), kTcThreads, kTcSmem, ctx->stream>>>(
-        ma, mb, ctx->tc_part.as<float>(), Mr, Nr, kps, kb_total, ctx->tc_err.as<int>(), fused ? C : nullptr,
-        ldc, (float)ar, (float)ai, (float)br, (float)bi);
+    tc_gemm_kernel<<<dim3((unsigned)tiles, splits, 1), kTcThreads, kTcSmem, ctx->stream>>>(
+        ma, mb, ctx->tc_part.as<float>(), Mr, Nr, tnn, kps, kb_total, Kp, ctx->tc_err.as<int>(),
+        fused ? C : nullptr, ldc, (float)ar, (float)ai, (float)br, (float)bi);
   }
   if (fused) {
     KSS_CHECK_CUDA(cudaGetLastError());
@@ -407,7 +427,7 @@ void run_tc(kss_ctx ctx, const __nv_bfloat16* Atc, int Mr, const __nv_bfloat16* 
   {
     ProfScope ps(ctx, prof_register((std::string("tc_combine:") + tag).c_str()));
     tc_combine<<<(unsigned)((mn + 255) / 256), 256, 0, ctx->stream>>>(
-        ctx->tc_part.as<float>(), splits, Mr, Nr, M, N, form, C, ldc, (float)ar, (float)ai, (float)br, (float)bi);
+        ctx->tc_part.as<float>(), splits, Mr, Nr, M, N, C, ldc, (float)ar, (float)ai, (float)br, (float)bi);
   }
   KSS_CHECK_CUDA(cudaGetLastError());
 }
@@ -420,52 +440,44 @@ int kpad(int K) { return ((2 * K + TK - 1) / TK) * TK; }
 void tc_gemm_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                 void* C, int ldc, double ar, double ai, double br, double bi, const char* tag) {
   if (M <= 0 || N <= 0 || K <= 0) return;
-  const int Kp = kpad(K), Kt = 3 * Kp;
-  const size_t abytes = (size_t)M * Kt * 2, bbytes = (size_t)2 * N * Kt * 2;
-  ctx->tc_a.ensure(abytes);
-  ctx->tc_b.ensure(bbytes);
+  const int Kp = kpad(K);
+  ctx->tc_a.ensure(tc_split_cn_bytes(M, K));
+  ctx->tc_b.ensure((size_t)N * 2 * Kp * 2);
   __nv_bfloat16* Atc = ctx->tc_a.as<__nv_bfloat16>();
-  __nv_bfloat16* Btc = ctx->tc_b.as<__nv_bfloat16>();
   {
     ProfScope ps(ctx, prof_register("tc_prep"));
-    const long long na = (long long)M * (Kp / 2), nb = (long long)N * (Kp / 2);
-    prep_kmajor<<<(unsigned)((na + 255) / 256), 256, 0, ctx->stream>>>((const float2*)A, lda, K, M, Kp, Atc, 0, 0, 0);
-    prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, 0, 1, 0);
-    prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, N, 1, 1);
+    const long long na = (long long)M * (Kp / 2);
+    prep_kmajor<<<(unsigned)((na + 255) / 256), 256, 0, ctx->stream>>>((const float2*)A, lda, K, M, Kp, Atc, 1);
   }
-  run_tc(ctx, Atc, M, Btc, 2 * N, Kt, 0, M, N, (float2*)C, ldc, ar, ai, br, bi, tag);
+  tc_gemm_cn_split(ctx, M, N, K, Atc, B, ldb, C, ldc, ar, ai, br, bi, tag);
 }
 
 // C (M x N) = alpha A B + beta C, complex64; A: M x K (lda, M contiguous), B: K x N (ldb).
 void tc_gemm_nn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                 void* C, int ldc, double ar, double ai, double br, double bi, const char* tag) {
   if (M <= 0 || N <= 0 || K <= 0) return;
-  const int Kp = kpad(K), Kt = 3 * Kp;
-  const size_t abytes = (size_t)2 * M * Kt * 2, bbytes = (size_t)N * Kt * 2;
-  ctx->tc_a.ensure(abytes);
-  ctx->tc_b.ensure(bbytes);
+  const int Kp = kpad(K);
+  ctx->tc_a.ensure(tc_split_nn_bytes(M, K));
   __nv_bfloat16* Atc = ctx->tc_a.as<__nv_bfloat16>();
-  __nv_bfloat16* Btc = ctx->tc_b.as<__nv_bfloat16>();
   {
     ProfScope ps(ctx, prof_register("tc_prep"));
     dim3 g((M + 31) / 32, (Kp / 2 + 31) / 32);
     prep_mmajor<<<g, dim3(32, 8), 0, ctx->stream>>>((const float2*)A, lda, M, K, Kp, Atc);
-    const long long nb = (long long)N * (Kp / 2);
-    prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, 0, 1, 0);
   }
-  run_tc(ctx, Atc, 2 * M, Btc, N, Kt, 1, M, N, (float2*)C, ldc, ar, ai, br, bi, tag);
+  tc_gemm_nn_split(ctx, M, N, K, Atc, B, ldb, C, ldc, ar, ai, br, bi, tag);
 }
 
 // Forms with A already split (static operands such as the projector table, prepared once with
-// tc_split_* and kept): only B is prepared per call.
-size_t tc_split_cn_bytes(int M, int K) { return (size_t)M * 3 * kpad(K) * 2; }
-size_t tc_split_nn_bytes(int M, int K) { return (size_t)2 * M * 3 * kpad(K) * 2; }
+// tc_split_* and kept): only B is prepared per call.  Both split forms of an M x K complex A hold
+// 2M rows of 2 * kpad(K) BF16 values.
+size_t tc_split_cn_bytes(int M, int K) { return (size_t)2 * M * 2 * kpad(K) * 2; }
+size_t tc_split_nn_bytes(int M, int K) { return (size_t)2 * M * 2 * kpad(K) * 2; }
 
 void tc_split_cn(kss_ctx ctx, int M, int K, const void* A, int lda, void* Atc) {
   const int Kp = kpad(K);
   const long long na = (long long)M * (Kp / 2);
   prep_kmajor<<<(unsigned)((na + 255) / 256), 256, 0, ctx->stream>>>((const float2*)A, lda, K, M, Kp,
-                                                                    (__nv_bfloat16*)Atc, 0, 0, 0);
+                                                                    (__nv_bfloat16*)Atc, 1);
   KSS_CHECK_CUDA(cudaGetLastError());
 }
 
@@ -476,33 +488,31 @@ void tc_split_nn(kss_ctx ctx, int M, int K, const void* A, int lda, void* Atc) {
   KSS_CHECK_CUDA(cudaGetLastError());
 }
 
+namespace {
+// B operand (K x N complex, ldb) -> N BF16 rows [hi | lo] of (re, im) pairs in the context buffer.
+const __nv_bfloat16* prep_b(kss_ctx ctx, int N, int K, const void* B, int ldb) {
+  const int Kp = kpad(K);
+  ctx->tc_b.ensure((size_t)N * 2 * Kp * 2);
+  __nv_bfloat16* Btc = ctx->tc_b.as<__nv_bfloat16>();
+  ProfScope ps(ctx, prof_register("tc_prep"));
+  const long long nb = (long long)N * (Kp / 2);
+  prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, 0);
+  return Btc;
+}
+}  // namespace
+
 void tc_gemm_cn_split(kss_ctx ctx, int M, int N, int K, const void* Atc, const void* B, int ldb, void* C, int ldc,
                       double ar, double ai, double br, double bi, const char* tag) {
   if (M <= 0 || N <= 0 || K <= 0) return;
-  const int Kp = kpad(K), Kt = 3 * Kp;
-  ctx->tc_b.ensure((size_t)2 * N * Kt * 2);
-  __nv_bfloat16* Btc = ctx->tc_b.as<__nv_bfloat16>();
-  {
-    ProfScope ps(ctx, prof_register("tc_prep"));
-    const long long nb = (long long)N * (Kp / 2);
-    prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, 0, 1, 0);
-    prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, N, 1, 1);
-  }
-  run_tc(ctx, (const __nv_bfloat16*)Atc, M, Btc, 2 * N, Kt, 0, M, N, (float2*)C, ldc, ar, ai, br, bi, tag);
+  const __nv_bfloat16* Btc = prep_b(ctx, N, K, B, ldb);
+  run_tc(ctx, (const __nv_bfloat16*)Atc, Btc, kpad(K), M, N, (float2*)C, ldc, ar, ai, br, bi, tag);
 }
 
 void tc_gemm_nn_split(kss_ctx ctx, int M, int N, int K, const void* Atc, const void* B, int ldb, void* C, int ldc,
                       double ar, double ai, double br, double bi, const char* tag) {
   if (M <= 0 || N <= 0 || K <= 0) return;
-  const int Kp = kpad(K), Kt = 3 * Kp;
-  ctx->tc_b.ensure((size_t)N * Kt * 2);
-  __nv_bfloat16* Btc = ctx->tc_b.as<__nv_bfloat16>();
-  {
-    ProfScope ps(ctx, prof_register("tc_prep"));
-    const long long nb = (long long)N * (Kp / 2);
-    prep_kmajor<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>((const float2*)B, ldb, K, N, Kp, Btc, 0, 1, 0);
-  }
-  run_tc(ctx, (const __nv_bfloat16*)Atc, 2 * M, Btc, N, Kt, 1, M, N, (float2*)C, ldc, ar, ai, br, bi, tag);
+  const __nv_bfloat16* Btc = prep_b(ctx, N, K, B, ldb);
+  run_tc(ctx, (const __nv_bfloat16*)Atc, Btc, kpad(K), M, N, (float2*)C, ldc, ar, ai, br, bi, tag);
 }
 
 // Device-side failure flag of the tensor-core kernels (bounded waits that gave up).

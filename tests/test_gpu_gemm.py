@@ -35,6 +35,8 @@ SHAPES = [  # (op, M, N, K)
     (1, 1503, 20, 16),      # C1 nonlocal accumulation
     (1, 3001, 70, 37),      # ragged
     (1, 2000, 140, 140),    # rotation-like
+    (1, 100, 30, 4000),     # A B form with a K-split (partial sums + combine)
+    (0, 1300, 1300, 64),    # more output tiles than SMs (several waves, no K-split)
 ]
 
 
