@@ -230,6 +230,7 @@ kss_status kss_destroy(kss_ctx ctx) {
 kss_status kss_setup(kss_ctx ctx, const kss_cell* cell, const kss_atoms* atoms, kss_sys* out) {
   if (!ctx) return KSS_EINVAL;
   return guard(ctx, [&] {
+    KSS_NVTX("setup");
     KSS_REQUIRE(cell && atoms && out, "kss_setup: null argument");
     *out = nullptr;
     KSS_REQUIRE(cell->ecut > 0 && std::isfinite(cell->ecut), "ecut must be positive");
@@ -511,6 +512,7 @@ kss_status kss_apply_H(kss_sys sys, int ik, int nb, const void* psi, void* hpsi,
                        kss_precision prec) {
   if (!sys) return KSS_EINVAL;
   return guard(sys->ctx, [&] {
+    KSS_NVTX("apply_H");
     KSS_CHECK_CUDA(cudaSetDevice(sys->ctx->device));
     apply_h(sys, ik, nb, psi, nullptr, hpsi, ld, ChebCoef{1.0, 0.0, 0.0}, prec);
   });

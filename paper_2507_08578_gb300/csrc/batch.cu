@@ -488,6 +488,7 @@ void BatchEngine::launch_filter_t() {
 }
 
 void BatchEngine::run_filter() {
+  KSS_NVTX("batch_filter");
   // The graph runs the largest effective degree among the units; a unit with a smaller one sits
   // out the remaining steps (its items are marked idle).  A change of that largest degree
   // changes the launch sequence and re-captures the graph.
@@ -639,6 +640,7 @@ void BatchEngine::decide(kss_solver_s* s) {
 void BatchEngine::rr_batched(const std::vector<kss_solver_s*>& us, const std::vector<int>& y,
                              const std::vector<int>& hy, const std::vector<int>& xo,
                              const std::vector<int>& hxo) {
+  KSS_NVTX("batch_rayleigh_ritz");
   const int U = (int)us.size();
   int np = 0;
   for (auto* s : us) np = std::max(np, s->nb);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
@@ -191,6 +192,28 @@ void prof_fold(kss_ctx ctx);     // add the helper contexts' counts and times in
 kss_ctx aux_ctx(kss_ctx ctx, int i);  // helper context i of ctx (created on first use)
 void aux_release(kss_ctx ctx);
 void prof_release(kss_ctx ctx);
+// Host-side NVTX range over one phase of the path (setup, H application, filter, Rayleigh-Ritz),
+// in an NVTX domain "kss" of its own so that a caller's ranges in the default domain keep their
+// nesting; profilers that read NVTX show it on the timeline, and it costs a few ns when none is
+// attached.
+inline nvtxDomainHandle_t nvtx_domain() {
+  static const nvtxDomainHandle_t d = nvtxDomainCreateA("kss");
+  return d;
+}
+struct NvtxRange {
+  explicit NvtxRange(const char* name) {
+    nvtxEventAttributes_t a = {};
+    a.version = NVTX_VERSION;
+    a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    a.message.ascii = name;
+    nvtxDomainRangePushEx(nvtx_domain(), &a);
+  }
+  ~NvtxRange() { nvtxDomainRangePop(nvtx_domain()); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define KSS_NVTX(name) ::kss::NvtxRange kss_nvtx_range_(name)
 #define KSS_PROF(ctx, name)                                   \
   static const int kss_prof_id_ = ::kss::prof_register(name); \
   ::kss::ProfScope kss_prof_scope_((ctx), kss_prof_id_)

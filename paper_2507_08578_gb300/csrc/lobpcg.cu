@@ -460,6 +460,7 @@ extern "C" kss_status kss_rmmdiis_solve(kss_sys sys, int ik, int nband, const ks
   if (!sys) return KSS_EINVAL;
   kss_ctx ctx = sys->ctx;
   try {
+    KSS_NVTX("rmmdiis_solve");
     KSS_REQUIRE(ik >= 0 && ik < (int)sys->k.size(), "k-point index out of range");
     KSS_REQUIRE(nband >= 1, "nband must be >= 1");
     KSS_REQUIRE(opts && opts->x0 && opts->x0_nb >= nband,
@@ -546,6 +547,7 @@ extern "C" kss_status kss_lobpcg_solve(kss_sys sys, int ik, int nband, const kss
   if (!sys) return KSS_EINVAL;
   kss_ctx ctx = sys->ctx;
   try {
+    KSS_NVTX("lobpcg_solve");
     KSS_REQUIRE(ik >= 0 && ik < (int)sys->k.size(), "k-point index out of range");
     KSS_REQUIRE(nband >= 1, "nband must be >= 1");
     kss_solve_opts o{};

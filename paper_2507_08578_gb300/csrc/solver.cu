@@ -511,10 +511,16 @@ void solver_step(kss_solver_s* s) {
   kss_ctx ctx = s->sys->ctx;
   const auto t0 = std::chrono::steady_clock::now();
   if (!s->started) {
-    apply_block(s, s->f64, s->blk[0].p, s->blk[1].p);
+    {
+      KSS_NVTX("apply_H");
+      apply_block(s, s->f64, s->blk[0].p, s->blk[1].p);
+    }
     const auto t1 = std::chrono::steady_clock::now();
-    rayleigh_ritz(s, s->f64, s->blk[0].p, s->blk[1].p, s->blk[2].p, s->blk[3].p);
-    gamma_fix(s, s->f64, s->blk[2].p, s->blk[3].p);
+    {
+      KSS_NVTX("rayleigh_ritz");
+      rayleigh_ritz(s, s->f64, s->blk[0].p, s->blk[1].p, s->blk[2].p, s->blk[3].p);
+      gamma_fix(s, s->f64, s->blk[2].p, s->blk[3].p);
+    }
     s->ix = 2;
     s->ihx = 3;
     s->started = true;
@@ -523,15 +529,21 @@ void solver_step(kss_solver_s* s) {
     int fr[2], nf = 0;
     for (int i = 0; i < 4; ++i)
       if (i != s->ix && i != s->ihx) fr[nf++] = i;
-    int prev = -1;
-    const int y = chebyshev_filter(s, fr[0], &prev);
-    // y and prev are two of {ix, fr[0]}; the HY block reuses prev.
-    apply_block(s, s->f64, s->blk[y].p, s->blk[prev].p);
-    KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    int prev = -1, y = -1;
+    {
+      KSS_NVTX("filter");
+      y = chebyshev_filter(s, fr[0], &prev);
+      // y and prev are two of {ix, fr[0]}; the HY block reuses prev.
+      apply_block(s, s->f64, s->blk[y].p, s->blk[prev].p);
+      KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
     const auto t1 = std::chrono::steady_clock::now();
     s->ms_filter += std::chrono::duration<double, std::milli>(t1 - t0).count();
-    rayleigh_ritz(s, s->f64, s->blk[y].p, s->blk[prev].p, s->blk[fr[1]].p, s->blk[s->ihx].p);
-    gamma_fix(s, s->f64, s->blk[fr[1]].p, s->blk[s->ihx].p);
+    {
+      KSS_NVTX("rayleigh_ritz");
+      rayleigh_ritz(s, s->f64, s->blk[y].p, s->blk[prev].p, s->blk[fr[1]].p, s->blk[s->ihx].p);
+      gamma_fix(s, s->f64, s->blk[fr[1]].p, s->blk[s->ihx].p);
+    }
     s->ix = fr[1];
     s->iter += 1;
     s->ms_rr += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
@@ -583,6 +595,7 @@ void step_many(kss_ctx ctx, const std::vector<kss_solver_s*>& us) {
       int fr[2], nf = 0;
       for (int i = 0; i < 4; ++i)
         if (i != s->ix && i != s->ihx) fr[nf++] = i;
+      KSS_NVTX("filter");
       int prev = -1;
       const int y = chebyshev_filter(s, fr[0], &prev);
       apply_block(s, s->f64, s->blk[y].p, s->blk[prev].p);
@@ -591,6 +604,7 @@ void step_many(kss_ctx ctx, const std::vector<kss_solver_s*>& us) {
       KSS_CHECK_CUDA(cudaEventRecord(ev[u], ctx->stream));
     };
     auto rr = [&](int u) {
+      KSS_NVTX("rayleigh_ritz");
       kss_solver_s* s = us[u];
       kss_ctx w = aux_ctx(ctx, u % kAux);
       w->prof.on = ctx->prof.on;
