@@ -240,10 +240,18 @@ kss_status kss_setup(kss_ctx ctx, const kss_cell* cell, const kss_atoms* atoms, 
     KSS_REQUIRE(atoms->nproj_per_atom == 0 || atoms->nproj_per_atom == 1 ||
                     atoms->nproj_per_atom == 4,
                 "nproj_per_atom must be 0, 1 or 4");
-    KSS_REQUIRE(atoms->vloc_sigma > 0, "vloc_sigma must be positive");
+    KSS_REQUIRE(atoms->vloc_sigma > 0 && std::isfinite(atoms->vloc_sigma), "vloc_sigma must be positive");
+    KSS_REQUIRE(std::isfinite(atoms->vloc_amp), "non-finite vloc_amp");
     KSS_REQUIRE(atoms->nproj_per_atom == 0 || atoms->natom == 0 ||
-                    (atoms->D && atoms->proj_alpha > 0),
+                    (atoms->D && atoms->proj_alpha > 0 && std::isfinite(atoms->proj_alpha)),
                 "projectors need D and proj_alpha > 0");
+    for (int i = 0; i < 9; ++i) KSS_REQUIRE(std::isfinite(cell->lattice[i]), "non-finite lattice vector");
+    for (int i = 0; i < 3 * cell->nk; ++i) KSS_REQUIRE(std::isfinite(cell->kpts_red[i]), "non-finite k-point");
+    for (int i = 0; i < 3 * atoms->natom; ++i)
+      KSS_REQUIRE(std::isfinite(atoms->pos_cart[i]), "non-finite atom position");
+    if (atoms->natom && atoms->nproj_per_atom)
+      for (int i = 0; i < atoms->natom * atoms->nproj_per_atom; ++i)
+        KSS_REQUIRE(std::isfinite(atoms->D[i]), "non-finite projector coefficient D");
     KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
     std::unique_ptr<kss_sys_s> s(new kss_sys_s());
     s->ctx = ctx;

@@ -123,6 +123,13 @@ APPLY_CASES = [
                                                   nproj_per_atom=1), 4, 0),
     ("no_projectors", lambda: W.tiny_system(a=5.0, ecut=2.5, natom=2, nproj_per_atom=0), 4, 0),
     ("C4.0_default_box", lambda: W.config4(1)[0], 9, 2),
+    # power-of-two and 2^3*3^2 box edges (the CTA-wide middle pass needs N2 == N3)
+    ("box_32_cubic", lambda: W.tiny_system(a=8.0, ecut=5.0, natom=3, fft_box=(32, 32, 32)), 5, 0),
+    ("box_64_cubic_k", lambda: W.tiny_system(a=10.0, ecut=6.0, natom=3, fft_box=(64, 64, 64),
+                                             kpts=[(0.25, 0.25, 0.25)]), 7, 2),
+    ("box_72_cubic", lambda: W.tiny_system(a=10.0, ecut=6.0, natom=3, fft_box=(72, 72, 72)), 3, 0),
+    ("box_32_64_72_k", lambda: W.tiny_system(a=10.0, ecut=6.0, natom=3, fft_box=(32, 64, 72),
+                                             kpts=[(0.25, 0.0, -0.25)]), 6, 1),
 ]
 
 
@@ -132,7 +139,10 @@ def test_apply_fp64(ctx, name, mk, nb, pad):
     assert err < FP64_TOL, err
 
 
-@pytest.mark.parametrize("name,mk,nb,pad", APPLY_CASES[:5], ids=[c[0] for c in APPLY_CASES[:5]])
+MIXED_CASES = APPLY_CASES[:5] + APPLY_CASES[-4:]
+
+
+@pytest.mark.parametrize("name,mk,nb,pad", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
 def test_apply_mixed(ctx, name, mk, nb, pad):
     err = _apply_case(ctx, mk(), nb, pad, K.KSS_PREC_MIXED)
     assert err < MIXED_TOL, err
@@ -238,6 +248,18 @@ def test_setup_rejects_bad_input(ctx):
         K.kss_setup(ctx, s.lattice, s.ecut, s.kpts, s.pos, s.D, fft_box=(29, 29, 29))  # not 2,3,5-smooth
     with pytest.raises(K.KssError):
         K.kss_setup(ctx, s.lattice, -1.0, s.kpts, s.pos, s.D)
+    # non-finite host inputs are refused at setup, before anything reaches the device
+    pos = np.array(s.pos, dtype=np.float64)
+    pos[1, 2] = np.nan
+    D = np.array(s.D, dtype=np.float64)
+    D[3] = np.inf
+    kp = np.array(s.kpts, dtype=np.float64)
+    kp[0, 0] = np.nan
+    for args in ((s.lattice, s.ecut, s.kpts, pos, s.D), (s.lattice, s.ecut, s.kpts, s.pos, D),
+                 (s.lattice, s.ecut, kp, s.pos, s.D)):
+        with pytest.raises(K.KssError) as e:
+            K.kss_setup(ctx, *args)
+        assert e.value.status == K.KSS_EINVAL and "non-finite" in str(e.value)
 
 
 def test_stream_ordering_with_torch(ctx):
