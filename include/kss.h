@@ -163,7 +163,10 @@ kss_status kss_footprint(kss_sys sys, int nband, kss_precision prec, size_t* byt
  * KSS_PREC_FP64 and complex64 for KSS_PREC_MIXED; they must not overlap.  Steps: projector
  * coefficients C = beta^H psi; per band, sphere -> box scatter, inverse 3D FFT, x V(r), forward
  * 3D FFT, box -> sphere gather, + 0.5|k+G|^2 psi; then hpsi += beta (D C).
- * nb == 0 is a no-op.  Errors: KSS_EINVAL (ik out of range, nb < 0, ld < npw, null pointers). */
+ * nb == 0 is a no-op.  Errors: KSS_EINVAL (ik out of range, nb < 0, ld < npw, null pointers).
+ * The call is stream-ordered and does not synchronise: if a bounded wait inside a
+ * KSS_PREC_MIXED projector product gave up, the next call of this context that synchronises
+ * (a solver step or solve, kss_gemm) returns KSS_ETIMEOUT. */
 kss_status kss_apply_H(kss_sys sys, int ik, int nb, const void* psi, void* hpsi, int ld,
                        kss_precision prec);
 
@@ -238,6 +241,14 @@ kss_status kss_apply_H_noalloc(kss_sys sys, int ik, int nb, const void* psi, voi
 kss_status kss_gemm(kss_ctx ctx, int op, int M, int N, int K, const void* A, int lda, const void* B,
                     int ldb, void* C, int ldc, double alpha_re, double alpha_im, double beta_re,
                     double beta_im, kss_precision prec);
+
+/* Failure path of the bounded device waits, exercised without a fault (test support; the paper
+ * has no counterpart).  Launches one thread that waits on a device word nothing writes, with the
+ * same %globaltimer limit pattern as the tensor-core pipeline waits; after limit_ms (0 < limit_ms
+ * <= 1000) it gives up and raises the context's device error flag, which this call reads back.
+ * Returns KSS_ETIMEOUT (the expected outcome) with the flag cleared and the context usable;
+ * KSS_EINVAL for a limit out of range. */
+kss_status kss_selftest_bounded_wait(kss_ctx ctx, double limit_ms);
 
 /* ------------------------------------------------------------------------------------------
  * Electron density after the solve (Eq. nandtau, §2)

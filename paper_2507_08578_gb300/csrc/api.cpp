@@ -615,6 +615,15 @@ kss_status kss_gemm(kss_ctx ctx, int op, int M, int N, int K, const void* A, int
   });
 }
 
+kss_status kss_selftest_bounded_wait(kss_ctx ctx, double limit_ms) {
+  if (!ctx) return KSS_EINVAL;
+  return guard(ctx, [&] {
+    KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    tc_wait_selftest(ctx, limit_ms);
+    if (tc_error_flag(ctx, true)) fail(KSS_ETIMEOUT, "bounded device wait gave up (self-test)");
+  });
+}
+
 kss_status kss_footprint(kss_sys sys, int nband, kss_precision prec, size_t* bytes) {
   if (!sys || !bytes || nband < 1) return KSS_EINVAL;
   size_t m = 0;

@@ -515,6 +515,36 @@ void tc_gemm_nn_split(kss_ctx ctx, int M, int N, int K, const void* Atc, const v
   run_tc(ctx, (const __nv_bfloat16*)Atc, Btc, kpad(K), M, N, (float2*)C, ldc, ar, ai, br, bi, tag);
 }
 
+// ---- the failure path of the bounded waits, exercised without a fault --------------------------
+namespace {
+// One thread waits on a device word that nothing writes, with the pipeline waits' %globaltimer
+// limit pattern, and then raises the tensor-core error flag as a pipeline wait that gave up does.
+__global__ void bounded_wait_probe(const int* __restrict__ word, unsigned long long limit_ns, int* __restrict__ err) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned long long t0 = globaltimer();
+  while (*(const volatile int*)word == 0)
+    if (globaltimer() - t0 > limit_ns) {
+      atomicExch(err, 1);
+      return;
+    }
+}
+}  // namespace
+
+void tc_wait_selftest(kss_ctx ctx, double limit_ms) {
+  KSS_REQUIRE(limit_ms > 0 && limit_ms <= 1000, "limit_ms must be in (0, 1000]");
+  if (!ctx->tc_err.p) {
+    ctx->tc_err.alloc(sizeof(int));
+    KSS_CHECK_CUDA(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), ctx->stream));
+  }
+  DevBuf word;
+  word.alloc(sizeof(int));
+  KSS_CHECK_CUDA(cudaMemsetAsync(word.p, 0, sizeof(int), ctx->stream));
+  bounded_wait_probe<<<1, 32, 0, ctx->stream>>>(word.as<int>(), (unsigned long long)(limit_ms * 1e6),
+                                                ctx->tc_err.as<int>());
+  KSS_CHECK_CUDA(cudaGetLastError());
+  KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
 // Device-side failure flag of the tensor-core kernels (bounded waits that gave up).
 int tc_error_flag(kss_ctx ctx, bool reset) {
   if (!ctx->tc_err.p) return 0;

@@ -299,6 +299,9 @@ void tc_gemm_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const 
 void tc_gemm_nn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                 void* C, int ldc, double ar, double ai, double br, double bi, const char* tag);
 int tc_error_flag(kss_ctx ctx, bool reset);
+// Runs one bounded wait on a word that nothing writes (it gives up after limit_ms and raises the
+// flag read by tc_error_flag): the failure path of the pipeline waits, without a fault.
+void tc_wait_selftest(kss_ctx ctx, double limit_ms);
 // The same products with the A operand split once in advance (static operands): tc_split_cn /
 // tc_split_nn write the split form of A (tc_split_*_bytes) for tc_gemm_cn_split / tc_gemm_nn_split.
 size_t tc_split_cn_bytes(int M, int K);

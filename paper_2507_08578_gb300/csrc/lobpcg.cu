@@ -254,6 +254,7 @@ struct Lobpcg {
     KSS_CHECK_CUDA(cudaMemcpyAsync(evals.data(), lam.p, (size_t)m * 8, cudaMemcpyDeviceToHost, ctx->stream));
     KSS_CHECK_CUDA(cudaMemcpyAsync(res.data(), resid.p, (size_t)m * 8, cudaMemcpyDeviceToHost, ctx->stream));
     KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (tc_error_flag(ctx, true)) fail(KSS_ETIMEOUT, "tensor-core GEMM: a bounded wait gave up");
     for (int n = 0; n < m; ++n)
       if (!std::isfinite(evals[n]) || !std::isfinite(res[n])) fail(KSS_ENUMERIC, "non-finite Ritz value or residual");
     return true;

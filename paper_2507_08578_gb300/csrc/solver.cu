@@ -554,6 +554,8 @@ void solver_step(kss_solver_s* s) {
 
 // Convergence bookkeeping after a Rayleigh-Ritz (and the FP64 refinement that ends a mixed solve).
 void after_iterate(kss_solver_s* s) {
+  // A tensor-core projector product whose bounded wait gave up left wrong values behind.
+  if (tc_error_flag(s->sys->ctx, true)) fail(KSS_ETIMEOUT, "tensor-core GEMM: a bounded wait gave up");
   const double r = max_wanted(s);
   s->hist.push_back(r);
   if (s->f64) {

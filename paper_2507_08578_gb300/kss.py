@@ -120,6 +120,7 @@ def signatures() -> dict:
                               POINTER(kss_solve_stats)], c_int),
         "kss_gemm": ([P, c_int, c_int, c_int, c_int, P, c_int, P, c_int, P, c_int, c_double,
                       c_double, c_double, c_double, c_int], c_int),
+        "kss_selftest_bounded_wait": ([P, c_double], c_int),
         "kss_solve_batch": ([P, c_int, P, P, P, POINTER(kss_solve_opts), P, P, P], c_int),
         "kss_server_start": ([P, c_size_t, c_int, POINTER(kss_solve_opts)], c_int),
         "kss_server_submit": ([P, POINTER(kss_cell), POINTER(kss_atoms), c_int, POINTER(c_uint64)], c_int),
@@ -572,6 +573,12 @@ def kss_gemm(ctx, op: int, A, B, C, alpha=1.0, beta=0.0, prec: int = KSS_PREC_FP
     _check(lib().kss_gemm(ctx, op, M, n, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc,
                           complex(alpha).real, complex(alpha).imag, complex(beta).real,
                           complex(beta).imag, prec), ctx)
+
+
+def kss_selftest_bounded_wait(ctx, limit_ms: float = 50.0) -> int:
+    """Run the bounded-wait failure path once (a wait on a word nothing writes); returns the
+    status, KSS_ETIMEOUT when the path works."""
+    return lib().kss_selftest_bounded_wait(ctx, float(limit_ms))
 
 
 def kss_solve_batch(ctx, systems, iks, nbands, opts: kss_solve_opts, allow_noconv: bool = False):

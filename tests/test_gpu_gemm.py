@@ -78,3 +78,30 @@ def test_gemm_rejects_bad_sizes(ctx):
     st = L.kss_gemm(ctx, 2, 4, 4, 8, a.data_ptr(), 8, a.data_ptr(), 8, a.data_ptr(), 8,
                     1.0, 0.0, 0.0, 0.0, K.KSS_PREC_MIXED)
     assert st == K.KSS_EINVAL
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable(ctx):
+    """The failure path of the bounded device waits, without a fault: a wait on a word that nothing
+    writes gives up after its limit, the host reads KSS_ETIMEOUT and a message, the flag is
+    cleared, and the context goes on computing correct products."""
+    import time
+    import torch
+    L = K.lib()
+    t0 = time.perf_counter()
+    st = K.kss_selftest_bounded_wait(ctx, 50.0)
+    dt = time.perf_counter() - t0
+    assert st == K.KSS_ETIMEOUT
+    assert b"gave up" in L.kss_last_error(ctx)
+    assert 0.045 < dt < 5.0
+    assert K.kss_selftest_bounded_wait(ctx, 0.0) == K.KSS_EINVAL
+    assert K.kss_selftest_bounded_wait(ctx, 2000.0) == K.KSS_EINVAL
+    rng = np.random.default_rng(3)
+    A, B = crand(rng, (40, 300)), crand(rng, (24, 300))
+    C = np.zeros((24, 40), dtype=np.complex128)
+    tA, tB = (torch.from_numpy(x).to(torch.complex64).cuda() for x in (A, B))
+    tC = torch.from_numpy(C).to(torch.complex64).cuda()
+    K.kss_gemm(ctx, 0, tA, tB, tC, 1.0, 0.0, K.KSS_PREC_MIXED)   # raises if the flag were still set
+    torch.cuda.synchronize()
+    ref = A.conj() @ B.T
+    got = tC.cpu().numpy().T
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-4

@@ -65,6 +65,16 @@ def test_settings_do_not_change_result(ctx):
     assert np.max(np.abs(a - b)) < 2e-9
 
 
+def test_rerun_is_bit_identical(ctx):
+    """Same system, same options, same process: the FP64 solve repeats bit for bit (every
+    reduction of the path runs in a fixed order; no atomics), on a fresh system handle each time."""
+    s = W.make_system("c2s", 10.0, 8.0, 8, 24, seed=1002, kpts=W.SHIFTED_222[:1], min_sep=2.0)
+    a = solve(ctx, s, 0, 24, tol=1e-8, seed=5)
+    b = solve(ctx, s, 0, 24, tol=1e-8, seed=5)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert a[2]["iters"] == b[2]["iters"] and a[2]["napply"] == b[2]["napply"]
+
+
 def test_kpoint_c2_shape_small(ctx):
     """Shifted k-points of a smaller cell with the C2 atom recipe (complex Hermitian H)."""
     s = W.make_system("c2s", 10.0, 8.0, 8, 24, seed=1002, kpts=W.SHIFTED_222[:2], min_sep=2.0)
