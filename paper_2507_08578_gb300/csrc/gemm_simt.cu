@@ -387,13 +387,12 @@ __global__ void scale_rows_kernel(int M, int N, typename CT<T>::C* __restrict__ 
 }
 
 int sm_count(kss_ctx ctx) {
-  static int n = 0;
-  if (!n) {
+  if (!ctx->nsm) {  // normally set when the context is created
     int v = 0;
     KSS_CHECK_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device));
-    n = v > 0 ? v : 1;
+    ctx->nsm = v > 0 ? v : 1;
   }
-  return n;
+  return ctx->nsm;
 }
 
 // Resident CTAs per SM of a 256-thread kernel without dynamic shared memory.

@@ -407,11 +407,9 @@ void run_tc(kss_ctx ctx, const __nv_bfloat16* Atc, const __nv_bfloat16* Btc, int
     KSS_CHECK_CUDA(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), ctx->stream));
   }
   const CUtensorMap ma = make_map(Atc, Mr, 2 * Kp), mb = make_map(Btc, Nr, 2 * Kp);
-  static bool attr = false;
-  if (!attr) {
-    KSS_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
-    attr = true;
-  }
+  // per device (the attribute belongs to the current device): set at every launch, as the
+  // other kernels of the path do
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
   const bool fused = splits == 1;
   {
     ProfScope ps(ctx, prof_register((std::string("tc_gemm_bf16x3:") + tag).c_str()));
