@@ -138,6 +138,20 @@ kss_status kss_sys_info_get(kss_sys sys, kss_sys_info* out);
  * (npw*3 int32, canonical order), valid until the system is destroyed. */
 kss_status kss_sphere(kss_sys sys, int ik, int* npw, const int32_t** miller_host);
 
+/* Host-only queries: no context and no device needed (the same host code kss_setup runs).
+ * kss_sphere_host: the G-sphere of one k-point, {m : 0.5|k+G_m|^2 <= ecut} in the canonical
+ * order of kss_sphere (ascending m3, m2, m1; the inclusion test evaluated in IEEE double without
+ * contraction, §1 and §5.2 plane-wave basis).  lattice: 9 doubles, rows a1, a2, a3 in bohr;
+ * kred: 3 reduced coordinates.  *npw receives the count; miller (host, caller-owned, may be NULL
+ * to query the count) receives npw triples when cap >= npw.  Errors: KSS_EINVAL (null npw/kred,
+ * non-finite or singular lattice, ecut <= 0, cap < npw with miller given), KSS_ENOMEM.
+ * kss_default_box: the FFT box kss_setup uses when the cell gives none: per axis the smallest
+ * {2,3,5}-smooth N_i >= 4 max|m_i| + 1 over the spheres of all nk k-points (kpts_red: nk * 3).
+ * Errors: KSS_EINVAL, KSS_ENOMEM. */
+kss_status kss_sphere_host(const double* lattice, double ecut, const double* kred, int cap, int* npw,
+                           int32_t* miller);
+kss_status kss_default_box(const double* lattice, double ecut, int nk, const double* kpts_red, int* box);
+
 /* Copy back from DEVICE memory the index maps the kernels use: miller (npw*3 int32) and the box
  * offsets (m1 mod N1) + N1*((m2 mod N2) + N2*(m3 mod N3)) (npw int32), into host buffers. */
 kss_status kss_get_maps(kss_sys sys, int ik, int32_t* miller_out, int32_t* offset_out);

@@ -46,6 +46,14 @@ static bool smooth235(int n) {
   return n == 1;
 }
 
+// Default FFT box edge along one axis: the smallest {2,3,5}-smooth N >= 4 max|m| + 1 (no aliasing
+// of products of two band functions).
+static int default_box_edge(int mmax) {
+  int n = 4 * mmax + 1;
+  while (!smooth235(n)) ++n;
+  return n;
+}
+
 FftDim make_fft_dim(int N) {
   FftDim d{};
   d.N = N;
@@ -300,9 +308,7 @@ kss_status kss_setup(kss_ctx ctx, const kss_cell* cell, const kss_atoms* atoms, 
     const bool dflt = cell->fft_box[0] == 0 && cell->fft_box[1] == 0 && cell->fft_box[2] == 0;
     for (int i = 0; i < 3; ++i) {
       if (dflt) {
-        int n = 4 * mmax[i] + 1;
-        while (!smooth235(n)) ++n;
-        s->N[i] = n;
+        s->N[i] = default_box_edge(mmax[i]);
       } else {
         s->N[i] = cell->fft_box[i];
       }
@@ -613,6 +619,58 @@ kss_status kss_gemm(kss_ctx ctx, int op, int M, int N, int K, const void* A, int
       if (tc_error_flag(ctx, true)) fail(KSS_ETIMEOUT, "tensor-core GEMM: a bounded wait gave up");
     }
   });
+}
+
+// ---- host-only queries (no context, no device) ----
+
+static bool host_cell_ok(const double* lattice, double ecut, double* B) {
+  if (!lattice || !(ecut > 0) || !std::isfinite(ecut)) return false;
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(lattice[i])) return false;
+  double vol = 0.0;
+  reciprocal(lattice, B, &vol);
+  return std::isfinite(vol) && vol > 0;
+}
+
+kss_status kss_sphere_host(const double* lattice, double ecut, const double* kred, int cap, int* npw,
+                           int32_t* miller) {
+  if (!npw || !kred) return KSS_EINVAL;
+  double B[9];
+  if (!host_cell_ok(lattice, ecut, B)) return KSS_EINVAL;
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(kred[i])) return KSS_EINVAL;
+  try {
+    std::vector<int32_t> m;
+    enumerate_sphere(lattice, B, ecut, kred, m);
+    *npw = (int)(m.size() / 3);
+    if (miller) {
+      if (cap < *npw) return KSS_EINVAL;
+      std::memcpy(miller, m.data(), m.size() * sizeof(int32_t));
+    }
+    return KSS_OK;
+  } catch (const std::bad_alloc&) {
+    return KSS_ENOMEM;
+  }
+}
+
+kss_status kss_default_box(const double* lattice, double ecut, int nk, const double* kpts_red, int* box) {
+  if (!box || nk < 1 || !kpts_red) return KSS_EINVAL;
+  double B[9];
+  if (!host_cell_ok(lattice, ecut, B)) return KSS_EINVAL;
+  try {
+    int mmax[3] = {0, 0, 0};
+    std::vector<int32_t> m;
+    for (int ik = 0; ik < nk; ++ik) {
+      for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(kpts_red[3 * ik + i])) return KSS_EINVAL;
+      enumerate_sphere(lattice, B, ecut, kpts_red + 3 * ik, m);
+      for (size_t g = 0; g < m.size(); ++g) mmax[g % 3] = std::max(mmax[g % 3], std::abs(m[g]));
+    }
+    for (int i = 0; i < 3; ++i) box[i] = default_box_edge(mmax[i]);
+    return KSS_OK;
+  } catch (const std::bad_alloc&) {
+    return KSS_ENOMEM;
+  }
 }
 
 kss_status kss_selftest_bounded_wait(kss_ctx ctx, double limit_ms) {

@@ -103,6 +103,8 @@ def signatures() -> dict:
         "kss_sys_destroy": ([P], c_int),
         "kss_sys_info_get": ([P, POINTER(kss_sys_info)], c_int),
         "kss_sphere": ([P, c_int, POINTER(c_int), POINTER(POINTER(c_int32))], c_int),
+        "kss_sphere_host": ([P, c_double, P, c_int, POINTER(c_int), P], c_int),
+        "kss_default_box": ([P, c_double, c_int, P, P], c_int),
         "kss_get_maps": ([P, c_int, P, P], c_int),
         "kss_get_tables": ([P, c_int, P, P, P], c_int),
         "kss_upper_bound": ([P, c_int, POINTER(c_double)], c_int),
@@ -275,6 +277,29 @@ def kss_sphere(sys: System, ik: int) -> np.ndarray:
     mp = POINTER(c_int32)()
     _check(lib().kss_sphere(sys.h, ik, byref(n), byref(mp)), sys.ctx)
     return np.ctypeslib.as_array(mp, shape=(n.value * 3,)).reshape(n.value, 3).copy()
+
+
+def kss_sphere_host(lattice, ecut: float, kred) -> np.ndarray:
+    """G-sphere of one k-point from the library's host code alone (no context, no device):
+    Miller triples (npw, 3) in canonical order."""
+    lat = np.ascontiguousarray(np.asarray(lattice, np.float64).reshape(9))
+    k = np.ascontiguousarray(np.asarray(kred, np.float64).reshape(3))
+    n = c_int()
+    _check(lib().kss_sphere_host(lat.ctypes.data, float(ecut), k.ctypes.data, 0, byref(n), None))
+    m = np.zeros((n.value, 3), np.int32)
+    _check(lib().kss_sphere_host(lat.ctypes.data, float(ecut), k.ctypes.data, n.value, byref(n),
+                                 m.ctypes.data))
+    return m
+
+
+def kss_default_box(lattice, ecut: float, kpts) -> tuple:
+    """The FFT box kss_setup picks when the cell gives none (host code only)."""
+    lat = np.ascontiguousarray(np.asarray(lattice, np.float64).reshape(9))
+    k = np.ascontiguousarray(np.asarray(kpts, np.float64).reshape(-1, 3))
+    box = np.zeros(3, np.int32)
+    _check(lib().kss_default_box(lat.ctypes.data, float(ecut), int(k.shape[0]), k.ctypes.data,
+                                 box.ctypes.data))
+    return tuple(int(v) for v in box)
 
 
 def kss_get_maps(sys: System, ik: int):
