@@ -77,7 +77,7 @@ kss_status kss_destroy(kss_ctx ctx);
  * until the next call on it.  Accepts NULL (returns a static message). */
 const char* kss_last_error(kss_ctx ctx);
 
-/* Library version as major*1000 + minor. */
+/* Library version as major*1000 + minor (no counterpart in the paper).  Cannot fail. */
 int kss_version(void);
 
 /* ------------------------------------------------------------------------------------------
@@ -121,6 +121,8 @@ typedef struct {
  * box dimension > 256), KSS_ENOMEM, KSS_ECUDA. */
 kss_status kss_setup(kss_ctx ctx, const kss_cell* cell, const kss_atoms* atoms, kss_sys* out);
 
+/* Waits for the context's stream and frees the system's device tables.  Errors: KSS_EINVAL
+ * (NULL, or solvers of this system still alive: destroy them first; the system is kept). */
 kss_status kss_sys_destroy(kss_sys sys);
 
 typedef struct {
@@ -132,10 +134,12 @@ typedef struct {
   double vloc_max;         /* max_j V(r_j) */
 } kss_sys_info;
 
+/* Sizes of a system as set up (host struct filled by the call).  Errors: KSS_EINVAL (NULL). */
 kss_status kss_sys_info_get(kss_sys sys, kss_sys_info* out);
 
 /* Number of plane waves of k-point ik and a library-owned host copy of its Miller triples
- * (npw*3 int32, canonical order), valid until the system is destroyed. */
+ * (npw*3 int32, canonical order; the plane-wave basis of §1 and §5.2), valid until the system is
+ * destroyed; miller_host may be NULL.  Errors: KSS_EINVAL (NULL sys/npw, ik out of range). */
 kss_status kss_sphere(kss_sys sys, int ik, int* npw, const int32_t** miller_host);
 
 /* Host-only queries: no context and no device needed (the same host code kss_setup runs).
@@ -147,26 +151,33 @@ kss_status kss_sphere(kss_sys sys, int ik, int* npw, const int32_t** miller_host
  * non-finite or singular lattice, ecut <= 0, cap < npw with miller given), KSS_ENOMEM.
  * kss_default_box: the FFT box kss_setup uses when the cell gives none: per axis the smallest
  * {2,3,5}-smooth N_i >= 4 max|m_i| + 1 over the spheres of all nk k-points (kpts_red: nk * 3).
- * Errors: KSS_EINVAL, KSS_ENOMEM. */
+ * Errors: KSS_EINVAL, KSS_ENOMEM (these two calls have no context, so no message is stored). */
 kss_status kss_sphere_host(const double* lattice, double ecut, const double* kred, int cap, int* npw,
                            int32_t* miller);
 kss_status kss_default_box(const double* lattice, double ecut, int nk, const double* kpts_red, int* box);
 
 /* Copy back from DEVICE memory the index maps the kernels use: miller (npw*3 int32) and the box
- * offsets (m1 mod N1) + N1*((m2 mod N2) + N2*(m3 mod N3)) (npw int32), into host buffers. */
+ * offsets (m1 mod N1) + N1*((m2 mod N2) + N2*(m3 mod N3)) (npw int32), into caller-owned host
+ * buffers (either may be NULL); synchronises the context's stream first.  Errors: KSS_EINVAL
+ * (ik out of range), KSS_ECUDA. */
 kss_status kss_get_maps(kss_sys sys, int ik, int32_t* miller_out, int32_t* offset_out);
 
 /* Copy back from device the local potential V(r_j) (N1*N2*N3 doubles, index j1 + N1*(j2 +
- * N2*j3), not scaled), the kinetic energies (npw doubles) and the projector table (npw*nproj
- * complex128, projector-major: element (i, g) at [i*npw + g]).  Any output may be NULL. */
+ * N2*j3), not scaled), the kinetic energies 0.5|k+G|^2 (npw doubles) and the projector table of
+ * Eq. ham-nl (§5.2) (npw*nproj complex128, projector-major: element (i, g) at [i*npw + g]) into
+ * caller-owned host buffers.  Any output may be NULL; synchronises the context's stream first.
+ * Errors: KSS_EINVAL (ik out of range), KSS_ECUDA. */
 kss_status kss_get_tables(kss_sys sys, int ik, double* vloc_out, double* kinetic_out,
                           double* beta_out);
 
-/* Rigorous upper bound of the spectrum of H(k): max T + max(max V, 0) + sum_i max(D_i,0)|beta_i|^2. */
+/* Rigorous upper bound of the spectrum of H(k): max T + max(max V, 0) + sum_i max(D_i,0)|beta_i|^2
+ * (the upper end of the Chebyshev filter interval, §5.1; for a system with an overlap the bound of
+ * S^-1 H).  Errors: KSS_EINVAL (NULL, ik out of range). */
 kss_status kss_upper_bound(kss_sys sys, int ik, double* bound);
 
 /* Device bytes the solver needs for nband bands at this precision (all k-points handled one at
- * a time), excluding the system tables already allocated. */
+ * a time), excluding the system tables already allocated (no counterpart in the paper; used for
+ * admission by memory footprint).  Errors: KSS_EINVAL (NULL, nband < 1). */
 kss_status kss_footprint(kss_sys sys, int nband, kss_precision prec, size_t* bytes);
 
 /* ------------------------------------------------------------------------------------------
@@ -193,22 +204,28 @@ kss_status kss_apply_H_gamma(kss_sys sys, int ik, int nb, const void* psi, void*
                              kss_precision prec);
 
 /* spsi = S(k_ik) psi = psi + beta (Q (beta^H psi)): the overlap of a system set up with Q
- * (spsi = psi without it).  Same layout and rules as kss_apply_H. */
+ * (spsi = psi without it; §5.2, the nonlocal overlap with the structure of Eq. ham-nl).  Same
+ * layout and rules as kss_apply_H.  Errors: KSS_EINVAL (ik out of range, nb < 0, ld < npw, unknown
+ * precision, null or identical psi / spsi). */
 kss_status kss_apply_S(kss_sys sys, int ik, int nb, const void* psi, void* spsi, int ld,
                        kss_precision prec);
 
-/* One Chebyshev three-term step fused into the application of the filter operator F:
+/* One Chebyshev three-term step (the filter of the Chebyshev-filtered subspace iteration, §5.1)
+ * fused into the application of the filter operator F:
  *   out = alpha * F psi + beta * psi + gamma * psi_prev
  * F = H, or F = S^-1 H for a system with an overlap (S^-1 = 1 - beta W beta^H with the
  * precomputed W = Q (1 + beta^H beta Q)^-1 per k-point).
  * psi_prev may be NULL (then gamma is ignored) and may alias out (out is written element by
- * element after psi_prev at the same element is read).  psi must not overlap out. */
+ * element after psi_prev at the same element is read).  psi must not overlap out.  Layout and
+ * stream ordering as kss_apply_H.  Errors: as kss_apply_H. */
 kss_status kss_cheb_step(kss_sys sys, int ik, int nb, const void* psi, const void* psi_prev,
                          void* out, int ld, double alpha, double beta, double gamma,
                          kss_precision prec);
 
-/* kss_apply_H with HOST psi/hpsi: copies psi to library-owned device staging, applies H and
- * copies the result back; synchronises the stream before returning. */
+/* kss_apply_H with HOST psi/hpsi (caller-owned, band-major [nb][ld]; pinned memory makes the
+ * copies asynchronous): copies psi to library-owned device staging, applies H and copies the
+ * result back; synchronises the stream before returning.  Errors: KSS_EINVAL (ik out of range,
+ * nb < 0, ld < npw, null buffers), KSS_ENOMEM, KSS_ECUDA. */
 kss_status kss_apply_H_host(kss_sys sys, int ik, int nb, const void* psi_host, void* hpsi_host,
                             int ld, kss_precision prec);
 
@@ -315,12 +332,16 @@ typedef struct {
  * Errors: KSS_EINVAL (nband < 1, nband+nbuffer > npw), KSS_ENOMEM. */
 kss_status kss_solver_create(kss_sys sys, int ik, int nband, const kss_solve_opts* opts,
                              kss_solver* out);
+/* Waits for the context's stream and frees the solver's blocks.  Errors: KSS_EINVAL (NULL). */
 kss_status kss_solver_destroy(kss_solver s);
 
 /* One iteration.  The first call performs the initial Rayleigh-Ritz on the starting block; each
  * later call filters (degree m), then Rayleigh-Ritz (FP64 Cholesky of the Gram matrix and FP64
  * Hermitian eigensolve on the GPU), then residuals.  *converged is set to 1 when every wanted
- * band has residual <= tol.  Synchronises the stream (the residuals decide convergence). */
+ * band has residual <= tol.  Synchronises the stream (the residuals decide convergence).
+ * Errors: KSS_EINVAL (NULL), KSS_ENUMERIC (a failed factorisation or a non-finite Ritz value or
+ * residual), KSS_ETIMEOUT (a bounded device wait of a mixed-precision projector product gave
+ * up), KSS_ENOMEM, KSS_ECUDA; after an error the iterate is undefined. */
 kss_status kss_solver_step(kss_solver s, int* converged);
 
 /* One iteration on each of n solvers of the same context (e.g. the k-points of one system; §5.3
@@ -337,13 +358,16 @@ kss_status kss_solver_step(kss_solver s, int* converged);
  * and ms_rr receive equal shares of the call's wall time. */
 kss_status kss_solver_step_many(int n, kss_solver const* solvers, int* converged);
 
-/* Results of the current iterate: evals/resid host [nband] (may be NULL); evecs DEVICE
- * band-major [nband][ld] of the solver's precision or NULL; stats may be NULL. */
+/* Results of the current iterate (the Ritz pairs of the last Rayleigh-Ritz, §5.1): evals/resid
+ * host [nband] (may be NULL); evecs DEVICE band-major [nband][ld] of the solver's precision or
+ * NULL; stats may be NULL.  Errors: KSS_EINVAL (NULL, no step taken yet, ld < npw), KSS_ECUDA. */
 kss_status kss_solver_results(kss_solver s, double* evals, double* resid, void* evecs, int ld,
                               kss_solve_stats* stats);
 
-/* Full solve = create + step until converged or max_iter + results + destroy.
- * Returns KSS_ENOCONV (outputs still filled) when max_iter is reached.
+/* Full solve = create + step until converged or max_iter + results + destroy (ChebFi with
+ * Rayleigh-Ritz, §5.1).  evals/resid: host [nband] (may be NULL); evecs: DEVICE band-major
+ * [nband][ld] of the precision's type, or NULL.  Returns KSS_ENOCONV (outputs still filled) when
+ * max_iter is reached; other errors as kss_solver_create and kss_solver_step.
  * For a system with an overlap (kss_atoms.Q) the solver returns the lowest generalised
  * eigenpairs H x = lambda S x: the filter polynomial is in S^-1 H, Rayleigh-Ritz uses the
  * metric Y^H S Y, residuals are |H x - lambda S x|, and the eigenvectors are S-orthonormal. */
@@ -416,6 +440,8 @@ typedef struct {
  * subspace of finished requests; a later request with identical content starts from it.
  * While the server runs, the context belongs to it: other calls on the context are not allowed
  * until kss_server_stop. */
+/* Errors: KSS_EINVAL (NULL, a server already running, zero budget or slots, opts with x0,
+ * unknown precision). */
 kss_status kss_server_start(kss_ctx ctx, size_t hbm_budget_bytes, int max_slots,
                             const kss_solve_opts* opts);
 
@@ -427,18 +453,23 @@ kss_status kss_server_submit(kss_ctx ctx, const kss_cell* cell, const kss_atoms*
 /* Drive the server from the calling thread for up to max_ms (at least one tick): each tick admits
  * what fits, runs one lockstep iteration over every unit in flight (new units start in the same
  * tick) and retires finished requests.  Returns early when idle.  in_flight / queued: requests
- * on the device / waiting (may be NULL). */
+ * on the device / waiting (may be NULL).  Errors: KSS_EINVAL (no server), and device errors of
+ * the lockstep engine (KSS_ENOMEM, KSS_ECUDA, KSS_ENUMERIC); a request whose own setup fails is
+ * retired with that status instead (see kss_server_poll). */
 kss_status kss_server_pump(kss_ctx ctx, double max_ms, int* in_flight, int* queued);
 
 /* *done = 1 when the request finished; then evals / resid (host, nk*nband, k-point-major) and
  * the latency are filled and the ticket is released.  Returns the request's status once done
- * (KSS_OK, KSS_ENOCONV, or the setup error). */
+ * (KSS_OK, KSS_ENOCONV, or the setup error).  Errors: KSS_EINVAL (no server, unknown or already
+ * collected ticket). */
 kss_status kss_server_poll(kss_ctx ctx, uint64_t ticket, int* done, double* evals, double* resid,
                            double* latency_ms);
 
+/* Counters and latency percentiles so far.  Errors: KSS_EINVAL (NULL, no server). */
 kss_status kss_server_get_stats(kss_ctx ctx, kss_server_stats* out);
 
-/* Stop the server and free everything it holds (pending and in-flight requests are dropped). */
+/* Stop the server and free everything it holds (pending and in-flight requests are dropped).
+ * Errors: KSS_EINVAL (NULL, no server), KSS_ECUDA. */
 kss_status kss_server_stop(kss_ctx ctx);
 
 /* ------------------------------------------------------------------------------------------
@@ -446,11 +477,12 @@ kss_status kss_server_stop(kss_ctx ctx);
  * ------------------------------------------------------------------------------------------ */
 
 /* Reset the context's counters; enable != 0 also brackets every later kernel launch of this
- * library with a pair of CUDA events on the context stream (small overhead per launch). */
+ * library with a pair of CUDA events on the context stream (small overhead per launch).
+ * Errors: KSS_EINVAL (NULL). */
 kss_status kss_profile_enable(kss_ctx ctx, int enable);
 
 /* Number of kernel names seen so far (entries) and launches since the last reset.  Waits for
- * the context stream when timing is enabled. */
+ * the context stream when timing is enabled.  Errors: KSS_EINVAL (NULL). */
 kss_status kss_profile_count(kss_ctx ctx, int* nkernels, long long* launches);
 
 /* Entry i < nkernels: kernel name (library-owned, static), launches and total event-timed
