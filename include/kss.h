@@ -59,7 +59,7 @@ typedef struct kss_sys_s* kss_sys;
 typedef struct kss_solver_s* kss_solver;
 
 /* ------------------------------------------------------------------------------------------
- * Context
+ * Context (device and stream plumbing; no counterpart in the paper)
  * ------------------------------------------------------------------------------------------ */
 
 /* Create a context on CUDA device `device` that queues all its work on `cuda_stream`, a
@@ -74,7 +74,7 @@ kss_status kss_create(kss_ctx* out, int device, void* cuda_stream);
 kss_status kss_destroy(kss_ctx ctx);
 
 /* Message of the last failed call on this context ("" if none).  Owned by the context; valid
- * until the next call on it.  Accepts NULL (returns a static message). */
+ * until the next call on it.  Cannot fail: accepts NULL (returns a static message). */
 const char* kss_last_error(kss_ctx ctx);
 
 /* Library version as major*1000 + minor (no counterpart in the paper).  Cannot fail. */
@@ -422,7 +422,8 @@ kss_status kss_solve_batch(kss_ctx ctx, int n, const kss_sys* sys, const int* ik
                            kss_solve_stats* stats);
 
 /* ------------------------------------------------------------------------------------------
- * Request server: continuous batching of eigensolves as they arrive
+ * Request server: continuous batching of eigensolves as they arrive (the high-throughput
+ * campaigns of many independent calculations, §7; the serving loop itself has no counterpart)
  * ------------------------------------------------------------------------------------------ */
 
 typedef struct {
@@ -516,7 +517,7 @@ typedef struct {
   int ncand;              /* candidates timed */
 } kss_tune_entry;
 
-/* Number of table entries (process-wide, all contexts). */
+/* Number of table entries (process-wide, all contexts).  Errors: KSS_EINVAL (n == NULL). */
 kss_status kss_autotune_count(int* n);
 /* Entry i (insertion order); KSS_EINVAL past the end or for a NULL out. */
 kss_status kss_autotune_get(int i, kss_tune_entry* out);
@@ -527,7 +528,7 @@ kss_status kss_autotune_get(int i, kss_tune_entry* out);
  * the per-warp form at use.  KSS_EINVAL for inconsistent fields (A * B != N, threads not in
  * {0, 256, 384}, W3 outside [1, N], unknown precision). */
 kss_status kss_autotune_put(const kss_tune_entry* e);
-/* Empty the table (later configurations are tuned again). */
+/* Empty the table (later configurations are tuned again).  Cannot fail (returns KSS_OK). */
 kss_status kss_autotune_clear(void);
 
 #ifdef __cplusplus
