@@ -499,3 +499,44 @@ def test_golden_values_reproduce():
     assert np.max(np.abs(ws - _golden("c1s_lowest16_Ha.txt"))) < 1e-12
     counts = _golden("sphere_counts.txt").astype(int)
     assert counts[0] == 1503 and np.all(counts[1:] == 34181)
+
+
+def test_pins_catch_planted_mistakes():
+    """The power of the pins above, shown on the CPU: each plausible slip, planted in a copy of an
+    oracle problem, moves the quantity its pin fixes far outside that pin's tolerance."""
+    from dataclasses import replace
+
+    # (1) kinetic energy at -k instead of +k: the free-electron levels at a shifted k move
+    kred = (0.25, -0.25, 0.25)
+    s = W.tiny_system(a=7.0, ecut=3.0, natom=2, kpts=[kred], vloc_amp=0.0, nproj_per_atom=0)
+    p = O.build_problem(s, 0, box=(16, 16, 16))
+    m = p.basis.miller - np.asarray(kred)
+    wrong_t = 0.5 * (2 * math.pi / 7.0) ** 2 * (m ** 2).sum(1)
+    bad = replace(p, basis=replace(p.basis, kinetic=wrong_t))
+    ref = free_electron_levels(7.0, 3.0, kred)
+    assert np.max(np.abs(O.all_eigenvalues(bad.dense()) - ref)) > 1e-2
+
+    # (2) nonlocal sign flipped: the rank-one secular roots no longer match
+    s = W.tiny_system(a=6.0, ecut=2.0, natom=1, vloc_amp=0.0, nproj_per_atom=1)
+    s.D[:] = 0.7
+    p = O.build_problem(s, 0, box=(15, 15, 15))
+    roots = secular_roots(p.basis.kinetic.copy(), np.abs(p.beta[:, 0]) ** 2, 0.7)
+    bad = replace(p, D=-p.D)
+    assert np.max(np.abs(O.all_eigenvalues(bad.dense()) - roots)) > 1e-3
+
+    # (3) potential offset by the mean (a dropped V_N(0) term): the constant-shift pin fails
+    s = W.tiny_system(a=6.0, ecut=2.5, natom=2)
+    p = O.build_problem(s, 0, box=(15, 15, 15))
+    v0 = -0.8125
+    w0 = O.all_eigenvalues(replace(p, V=np.zeros_like(p.V)).dense())
+    w1 = O.all_eigenvalues(replace(p, V=np.full_like(p.V, v0) - v0).dense())
+    assert np.max(np.abs(w1 - w0 - v0)) > 0.5
+
+    # (4) projector table conjugated in the dense matrix only: the naive apply and the dense
+    # matrix (the two independent forms) disagree
+    s = W.tiny_system(a=6.5, ecut=2.5, natom=3, kpts=[(0.25, 0.25, -0.25)])
+    p = O.build_problem(s, 0, box=(16, 15, 18))
+    c = W.random_block(p.basis.npw, 2, seed=4)
+    good = p.apply(c)
+    bad_dense = replace(p, beta=np.conj(p.beta)).dense()
+    assert np.max(np.abs(c @ bad_dense.T - good)) > 1e-3 * np.max(np.abs(good))
