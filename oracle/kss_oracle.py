@@ -278,6 +278,32 @@ def dense_hamiltonian(basis: Basis, V: np.ndarray, beta: np.ndarray, D: np.ndarr
     return H
 
 
+def dense_hamiltonian_rowwise(basis: Basis, V: np.ndarray, beta: np.ndarray, D: np.ndarray,
+                              block: int = 1024, order: str = "C") -> np.ndarray:
+    """The same matrix as ``dense_hamiltonian``, filled one block of rows at a time, so that the
+    index arrays never exceed block x npw (the config-2 matrix, 34181^2 complex128 = 18.7 GB,
+    leaves no room for full-size index arrays).  order="F" allocates the result column-major,
+    which LAPACK takes without a copy."""
+    VN = vloc_fourier_grid(V)
+    m = basis.miller.astype(np.int64)
+    N1, N2, N3 = basis.box
+    n = basis.npw
+    H = np.empty((n, n), np.complex128, order=order)
+    bD = beta * D[None, :] if beta.shape[1] else None
+    for r0 in range(0, n, block):
+        r1 = min(n, r0 + block)
+        d1 = (m[r0:r1, None, 0] - m[None, :, 0]) % N1
+        d2 = (m[r0:r1, None, 1] - m[None, :, 1]) % N2
+        d3 = (m[r0:r1, None, 2] - m[None, :, 2]) % N3
+        rows = VN[d3, d2, d1]
+        idx = np.arange(r0, r1)
+        rows[idx - r0, idx] += basis.kinetic[r0:r1]
+        if bD is not None:
+            rows += bD[r0:r1] @ beta.conj().T
+        H[r0:r1, :] = rows
+    return H
+
+
 def _dft_matrix(N: int, sign: int) -> np.ndarray:
     """F[a, b] = exp(sign * 2 pi i * a*b / N), with the exponent reduced mod N first."""
     a = np.arange(N)

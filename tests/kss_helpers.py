@@ -31,3 +31,13 @@ def rel_err_rows(a, b):
     num = np.linalg.norm(a - b, axis=-1)
     den = np.maximum(np.linalg.norm(b, axis=-1), 1e-300)
     return float(np.max(num / den))
+
+
+def rel_err_elem(a, b):
+    """max over rows of max_g |a_ng - b_ng| / max_g |b_ng|: the element-wise form of the parity
+    bar (a row norm can hide large relative errors in the small coefficients of a row)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    num = np.max(np.abs(a - b), axis=-1)
+    den = np.maximum(np.max(np.abs(b), axis=-1), 1e-300)
+    return float(np.max(num / den))

@@ -540,3 +540,168 @@ def test_pins_catch_planted_mistakes():
     good = p.apply(c)
     bad_dense = replace(p, beta=np.conj(p.beta)).dense()
     assert np.max(np.abs(c @ bad_dense.T - good)) > 1e-3 * np.max(np.abs(good))
+
+
+# ---------------------------------------------------------------------------------------------
+# Sheared (triclinic) cells: the general image sum of V and the projector phases, pinned by
+# closed forms that hold on any lattice
+# ---------------------------------------------------------------------------------------------
+
+TRICLINIC = np.array([[9.0, 0.0, 0.0], [1.65, 9.45, 0.0], [-1.05, 1.35, 9.9]])
+FLAT_SHEAR = np.array([[6.0, 0.0, 0.0], [5.5, 1.5, 0.0], [0.0, 0.0, 6.0]])
+
+
+def _vloc_series(lat, pos, amp, sig, m):
+    """Continuum Fourier coefficient of the periodic Gaussian sum at G = m . B:
+    A (2 pi sigma^2)^{3/2} / Omega exp(-sigma^2 |G|^2 / 2) sum_a exp(-i G . R_a)."""
+    B, vol = O.reciprocal_lattice(lat)
+    G = np.asarray(m, float) @ B
+    return (amp * (2 * math.pi * sig ** 2) ** 1.5 / vol * math.exp(-0.5 * sig ** 2 * G @ G)
+            * np.exp(-1j * (pos @ G)).sum())
+
+
+@pytest.mark.parametrize("lat", [TRICLINIC, FLAT_SHEAR], ids=["triclinic", "flat_shear"])
+def test_vloc_continuum_series_sheared_cell(lat):
+    """On a sheared cell the grid DFT of V equals the continuum Fourier series of the periodic
+    Gaussian sum (aliasing below 1e-14 on these boxes): fixes the grid points r_j = sum (j_i/N_i) a_i,
+    the image sum and G . R for a non-diagonal lattice."""
+    rng = np.random.default_rng(31)
+    pos = rng.random((3, 3)) @ lat
+    box = (36, 36, 40) if lat is TRICLINIC else (32, 12, 32)
+    V = O.vloc_grid(lat, pos, -2.0, 1.0, box)
+    VN = O.vloc_fourier_grid(V)
+    for m in [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, -1), (1, -1, 2), (-2, 1, 1), (3, 0, -1)]:
+        got = VN[m[2] % box[2], m[1] % box[1], m[0] % box[0]]
+        ana = _vloc_series(lat, pos, -2.0, 1.0, m)
+        assert abs(got - ana) < 1e-12, (m, got, ana)
+
+
+@pytest.mark.parametrize("lat", [TRICLINIC, FLAT_SHEAR], ids=["triclinic", "flat_shear"])
+def test_vloc_translation_by_grid_vector_sheared_cell(lat):
+    """Moving every atom by a grid vector t = sum (s_i/N_i) a_i rolls V on the grid by s exactly
+    (to rounding): the full periodic image sum is translation covariant, a truncated one is not."""
+    rng = np.random.default_rng(32)
+    pos = rng.random((2, 3)) @ lat
+    box = (20, 18, 24)
+    s = np.array([7, -5, 11])
+    t = (s / np.array(box)) @ lat
+    V0 = O.vloc_grid(lat, pos, -2.0, 1.0, box)
+    V1 = O.vloc_grid(lat, pos + t, -2.0, 1.0, box)
+    assert np.max(np.abs(V1 - np.roll(V0, shift=(s[2], s[1], s[0]), axis=(0, 1, 2)))) < 1e-13
+
+
+def _images_covering(lat, reach):
+    """Image counts n_i such that every lattice vector within `reach` of the origin has
+    |n_i| <= n_i: the spacing of the lattice planes is 1/|column i of lat^-1|."""
+    inv = np.linalg.inv(lat)
+    return [int(math.ceil(reach * float(np.linalg.norm(inv[:, i])))) + 1 for i in range(3)]
+
+
+def _projector_overlap_closed_form(lat, d, alpha):
+    """sum_G c_s^2 exp(-2 alpha |G|^2) exp(i G . d) = sum_L exp(-|d + L|^2 / (8 alpha)) (Poisson
+    summation at Gamma with the continuum unit-norm constant c_s)."""
+    reach = math.sqrt(8 * alpha * 50.0) + float(np.linalg.norm(d))
+    n = _images_covering(lat, reach)
+    tot = 0.0
+    for n1 in range(-n[0], n[0] + 1):
+        for n2 in range(-n[1], n[1] + 1):
+            for n3 in range(-n[2], n[2] + 1):
+                L = n1 * lat[0] + n2 * lat[1] + n3 * lat[2]
+                x = d + L
+                tot += math.exp(-(x @ x) / (8 * alpha))
+    return tot
+
+
+@pytest.mark.parametrize("lat", [TRICLINIC, FLAT_SHEAR], ids=["triclinic", "flat_shear"])
+def test_projectors_sheared_cell_closed_form(lat):
+    """s-projectors of two atoms on a sheared cell at Gamma: <beta_a|beta_b> and |beta_a|^2 equal
+    the periodic Gaussian of the separation in closed form (cutoff tail e^-40).  On the large
+    triclinic cell the image terms are negligible and the norm is the continuum value 1; on the
+    flat cell (lattice planes 1.5 bohr apart) the images carry O(1) weight, so the pin also fixes
+    the reciprocal vectors, the phases e^{-iq.R} and c_s on a skew lattice."""
+    pos = np.array([[1.0, 2.0, 0.5], [3.1, 0.4, 2.2]]) @ np.diag([1.0, 0.5 if lat is FLAT_SHEAR else 1.0, 1.0])
+    spheres = [O.enumerate_sphere(lat, 40.0, (0, 0, 0))]
+    b = O.make_basis(lat, 40.0, (0, 0, 0), O.default_box(spheres))
+    beta = O.projectors(lat, b, pos, 4, 0.25)
+    S = beta.conj().T @ beta
+    norm = _projector_overlap_closed_form(lat, np.zeros(3), 0.25)
+    if lat is TRICLINIC:
+        assert abs(norm - 1.0) < 1e-12
+    for i in (0, 4):
+        assert abs(S[i, i] - norm) < 1e-10
+    ana = _projector_overlap_closed_form(lat, pos[0] - pos[1], 0.25)
+    assert 1e-3 < ana
+    assert abs(S[0, 4] - ana) < 1e-10, (S[0, 4], ana)
+
+
+def test_sheared_cell_pins_catch_planted_mistakes():
+    """Each plausible skew-lattice slip, planted in a copy of the oracle's arithmetic, fails the
+    pin above that covers it by a wide margin."""
+    # (5) grid points built with the transposed lattice: the continuum series pin fails
+    lat = TRICLINIC
+    rng = np.random.default_rng(31)
+    pos = rng.random((3, 3)) @ lat
+    box = (36, 36, 40)
+
+    def vloc_transposed(lat_, pos_, box_):
+        N1, N2, N3 = box_
+        j3, j2, j1 = np.meshgrid(np.arange(N3), np.arange(N2), np.arange(N1), indexing="ij")
+        f = np.stack([j1 / N1, j2 / N2, j3 / N3], axis=-1)
+        r = (f @ lat_.T).reshape(-1, 3)
+        n = _images_covering(lat_, O.GAUSS_CUT_SIGMAS + float(np.abs(lat_).sum()))
+        V = np.zeros(r.shape[0])
+        for R in pos_:
+            for n1 in range(-n[0], n[0] + 1):
+                for n2 in range(-n[1], n[1] + 1):
+                    for n3 in range(-n[2], n[2] + 1):
+                        d = r - (R + n1 * lat_[0] + n2 * lat_[1] + n3 * lat_[2])
+                        V += np.exp(-(d * d).sum(axis=1) * 0.5)
+        return (-2.0 * V).reshape(N3, N2, N1)
+
+    VN = O.vloc_fourier_grid(vloc_transposed(lat, pos, box))
+    m = (1, -1, 2)
+    got = VN[m[2] % box[2], m[1] % box[1], m[0] % box[0]]
+    assert abs(got - _vloc_series(lat, pos, -2.0, 1.0, m)) > 1e-4
+
+    # (6) image range from the lengths of the lattice vectors instead of the spacing of the
+    # lattice planes: on a flat sheared cell images are missing and translation covariance fails
+    lat = FLAT_SHEAR
+
+    def vloc_short_images(lat_, pos_, box_):
+        r = O.grid_points(lat_, box_).reshape(-1, 3)
+        n = [int(math.ceil(O.GAUSS_CUT_SIGMAS / float(np.linalg.norm(lat_[i])))) + 1 for i in range(3)]
+        V = np.zeros(r.shape[0])
+        for R in pos_:
+            for n1 in range(-n[0], n[0] + 1):
+                for n2 in range(-n[1], n[1] + 1):
+                    for n3 in range(-n[2], n[2] + 1):
+                        d = r - (R + n1 * lat_[0] + n2 * lat_[1] + n3 * lat_[2])
+                        V += np.exp(-(d * d).sum(axis=1) * 0.5)
+        N1, N2, N3 = box_
+        return (-2.0 * V).reshape(N3, N2, N1)
+
+    rng = np.random.default_rng(32)
+    pos = rng.random((2, 3)) @ lat
+    box = (20, 18, 24)
+    s = np.array([7, -5, 11])
+    t = (s / np.array(box)) @ lat
+    V0 = vloc_short_images(lat, pos, box)
+    V1 = vloc_short_images(lat, pos + t, box)
+    assert np.max(np.abs(V1 - np.roll(V0, shift=(s[2], s[1], s[0]), axis=(0, 1, 2)))) > 1e-7  # pin: 1e-13
+
+    # (7) projector phases with the transposed reciprocal lattice: the two-atom closed form on the
+    # flat sheared cell fails
+    lat = FLAT_SHEAR
+    pos = np.array([[1.0, 1.0, 0.5], [3.1, 0.2, 2.2]])
+    b = O.make_basis(lat, 40.0, (0, 0, 0), O.default_box([O.enumerate_sphere(lat, 40.0, (0, 0, 0))]))
+    B, _ = O.reciprocal_lattice(lat)
+    qbad = b.miller.astype(float) @ B.T
+    bad = replace_basis_q(b, qbad)
+    beta = O.projectors(lat, bad, pos, 1, 0.25)
+    S = beta.conj().T @ beta
+    assert abs(S[0, 1] - _projector_overlap_closed_form(lat, pos[0] - pos[1], 0.25)) > 1e-3
+
+
+def replace_basis_q(b, q):
+    from dataclasses import replace
+    return replace(b, q=q)
