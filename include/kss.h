@@ -249,8 +249,11 @@ kss_status kss_apply_H_host(kss_sys sys, int ik, int nb, const void* psi_host, v
  * on the CUDA cores in both precisions (the tensor-core path needs operand buffers larger than
  * the scratch), so MIXED results agree with kss_apply_H to single-precision rounding.
  *
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress, once
- * per device, with that device current); make that first call before any stream capture.
+ * The first call on each context looks up the array's device address (cudaGetSymbolAddress,
+ * with the context's device current) and keeps it in the context; make that first call before
+ * any stream capture.  With CUDA's default lazy module loading, the first call in a process on a
+ * device is also when the device commits the array's KSS_NOALLOC_SCRATCH_BYTES (the module that
+ * holds it is loaded then); every later call, on any context of that device, commits nothing.
  * All calls share the array and it keeps the last call's contents; nothing in it needs to start
  * at zero (every byte read is written first by the same call).  Calls whose work overlaps on
  * the GPU (two streams, or two contexts on one device) race on the array: order them.
@@ -272,6 +275,24 @@ kss_status kss_apply_H_noalloc(kss_sys sys, int ik, int nb, const void* psi, voi
 kss_status kss_gemm(kss_ctx ctx, int op, int M, int N, int K, const void* A, int lda, const void* B,
                     int ldb, void* C, int ldc, double alpha_re, double alpha_im, double beta_re,
                     double beta_im, kss_precision prec);
+
+/* Dense FP64 generalised Hermitian eigensolve A x = lambda B x, the subspace problem of
+ * Rayleigh-Ritz (§5.1: the projected H and the Gram matrix of the filtered block; Cholesky
+ * orthonormalisation and the Rayleigh-Ritz eigensolve in one), exposed for direct testing and
+ * reuse.  count independent pencils: pencil i has order n[i] >= 0 and DEVICE complex128
+ * column-major matrices A[i] (lda[i] >= max(1, n[i])) and B[i] (ldb[i] >= max(1, n[i])), of
+ * which only the lower triangles are read; B[i] must be Hermitian positive definite.  On return
+ * the leading n x n block of A[i] holds the eigenvectors (columns, B-orthonormal, eigenvalues
+ * ascending), w[i] (DEVICE, n[i] doubles) the eigenvalues, B[i] its Cholesky factor (lower) and
+ * info[i] (HOST) 0, or j + 1 when B[i] is not positive definite at column j (outputs then
+ * undefined).  real != 0: the pencils are real symmetric (imaginary parts ignored; real
+ * eigenvectors).  Hand-written kernels (Cholesky, reduction to standard form, Householder
+ * tridiagonalisation, bisection and inverse iteration, back-transformation): one CTA per pencil,
+ * or a cooperative grid for a single pencil of order >= 160.  Synchronises the context stream.
+ * Errors: KSS_EINVAL (count < 0, NULL arrays, bad sizes), KSS_ETIMEOUT (a bounded grid-barrier
+ * wait gave up), KSS_ECUDA. */
+kss_status kss_dense_hegv(kss_ctx ctx, int count, const int* n, void* const* A, const int* lda,
+                          void* const* B, const int* ldb, double* const* w, int* info, int real);
 
 /* Failure path of the bounded device waits, exercised without a fault (test support; the paper
  * has no counterpart).  Launches one thread that waits on a device word nothing writes, with the
@@ -302,7 +323,9 @@ kss_status kss_density_accumulate(kss_sys sys, int ik, int nb, const void* psi, 
 
 typedef struct {
   int degree;              /* filter polynomial degree m (>= 1; 0 => 10) */
-  double tol;              /* residual tolerance |H x - lambda S x| (Ha) on the wanted bands (<= 0 => 1e-8) */
+  double tol;              /* residual tolerance |H x - lambda S x| (Ha) on the wanted bands (<= 0 => 1e-8
+                              in FP64; in the mixed form max(1e-5, 2e-6 x the spectral upper bound),
+                              twice the single-precision floor of the residual) */
   int max_iter;            /* filter iterations (<= 0 => 200) */
   int nbuffer;             /* extra bands (< 0 => max(4, ceil(nband/10))) */
   kss_precision prec;

@@ -1,7 +1,8 @@
 """Build the in-tree CUDA library ``libkss.so`` for GB300 (sm_103a).
 
 Every translation unit under ``csrc/`` is compiled by nvcc in parallel into ``_build/`` and
-linked into ``paper_2507_08578_gb300/libkss.so`` (cuSOLVER for the FP64 subspace eigensolve).
+linked into ``paper_2507_08578_gb300/libkss.so`` against the CUDA runtime alone (no vendor
+math library: every kernel of the path, the dense FP64 eigensolver included, is in ``csrc/``).
 Rebuilds only when a source, header or flag changed.
 """
 from __future__ import annotations
@@ -36,7 +37,7 @@ def cuda_lib_dir() -> str:
     home = os.path.dirname(os.path.dirname(os.path.realpath(nvcc())))
     for d in ("lib64", "targets/sbsa-linux/lib", "targets/x86_64-linux/lib", "lib"):
         p = os.path.join(home, d)
-        if os.path.exists(os.path.join(p, "libcusolver.so")):
+        if os.path.exists(os.path.join(p, "libcudart.so")):
             return p
     return os.path.join(home, "lib64")
 
@@ -85,7 +86,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
     libdir = cuda_lib_dir()
     tmp = LIB + ".tmp"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + [
-        "-L", libdir, "-lcusolver", "-lcublas", "-lcudart",
+        "-L", libdir, "-lcudart",
         "-Xlinker", "-rpath", "-Xlinker", libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

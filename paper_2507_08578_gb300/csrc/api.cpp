@@ -167,7 +167,6 @@ static kss_status guard(kss_ctx ctx, F&& f) {
 using namespace kss;
 
 namespace kss {
-void ctx_release_solver(kss_ctx ctx);  // solver.cu
 }
 
 extern "C" {
@@ -219,7 +218,6 @@ kss_status kss_destroy(kss_ctx ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   aux_release(ctx);
-  ctx_release_solver(ctx);
   prof_release(ctx);
   ctx->ws_local.release();
   ctx->ws_gemm.release();
@@ -606,8 +604,13 @@ kss_status kss_gemm(kss_ctx ctx, int op, int M, int N, int K, const void* A, int
                 "bad leading dimension");
     KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
     if (prec == KSS_PREC_FP64) {
-      if (op == 0) gemm_cn(ctx, true, M, N, K, A, lda, B, ldb, C, ldc, alpha_re, alpha_im, beta_re, beta_im, "user");
-      else gemm_nn(ctx, true, M, N, K, A, lda, B, ldb, C, ldc, alpha_re, alpha_im, beta_re, beta_im, "user");
+      if (K == 0) {  // C = beta C
+        gemm_cn(ctx, true, M, N, K, A, lda, B, ldb, C, ldc, alpha_re, alpha_im, beta_re, beta_im, "user");
+        return;
+      }
+      if (op == 0) oz_gemm_cn(ctx, M, N, K, A, lda, B, ldb, C, ldc, alpha_re, alpha_im, beta_re, beta_im, "user");
+      else oz_gemm_nn(ctx, M, N, K, A, lda, B, ldb, C, ldc, alpha_re, alpha_im, beta_re, beta_im, "user");
+      if (tc_error_flag(ctx, true)) fail(KSS_ETIMEOUT, "tensor-core GEMM: a bounded wait gave up");
     } else {
       KSS_REQUIRE(K > 0 || (beta_re == 0 && beta_im == 0), "K == 0 with beta != 0 is not supported");
       if (K == 0) {

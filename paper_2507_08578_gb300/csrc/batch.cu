@@ -15,8 +15,6 @@
 #include <map>
 #include <memory>
 
-#include <cublas_v2.h>
-#include <cusolverDn.h>
 
 #include "batch.h"
 #include "batch_kernels.cuh"
@@ -98,20 +96,6 @@ void fill_args(kss_sys s, int ik, LocalArgs<T>& a) {
 
 size_t al256(size_t n) { return (n + 255) & ~(size_t)255; }
 
-// Pad block of unit u's np x np matrices: S gets the identity, H gets shift * identity (so the
-// padded eigenvalues sort after every real one); rows/columns >= nb[u] only.
-__global__ void pad_init(double2* Sb, double2* Hb, const int* __restrict__ nbs, int np, double shift) {
-  const int u = blockIdx.y;
-  const int nb = nbs[u];
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)np * np) return;
-  const int i = (int)(idx % np), j = (int)(idx / np);
-  if (i < nb && j < nb) return;
-  const size_t o = (size_t)u * np * np + idx;
-  Sb[o] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-  Hb[o] = make_double2(i == j ? shift : 0.0, 0.0);
-}
-
 // Copy the leading m x m block of a complex64 matrix (ld m) into a complex128 matrix (ld np).
 __global__ void c64_to_c128_ld(const float2* __restrict__ in, int m, double2* __restrict__ out, int np) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -134,17 +118,11 @@ __global__ void c128_ld_to_c64(const double2* __restrict__ in, int np, float2* _
 // BatchEngine
 // ---------------------------------------------------------------------------------------------
 
-void ctx_release_solver(kss_ctx ctx);               // solver.cu
-cusolverDnHandle_t solver_handle_for(kss_ctx ctx);  // solver.cu (handle bound to ctx->stream)
-
 BatchEngine::~BatchEngine() {
   drop_graph();
-  if (blas) cublasDestroy((cublasHandle_t)blas);
-  if (sparams) cusolverDnDestroyParams((cusolverDnParams_t)sparams);
   if (cap) cudaStreamDestroy((cudaStream_t)cap);
   for (auto w : workers) {
     cudaStreamSynchronize(w->stream);
-    ctx_release_solver(w);
     cudaStreamDestroy(w->stream);
     delete w;
   }
@@ -645,44 +623,13 @@ void BatchEngine::rr_batched(const std::vector<kss_solver_s*>& us, const std::ve
   int np = 0;
   for (auto* s : us) np = std::max(np, s->nb);
   cudaStream_t st = ctx->stream;
-  if (!blas) {
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) fail(KSS_ECUDA, "cublasCreate failed");
-    blas = h;
-    cusolverDnParams_t p = nullptr;
-    if (cusolverDnCreateParams(&p) != CUSOLVER_STATUS_SUCCESS) fail(KSS_ECUDA, "cusolverDnCreateParams failed");
-    sparams = p;
-  }
-  cublasSetStream((cublasHandle_t)blas, st);
-  cusolverDnHandle_t sh = solver_handle_for(ctx);
   const size_t mat = (size_t)np * np;
   Sb.ensure((size_t)U * mat * sizeof(double2));
   Hb.ensure((size_t)U * mat * sizeof(double2));
   Wb.ensure((size_t)U * np * sizeof(double));
-  ptrs.ensure((size_t)2 * U * sizeof(void*) + (size_t)U * sizeof(int));
-  binfo.ensure((size_t)2 * U * sizeof(int));
+  binfo.ensure((size_t)U * sizeof(int));
   double2* S = Sb.as<double2>();
   double2* H = Hb.as<double2>();
-  // per-unit pad sizes and matrix pointer arrays
-  std::vector<void*> hp(2 * U);
-  std::vector<int> nbs(U);
-  double shift = 1.0;
-  for (int u = 0; u < U; ++u) {
-    hp[u] = S + u * mat;
-    hp[U + u] = H + u * mat;
-    nbs[u] = us[u]->nb;
-    shift = std::max(shift, std::fabs(us[u]->sys->k[us[u]->ik].bound));
-  }
-  shift = 16.0 * shift + 1.0;
-  void** dS = (void**)ptrs.p;
-  void** dH = dS + U;
-  int* dnb = (int*)(dH + U);
-  KSS_CHECK_CUDA(cudaMemcpyAsync(ptrs.p, hp.data(), 2 * U * sizeof(void*), cudaMemcpyHostToDevice, st));
-  KSS_CHECK_CUDA(cudaMemcpyAsync(dnb, nbs.data(), U * sizeof(int), cudaMemcpyHostToDevice, st));
-  {
-    dim3 g((unsigned)((mat + 255) / 256), U);
-    pad_init<<<g, 256, 0, st>>>(S, H, dnb, np, shift);
-  }
   // Gram and projected-H matrices of every unit, into the leading nb x nb blocks
   for (int u = 0; u < U; ++u) {
     kss_solver_s* s = us[u];
@@ -700,36 +647,12 @@ void BatchEngine::rr_batched(const std::vector<kss_solver_s*>& us, const std::ve
       c64_to_c128_ld<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(s->Hs32.as<float2>(), nb, H + u * mat, np);
     }
   }
-  // S = L L^H ; H <- L^{-1} H L^{-H} ; H = V W V^H ; Q = L^{-H} V
+  // every unit's FP64 generalised eigensolve (H_s q = lambda S q) in one launch, one CTA per unit
   int* dinfo = binfo.as<int>();
-  if (cusolverDnZpotrfBatched(sh, CUBLAS_FILL_MODE_LOWER, np, (cuDoubleComplex**)dS, np, dinfo, U) !=
-      CUSOLVER_STATUS_SUCCESS)
-    fail(KSS_ECUDA, "cusolverDnZpotrfBatched failed");
-  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0);
-  cublasHandle_t bh = (cublasHandle_t)blas;
-  if (cublasZtrsmBatched(bh, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, np, np,
-                         &one, (const cuDoubleComplex* const*)dS, np, (cuDoubleComplex* const*)dH, np, U) !=
-          CUBLAS_STATUS_SUCCESS ||
-      cublasZtrsmBatched(bh, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, CUBLAS_DIAG_NON_UNIT, np, np,
-                         &one, (const cuDoubleComplex* const*)dS, np, (cuDoubleComplex* const*)dH, np, U) !=
-          CUBLAS_STATUS_SUCCESS)
-    fail(KSS_ECUDA, "cublasZtrsmBatched failed");
-  size_t dws = 0, hws = 0;
-  if (cusolverDnXsyevBatched_bufferSize(sh, (cusolverDnParams_t)sparams, CUSOLVER_EIG_MODE_VECTOR,
-                                        CUBLAS_FILL_MODE_LOWER, np, CUDA_C_64F, H, np, CUDA_R_64F,
-                                        Wb.p, CUDA_C_64F, &dws, &hws, U) != CUSOLVER_STATUS_SUCCESS)
-    fail(KSS_ECUDA, "cusolverDnXsyevBatched_bufferSize failed");
-  bwork.ensure(std::max<size_t>(dws, 16));
-  if (hwork.size() < hws) hwork.resize(hws);
-  if (cusolverDnXsyevBatched(sh, (cusolverDnParams_t)sparams, CUSOLVER_EIG_MODE_VECTOR,
-                             CUBLAS_FILL_MODE_LOWER, np, CUDA_C_64F, H, np, CUDA_R_64F, Wb.p, CUDA_C_64F,
-                             bwork.p, dws, hws ? hwork.data() : nullptr, hws, dinfo + U, U) !=
-      CUSOLVER_STATUS_SUCCESS)
-    fail(KSS_ECUDA, "cusolverDnXsyevBatched failed");
-  if (cublasZtrsmBatched(bh, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, CUBLAS_DIAG_NON_UNIT, np, np,
-                         &one, (const cuDoubleComplex* const*)dS, np, (cuDoubleComplex* const*)dH, np, U) !=
-      CUBLAS_STATUS_SUCCESS)
-    fail(KSS_ECUDA, "cublasZtrsmBatched failed");
+  std::vector<HegvItem> items(U);
+  for (int u = 0; u < U; ++u)
+    items[u] = HegvItem{H + u * mat, S + u * mat, Wb.as<double>() + (size_t)u * np, dinfo + u, us[u]->nb, np, np, false};
+  hegv_batched(ctx, items);
   // rotations, residuals and results of every unit
   for (int u = 0; u < U; ++u) {
     kss_solver_s* s = us[u];
@@ -754,13 +677,12 @@ void BatchEngine::rr_batched(const std::vector<kss_solver_s*>& us, const std::ve
     KSS_CHECK_CUDA(cudaMemcpyAsync(s->hpin, W, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
     KSS_CHECK_CUDA(cudaMemcpyAsync(s->hpin + nb, s->resid_d.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
   }
-  binfo_h.assign(2 * U, 0);
-  KSS_CHECK_CUDA(cudaMemcpyAsync(binfo_h.data(), dinfo, 2 * U * sizeof(int), cudaMemcpyDeviceToHost, st));
+  binfo_h.assign(U, 0);
+  KSS_CHECK_CUDA(cudaMemcpyAsync(binfo_h.data(), dinfo, U * sizeof(int), cudaMemcpyDeviceToHost, st));
   KSS_CHECK_CUDA(cudaStreamSynchronize(st));
   for (int u = 0; u < U; ++u) {
-    // status word read by rr_finish: a failed Cholesky reports n + i like the generalised solver
-    const int pi = binfo_h[u], ei = binfo_h[U + u];
-    const int info = pi != 0 ? us[u]->nb + pi : ei;
+    // status word read by rr_finish
+    const int info = binfo_h[u];
     std::memcpy(us[u]->hpin + 2 * us[u]->nb, &info, sizeof(int));
   }
   KSS_CHECK_CUDA(cudaGetLastError());

@@ -80,10 +80,7 @@ class BatchEngine {
   // triangular solves and Hermitian eigensolve (one call each for every unit).
   void rr_batched(const std::vector<kss_solver_s*>& us, const std::vector<int>& y,
                   const std::vector<int>& hy, const std::vector<int>& xo, const std::vector<int>& hxo);
-  void* blas = nullptr;      // cublasHandle_t
-  void* sparams = nullptr;   // cusolverDnParams_t
-  DevBuf Sb, Hb, Wb, ptrs, binfo, bwork, q32;
-  std::vector<char> hwork;
+  DevBuf Sb, Hb, Wb, binfo, q32;
   std::vector<int> binfo_h;
   void* cap = nullptr;    // cudaStream_t used only to record the graph
 };

@@ -1,0 +1,947 @@
+// FP64 dense generalised Hermitian eigensolver for the Rayleigh-Ritz step (§5.1: the subspace
+// problem of the Chebyshev-filtered iteration, "less efficient on GPU" and called rarely).
+//
+// Solves A x = lambda B x for Hermitian A and Hermitian positive definite B (n x n, complex128,
+// column-major, lower triangles read), returning all eigenvalues ascending and B-orthonormal
+// eigenvectors, in five phases written out here:
+//
+//   1. Cholesky B = L L^H (right-looking, one rank-1 update of the trailing lower triangle per
+//      column with unscaled columns, then the columns scaled by 1/sqrt(pivot)).
+//   2. Reduction to standard form C = L^{-1} A L^{-H}: two forward substitutions with n
+//      right-hand sides each (X = L^{-1} A, then C = L^{-1} X^H, using A = A^H).
+//   3. Householder tridiagonalisation C = Q T Q^H (unblocked, on the full Hermitian matrix):
+//      per column, the reflector H = I - tau v v^H with a real subdiagonal (beta = -sign(Re
+//      alpha) |x|), p = tau C v, w = p - (tau/2)(p^H v) v, C <- C - v w^H - w v^H.
+//   4. Eigenpairs of the real symmetric tridiagonal T: every eigenvalue by bisection on the
+//      Sturm count (the number of negative pivots of the LDL^T factorisation of T - sigma I),
+//      every eigenvector by inverse iteration with the partially pivoted LU of T - lambda I;
+//      eigenvalues closer than 1e-5 |T| form a cluster whose vectors are orthogonalised against
+//      each other (modified Gram-Schmidt) in every iteration.
+//   5. Back-transformation x = L^{-H} Q z (the reflectors applied to each column of Z in
+//      reverse order, then a backward substitution with L^H).
+//
+// Parallel organisation.  The same phase code runs on a "team": either one CTA (many small
+// pencils, one CTA each, barrier = __syncthreads) or a whole cooperative grid (one large pencil,
+// barrier = a grid barrier of this file with a bounded wait).  Work that is independent per
+// column (the triangular solves, the reflector applications, the inverse iterations) needs no
+// team barrier: one warp owns a column and each lane owns the rows r = lane (mod 32), so values
+// written by one lane are read back only by that lane and everything else travels by shuffles.
+// The barrier count is about 3n per pencil (n Cholesky steps, 2n tridiagonalisation steps).
+//
+// Every grid-barrier wait gives up after a time limit; the kernel then raises the control
+// block's error word, sets the pencil's info to -1, and every thread leaves at its next barrier;
+// callers report KSS_ETIMEOUT.  A non-positive Cholesky pivot at column j stops the solve with
+// info = j + 1 (the LAPACK convention) and leaves the outputs undefined.
+#include <cuda/atomic>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "kss_internal.h"
+
+namespace kss {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// ---- complex helpers ---------------------------------------------------------------------------
+// On GB300 an SM retires about two FP64 fused multiply-adds per clock, so every FP64 instruction
+// counts: complex products are written as chains of fused multiply-adds (4 per complex
+// multiply-accumulate) and scalars a whole warp or CTA needs are computed once and broadcast.
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // conj(a) * b
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // c + a b
+  return make_double2(fma(-a.y, b.y, fma(a.x, b.x, c.x)), fma(a.y, b.x, fma(a.x, b.y, c.y)));
+}
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {  // c - a b
+  return make_double2(fma(a.y, b.y, fma(-a.x, b.x, c.x)), fma(-a.y, b.x, fma(-a.x, b.y, c.y)));
+}
+__device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {  // c + conj(a) b
+  return make_double2(fma(a.y, b.y, fma(a.x, b.x, c.x)), fma(-a.y, b.x, fma(a.x, b.y, c.y)));
+}
+__device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 shfl_c(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ double2 warp_sum_c(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Control block of one grid-team solve (zeroed before the launch).
+struct Ctl {
+  unsigned count;
+  unsigned gen;
+  int err;  // 1: a barrier wait gave up
+  int pad;
+};
+
+struct CtaTeam {
+  __device__ int rank() const { return threadIdx.x; }
+  // rank for per-thread independent work (the same as rank() on one CTA)
+  __device__ int srank() const { return threadIdx.x; }
+  __device__ int swrank() const { return threadIdx.x >> 5; }  // the same for per-warp work
+  __device__ int size() const { return blockDim.x; }
+  __device__ int wrank() const { return threadIdx.x >> 5; }
+  __device__ int wsize() const { return blockDim.x >> 5; }
+  __device__ bool sync() const {
+    __syncthreads();
+    return true;
+  }
+};
+
+struct GridTeam {
+  Ctl* ctl;
+  int* info;  // the pencil's status word: -1 when a barrier wait gave up
+  unsigned long long limit_ns;
+  __device__ int rank() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+  // rank for per-thread independent work, spread over the CTAs first so that n work items use
+  // every SM's FP64 units instead of the first few CTAs'
+  __device__ int srank() const { return threadIdx.x * gridDim.x + blockIdx.x; }
+  __device__ int swrank() const { return (threadIdx.x >> 5) * gridDim.x + blockIdx.x; }
+  __device__ int size() const { return gridDim.x * blockDim.x; }
+  __device__ int wrank() const { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+  __device__ int wsize() const { return (gridDim.x * blockDim.x) >> 5; }
+  // Grid barrier (all CTAs are resident: cooperative launch).  Arrival is an acq_rel add on a
+  // counter; the last CTA to arrive resets the counter and releases a new generation, the others
+  // wait for it with a bounded spin.  Returns false when the solve has been abandoned.
+  __device__ bool sync() const {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(ctl->gen), cnt(ctl->count);
+      cuda::atomic_ref<int, cuda::thread_scope_device> err(ctl->err);
+      int ok = err.load(cuda::memory_order_relaxed) == 0;
+      if (ok) {
+        __threadfence();
+        const unsigned g = gen.load(cuda::memory_order_acquire);
+        const unsigned a = cnt.fetch_add(1u, cuda::memory_order_acq_rel) + 1u;
+        if (a == gridDim.x) {
+          cnt.store(0u, cuda::memory_order_relaxed);
+          gen.store(g + 1u, cuda::memory_order_release);
+        } else {
+          const unsigned long long t0 = global_ns();
+          unsigned spins = 0;
+          while (gen.load(cuda::memory_order_acquire) == g) {
+            if (err.load(cuda::memory_order_relaxed)) {
+              ok = 0;
+              break;
+            }
+            if ((++spins & 63u) == 0 && global_ns() - t0 > limit_ns) {
+              err.store(1, cuda::memory_order_relaxed);
+              *info = -1;
+              ok = 0;
+              break;
+            }
+          }
+        }
+        __threadfence();
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+  }
+};
+
+// One pencil and its workspace.
+struct Pencil {
+  double2* A;   // n x n (lda): in A, out eigenvectors
+  double2* B;   // n x n (ldb): in B, out Cholesky factor L (lower)
+  double* w;    // n eigenvalues (out)
+  int* info;    // out: 0, or j + 1 for a non-positive pivot at column j
+  int n, lda, ldb, real;
+  double2* R;   // n x n (ld n): reduction workspace, then the reflector vectors
+  double* Z;    // n x n (ld n): eigenvectors of T
+  double* wk;   // 6 n^2 doubles: inverse-iteration arrays
+  double* vec;  // 9 n + 8 doubles: d, e, tau (complex), p (complex), 1/L_jj, e^2, FP32 d and e^2
+  int smem_cols;  // 1: the launch gives every warp n complex words of dynamic shared memory
+};
+
+// ---- phase 0: inputs ---------------------------------------------------------------------------
+template <class Team>
+__device__ bool prepare(const Team& T, const Pencil& P) {
+  const int n = P.n;
+  if (P.real) {
+    for (long long t = T.rank(); t < (long long)n * n; t += T.size()) {
+      const int i = (int)(t % n), j = (int)(t / n);
+      P.A[i + (size_t)j * P.lda].y = 0.0;
+      P.B[i + (size_t)j * P.ldb].y = 0.0;
+    }
+  }
+  return T.sync();
+}
+
+// ---- phase 1: Cholesky B = L L^H -----------------------------------------------------------------
+__device__ __forceinline__ double* vrdiag(const Pencil& P) { return P.vec + 6 * P.n; }
+
+// Returns false when the solve stops (non-positive pivot: *info set; or an abandoned barrier).
+template <class Team>
+__device__ bool cholesky(const Team& T, const Pencil& P) {
+  const int n = P.n, ld = P.ldb;
+  double2* B = P.B;
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < n; ++j) {
+    const double d = B[j + (size_t)j * ld].x;
+    if (!(d > 0.0) || !isfinite(d)) {
+      if (T.rank() == 0) *P.info = j + 1;
+      return false;
+    }
+    const double2* __restrict__ cj = B + (size_t)j * ld;
+    bool have = false;
+    double dinv = 0.0;
+    for (int k = j + 1 + T.wrank(); k < n; k += T.wsize()) {
+      if (!have) {  // one division per warp, not per thread
+        dinv = __shfl_sync(0xffffffffu, lane == 0 ? 1.0 / d : 0.0, 0);
+        have = true;
+      }
+      const double2 f = cscale(conjd(cj[k]), dinv);
+      double2* __restrict__ ck = B + (size_t)k * ld;
+      int i = k + lane;
+      // four rows per lane per pass, loads first (columns j and k never alias)
+      for (; i + 96 < n; i += 128) {
+        const double2 a0 = ck[i], a1 = ck[i + 32], a2 = ck[i + 64], a3 = ck[i + 96];
+        const double2 b0 = cj[i], b1 = cj[i + 32], b2 = cj[i + 64], b3 = cj[i + 96];
+        ck[i] = cfms(b0, f, a0);
+        ck[i + 32] = cfms(b1, f, a1);
+        ck[i + 64] = cfms(b2, f, a2);
+        ck[i + 96] = cfms(b3, f, a3);
+      }
+      for (; i < n; i += 32) ck[i] = cfms(cj[i], f, ck[i]);
+    }
+    if (!T.sync()) return false;
+  }
+  // scale the columns: L[i][j] = B[i][j] / sqrt(d_j), L[j][j] = sqrt(d_j); keep 1/L[j][j]
+  double* rd = vrdiag(P);
+  for (int j = T.wrank(); j < n; j += T.wsize()) {
+    double2* cj = B + (size_t)j * ld;
+    double s = 0.0, r = 0.0;
+    if (lane == 0) {
+      s = sqrt(cj[j].x);
+      r = 1.0 / s;
+    }
+    s = __shfl_sync(0xffffffffu, s, 0);
+    r = __shfl_sync(0xffffffffu, r, 0);
+    for (int i = j + 1 + lane; i < n; i += 32) cj[i] = cscale(cj[i], r);
+    __syncwarp();
+    if (lane == 0) {
+      cj[j] = make_double2(s, 0.0);
+      rd[j] = r;
+    }
+  }
+  return T.sync();
+}
+
+// x <- L^{-1} x for one column x (stride 1) by the calling warp, in blocks of 32 rows: the
+// diagonal block is solved in registers (lane l holds row b0 + l, values pass by shuffles), then the
+// rows below are updated by a block product whose loads are all independent.  rd: 1 / L[i][i].
+__device__ __forceinline__ void forward_subst(const double2* __restrict__ L, const double* __restrict__ rd,
+                                              int ld, int n, double2* __restrict__ x) {
+  const int lane = threadIdx.x & 31;
+  for (int b0 = 0; b0 < n; b0 += 32) {
+    const int bn = min(32, n - b0);
+    double2 xl = lane < bn ? x[b0 + lane] : make_double2(0.0, 0.0);
+    const double rl = lane < bn ? rd[b0 + lane] : 0.0;
+    for (int i = 0; i < bn; ++i) {
+      if (lane == i) xl = cscale(xl, rl);
+      const double2 xi = shfl_c(xl, i);
+      if (lane > i && lane < bn) xl = cfms(L[(size_t)(b0 + i) * ld + b0 + lane], xi, xl);
+    }
+    if (lane < bn) x[b0 + lane] = xl;
+    for (int r0 = b0 + bn; r0 < n; r0 += 32) {
+      const int r = r0 + lane;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int i = 0; i < bn; ++i) {
+        const double2 xi = shfl_c(xl, i);
+        if (r < n) acc = cfma(L[(size_t)(b0 + i) * ld + r], xi, acc);
+      }
+      if (r < n) x[r] = csub(x[r], acc);
+    }
+  }
+}
+
+// x <- L^{-H} x for one column x by the calling warp, in blocks of 32 rows from the bottom: the
+// diagonal block of L^H is solved in registers, then the rows above are updated (lane i reads the
+// contiguous segment L[b0..b1), i] of column i).
+__device__ __forceinline__ void backward_subst_h(const double2* __restrict__ L, const double* __restrict__ rd,
+                                                 int ld, int n, double2* __restrict__ x) {
+  const int lane = threadIdx.x & 31;
+  for (int b1 = n; b1 > 0; b1 -= 32) {
+    const int b0 = max(0, b1 - 32), bn = b1 - b0;
+    double2 xl = lane < bn ? x[b0 + lane] : make_double2(0.0, 0.0);
+    const double rl = lane < bn ? rd[b0 + lane] : 0.0;
+    for (int i = bn - 1; i >= 0; --i) {
+      if (lane == i) xl = cscale(xl, rl);
+      const double2 xi = shfl_c(xl, i);
+      if (lane < i) xl = csub(xl, cmulc(L[(size_t)(b0 + lane) * ld + b0 + i], xi));
+    }
+    if (lane < bn) x[b0 + lane] = xl;
+    for (int r0 = 0; r0 < b0; r0 += 32) {
+      const int r = r0 + lane;
+      double2 acc = make_double2(0.0, 0.0);
+      const double2* lr = L + (size_t)r * ld + b0;
+      for (int t = 0; t < bn; ++t) {
+        const double2 xt = shfl_c(xl, t);
+        if (r < b0) acc = cfmac(lr[t], xt, acc);
+      }
+      if (r < b0) x[r] = csub(x[r], acc);
+    }
+  }
+}
+
+// ---- phase 2: C = L^{-1} A L^{-H} ---------------------------------------------------------------
+template <class Team>
+__device__ bool reduce_standard(const Team& T, const Pencil& P) {
+  const int n = P.n, la = P.lda;
+  double2* A = P.A;
+  double2* R = P.R;
+  const int lane = threadIdx.x & 31;
+  // full Hermitian A from its lower triangle
+  for (int i = T.wrank(); i < n; i += T.wsize()) {
+    double2* ci = A + (size_t)i * la;
+    for (int j = lane; j < i; j += 32) ci[j] = conjd(A[i + (size_t)j * la]);
+    if (lane == 0) ci[i].y = 0.0;
+  }
+  if (!T.sync()) return false;
+  // X = L^{-1} A, column by column, in place in A
+  for (int c = T.wrank(); c < n; c += T.wsize()) forward_subst(P.B, vrdiag(P), P.ldb, n, A + (size_t)c * la);
+  if (!T.sync()) return false;
+  // R = X^H
+  for (int r = T.wrank(); r < n; r += T.wsize()) {
+    double2* cr = R + (size_t)r * n;
+    for (int c = lane; c < n; c += 32) cr[c] = conjd(A[r + (size_t)c * la]);
+  }
+  if (!T.sync()) return false;
+  // C = L^{-1} X^H = L^{-1} A L^{-H}, in place in R
+  for (int c = T.wrank(); c < n; c += T.wsize()) forward_subst(P.B, vrdiag(P), P.ldb, n, R + (size_t)c * n);
+  if (!T.sync()) return false;
+  // A = C, made exactly Hermitian (lower triangle kept, upper = its conjugate, real diagonal)
+  for (int c = T.wrank(); c < n; c += T.wsize()) {
+    double2* ac = A + (size_t)c * la;
+    for (int r = lane; r < n; r += 32) {
+      double2 v;
+      if (r > c) v = R[r + (size_t)c * n];
+      else if (r < c) v = conjd(R[c + (size_t)r * n]);
+      else v = make_double2(R[c + (size_t)c * n].x, 0.0);
+      ac[r] = v;
+    }
+  }
+  return T.sync();
+}
+
+// ---- phase 3: Householder tridiagonalisation ------------------------------------------------------
+// vec layout: d[n], e[n], tau[2n] (complex), p[2n] (complex), colnorm[2]
+__device__ __forceinline__ double* vd(const Pencil& P) { return P.vec; }
+__device__ __forceinline__ double* ve(const Pencil& P) { return P.vec + P.n; }
+__device__ __forceinline__ double2* vtau(const Pencil& P) { return reinterpret_cast<double2*>(P.vec + 2 * P.n); }
+__device__ __forceinline__ double2* vp(const Pencil& P) { return reinterpret_cast<double2*>(P.vec + 4 * P.n); }
+__device__ __forceinline__ double* ve2(const Pencil& P) { return P.vec + 7 * P.n; }   // e^2
+__device__ __forceinline__ float* vd32(const Pencil& P) { return reinterpret_cast<float*>(P.vec + 8 * P.n); }
+__device__ __forceinline__ float* ve232(const Pencil& P) { return vd32(P) + P.n; }   // e^2 in FP32
+
+
+// Reflector j, by one warp, from column j of A after every earlier update: x = A[j+1..n-1][j],
+// beta = -sign(Re x_0) |x| (the real subdiagonal), tau = (beta - x_0) / beta and v = x / (x_0 - beta)
+// with v_{j+1} = 1, stored in column j of R; d_j and e_j of T.  The scalars are formed by one lane.
+__device__ __forceinline__ void make_reflector(const Pencil& P, int j) {
+  const int n = P.n, lane = threadIdx.x & 31;
+  const double2* cj = P.A + (size_t)j * P.lda;
+  double s = 0.0;
+  for (int i = j + 2 + lane; i < n; i += 32) {
+    const double2 a = cj[i];
+    s = fma(a.x, a.x, fma(a.y, a.y, s));
+  }
+  s = warp_sum(s);
+  double beta = 0.0;
+  double2 tj = make_double2(0.0, 0.0), vs = make_double2(0.0, 0.0);
+  if (lane == 0) {
+    const double2 alpha = cj[j + 1];
+    if (s == 0.0 && alpha.y == 0.0) {
+      beta = alpha.x;
+    } else {
+      const double an = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + s);
+      beta = alpha.x >= 0.0 ? -an : an;
+      const double rb = 1.0 / beta;
+      tj = make_double2((beta - alpha.x) * rb, -alpha.y * rb);
+      const double2 den = make_double2(alpha.x - beta, alpha.y);  // v_i = x_i / (alpha - beta)
+      const double rd = 1.0 / (den.x * den.x + den.y * den.y);
+      vs = make_double2(den.x * rd, -den.y * rd);
+    }
+    vd(P)[j] = cj[j].x;
+    ve(P)[j] = beta;
+    vtau(P)[j] = tj;
+  }
+  vs = shfl_c(vs, 0);
+  double2* rj = P.R + (size_t)j * n;
+  for (int i = j + 1 + lane; i < n; i += 32) rj[i] = i == j + 1 ? make_double2(1.0, 0.0) : cmul(cj[i], vs);
+}
+
+// Sum over the CTA (every thread passes a value; every thread gets the same total, reduced in a
+// fixed order so that all CTAs of a grid team obtain bit-identical results).
+__device__ __forceinline__ double2 cta_sum_c(double2 v) {
+  __shared__ double2 red[kWarps];
+  v = warp_sum_c(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double2 s = make_double2(0.0, 0.0);
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = cadd(s, red[w]);
+  return s;
+}
+
+// sv, sw: 2 m complex words of shared memory per CTA (m <= n).
+template <class Team>
+__device__ bool tridiagonalise(const Team& T, const Pencil& P, double2* sv) {
+  const int n = P.n, la = P.lda;
+  double2* A = P.A;
+  double2* __restrict__ p = vp(P);
+  const int lane = threadIdx.x & 31;
+  if (n == 1) {
+    if (T.rank() == 0) vd(P)[0] = A[0].x;
+    return T.sync();
+  }
+  double2* sw = sv + n;
+  if (T.wrank() == 0) make_reflector(P, 0);
+  if (!T.sync()) return false;
+  for (int j = 0; j < n - 1; ++j) {
+    const double2 tj = vtau(P)[j];
+    const double2* __restrict__ rj = P.R + (size_t)j * n;
+    const int m = n - j - 1;
+    // p_i = tau sum_k conj(A[k][i]) v_k over the trailing block (column i of A is row i of A^H)
+    for (int i = j + 1 + T.wrank(); i < n; i += T.wsize()) {
+      const double2* __restrict__ ci = A + (size_t)i * la;
+      double2 s = make_double2(0.0, 0.0);
+      for (int k = j + 1 + lane; k < n; k += 32) s = cfmac(ci[k], rj[k], s);
+      s = warp_sum_c(s);
+      if (lane == 0) p[i] = cmul(tj, s);
+    }
+    if (!T.sync()) return false;
+    // gamma = -(tau/2) p^H v (each CTA reduces it in the same order); v and w = p + gamma v staged
+    double2 g = make_double2(0.0, 0.0);
+    for (int t = threadIdx.x; t < m; t += blockDim.x) g = cfmac(p[j + 1 + t], rj[j + 1 + t], g);
+    g = cta_sum_c(g);
+    const double2 gamma = cscale(cmul(tj, g), -0.5);
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+      const double2 v = rj[j + 1 + t];
+      sv[t] = v;
+      sw[t] = cfma(gamma, v, p[j + 1 + t]);
+    }
+    __syncthreads();
+    // A <- A - v w^H - w v^H on the trailing block
+    for (int k = j + 1 + T.wrank(); k < n; k += T.wsize()) {
+      const double2 cvk = conjd(sv[k - j - 1]), cwk = conjd(sw[k - j - 1]);
+      double2* __restrict__ ck = A + (size_t)k * la;
+      int i = j + 1 + lane;
+      for (; i + 96 < n; i += 128) {
+        double2 a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = ck[i + 32 * u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int t = i + 32 * u - j - 1;
+          ck[i + 32 * u] = cfms(sw[t], cvk, cfms(sv[t], cwk, a[u]));
+        }
+      }
+      for (; i < n; i += 32) {
+        const int t = i - j - 1;
+        ck[i] = cfms(sw[t], cvk, cfms(sv[t], cwk, ck[i]));
+      }
+      if (k == j + 1 && j + 1 < n - 1) {  // the next reflector, from the column just updated
+        __syncwarp();
+        make_reflector(P, j + 1);
+      }
+    }
+    if (!T.sync()) return false;
+  }
+  if (T.rank() == 0) vd(P)[n - 1] = A[(n - 1) + (size_t)(n - 1) * la].x;
+  return T.sync();
+}
+
+// ---- phase 4: eigenpairs of the symmetric tridiagonal T (d, e) -----------------------------------
+// Number of eigenvalues of T below s (Sturm count of the LDL^T pivots of T - s I); e2 = e^2.
+__device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int n,
+                                           double s, double pivmin) {
+  int c = 0;
+  double q = d[0] - s;
+  if (fabs(q) < pivmin) q = -pivmin;
+  c += q < 0.0;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - s) - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += q < 0.0;
+  }
+  return c;
+}
+// The same count in FP32 (about 64 times cheaper on GB300), used only to narrow the bracket.
+__device__ __forceinline__ int sturm_count32(const float* __restrict__ d, const float* __restrict__ e2, int n,
+                                             float s, float pivmin) {
+  int c = 0;
+  float q = d[0] - s;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  c += q < 0.f;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - s) - __fdividef(e2[i - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += q < 0.f;
+  }
+  return c;
+}
+
+// Deterministic start vector entry in (-1, 1) for eigenvector k, row i.
+__device__ __forceinline__ double start_entry(int k, int i) {
+  unsigned h = (unsigned)k * 0x9E3779B1u ^ ((unsigned)i + 0x7F4A7C15u) * 0x85EBCA77u;
+  h ^= h >> 16;
+  h *= 0x7FEB352Du;
+  h ^= h >> 15;
+  h *= 0x846CA68Bu;
+  h ^= h >> 16;
+  return ((double)(h >> 8) + 0.5) * (2.0 / 16777216.0) - 1.0;
+}
+
+template <class Team>
+__device__ bool tridiagonal_eig(const Team& T, const Pencil& P) {
+  const int n = P.n;
+  const double* d = vd(P);
+  const double* e = ve(P);
+  double* e2 = ve2(P);
+  float* d32 = vd32(P);
+  float* e232 = ve232(P);
+  double* w = P.w;
+  for (int i = T.rank(); i < n; i += T.size()) {
+    const double ei = i < n - 1 ? e[i] : 0.0;
+    e2[i] = ei * ei;
+    d32[i] = (float)d[i];
+    e232[i] = (float)(ei * ei);
+  }
+  // norms and Gershgorin interval (every thread computes them the same way)
+  double tn = 0.0, gl = 0.0, gu = 0.0, emax2 = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+    tn = fmax(tn, fabs(d[i]) + r);
+    gl = i ? fmin(gl, d[i] - r) : d[i] - r;
+    gu = i ? fmax(gu, d[i] + r) : d[i] + r;
+    if (i < n - 1) emax2 = fmax(emax2, e[i] * e[i]);
+  }
+  const double eps = 2.220446049250313e-16;
+  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, emax2);
+  tn = fmax(tn, 1e-300);
+  gl -= 2.0 * eps * tn + 2.0 * pivmin;
+  gu += 2.0 * eps * tn + 2.0 * pivmin;
+  if (!T.sync()) return false;
+  // Eigenvalue k by multisection, one warp per eigenvalue: in every round the 32 lanes count at 32
+  // interior points of the bracket [lo, hi] (count(lo) <= k < count(hi)) and the bracket shrinks
+  // to the 1/33 between the last point below eigenvalue k and the first above it, so a FP64
+  // Sturm count (a chain of dependent divisions, slow on GB300) is needed only ~7 times in
+  // sequence.  The bracket is first narrowed with FP32 counts to 1e-6 |T|, widened by 2e-6 |T|
+  // and accepted only if the FP64 counts at both ends confirm it (else the Gershgorin interval is
+  // used).
+  const float pivmin32 = 1e-30f * (float)fmax(1.0, emax2);
+  const int lane = threadIdx.x & 31;
+  if (T.wsize() >= n) {
+    for (int k = T.swrank(); k < n; k += T.wsize()) {
+      float l32 = (float)gl, h32 = (float)gu;
+      const float wid = (float)(1e-6 * tn);
+      for (int it = 0; it < 12 && h32 - l32 > wid; ++it) {
+        const float step = (h32 - l32) * (1.0f / 33.0f);
+        const float pt = l32 + (float)(lane + 1) * step;
+        const unsigned above = __ballot_sync(0xffffffffu, pt < h32 && sturm_count32(d32, e232, n, pt, pivmin32) > k);
+        const int f = above ? __ffs(above) - 1 : 32;
+        const float nl = f == 0 ? l32 : l32 + (float)f * step;
+        const float nh = f == 32 ? h32 : l32 + (float)(f + 1) * step;
+        if (!(nh > nl)) break;
+        l32 = nl;
+        h32 = fminf(nh, h32);
+      }
+      double lo = fmax(gl, (double)l32 - 2e-6 * tn), hi = fmin(gu, (double)h32 + 2e-6 * tn);
+      {
+        const int c = lane == 0 ? sturm_count(d, e2, n, lo, pivmin) : (lane == 1 ? sturm_count(d, e2, n, hi, pivmin) : 0);
+        const int c0 = __shfl_sync(0xffffffffu, c, 0), c1 = __shfl_sync(0xffffffffu, c, 1);
+        if (!(c0 <= k && c1 > k)) {
+          lo = gl;
+          hi = gu;
+        }
+      }
+      for (int it = 0; it < 40; ++it) {
+        if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+        const double step = (hi - lo) * (1.0 / 33.0);
+        const double pt = lo + (double)(lane + 1) * step;
+        const unsigned above = __ballot_sync(0xffffffffu, pt < hi && sturm_count(d, e2, n, pt, pivmin) > k);
+        const int f = above ? __ffs(above) - 1 : 32;
+        const double nl = f == 0 ? lo : lo + (double)f * step;
+        const double nh = f == 32 ? hi : lo + (double)(f + 1) * step;
+        if (!(nh > nl) || (nl == lo && nh >= hi)) break;
+        lo = nl;
+        hi = fmin(nh, hi);
+      }
+      if (lane == 0) w[k] = 0.5 * (lo + hi);
+    }
+  } else {
+    // fewer warps than eigenvalues (one CTA per pencil): plain bisection, one thread per
+    // eigenvalue, with the same FP32 narrowing and FP64 confirmation of the bracket
+    for (int k = T.srank(); k < n; k += T.size()) {
+      float l32 = (float)gl, h32 = (float)gu;
+      const float wid = (float)(1e-5 * tn);
+      for (int it = 0; it < 64 && h32 - l32 > wid; ++it) {
+        const float mid = 0.5f * (l32 + h32);
+        if (mid <= l32 || mid >= h32) break;
+        if (sturm_count32(d32, e232, n, mid, pivmin32) > k) h32 = mid;
+        else l32 = mid;
+      }
+      double lo = fmax(gl, (double)l32 - 1e-5 * tn), hi = fmin(gu, (double)h32 + 1e-5 * tn);
+      if (!(sturm_count(d, e2, n, lo, pivmin) <= k && sturm_count(d, e2, n, hi, pivmin) > k)) {
+        lo = gl;
+        hi = gu;
+      }
+      for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin || mid <= lo || mid >= hi) break;
+        if (sturm_count(d, e2, n, mid, pivmin) > k) hi = mid;
+        else lo = mid;
+      }
+      w[k] = 0.5 * (lo + hi);
+    }
+  }
+  if (!T.sync()) return false;
+  // eigenvectors by inverse iteration, one cluster per thread
+  const double ortol = 1e-5 * tn;
+  const double tiny = eps * tn;
+  const size_t nn = (size_t)n * n;
+  double* ua = P.wk;           // reciprocals of U's diagonal
+  double* ub = P.wk + nn;      // U first superdiagonal
+  double* uc = P.wk + 2 * nn;  // U second superdiagonal (fill-in of row swaps)
+  double* ml = P.wk + 3 * nn;  // multipliers
+  double* sw = P.wk + 4 * nn;  // 1: rows i, i+1 swapped
+  double* x = P.wk + 5 * nn;   // iterate
+  for (int k0 = T.srank(); k0 < n; k0 += T.size()) {
+    if (k0 > 0 && w[k0] - w[k0 - 1] <= ortol) continue;  // not the first of its cluster
+    int k1 = k0 + 1;
+    while (k1 < n && w[k1] - w[k1 - 1] <= ortol) ++k1;
+    double sprev = 0.0;
+    for (int m = k0; m < k1; ++m) {
+      // slot m of the interleaved arrays: element i at [i * n + m]
+      double s = w[m];
+      const double pert = 10.0 * eps * fmax(fabs(s), tn);
+      if (m > k0 && s - sprev < pert) s = sprev + pert;
+      sprev = s;
+      // factor T - s I = P L U with partial pivoting
+      {
+        double a = d[0] - s, b = n > 1 ? e[0] : 0.0;
+        for (int i = 0; i < n - 1; ++i) {
+          const double sub = e[i];
+          const double nd = d[i + 1] - s;
+          const double ns = i + 1 < n - 1 ? e[i + 1] : 0.0;
+          const size_t o = (size_t)i * n + m;
+          // ua holds the reciprocal pivot: one division per row, none in the solves
+          if (fabs(a) >= fabs(sub)) {
+            if (a == 0.0) a = tiny;
+            const double r = 1.0 / a;
+            const double l = sub * r;
+            ua[o] = r;
+            ub[o] = b;
+            uc[o] = 0.0;
+            ml[o] = l;
+            sw[o] = 0.0;
+            a = nd - l * b;
+            b = ns;
+          } else {
+            const double r = 1.0 / sub;
+            const double l = a * r;
+            ua[o] = r;
+            ub[o] = nd;
+            uc[o] = ns;
+            ml[o] = l;
+            sw[o] = 1.0;
+            a = b - l * nd;
+            b = -l * ns;
+          }
+        }
+        if (a == 0.0) a = tiny;
+        ua[(size_t)(n - 1) * n + m] = 1.0 / a;
+      }
+      for (int i = 0; i < n; ++i) x[(size_t)i * n + m] = start_entry(m, i);
+      const int iters = (k1 - k0 > 1) ? 4 : 3;
+      for (int it = 0; it < iters; ++it) {
+        // forward: apply the row operations of the factorisation (the running row in a register)
+        {
+          double cur = x[m];
+          for (int i = 0; i < n - 1; ++i) {
+            const size_t o = (size_t)i * n + m;
+            double nxt = x[o + n];
+            if (sw[o] != 0.0) {
+              const double t = cur;
+              cur = nxt;
+              nxt = t;
+            }
+            x[o] = cur;
+            cur = nxt - ml[o] * cur;
+          }
+          x[(size_t)(n - 1) * n + m] = cur;
+        }
+        // backward with U (the two solved rows below in registers; scaled when the iterate grows)
+        {
+          double x1 = 0.0, x2 = 0.0;
+          for (int i = n - 1; i >= 0; --i) {
+            const size_t o = (size_t)i * n + m;
+            double v = x[o];
+            if (i + 1 < n) v -= ub[o] * x1;
+            if (i + 2 < n) v -= uc[o] * x2;
+            v *= ua[o];
+            x[o] = v;
+            x2 = x1;
+            x1 = v;
+            if (fabs(v) > 1e100) {
+              for (int r = 0; r < n; ++r) x[(size_t)r * n + m] *= 1e-100;
+              x1 *= 1e-100;
+              x2 *= 1e-100;
+            }
+          }
+        }
+        // orthogonalise against the cluster's earlier vectors, then normalise
+        for (int q = k0; q < m; ++q) {
+          const double* zq = P.Z + (size_t)q * n;
+          double s2 = 0.0;
+          for (int i = 0; i < n; ++i) s2 += zq[i] * x[(size_t)i * n + m];
+          for (int i = 0; i < n; ++i) x[(size_t)i * n + m] -= s2 * zq[i];
+        }
+        double nrm = 0.0;
+        for (int i = 0; i < n; ++i) {
+          const double v = x[(size_t)i * n + m];
+          nrm += v * v;
+        }
+        nrm = sqrt(nrm);
+        const double r = nrm > 0.0 ? 1.0 / nrm : 0.0;
+        for (int i = 0; i < n; ++i) x[(size_t)i * n + m] *= r;
+      }
+      double* zm = P.Z + (size_t)m * n;
+      for (int i = 0; i < n; ++i) zm[i] = x[(size_t)i * n + m];
+    }
+  }
+  return T.sync();
+}
+
+// ---- phase 5: x = L^{-H} Q z ------------------------------------------------------------------
+template <class Team>
+__device__ bool back_transform(const Team& T, const Pencil& P, double2* smem) {
+  const int n = P.n;
+  const int lane = threadIdx.x & 31;
+  const double2* tau = vtau(P);
+  for (int c = T.wrank(); c < n; c += T.wsize()) {
+    // The column is built in this warp's shared-memory slot when the launch provided one, else in
+    // place in A's column c (A is free: the reflectors live in R, L in B).
+    double2* ac = P.A + (size_t)c * P.lda;
+    double2* vc = smem ? smem + (size_t)(threadIdx.x >> 5) * n : ac;
+    const double* zc = P.Z + (size_t)c * n;
+    for (int i = lane; i < n; i += 32) vc[i] = make_double2(zc[i], 0.0);
+    __syncwarp();
+    // V = H_0 H_1 ... H_{n-2} Z: reflector j (rows j+1..n-1, stored in column j of R) applied last-first
+    for (int j = n - 2; j >= 0; --j) {
+      const double2 tj = tau[j];
+      if (tj.x == 0.0 && tj.y == 0.0) continue;
+      const double2* __restrict__ rj = P.R + (size_t)j * n;
+      const int r0 = j + 1 + ((lane - j - 1) & 31);
+      double2 s = make_double2(0.0, 0.0);
+      for (int i = r0; i < n; i += 32) s = cadd(s, cmulc(rj[i], vc[i]));
+      s = cmul(tj, warp_sum_c(s));
+      for (int i = r0; i < n; i += 32) vc[i] = csub(vc[i], cmul(rj[i], s));
+    }
+    __syncwarp();
+    backward_subst_h(P.B, vrdiag(P), P.ldb, n, vc);
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      double2 v = vc[i];
+      if (P.real) v.y = 0.0;
+      ac[i] = v;
+    }
+    __syncwarp();
+  }
+  return T.sync();
+}
+
+template <class Team>
+__device__ void solve_pencil(const Team& T, const Pencil& P) {
+  extern __shared__ double2 dyn_smem[];
+  if (T.rank() == 0) *P.info = 0;
+  if (P.n <= 0) return;
+  if (!prepare(T, P)) return;
+  if (!cholesky(T, P)) return;
+  if (!reduce_standard(T, P)) return;
+  if (!tridiagonalise(T, P, dyn_smem)) return;
+  if (!tridiagonal_eig(T, P)) return;
+  back_transform(T, P, P.smem_cols ? dyn_smem : nullptr);
+}
+
+__global__ void __launch_bounds__(kThreads) hegv_grid_kernel(Pencil P, Ctl* ctl, unsigned long long limit_ns) {
+  GridTeam T{ctl, P.info, limit_ns};
+  solve_pencil(T, P);
+}
+
+__global__ void __launch_bounds__(kThreads) hegv_cta_kernel(const Pencil* __restrict__ items, int count) {
+  if ((int)blockIdx.x >= count) return;
+  const Pencil P = items[blockIdx.x];
+  CtaTeam T;
+  solve_pencil(T, P);
+}
+
+size_t work_doubles(int n) {
+  const size_t nn = (size_t)n * n;
+  // R (complex n^2) + Z (n^2) + wk (6 n^2) + vec (6 n + 8), each padded to 32 doubles
+  auto pad = [](size_t x) { return (x + 31) & ~(size_t)31; };
+  return pad(2 * nn) + pad(nn) + pad(6 * nn) + pad(9 * (size_t)n + 8);
+}
+
+Pencil make_pencil(double2* A, int lda, double2* B, int ldb, double* w, int* info, int n, bool real, double* ws) {
+  auto pad = [](size_t x) { return (x + 31) & ~(size_t)31; };
+  const size_t nn = (size_t)n * n;
+  Pencil P;
+  P.A = A;
+  P.B = B;
+  P.w = w;
+  P.info = info;
+  P.n = n;
+  P.lda = lda;
+  P.ldb = ldb;
+  P.real = real ? 1 : 0;
+  P.R = reinterpret_cast<double2*>(ws);
+  P.Z = ws + pad(2 * nn);
+  P.wk = P.Z + pad(nn);
+  P.vec = P.wk + pad(6 * nn);
+  P.smem_cols = 0;
+  return P;
+}
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per grid-barrier wait
+constexpr int kGridMinN = 160;  // pencils at least this large run on a cooperative grid
+
+// Dynamic shared memory: 2 n complex words for the tridiagonalisation's v and w, and, when it fits
+// in 200 KB, one column of n complex words per warp for the back-transformation.
+size_t col_smem_bytes(int n) {
+  const size_t b = (size_t)kWarps * (size_t)std::max(n, 1) * sizeof(double2);
+  return b <= 200u * 1024u ? b : 0;
+}
+size_t dyn_smem_bytes(int n) {
+  return std::max(col_smem_bytes(n), (size_t)2 * std::max(n, 1) * sizeof(double2));
+}
+constexpr int kMaxN = 6000;  // 2 n complex words must fit in shared memory
+
+}  // namespace
+
+void hegv_batched(kss_ctx ctx, const std::vector<HegvItem>& items) {
+  if (items.empty()) return;
+  cudaStream_t st = ctx->stream;
+  size_t total = 0;
+  for (const auto& it : items) total += work_doubles(std::max(it.n, 1));
+  ctx->dense_ws.ensure(total * sizeof(double));
+  std::vector<Pencil> small;  // one CTA each
+  std::vector<std::pair<Pencil, int>> large;
+  double* p = ctx->dense_ws.as<double>();
+  for (const auto& it : items) {
+    KSS_REQUIRE(it.n >= 0 && it.lda >= std::max(it.n, 1) && it.ldb >= std::max(it.n, 1), "hegv: bad sizes");
+    KSS_REQUIRE(it.n <= kMaxN, "hegv: order above " + std::to_string(kMaxN));
+    const Pencil P = make_pencil((double2*)it.A, it.lda, (double2*)it.B, it.ldb, it.w, it.info, it.n, it.real, p);
+    p += work_doubles(std::max(it.n, 1));
+    if (it.n >= kGridMinN && items.size() == 1) large.push_back({P, it.n});
+    else small.push_back(P);
+  }
+  if (!small.empty()) {
+    int nmax = 1;
+    for (const auto& P : small) nmax = std::max(nmax, P.n);
+    const size_t sm = dyn_smem_bytes(nmax);
+    for (auto& P : small) P.smem_cols = col_smem_bytes(nmax) ? 1 : 0;
+    ctx->dense_items.ensure(small.size() * sizeof(Pencil));
+    KSS_CHECK_CUDA(cudaMemcpyAsync(ctx->dense_items.p, small.data(), small.size() * sizeof(Pencil),
+                                   cudaMemcpyHostToDevice, st));
+    KSS_CHECK_CUDA(cudaFuncSetAttribute(hegv_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    static const int id = prof_register("dense_hegv_cta");
+    ProfScope ps(ctx, id);
+    hegv_cta_kernel<<<(unsigned)small.size(), kThreads, sm, st>>>(ctx->dense_items.as<Pencil>(), (int)small.size());
+    KSS_CHECK_CUDA(cudaGetLastError());
+  }
+  for (auto& lp : large) {
+    const int n = lp.second;
+    const size_t sm = dyn_smem_bytes(n);
+    KSS_CHECK_CUDA(cudaFuncSetAttribute(hegv_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0;
+    KSS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hegv_grid_kernel, kThreads, sm));
+    const int coop = std::max(1, per_sm) * std::max(1, ctx->nsm);
+    const int G = std::max(1, std::min({(n + 3) / 4, ctx->nsm > 0 ? ctx->nsm : 1, coop}));
+    ctx->dense_ctl.ensure(sizeof(Ctl));
+    KSS_CHECK_CUDA(cudaMemsetAsync(ctx->dense_ctl.p, 0, sizeof(Ctl), st));
+    Pencil P = lp.first;
+    P.smem_cols = col_smem_bytes(n) ? 1 : 0;
+    Ctl* ctl = ctx->dense_ctl.as<Ctl>();
+    unsigned long long lim = kWaitLimitNs;
+    void* args[] = {&P, &ctl, &lim};
+    static const int id = prof_register("dense_hegv_grid");
+    ProfScope ps(ctx, id);
+    KSS_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)hegv_grid_kernel, dim3(G), dim3(kThreads), args, sm, st));
+  }
+}
+
+void hegv(kss_ctx ctx, int n, void* A, int lda, void* B, int ldb, double* w, int* info, bool real) {
+  hegv_batched(ctx, {HegvItem{A, B, w, info, n, lda, ldb, real}});
+}
+
+}  // namespace kss
+
+using namespace kss;
+
+extern "C" kss_status kss_dense_hegv(kss_ctx ctx, int count, const int* n, void* const* A, const int* lda,
+                                     void* const* B, const int* ldb, double* const* w, int* info, int real) {
+  if (!ctx) return KSS_EINVAL;
+  try {
+    KSS_REQUIRE(count >= 0, "count < 0");
+    if (count == 0) {
+      ctx->err.clear();
+      return KSS_OK;
+    }
+    KSS_REQUIRE(n && A && lda && B && ldb && w && info, "NULL argument");
+    KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    std::vector<HegvItem> items(count);
+    DevBuf dinfo;
+    dinfo.alloc((size_t)count * sizeof(int));
+    for (int i = 0; i < count; ++i) {
+      KSS_REQUIRE(n[i] >= 0 && lda[i] >= std::max(1, n[i]) && ldb[i] >= std::max(1, n[i]), "bad order or leading dimension");
+      KSS_REQUIRE(n[i] == 0 || (A[i] && B[i] && w[i]), "NULL matrix");
+      items[i] = HegvItem{A[i], B[i], w[i], dinfo.as<int>() + i, n[i], lda[i], ldb[i], real != 0};
+    }
+    hegv_batched(ctx, items);
+    KSS_CHECK_CUDA(cudaMemcpyAsync(info, dinfo.p, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    KSS_CHECK_CUDA(cudaGetLastError());
+    for (int i = 0; i < count; ++i)
+      if (info[i] < 0) fail(KSS_ETIMEOUT, "kss_dense_hegv: a bounded grid-barrier wait gave up");
+    ctx->err.clear();
+    return KSS_OK;
+  } catch (const KssError& e) {
+    ctx->err = e.msg;
+    return e.st;
+  } catch (...) {
+    ctx->err = "unexpected internal error";
+    return KSS_ECUDA;
+  }
+}

@@ -22,15 +22,13 @@
 // reduction kernel adds the K-splits in a fixed order and forms the complex result.  Every
 // mbarrier wait is bounded; on time-out the kernel raises an error flag, drains its own copies,
 // frees TMEM and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cstring>
 #include <string>
 
-#include "kss_internal.h"
+#include "tc_common.cuh"
 
 namespace kss {
 
@@ -46,43 +44,14 @@ constexpr uint32_t kStageBytes = 4 * kTileBytes;  // A hi, A lo, B hi, B lo
 constexpr size_t kTcSmem = 1024 + (size_t)STAGES * kStageBytes + 256;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
+using tc::globaltimer;
+using tc::mbar_expect_tx;
+using tc::mbar_init;
+using tc::mbar_try;
+using tc::smem_u32;
+using tc::tma_load_2d;
 // Wait for the phase of the given parity to complete, at most kWaitNs; false on time-out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  while (!mbar_try(bar, parity))
-    if (globaltimer() - t0 > kWaitNs) return false;
-  return true;
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(dst), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) { return tc::mbar_wait(bar, parity, kWaitNs); }
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
@@ -343,18 +312,7 @@ __global__ void tc_combine(const float* __restrict__ P, int nsplit, int Mr, int 
   *dst = out;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
-      fail(KSS_ECUDA, "cuTensorMapEncodeTiled is not available");
-    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
-  return fn;
-}
+using tc::encode_fn;
 
 CUtensorMap make_map(const void* base, int rows, int kt) {
   CUtensorMap m;

@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.  Not part of the ABI.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -61,6 +62,15 @@ struct FftDim {
 };
 FftDim make_fft_dim(int N);  // N must be {2,3,5}-smooth, 1 < N <= 256
 
+// An operand of the FP64 tensor-core GEMMs (gemm_oz.cu) in digit form: 7 planes [rows][KT] of
+// BF16 digits (KT = 2K rounded up to 32, the (re, im) pairs interleaved along K) and one exponent
+// per row.
+struct OzOperand {
+  __nv_bfloat16* planes = nullptr;
+  int* e = nullptr;
+  int rows = 0, KT = 0;
+};
+
 // Per-k-point data.
 struct KData {
   double kred[3];
@@ -73,6 +83,8 @@ struct KData {
   DevBuf d_kin64, d_kin32;         // 0.5 |k+G|^2
   DevBuf d_beta64, d_beta32;       // projector-major [nproj][npw] complex
   DevBuf d_btc_cn, d_btc_nn;       // mixed: split-BF16 forms of beta for beta^H psi and beta C (lazy)
+  DevBuf d_oz_cn, d_oz_nn;         // FP64: digit planes of beta for beta^H psi and beta C (lazy)
+  OzOperand oz_cn, oz_nn;          //   and their descriptions
   DevBuf d_q;                      // Cartesian k+G, npw*3 doubles (setup only)
   double tmax = 0;
   double bound = 0;                // rigorous spectral upper bound of H
@@ -107,7 +119,6 @@ struct kss_ctx_s {
   bool own_stream = false;
   std::string err;
   int nsys = 0;
-  void* cusolver = nullptr;        // cusolverDnHandle_t, created lazily
   kss::DevBuf ws_local;            // FFT plane workspace
   kss::DevBuf ws_gemm;             // split-K partial sums
   kss::DevBuf ws_cprj;             // projector coefficients
@@ -123,6 +134,11 @@ struct kss_ctx_s {
   kss::DevBuf ws_gpack;            // Gamma-packed raw transforms (pairs x ld)
   kss::DevBuf ws_tune;             // scratch slab of the autotuner
   std::vector<kss_ctx_s*> aux;     // helper contexts on their own streams (concurrent Rayleigh-Ritz)
+  kss::DevBuf oz_a, oz_b, oz_part;  // FP64 tensor-core GEMMs: digit planes of A and B, partial sums
+  kss::DevBuf dense_ws, dense_ctl, dense_items;  // dense FP64 eigensolver: workspace, grid
+                                   // barrier control block, pencil table
+  void* noalloc_scratch = nullptr; // device address of the no-alloc scratch array, looked up on
+                                   // this context's first kss_apply_H_noalloc call (noalloc.cu)
 };
 
 struct kss_sys_s {
@@ -161,7 +177,6 @@ struct kss_solver_s {
   kss::DevBuf S32, Hs32, Q32;
   kss::DevBuf r64[4];  // FP64 refinement blocks (mixed precision)
   kss::DevBuf sblk, sblk64;  // overlap only: S Y, then S X (solver precision / FP64 refinement)
-  kss::DevBuf Sr, Hr;        // Gamma only: real parts of the pencil for the real eigensolve
   int lwork = 0;
   std::vector<double> evals, resid;
   int iter = 0;
@@ -323,6 +338,41 @@ void gemm_cn_c64_acc64_lower(kss_ctx ctx, int M, int K, const void* A, int lda, 
                              void* C, int ldc, const char* tag);
 // Scale row i of a complex (M x N, col-major) matrix by real d[i] * s.
 void scale_rows(kss_ctx ctx, bool fp64, int M, int N, void* C, int ldc, const void* d, double s);
+
+// ---- FP64-accurate complex GEMMs on the BF16 tensor cores (gemm_oz.cu) ----
+enum OzKind { OZ_CN_A = 0, OZ_B = 1, OZ_MMAJOR_A = 2 };
+size_t oz_operand_bytes(int rows, int K);
+OzOperand oz_operand_at(void* mem, int rows, int K);
+// Digit planes of an n-column (K-major: OZ_CN_A, OZ_B) or n-row (M-major: OZ_MMAJOR_A) complex128
+// matrix into mem (oz_operand_bytes(rows, K) bytes, rows = 2n for the A kinds, n for OZ_B).
+OzOperand oz_prepare(kss_ctx ctx, OzKind kind, int n, int K, const void* src, long long ld, void* mem);
+// C = alpha A^H B + beta C (A: K x M) and C = alpha A B + beta C (A: M x K, M contiguous),
+// complex128 column-major; a_pre: A already in digit form (static operands), else prepared here.
+void oz_gemm_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb, void* C, int ldc,
+                double ar, double ai, double br, double bi, const char* tag, const OzOperand* a_pre = nullptr);
+void oz_gemm_nn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb, void* C, int ldc,
+                double ar, double ai, double br, double bi, const char* tag, const OzOperand* a_pre = nullptr);
+// Digit forms of a k-point's FP64 projector table for beta^H psi and beta C (built on first use).
+const OzOperand& beta_oz_cn(kss_sys s, int ik);
+const OzOperand& beta_oz_nn(kss_sys s, int ik);
+
+// ---- dense FP64 generalised Hermitian eigensolver (dense64.cu) ----
+// A x = lambda B x: A, B complex128 column-major (lower triangles read); on return the leading
+// n x n block of A holds B-orthonormal eigenvectors (columns, eigenvalues ascending), w[n] the
+// eigenvalues, B its Cholesky factor, *info 0, j + 1 (B not positive definite at column j) or -1
+// (a bounded grid-barrier wait gave up);
+// real: the pencil is real symmetric (imaginary parts ignored, real eigenvectors).  All device
+// pointers; queued on ctx's stream.
+struct HegvItem {
+  void* A;
+  void* B;
+  double* w;
+  int* info;
+  int n, lda, ldb;
+  bool real;
+};
+void hegv(kss_ctx ctx, int n, void* A, int lda, void* B, int ldb, double* w, int* info, bool real);
+void hegv_batched(kss_ctx ctx, const std::vector<HegvItem>& items);
 
 // ---- solver pieces (solver.cu) ----
 void random_block(kss_ctx ctx, bool fp64, void* X, int npw, int nb, int ld, uint64_t seed,

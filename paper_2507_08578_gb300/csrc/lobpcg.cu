@@ -16,12 +16,10 @@
 #include <memory>
 #include <vector>
 
-#include <cusolverDn.h>
 
 #include "kss_internal.h"
 
 namespace kss {
-cusolverDnHandle_t solver_handle_for(kss_ctx ctx);  // solver.cu (handle bound to ctx->stream)
 }
 
 namespace kss {
@@ -171,7 +169,7 @@ struct Lobpcg {
   double tol = 1e-8;
   int max_iter = 500;
   DevBuf X, HX, W, HW, P, HP, T1, T2, T3, T4;
-  DevBuf A, B, ev, work, info, lam, ek, resid, M;
+  DevBuf A, B, ev, info, lam, ek, resid, M;
   bool have_p = false;
   int iters = 0;
   long long napply = 0;
@@ -205,22 +203,14 @@ struct Lobpcg {
       }
   }
 
-  // Generalised eigensolve of the k x k pencil (A, B); returns cuSOLVER's info (0 = success).
+  // Generalised eigensolve of the k x k pencil (A, B); returns the status word (0 = success,
+  // j + 1 = the metric is not positive definite at column j).
   int eig(int k) {
-    cusolverDnHandle_t h = solver_handle_for(ctx);
-    int lwork = 0;
-    if (cusolverDnZhegvd_bufferSize(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, k,
-                                    A.as<cuDoubleComplex>(), k, B.as<cuDoubleComplex>(), k, ev.as<double>(),
-                                    &lwork) != CUSOLVER_STATUS_SUCCESS)
-      fail(KSS_ECUDA, "cusolverDnZhegvd_bufferSize failed");
-    work.ensure((size_t)std::max(lwork, 1) * 16);
-    if (cusolverDnZhegvd(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, k,
-                         A.as<cuDoubleComplex>(), k, B.as<cuDoubleComplex>(), k, ev.as<double>(),
-                         work.as<cuDoubleComplex>(), lwork, info.as<int>()) != CUSOLVER_STATUS_SUCCESS)
-      fail(KSS_ECUDA, "cusolverDnZhegvd failed");
+    hegv(ctx, k, A.p, k, B.p, k, ev.as<double>(), info.as<int>(), false);
     int inf = 0;
     KSS_CHECK_CUDA(cudaMemcpyAsync(&inf, info.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (inf < 0) fail(KSS_ETIMEOUT, "LOBPCG Rayleigh-Ritz: a bounded grid-barrier wait gave up");
     return inf;
   }
 

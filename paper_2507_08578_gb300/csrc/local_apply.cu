@@ -777,6 +777,23 @@ const void* beta_split_nn(kss_sys s, int ik) {
   return kd.d_btc_nn.p;
 }
 
+const OzOperand& beta_oz_cn(kss_sys s, int ik) {
+  KData& kd = s->k[ik];
+  if (!kd.d_oz_cn.p) {
+    kd.d_oz_cn.alloc(oz_operand_bytes(2 * s->nproj, kd.npw));
+    kd.oz_cn = oz_prepare(s->ctx, OZ_CN_A, s->nproj, kd.npw, kd.d_beta64.p, kd.npw, kd.d_oz_cn.p);
+  }
+  return kd.oz_cn;
+}
+const OzOperand& beta_oz_nn(kss_sys s, int ik) {
+  KData& kd = s->k[ik];
+  if (!kd.d_oz_nn.p) {
+    kd.d_oz_nn.alloc(oz_operand_bytes(2 * kd.npw, s->nproj));
+    kd.oz_nn = oz_prepare(s->ctx, OZ_MMAJOR_A, kd.npw, s->nproj, kd.d_beta64.p, kd.npw, kd.d_oz_nn.p);
+  }
+  return kd.oz_nn;
+}
+
 void apply_local(kss_sys s, int ik, int nb, const void* psi, void* out, int ld, kss_precision prec) {
   if (nb == 0) return;
   if (prec == KSS_PREC_FP64)
@@ -802,8 +819,8 @@ void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, v
   if (s->nproj) {
     ctx->ws_cprj.ensure((size_t)s->nproj * nb * es);
     if (f64)
-      gemm_cn(ctx, true, s->nproj, nb, kd.npw, kd.d_beta64.p, kd.npw, psi, ld, ctx->ws_cprj.p,
-              s->nproj, 1.0, 0.0, 0.0, 0.0, "cprj");
+      oz_gemm_cn(ctx, s->nproj, nb, kd.npw, kd.d_beta64.p, kd.npw, psi, ld, ctx->ws_cprj.p, s->nproj, 1.0, 0.0,
+                 0.0, 0.0, "cprj", &beta_oz_cn(s, ik));
     else
       tc_gemm_cn_split(ctx, s->nproj, nb, kd.npw, beta_split_cn(s, ik), psi, ld, ctx->ws_cprj.p, s->nproj,
                        1.0, 0.0, 0.0, 0.0, "cprj");
@@ -817,8 +834,8 @@ void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, v
   // Nonlocal, second half: out += beta (alpha D C).
   if (s->nproj) {
     if (f64)
-      gemm_nn(ctx, true, kd.npw, nb, s->nproj, kd.d_beta64.p, kd.npw, ctx->ws_cprj.p, s->nproj, out,
-              ld, 1.0, 0.0, 1.0, 0.0, "nonlocal");
+      oz_gemm_nn(ctx, kd.npw, nb, s->nproj, kd.d_beta64.p, kd.npw, ctx->ws_cprj.p, s->nproj, out, ld, 1.0, 0.0,
+                 1.0, 0.0, "nonlocal", &beta_oz_nn(s, ik));
     else
       tc_gemm_nn_split(ctx, kd.npw, nb, s->nproj, beta_split_nn(s, ik), ctx->ws_cprj.p, s->nproj, out, ld,
                        1.0, 0.0, 1.0, 0.0, "nonlocal");

@@ -8,9 +8,6 @@
 // slab of a band chunk, the projector coefficients and the split-K partial sums of the
 // coefficient product -- lives in one file-scope device array of KSS_NOALLOC_SCRATCH_BYTES that
 // every GPU which loads the library holds until the process exits.
-#include <mutex>
-#include <vector>
-
 #include "kss_internal.h"
 
 namespace {
@@ -19,13 +16,12 @@ namespace {
 // symbol, never a device address: host code must use the address from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[KSS_NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_mu;
-std::vector<void*> g_addr;  // per device ordinal, resolved once with that device current
-
-void* scratch_address(int device) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  if ((int)g_addr.size() <= device) g_addr.resize(device + 1, nullptr);
-  if (!g_addr[device]) {
+// The address is looked up once per context, on that context's first call, with its device
+// current, and kept in the context.  A context made after the CUDA context of its device was torn
+// down and rebuilt (cudaDeviceReset, or a runtime that released the primary context) looks the
+// symbol up again, so no call ever uses an address from an earlier CUDA context.
+void* scratch_address(kss_ctx ctx) {
+  if (!ctx->noalloc_scratch) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
@@ -33,9 +29,9 @@ void* scratch_address(int device) {
       kss::fail(KSS_ECUDA, std::string("cudaGetSymbolAddress of the no-alloc scratch failed: ") +
                                cudaGetErrorString(e));
     }
-    g_addr[device] = p;
+    ctx->noalloc_scratch = p;
   }
-  return g_addr[device];
+  return ctx->noalloc_scratch;
 }
 
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
@@ -74,7 +70,7 @@ extern "C" kss_status kss_apply_H_noalloc(kss_sys sys, int ik, int nb, const voi
                            " bytes) but the static scratch holds " + std::to_string(cap) +
                            " bytes; split the band block");
     KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
-    unsigned char* base = static_cast<unsigned char*>(scratch_address(ctx->device));
+    unsigned char* base = static_cast<unsigned char*>(scratch_address(ctx));
     // Partial sums get up to half of what the slab does not need for one band.
     size_t part = 0;
     if (sys->nproj) {

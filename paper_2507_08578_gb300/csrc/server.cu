@@ -129,7 +129,9 @@ struct Server {
         auto hit = cache.find(r.key);
         for (int ik = 0; ik < nk; ++ik) {
           kss_solve_opts o = opts;
-          o.seed = opts.seed + r.id * 16 + ik;
+          // The start block depends on the request's content (its cache key), not on when it
+          // arrived: the same cell starts from the same block alone or in any mix.
+          o.seed = opts.seed + r.key * 16 + (uint64_t)ik;
           if (hit != cache.end() && hit->second.npw[ik] == r.sys->k[ik].npw) {
             o.x0 = hit->second.x[ik].p;
             o.x0_nb = r.nband;

@@ -16,8 +16,6 @@
 // promoted to FP64 for the eigensolve; a converged FP32 subspace is finished by one FP64
 // H application and an FP64 Rayleigh-Ritz (Ritz values are quadratically accurate in the
 // subspace error), whose eigenvalues and residuals are what the solver returns.
-#include <cusolverDn.h>
-
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -140,29 +138,10 @@ __global__ void copy_block(const Ci* __restrict__ in, long long ldi, Co* __restr
 
 unsigned blocks_for(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-cusolverDnHandle_t solver_handle(kss_ctx ctx) {
-  if (!ctx->cusolver) {
-    cusolverDnHandle_t h = nullptr;
-    if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) fail(KSS_ECUDA, "cusolverDnCreate failed");
-    ctx->cusolver = h;
-  }
-  cusolverDnHandle_t h = (cusolverDnHandle_t)ctx->cusolver;
-  if (cusolverDnSetStream(h, ctx->stream) != CUSOLVER_STATUS_SUCCESS)
-    fail(KSS_ECUDA, "cusolverDnSetStream failed");
-  return h;
-}
-
 }  // namespace
 
-cusolverDnHandle_t solver_handle_for(kss_ctx ctx) { return solver_handle(ctx); }
-
-void ctx_release_solver(kss_ctx ctx) {
-  if (ctx->cusolver) cusolverDnDestroy((cusolverDnHandle_t)ctx->cusolver);
-  ctx->cusolver = nullptr;
-}
-
 // Helper contexts: same device and settings, own non-blocking stream, own workspaces and
-// eigensolver handle, so that work issued on them can run beside the context stream's.
+// dense-eigensolver workspace, so that work issued on them can run beside the context stream's.
 kss_ctx aux_ctx(kss_ctx ctx, int i) {
   while ((int)ctx->aux.size() <= i) {
     std::unique_ptr<kss_ctx_s> w(new kss_ctx_s());
@@ -182,7 +161,6 @@ void aux_release(kss_ctx ctx) {
   prof_fold(ctx);
   for (kss_ctx w : ctx->aux) {
     cudaStreamSynchronize(w->stream);
-    ctx_release_solver(w);
     prof_release(w);
     cudaStreamDestroy(w->stream);
     delete w;
@@ -233,51 +211,12 @@ namespace {
 
 size_t esize(bool f64) { return f64 ? 16 : 8; }
 
-// Gamma point: the pencil of real-space-real blocks is real symmetric; a real eigensolve gives a
-// real rotation Q, which keeps the rotated bands real in real space (a complex eigensolver may
-// return each eigenvector with an arbitrary complex phase).
-void subspace_eig_real(kss_solver_s* s, kss_ctx ctx) {
-  cusolverDnHandle_t h = solver_handle(ctx);
-  const int nb = s->nb;
-  const long long nn = (long long)nb * nb;
-  s->Sr.ensure((size_t)nn * 8);
-  s->Hr.ensure((size_t)nn * 8);
-  real_part<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->S.as<double2>(), s->Sr.as<double>(), nn);
-  real_part<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hs.as<double2>(), s->Hr.as<double>(), nn);
-  int lwork = 0;
-  if (cusolverDnDsygvd_bufferSize(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nb,
-                                  s->Hr.as<double>(), nb, s->Sr.as<double>(), nb, s->W.as<double>(),
-                                  &lwork) != CUSOLVER_STATUS_SUCCESS)
-    fail(KSS_ECUDA, "cusolverDnDsygvd_bufferSize failed");
-  s->work.ensure((size_t)std::max(lwork, 1) * sizeof(double));
-  if (cusolverDnDsygvd(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nb,
-                       s->Hr.as<double>(), nb, s->Sr.as<double>(), nb, s->W.as<double>(), s->work.as<double>(),
-                       lwork, s->info.as<int>()) != CUSOLVER_STATUS_SUCCESS)
-    fail(KSS_ECUDA, "cusolverDnDsygvd failed");
-  real_to_complex<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hr.as<double>(), s->Hs.as<double2>(), nn);
-  KSS_CHECK_CUDA(cudaGetLastError());
-}
-
-// FP64 generalised eigensolve of (Hs, S) in place: Hs <- Q with Q^H S Q = I, W <- eigenvalues.
+// FP64 generalised eigensolve of (Hs, S) in place: Hs <- Q with Q^H S Q = I, W <- eigenvalues,
+// info <- status.  At Gamma the pencil of real-space-real blocks is real symmetric and is solved
+// as such: a real rotation Q keeps the rotated bands real in real space (a complex eigensolver
+// may return each eigenvector with an arbitrary complex phase).
 void subspace_eig(kss_solver_s* s, kss_ctx ctx) {
-  if (s->gamma) {
-    subspace_eig_real(s, ctx);
-    return;
-  }
-  cusolverDnHandle_t h = solver_handle(ctx);
-  const int nb = s->nb;
-  int lwork = 0;
-  if (cusolverDnZhegvd_bufferSize(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
-                                  CUBLAS_FILL_MODE_LOWER, nb, s->Hs.as<cuDoubleComplex>(), nb,
-                                  s->S.as<cuDoubleComplex>(), nb, s->W.as<double>(),
-                                  &lwork) != CUSOLVER_STATUS_SUCCESS)
-    fail(KSS_ECUDA, "cusolverDnZhegvd_bufferSize failed");
-  s->work.ensure((size_t)std::max(lwork, 1) * sizeof(cuDoubleComplex));
-  if (cusolverDnZhegvd(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nb,
-                       s->Hs.as<cuDoubleComplex>(), nb, s->S.as<cuDoubleComplex>(), nb,
-                       s->W.as<double>(), s->work.as<cuDoubleComplex>(), lwork,
-                       s->info.as<int>()) != CUSOLVER_STATUS_SUCCESS)
-    fail(KSS_ECUDA, "cusolverDnZhegvd failed");
+  hegv(ctx, s->nb, s->Hs.p, s->nb, s->S.p, s->nb, s->W.as<double>(), s->info.as<int>(), s->gamma);
 }
 
 }  // namespace
@@ -303,8 +242,9 @@ void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo
   // The generalised eigensolve reads the lower triangles of S and Hs only: the Gram products
   // compute the tiles on and below the diagonal (about half the work) and zero the rest.
   if (f64) {
-    gemm_cn_lower(ctx, true, nb, npw, Y, npw, MY, npw, s->S.p, nb, "gram");
-    gemm_cn_lower(ctx, true, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, "gram");
+    // FP64 Gram matrices on the tensor cores (FP64-accurate digit products, full matrices)
+    oz_gemm_cn(ctx, nb, nb, npw, Y, npw, MY, npw, s->S.p, nb, 1, 0, 0, 0, "gram");
+    oz_gemm_cn(ctx, nb, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, 1, 0, 0, 0, "gram");
   } else if (s->gram64) {
     gemm_cn_c64_acc64_lower(ctx, nb, npw, Y, npw, MY, npw, s->S.p, nb, "gram");
     gemm_cn_c64_acc64_lower(ctx, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, "gram");
@@ -323,8 +263,8 @@ void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo
   }
   subspace_eig(s, ctx);  // real symmetric at Gamma (real-space-real blocks)
   if (f64) {
-    gemm_nn(ctx, true, npw, nb, nb, Y, npw, s->Hs.p, nb, Xo, npw, 1, 0, 0, 0, "rotate");
-    gemm_nn(ctx, true, npw, nb, nb, HY, npw, s->Hs.p, nb, HXo, npw, 1, 0, 0, 0, "rotate");
+    oz_gemm_nn(ctx, npw, nb, nb, Y, npw, s->Hs.p, nb, Xo, npw, 1, 0, 0, 0, "rotate");
+    oz_gemm_nn(ctx, npw, nb, nb, HY, npw, s->Hs.p, nb, HXo, npw, 1, 0, 0, 0, "rotate");
   } else {
     {
       static const int idq = prof_register("convert_c128_c64");
@@ -368,6 +308,7 @@ void rr_finish(kss_solver_s* s) {
   std::memcpy(&info, s->hpin + 2 * nb, sizeof(int));
   s->evals.assign(s->hpin, s->hpin + nb);
   s->resid.assign(s->hpin + nb, s->hpin + 2 * nb);
+  if (info < 0) fail(KSS_ETIMEOUT, "subspace eigensolve: a bounded grid-barrier wait gave up");
   if (info != 0)
     fail(KSS_ENUMERIC, "subspace eigensolve failed (info = " + std::to_string(info) +
                            "): the Gram matrix is not numerically positive definite");
@@ -691,7 +632,10 @@ kss_status kss_solver_create(kss_sys sys, int ik, int nband, const kss_solve_opt
     if (o.nbuffer < 0) o.nbuffer = std::max(4, (nband + 9) / 10);
     KSS_REQUIRE(o.prec == KSS_PREC_FP64 || o.prec == KSS_PREC_MIXED, "unknown precision");
     s->f64 = o.prec == KSS_PREC_FP64;
-    s->tol = o.tol > 0 ? o.tol : (s->f64 ? 1e-8 : 1e-5);
+    // Default tolerances: 1e-8 Ha in FP64; in the mixed form twice the single-precision floor of
+    // the residual, which grows with the spectral range (about 1e-6 of the upper bound of H:
+    // complex64 carries ~7 digits of H x), and never below 1e-5 Ha.
+    s->tol = o.tol > 0 ? o.tol : (s->f64 ? 1e-8 : std::max(1e-5, 2e-6 * std::fabs(sys->k[ik].bound_f)));
     s->nb = nband + o.nbuffer;
     KSS_REQUIRE(s->nb <= s->npw, "nband + nbuffer exceeds the number of plane waves");
     s->o = o;

@@ -120,6 +120,7 @@ def signatures() -> dict:
         "kss_solver_results": ([P, P, P, P, c_int, POINTER(kss_solve_stats)], c_int),
         "kss_chebfi_solve": ([P, c_int, c_int, POINTER(kss_solve_opts), P, P, c_int, P,
                               POINTER(kss_solve_stats)], c_int),
+        "kss_dense_hegv": ([P, c_int, P, P, P, P, P, P, P, c_int], c_int),
         "kss_gemm": ([P, c_int, c_int, c_int, c_int, P, c_int, P, c_int, P, c_int, c_double,
                       c_double, c_double, c_double, c_int], c_int),
         "kss_selftest_bounded_wait": ([P, c_double], c_int),
@@ -598,6 +599,22 @@ def kss_gemm(ctx, op: int, A, B, C, alpha=1.0, beta=0.0, prec: int = KSS_PREC_FP
     _check(lib().kss_gemm(ctx, op, M, n, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc,
                           complex(alpha).real, complex(alpha).imag, complex(beta).real,
                           complex(beta).imag, prec), ctx)
+
+
+def kss_dense_hegv(ctx, As, Bs, ws, real: bool = False):
+    """FP64 generalised Hermitian eigensolves A x = lambda B x of several pencils (torch complex128
+    device tensors holding column-major matrices as (n, ld) arrays, one column per row; ws: float64
+    device tensors of n entries).  Returns the host info array."""
+    count = len(As)
+    n = (c_int * count)(*[int(a.shape[0]) for a in As])
+    lda = (c_int * count)(*[int(a.shape[1]) for a in As])
+    ldb = (c_int * count)(*[int(b.shape[1]) for b in Bs])
+    pa = (c_void_p * count)(*[a.data_ptr() for a in As])
+    pb = (c_void_p * count)(*[b.data_ptr() for b in Bs])
+    pw = (c_void_p * count)(*[w.data_ptr() for w in ws])
+    info = (c_int * count)()
+    _check(lib().kss_dense_hegv(ctx, count, n, pa, lda, pb, ldb, pw, info, 1 if real else 0), ctx)
+    return np.array(list(info), dtype=np.int32)
 
 
 def kss_selftest_bounded_wait(ctx, limit_ms: float = 50.0) -> int:

@@ -70,3 +70,20 @@ def whole_job_rate(units_done: float, seconds: float, dist=None, device: Optiona
     total = sum_over_ranks(units_done, dist, device)
     slowest = max_over_ranks(seconds, dist, device)
     return total / slowest if slowest > 0 else 0.0
+
+
+def gather_results(mine: dict, dist=None) -> dict:
+    """Union of every rank's per-unit results ({unit index: result}) on every rank (the rank's own
+    dict without a group).  The units are disjoint by construction (lpt_partition), so a unit seen
+    twice is an error."""
+    if dist is None:
+        return dict(mine)
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, dict(mine))
+    out = {}
+    for part in parts:
+        for u, r in part.items():
+            if u in out:
+                raise ValueError(f"unit {u} was processed by two ranks")
+            out[u] = r
+    return out

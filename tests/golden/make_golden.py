@@ -33,6 +33,12 @@ def main():
           ["config 1 (a=10 bohr, Ecut=10 Ha, Gamma, box 24^3, 4 atoms seed 1001, 16 projectors):",
            "the 16 lowest eigenvalues (Ha) of the dense plane-wave Hamiltonian, oracle (LAPACK evr)",
            "written by tests/golden/make_golden.py"], list(w))
+    s = W.config3()
+    w, _ = O.build_problem(s, 0).lowest(1024)
+    write("c3_lowest1024_Ha.txt",
+          ["config 3 (the config-1 cell: a=10 bohr, Ecut=10 Ha, Gamma, box 24^3, 4 atoms seed 1001):",
+           "the 1024 lowest eigenvalues (Ha) of the dense plane-wave Hamiltonian, oracle (LAPACK evr)",
+           "written by tests/golden/make_golden.py"], list(w))
     s = W.config1s()
     w, _ = O.build_problem(s, 0).lowest(16)
     write("c1s_lowest16_Ha.txt",

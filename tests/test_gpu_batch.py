@@ -104,13 +104,50 @@ def test_server_same_result_alone_and_in_mix(ctx):
         K.kss_server_stop(ctx)
     mixed = res[2]
     assert alone[0] == K.KSS_OK and mixed[0] == K.KSS_OK
-    assert np.max(np.abs(alone[1] - mixed[1])) < 1e-8
+    # the start block comes from the request's content, so alone and in the mix the target starts
+    # from the same block: the results agree far below the convergence tolerance
+    assert np.max(np.abs(alone[1] - mixed[1])) < 1e-11
     for ik in range(2):
         assert np.max(np.abs(mixed[1][ik] - oracle_levels(target, ik, target.nband))) < 1e-8
     for s, r in zip(reqs, res):
         for ik in range(len(s.kpts)):
             assert np.max(np.abs(r[1][ik] - oracle_levels(s, ik, s.nband))) < 1e-8
     assert stats["completed"] == len(reqs) and stats["p99_ms"] >= stats["p50_ms"] > 0
+
+
+def test_server_same_result_alone_and_in_mix_mixed_precision(ctx):
+    """The served form at its production precision (complex64 filter, split-BF16 projector products,
+    FP64 Rayleigh-Ritz and finish): a request gives the same eigenvalues alone and in a mix of
+    requests that arrive while it is on the GPU, within the mixed-form bar of 1e-6 Ha, and both
+    agree with the oracle to 1e-6 Ha."""
+    opts = K.make_opts(seed=3, prec=K.KSS_PREC_MIXED)
+    target = W.make_system("t", 8.5, 9.0, 6, 12, seed=31, kpts=W.SHIFTED_222[:2])
+    others = small_systems() + [W.make_system("o", 9.0, 6.0, 6, 12, seed=32)]
+    K.kss_server_start(ctx, 8 << 30, 64, opts)
+    try:
+        (alone,) = drain(ctx, [submit(ctx, target)], [(2, target.nband)])
+    finally:
+        K.kss_server_stop(ctx)
+    K.kss_server_start(ctx, 8 << 30, 64, opts)
+    try:
+        first = [submit(ctx, s) for s in others[:2]]
+        K.kss_server_pump(ctx, 20.0)  # the target arrives while the first requests are running
+        tickets = first + [submit(ctx, target)] + [submit(ctx, s) for s in others[2:]]
+        reqs = others[:2] + [target] + others[2:]
+        res = drain(ctx, tickets, [(len(s.kpts), s.nband) for s in reqs])
+    finally:
+        K.kss_server_stop(ctx)
+    mixed = res[2]
+    assert alone[0] == K.KSS_OK and mixed[0] == K.KSS_OK
+    assert np.max(np.abs(alone[1] - mixed[1])) < 1e-6
+    for ik in range(2):
+        ref = oracle_levels(target, ik, target.nband)
+        assert np.max(np.abs(mixed[1][ik] - ref)) < 1e-6
+        assert np.max(np.abs(alone[1][ik] - ref)) < 1e-6
+    for s, r in zip(reqs, res):
+        assert r[0] == K.KSS_OK
+        for ik in range(len(s.kpts)):
+            assert np.max(np.abs(r[1][ik] - oracle_levels(s, ik, s.nband))) < 1e-6
 
 
 def test_server_admission_budget_and_busy(ctx):
@@ -152,7 +189,7 @@ def test_config4_full_batch_mixed(ctx):
     """The full config-4 workload (48 systems, 217 (system, k) units, npw 1637-13286, boxes
     30^3-60^3, 16-128 bands) in one mixed-precision batch: every unit converges; units small
     enough for the oracle's dense diagonalisation (npw <= 2100, one k-point each) match it to
-    1e-6 Ha; every unit's wanted residuals are below the mixed tolerance after the FP64 finish."""
+    1e-6 Ha; every unit's wanted residuals are below its mixed tolerance after the FP64 finish."""
     systems = W.config4(48)
     handles = [setup(ctx, s) for s in systems]
     try:
@@ -162,7 +199,10 @@ def test_config4_full_batch_mixed(ctx):
         ev, rs, st, status = K.kss_solve_batch(ctx, [u[0] for u in units], [u[2] for u in units],
                                                [u[1].nband for u in units], opts)
         assert status == K.KSS_OK
-        assert max(r.max() for r in rs) < 1e-5
+        # every unit's wanted residuals within the mixed form's default tolerance, twice the
+        # single-precision floor: max(1e-5, 2e-6 x the spectral upper bound of its H)
+        for (h, s, ik), r in zip(units, rs):
+            assert r.max() <= max(1e-5, 2e-6 * K.kss_upper_bound(h, ik)), (s.name, ik, r.max())
         checked = 0
         for (h, s, ik), e in zip(units, ev):
             if ik != 0:

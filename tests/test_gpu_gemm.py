@@ -1,6 +1,6 @@
 """GPU parity of the path's complex GEMMs (kss_gemm) against numpy complex128 products.
 
-FP64 engine: within 1e-12 relative.  Tensor-core engine (complex64 data, BF16 hi/lo split,
+FP64 engine (FP64-accurate digit products on the tensor cores): within 1e-12 relative.  Tensor-core engine (complex64 data, BF16 hi/lo split,
 FP32 accumulation): the dropped lo*lo term and the BF16 rounding of the split leave a relative
 error of order 2^-16 per product, so max|dC| / max|C| < 1e-4 is the bar.
 """
@@ -66,6 +66,34 @@ def test_gemm(ctx, op, M, N, Kd, prec):
     err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
     tol = 1e-12 if prec == K.KSS_PREC_FP64 else 1e-4
     assert err < tol, err
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_gemm_fp64_badly_scaled_rows(ctx, op):
+    """FP64 products with rows and columns spanning 30 orders of magnitude (the filtered block's
+    columns and the projector table's decaying entries differ in scale): every row and column
+    of the digit form carries its own exponent, so each entry of C keeps the accuracy of the
+    49-bit digit form (about 1e-13 of its own row and column scales times sqrt(K)) instead of losing
+    it to the largest scale in the matrix."""
+    import torch
+    rng = np.random.default_rng(11 + op)
+    M, N, Kd = 150, 70, 3000
+    ra = 10.0 ** rng.uniform(-15, 15, M)
+    rb = 10.0 ** rng.uniform(-15, 15, N)
+    if op == 0:
+        A = crand(rng, (M, Kd)) * ra[:, None]
+    else:
+        A = crand(rng, (Kd, M)) * ra[None, :]
+    B = crand(rng, (N, Kd)) * rb[:, None]
+    C0 = np.zeros((N, M), dtype=np.complex128)
+    Am, Bm = A.T, B.T
+    ref = (Am.conj().T if op == 0 else Am) @ Bm
+    tA, tB, tC = (torch.from_numpy(x).cuda() for x in (A, B, C0))
+    K.kss_gemm(ctx, op, tA, tB, tC, 1.0, 0.0, K.KSS_PREC_FP64)
+    torch.cuda.synchronize()
+    got = tC.cpu().numpy().T
+    scale = np.abs(ra)[:, None] * np.abs(rb)[None, :] * np.sqrt(Kd)
+    assert np.max(np.abs(got - ref) / scale) < 1e-12
 
 
 def test_gemm_rejects_bad_sizes(ctx):

@@ -495,6 +495,8 @@ def _golden(name):
 def test_golden_values_reproduce():
     w, _ = O.build_problem(W.config1(), 0).lowest(16)
     assert np.max(np.abs(w - _golden("c1_lowest16_Ha.txt"))) < 1e-12
+    w3, _ = O.build_problem(W.config3(), 0).lowest(1024)
+    assert np.max(np.abs(w3 - _golden("c3_lowest1024_Ha.txt"))) < 1e-12
     ws, _ = O.build_problem(W.config1s(), 0).lowest(16)
     assert np.max(np.abs(ws - _golden("c1s_lowest16_Ha.txt"))) < 1e-12
     counts = _golden("sphere_counts.txt").astype(int)
