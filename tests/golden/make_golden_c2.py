@@ -6,8 +6,8 @@ the dense 34181 x 34181 Hamiltonian (18.7 GB) and asks LAPACK (zheevr through Sc
 lowest eigenvalues.  That is the plain definition of what the Chebyshev-filtered solve converges
 to; the paper prints no eigenvalues for this path, so the stored file is oracle output.
 
-Slow: about an hour on 8 x86 cores (the tridiagonal reduction streams the matrix from memory
-once per column).  Run from the repository root:
+Slow: an hour on 8 x86 cores (the dense eigensolve took 3568 s there: the tridiagonal reduction
+streams the 18.7 GB matrix from memory once per column).  Run from the repository root:
 
     python tests/golden/make_golden_c2.py [ik] [nvals]
 """
