@@ -57,9 +57,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--nk", type=int, default=0, help="use only the first nk k-points (profiling)")
-    ap.add_argument("--workload", choices=["c2", "c2s", "c3", "c4", "c5", "density", "lobpcg"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c2s", "c3", "c4", "c5", "density", "lobpcg", "gemm", "dense"],
+                    default="c2",
                     help="c2: default FP64 ChebFi iterations; c3/c4/c5: mixed-precision full solves, "
-                         "batched and served forms (auxiliary lines)")
+                         "batched and served forms; gemm: the path's complex products at the C2 "
+                         "shapes; dense: the Rayleigh-Ritz eigensolve (auxiliary lines)")
     ap.add_argument("--requests", type=int, default=60, help="c5: number of requests")
     ap.add_argument("--no-extras", action="store_true",
                     help="c2 line without the full-solve, config-3 and served measurements")
@@ -933,11 +935,107 @@ def run_c5(args):
                       "clocks": ck}), flush=True)
 
 
+def run_gemm(args):
+    """The path's complex products at their C2 shapes, through kss_gemm, in both precisions:
+    projector coefficients beta^H psi (256 x 564 x 34181), nonlocal accumulate beta C' (34181 x 564 x
+    256), Gram matrix Y^H Y (564 x 564 x 34181), rotation Y Q (34181 x 564 x 564).  Per call:
+    operand preparation (digit planes / BF16 splits) + product; conventional 8 M N K flops."""
+    import torch
+    import paper_2507_08578_gb300.kss as K
+    from paper_2507_08578_gb300 import build as B
+    B.build()
+    ctx = K.kss_create(0, torch.cuda.current_stream().cuda_stream)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    shapes = [("cprj", 0, 256, 564, 34181), ("nonlocal", 1, 34181, 564, 256),
+              ("gram", 0, 564, 564, 34181), ("rotate", 1, 34181, 564, 564)]
+    out = {}
+    stream = torch.cuda.current_stream()
+    K.kss_profile_enable(ctx, True)
+    for prec, cdt in ((K.KSS_PREC_FP64, torch.complex128), (K.KSS_PREC_MIXED, torch.complex64)):
+        for name, op, M, N, Kd in shapes:
+            A = torch.randn((M, Kd) if op == 0 else (Kd, M), dtype=cdt, device="cuda", generator=g)
+            Bm = torch.randn((N, Kd), dtype=cdt, device="cuda", generator=g)
+            C = torch.zeros((N, M), dtype=cdt, device="cuda")
+            for _ in range(args.warmup):
+                K.kss_gemm(ctx, op, A, Bm, C, 1.0, 0.0, prec)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                K.kss_gemm(ctx, op, A, Bm, C, 1.0, 0.0, prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            key = ("fp64_" if prec == K.KSS_PREC_FP64 else "mixed_") + name
+            out[key] = {"M": M, "N": N, "K": Kd, "op": "A^H B" if op == 0 else "A B", "ms": ms,
+                        "tflops_conventional": 8.0 * M * N * Kd / ms / 1e9}
+            del A, Bm, C
+    prof = K.profile_table(ctx)
+    K.kss_profile_enable(ctx, False)
+    K.kss_destroy(ctx)
+    pk, pnote = bf16_peak()
+    for k, v in out.items():
+        mult = OZ_EXECUTED_PER_CONVENTIONAL if k.startswith("fp64") else 3.0
+        v["executed_bf16_tflops"] = v["tflops_conventional"] * mult
+        v["frac_of_bf16_peak"] = v["executed_bf16_tflops"] / pk
+    print(json.dumps({"metric": "complex GEMM TFLOP/s (conventional 8MNK)", "value": out["fp64_cprj"]["tflops_conventional"],
+                      "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": True, "dtype": "f64 (7-digit BF16 products) / c64 (split BF16)",
+                      "data": "synthetic", "config": {"workload": "C2 shapes of the path's complex products"},
+                      "peak": pk, "peak_note": pnote, "shapes": out,
+                      "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in
+                                  sorted(prof.items(), key=lambda kv: -kv[1][1])}}), flush=True)
+
+
+def run_dense(args):
+    """The Rayleigh-Ritz eigensolve (kss_dense_hegv) at the orders of the solves: one 564 x 564
+    pencil (C2: 512 + 52 bands), one 1127 x 1127 pencil (C3) and a batch of 217 pencils of orders
+    20-141 (the C4 units); random Hermitian A and Hermitian positive definite B."""
+    import numpy as np
+    import torch
+    import paper_2507_08578_gb300.kss as K
+    from paper_2507_08578_gb300 import build as B
+    B.build()
+    ctx = K.kss_create(0, torch.cuda.current_stream().cuda_stream)
+    g = torch.Generator(device="cuda").manual_seed(9)
+
+    def pencil(n):
+        a = torch.randn((n, n), dtype=torch.complex128, device="cuda", generator=g)
+        m = torch.randn((n, n), dtype=torch.complex128, device="cuda", generator=g)
+        A = (a + a.conj().T) / 2
+        Bp = m @ m.conj().T / n + torch.eye(n, dtype=torch.complex128, device="cuda")
+        return A.T.contiguous(), Bp.T.contiguous()
+
+    out = {}
+    rng = np.random.default_rng(5)
+    cases = [("c2_564", [564]), ("c3_1127", [1127]), ("c4_batch_217", list(rng.integers(20, 142, size=217)))]
+    for name, ns in cases:
+        src = [pencil(int(n)) for n in ns]
+        times = []
+        for it in range(args.warmup + args.steps):
+            As = [a.clone() for a, _ in src]
+            Bs = [b.clone() for _, b in src]
+            ws = [torch.zeros(int(n), dtype=torch.float64, device="cuda") for n in ns]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = K.kss_dense_hegv(ctx, As, Bs, ws)
+            times.append(time.perf_counter() - t0)
+            assert not np.any(info)
+        ms = 1000.0 * float(np.median(times[args.warmup:]))
+        out[name] = {"pencils": len(ns), "max_order": int(max(ns)), "ms": ms}
+    K.kss_destroy(ctx)
+    print(json.dumps({"metric": "dense FP64 generalised eigensolve time", "value": out["c2_564"]["ms"],
+                      "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "Rayleigh-Ritz pencils of the C2, C3 and C4 solves"},
+                      "cases": out}), flush=True)
+
+
 def main():
     args = parse()
     if args.workload not in ("c2", "c2s") and args.impl == "ours":
         {"c3": run_c3, "c4": run_c4, "c5": run_c5, "density": run_density,
-         "lobpcg": run_lobpcg}[args.workload](args)
+         "lobpcg": run_lobpcg, "gemm": run_gemm, "dense": run_dense}[args.workload](args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

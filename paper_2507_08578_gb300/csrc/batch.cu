@@ -630,7 +630,9 @@ void BatchEngine::rr_batched(const std::vector<kss_solver_s*>& us, const std::ve
   binfo.ensure((size_t)U * sizeof(int));
   double2* S = Sb.as<double2>();
   double2* H = Hb.as<double2>();
-  // Gram and projected-H matrices of every unit, into the leading nb x nb blocks
+  // Gram and projected-H matrices of every unit, into the leading nb x nb blocks.  The batch's
+  // units are small (16-141 bands): one SIMT product per unit beats the tensor-core digit products,
+  // whose operand preparation and 128 x 64 tiles do not pay at these sizes (measured).
   for (int u = 0; u < U; ++u) {
     kss_solver_s* s = us[u];
     const int nb = s->nb, npw = s->npw;

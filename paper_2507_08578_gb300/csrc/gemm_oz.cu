@@ -43,19 +43,26 @@ namespace kss {
 
 namespace {
 
-constexpr int S = 7;                                 // digits per FP64 value
 constexpr int TM = 128;                              // real A rows per tile (UMMA M)
 constexpr int TN = 64;                               // B rows (complex columns) per tile (UMMA N)
 constexpr int TK = 32;                               // BF16 per k-block: one 64-byte swizzle row
-constexpr int STAGES = 2;
+constexpr int NG = 7;                                // digit-pair groups g = p + q <= 6 (TMEM: 7 x 64 columns)
 constexpr uint32_t ATILE = TM * TK * 2;              // 8 KB
 constexpr uint32_t BTILE = TN * TK * 2;              // 4 KB
-constexpr uint32_t STAGE = S * (ATILE + BTILE);      // 84 KB
 constexpr int CHUNK = 12;                            // k-blocks per exact chunk (384 BF16 of K)
 constexpr int kOzThreads = 192;
-constexpr size_t kOzSmem = 1024 + (size_t)STAGES * STAGE + 256;
 constexpr uint32_t kTmemCols = 512;                  // 7 groups x 64 columns, rounded up
 constexpr unsigned long long kWaitNs = 2000000000ull;
+
+// Digits per value: 7 for FP64 data (49 bits), 4 for FP32 data (28 bits: every FP32 value of a
+// row whose scale is within 2^4 of it is represented exactly).  The ring holds SA + SB digit tiles
+// per stage: 2 stages of 84 KB for 7 + 7, 4 stages of 48 KB for 4 + 4.
+template <int SA, int SB>
+struct OzCfg {
+  static constexpr uint32_t STAGE = SA * ATILE + SB * BTILE;
+  static constexpr int STAGES = (SA + SB) > 8 ? 2 : 4;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256;
+};
 
 using tc::mbar_arrive;
 using tc::mbar_expect_tx;
@@ -92,11 +99,14 @@ __device__ __forceinline__ double pow2(int e) {  // 2^e for |e| < 1000, exactly
   return __longlong_as_double((long long)(1023 + e) << 52);
 }
 
+template <int SA, int SB, typename CT>
 __global__ void __launch_bounds__(kOzThreads, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int rowsA,
                int rowsB, int Mr, int Nr, int tnn, int kb_per_split, int kb_total, const int* __restrict__ ea,
                const int* __restrict__ eb, int* __restrict__ err, double* __restrict__ part,
-               double2* __restrict__ C, long long ldc, double ar, double ai, double br, double bi) {
+               CT* __restrict__ C, long long ldc, double ar, double ai, double br, double bi) {
+  constexpr uint32_t STAGE = OzCfg<SA, SB>::STAGE;
+  constexpr int STAGES = OzCfg<SA, SB>::STAGES;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE);
@@ -147,8 +157,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       mbar_expect_tx(smem_u32(&full[s]), STAGE);
       const int x = (kb0 + kb) * TK;
       const uint32_t st = smem_u32(base + s * STAGE), fb = smem_u32(&full[s]);
-      for (int p = 0; p < S; ++p) tma_load_2d(st + p * ATILE, &tmA, x, p * rowsA + tm * TM, fb);
-      for (int q = 0; q < S; ++q) tma_load_2d(st + S * ATILE + q * BTILE, &tmB, x, q * rowsB + tn * TN, fb);
+      for (int p = 0; p < SA; ++p) tma_load_2d(st + p * ATILE, &tmA, x, p * rowsA + tm * TM, fb);
+      for (int q = 0; q < SB; ++q) tma_load_2d(st + SA * ATILE + q * BTILE, &tmB, x, q * rowsB + tn * TN, fb);
       ++issued;
     }
     // Drain: every issued copy has landed before the CTA can leave (bounded).
@@ -170,17 +180,20 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(base + s * STAGE), b0 = a0 + S * ATILE;
+      const uint32_t a0 = smem_u32(base + s * STAGE), b0 = a0 + SA * ATILE;
 #pragma unroll
       for (int k16 = 0; k16 < TK / 16; ++k16) {
 #pragma unroll
-        for (int p = 0; p < S; ++p) {
+        for (int p = 0; p < SA; ++p) {
           const uint64_t da = desc64(a0 + p * ATILE + 32 * k16);
 #pragma unroll
-          for (int q = 0; q < S - p; ++q) {
+          for (int q = 0; q < SB && p + q < NG; ++q) {
             const uint64_t db = desc64(b0 + q * BTILE + 32 * k16);
-            // the first product of every group in a chunk overwrites (p = 0 reaches every group)
-            const uint32_t acc = (kc == 0 && k16 == 0 && p == 0) ? 0u : 1u;
+            // the first product of every group in a chunk overwrites: in issue order that is the
+            // pair with the smallest p, p = max(0, g - (SB - 1))
+            const int g = p + q;
+            const int pfirst = g > SB - 1 ? g - (SB - 1) : 0;
+            const uint32_t acc = (kc == 0 && k16 == 0 && p == pfirst) ? 0u : 1u;
             const uint32_t dcol = tmem + (uint32_t)((p + q) * TN);
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -215,7 +228,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       for (int c0 = 0; c0 < TN; c0 += 16) {
         float hi[16], lo[16];
 #pragma unroll
-        for (int g = 0; g < S; ++g) {
+        for (int g = 0; g < NG; ++g) {
           uint32_t r[16];
           const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * TN + c0);
           asm volatile(
@@ -267,13 +280,16 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           const double v = (row < Mr && col < Nr) ? acc[j] * pow2(er + eb[col]) : 0.0;
           const double w = __shfl_down_sync(0xffffffffu, v, 1);
           if (!(lane & 1) && row < Mr && col < Nr) {
-            double2* dst = C + (size_t)col * ldc + (row >> 1);
-            double2 o = make_double2(ar * v - ai * w, ar * w + ai * v);
+            CT* dst = C + (size_t)col * ldc + (row >> 1);
+            double ox = ar * v - ai * w, oy = ar * w + ai * v;
             if (br != 0.0 || bi != 0.0) {
-              const double2 q = *dst;
-              o.x += br * q.x - bi * q.y;
-              o.y += br * q.y + bi * q.x;
+              const CT q = *dst;
+              ox += br * (double)q.x - bi * (double)q.y;
+              oy += br * (double)q.y + bi * (double)q.x;
             }
+            CT o;
+            o.x = ox;
+            o.y = oy;
             *dst = o;
           }
         }
@@ -287,25 +303,43 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 }
 
 // ---- operand preparation (digit planes) --------------------------------------------------------
-constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
+// IEEE layout of the source precision.
+template <typename R> struct Bits;
+template <> struct Bits<double> {
+  using U = unsigned long long;
+  static constexpr int kFrac = 52, kBias = 1023, kExpMask = 0x7FF;
+  static constexpr U kAbs = 0x7FFFFFFFFFFFFFFFull;
+  __device__ static U of(double v) { return (U)__double_as_longlong(v); }
+};
+template <> struct Bits<float> {
+  using U = unsigned int;
+  static constexpr int kFrac = 23, kBias = 127, kExpMask = 0xFF;
+  static constexpr U kAbs = 0x7FFFFFFFu;
+  __device__ static U of(float v) { return (U)__float_as_uint(v); }
+};
 
 // Exponent e with every |x| of the row below 2^e, from the largest magnitude's bit pattern
-// (for non-negative doubles the integer order of the bit patterns is the numeric order).
+// (for non-negative IEEE values the integer order of the bit patterns is the numeric order).
+template <typename R>
 __device__ __forceinline__ int row_exponent(unsigned long long maxbits) {
-  const int ev = (int)(maxbits >> 52);
-  return ev ? ev - 1022 : 0;
+  const int ev = (int)(maxbits >> Bits<R>::kFrac);
+  return ev ? ev - Bits<R>::kBias + 1 : 0;
 }
 
-// The 7 balanced base-128 digits of v 2^{49 - e} (|v| < 2^e), most significant first, taken
-// from the bit pattern with integer operations only (bits below 2^{e-49} truncated).
-__device__ __forceinline__ void digits(double v, int e, float d[S]) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-  const int ev = (int)((bits >> 52) & 0x7FF);
+// The S balanced base-128 digits of v 2^{7S - e} (|v| < 2^e), most significant first, taken from
+// the bit pattern with integer operations only (bits below 2^{e - 7S} truncated).
+template <int S, typename R>
+__device__ __forceinline__ void digits(R v, int e, float d[S]) {
+  const auto bits = Bits<R>::of(v);
+  const int ev = (int)((bits >> Bits<R>::kFrac) & Bits<R>::kExpMask);
   long long N = 0;
   if (ev != 0) {
-    const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = 1026 + e - ev;  // v 2^{49-e} = mant 2^{ev - 1075 + 49 - e}; sh >= 4 as |v| < 2^e
-    N = sh >= 64 ? 0 : (long long)(mant >> sh);
+    const unsigned long long mant =
+        (unsigned long long)(bits & ((((decltype(bits))1) << Bits<R>::kFrac) - 1)) | (1ull << Bits<R>::kFrac);
+    // v 2^{7S-e} = mant 2^{ev - bias - frac + 7S - e}; the shift is at most 7S - frac - 1 + ... so
+    // that the result stays below 2^{7S}
+    const int sh = ev - Bits<R>::kBias - Bits<R>::kFrac + 7 * S - e;
+    N = sh >= 0 ? (long long)(mant << sh) : (sh <= -64 ? 0 : (long long)(mant >> -sh));
   }
   int u[S];
 #pragma unroll
@@ -316,7 +350,7 @@ __device__ __forceinline__ void digits(double v, int e, float d[S]) {
       u[p] -= 128;
       u[p - 1] += 1;
     }
-  const bool neg = (bits >> 63) != 0;
+  const bool neg = (bits >> (8 * sizeof(bits) - 1)) != 0;
 #pragma unroll
   for (int p = 0; p < S; ++p) d[p] = (float)(neg ? -u[p] : u[p]);
 }
@@ -330,23 +364,29 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
   return v;
 }
 
+template <typename CS> struct Real;
+template <> struct Real<double2> { using T = double; };
+template <> struct Real<float2> { using T = float; };
+
 // K-major complex source (column c: K values at src + c ld) -> digit planes [S][rows][KT] of
 // interleaved (re, im) pairs, one warp per column.  pair = 1 (the A operand of A^H B): row 2c holds
 // (re, im) and row 2c + 1 (-im, re), both with the column's exponent.
-__global__ void oz_prep_k(const double2* __restrict__ src, long long ld, int K, int ncols, int KT,
+template <int S, typename CS>
+__global__ void oz_prep_k(const CS* __restrict__ src, long long ld, int K, int ncols, int KT,
                           __nv_bfloat16* __restrict__ dst, int rows, int* __restrict__ erow, int pair) {
+  using R = typename Real<CS>::T;
   const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (c >= ncols) return;
-  const double2* x = src + (size_t)c * ld;
+  const CS* x = src + (size_t)c * ld;
   unsigned long long mx = 0;
   for (int k = lane; k < K; k += 32) {
-    const double2 v = x[k];
-    const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & kAbs;
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & kAbs;
+    const CS v = x[k];
+    const unsigned long long a = Bits<R>::of(v.x) & Bits<R>::kAbs;
+    const unsigned long long b = Bits<R>::of(v.y) & Bits<R>::kAbs;
     mx = a > mx ? a : mx;
     mx = b > mx ? b : mx;
   }
-  const int e = row_exponent(warp_max_u64(mx));
+  const int e = row_exponent<R>(warp_max_u64(mx));
   const int r0 = pair ? 2 * c : c;
   if (lane == 0) {
     erow[r0] = e;
@@ -354,15 +394,15 @@ __global__ void oz_prep_k(const double2* __restrict__ src, long long ld, int K, 
   }
   const size_t plane = (size_t)rows * KT;
   for (int k = lane; k < KT / 2; k += 32) {
-    double re = 0.0, im = 0.0;
+    R re = 0, im = 0;
     if (k < K) {
-      const double2 v = x[k];
+      const CS v = x[k];
       re = v.x;
       im = v.y;
     }
     float dr[S], di[S];
-    digits(re, e, dr);
-    digits(im, e, di);
+    digits<S>(re, e, dr);
+    digits<S>(im, e, di);
 #pragma unroll
     for (int p = 0; p < S; ++p) {
       __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(dst + p * plane + (size_t)r0 * KT);
@@ -376,42 +416,48 @@ __global__ void oz_prep_k(const double2* __restrict__ src, long long ld, int K, 
 }
 
 // Exponents of the rows of an M-major complex A (element (i, k) at src[k ld + i]), one thread per i.
-__global__ void oz_exp_m(const double2* __restrict__ src, long long ld, int M, int K, int* __restrict__ erow) {
+template <typename CS>
+__global__ void oz_exp_m(const CS* __restrict__ src, long long ld, int M, int K, int* __restrict__ erow) {
+  using R = typename Real<CS>::T;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   unsigned long long mx = 0;
   for (int k = 0; k < K; ++k) {
-    const double2 v = src[(size_t)k * ld + i];
-    const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & kAbs;
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & kAbs;
+    const CS v = src[(size_t)k * ld + i];
+    const unsigned long long a = Bits<R>::of(v.x) & Bits<R>::kAbs;
+    const unsigned long long b = Bits<R>::of(v.y) & Bits<R>::kAbs;
     mx = a > mx ? a : mx;
     mx = b > mx ? b : mx;
   }
-  const int e = row_exponent(mx);
+  const int e = row_exponent<R>(mx);
   erow[2 * i] = e;
   erow[2 * i + 1] = e;
 }
 
 // M-major complex A -> digit planes of the A operand of C = A B: row 2i holds (re, -im) pairs,
 // row 2i + 1 (im, re); a 32 x 32 transpose through shared memory.
-__global__ void oz_prep_m(const double2* __restrict__ src, long long ld, int M, int K, int KT,
+template <int S, typename CS>
+__global__ void oz_prep_m(const CS* __restrict__ src, long long ld, int M, int K, int KT,
                           __nv_bfloat16* __restrict__ dst, int rows, const int* __restrict__ erow) {
-  __shared__ double2 t[32][33];
+  __shared__ CS t[32][33];
   const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int k = k0 + r, i = i0 + threadIdx.x;
-    t[r][threadIdx.x] = (k < K && i < M) ? src[(size_t)k * ld + i] : make_double2(0.0, 0.0);
+    CS z;
+    z.x = 0;
+    z.y = 0;
+    t[r][threadIdx.x] = (k < K && i < M) ? src[(size_t)k * ld + i] : z;
   }
   __syncthreads();
   const size_t plane = (size_t)rows * KT;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int i = i0 + r, k = k0 + threadIdx.x;
     if (i >= M || k >= KT / 2) continue;
-    const double2 v = t[threadIdx.x][r];
+    const CS v = t[threadIdx.x][r];
     const int e = erow[2 * i];
     float dr[S], di[S];
-    digits(v.x, e, dr);
-    digits(v.y, e, di);
+    digits<S>(v.x, e, dr);
+    digits<S>(v.y, e, di);
 #pragma unroll
     for (int p = 0; p < S; ++p) {
       __nv_bfloat162* ra = reinterpret_cast<__nv_bfloat162*>(dst + p * plane + (size_t)(2 * i) * KT);
@@ -424,8 +470,9 @@ __global__ void oz_prep_m(const double2* __restrict__ src, long long ld, int M, 
 
 // C (complex, col-major ldc) = alpha * D + beta * C from the FP64 K-split partials (col-major
 // Mr x Nr each, Mr = 2M): re = D(2i, j), im = D(2i + 1, j), splits added in a fixed order.
+template <typename CT>
 __global__ void oz_combine(const double* __restrict__ P, int nsplit, int Mr, int Nr, int M, int N,
-                           double2* __restrict__ C, long long ldc, double ar, double ai, double br, double bi) {
+                           CT* __restrict__ C, long long ldc, double ar, double ai, double br, double bi) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)M * N) return;
   const int i = (int)(idx % M), j = (int)(idx / M);
@@ -436,14 +483,17 @@ __global__ void oz_combine(const double* __restrict__ P, int nsplit, int Mr, int
     sr += P[z * stride + o];
     si += P[z * stride + o + 1];
   }
-  double2 out = make_double2(ar * sr - ai * si, ar * si + ai * sr);
-  double2* dst = C + (size_t)j * ldc + i;
+  double ox = ar * sr - ai * si, oy = ar * si + ai * sr;
+  CT* dst = C + (size_t)j * ldc + i;
   if (br != 0.0 || bi != 0.0) {
-    const double2 q = *dst;
-    out.x += br * q.x - bi * q.y;
-    out.y += br * q.y + bi * q.x;
+    const CT q = *dst;
+    ox += br * (double)q.x - bi * (double)q.y;
+    oy += br * (double)q.y + bi * (double)q.x;
   }
-  *dst = out;
+  CT r;
+  r.x = ox;
+  r.y = oy;
+  *dst = r;
 }
 
 CUtensorMap make_map(const void* base, long long rows, int kt, int box_rows) {
@@ -471,17 +521,18 @@ int* err_flag(kss_ctx ctx) {
 }
 
 // C (M x N complex) = alpha * A_op (2M real rows) * B_op (N rows)^T + beta * C.
-void run_oz(kss_ctx ctx, const OzOperand& a, const OzOperand& b, int M, int N, double2* C, int ldc, double ar,
-            double ai, double br, double bi, const char* tag) {
+template <int SA, int SB, typename CT>
+void launch_oz(kss_ctx ctx, const OzOperand& a, const OzOperand& b, int M, int N, CT* C, int ldc, double ar,
+               double ai, double br, double bi, const char* tag) {
+  using Cfg = OzCfg<SA, SB>;
   const int Mr = 2 * M, Nr = N;
-  KSS_REQUIRE(a.KT == b.KT && a.rows == Mr && b.rows == Nr, "FP64 tensor-core GEMM: operand shapes differ");
   const int tmn = (Mr + TM - 1) / TM, tnn = (Nr + TN - 1) / TN;
   const int kb_total = a.KT / TK;
   const long long tiles = (long long)tmn * tnn;
-  if (tiles > 0x7fffffffLL) fail(KSS_EINVAL, "FP64 tensor-core GEMM: too many output tiles");
-  // K-split plan: one CTA per SM (the ring takes 169 KB of shared memory); with fewer tiles than
-  // SMs, split K so that the grid fills the SMs in one wave, keeping at least two exact chunks per
-  // CTA.
+  if (tiles > 0x7fffffffLL) fail(KSS_EINVAL, "digit-product GEMM: too many output tiles");
+  // K-split plan: one CTA per SM (the ring takes 169 / 193 KB of shared memory); with fewer tiles
+  // than SMs, split K so that the grid fills the SMs in one wave, keeping at least two exact
+  // chunks per CTA.
   int nsm = ctx->nsm;
   if (!nsm) {
     KSS_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -493,13 +544,14 @@ void run_oz(kss_ctx ctx, const OzOperand& a, const OzOperand& b, int M, int N, d
   kps = ((kps + CHUNK - 1) / CHUNK) * CHUNK;
   splits = (kb_total + kps - 1) / kps;
   if (splits > 1) ctx->oz_part.ensure((size_t)splits * Mr * Nr * sizeof(double));
-  const CUtensorMap ma = make_map(a.planes, (long long)S * a.rows, a.KT, TM);
-  const CUtensorMap mb = make_map(b.planes, (long long)S * b.rows, b.KT, TN);
-  KSS_CHECK_CUDA(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem));
+  const CUtensorMap ma = make_map(a.planes, (long long)SA * a.rows, a.KT, TM);
+  const CUtensorMap mb = make_map(b.planes, (long long)SB * b.rows, b.KT, TN);
+  auto kern = oz_gemm_kernel<SA, SB, CT>;
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
   const bool fused = splits == 1;
   {
-    ProfScope ps(ctx, prof_register((std::string("tc_gemm_oz7:") + tag).c_str()));
-    oz_gemm_kernel<<<dim3((unsigned)tiles, splits, 1), kOzThreads, kOzSmem, ctx->stream>>>(
+    ProfScope ps(ctx, prof_register((std::string(SA == 7 ? "tc_gemm_oz7:" : "tc_gemm_oz4:") + tag).c_str()));
+    kern<<<dim3((unsigned)tiles, splits, 1), kOzThreads, Cfg::SMEM, ctx->stream>>>(
         ma, mb, a.rows, b.rows, Mr, Nr, tnn, kps, kb_total, a.e, b.e, err_flag(ctx),
         fused ? nullptr : ctx->oz_part.as<double>(), C, ldc, ar, ai, br, bi);
   }
@@ -507,19 +559,35 @@ void run_oz(kss_ctx ctx, const OzOperand& a, const OzOperand& b, int M, int N, d
   if (fused) return;
   const long long mn = (long long)M * N;
   ProfScope ps(ctx, prof_register((std::string("oz_combine:") + tag).c_str()));
-  oz_combine<<<(unsigned)((mn + 255) / 256), 256, 0, ctx->stream>>>(ctx->oz_part.as<double>(), splits, Mr, Nr, M, N,
-                                                                    C, ldc, ar, ai, br, bi);
+  oz_combine<CT><<<(unsigned)((mn + 255) / 256), 256, 0, ctx->stream>>>(ctx->oz_part.as<double>(), splits, Mr, Nr, M,
+                                                                        N, C, ldc, ar, ai, br, bi);
   KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+void run_oz(kss_ctx ctx, const OzOperand& a, const OzOperand& b, int M, int N, void* C, bool c128out, int ldc,
+            double ar, double ai, double br, double bi, const char* tag) {
+  KSS_REQUIRE(a.KT == b.KT && a.rows == 2 * M && b.rows == N, "digit-product GEMM: operand shapes differ");
+  if (a.S == 7 && b.S == 7 && c128out)
+    launch_oz<7, 7>(ctx, a, b, M, N, (double2*)C, ldc, ar, ai, br, bi, tag);
+  else if (a.S == 7 && b.S == 7)
+    launch_oz<7, 7>(ctx, a, b, M, N, (float2*)C, ldc, ar, ai, br, bi, tag);
+  else if (a.S == 4 && b.S == 4 && c128out)
+    launch_oz<4, 4>(ctx, a, b, M, N, (double2*)C, ldc, ar, ai, br, bi, tag);
+  else
+    fail(KSS_EINVAL, "digit-product GEMM: unsupported digit counts");
 }
 
 }  // namespace
 
-size_t oz_operand_bytes(int rows, int K) { return (size_t)S * rows * ktile(K) * 2 + (size_t)rows * sizeof(int) + 256; }
+size_t oz_operand_bytes(int rows, int K, int S) {
+  return (size_t)S * rows * ktile(K) * 2 + (size_t)rows * sizeof(int) + 256;
+}
 
-OzOperand oz_operand_at(void* mem, int rows, int K) {
+OzOperand oz_operand_at(void* mem, int rows, int K, int S) {
   OzOperand o;
   o.rows = rows;
   o.KT = ktile(K);
+  o.S = S;
   o.planes = static_cast<__nv_bfloat16*>(mem);
   const size_t pb = ((size_t)S * rows * o.KT * 2 + 255) & ~(size_t)255;
   o.e = reinterpret_cast<int*>(static_cast<unsigned char*>(mem) + pb);
@@ -527,55 +595,73 @@ OzOperand oz_operand_at(void* mem, int rows, int K) {
 }
 
 // Digit planes of an operand: cn_a (A of A^H B, K-major, 2 rows per column), kmajor (B, K-major, one
-// row per column), mmajor (A of A B, M-major, 2 rows per row).
-OzOperand oz_prepare(kss_ctx ctx, OzKind kind, int n, int K, const void* src, long long ld, void* mem) {
-  const int rows = kind == OZ_B ? n : 2 * n;
-  OzOperand o = oz_operand_at(mem, rows, K);
-  ProfScope ps(ctx, prof_register("oz_prep"));
+// row per column), mmajor (A of A B, M-major, 2 rows per row); S = 7 or 4 digits per value from
+// complex128 (f64src) or complex64 data.
+template <int S, typename CS>
+void prepare_as(kss_ctx ctx, OzKind kind, int n, int K, const CS* src, long long ld, const OzOperand& o) {
   if (kind == OZ_MMAJOR_A) {
-    oz_exp_m<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>((const double2*)src, ld, n, K, o.e);
     dim3 g((n + 31) / 32, (o.KT / 2 + 31) / 32);
-    oz_prep_m<<<g, dim3(32, 8), 0, ctx->stream>>>((const double2*)src, ld, n, K, o.KT, o.planes, rows, o.e);
+    oz_exp_m<CS><<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(src, ld, n, K, o.e);
+    oz_prep_m<S, CS><<<g, dim3(32, 8), 0, ctx->stream>>>(src, ld, n, K, o.KT, o.planes, o.rows, o.e);
   } else {
-    oz_prep_k<<<(unsigned)((n + 7) / 8), 256, 0, ctx->stream>>>((const double2*)src, ld, K, n, o.KT, o.planes,
-                                                                 rows, o.e, kind == OZ_CN_A ? 1 : 0);
+    oz_prep_k<S, CS><<<(unsigned)((n + 7) / 8), 256, 0, ctx->stream>>>(src, ld, K, n, o.KT, o.planes, o.rows, o.e,
+                                                                      kind == OZ_CN_A ? 1 : 0);
   }
+}
+
+OzOperand oz_prepare(kss_ctx ctx, OzKind kind, int n, int K, const void* src, long long ld, void* mem, bool f64src,
+                     int S) {
+  if (S <= 0) S = f64src ? 7 : 4;
+  KSS_REQUIRE(S == 7 || (S == 4 && !f64src), "digit-product GEMM: 7 digits (complex128 or complex64 data) or 4 "
+                                             "(complex64 data)");
+  const int rows = kind == OZ_B ? n : 2 * n;
+  OzOperand o = oz_operand_at(mem, rows, K, S);
+  ProfScope ps(ctx, prof_register("oz_prep"));
+  if (f64src) prepare_as<7, double2>(ctx, kind, n, K, (const double2*)src, ld, o);
+  else if (S == 7) prepare_as<7, float2>(ctx, kind, n, K, (const float2*)src, ld, o);
+  else prepare_as<4, float2>(ctx, kind, n, K, (const float2*)src, ld, o);
   KSS_CHECK_CUDA(cudaGetLastError());
   return o;
 }
 
-// C (M x N) = alpha A^H B + beta C, complex128; A: K x M (lda), B: K x N (ldb).
+// C (M x N) = alpha A^H B + beta C; A: K x M (lda), B: K x N (ldb).  f64in: complex128 operands,
+// else complex64; f64out: complex128 C, else complex64; digits: per value (0: 7 for complex128, 4
+// for complex64 data).
 void oz_gemm_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb, void* C, int ldc,
-                double ar, double ai, double br, double bi, const char* tag, const OzOperand* a_pre) {
+                double ar, double ai, double br, double bi, const char* tag, const OzOperand* a_pre, bool f64in,
+                bool f64out, int digits) {
   if (M <= 0 || N <= 0) return;
-  KSS_REQUIRE(K > 0, "FP64 tensor-core GEMM: K = 0");
+  KSS_REQUIRE(K > 0, "digit-product GEMM: K = 0");
+  const int S = digits > 0 ? digits : (f64in ? 7 : 4);
   OzOperand a;
   if (a_pre) {
     a = *a_pre;
   } else {
-    ctx->oz_a.ensure(oz_operand_bytes(2 * M, K));
-    a = oz_prepare(ctx, OZ_CN_A, M, K, A, lda, ctx->oz_a.p);
+    ctx->oz_a.ensure(oz_operand_bytes(2 * M, K, S));
+    a = oz_prepare(ctx, OZ_CN_A, M, K, A, lda, ctx->oz_a.p, f64in, S);
   }
-  ctx->oz_b.ensure(oz_operand_bytes(N, K));
-  const OzOperand b = oz_prepare(ctx, OZ_B, N, K, B, ldb, ctx->oz_b.p);
-  run_oz(ctx, a, b, M, N, (double2*)C, ldc, ar, ai, br, bi, tag);
+  ctx->oz_b.ensure(oz_operand_bytes(N, K, S));
+  const OzOperand b = oz_prepare(ctx, OZ_B, N, K, B, ldb, ctx->oz_b.p, f64in, S);
+  run_oz(ctx, a, b, M, N, C, f64out, ldc, ar, ai, br, bi, tag);
 }
 
-// C (M x N) = alpha A B + beta C, complex128; A: M x K (lda, M contiguous), B: K x N (ldb).
+// C (M x N) = alpha A B + beta C; A: M x K (lda, M contiguous), B: K x N (ldb).
 void oz_gemm_nn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb, void* C, int ldc,
-                double ar, double ai, double br, double bi, const char* tag, const OzOperand* a_pre) {
+                double ar, double ai, double br, double bi, const char* tag, const OzOperand* a_pre, bool f64in,
+                bool f64out, int digits) {
   if (M <= 0 || N <= 0) return;
-  KSS_REQUIRE(K > 0, "FP64 tensor-core GEMM: K = 0");
+  KSS_REQUIRE(K > 0, "digit-product GEMM: K = 0");
+  const int S = digits > 0 ? digits : (f64in ? 7 : 4);
   OzOperand a;
   if (a_pre) {
     a = *a_pre;
   } else {
-    ctx->oz_a.ensure(oz_operand_bytes(2 * M, K));
-    a = oz_prepare(ctx, OZ_MMAJOR_A, M, K, A, lda, ctx->oz_a.p);
+    ctx->oz_a.ensure(oz_operand_bytes(2 * M, K, S));
+    a = oz_prepare(ctx, OZ_MMAJOR_A, M, K, A, lda, ctx->oz_a.p, f64in, S);
   }
-  ctx->oz_b.ensure(oz_operand_bytes(N, K));
-  const OzOperand b = oz_prepare(ctx, OZ_B, N, K, B, ldb, ctx->oz_b.p);
-  run_oz(ctx, a, b, M, N, (double2*)C, ldc, ar, ai, br, bi, tag);
+  ctx->oz_b.ensure(oz_operand_bytes(N, K, S));
+  const OzOperand b = oz_prepare(ctx, OZ_B, N, K, B, ldb, ctx->oz_b.p, f64in, S);
+  run_oz(ctx, a, b, M, N, C, f64out, ldc, ar, ai, br, bi, tag);
 }
 
 }  // namespace kss

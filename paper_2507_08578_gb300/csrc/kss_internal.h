@@ -69,6 +69,7 @@ struct OzOperand {
   __nv_bfloat16* planes = nullptr;
   int* e = nullptr;
   int rows = 0, KT = 0;
+  int S = 7;                       // digits per value: 7 (complex128 data) or 4 (complex64 data)
 };
 
 // Per-k-point data.
@@ -341,17 +342,25 @@ void scale_rows(kss_ctx ctx, bool fp64, int M, int N, void* C, int ldc, const vo
 
 // ---- FP64-accurate complex GEMMs on the BF16 tensor cores (gemm_oz.cu) ----
 enum OzKind { OZ_CN_A = 0, OZ_B = 1, OZ_MMAJOR_A = 2 };
-size_t oz_operand_bytes(int rows, int K);
-OzOperand oz_operand_at(void* mem, int rows, int K);
-// Digit planes of an n-column (K-major: OZ_CN_A, OZ_B) or n-row (M-major: OZ_MMAJOR_A) complex128
-// matrix into mem (oz_operand_bytes(rows, K) bytes, rows = 2n for the A kinds, n for OZ_B).
-OzOperand oz_prepare(kss_ctx ctx, OzKind kind, int n, int K, const void* src, long long ld, void* mem);
+size_t oz_operand_bytes(int rows, int K, int S = 7);
+OzOperand oz_operand_at(void* mem, int rows, int K, int S = 7);
+// Digit planes of an n-column (K-major: OZ_CN_A, OZ_B) or n-row (M-major: OZ_MMAJOR_A) complex
+// matrix into mem (oz_operand_bytes(rows, K, S) bytes, rows = 2n for the A kinds, n for OZ_B):
+// S digits per value (0: 7 from complex128 data, 4 from complex64 data; 7 from complex64 data
+// keeps 49 bits below each row's largest entry, for rows whose entries span many scales).
+OzOperand oz_prepare(kss_ctx ctx, OzKind kind, int n, int K, const void* src, long long ld, void* mem,
+                     bool f64src = true, int S = 0);
 // C = alpha A^H B + beta C (A: K x M) and C = alpha A B + beta C (A: M x K, M contiguous),
-// complex128 column-major; a_pre: A already in digit form (static operands), else prepared here.
+// column-major; f64in: complex128 operands (FP64-accurate products), else complex64 (with 4
+// digits: exact products of the FP32 values to 28 bits of the row scales; with 7: to 49 bits);
+// f64out: complex128 C, else complex64.  a_pre: A already in digit form (static operands), else
+// prepared here.
 void oz_gemm_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb, void* C, int ldc,
-                double ar, double ai, double br, double bi, const char* tag, const OzOperand* a_pre = nullptr);
+                double ar, double ai, double br, double bi, const char* tag, const OzOperand* a_pre = nullptr,
+                bool f64in = true, bool f64out = true, int digits = 0);
 void oz_gemm_nn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb, void* C, int ldc,
-                double ar, double ai, double br, double bi, const char* tag, const OzOperand* a_pre = nullptr);
+                double ar, double ai, double br, double bi, const char* tag, const OzOperand* a_pre = nullptr,
+                bool f64in = true, bool f64out = true, int digits = 0);
 // Digit forms of a k-point's FP64 projector table for beta^H psi and beta C (built on first use).
 const OzOperand& beta_oz_cn(kss_sys s, int ik);
 const OzOperand& beta_oz_nn(kss_sys s, int ik);

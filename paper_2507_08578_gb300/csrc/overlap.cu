@@ -39,14 +39,15 @@ __global__ void cheb_combine(const C* __restrict__ f, long long ldf, const C* __
   }
 }
 
-// Projector products at the precision of the path: FP64 SIMT, or split-BF16 tensor cores for
-// complex64 (the same kernels as the H application).
+// Projector products at the precision of the path: FP64-accurate digit products or split-BF16
+// products on the tensor cores (the same kernels as the H application).
 void proj_cn(kss_ctx ctx, bool f64, kss_sys s, int ik, int nb, const void* psi, int ld, void* out,
              const char* tag) {
   const KData& kd = s->k[ik];
   const int nproj = s->nproj;
   if (f64)
-    gemm_cn(ctx, true, nproj, nb, kd.npw, kd.d_beta64.p, kd.npw, psi, ld, out, nproj, 1, 0, 0, 0, tag);
+    oz_gemm_cn(ctx, nproj, nb, kd.npw, kd.d_beta64.p, kd.npw, psi, ld, out, nproj, 1, 0, 0, 0, tag,
+               &beta_oz_cn(s, ik));
   else
     tc_gemm_cn_split(ctx, nproj, nb, kd.npw, beta_split_cn(s, ik), psi, ld, out, nproj, 1, 0, 0, 0, tag);
 }
@@ -55,7 +56,8 @@ void proj_nn(kss_ctx ctx, bool f64, kss_sys s, int ik, int nb, const void* coef,
   const KData& kd = s->k[ik];
   const int nproj = s->nproj;
   if (f64)
-    gemm_nn(ctx, true, kd.npw, nb, nproj, kd.d_beta64.p, kd.npw, coef, nproj, out, ld, 1, 0, 1, 0, tag);
+    oz_gemm_nn(ctx, kd.npw, nb, nproj, kd.d_beta64.p, kd.npw, coef, nproj, out, ld, 1, 0, 1, 0, tag,
+               &beta_oz_nn(s, ik));
   else
     tc_gemm_nn_split(ctx, kd.npw, nb, nproj, beta_split_nn(s, ik), coef, nproj, out, ld, 1, 0, 1, 0, tag);
 }

@@ -249,17 +249,10 @@ void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo
     gemm_cn_c64_acc64_lower(ctx, nb, npw, Y, npw, MY, npw, s->S.p, nb, "gram");
     gemm_cn_c64_acc64_lower(ctx, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, "gram");
   } else {
-    gemm_cn_lower(ctx, false, nb, npw, Y, npw, MY, npw, s->S32.p, nb, "gram");
-    gemm_cn_lower(ctx, false, nb, npw, Y, npw, HY, npw, s->Hs32.p, nb, "gram");
-    static const int idc = prof_register("convert_c64_c128");
-    {
-      ProfScope ps(ctx, idc);
-      c64_to_c128<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->S32.as<float2>(), s->S.as<double2>(), nn);
-    }
-    {
-      ProfScope ps(ctx, idc);
-      c64_to_c128<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hs32.as<float2>(), s->Hs.as<double2>(), nn);
-    }
+    // Gram matrices of the complex64 block on the tensor cores: exact products of the FP32 values
+    // (4 digits each), summed exactly per chunk and in FP64 across chunks, delivered in FP64
+    oz_gemm_cn(ctx, nb, nb, npw, Y, npw, MY, npw, s->S.p, nb, 1, 0, 0, 0, "gram", nullptr, false, true);
+    oz_gemm_cn(ctx, nb, nb, npw, Y, npw, HY, npw, s->Hs.p, nb, 1, 0, 0, 0, "gram", nullptr, false, true);
   }
   subspace_eig(s, ctx);  // real symmetric at Gamma (real-space-real blocks)
   if (f64) {
@@ -271,6 +264,8 @@ void rr_issue(kss_solver_s* s, bool f64, const void* Y, const void* HY, void* Xo
       ProfScope ps(ctx, idq);
       c128_to_c64<<<blocks_for(nn), 256, 0, ctx->stream>>>(s->Hs.as<double2>(), s->Q32.as<float2>(), nn);
     }
+    // complex64 rotations on the FP32 pipe: the filtered block's columns span up to 2^12 in scale,
+    // which digit products would have to cover with 7 digits per value (measured slower here)
     gemm_nn(ctx, false, npw, nb, nb, Y, npw, s->Q32.p, nb, Xo, npw, 1, 0, 0, 0, "rotate");
     gemm_nn(ctx, false, npw, nb, nb, HY, npw, s->Q32.p, nb, HXo, npw, 1, 0, 0, 0, "rotate");
   }

@@ -707,3 +707,19 @@ def test_sheared_cell_pins_catch_planted_mistakes():
 def replace_basis_q(b, q):
     from dataclasses import replace
     return replace(b, q=q)
+
+
+def test_stored_c2_spectrum_against_lanczos_on_the_naive_apply():
+    """The stored config-2 spectrum (LAPACK on the dense 34181^2 matrix, an hour of CPU) against an
+    independent route through the oracle: Lanczos (ARPACK) on the naive-DFT H-apply, which never
+    forms the matrix, for the lowest two eigenvalues."""
+    import scipy.sparse.linalg as sla
+    p = O.build_problem(W.config2(), 0)
+    n = p.basis.npw
+    op = sla.LinearOperator((n, n), matvec=lambda x: p.apply(np.asarray(x).reshape(1, -1))[0],
+                            dtype=np.complex128)
+    w = np.sort(sla.eigsh(op, k=2, which="SA", tol=1e-11, return_eigenvectors=False,
+                          v0=np.ones(n, complex)))
+    ref = _golden("c2_k0_lowest576_Ha.txt")
+    assert ref.size == 576 and np.all(np.diff(ref) >= 0)
+    assert np.max(np.abs(w - ref[:2])) < 1e-10
