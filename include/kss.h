@@ -551,8 +551,33 @@ kss_status kss_autotune_get(int i, kss_tune_entry* out);
  * the per-warp form at use.  KSS_EINVAL for inconsistent fields (A * B != N, threads not in
  * {0, 256, 384}, W3 outside [1, N], unknown precision). */
 kss_status kss_autotune_put(const kss_tune_entry* e);
-/* Empty the table (later configurations are tuned again).  Cannot fail (returns KSS_OK). */
+/* Empty the tables of the FFT schedules and of the GEMM K-splits below (later configurations are
+ * tuned again).  Cannot fail (returns KSS_OK). */
 kss_status kss_autotune_clear(void);
+
+/* The tensor-core GEMMs (the projector products, Eq. ham-nl of §5.2; the Gram and rotation
+ * products of Rayleigh-Ritz, §5.1) split K across CTAs when a product has few output tiles.  With
+ * tuning on (kss_autotune_set), the first product of each (kind, shape) times the candidate splits
+ * (no split, the closed-form plan, and the splits that fill the SMs in one, two or three waves) on
+ * the device and keeps the fastest for the process; every split computes the same product (the
+ * K ranges are added in a fixed order).  kind: 0 split-BF16 complex64 products, 1 FP64 digit
+ * products, 2 the same with a complex64 result, 3 4-digit products of complex64 data.  Mr: real
+ * rows of the product (twice the complex rows), Nr: columns, kblocks: K in k-blocks of the kernel. */
+typedef struct {
+  int device, kind, Mr, Nr, kblocks;
+  int splits;  /* chosen K-split (CTAs along K) */
+  double ms;   /* time of one tuning run of the chosen split (0 for a pinned entry) */
+  int ncand;   /* candidates timed (0 for a pinned entry) */
+} kss_gemm_tune_entry;
+
+/* Number of GEMM K-split table entries (process-wide).  Errors: KSS_EINVAL (n == NULL). */
+kss_status kss_autotune_gemm_count(int* n);
+/* Entry i (insertion order); KSS_EINVAL past the end or for a NULL out. */
+kss_status kss_autotune_gemm_get(int i, kss_gemm_tune_entry* out);
+/* Insert or replace the entry for (device, kind, Mr, Nr, kblocks): pins a split (clamped at use to
+ * the kernel's minimum k-blocks per CTA).  ms and ncand are ignored.  Errors: KSS_EINVAL (NULL,
+ * kind outside 0..3, sizes < 1, splits outside [1, kblocks]). */
+kss_status kss_autotune_gemm_put(const kss_gemm_tune_entry* e);
 
 #ifdef __cplusplus
 }

@@ -37,6 +37,7 @@
 #include <cstring>
 #include <string>
 
+#include "gemm_tune.h"
 #include "tc_common.cuh"
 
 namespace kss {
@@ -538,30 +539,42 @@ void launch_oz(kss_ctx ctx, const OzOperand& a, const OzOperand& b, int M, int N
     KSS_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     ctx->nsm = nsm = std::max(nsm, 1);
   }
-  int splits = 1;
-  if (tiles < nsm) splits = (int)std::max(1LL, std::min<long long>(nsm / tiles, kb_total / (2 * CHUNK)));
-  int kps = (kb_total + splits - 1) / splits;
-  kps = ((kps + CHUNK - 1) / CHUNK) * CHUNK;
-  splits = (kb_total + kps - 1) / kps;
-  if (splits > 1) ctx->oz_part.ensure((size_t)splits * Mr * Nr * sizeof(double));
+  // closed-form plan; the autotuner times it against other splits at first use of the shape
+  int plan = 1;
+  if (tiles < nsm) plan = (int)std::max(1LL, std::min<long long>(nsm / tiles, kb_total / (2 * CHUNK)));
   const CUtensorMap ma = make_map(a.planes, (long long)SA * a.rows, a.KT, TM);
   const CUtensorMap mb = make_map(b.planes, (long long)SB * b.rows, b.KT, TN);
   auto kern = oz_gemm_kernel<SA, SB, CT>;
   KSS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
-  const bool fused = splits == 1;
-  {
-    ProfScope ps(ctx, prof_register((std::string(SA == 7 ? "tc_gemm_oz7:" : "tc_gemm_oz4:") + tag).c_str()));
-    kern<<<dim3((unsigned)tiles, splits, 1), kOzThreads, Cfg::SMEM, ctx->stream>>>(
-        ma, mb, a.rows, b.rows, Mr, Nr, tnn, kps, kb_total, a.e, b.e, err_flag(ctx),
-        fused ? nullptr : ctx->oz_part.as<double>(), C, ldc, ar, ai, br, bi);
-  }
-  KSS_CHECK_CUDA(cudaGetLastError());
-  if (fused) return;
-  const long long mn = (long long)M * N;
-  ProfScope ps(ctx, prof_register((std::string("oz_combine:") + tag).c_str()));
-  oz_combine<CT><<<(unsigned)((mn + 255) / 256), 256, 0, ctx->stream>>>(ctx->oz_part.as<double>(), splits, Mr, Nr, M,
-                                                                        N, C, ldc, ar, ai, br, bi);
-  KSS_CHECK_CUDA(cudaGetLastError());
+  const std::string name = std::string(SA == 7 ? "tc_gemm_oz7:" : "tc_gemm_oz4:") + tag;
+  const std::string cname = std::string("oz_combine:") + tag;
+  // One product with `splits` K-splits into C (ldc, alpha, beta).
+  auto launch = [&](int splits, CT* Cd, int ldd, double br_, double bi_, bool prof) {
+    int kps = (kb_total + splits - 1) / splits;
+    kps = ((kps + CHUNK - 1) / CHUNK) * CHUNK;
+    splits = (kb_total + kps - 1) / kps;
+    if (splits > 1) ctx->oz_part.ensure((size_t)splits * Mr * Nr * sizeof(double));
+    const bool fused = splits == 1;
+    {
+      ProfScope ps(ctx, prof ? prof_register(name.c_str()) : prof_register("gemm_tuning"));
+      kern<<<dim3((unsigned)tiles, splits, 1), kOzThreads, Cfg::SMEM, ctx->stream>>>(
+          ma, mb, a.rows, b.rows, Mr, Nr, tnn, kps, kb_total, a.e, b.e, err_flag(ctx),
+          fused ? nullptr : ctx->oz_part.as<double>(), Cd, ldd, ar, ai, br_, bi_);
+    }
+    KSS_CHECK_CUDA(cudaGetLastError());
+    if (fused) return;
+    const long long mn = (long long)M * N;
+    ProfScope ps(ctx, prof ? prof_register(cname.c_str()) : prof_register("gemm_tuning"));
+    oz_combine<CT><<<(unsigned)((mn + 255) / 256), 256, 0, ctx->stream>>>(ctx->oz_part.as<double>(), splits, Mr,
+                                                                          Nr, M, N, Cd, ldd, ar, ai, br_, bi_);
+    KSS_CHECK_CUDA(cudaGetLastError());
+  };
+  const int kind = SA == 4 ? GT_OZ44 : (sizeof(CT) == sizeof(double2) ? GT_OZ77 : GT_OZ77_C64OUT);
+  const int splits = tuned_split(ctx, kind, Mr, Nr, kb_total, tiles, 2 * CHUNK, plan, [&](int sp) {
+    ctx->tune_c.ensure((size_t)M * N * sizeof(CT));
+    launch(sp, ctx->tune_c.as<CT>(), M, 0.0, 0.0, false);
+  });
+  launch(splits, C, ldc, br, bi, true);
 }
 
 void run_oz(kss_ctx ctx, const OzOperand& a, const OzOperand& b, int M, int N, void* C, bool c128out, int ldc,

@@ -28,6 +28,7 @@
 #include <cstring>
 #include <string>
 
+#include "gemm_tune.h"
 #include "tc_common.cuh"
 
 namespace kss {
@@ -353,13 +354,11 @@ void run_tc(kss_ctx ctx, const __nv_bfloat16* Atc, const __nv_bfloat16* Btc, int
   // CTA.  Every extra split costs a CTA's fixed work (TMEM allocation, pipeline fill, epilogue)
   // and one more set of FP32 partial sums written and read back, so more than one wave of split
   // CTAs does not pay.
+  // This is the closed-form plan; the autotuner times it against other splits at first use of the
+  // shape.
   const int nsm = sms(ctx);
-  int splits = 1;
-  if (tiles < nsm) splits = (int)std::max(1LL, std::min<long long>(nsm / tiles, kb_total / 8));
-  int kps = (kb_total + splits - 1) / splits;
-  splits = (kb_total + kps - 1) / kps;
-  const size_t pbytes = (size_t)splits * Mr * Nr * sizeof(float);
-  if (splits > 1) ctx->tc_part.ensure(pbytes);
+  int plan = 1;
+  if (tiles < nsm) plan = (int)std::max(1LL, std::min<long long>(nsm / tiles, kb_total / 8));
   if (!ctx->tc_err.p) {
     ctx->tc_err.alloc(sizeof(int));
     KSS_CHECK_CUDA(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), ctx->stream));
@@ -368,24 +367,32 @@ void run_tc(kss_ctx ctx, const __nv_bfloat16* Atc, const __nv_bfloat16* Btc, int
   // per device (the attribute belongs to the current device): set at every launch, as the
   // other kernels of the path do
   KSS_CHECK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
-  const bool fused = splits == 1;
-  {
-    ProfScope ps(ctx, prof_register((std::string("tc_gemm_bf16x3:") + tag).c_str()));
-    tc_gemm_kernel<<<dim3((unsigned)tiles, splits, 1), kTcThreads, kTcSmem, ctx->stream>>>(
-        ma, mb, ctx->tc_part.as<float>(), Mr, Nr, tnn, kps, kb_total, Kp, ctx->tc_err.as<int>(),
-        fused ? C : nullptr, ldc, (float)ar, (float)ai, (float)br, (float)bi);
-  }
-  if (fused) {
+  const std::string name = std::string("tc_gemm_bf16x3:") + tag, cname = std::string("tc_combine:") + tag;
+  // One product with `splits` K-splits into Cd (ldd, alpha, beta).
+  auto launch = [&](int splits, float2* Cd, int ldd, double br_, double bi_, bool prof) {
+    const int kps = (kb_total + splits - 1) / splits;
+    splits = (kb_total + kps - 1) / kps;
+    if (splits > 1) ctx->tc_part.ensure((size_t)splits * Mr * Nr * sizeof(float));
+    const bool fused = splits == 1;
+    {
+      ProfScope ps(ctx, prof_register(prof ? name.c_str() : "gemm_tuning"));
+      tc_gemm_kernel<<<dim3((unsigned)tiles, splits, 1), kTcThreads, kTcSmem, ctx->stream>>>(
+          ma, mb, ctx->tc_part.as<float>(), Mr, Nr, tnn, kps, kb_total, Kp, ctx->tc_err.as<int>(),
+          fused ? Cd : nullptr, ldd, (float)ar, (float)ai, (float)br_, (float)bi_);
+    }
     KSS_CHECK_CUDA(cudaGetLastError());
-    return;
-  }
-  const long long mn = (long long)M * N;
-  {
-    ProfScope ps(ctx, prof_register((std::string("tc_combine:") + tag).c_str()));
+    if (fused) return;
+    const long long mn = (long long)M * N;
+    ProfScope ps(ctx, prof_register(prof ? cname.c_str() : "gemm_tuning"));
     tc_combine<<<(unsigned)((mn + 255) / 256), 256, 0, ctx->stream>>>(
-        ctx->tc_part.as<float>(), splits, Mr, Nr, M, N, C, ldc, (float)ar, (float)ai, (float)br, (float)bi);
-  }
-  KSS_CHECK_CUDA(cudaGetLastError());
+        ctx->tc_part.as<float>(), splits, Mr, Nr, M, N, Cd, ldd, (float)ar, (float)ai, (float)br_, (float)bi_);
+    KSS_CHECK_CUDA(cudaGetLastError());
+  };
+  const int splits = tuned_split(ctx, GT_BF16X3, Mr, Nr, kb_total, tiles, 8, plan, [&](int sp) {
+    ctx->tune_c.ensure((size_t)M * N * sizeof(float2));
+    launch(sp, ctx->tune_c.as<float2>(), M, 0.0, 0.0, false);
+  });
+  launch(splits, C, ldc, br, bi, true);
 }
 
 int kpad(int K) { return ((2 * K + TK - 1) / TK) * TK; }

@@ -136,6 +136,7 @@ struct kss_ctx_s {
   kss::DevBuf ws_tune;             // scratch slab of the autotuner
   std::vector<kss_ctx_s*> aux;     // helper contexts on their own streams (concurrent Rayleigh-Ritz)
   kss::DevBuf oz_a, oz_b, oz_part;  // FP64 tensor-core GEMMs: digit planes of A and B, partial sums
+  kss::DevBuf tune_c;              // scratch output of the GEMM K-split tuner
   kss::DevBuf dense_ws, dense_ctl, dense_items;  // dense FP64 eigensolver: workspace, grid
                                    // barrier control block, pencil table
   void* noalloc_scratch = nullptr; // device address of the no-alloc scratch array, looked up on

@@ -9,6 +9,7 @@
 #include <mutex>
 #include <tuple>
 
+#include "gemm_tune.h"
 #include "local_wide.h"
 #include "tune.h"
 
@@ -171,9 +172,12 @@ kss_status kss_autotune_put(const kss_tune_entry* e) {
 }
 
 kss_status kss_autotune_clear(void) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  g_table.clear();
-  g_order.clear();
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_table.clear();
+    g_order.clear();
+  }
+  gemm_tune_clear();
   return KSS_OK;
 }
 

@@ -121,6 +121,9 @@ def signatures() -> dict:
         "kss_chebfi_solve": ([P, c_int, c_int, POINTER(kss_solve_opts), P, P, c_int, P,
                               POINTER(kss_solve_stats)], c_int),
         "kss_dense_hegv": ([P, c_int, P, P, P, P, P, P, P, c_int], c_int),
+        "kss_autotune_gemm_count": ([P], c_int),
+        "kss_autotune_gemm_get": ([c_int, P], c_int),
+        "kss_autotune_gemm_put": ([P], c_int),
         "kss_gemm": ([P, c_int, c_int, c_int, c_int, P, c_int, P, c_int, P, c_int, c_double,
                       c_double, c_double, c_double, c_int], c_int),
         "kss_selftest_bounded_wait": ([P, c_double], c_int),
@@ -615,6 +618,29 @@ def kss_dense_hegv(ctx, As, Bs, ws, real: bool = False):
     info = (c_int * count)()
     _check(lib().kss_dense_hegv(ctx, count, n, pa, lda, pb, ldb, pw, info, 1 if real else 0), ctx)
     return np.array(list(info), dtype=np.int32)
+
+
+class kss_gemm_tune_entry(ctypes.Structure):
+    _fields_ = [("device", c_int), ("kind", c_int), ("Mr", c_int), ("Nr", c_int), ("kblocks", c_int),
+                ("splits", c_int), ("ms", c_double), ("ncand", c_int)]
+
+
+def kss_autotune_gemm_table():
+    """The GEMM K-split table (process-wide) as a list of dicts."""
+    n = c_int()
+    _check(lib().kss_autotune_gemm_count(byref(n)))
+    out = []
+    for i in range(n.value):
+        e = kss_gemm_tune_entry()
+        _check(lib().kss_autotune_gemm_get(i, byref(e)))
+        out.append({f: getattr(e, f) for f, _ in e._fields_})
+    return out
+
+
+def kss_autotune_gemm_put(device: int, kind: int, Mr: int, Nr: int, kblocks: int, splits: int):
+    """Pin the K-split of a (kind, shape) GEMM configuration."""
+    e = kss_gemm_tune_entry(device, kind, Mr, Nr, kblocks, splits, 0.0, 0)
+    _check(lib().kss_autotune_gemm_put(byref(e)))
 
 
 def kss_selftest_bounded_wait(ctx, limit_ms: float = 50.0) -> int:

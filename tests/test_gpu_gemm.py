@@ -133,3 +133,39 @@ def test_bounded_wait_gives_up_and_context_stays_usable(ctx):
     ref = A.conj() @ B.T
     got = tC.cpu().numpy().T
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-4
+
+
+@pytest.mark.parametrize("prec", [K.KSS_PREC_FP64, K.KSS_PREC_MIXED], ids=["fp64", "mixed"])
+def test_gemm_split_autotuner_and_every_candidate(ctx, prec):
+    """The K-split of the tensor-core products is tuned at first use of a shape (table entry with
+    several candidates timed), and every split computes the same product: each one pinned in turn
+    gives the numpy product within the precision's bar."""
+    import torch
+    K.kss_autotune_clear()
+    rng = np.random.default_rng(21)
+    M, N, Kd = 150, 130, 9000                 # few output tiles, long K: the split matters
+    A = crand(rng, (M, Kd))
+    B = crand(rng, (N, Kd))
+    ref = A.conj() @ B.T                     # (M x N)
+    cdt = torch.complex128 if prec == K.KSS_PREC_FP64 else torch.complex64
+    tol = 1e-12 if prec == K.KSS_PREC_FP64 else 1e-4
+    tA, tB = (torch.from_numpy(x).to(cdt).cuda() for x in (A, B))
+
+    def run():
+        tC = torch.zeros((N, M), dtype=cdt, device="cuda")
+        K.kss_gemm(ctx, 0, tA, tB, tC, 1.0, 0.0, prec)
+        torch.cuda.synchronize()
+        got = tC.cpu().numpy().T
+        return np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+
+    assert run() < tol
+    kind = 1 if prec == K.KSS_PREC_FP64 else 0
+    entries = [e for e in K.kss_autotune_gemm_table() if e["kind"] == kind and e["Nr"] == N]
+    assert len(entries) == 1 and entries[0]["ncand"] >= 2 and entries[0]["ms"] > 0
+    e = entries[0]
+    assert e["Mr"] == 2 * M
+    for sp in sorted({1, 2, 3, 5, e["splits"], max(1, e["kblocks"] // 24)}):
+        K.kss_autotune_gemm_put(e["device"], kind, e["Mr"], e["Nr"], e["kblocks"], sp)
+        assert run() < tol, sp
+    K.kss_autotune_clear()
+    assert K.kss_autotune_gemm_table() == []
