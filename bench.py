@@ -989,8 +989,9 @@ def run_gemm(args):
 
 def run_dense(args):
     """The Rayleigh-Ritz eigensolve (kss_dense_hegv) at the orders of the solves: one 564 x 564
-    pencil (C2: 512 + 52 bands), one 1127 x 1127 pencil (C3) and a batch of 217 pencils of orders
-    20-141 (the C4 units); random Hermitian A and Hermitian positive definite B."""
+    pencil (C2: 512 + 52 bands), one 1127 x 1127 pencil (C3: real symmetric at the Gamma point,
+    and the same order complex for comparison) and a batch of 217 pencils of orders 20-141 (the
+    C4 units); random Hermitian A and Hermitian positive definite B."""
     import numpy as np
     import torch
     import paper_2507_08578_gb300.kss as K
@@ -999,18 +1000,20 @@ def run_dense(args):
     ctx = K.kss_create(0, torch.cuda.current_stream().cuda_stream)
     g = torch.Generator(device="cuda").manual_seed(9)
 
-    def pencil(n):
-        a = torch.randn((n, n), dtype=torch.complex128, device="cuda", generator=g)
-        m = torch.randn((n, n), dtype=torch.complex128, device="cuda", generator=g)
+    def pencil(n, real):
+        dt = torch.float64 if real else torch.complex128
+        a = torch.randn((n, n), dtype=dt, device="cuda", generator=g).to(torch.complex128)
+        m = torch.randn((n, n), dtype=dt, device="cuda", generator=g).to(torch.complex128)
         A = (a + a.conj().T) / 2
         Bp = m @ m.conj().T / n + torch.eye(n, dtype=torch.complex128, device="cuda")
         return A.T.contiguous(), Bp.T.contiguous()
 
     out = {}
     rng = np.random.default_rng(5)
-    cases = [("c2_564", [564]), ("c3_1127", [1127]), ("c4_batch_217", list(rng.integers(20, 142, size=217)))]
-    for name, ns in cases:
-        src = [pencil(int(n)) for n in ns]
+    cases = [("c2_564", [564], False), ("c3_1127_real", [1127], True), ("c3_1127_complex", [1127], False),
+             ("c4_batch_217", list(rng.integers(20, 142, size=217)), False)]
+    for name, ns, real in cases:
+        src = [pencil(int(n), real) for n in ns]
         times = []
         for it in range(args.warmup + args.steps):
             As = [a.clone() for a, _ in src]
@@ -1018,11 +1021,11 @@ def run_dense(args):
             ws = [torch.zeros(int(n), dtype=torch.float64, device="cuda") for n in ns]
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            info = K.kss_dense_hegv(ctx, As, Bs, ws)
+            info = K.kss_dense_hegv(ctx, As, Bs, ws, real=real)
             times.append(time.perf_counter() - t0)
             assert not np.any(info)
         ms = 1000.0 * float(np.median(times[args.warmup:]))
-        out[name] = {"pencils": len(ns), "max_order": int(max(ns)), "ms": ms}
+        out[name] = {"pencils": len(ns), "max_order": int(max(ns)), "real": real, "ms": ms}
     K.kss_destroy(ctx)
     print(json.dumps({"metric": "dense FP64 generalised eigensolve time", "value": out["c2_564"]["ms"],
                       "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,

@@ -285,10 +285,11 @@ kss_status kss_gemm(kss_ctx ctx, int op, int M, int N, int K, const void* A, int
  * the leading n x n block of A[i] holds the eigenvectors (columns, B-orthonormal, eigenvalues
  * ascending), w[i] (DEVICE, n[i] doubles) the eigenvalues, B[i] its Cholesky factor (lower) and
  * info[i] (HOST) 0, or j + 1 when B[i] is not positive definite at column j (outputs then
- * undefined).  real != 0: the pencils are real symmetric (imaginary parts ignored; real
- * eigenvectors).  Hand-written kernels (Cholesky, reduction to standard form, Householder
- * tridiagonalisation, bisection and inverse iteration, back-transformation): one CTA per pencil,
- * or a cooperative grid for a single pencil of order >= 160.  Synchronises the context stream.
+ * undefined).  real != 0: the pencils are real symmetric (imaginary parts ignored; solved in
+ * real arithmetic; eigenvectors and factor written with zero imaginary parts).  Hand-written
+ * kernels (Cholesky, reduction to standard form, Householder tridiagonalisation, bisection and
+ * inverse iteration, back-transformation): one CTA per pencil, or a cooperative grid for a
+ * single pencil of order >= 160.  Synchronises the context stream.
  * Errors: KSS_EINVAL (count < 0, NULL arrays, bad sizes), KSS_ETIMEOUT (a bounded grid-barrier
  * wait gave up), KSS_ECUDA. */
 kss_status kss_dense_hegv(kss_ctx ctx, int count, const int* n, void* const* A, const int* lda,

@@ -20,6 +20,9 @@
 //   5. Back-transformation x = L^{-H} Q z (the reflectors applied to each column of Z in
 //      reverse order, then a backward substitution with L^H).
 //
+// Real symmetric pencils (the Gamma point) run the same phases in real arithmetic on compact real
+// copies of the lower triangles: a quarter of the FP64 operations of the O(n^3) phases.
+//
 // Parallel organisation.  The same phase code runs on a "team": either one CTA (many small
 // pencils, one CTA each, barrier = __syncthreads) or a whole cooperative grid (one large pencil,
 // barrier = a grid barrier of this file with a bounded wait).  Work that is independent per
@@ -86,6 +89,44 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+// The same operations on real scalars: the phases are templates on the scalar type S (double2 for
+// Hermitian pencils, double for real symmetric ones, which then take a quarter of the FP64 work of
+// the O(n^3) phases and half the memory traffic).
+__device__ __forceinline__ double cmul(double a, double b) { return a * b; }
+__device__ __forceinline__ double cmulc(double a, double b) { return a * b; }
+__device__ __forceinline__ double cfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ double cfms(double a, double b, double c) { return fma(-a, b, c); }
+__device__ __forceinline__ double cfmac(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ double conjd(double a) { return a; }
+__device__ __forceinline__ double cadd(double a, double b) { return a + b; }
+__device__ __forceinline__ double csub(double a, double b) { return a - b; }
+__device__ __forceinline__ double cscale(double a, double s) { return a * s; }
+__device__ __forceinline__ double shfl_c(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double warp_sum_c(double v) { return warp_sum(v); }
+
+__device__ __forceinline__ double re(double a) { return a; }
+__device__ __forceinline__ double re(double2 a) { return a.x; }
+__device__ __forceinline__ double im(double) { return 0.0; }
+__device__ __forceinline__ double im(double2 a) { return a.y; }
+template <class S>
+__device__ __forceinline__ S mk(double x, double y);
+template <>
+__device__ __forceinline__ double mk<double>(double x, double) { return x; }
+template <>
+__device__ __forceinline__ double2 mk<double2>(double x, double y) { return make_double2(x, y); }
+// s + |a|^2
+__device__ __forceinline__ double abs2_acc(double a, double s) { return fma(a, a, s); }
+__device__ __forceinline__ double abs2_acc(double2 a, double s) { return fma(a.x, a.x, fma(a.y, a.y, s)); }
+// 1 / a
+__device__ __forceinline__ double cinv(double a) { return 1.0 / a; }
+__device__ __forceinline__ double2 cinv(double2 a) {
+  const double r = 1.0 / (a.x * a.x + a.y * a.y);
+  return make_double2(a.x * r, -a.y * r);
+}
+// complex128 value of a scalar (the caller's matrices are complex128 in both cases)
+__device__ __forceinline__ double2 widen(double a) { return make_double2(a, 0.0); }
+__device__ __forceinline__ double2 widen(double2 a) { return a; }
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -169,50 +210,78 @@ struct GridTeam {
   }
 };
 
-// One pencil and its workspace.
+// One pencil and its workspace.  For a complex pencil (S = double2) A and B are the caller's
+// matrices, worked on in place; for a real one (S = double) they are compact real copies (ld n) in
+// the workspace, and the results are written back to the caller's complex matrices at the end.
+template <class S>
 struct Pencil {
-  double2* A;   // n x n (lda): in A, out eigenvectors
-  double2* B;   // n x n (ldb): in B, out Cholesky factor L (lower)
+  S* A;         // n x n (lda): in A, out eigenvectors
+  S* B;         // n x n (ldb): in B, out Cholesky factor L (lower)
   double* w;    // n eigenvalues (out)
   int* info;    // out: 0, or j + 1 for a non-positive pivot at column j
-  int n, lda, ldb, real;
-  double2* R;   // n x n (ld n): reduction workspace, then the reflector vectors
+  int n, lda, ldb;
+  S* R;         // n x n (ld n): reduction workspace, then the reflector vectors
   double* Z;    // n x n (ld n): eigenvectors of T
   double* wk;   // 6 n^2 doubles: inverse-iteration arrays
-  double* vec;  // 9 n + 8 doubles: d, e, tau (complex), p (complex), 1/L_jj, e^2, FP32 d and e^2
-  int smem_cols;  // 1: the launch gives every warp n complex words of dynamic shared memory
+  double* vec;  // 9 n + 8 doubles: d, e, tau (S), p (S), 1/L_jj, e^2, FP32 d and e^2
+  int smem_cols;  // 1: the launch gives every warp n words of S of dynamic shared memory
+  double2* outA;  // the caller's A and B (complex128; the same as A and B when S = double2)
+  double2* outB;
+  int ldoa, ldob;
 };
 
 // ---- phase 0: inputs ---------------------------------------------------------------------------
+// Real pencils: the real parts of the lower triangles into the compact copies.
 template <class Team>
-__device__ bool prepare(const Team& T, const Pencil& P) {
-  const int n = P.n;
-  if (P.real) {
-    for (long long t = T.rank(); t < (long long)n * n; t += T.size()) {
-      const int i = (int)(t % n), j = (int)(t / n);
-      P.A[i + (size_t)j * P.lda].y = 0.0;
-      P.B[i + (size_t)j * P.ldb].y = 0.0;
+__device__ bool prepare(const Team& T, const Pencil<double>& P) {
+  const int n = P.n, lane = threadIdx.x & 31;
+  for (int c = T.wrank(); c < n; c += T.wsize()) {
+    const double2* __restrict__ ia = P.outA + (size_t)c * P.ldoa;
+    const double2* __restrict__ ib = P.outB + (size_t)c * P.ldob;
+    double* __restrict__ a = P.A + (size_t)c * P.lda;
+    double* __restrict__ b = P.B + (size_t)c * P.ldb;
+    for (int i = c + lane; i < n; i += 32) {
+      a[i] = ia[i].x;
+      b[i] = ib[i].x;
     }
   }
   return T.sync();
 }
+template <class Team>
+__device__ bool prepare(const Team&, const Pencil<double2>&) {
+  return true;  // worked on in place
+}
+
+// Real pencils: L (lower triangle) back into the caller's B.
+template <class Team>
+__device__ void finish(const Team& T, const Pencil<double>& P) {
+  const int n = P.n, lane = threadIdx.x & 31;
+  for (int c = T.wrank(); c < n; c += T.wsize()) {
+    const double* __restrict__ b = P.B + (size_t)c * P.ldb;
+    double2* __restrict__ ob = P.outB + (size_t)c * P.ldob;
+    for (int i = c + lane; i < n; i += 32) ob[i] = make_double2(b[i], 0.0);
+  }
+}
+template <class Team>
+__device__ void finish(const Team&, const Pencil<double2>&) {}
 
 // ---- phase 1: Cholesky B = L L^H -----------------------------------------------------------------
-__device__ __forceinline__ double* vrdiag(const Pencil& P) { return P.vec + 6 * P.n; }
+template <class S>
+__device__ __forceinline__ double* vrdiag(const Pencil<S>& P) { return P.vec + 6 * P.n; }
 
 // Returns false when the solve stops (non-positive pivot: *info set; or an abandoned barrier).
-template <class Team>
-__device__ bool cholesky(const Team& T, const Pencil& P) {
+template <class Team, class S>
+__device__ bool cholesky(const Team& T, const Pencil<S>& P) {
   const int n = P.n, ld = P.ldb;
-  double2* B = P.B;
+  S* B = P.B;
   const int lane = threadIdx.x & 31;
   for (int j = 0; j < n; ++j) {
-    const double d = B[j + (size_t)j * ld].x;
+    const double d = re(B[j + (size_t)j * ld]);
     if (!(d > 0.0) || !isfinite(d)) {
       if (T.rank() == 0) *P.info = j + 1;
       return false;
     }
-    const double2* __restrict__ cj = B + (size_t)j * ld;
+    const S* __restrict__ cj = B + (size_t)j * ld;
     bool have = false;
     double dinv = 0.0;
     for (int k = j + 1 + T.wrank(); k < n; k += T.wsize()) {
@@ -220,13 +289,13 @@ __device__ bool cholesky(const Team& T, const Pencil& P) {
         dinv = __shfl_sync(0xffffffffu, lane == 0 ? 1.0 / d : 0.0, 0);
         have = true;
       }
-      const double2 f = cscale(conjd(cj[k]), dinv);
-      double2* __restrict__ ck = B + (size_t)k * ld;
+      const S f = cscale(conjd(cj[k]), dinv);
+      S* __restrict__ ck = B + (size_t)k * ld;
       int i = k + lane;
       // four rows per lane per pass, loads first (columns j and k never alias)
       for (; i + 96 < n; i += 128) {
-        const double2 a0 = ck[i], a1 = ck[i + 32], a2 = ck[i + 64], a3 = ck[i + 96];
-        const double2 b0 = cj[i], b1 = cj[i + 32], b2 = cj[i + 64], b3 = cj[i + 96];
+        const S a0 = ck[i], a1 = ck[i + 32], a2 = ck[i + 64], a3 = ck[i + 96];
+        const S b0 = cj[i], b1 = cj[i + 32], b2 = cj[i + 64], b3 = cj[i + 96];
         ck[i] = cfms(b0, f, a0);
         ck[i + 32] = cfms(b1, f, a1);
         ck[i + 64] = cfms(b2, f, a2);
@@ -239,10 +308,10 @@ __device__ bool cholesky(const Team& T, const Pencil& P) {
   // scale the columns: L[i][j] = B[i][j] / sqrt(d_j), L[j][j] = sqrt(d_j); keep 1/L[j][j]
   double* rd = vrdiag(P);
   for (int j = T.wrank(); j < n; j += T.wsize()) {
-    double2* cj = B + (size_t)j * ld;
+    S* cj = B + (size_t)j * ld;
     double s = 0.0, r = 0.0;
     if (lane == 0) {
-      s = sqrt(cj[j].x);
+      s = sqrt(re(cj[j]));
       r = 1.0 / s;
     }
     s = __shfl_sync(0xffffffffu, s, 0);
@@ -250,7 +319,7 @@ __device__ bool cholesky(const Team& T, const Pencil& P) {
     for (int i = j + 1 + lane; i < n; i += 32) cj[i] = cscale(cj[i], r);
     __syncwarp();
     if (lane == 0) {
-      cj[j] = make_double2(s, 0.0);
+      cj[j] = mk<S>(s, 0.0);
       rd[j] = r;
     }
   }
@@ -260,24 +329,25 @@ __device__ bool cholesky(const Team& T, const Pencil& P) {
 // x <- L^{-1} x for one column x (stride 1) by the calling warp, in blocks of 32 rows: the
 // diagonal block is solved in registers (lane l holds row b0 + l, values pass by shuffles), then the
 // rows below are updated by a block product whose loads are all independent.  rd: 1 / L[i][i].
-__device__ __forceinline__ void forward_subst(const double2* __restrict__ L, const double* __restrict__ rd,
-                                              int ld, int n, double2* __restrict__ x) {
+template <class S>
+__device__ __forceinline__ void forward_subst(const S* __restrict__ L, const double* __restrict__ rd,
+                                              int ld, int n, S* __restrict__ x) {
   const int lane = threadIdx.x & 31;
   for (int b0 = 0; b0 < n; b0 += 32) {
     const int bn = min(32, n - b0);
-    double2 xl = lane < bn ? x[b0 + lane] : make_double2(0.0, 0.0);
+    S xl = lane < bn ? x[b0 + lane] : mk<S>(0.0, 0.0);
     const double rl = lane < bn ? rd[b0 + lane] : 0.0;
     for (int i = 0; i < bn; ++i) {
       if (lane == i) xl = cscale(xl, rl);
-      const double2 xi = shfl_c(xl, i);
+      const S xi = shfl_c(xl, i);
       if (lane > i && lane < bn) xl = cfms(L[(size_t)(b0 + i) * ld + b0 + lane], xi, xl);
     }
     if (lane < bn) x[b0 + lane] = xl;
     for (int r0 = b0 + bn; r0 < n; r0 += 32) {
       const int r = r0 + lane;
-      double2 acc = make_double2(0.0, 0.0);
+      S acc = mk<S>(0.0, 0.0);
       for (int i = 0; i < bn; ++i) {
-        const double2 xi = shfl_c(xl, i);
+        const S xi = shfl_c(xl, i);
         if (r < n) acc = cfma(L[(size_t)(b0 + i) * ld + r], xi, acc);
       }
       if (r < n) x[r] = csub(x[r], acc);
@@ -288,25 +358,26 @@ __device__ __forceinline__ void forward_subst(const double2* __restrict__ L, con
 // x <- L^{-H} x for one column x by the calling warp, in blocks of 32 rows from the bottom: the
 // diagonal block of L^H is solved in registers, then the rows above are updated (lane i reads the
 // contiguous segment L[b0..b1), i] of column i).
-__device__ __forceinline__ void backward_subst_h(const double2* __restrict__ L, const double* __restrict__ rd,
-                                                 int ld, int n, double2* __restrict__ x) {
+template <class S>
+__device__ __forceinline__ void backward_subst_h(const S* __restrict__ L, const double* __restrict__ rd,
+                                                 int ld, int n, S* __restrict__ x) {
   const int lane = threadIdx.x & 31;
   for (int b1 = n; b1 > 0; b1 -= 32) {
     const int b0 = max(0, b1 - 32), bn = b1 - b0;
-    double2 xl = lane < bn ? x[b0 + lane] : make_double2(0.0, 0.0);
+    S xl = lane < bn ? x[b0 + lane] : mk<S>(0.0, 0.0);
     const double rl = lane < bn ? rd[b0 + lane] : 0.0;
     for (int i = bn - 1; i >= 0; --i) {
       if (lane == i) xl = cscale(xl, rl);
-      const double2 xi = shfl_c(xl, i);
+      const S xi = shfl_c(xl, i);
       if (lane < i) xl = csub(xl, cmulc(L[(size_t)(b0 + lane) * ld + b0 + i], xi));
     }
     if (lane < bn) x[b0 + lane] = xl;
     for (int r0 = 0; r0 < b0; r0 += 32) {
       const int r = r0 + lane;
-      double2 acc = make_double2(0.0, 0.0);
-      const double2* lr = L + (size_t)r * ld + b0;
+      S acc = mk<S>(0.0, 0.0);
+      const S* lr = L + (size_t)r * ld + b0;
       for (int t = 0; t < bn; ++t) {
-        const double2 xt = shfl_c(xl, t);
+        const S xt = shfl_c(xl, t);
         if (r < b0) acc = cfmac(lr[t], xt, acc);
       }
       if (r < b0) x[r] = csub(x[r], acc);
@@ -315,17 +386,17 @@ __device__ __forceinline__ void backward_subst_h(const double2* __restrict__ L, 
 }
 
 // ---- phase 2: C = L^{-1} A L^{-H} ---------------------------------------------------------------
-template <class Team>
-__device__ bool reduce_standard(const Team& T, const Pencil& P) {
+template <class Team, class S>
+__device__ bool reduce_standard(const Team& T, const Pencil<S>& P) {
   const int n = P.n, la = P.lda;
-  double2* A = P.A;
-  double2* R = P.R;
+  S* A = P.A;
+  S* R = P.R;
   const int lane = threadIdx.x & 31;
   // full Hermitian A from its lower triangle
   for (int i = T.wrank(); i < n; i += T.wsize()) {
-    double2* ci = A + (size_t)i * la;
+    S* ci = A + (size_t)i * la;
     for (int j = lane; j < i; j += 32) ci[j] = conjd(A[i + (size_t)j * la]);
-    if (lane == 0) ci[i].y = 0.0;
+    if (lane == 0) ci[i] = mk<S>(re(ci[i]), 0.0);
   }
   if (!T.sync()) return false;
   // X = L^{-1} A, column by column, in place in A
@@ -333,7 +404,7 @@ __device__ bool reduce_standard(const Team& T, const Pencil& P) {
   if (!T.sync()) return false;
   // R = X^H
   for (int r = T.wrank(); r < n; r += T.wsize()) {
-    double2* cr = R + (size_t)r * n;
+    S* cr = R + (size_t)r * n;
     for (int c = lane; c < n; c += 32) cr[c] = conjd(A[r + (size_t)c * la]);
   }
   if (!T.sync()) return false;
@@ -342,12 +413,12 @@ __device__ bool reduce_standard(const Team& T, const Pencil& P) {
   if (!T.sync()) return false;
   // A = C, made exactly Hermitian (lower triangle kept, upper = its conjugate, real diagonal)
   for (int c = T.wrank(); c < n; c += T.wsize()) {
-    double2* ac = A + (size_t)c * la;
+    S* ac = A + (size_t)c * la;
     for (int r = lane; r < n; r += 32) {
-      double2 v;
+      S v;
       if (r > c) v = R[r + (size_t)c * n];
       else if (r < c) v = conjd(R[c + (size_t)r * n]);
-      else v = make_double2(R[c + (size_t)c * n].x, 0.0);
+      else v = mk<S>(re(R[c + (size_t)c * n]), 0.0);
       ac[r] = v;
     }
   }
@@ -355,110 +426,114 @@ __device__ bool reduce_standard(const Team& T, const Pencil& P) {
 }
 
 // ---- phase 3: Householder tridiagonalisation ------------------------------------------------------
-// vec layout: d[n], e[n], tau[2n] (complex), p[2n] (complex), colnorm[2]
-__device__ __forceinline__ double* vd(const Pencil& P) { return P.vec; }
-__device__ __forceinline__ double* ve(const Pencil& P) { return P.vec + P.n; }
-__device__ __forceinline__ double2* vtau(const Pencil& P) { return reinterpret_cast<double2*>(P.vec + 2 * P.n); }
-__device__ __forceinline__ double2* vp(const Pencil& P) { return reinterpret_cast<double2*>(P.vec + 4 * P.n); }
-__device__ __forceinline__ double* ve2(const Pencil& P) { return P.vec + 7 * P.n; }   // e^2
-__device__ __forceinline__ float* vd32(const Pencil& P) { return reinterpret_cast<float*>(P.vec + 8 * P.n); }
-__device__ __forceinline__ float* ve232(const Pencil& P) { return vd32(P) + P.n; }   // e^2 in FP32
+// vec layout: d[n], e[n], tau[2n] (n words of S), p[2n] (n words of S), 1/L_jj[n], e^2[n], FP32 d, e^2
+template <class S>
+__device__ __forceinline__ double* vd(const Pencil<S>& P) { return P.vec; }
+template <class S>
+__device__ __forceinline__ double* ve(const Pencil<S>& P) { return P.vec + P.n; }
+template <class S>
+__device__ __forceinline__ S* vtau(const Pencil<S>& P) { return reinterpret_cast<S*>(P.vec + 2 * P.n); }
+template <class S>
+__device__ __forceinline__ S* vp(const Pencil<S>& P) { return reinterpret_cast<S*>(P.vec + 4 * P.n); }
+template <class S>
+__device__ __forceinline__ double* ve2(const Pencil<S>& P) { return P.vec + 7 * P.n; }   // e^2
+template <class S>
+__device__ __forceinline__ float* vd32(const Pencil<S>& P) { return reinterpret_cast<float*>(P.vec + 8 * P.n); }
+template <class S>
+__device__ __forceinline__ float* ve232(const Pencil<S>& P) { return vd32(P) + P.n; }   // e^2 in FP32
 
 
 // Reflector j, by one warp, from column j of A after every earlier update: x = A[j+1..n-1][j],
 // beta = -sign(Re x_0) |x| (the real subdiagonal), tau = (beta - x_0) / beta and v = x / (x_0 - beta)
 // with v_{j+1} = 1, stored in column j of R; d_j and e_j of T.  The scalars are formed by one lane.
-__device__ __forceinline__ void make_reflector(const Pencil& P, int j) {
+template <class S>
+__device__ __forceinline__ void make_reflector(const Pencil<S>& P, int j) {
   const int n = P.n, lane = threadIdx.x & 31;
-  const double2* cj = P.A + (size_t)j * P.lda;
+  const S* cj = P.A + (size_t)j * P.lda;
   double s = 0.0;
-  for (int i = j + 2 + lane; i < n; i += 32) {
-    const double2 a = cj[i];
-    s = fma(a.x, a.x, fma(a.y, a.y, s));
-  }
+  for (int i = j + 2 + lane; i < n; i += 32) s = abs2_acc(cj[i], s);
   s = warp_sum(s);
   double beta = 0.0;
-  double2 tj = make_double2(0.0, 0.0), vs = make_double2(0.0, 0.0);
+  S tj = mk<S>(0.0, 0.0), vs = mk<S>(0.0, 0.0);
   if (lane == 0) {
-    const double2 alpha = cj[j + 1];
-    if (s == 0.0 && alpha.y == 0.0) {
-      beta = alpha.x;
+    const S alpha = cj[j + 1];
+    if (s == 0.0 && im(alpha) == 0.0) {
+      beta = re(alpha);
     } else {
-      const double an = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + s);
-      beta = alpha.x >= 0.0 ? -an : an;
+      const double an = sqrt(abs2_acc(alpha, s));
+      beta = re(alpha) >= 0.0 ? -an : an;
       const double rb = 1.0 / beta;
-      tj = make_double2((beta - alpha.x) * rb, -alpha.y * rb);
-      const double2 den = make_double2(alpha.x - beta, alpha.y);  // v_i = x_i / (alpha - beta)
-      const double rd = 1.0 / (den.x * den.x + den.y * den.y);
-      vs = make_double2(den.x * rd, -den.y * rd);
+      tj = mk<S>((beta - re(alpha)) * rb, -im(alpha) * rb);
+      vs = cinv(csub(alpha, mk<S>(beta, 0.0)));  // v_i = x_i / (alpha - beta)
     }
-    vd(P)[j] = cj[j].x;
+    vd(P)[j] = re(cj[j]);
     ve(P)[j] = beta;
     vtau(P)[j] = tj;
   }
   vs = shfl_c(vs, 0);
-  double2* rj = P.R + (size_t)j * n;
-  for (int i = j + 1 + lane; i < n; i += 32) rj[i] = i == j + 1 ? make_double2(1.0, 0.0) : cmul(cj[i], vs);
+  S* rj = P.R + (size_t)j * n;
+  for (int i = j + 1 + lane; i < n; i += 32) rj[i] = i == j + 1 ? mk<S>(1.0, 0.0) : cmul(cj[i], vs);
 }
 
 // Sum over the CTA (every thread passes a value; every thread gets the same total, reduced in a
 // fixed order so that all CTAs of a grid team obtain bit-identical results).
-__device__ __forceinline__ double2 cta_sum_c(double2 v) {
-  __shared__ double2 red[kWarps];
+template <class S>
+__device__ __forceinline__ S cta_sum_c(S v) {
+  __shared__ S red[kWarps];
   v = warp_sum_c(v);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double2 s = make_double2(0.0, 0.0);
+  S s = mk<S>(0.0, 0.0);
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = cadd(s, red[w]);
   return s;
 }
 
-// sv, sw: 2 m complex words of shared memory per CTA (m <= n).
-template <class Team>
-__device__ bool tridiagonalise(const Team& T, const Pencil& P, double2* sv) {
+// sv, sw: 2 m words of S of shared memory per CTA (m <= n).
+template <class Team, class S>
+__device__ bool tridiagonalise(const Team& T, const Pencil<S>& P, S* sv) {
   const int n = P.n, la = P.lda;
-  double2* A = P.A;
-  double2* __restrict__ p = vp(P);
+  S* A = P.A;
+  S* __restrict__ p = vp(P);
   const int lane = threadIdx.x & 31;
   if (n == 1) {
-    if (T.rank() == 0) vd(P)[0] = A[0].x;
+    if (T.rank() == 0) vd(P)[0] = re(A[0]);
     return T.sync();
   }
-  double2* sw = sv + n;
+  S* sw = sv + n;
   if (T.wrank() == 0) make_reflector(P, 0);
   if (!T.sync()) return false;
   for (int j = 0; j < n - 1; ++j) {
-    const double2 tj = vtau(P)[j];
-    const double2* __restrict__ rj = P.R + (size_t)j * n;
+    const S tj = vtau(P)[j];
+    const S* __restrict__ rj = P.R + (size_t)j * n;
     const int m = n - j - 1;
     // p_i = tau sum_k conj(A[k][i]) v_k over the trailing block (column i of A is row i of A^H)
     for (int i = j + 1 + T.wrank(); i < n; i += T.wsize()) {
-      const double2* __restrict__ ci = A + (size_t)i * la;
-      double2 s = make_double2(0.0, 0.0);
+      const S* __restrict__ ci = A + (size_t)i * la;
+      S s = mk<S>(0.0, 0.0);
       for (int k = j + 1 + lane; k < n; k += 32) s = cfmac(ci[k], rj[k], s);
       s = warp_sum_c(s);
       if (lane == 0) p[i] = cmul(tj, s);
     }
     if (!T.sync()) return false;
     // gamma = -(tau/2) p^H v (each CTA reduces it in the same order); v and w = p + gamma v staged
-    double2 g = make_double2(0.0, 0.0);
+    S g = mk<S>(0.0, 0.0);
     for (int t = threadIdx.x; t < m; t += blockDim.x) g = cfmac(p[j + 1 + t], rj[j + 1 + t], g);
     g = cta_sum_c(g);
-    const double2 gamma = cscale(cmul(tj, g), -0.5);
+    const S gamma = cscale(cmul(tj, g), -0.5);
     for (int t = threadIdx.x; t < m; t += blockDim.x) {
-      const double2 v = rj[j + 1 + t];
+      const S v = rj[j + 1 + t];
       sv[t] = v;
       sw[t] = cfma(gamma, v, p[j + 1 + t]);
     }
     __syncthreads();
     // A <- A - v w^H - w v^H on the trailing block
     for (int k = j + 1 + T.wrank(); k < n; k += T.wsize()) {
-      const double2 cvk = conjd(sv[k - j - 1]), cwk = conjd(sw[k - j - 1]);
-      double2* __restrict__ ck = A + (size_t)k * la;
+      const S cvk = conjd(sv[k - j - 1]), cwk = conjd(sw[k - j - 1]);
+      S* __restrict__ ck = A + (size_t)k * la;
       int i = j + 1 + lane;
       for (; i + 96 < n; i += 128) {
-        double2 a[4];
+        S a[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) a[u] = ck[i + 32 * u];
 #pragma unroll
@@ -478,7 +553,7 @@ __device__ bool tridiagonalise(const Team& T, const Pencil& P, double2* sv) {
     }
     if (!T.sync()) return false;
   }
-  if (T.rank() == 0) vd(P)[n - 1] = A[(n - 1) + (size_t)(n - 1) * la].x;
+  if (T.rank() == 0) vd(P)[n - 1] = re(A[(n - 1) + (size_t)(n - 1) * la]);
   return T.sync();
 }
 
@@ -523,8 +598,8 @@ __device__ __forceinline__ double start_entry(int k, int i) {
   return ((double)(h >> 8) + 0.5) * (2.0 / 16777216.0) - 1.0;
 }
 
-template <class Team>
-__device__ bool tridiagonal_eig(const Team& T, const Pencil& P) {
+template <class Team, class S>
+__device__ bool tridiagonal_eig(const Team& T, const Pencil<S>& P) {
   const int n = P.n;
   const double* d = vd(P);
   const double* e = ve(P);
@@ -745,26 +820,26 @@ __device__ bool tridiagonal_eig(const Team& T, const Pencil& P) {
 }
 
 // ---- phase 5: x = L^{-H} Q z ------------------------------------------------------------------
-template <class Team>
-__device__ bool back_transform(const Team& T, const Pencil& P, double2* smem) {
+template <class Team, class S>
+__device__ bool back_transform(const Team& T, const Pencil<S>& P, S* smem) {
   const int n = P.n;
   const int lane = threadIdx.x & 31;
-  const double2* tau = vtau(P);
+  const S* tau = vtau(P);
   for (int c = T.wrank(); c < n; c += T.wsize()) {
     // The column is built in this warp's shared-memory slot when the launch provided one, else in
     // place in A's column c (A is free: the reflectors live in R, L in B).
-    double2* ac = P.A + (size_t)c * P.lda;
-    double2* vc = smem ? smem + (size_t)(threadIdx.x >> 5) * n : ac;
+    S* ac = P.A + (size_t)c * P.lda;
+    S* vc = smem ? smem + (size_t)(threadIdx.x >> 5) * n : ac;
     const double* zc = P.Z + (size_t)c * n;
-    for (int i = lane; i < n; i += 32) vc[i] = make_double2(zc[i], 0.0);
+    for (int i = lane; i < n; i += 32) vc[i] = mk<S>(zc[i], 0.0);
     __syncwarp();
     // V = H_0 H_1 ... H_{n-2} Z: reflector j (rows j+1..n-1, stored in column j of R) applied last-first
     for (int j = n - 2; j >= 0; --j) {
-      const double2 tj = tau[j];
-      if (tj.x == 0.0 && tj.y == 0.0) continue;
-      const double2* __restrict__ rj = P.R + (size_t)j * n;
+      const S tj = tau[j];
+      if (re(tj) == 0.0 && im(tj) == 0.0) continue;
+      const S* __restrict__ rj = P.R + (size_t)j * n;
       const int r0 = j + 1 + ((lane - j - 1) & 31);
-      double2 s = make_double2(0.0, 0.0);
+      S s = mk<S>(0.0, 0.0);
       for (int i = r0; i < n; i += 32) s = cadd(s, cmulc(rj[i], vc[i]));
       s = cmul(tj, warp_sum_c(s));
       for (int i = r0; i < n; i += 32) vc[i] = csub(vc[i], cmul(rj[i], s));
@@ -772,64 +847,82 @@ __device__ bool back_transform(const Team& T, const Pencil& P, double2* smem) {
     __syncwarp();
     backward_subst_h(P.B, vrdiag(P), P.ldb, n, vc);
     __syncwarp();
-    for (int i = lane; i < n; i += 32) {
-      double2 v = vc[i];
-      if (P.real) v.y = 0.0;
-      ac[i] = v;
-    }
+    // into the caller's complex A (in place for a complex pencil: the same lane, the same element)
+    double2* oc = P.outA + (size_t)c * P.ldoa;
+    for (int i = lane; i < n; i += 32) oc[i] = widen(vc[i]);
     __syncwarp();
   }
   return T.sync();
 }
 
-template <class Team>
-__device__ void solve_pencil(const Team& T, const Pencil& P) {
+template <class Team, class S>
+__device__ void solve_pencil(const Team& T, const Pencil<S>& P) {
   extern __shared__ double2 dyn_smem[];
+  S* smem = reinterpret_cast<S*>(dyn_smem);
   if (T.rank() == 0) *P.info = 0;
   if (P.n <= 0) return;
   if (!prepare(T, P)) return;
   if (!cholesky(T, P)) return;
   if (!reduce_standard(T, P)) return;
-  if (!tridiagonalise(T, P, dyn_smem)) return;
+  if (!tridiagonalise(T, P, smem)) return;
   if (!tridiagonal_eig(T, P)) return;
-  back_transform(T, P, P.smem_cols ? dyn_smem : nullptr);
+  if (!back_transform(T, P, P.smem_cols ? smem : nullptr)) return;
+  finish(T, P);
 }
 
-__global__ void __launch_bounds__(kThreads) hegv_grid_kernel(Pencil P, Ctl* ctl, unsigned long long limit_ns) {
+template <class S>
+__global__ void __launch_bounds__(kThreads) hegv_grid_kernel(Pencil<S> P, Ctl* ctl, unsigned long long limit_ns) {
   GridTeam T{ctl, P.info, limit_ns};
   solve_pencil(T, P);
 }
 
-__global__ void __launch_bounds__(kThreads) hegv_cta_kernel(const Pencil* __restrict__ items, int count) {
+template <class S>
+__global__ void __launch_bounds__(kThreads) hegv_cta_kernel(const Pencil<S>* __restrict__ items, int count) {
   if ((int)blockIdx.x >= count) return;
-  const Pencil P = items[blockIdx.x];
+  const Pencil<S> P = items[blockIdx.x];
   CtaTeam T;
   solve_pencil(T, P);
 }
 
-size_t work_doubles(int n) {
+size_t pad32(size_t x) { return (x + 31) & ~(size_t)31; }
+
+// Workspace doubles of one pencil, each array padded to 32 doubles: complex, R (complex n^2);
+// real, the compact A, B and R (n^2 each); then Z (n^2), wk (6 n^2) and vec (9 n + 8).
+size_t work_doubles(int n, bool real) {
   const size_t nn = (size_t)n * n;
-  // R (complex n^2) + Z (n^2) + wk (6 n^2) + vec (6 n + 8), each padded to 32 doubles
-  auto pad = [](size_t x) { return (x + 31) & ~(size_t)31; };
-  return pad(2 * nn) + pad(nn) + pad(6 * nn) + pad(9 * (size_t)n + 8);
+  const size_t own = real ? 3 * pad32(nn) : pad32(2 * nn);
+  return own + pad32(nn) + pad32(6 * nn) + pad32(9 * (size_t)n + 8);
 }
 
-Pencil make_pencil(double2* A, int lda, double2* B, int ldb, double* w, int* info, int n, bool real, double* ws) {
-  auto pad = [](size_t x) { return (x + 31) & ~(size_t)31; };
+template <class S>
+Pencil<S> make_pencil(double2* A, int lda, double2* B, int ldb, double* w, int* info, int n, double* ws) {
   const size_t nn = (size_t)n * n;
-  Pencil P;
-  P.A = A;
-  P.B = B;
+  Pencil<S> P;
   P.w = w;
   P.info = info;
   P.n = n;
-  P.lda = lda;
-  P.ldb = ldb;
-  P.real = real ? 1 : 0;
-  P.R = reinterpret_cast<double2*>(ws);
-  P.Z = ws + pad(2 * nn);
-  P.wk = P.Z + pad(nn);
-  P.vec = P.wk + pad(6 * nn);
+  P.outA = A;
+  P.outB = B;
+  P.ldoa = lda;
+  P.ldob = ldb;
+  double* rest;
+  if constexpr (sizeof(S) == sizeof(double)) {  // real: compact copies in the workspace
+    P.A = reinterpret_cast<S*>(ws);
+    P.B = reinterpret_cast<S*>(ws + pad32(nn));
+    P.R = reinterpret_cast<S*>(ws + 2 * pad32(nn));
+    P.lda = P.ldb = n;
+    rest = ws + 3 * pad32(nn);
+  } else {
+    P.A = reinterpret_cast<S*>(A);
+    P.B = reinterpret_cast<S*>(B);
+    P.lda = lda;
+    P.ldb = ldb;
+    P.R = reinterpret_cast<S*>(ws);
+    rest = ws + pad32(2 * nn);
+  }
+  P.Z = rest;
+  P.wk = P.Z + pad32(nn);
+  P.vec = P.wk + pad32(6 * nn);
   P.smem_cols = 0;
   return P;
 }
@@ -837,69 +930,85 @@ Pencil make_pencil(double2* A, int lda, double2* B, int ldb, double* w, int* inf
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per grid-barrier wait
 constexpr int kGridMinN = 160;  // pencils at least this large run on a cooperative grid
 
-// Dynamic shared memory: 2 n complex words for the tridiagonalisation's v and w, and, when it fits
-// in 200 KB, one column of n complex words per warp for the back-transformation.
-size_t col_smem_bytes(int n) {
-  const size_t b = (size_t)kWarps * (size_t)std::max(n, 1) * sizeof(double2);
+// Dynamic shared memory: 2 n words of S for the tridiagonalisation's v and w, and, when it fits in
+// 200 KB, one column of n words of S per warp for the back-transformation.
+size_t col_smem_bytes(int n, size_t ws) {
+  const size_t b = (size_t)kWarps * (size_t)std::max(n, 1) * ws;
   return b <= 200u * 1024u ? b : 0;
 }
-size_t dyn_smem_bytes(int n) {
-  return std::max(col_smem_bytes(n), (size_t)2 * std::max(n, 1) * sizeof(double2));
-}
+size_t dyn_smem_bytes(int n, size_t ws) { return std::max(col_smem_bytes(n, ws), (size_t)2 * std::max(n, 1) * ws); }
 constexpr int kMaxN = 6000;  // 2 n complex words must fit in shared memory
+
+template <class S>
+void launch_cta(kss_ctx ctx, std::vector<Pencil<S>>& small, size_t items_offset, const char* name) {
+  if (small.empty()) return;
+  cudaStream_t st = ctx->stream;
+  int nmax = 1;
+  for (const auto& P : small) nmax = std::max(nmax, P.n);
+  const size_t sm = dyn_smem_bytes(nmax, sizeof(S));
+  for (auto& P : small) P.smem_cols = col_smem_bytes(nmax, sizeof(S)) ? 1 : 0;
+  Pencil<S>* d_items = reinterpret_cast<Pencil<S>*>(static_cast<char*>(ctx->dense_items.p) + items_offset);
+  KSS_CHECK_CUDA(cudaMemcpyAsync(d_items, small.data(), small.size() * sizeof(Pencil<S>), cudaMemcpyHostToDevice, st));
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(hegv_cta_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  ProfScope ps(ctx, prof_register(name));
+  hegv_cta_kernel<S><<<(unsigned)small.size(), kThreads, sm, st>>>(d_items, (int)small.size());
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+template <class S>
+void launch_grid(kss_ctx ctx, Pencil<S> P, const char* name) {
+  cudaStream_t st = ctx->stream;
+  const int n = P.n;
+  const size_t sm = dyn_smem_bytes(n, sizeof(S));
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(hegv_grid_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  int per_sm = 0;
+  KSS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hegv_grid_kernel<S>, kThreads, sm));
+  const int coop = std::max(1, per_sm) * std::max(1, ctx->nsm);
+  const int G = std::max(1, std::min({(n + 3) / 4, ctx->nsm > 0 ? ctx->nsm : 1, coop}));
+  ctx->dense_ctl.ensure(sizeof(Ctl));
+  KSS_CHECK_CUDA(cudaMemsetAsync(ctx->dense_ctl.p, 0, sizeof(Ctl), st));
+  P.smem_cols = col_smem_bytes(n, sizeof(S)) ? 1 : 0;
+  Ctl* ctl = ctx->dense_ctl.as<Ctl>();
+  unsigned long long lim = kWaitLimitNs;
+  void* args[] = {&P, &ctl, &lim};
+  ProfScope ps(ctx, prof_register(name));
+  KSS_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)hegv_grid_kernel<S>, dim3(G), dim3(kThreads), args, sm, st));
+}
 
 }  // namespace
 
 void hegv_batched(kss_ctx ctx, const std::vector<HegvItem>& items) {
   if (items.empty()) return;
-  cudaStream_t st = ctx->stream;
   size_t total = 0;
-  for (const auto& it : items) total += work_doubles(std::max(it.n, 1));
+  for (const auto& it : items) total += work_doubles(std::max(it.n, 1), it.real);
   ctx->dense_ws.ensure(total * sizeof(double));
-  std::vector<Pencil> small;  // one CTA each
-  std::vector<std::pair<Pencil, int>> large;
+  // one CTA per pencil, real and complex pencils in separate launches; a single large pencil on a
+  // cooperative grid
+  std::vector<Pencil<double>> small_r;
+  std::vector<Pencil<double2>> small_c;
   double* p = ctx->dense_ws.as<double>();
+  const bool alone = items.size() == 1;
   for (const auto& it : items) {
     KSS_REQUIRE(it.n >= 0 && it.lda >= std::max(it.n, 1) && it.ldb >= std::max(it.n, 1), "hegv: bad sizes");
     KSS_REQUIRE(it.n <= kMaxN, "hegv: order above " + std::to_string(kMaxN));
-    const Pencil P = make_pencil((double2*)it.A, it.lda, (double2*)it.B, it.ldb, it.w, it.info, it.n, it.real, p);
-    p += work_doubles(std::max(it.n, 1));
-    if (it.n >= kGridMinN && items.size() == 1) large.push_back({P, it.n});
-    else small.push_back(P);
+    double2* A = (double2*)it.A;
+    double2* B = (double2*)it.B;
+    const bool large = alone && it.n >= kGridMinN;
+    if (it.real) {
+      const Pencil<double> P = make_pencil<double>(A, it.lda, B, it.ldb, it.w, it.info, it.n, p);
+      if (large) launch_grid(ctx, P, "dense_hegv_grid_real");
+      else small_r.push_back(P);
+    } else {
+      const Pencil<double2> P = make_pencil<double2>(A, it.lda, B, it.ldb, it.w, it.info, it.n, p);
+      if (large) launch_grid(ctx, P, "dense_hegv_grid");
+      else small_c.push_back(P);
+    }
+    p += work_doubles(std::max(it.n, 1), it.real);
   }
-  if (!small.empty()) {
-    int nmax = 1;
-    for (const auto& P : small) nmax = std::max(nmax, P.n);
-    const size_t sm = dyn_smem_bytes(nmax);
-    for (auto& P : small) P.smem_cols = col_smem_bytes(nmax) ? 1 : 0;
-    ctx->dense_items.ensure(small.size() * sizeof(Pencil));
-    KSS_CHECK_CUDA(cudaMemcpyAsync(ctx->dense_items.p, small.data(), small.size() * sizeof(Pencil),
-                                   cudaMemcpyHostToDevice, st));
-    KSS_CHECK_CUDA(cudaFuncSetAttribute(hegv_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    static const int id = prof_register("dense_hegv_cta");
-    ProfScope ps(ctx, id);
-    hegv_cta_kernel<<<(unsigned)small.size(), kThreads, sm, st>>>(ctx->dense_items.as<Pencil>(), (int)small.size());
-    KSS_CHECK_CUDA(cudaGetLastError());
-  }
-  for (auto& lp : large) {
-    const int n = lp.second;
-    const size_t sm = dyn_smem_bytes(n);
-    KSS_CHECK_CUDA(cudaFuncSetAttribute(hegv_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    int per_sm = 0;
-    KSS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hegv_grid_kernel, kThreads, sm));
-    const int coop = std::max(1, per_sm) * std::max(1, ctx->nsm);
-    const int G = std::max(1, std::min({(n + 3) / 4, ctx->nsm > 0 ? ctx->nsm : 1, coop}));
-    ctx->dense_ctl.ensure(sizeof(Ctl));
-    KSS_CHECK_CUDA(cudaMemsetAsync(ctx->dense_ctl.p, 0, sizeof(Ctl), st));
-    Pencil P = lp.first;
-    P.smem_cols = col_smem_bytes(n) ? 1 : 0;
-    Ctl* ctl = ctx->dense_ctl.as<Ctl>();
-    unsigned long long lim = kWaitLimitNs;
-    void* args[] = {&P, &ctl, &lim};
-    static const int id = prof_register("dense_hegv_grid");
-    ProfScope ps(ctx, id);
-    KSS_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)hegv_grid_kernel, dim3(G), dim3(kThreads), args, sm, st));
-  }
+  const size_t off_c = (small_r.size() * sizeof(Pencil<double>) + 255) & ~(size_t)255;
+  ctx->dense_items.ensure(off_c + small_c.size() * sizeof(Pencil<double2>) + 1);
+  launch_cta(ctx, small_r, 0, "dense_hegv_cta_real");
+  launch_cta(ctx, small_c, off_c, "dense_hegv_cta");
 }
 
 void hegv(kss_ctx ctx, int n, void* A, int lda, void* B, int ldb, double* w, int* info, bool real) {

@@ -4,7 +4,9 @@
 Bars: eigenvalues within 1e-11 of the largest |eigenvalue| of the oracle's (a backward-stable
 solver's error on these well-conditioned B); eigenvectors checked by their own invariants, since
 degenerate and clustered eigenvalues make individual vectors gauge-dependent: the residual
-|A X - B X diag(w)| <= 1e-11 |A| and B-orthonormality |X^H B X - I| <= 1e-11.
+|A X - B X diag(w)| <= 1e-11 |A| and B-orthonormality |X^H B X - I| <= 1e-11.  Real symmetric
+pencils run in real arithmetic and are checked the same way (and for exactly real outputs); the
+returned Cholesky factor is checked against LAPACK's.
 """
 import numpy as np
 import pytest
@@ -110,13 +112,61 @@ def test_degenerate_clusters(ctx, n):
     check(A, B, w, X)
 
 
-@pytest.mark.parametrize("n", [24, 300])
+@pytest.mark.parametrize("n", [1, 2, 24, 159, 160, 300, 700])
 def test_real_symmetric(ctx, n):
+    """Real symmetric pencils (solved in real arithmetic): one CTA below order 160, the cooperative
+    grid from 160; imaginary parts planted in the inputs are ignored."""
     A, B = pencil(n, seed=3 * n, real=True)
-    info, [(w, X)] = run(ctx, [(A, B)], real=True)
+    rng = np.random.default_rng(n)
+    junk = 1j * rng.standard_normal((n, n))
+    info, [(w, X)] = run(ctx, [(A + junk, B + junk.T)], real=True)
     assert info[0] == 0
     assert np.all(X.imag == 0)
+    check(A.real.astype(np.complex128), B.real.astype(np.complex128), w, X)
+
+
+def test_real_batched_pencils_of_uneven_order_with_padding(ctx):
+    ps = [pencil(n, seed=200 + n, real=True) for n in (3, 40, 97, 150, 8)]
+    lds = [p[0].shape[0] + 5 for p in ps]
+    info, out = run(ctx, ps, real=True, lds=lds)
+    assert np.all(info == 0)
+    for (A, B), (w, X) in zip(ps, out):
+        assert np.all(X.imag == 0)
+        check(A, B, w, X)
+
+
+@pytest.mark.parametrize("n", [40, 200])
+def test_real_degenerate_clusters(ctx, n):
+    """Exactly degenerate shells in a random orthogonal frame, B = I, in real arithmetic."""
+    rng = np.random.default_rng(9)
+    lam = np.concatenate([np.zeros(1), np.full(6, 0.2), np.full(12, 0.4), np.linspace(0.5, 2.0, n - 19)])
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (q * lam[None, :]) @ q.T
+    A = ((A + A.T) / 2).astype(np.complex128)
+    B = np.eye(n, dtype=np.complex128)
+    info, [(w, X)] = run(ctx, [(A, B)], real=True)
+    assert info[0] == 0
     check(A, B, w, X)
+
+
+@pytest.mark.parametrize("n,real", [(50, False), (50, True), (260, False), (260, True)])
+def test_cholesky_factor_returned(ctx, n, real):
+    """On return the lower triangle of B holds L with B = L L^H (LAPACK's factor: positive real
+    diagonal), the strictly upper triangle is untouched."""
+    import torch
+    A, B = pencil(n, seed=11 * n, real=real)
+    Bd = to_dev(B)
+    Ad = to_dev(A)
+    w = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = K.kss_dense_hegv(ctx, [Ad], [Bd], [w], real=real)
+    assert info[0] == 0
+    T = Bd.cpu().numpy().T  # column-major back to (row, col)
+    L = np.tril(T)
+    ref = np.linalg.cholesky(B)
+    assert np.max(np.abs(L - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert np.all(np.isnan(T[np.triu_indices(n, 1)]))
+    if real:
+        assert np.all(L.imag == 0)
 
 
 @pytest.mark.parametrize("n", [12, 200])
