@@ -1026,6 +1026,8 @@ def run_dense(args):
             assert not np.any(info)
         ms = 1000.0 * float(np.median(times[args.warmup:]))
         out[name] = {"pencils": len(ns), "max_order": int(max(ns)), "real": real, "ms": ms}
+        if len(ns) == 1:  # device-clock phase times of the last (grid-team) solve
+            out[name]["phase_ms"] = {k: round(v, 3) for k, v in K.kss_dense_hegv_phase_ms(ctx).items()}
     K.kss_destroy(ctx)
     print(json.dumps({"metric": "dense FP64 generalised eigensolve time", "value": out["c2_564"]["ms"],
                       "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,

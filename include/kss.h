@@ -295,6 +295,13 @@ kss_status kss_gemm(kss_ctx ctx, int op, int M, int N, int K, const void* A, int
 kss_status kss_dense_hegv(kss_ctx ctx, int count, const int* n, void* const* A, const int* lda,
                           void* const* B, const int* ldb, double* const* w, int* info, int real);
 
+/* Phase times of the last single-pencil solve that ran on a cooperative grid (order >= 160) in
+ * this context, from the device clock: ms[0] Cholesky (with the real-pencil input copy), ms[1]
+ * reduction to standard form, ms[2] tridiagonalisation, ms[3] eigenvalues of the tridiagonal
+ * matrix (bisection), ms[4] its eigenvectors (inverse iteration), ms[5] back-transformation.  Measurement support (the paper has no counterpart).  Synchronises the context stream; all zeros when
+ * no grid solve has completed.  Errors: KSS_EINVAL (NULL), KSS_ECUDA. */
+kss_status kss_dense_hegv_phase_ms(kss_ctx ctx, double* ms);
+
 /* Failure path of the bounded device waits, exercised without a fault (test support; the paper
  * has no counterpart).  Launches one thread that waits on a device word nothing writes, with the
  * same %globaltimer limit pattern as the tensor-core pipeline waits; after limit_ms (0 < limit_ms

@@ -49,6 +49,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+static_assert((kWarps & (kWarps - 1)) == 0, "the CTA reductions take a power-of-two warp count");
 
 // ---- complex helpers ---------------------------------------------------------------------------
 // On GB300 an SM retires about two FP64 fused multiply-adds per clock, so every FP64 instruction
@@ -104,6 +105,10 @@ __device__ __forceinline__ double csub(double a, double b) { return a - b; }
 __device__ __forceinline__ double cscale(double a, double s) { return a * s; }
 __device__ __forceinline__ double shfl_c(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ double warp_sum_c(double v) { return warp_sum(v); }
+__device__ __forceinline__ double shfl_xor_c(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double2 shfl_xor_c(double2 v, int o) {
+  return make_double2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
 
 __device__ __forceinline__ double re(double a) { return a; }
 __device__ __forceinline__ double re(double2 a) { return a.x; }
@@ -136,10 +141,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Control block of one grid-team solve (zeroed before the launch).
 struct Ctl {
-  unsigned count;
-  unsigned gen;
+  unsigned count;  // barrier arrivals (monotonic)
+  unsigned pad0;
   int err;  // 1: a barrier wait gave up
-  int pad;
+  int pad1;
+  unsigned long long t[8];  // %globaltimer at the start and after each phase (measurement)
 };
 
 struct CtaTeam {
@@ -148,12 +154,12 @@ struct CtaTeam {
   __device__ int srank() const { return threadIdx.x; }
   __device__ int swrank() const { return threadIdx.x >> 5; }  // the same for per-warp work
   __device__ int size() const { return blockDim.x; }
-  __device__ int wrank() const { return threadIdx.x >> 5; }
   __device__ int wsize() const { return blockDim.x >> 5; }
   __device__ bool sync() const {
     __syncthreads();
     return true;
   }
+  __device__ void stamp(int) const {}
 };
 
 struct GridTeam {
@@ -166,42 +172,42 @@ struct GridTeam {
   __device__ int srank() const { return threadIdx.x * gridDim.x + blockIdx.x; }
   __device__ int swrank() const { return (threadIdx.x >> 5) * gridDim.x + blockIdx.x; }
   __device__ int size() const { return gridDim.x * blockDim.x; }
-  __device__ int wrank() const { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
   __device__ int wsize() const { return (gridDim.x * blockDim.x) >> 5; }
-  // Grid barrier (all CTAs are resident: cooperative launch).  Arrival is an acq_rel add on a
-  // counter; the last CTA to arrive resets the counter and releases a new generation, the others
-  // wait for it with a bounded spin.  Returns false when the solve has been abandoned.
+  // time stamp k (by one thread, after the barrier that ends a phase)
+  __device__ void stamp(int k) const {
+    if (rank() == 0) ctl->t[k] = global_ns();
+  }
+  // Grid barrier (all CTAs are resident: cooperative launch).  The counter only grows: barrier
+  // number b (counted by every thread in its own copy of the team) is passed once it reaches
+  // b x gridDim.x.  Each CTA arrives with one release add, which makes the writes of all its
+  // threads (ordered before it by __syncthreads) visible to any thread that acquires the counter,
+  // and waits with acquire loads in a bounded spin.  Returns false when the solve has been
+  // abandoned.
+  mutable unsigned epoch = 0;
   __device__ bool sync() const {
     __shared__ int s_ok;
     __syncthreads();
+    const unsigned target = ++epoch * gridDim.x;
     if (threadIdx.x == 0) {
-      cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(ctl->gen), cnt(ctl->count);
+      cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(ctl->count);
       cuda::atomic_ref<int, cuda::thread_scope_device> err(ctl->err);
       int ok = err.load(cuda::memory_order_relaxed) == 0;
       if (ok) {
-        __threadfence();
-        const unsigned g = gen.load(cuda::memory_order_acquire);
-        const unsigned a = cnt.fetch_add(1u, cuda::memory_order_acq_rel) + 1u;
-        if (a == gridDim.x) {
-          cnt.store(0u, cuda::memory_order_relaxed);
-          gen.store(g + 1u, cuda::memory_order_release);
-        } else {
-          const unsigned long long t0 = global_ns();
-          unsigned spins = 0;
-          while (gen.load(cuda::memory_order_acquire) == g) {
-            if (err.load(cuda::memory_order_relaxed)) {
-              ok = 0;
-              break;
-            }
-            if ((++spins & 63u) == 0 && global_ns() - t0 > limit_ns) {
-              err.store(1, cuda::memory_order_relaxed);
-              *info = -1;
-              ok = 0;
-              break;
-            }
+        cnt.fetch_add(1u, cuda::memory_order_release);
+        const unsigned long long t0 = global_ns();
+        unsigned spins = 0;
+        while (cnt.load(cuda::memory_order_acquire) < target) {
+          if (err.load(cuda::memory_order_relaxed)) {
+            ok = 0;
+            break;
+          }
+          if ((++spins & 63u) == 0 && global_ns() - t0 > limit_ns) {
+            err.store(1, cuda::memory_order_relaxed);
+            *info = -1;
+            ok = 0;
+            break;
           }
         }
-        __threadfence();
       }
       s_ok = ok;
     }
@@ -222,8 +228,8 @@ struct Pencil {
   int n, lda, ldb;
   S* R;         // n x n (ld n): reduction workspace, then the reflector vectors
   double* Z;    // n x n (ld n): eigenvectors of T
-  double* wk;   // 6 n^2 doubles: inverse-iteration arrays
-  double* vec;  // 9 n + 8 doubles: d, e, tau (S), p (S), 1/L_jj, e^2, FP32 d and e^2
+  double* wk;   // 7 n^2 doubles: inverse-iteration arrays
+  double* vec;  // 11 n + 8 doubles: d, e, tau (S), p (2 x S), 1/L_jj, e^2, FP32 d and e^2
   int smem_cols;  // 1: the launch gives every warp n words of S of dynamic shared memory
   double2* outA;  // the caller's A and B (complex128; the same as A and B when S = double2)
   double2* outB;
@@ -235,7 +241,7 @@ struct Pencil {
 template <class Team>
 __device__ bool prepare(const Team& T, const Pencil<double>& P) {
   const int n = P.n, lane = threadIdx.x & 31;
-  for (int c = T.wrank(); c < n; c += T.wsize()) {
+  for (int c = T.swrank(); c < n; c += T.wsize()) {
     const double2* __restrict__ ia = P.outA + (size_t)c * P.ldoa;
     const double2* __restrict__ ib = P.outB + (size_t)c * P.ldob;
     double* __restrict__ a = P.A + (size_t)c * P.lda;
@@ -256,7 +262,7 @@ __device__ bool prepare(const Team&, const Pencil<double2>&) {
 template <class Team>
 __device__ void finish(const Team& T, const Pencil<double>& P) {
   const int n = P.n, lane = threadIdx.x & 31;
-  for (int c = T.wrank(); c < n; c += T.wsize()) {
+  for (int c = T.swrank(); c < n; c += T.wsize()) {
     const double* __restrict__ b = P.B + (size_t)c * P.ldb;
     double2* __restrict__ ob = P.outB + (size_t)c * P.ldob;
     for (int i = c + lane; i < n; i += 32) ob[i] = make_double2(b[i], 0.0);
@@ -267,7 +273,7 @@ __device__ void finish(const Team&, const Pencil<double2>&) {}
 
 // ---- phase 1: Cholesky B = L L^H -----------------------------------------------------------------
 template <class S>
-__device__ __forceinline__ double* vrdiag(const Pencil<S>& P) { return P.vec + 6 * P.n; }
+__device__ __forceinline__ double* vrdiag(const Pencil<S>& P) { return P.vec + 8 * P.n; }
 
 // Returns false when the solve stops (non-positive pivot: *info set; or an abandoned barrier).
 template <class Team, class S>
@@ -284,7 +290,7 @@ __device__ bool cholesky(const Team& T, const Pencil<S>& P) {
     const S* __restrict__ cj = B + (size_t)j * ld;
     bool have = false;
     double dinv = 0.0;
-    for (int k = j + 1 + T.wrank(); k < n; k += T.wsize()) {
+    for (int k = j + 1 + T.swrank(); k < n; k += T.wsize()) {
       if (!have) {  // one division per warp, not per thread
         dinv = __shfl_sync(0xffffffffu, lane == 0 ? 1.0 / d : 0.0, 0);
         have = true;
@@ -307,7 +313,7 @@ __device__ bool cholesky(const Team& T, const Pencil<S>& P) {
   }
   // scale the columns: L[i][j] = B[i][j] / sqrt(d_j), L[j][j] = sqrt(d_j); keep 1/L[j][j]
   double* rd = vrdiag(P);
-  for (int j = T.wrank(); j < n; j += T.wsize()) {
+  for (int j = T.swrank(); j < n; j += T.wsize()) {
     S* cj = B + (size_t)j * ld;
     double s = 0.0, r = 0.0;
     if (lane == 0) {
@@ -393,26 +399,26 @@ __device__ bool reduce_standard(const Team& T, const Pencil<S>& P) {
   S* R = P.R;
   const int lane = threadIdx.x & 31;
   // full Hermitian A from its lower triangle
-  for (int i = T.wrank(); i < n; i += T.wsize()) {
+  for (int i = T.swrank(); i < n; i += T.wsize()) {
     S* ci = A + (size_t)i * la;
     for (int j = lane; j < i; j += 32) ci[j] = conjd(A[i + (size_t)j * la]);
     if (lane == 0) ci[i] = mk<S>(re(ci[i]), 0.0);
   }
   if (!T.sync()) return false;
   // X = L^{-1} A, column by column, in place in A
-  for (int c = T.wrank(); c < n; c += T.wsize()) forward_subst(P.B, vrdiag(P), P.ldb, n, A + (size_t)c * la);
+  for (int c = T.swrank(); c < n; c += T.wsize()) forward_subst(P.B, vrdiag(P), P.ldb, n, A + (size_t)c * la);
   if (!T.sync()) return false;
   // R = X^H
-  for (int r = T.wrank(); r < n; r += T.wsize()) {
+  for (int r = T.swrank(); r < n; r += T.wsize()) {
     S* cr = R + (size_t)r * n;
     for (int c = lane; c < n; c += 32) cr[c] = conjd(A[r + (size_t)c * la]);
   }
   if (!T.sync()) return false;
   // C = L^{-1} X^H = L^{-1} A L^{-H}, in place in R
-  for (int c = T.wrank(); c < n; c += T.wsize()) forward_subst(P.B, vrdiag(P), P.ldb, n, R + (size_t)c * n);
+  for (int c = T.swrank(); c < n; c += T.wsize()) forward_subst(P.B, vrdiag(P), P.ldb, n, R + (size_t)c * n);
   if (!T.sync()) return false;
   // A = C, made exactly Hermitian (lower triangle kept, upper = its conjugate, real diagonal)
-  for (int c = T.wrank(); c < n; c += T.wsize()) {
+  for (int c = T.swrank(); c < n; c += T.wsize()) {
     S* ac = A + (size_t)c * la;
     for (int r = lane; r < n; r += 32) {
       S v;
@@ -426,7 +432,8 @@ __device__ bool reduce_standard(const Team& T, const Pencil<S>& P) {
 }
 
 // ---- phase 3: Householder tridiagonalisation ------------------------------------------------------
-// vec layout: d[n], e[n], tau[2n] (n words of S), p[2n] (n words of S), 1/L_jj[n], e^2[n], FP32 d, e^2
+// vec layout: d[n], e[n], tau[2n] (n words of S), p[4n] (2 n words of S: p of two consecutive
+// steps), 1/L_jj[n], e^2[n], FP32 d and e^2[n]
 template <class S>
 __device__ __forceinline__ double* vd(const Pencil<S>& P) { return P.vec; }
 template <class S>
@@ -436,44 +443,11 @@ __device__ __forceinline__ S* vtau(const Pencil<S>& P) { return reinterpret_cast
 template <class S>
 __device__ __forceinline__ S* vp(const Pencil<S>& P) { return reinterpret_cast<S*>(P.vec + 4 * P.n); }
 template <class S>
-__device__ __forceinline__ double* ve2(const Pencil<S>& P) { return P.vec + 7 * P.n; }   // e^2
+__device__ __forceinline__ double* ve2(const Pencil<S>& P) { return P.vec + 9 * P.n; }   // e^2
 template <class S>
-__device__ __forceinline__ float* vd32(const Pencil<S>& P) { return reinterpret_cast<float*>(P.vec + 8 * P.n); }
+__device__ __forceinline__ float* vd32(const Pencil<S>& P) { return reinterpret_cast<float*>(P.vec + 10 * P.n); }
 template <class S>
 __device__ __forceinline__ float* ve232(const Pencil<S>& P) { return vd32(P) + P.n; }   // e^2 in FP32
-
-
-// Reflector j, by one warp, from column j of A after every earlier update: x = A[j+1..n-1][j],
-// beta = -sign(Re x_0) |x| (the real subdiagonal), tau = (beta - x_0) / beta and v = x / (x_0 - beta)
-// with v_{j+1} = 1, stored in column j of R; d_j and e_j of T.  The scalars are formed by one lane.
-template <class S>
-__device__ __forceinline__ void make_reflector(const Pencil<S>& P, int j) {
-  const int n = P.n, lane = threadIdx.x & 31;
-  const S* cj = P.A + (size_t)j * P.lda;
-  double s = 0.0;
-  for (int i = j + 2 + lane; i < n; i += 32) s = abs2_acc(cj[i], s);
-  s = warp_sum(s);
-  double beta = 0.0;
-  S tj = mk<S>(0.0, 0.0), vs = mk<S>(0.0, 0.0);
-  if (lane == 0) {
-    const S alpha = cj[j + 1];
-    if (s == 0.0 && im(alpha) == 0.0) {
-      beta = re(alpha);
-    } else {
-      const double an = sqrt(abs2_acc(alpha, s));
-      beta = re(alpha) >= 0.0 ? -an : an;
-      const double rb = 1.0 / beta;
-      tj = mk<S>((beta - re(alpha)) * rb, -im(alpha) * rb);
-      vs = cinv(csub(alpha, mk<S>(beta, 0.0)));  // v_i = x_i / (alpha - beta)
-    }
-    vd(P)[j] = re(cj[j]);
-    ve(P)[j] = beta;
-    vtau(P)[j] = tj;
-  }
-  vs = shfl_c(vs, 0);
-  S* rj = P.R + (size_t)j * n;
-  for (int i = j + 1 + lane; i < n; i += 32) rj[i] = i == j + 1 ? mk<S>(1.0, 0.0) : cmul(cj[i], vs);
-}
 
 // Sum over the CTA (every thread passes a value; every thread gets the same total, reduced in a
 // fixed order so that all CTAs of a grid team obtain bit-identical results).
@@ -484,91 +458,192 @@ __device__ __forceinline__ S cta_sum_c(S v) {
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  S s = mk<S>(0.0, 0.0);
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = cadd(s, red[w]);
+  // second level: the kWarps warp totals in every group of kWarps lanes, a butterfly within the
+  // group (every lane ends with the same value: each level adds the same two operands, in either
+  // order); the launch has kThreads threads
+  S s = red[threadIdx.x & (kWarps - 1)];
+#pragma unroll
+  for (int o = kWarps / 2; o > 0; o >>= 1) s = cadd(s, shfl_xor_c(s, o));
   return s;
 }
 
-// sv, sw: 2 m words of S of shared memory per CTA (m <= n).
+// Reflector j from x = column j of the updated matrix, rows j+1..n-1, staged in sx[j+1..n-1] by the
+// whole CTA: beta = -sign(Re x_0) |x| (the real subdiagonal e_j), tau = (beta - x_0) / beta and
+// v = x / (x_0 - beta) with v_{j+1} = 1, left in sx.  Every CTA of a grid team computes it the same
+// way (fixed-order sums); the writer CTA also stores e_j, tau_j and v (column j of R).
+template <class S>
+__device__ S cta_reflector(const Pencil<S>& P, int j, S* sx, bool writer) {
+  __shared__ S s_tau, s_vs;
+  const int n = P.n, tid = threadIdx.x;
+  __syncthreads();  // sx was staged by other threads
+  double s = 0.0;
+  for (int i = j + 2 + tid; i < n; i += blockDim.x) s = abs2_acc(sx[i], s);
+  s = cta_sum_c(s);  // (its barriers also publish sx)
+  if (tid == 0) {
+    const S alpha = sx[j + 1];
+    double beta;
+    S tj = mk<S>(0.0, 0.0), vs = mk<S>(0.0, 0.0);
+    if (s == 0.0 && im(alpha) == 0.0) {
+      beta = re(alpha);  // nothing to annihilate: H = I
+    } else {
+      const double an = sqrt(abs2_acc(alpha, s));
+      beta = re(alpha) >= 0.0 ? -an : an;
+      const double rb = 1.0 / beta;
+      tj = mk<S>((beta - re(alpha)) * rb, -im(alpha) * rb);
+      vs = cinv(csub(alpha, mk<S>(beta, 0.0)));  // v_i = x_i / (alpha - beta)
+    }
+    s_tau = tj;
+    s_vs = vs;
+    if (writer) {
+      ve(P)[j] = beta;
+      vtau(P)[j] = tj;
+    }
+  }
+  __syncthreads();
+  const S vs = s_vs, tj = s_tau;
+  S* __restrict__ rj = P.R + (size_t)j * n;
+  for (int i = j + 1 + tid; i < n; i += blockDim.x) {
+    const S v = i == j + 1 ? mk<S>(1.0, 0.0) : cmul(sx[i], vs);
+    sx[i] = v;
+    if (writer) rj[i] = v;
+  }
+  __syncthreads();
+  return tj;
+}
+
+// One team barrier per column.  Step j applies reflector j (v_j, tau_j, and p_j = tau_j C v_j from
+// the previous step) to the trailing matrix: gamma = -(tau_j / 2) p_j^H v_j, w = p_j + gamma v_j,
+// C <- C - v w^H - w v^H.  Every CTA forms column j+1 of the updated matrix and reflector j+1 from
+// it in shared memory (the same values in every CTA), then each warp updates its columns k >= j+2
+// and, in the same pass over the column, accumulates p_{j+1}[k] = tau_{j+1} (column k)^H v_{j+1}
+// (C is Hermitian, so that is row k of C v_{j+1}).  Rows < j+2 of those columns are never read
+// again and are not updated.  p of consecutive steps alternate between two buffers, so that a
+// CTA still reading p_j never meets the p_{j+1} that faster CTAs write.
+// sbuf: 3 n words of S of shared memory per CTA (v_j, w and v_{j+1}, indexed by row).
 template <class Team, class S>
-__device__ bool tridiagonalise(const Team& T, const Pencil<S>& P, S* sv) {
+__device__ bool tridiagonalise(const Team& T, const Pencil<S>& P, S* sbuf) {
   const int n = P.n, la = P.lda;
   S* A = P.A;
-  S* __restrict__ p = vp(P);
-  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const bool writer = T.rank() < (int)blockDim.x;  // the first CTA writes d, e, tau and R
   if (n == 1) {
     if (T.rank() == 0) vd(P)[0] = re(A[0]);
     return T.sync();
   }
-  S* sw = sv + n;
-  if (T.wrank() == 0) make_reflector(P, 0);
-  if (!T.sync()) return false;
-  for (int j = 0; j < n - 1; ++j) {
-    const S tj = vtau(P)[j];
-    const S* __restrict__ rj = P.R + (size_t)j * n;
-    const int m = n - j - 1;
-    // p_i = tau sum_k conj(A[k][i]) v_k over the trailing block (column i of A is row i of A^H)
-    for (int i = j + 1 + T.wrank(); i < n; i += T.wsize()) {
-      const S* __restrict__ ci = A + (size_t)i * la;
-      S s = mk<S>(0.0, 0.0);
-      for (int k = j + 1 + lane; k < n; k += 32) s = cfmac(ci[k], rj[k], s);
-      s = warp_sum_c(s);
-      if (lane == 0) p[i] = cmul(tj, s);
+  S* sv = sbuf;
+  S* sw = sbuf + n;
+  S* sn = sbuf + 2 * n;
+  // reflector 0 from column 0, and p_0 = tau_0 C v_0 (rows 1..n-1)
+  for (int i = 1 + tid; i < n; i += blockDim.x) sv[i] = A[i];
+  if (writer && tid == 0) vd(P)[0] = re(A[0]);
+  S tau = cta_reflector(P, 0, sv, writer);
+  {
+    S* __restrict__ p0 = vp(P);
+    for (int k = 1 + T.swrank(); k < n; k += T.wsize()) {
+      const S* __restrict__ ck = A + (size_t)k * la;
+      S acc = mk<S>(0.0, 0.0);
+      for (int i = 1 + lane; i < n; i += 32) acc = cfmac(ck[i], sv[i], acc);
+      acc = warp_sum_c(acc);
+      if (lane == 0) p0[k] = cmul(tau, acc);
     }
-    if (!T.sync()) return false;
-    // gamma = -(tau/2) p^H v (each CTA reduces it in the same order); v and w = p + gamma v staged
-    S g = mk<S>(0.0, 0.0);
-    for (int t = threadIdx.x; t < m; t += blockDim.x) g = cfmac(p[j + 1 + t], rj[j + 1 + t], g);
-    g = cta_sum_c(g);
-    const S gamma = cscale(cmul(tj, g), -0.5);
-    for (int t = threadIdx.x; t < m; t += blockDim.x) {
-      const S v = rj[j + 1 + t];
-      sv[t] = v;
-      sw[t] = cfma(gamma, v, p[j + 1 + t]);
-    }
-    __syncthreads();
-    // A <- A - v w^H - w v^H on the trailing block
-    for (int k = j + 1 + T.wrank(); k < n; k += T.wsize()) {
-      const S cvk = conjd(sv[k - j - 1]), cwk = conjd(sw[k - j - 1]);
-      S* __restrict__ ck = A + (size_t)k * la;
-      int i = j + 1 + lane;
-      for (; i + 96 < n; i += 128) {
-        S a[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = ck[i + 32 * u];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int t = i + 32 * u - j - 1;
-          ck[i + 32 * u] = cfms(sw[t], cvk, cfms(sv[t], cwk, a[u]));
-        }
-      }
-      for (; i < n; i += 32) {
-        const int t = i - j - 1;
-        ck[i] = cfms(sw[t], cvk, cfms(sv[t], cwk, ck[i]));
-      }
-      if (k == j + 1 && j + 1 < n - 1) {  // the next reflector, from the column just updated
-        __syncwarp();
-        make_reflector(P, j + 1);
-      }
-    }
-    if (!T.sync()) return false;
   }
-  if (T.rank() == 0) vd(P)[n - 1] = re(A[(n - 1) + (size_t)(n - 1) * la]);
-  return T.sync();
+  if (!T.sync()) return false;
+  for (int j = 0; j <= n - 2; ++j) {
+    const S* __restrict__ pj = vp(P) + (size_t)(j & 1) * n;
+    S* __restrict__ pn = vp(P) + (size_t)((j + 1) & 1) * n;
+    // p_j and column j+1 of C are read together (one round trip to L2), staged raw in sw and sn;
+    // then w = p_j + gamma v_j and column j+1 of the updated matrix, x - v conj(w_{j+1}) - w (the
+    // entry of v_j in row j+1 is 1), each thread on its own rows
+    const S* __restrict__ c1 = A + (size_t)(j + 1) * la;
+    S g = mk<S>(0.0, 0.0);
+    for (int i = j + 1 + tid; i < n; i += blockDim.x) {
+      const S pi = pj[i];
+      sn[i] = c1[i];
+      sw[i] = pi;
+      g = cfmac(pi, sv[i], g);
+    }
+    g = cta_sum_c(g);
+    const S gamma = cscale(cmul(tau, g), -0.5);
+    const S cw1 = conjd(cadd(pj[j + 1], gamma));
+    for (int i = j + 1 + tid; i < n; i += blockDim.x) {
+      const S wi = cfma(gamma, sv[i], sw[i]);
+      const S x = csub(cfms(sv[i], cw1, sn[i]), wi);
+      sw[i] = wi;
+      sn[i] = x;
+      if (i == j + 1 && writer) vd(P)[j + 1] = re(x);
+    }
+    if (j + 1 <= n - 2) {
+      const S tn = cta_reflector(P, j + 1, sn, writer);
+      // columns k >= j+2: rank-2 update of rows j+2..n-1 fused with p_{j+1}[k]
+      for (int k = j + 2 + T.swrank(); k < n; k += T.wsize()) {
+        const S cvk = conjd(sv[k]), cwk = conjd(sw[k]);
+        S* __restrict__ ck = A + (size_t)k * la;
+        S acc = mk<S>(0.0, 0.0);
+        int i = j + 2 + lane;
+        for (; i + 96 < n; i += 128) {
+          S a[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a[u] = ck[i + 32 * u];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = i + 32 * u;
+            a[u] = cfms(sw[r], cvk, cfms(sv[r], cwk, a[u]));
+            ck[r] = a[u];
+            acc = cfmac(a[u], sn[r], acc);
+          }
+        }
+        for (; i < n; i += 32) {
+          const S a = cfms(sw[i], cvk, cfms(sv[i], cwk, ck[i]));
+          ck[i] = a;
+          acc = cfmac(a, sn[i], acc);
+        }
+        acc = warp_sum_c(acc);
+        if (lane == 0) pn[k] = cmul(tn, acc);
+      }
+      tau = tn;
+    }
+    if (!T.sync()) return false;
+    S* t = sv;  // v_{j+1} becomes the current reflector
+    sv = sn;
+    sn = t;
+  }
+  return true;
 }
 
 // ---- phase 4: eigenpairs of the symmetric tridiagonal T (d, e) -----------------------------------
-// Number of eigenvalues of T below s (Sturm count of the LDL^T pivots of T - s I); e2 = e^2.
+// Number of eigenvalues of T below s, from the signs of the leading principal minors p_i of
+// T - s I (a Sturm sequence): p_0 = 1, p_1 = d_0 - s, p_{i+1} = (d_i - s) p_i - e_{i-1}^2 p_{i-1};
+// the count is the number of sign changes between consecutive minors, i.e. of negative pivots
+// p_{i+1} / p_i of the LDL^T factorisation (Sylvester's law of inertia).  Division-free: one fused
+// multiply-add per row on the dependent chain (an FP64 division has about seven times the latency
+// of a fused multiply-add on GB300, where that latency is already 64 cycles).  The pair
+// (p_i, p_{i+1}) is rescaled by an exact power of two when p_{i+1} leaves [2^-600, 2^600]; an
+// exactly zero minor is replaced by -2^-600 times the previous one (a tiny negative pivot, the
+// guard of the pivot form), which also carries the sequence across a split (e_i = 0).  e2 = e^2.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// |x| as an integer: ordered like |x| for all non-NaN doubles
+__device__ __forceinline__ unsigned long long dmag(double x) {
+  return (unsigned long long)dbits(x) & 0x7FFFFFFFFFFFFFFFull;
+}
 __device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int n,
-                                           double s, double pivmin) {
-  int c = 0;
-  double q = d[0] - s;
-  if (fabs(q) < pivmin) q = -pivmin;
-  c += q < 0.0;
+                                           double s) {
+  double pm = 1.0, p = d[0] - s;
+  if (((unsigned long long)dbits(p) << 1) == 0) p = -0x1p-600;
+  int c = (int)((unsigned long long)dbits(p) >> 63);
   for (int i = 1; i < n; ++i) {
-    q = (d[i] - s) - e2[i - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    c += q < 0.0;
+    double pn = fma(d[i] - s, p, -e2[i - 1] * pm);
+    if (((unsigned long long)dbits(pn) << 1) == 0) pn = -0x1p-600 * p;
+    c += (int)((unsigned long long)(dbits(pn) ^ dbits(p)) >> 63);
+    pm = p;
+    p = pn;
+    const int ex = (int)((dbits(p) >> 52) & 0x7FF);  // biased exponent of |p|
+    if (ex > 1023 + 600) {
+      p *= 0x1p-600;
+      pm *= 0x1p-600;
+    } else if (ex < 1023 - 600 && (int)((dbits(pm) >> 52) & 0x7FF) < 1023 + 400) {
+      p *= 0x1p+600;
+      pm *= 0x1p+600;
+    }
   }
   return c;
 }
@@ -614,72 +689,96 @@ __device__ bool tridiagonal_eig(const Team& T, const Pencil<S>& P) {
     e232[i] = (float)(ei * ei);
   }
   // norms and Gershgorin interval (every thread computes them the same way)
-  double tn = 0.0, gl = 0.0, gu = 0.0, emax2 = 0.0;
+  double tn = 0.0, glo = 0.0, gu = 0.0, emax2 = 0.0;
   for (int i = 0; i < n; ++i) {
     const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
     tn = fmax(tn, fabs(d[i]) + r);
-    gl = i ? fmin(gl, d[i] - r) : d[i] - r;
+    glo = i ? fmin(glo, d[i] - r) : d[i] - r;
     gu = i ? fmax(gu, d[i] + r) : d[i] + r;
     if (i < n - 1) emax2 = fmax(emax2, e[i] * e[i]);
   }
   const double eps = 2.220446049250313e-16;
   const double pivmin = 2.2250738585072014e-308 * fmax(1.0, emax2);
   tn = fmax(tn, 1e-300);
-  gl -= 2.0 * eps * tn + 2.0 * pivmin;
+  glo -= 2.0 * eps * tn + 2.0 * pivmin;
   gu += 2.0 * eps * tn + 2.0 * pivmin;
   if (!T.sync()) return false;
-  // Eigenvalue k by multisection, one warp per eigenvalue: in every round the 32 lanes count at 32
-  // interior points of the bracket [lo, hi] (count(lo) <= k < count(hi)) and the bracket shrinks
-  // to the 1/33 between the last point below eigenvalue k and the first above it, so a FP64
-  // Sturm count (a chain of dependent divisions, slow on GB300) is needed only ~7 times in
-  // sequence.  The bracket is first narrowed with FP32 counts to 1e-6 |T|, widened by 2e-6 |T|
-  // and accepted only if the FP64 counts at both ends confirm it (else the Gershgorin interval is
-  // used).
+  // Eigenvalue k by multisection, one group of kSect lanes per eigenvalue (32 / kSect eigenvalues
+  // per warp): in every round the group's lanes count at kSect interior points of the bracket
+  // [lo, hi] (count(lo) <= k < count(hi)) and the bracket shrinks to the 1/(kSect+1) between the
+  // last point below eigenvalue k and the first above it.  The bracket is first narrowed with FP32
+  // counts (about 64 times cheaper than FP64 on GB300) to 1e-6 |T|, widened by 2e-6 |T| and
+  // accepted only if the FP64 counts at both ends confirm it (else the Gershgorin interval is
+  // used); FP64 rounds then take it to 2 eps |lambda|.  The rounds are a sequence of dependent
+  // Sturm counts, so the lane groups trade a few times more FP64 work than plain bisection for a
+  // sequence about three times shorter.
   const float pivmin32 = 1e-30f * (float)fmax(1.0, emax2);
   const int lane = threadIdx.x & 31;
-  if (T.wsize() >= n) {
-    for (int k = T.swrank(); k < n; k += T.wsize()) {
-      float l32 = (float)gl, h32 = (float)gu;
+  constexpr int kSect = 8, kGroups = 32 / kSect;
+  if (T.wsize() * kGroups >= n) {
+    const int grp = lane / kSect, gi = lane % kSect;
+    const unsigned gmask = ((1u << kSect) - 1u) << (grp * kSect);
+    for (int k0 = T.swrank() * kGroups; k0 < n; k0 += T.wsize() * kGroups) {
+      const int k = k0 + grp;
+      const bool act = k < n;
+      float l32 = (float)glo, h32 = (float)gu;
       const float wid = (float)(1e-6 * tn);
-      for (int it = 0; it < 12 && h32 - l32 > wid; ++it) {
-        const float step = (h32 - l32) * (1.0f / 33.0f);
-        const float pt = l32 + (float)(lane + 1) * step;
-        const unsigned above = __ballot_sync(0xffffffffu, pt < h32 && sturm_count32(d32, e232, n, pt, pivmin32) > k);
-        const int f = above ? __ffs(above) - 1 : 32;
-        const float nl = f == 0 ? l32 : l32 + (float)f * step;
-        const float nh = f == 32 ? h32 : l32 + (float)(f + 1) * step;
-        if (!(nh > nl)) break;
-        l32 = nl;
-        h32 = fminf(nh, h32);
+      bool open = act;
+      for (int it = 0; it < 16; ++it) {
+        open = open && h32 - l32 > wid;
+        if (!__any_sync(0xffffffffu, open)) break;
+        const float step = (h32 - l32) * (1.0f / (float)(kSect + 1));
+        const float pt = l32 + (float)(gi + 1) * step;
+        const bool above = open && pt < h32 && sturm_count32(d32, e232, n, pt, pivmin32) > k;
+        const unsigned bits = (__ballot_sync(0xffffffffu, above) & gmask) >> (grp * kSect);
+        const int f = bits ? __ffs(bits) - 1 : kSect;
+        if (open) {
+          const float nl = f == 0 ? l32 : l32 + (float)f * step;
+          const float nh = f == kSect ? h32 : l32 + (float)(f + 1) * step;
+          if (nh > nl) {
+            l32 = nl;
+            h32 = fminf(nh, h32);
+          } else {
+            open = false;
+          }
+        }
       }
-      double lo = fmax(gl, (double)l32 - 2e-6 * tn), hi = fmin(gu, (double)h32 + 2e-6 * tn);
+      double lo = fmax(glo, (double)l32 - 2e-6 * tn), hi = fmin(gu, (double)h32 + 2e-6 * tn);
       {
-        const int c = lane == 0 ? sturm_count(d, e2, n, lo, pivmin) : (lane == 1 ? sturm_count(d, e2, n, hi, pivmin) : 0);
-        const int c0 = __shfl_sync(0xffffffffu, c, 0), c1 = __shfl_sync(0xffffffffu, c, 1);
+        const int c = !act ? 0 : gi == 0 ? sturm_count(d, e2, n, lo) : (gi == 1 ? sturm_count(d, e2, n, hi) : 0);
+        const int c0 = __shfl_sync(0xffffffffu, c, grp * kSect), c1 = __shfl_sync(0xffffffffu, c, grp * kSect + 1);
         if (!(c0 <= k && c1 > k)) {
-          lo = gl;
+          lo = glo;
           hi = gu;
         }
       }
-      for (int it = 0; it < 40; ++it) {
-        if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin) break;
-        const double step = (hi - lo) * (1.0 / 33.0);
-        const double pt = lo + (double)(lane + 1) * step;
-        const unsigned above = __ballot_sync(0xffffffffu, pt < hi && sturm_count(d, e2, n, pt, pivmin) > k);
-        const int f = above ? __ffs(above) - 1 : 32;
-        const double nl = f == 0 ? lo : lo + (double)f * step;
-        const double nh = f == 32 ? hi : lo + (double)(f + 1) * step;
-        if (!(nh > nl) || (nl == lo && nh >= hi)) break;
-        lo = nl;
-        hi = fmin(nh, hi);
+      open = act;
+      for (int it = 0; it < 64; ++it) {
+        open = open && !(hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin);
+        if (!__any_sync(0xffffffffu, open)) break;
+        const double step = (hi - lo) * (1.0 / (double)(kSect + 1));
+        const double pt = lo + (double)(gi + 1) * step;
+        const bool above = open && pt < hi && sturm_count(d, e2, n, pt) > k;
+        const unsigned bits = (__ballot_sync(0xffffffffu, above) & gmask) >> (grp * kSect);
+        const int f = bits ? __ffs(bits) - 1 : kSect;
+        if (open) {
+          const double nl = f == 0 ? lo : lo + (double)f * step;
+          const double nh = f == kSect ? hi : lo + (double)(f + 1) * step;
+          if (!(nh > nl) || (nl == lo && nh >= hi)) {
+            open = false;
+          } else {
+            lo = nl;
+            hi = fmin(nh, hi);
+          }
+        }
       }
-      if (lane == 0) w[k] = 0.5 * (lo + hi);
+      if (act && gi == 0) w[k] = 0.5 * (lo + hi);
     }
   } else {
     // fewer warps than eigenvalues (one CTA per pencil): plain bisection, one thread per
     // eigenvalue, with the same FP32 narrowing and FP64 confirmation of the bracket
     for (int k = T.srank(); k < n; k += T.size()) {
-      float l32 = (float)gl, h32 = (float)gu;
+      float l32 = (float)glo, h32 = (float)gu;
       const float wid = (float)(1e-5 * tn);
       for (int it = 0; it < 64 && h32 - l32 > wid; ++it) {
         const float mid = 0.5f * (l32 + h32);
@@ -687,32 +786,38 @@ __device__ bool tridiagonal_eig(const Team& T, const Pencil<S>& P) {
         if (sturm_count32(d32, e232, n, mid, pivmin32) > k) h32 = mid;
         else l32 = mid;
       }
-      double lo = fmax(gl, (double)l32 - 1e-5 * tn), hi = fmin(gu, (double)h32 + 1e-5 * tn);
-      if (!(sturm_count(d, e2, n, lo, pivmin) <= k && sturm_count(d, e2, n, hi, pivmin) > k)) {
-        lo = gl;
+      double lo = fmax(glo, (double)l32 - 1e-5 * tn), hi = fmin(gu, (double)h32 + 1e-5 * tn);
+      if (!(sturm_count(d, e2, n, lo) <= k && sturm_count(d, e2, n, hi) > k)) {
+        lo = glo;
         hi = gu;
       }
       for (int it = 0; it < 200; ++it) {
         const double mid = 0.5 * (lo + hi);
         if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin || mid <= lo || mid >= hi) break;
-        if (sturm_count(d, e2, n, mid, pivmin) > k) hi = mid;
+        if (sturm_count(d, e2, n, mid) > k) hi = mid;
         else lo = mid;
       }
       w[k] = 0.5 * (lo + hi);
     }
   }
   if (!T.sync()) return false;
+  T.stamp(4);
   // eigenvectors by inverse iteration, one cluster per thread
   const double ortol = 1e-5 * tn;
   const double tiny = eps * tn;
   const size_t nn = (size_t)n * n;
-  double* ua = P.wk;           // reciprocals of U's diagonal
-  double* ub = P.wk + nn;      // U first superdiagonal
-  double* uc = P.wk + 2 * nn;  // U second superdiagonal (fill-in of row swaps)
-  double* ml = P.wk + 3 * nn;  // multipliers
-  double* sw = P.wk + 4 * nn;  // 1: rows i, i+1 swapped
-  double* x = P.wk + 5 * nn;   // iterate
-  for (int k0 = T.srank(); k0 < n; k0 += T.size()) {
+  // (separate input and output arrays in every sweep, so that the loads of later rows can be
+  // issued ahead of the dependent arithmetic)
+  double* __restrict__ ua = P.wk;           // reciprocals of U's diagonal
+  double* __restrict__ ub = P.wk + nn;      // U first superdiagonal
+  double* __restrict__ uc = P.wk + 2 * nn;  // U second superdiagonal (fill-in of row swaps)
+  double* __restrict__ ml = P.wk + 3 * nn;  // multipliers
+  double* __restrict__ sw = P.wk + 4 * nn;  // 1: rows i, i+1 swapped
+  double* __restrict__ x = P.wk + 5 * nn;   // iterate
+  double* __restrict__ y = P.wk + 6 * nn;   // L^{-1} P x
+  // 32 consecutive eigenvalues per warp (the interleaved arrays are then read in full 256-byte
+  // rows), the warps spread over the CTAs
+  for (int k0 = T.swrank() * 32 + (threadIdx.x & 31); k0 < n; k0 += T.size()) {
     if (k0 > 0 && w[k0] - w[k0 - 1] <= ortol) continue;  // not the first of its cluster
     int k1 = k0 + 1;
     while (k1 < n && w[k1] - w[k1 - 1] <= ortol) ++k1;
@@ -731,9 +836,10 @@ __device__ bool tridiagonal_eig(const Team& T, const Pencil<S>& P) {
           const double nd = d[i + 1] - s;
           const double ns = i + 1 < n - 1 ? e[i + 1] : 0.0;
           const size_t o = (size_t)i * n + m;
-          // ua holds the reciprocal pivot: one division per row, none in the solves
-          if (fabs(a) >= fabs(sub)) {
-            if (a == 0.0) a = tiny;
+          // ua holds the reciprocal pivot: one division per row, none in the solves; the pivot
+          // choice compares magnitudes as integers (the FP64 compare would add 64 cycles a row)
+          if (dmag(a) >= dmag(sub)) {
+            if (dmag(a) == 0) a = tiny;
             const double r = 1.0 / a;
             const double l = sub * r;
             ua[o] = r;
@@ -755,42 +861,48 @@ __device__ bool tridiagonal_eig(const Team& T, const Pencil<S>& P) {
             b = -l * ns;
           }
         }
-        if (a == 0.0) a = tiny;
+        if (dmag(a) == 0) a = tiny;
         ua[(size_t)(n - 1) * n + m] = 1.0 / a;
       }
       for (int i = 0; i < n; ++i) x[(size_t)i * n + m] = start_entry(m, i);
       const int iters = (k1 - k0 > 1) ? 4 : 3;
       for (int it = 0; it < iters; ++it) {
-        // forward: apply the row operations of the factorisation (the running row in a register)
+        // forward: y = L^{-1} P x, the row operations of the factorisation (running row in a register)
         {
           double cur = x[m];
+#pragma unroll 4
           for (int i = 0; i < n - 1; ++i) {
             const size_t o = (size_t)i * n + m;
             double nxt = x[o + n];
-            if (sw[o] != 0.0) {
+            if (dmag(sw[o]) != 0) {
               const double t = cur;
               cur = nxt;
               nxt = t;
             }
-            x[o] = cur;
-            cur = nxt - ml[o] * cur;
+            y[o] = cur;
+            cur = fma(-ml[o], cur, nxt);
           }
-          x[(size_t)(n - 1) * n + m] = cur;
+          y[(size_t)(n - 1) * n + m] = cur;
         }
-        // backward with U (the two solved rows below in registers; scaled when the iterate grows)
+        // backward: x = U^{-1} y (the two solved rows below in registers; the iterate and the rows
+        // still to solve are scaled down together when it grows)
         {
           double x1 = 0.0, x2 = 0.0;
+#pragma unroll 4
           for (int i = n - 1; i >= 0; --i) {
             const size_t o = (size_t)i * n + m;
-            double v = x[o];
-            if (i + 1 < n) v -= ub[o] * x1;
-            if (i + 2 < n) v -= uc[o] * x2;
+            double v = y[o];
+            if (i + 2 < n) v = fma(-uc[o], x2, v);
+            if (i + 1 < n) v = fma(-ub[o], x1, v);
             v *= ua[o];
             x[o] = v;
             x2 = x1;
             x1 = v;
-            if (fabs(v) > 1e100) {
-              for (int r = 0; r < n; ++r) x[(size_t)r * n + m] *= 1e-100;
+            if (dmag(v) > dmag(1e100)) {
+              for (int r = 0; r < n; ++r) {
+                x[(size_t)r * n + m] *= 1e-100;
+                y[(size_t)r * n + m] *= 1e-100;
+              }
               x1 *= 1e-100;
               x2 *= 1e-100;
             }
@@ -803,12 +915,21 @@ __device__ bool tridiagonal_eig(const Team& T, const Pencil<S>& P) {
           for (int i = 0; i < n; ++i) s2 += zq[i] * x[(size_t)i * n + m];
           for (int i = 0; i < n; ++i) x[(size_t)i * n + m] -= s2 * zq[i];
         }
-        double nrm = 0.0;
-        for (int i = 0; i < n; ++i) {
-          const double v = x[(size_t)i * n + m];
-          nrm += v * v;
+        double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;  // four independent chains
+        int i = 0;
+        for (; i + 3 < n; i += 4) {
+          const double v0 = x[(size_t)i * n + m], v1 = x[(size_t)(i + 1) * n + m];
+          const double v2 = x[(size_t)(i + 2) * n + m], v3 = x[(size_t)(i + 3) * n + m];
+          n0 = fma(v0, v0, n0);
+          n1 = fma(v1, v1, n1);
+          n2 = fma(v2, v2, n2);
+          n3 = fma(v3, v3, n3);
         }
-        nrm = sqrt(nrm);
+        for (; i < n; ++i) {
+          const double v = x[(size_t)i * n + m];
+          n0 = fma(v, v, n0);
+        }
+        const double nrm = sqrt((n0 + n1) + (n2 + n3));
         const double r = nrm > 0.0 ? 1.0 / nrm : 0.0;
         for (int i = 0; i < n; ++i) x[(size_t)i * n + m] *= r;
       }
@@ -825,7 +946,7 @@ __device__ bool back_transform(const Team& T, const Pencil<S>& P, S* smem) {
   const int n = P.n;
   const int lane = threadIdx.x & 31;
   const S* tau = vtau(P);
-  for (int c = T.wrank(); c < n; c += T.wsize()) {
+  for (int c = T.swrank(); c < n; c += T.wsize()) {
     // The column is built in this warp's shared-memory slot when the launch provided one, else in
     // place in A's column c (A is free: the reflectors live in R, L in B).
     S* ac = P.A + (size_t)c * P.lda;
@@ -840,9 +961,9 @@ __device__ bool back_transform(const Team& T, const Pencil<S>& P, S* smem) {
       const S* __restrict__ rj = P.R + (size_t)j * n;
       const int r0 = j + 1 + ((lane - j - 1) & 31);
       S s = mk<S>(0.0, 0.0);
-      for (int i = r0; i < n; i += 32) s = cadd(s, cmulc(rj[i], vc[i]));
+      for (int i = r0; i < n; i += 32) s = cfmac(rj[i], vc[i], s);
       s = cmul(tj, warp_sum_c(s));
-      for (int i = r0; i < n; i += 32) vc[i] = csub(vc[i], cmul(rj[i], s));
+      for (int i = r0; i < n; i += 32) vc[i] = cfms(rj[i], s, vc[i]);
     }
     __syncwarp();
     backward_subst_h(P.B, vrdiag(P), P.ldb, n, vc);
@@ -861,23 +982,29 @@ __device__ void solve_pencil(const Team& T, const Pencil<S>& P) {
   S* smem = reinterpret_cast<S*>(dyn_smem);
   if (T.rank() == 0) *P.info = 0;
   if (P.n <= 0) return;
+  T.stamp(0);
   if (!prepare(T, P)) return;
   if (!cholesky(T, P)) return;
+  T.stamp(1);
   if (!reduce_standard(T, P)) return;
+  T.stamp(2);
   if (!tridiagonalise(T, P, smem)) return;
+  T.stamp(3);
   if (!tridiagonal_eig(T, P)) return;
+  T.stamp(5);
   if (!back_transform(T, P, P.smem_cols ? smem : nullptr)) return;
   finish(T, P);
+  T.stamp(6);
 }
 
 template <class S>
-__global__ void __launch_bounds__(kThreads) hegv_grid_kernel(Pencil<S> P, Ctl* ctl, unsigned long long limit_ns) {
+__global__ void __launch_bounds__(kThreads, 2) hegv_grid_kernel(Pencil<S> P, Ctl* ctl, unsigned long long limit_ns) {
   GridTeam T{ctl, P.info, limit_ns};
   solve_pencil(T, P);
 }
 
 template <class S>
-__global__ void __launch_bounds__(kThreads) hegv_cta_kernel(const Pencil<S>* __restrict__ items, int count) {
+__global__ void __launch_bounds__(kThreads, 2) hegv_cta_kernel(const Pencil<S>* __restrict__ items, int count) {
   if ((int)blockIdx.x >= count) return;
   const Pencil<S> P = items[blockIdx.x];
   CtaTeam T;
@@ -887,11 +1014,11 @@ __global__ void __launch_bounds__(kThreads) hegv_cta_kernel(const Pencil<S>* __r
 size_t pad32(size_t x) { return (x + 31) & ~(size_t)31; }
 
 // Workspace doubles of one pencil, each array padded to 32 doubles: complex, R (complex n^2);
-// real, the compact A, B and R (n^2 each); then Z (n^2), wk (6 n^2) and vec (9 n + 8).
+// real, the compact A, B and R (n^2 each); then Z (n^2), wk (7 n^2) and vec (11 n + 8).
 size_t work_doubles(int n, bool real) {
   const size_t nn = (size_t)n * n;
   const size_t own = real ? 3 * pad32(nn) : pad32(2 * nn);
-  return own + pad32(nn) + pad32(6 * nn) + pad32(9 * (size_t)n + 8);
+  return own + pad32(nn) + pad32(7 * nn) + pad32(11 * (size_t)n + 8);
 }
 
 template <class S>
@@ -922,7 +1049,7 @@ Pencil<S> make_pencil(double2* A, int lda, double2* B, int ldb, double* w, int* 
   }
   P.Z = rest;
   P.wk = P.Z + pad32(nn);
-  P.vec = P.wk + pad32(6 * nn);
+  P.vec = P.wk + pad32(7 * nn);
   P.smem_cols = 0;
   return P;
 }
@@ -930,14 +1057,14 @@ Pencil<S> make_pencil(double2* A, int lda, double2* B, int ldb, double* w, int* 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per grid-barrier wait
 constexpr int kGridMinN = 160;  // pencils at least this large run on a cooperative grid
 
-// Dynamic shared memory: 2 n words of S for the tridiagonalisation's v and w, and, when it fits in
-// 200 KB, one column of n words of S per warp for the back-transformation.
+// Dynamic shared memory: 3 n words of S for the tridiagonalisation's v_j, w and v_{j+1}, and, when
+// it fits in 200 KB, one column of n words of S per warp for the back-transformation.
 size_t col_smem_bytes(int n, size_t ws) {
   const size_t b = (size_t)kWarps * (size_t)std::max(n, 1) * ws;
   return b <= 200u * 1024u ? b : 0;
 }
-size_t dyn_smem_bytes(int n, size_t ws) { return std::max(col_smem_bytes(n, ws), (size_t)2 * std::max(n, 1) * ws); }
-constexpr int kMaxN = 6000;  // 2 n complex words must fit in shared memory
+size_t dyn_smem_bytes(int n, size_t ws) { return std::max(col_smem_bytes(n, ws), (size_t)3 * std::max(n, 1) * ws); }
+constexpr int kMaxN = 4608;  // 3 n complex words must fit in shared memory (221 KB)
 
 template <class S>
 void launch_cta(kss_ctx ctx, std::vector<Pencil<S>>& small, size_t items_offset, const char* name) {
@@ -1052,5 +1179,27 @@ extern "C" kss_status kss_dense_hegv(kss_ctx ctx, int count, const int* n, void*
   } catch (...) {
     ctx->err = "unexpected internal error";
     return KSS_ECUDA;
+  }
+}
+
+extern "C" kss_status kss_dense_hegv_phase_ms(kss_ctx ctx, double* ms) {
+  if (!ctx || !ms) return KSS_EINVAL;
+  try {
+    for (int k = 0; k < 6; ++k) ms[k] = 0.0;
+    if (!ctx->dense_ctl.p) {
+      ctx->err.clear();
+      return KSS_OK;
+    }
+    KSS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    Ctl c;
+    KSS_CHECK_CUDA(cudaMemcpyAsync(&c, ctx->dense_ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    KSS_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (c.t[6] > c.t[0])
+      for (int k = 0; k < 6; ++k) ms[k] = c.t[k + 1] > c.t[k] ? 1e-6 * (double)(c.t[k + 1] - c.t[k]) : 0.0;
+    ctx->err.clear();
+    return KSS_OK;
+  } catch (const KssError& e) {
+    ctx->err = e.msg;
+    return e.st;
   }
 }

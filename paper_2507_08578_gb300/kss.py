@@ -121,6 +121,7 @@ def signatures() -> dict:
         "kss_chebfi_solve": ([P, c_int, c_int, POINTER(kss_solve_opts), P, P, c_int, P,
                               POINTER(kss_solve_stats)], c_int),
         "kss_dense_hegv": ([P, c_int, P, P, P, P, P, P, P, c_int], c_int),
+        "kss_dense_hegv_phase_ms": ([P, P], c_int),
         "kss_autotune_gemm_count": ([P], c_int),
         "kss_autotune_gemm_get": ([c_int, P], c_int),
         "kss_autotune_gemm_put": ([P], c_int),
@@ -618,6 +619,16 @@ def kss_dense_hegv(ctx, As, Bs, ws, real: bool = False):
     info = (c_int * count)()
     _check(lib().kss_dense_hegv(ctx, count, n, pa, lda, pb, ldb, pw, info, 1 if real else 0), ctx)
     return np.array(list(info), dtype=np.int32)
+
+
+DENSE_PHASES = ("cholesky", "reduce", "tridiagonalise", "bisection", "inverse_iteration", "back_transform")
+
+
+def kss_dense_hegv_phase_ms(ctx) -> dict:
+    """{phase: ms} of the last grid-team (order >= 160) dense eigensolve of the context."""
+    ms = (c_double * 6)()
+    _check(lib().kss_dense_hegv_phase_ms(ctx, ms), ctx)
+    return dict(zip(DENSE_PHASES, list(ms)))
 
 
 class kss_gemm_tune_entry(ctypes.Structure):
