@@ -160,6 +160,7 @@ struct kss_sys_s {
   kss::DevBuf d_tw64[3], d_tw32[3];// e^{-2 pi i k/N_d}, k < N_d
   kss::DevBuf d_D64, d_D32;
   std::map<int, kss::DevBuf> vpi64, vpi32;  // V/N^3 as [x][z][p] per split code A*32+B (lazy)
+  std::map<int, kss::DevBuf> vfused32;       // V/N^3 in the fused kernel's digit-reversed order (lazy)
   bool has_S = false;              // generalised problem: S = 1 + sum_i |beta_i> q_i <beta_i|
   std::vector<double> Q;           // overlap coefficients (nproj), empty without an overlap
   kss::DevBuf d_Q64, d_Q32;

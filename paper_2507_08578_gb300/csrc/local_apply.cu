@@ -23,6 +23,7 @@
 // The slab lives in a workspace of nc bands (chunked so that it stays L2-resident).
 #include <algorithm>
 
+#include "local_fused.h"
 #include "local_kernels.cuh"
 #include "density.h"
 #include "local_wide.h"
@@ -463,6 +464,23 @@ LocalArgs<T> local_args(kss_sys s, int ik, const void* psi, const void* psi_prev
   return a;
 }
 
+// Gamma point: unpack the pair transforms in the context's pair workspace and finish the epilogue.
+template <typename T>
+void gamma_finish(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, void* out, int ld,
+                  ChebCoef c) {
+  using C = typename CT<T>::C;
+  const bool f64 = sizeof(T) == 8;
+  kss_ctx ctx = s->ctx;
+  const KData& kd = s->k[ik];
+  static const int idu = prof_register(f64 ? "gamma_unpack<f64>" : "gamma_unpack<f32>");
+  ProfScope ps(ctx, idu);
+  const long long n = (long long)kd.npw * nb;
+  const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 32);
+  gamma_unpack<C, T><<<blocks, 256, 0, ctx->stream>>>(
+      ctx->ws_gpack.as<C>(), ld, kd.d_mirror.as<int>(), (const C*)psi, (const C*)psi_prev, (C*)out,
+      (const T*)(f64 ? kd.d_kin64.p : kd.d_kin32.p), kd.npw, nb, (T)c.alpha, (T)c.beta, (T)c.gamma);
+}
+
 template <typename T>
 void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, void* out,
                int ld, ChebCoef c) {
@@ -470,6 +488,27 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
   const bool f64 = sizeof(T) == 8;
   kss_ctx ctx = s->ctx;
   LocalArgs<T> a = local_args<T>(s, ik, psi, psi_prev, out, ld, c);
+  if constexpr (sizeof(T) == 4) {
+    // small cubic boxes: the whole local part in one kernel (local_fused.cu)
+    if (fused_local_available(s)) {
+      const bool packed = c.packed && s->k[ik].gamma && nb >= 2;
+      int units = nb;
+      if (packed) {
+        units = (nb + 1) / 2;
+        ctx->ws_gpack.ensure((size_t)units * ld * sizeof(C));
+        a.packed = 1;
+        a.nbands = nb;
+        a.out = ctx->ws_gpack.as<C>();
+        a.psi_prev = nullptr;
+      }
+      if (fused_local_apply(s, a, units)) {
+        if (packed) gamma_finish<T>(s, ik, nb, psi, psi_prev, out, ld, c);
+        KSS_CHECK_CUDA(cudaGetLastError());
+        return;
+      }
+      a = local_args<T>(s, ik, psi, psi_prev, out, ld, c);
+    }
+  }
   const size_t sa = smem_a(a), sb = smem_b(a);
   const size_t smax = 227 * 1024;
   if (sa > smax || sb > smax)
@@ -528,15 +567,7 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
           kk.c<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
         }
       }
-      if (packed) {
-        static const int idu = prof_register(f64 ? "gamma_unpack<f64>" : "gamma_unpack<f32>");
-        ProfScope ps(ctx, idu);
-        const long long n = (long long)kd.npw * nb;
-        const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 32);
-        gamma_unpack<C, T><<<blocks, 256, 0, ctx->stream>>>(
-            ctx->ws_gpack.as<C>(), ld, kd.d_mirror.as<int>(), (const C*)psi, (const C*)psi_prev, (C*)out,
-            (const T*)(f64 ? kd.d_kin64.p : kd.d_kin32.p), kd.npw, nb, (T)c.alpha, (T)c.beta, (T)c.gamma);
-      }
+      if (packed) gamma_finish<T>(s, ik, nb, psi, psi_prev, out, ld, c);
       KSS_CHECK_CUDA(cudaGetLastError());
       return;
     }

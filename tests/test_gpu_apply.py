@@ -149,6 +149,41 @@ def test_apply_mixed(ctx, name, mk, nb, pad):
     assert err < MIXED_TOL, err
 
 
+# Cubic boxes of every length the fused single-kernel local path has an instance for (single
+# precision: the whole box and V in one SM's shared memory), at shifted k-points (unpacked), with
+# ragged band counts, padded rows, and more bands than CTAs (the persistent loop over bands).
+FUSED_CASES = [
+    ("fused_10_k_310_bands", lambda: W.tiny_system(a=5.0, ecut=2.0, natom=2, fft_box=(10, 10, 10),
+                                                   kpts=[(0.25, 0.0, 0.0)]), 310, 3),
+    ("fused_12_k", lambda: W.tiny_system(a=5.5, ecut=2.5, natom=2, fft_box=(12, 12, 12),
+                                         kpts=[(0.1, 0.2, 0.3)]), 7, 0),
+    ("fused_15_k", lambda: W.tiny_system(a=6.0, ecut=3.0, natom=2, fft_box=(15, 15, 15),
+                                         kpts=[(0.25, 0.25, -0.25)]), 5, 2),
+    ("fused_16_k", lambda: W.tiny_system(a=6.0, ecut=3.0, natom=3, fft_box=(16, 16, 16),
+                                         kpts=[(0.5, 0.0, 0.25)]), 9, 1),
+    ("fused_18_k", lambda: W.tiny_system(a=7.0, ecut=3.5, natom=3, fft_box=(18, 18, 18),
+                                         kpts=[(0.0, 0.25, 0.0)]), 4, 0),
+    ("fused_20_k", lambda: W.tiny_system(a=7.5, ecut=4.0, natom=3, fft_box=(20, 20, 20),
+                                         kpts=[(0.125, -0.25, 0.375)]), 11, 4),
+    ("fused_24_gamma", lambda: W.tiny_system(a=8.0, ecut=5.0, natom=3, fft_box=(24, 24, 24)), 6, 1),
+    ("fused_25_k", lambda: W.tiny_system(a=9.0, ecut=5.0, natom=3, fft_box=(25, 25, 25),
+                                         kpts=[(0.25, 0.25, 0.25)]), 3, 0),
+]
+
+
+@pytest.mark.parametrize("name,mk,nb,pad", FUSED_CASES, ids=[c[0] for c in FUSED_CASES])
+def test_apply_mixed_fused_boxes(ctx, name, mk, nb, pad):
+    """Against the oracle, element by element and per band, at the mixed-form tolerance; the
+    profile shows the fused kernel ran (and none of the three slab passes)."""
+    K.kss_profile_enable(ctx, True)
+    err = _apply_case(ctx, mk(), nb, pad, K.KSS_PREC_MIXED)
+    prof = K.profile_table(ctx)
+    K.kss_profile_enable(ctx, False)
+    assert err < MIXED_TOL, err
+    assert prof.get("local_fused<f32>", (0, 0))[0] >= 1, prof
+    assert not any(k.startswith("local_pass") for k in prof), prof
+
+
 def test_apply_c2_sampled_bands(ctx):
     """Full-size C2 cell (96^3 box, 256 projectors): 4 bands per k-point against the oracle."""
     import torch
