@@ -1011,7 +1011,8 @@ def run_dense(args):
     out = {}
     rng = np.random.default_rng(5)
     cases = [("c2_564", [564], False), ("c3_1127_real", [1127], True), ("c3_1127_complex", [1127], False),
-             ("c4_batch_217", list(rng.integers(20, 142, size=217)), False)]
+             ("c4_batch_217", list(rng.integers(20, 142, size=217)), False),
+             ("single_141", [141], False), ("single_64", [64], False)]
     for name, ns, real in cases:
         src = [pencil(int(n), real) for n in ns]
         times = []

@@ -289,13 +289,13 @@ kss_status kss_gemm(kss_ctx ctx, int op, int M, int N, int K, const void* A, int
  * real arithmetic; eigenvectors and factor written with zero imaginary parts).  Hand-written
  * kernels (Cholesky, reduction to standard form, Householder tridiagonalisation, bisection and
  * inverse iteration, back-transformation): one CTA per pencil, or a cooperative grid for a
- * single pencil of order >= 160.  Synchronises the context stream.
+ * single pencil of order >= 32.  Synchronises the context stream.
  * Errors: KSS_EINVAL (count < 0, NULL arrays, bad sizes), KSS_ETIMEOUT (a bounded grid-barrier
  * wait gave up), KSS_ECUDA. */
 kss_status kss_dense_hegv(kss_ctx ctx, int count, const int* n, void* const* A, const int* lda,
                           void* const* B, const int* ldb, double* const* w, int* info, int real);
 
-/* Phase times of the last single-pencil solve that ran on a cooperative grid (order >= 160) in
+/* Phase times of the last single-pencil solve that ran on a cooperative grid (order >= 32) in
  * this context, from the device clock: ms[0] Cholesky (with the real-pencil input copy), ms[1]
  * reduction to standard form, ms[2] tridiagonalisation, ms[3] eigenvalues of the tridiagonal
  * matrix (bisection), ms[4] its eigenvectors (inverse iteration), ms[5] back-transformation.  Measurement support (the paper has no counterpart).  Synchronises the context stream; all zeros when

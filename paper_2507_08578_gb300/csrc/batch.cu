@@ -18,6 +18,7 @@
 
 #include "batch.h"
 #include "batch_kernels.cuh"
+#include "local_fused.h"
 #include "local_kernels.cuh"
 #include "tune.h"
 
@@ -234,10 +235,13 @@ void BatchEngine::prepare_t() {
     const long long k2 = bs[u].threads ? 10001 + (long long)(bs[u].A * 32 + bs[u].B) * 2 + (bs[u].threads == 384)
                                        : (long long)(c23 + 1);
     key[u] = {(long long)(c1 + 1) * 100000 + k2, u};
+    if (sizeof(T) == 4 && fused_code(units[u]->sys)) key[u].first = -100000 + fused_code(units[u]->sys);
   }
   vpi.assign(n, nullptr);
-  for (int u = 0; u < n; ++u)
-    if (bs[u].threads) vpi[u] = vpi_view(units[u]->sys, bs[u].A, bs[u].B, sizeof(T) == 8);
+  for (int u = 0; u < n; ++u) {
+    if (key[u].first < 0) vpi[u] = fused_potential_view(units[u]->sys);
+    else if (bs[u].threads) vpi[u] = vpi_view(units[u]->sys, bs[u].A, bs[u].B, sizeof(T) == 8);
+  }
   std::stable_sort(key.begin(), key.end());
   pos.assign(n, 0);
   classes.clear();
@@ -248,12 +252,19 @@ void BatchEngine::prepare_t() {
     const int c1 = (int)(key[i].first / 100000) - 1;
     const int c23 = (p.s2.A == p.s3.A && p.s2.B == p.s3.B && has_ct(p.s2.A * 32 + p.s2.B)) ? p.s2.A * 32 + p.s2.B : -1;
     const PassBSched& b = bs[u];
-    if (classes.empty() || i == 0 || key[i].first != key[i - 1].first)
+    if (classes.empty() || i == 0 || key[i].first != key[i - 1].first) {
       classes.push_back(PassClass{c1, b.threads ? -1 : c23, i, 0, 0, 0, 0, 0, 0, b.A, b.B, b.threads});
+      if (key[i].first < 0) classes.back().fcode = (int)(key[i].first + 100000);
+    }
     PassClass& pc = classes.back();
     kss_sys sy = units[u]->sys;
     const KData& kd = sy->k[units[u]->ik];
     pc.count += 1;
+    if (pc.fcode) {  // the fused class launches none of the three passes
+      pc.ftasks += units[u]->nb;
+      pc.smem_f = std::max(pc.smem_f, fused_smem_bytes(sy));
+      continue;
+    }
     pc.blocks_ac += kd.W[2] * units[u]->nb;
     pc.blocks_b += sy->N[0] * units[u]->nb;
     pc.smem_ac = std::max(pc.smem_ac, es * ((size_t)sy->N[0] + (size_t)kd.W[1] * (sy->N[0] + 1) + (size_t)kWarps * scr_warp));
@@ -284,6 +295,10 @@ void BatchEngine::prepare_t() {
     v = std::max(v, bytes);
   };
   for (const PassClass& pc : classes) {
+    if (pc.fcode) {
+      fused_group_prepare(ctx, pc.fcode, pc.smem_f);
+      continue;
+    }
     want(group_kernel<T, 0>(pc.code1), pc.smem_ac);
     want(group_kernel<T, 2>(pc.code1), pc.smem_ac);
     if (pc.wnt) want(group_kernel_w<T>(pc.wa, pc.wb, pc.wnt), pc.smem_bw);
@@ -328,6 +343,10 @@ void BatchEngine::fill_tables_t() {
       while (pos[u] != i) ++u;
       off_ac[u] = bac;
       off_b[u] = bb;
+      if (pc.fcode) {  // the fused class numbers (unit, band) tasks
+        bac += units[u]->nb;
+        continue;
+      }
       bac += units[u]->sys->k[units[u]->ik].W[2] * units[u]->nb;
       bb += units[u]->sys->N[0] * units[u]->nb;
     }
@@ -377,6 +396,7 @@ void BatchEngine::fill_tables_t() {
       LocalItem<T> it;
       fill_args<T>(sy, s->ik, it.a);
       it.a.Vpi = (const T*)vpi[u];
+      it.a.nbands = s->nb;
       it.a.psi = (const C*)psi;
       it.a.psi_prev = (const C*)pp;
       it.a.out = (C*)out;
@@ -447,10 +467,15 @@ void BatchEngine::launch_filter_t() {
     if (cn_blocks) group_gemm_cn(ctx, f64, cn, n, cn_blocks, cn_rblocks);
     for (const PassClass& pc : classes) {
       const LocalItem<T>* it = dl + (size_t)j * n + pc.first;
+      if (pc.fcode) {
+        if constexpr (sizeof(T) == 4) fused_group_launch(ctx, pc.fcode, it, pc.count, pc.ftasks, pc.smem_f);
+        continue;
+      }
       group_kernel<T, 0>(pc.code1)<<<pc.blocks_ac, kThreads, pc.smem_ac, ctx->stream>>>(it, pc.count, scr_warp);
     }
     for (const PassClass& pc : classes) {
       const LocalItem<T>* it = dl + (size_t)j * n + pc.first;
+      if (pc.fcode) continue;
       if (pc.wnt)
         group_kernel_w<T>(pc.wa, pc.wb, pc.wnt)<<<pc.blocks_b, pc.wnt, pc.smem_bw, ctx->stream>>>(it, pc.count, scr_warp);
       else
@@ -458,6 +483,7 @@ void BatchEngine::launch_filter_t() {
     }
     for (const PassClass& pc : classes) {
       const LocalItem<T>* it = dl + (size_t)j * n + pc.first;
+      if (pc.fcode) continue;
       group_kernel<T, 2>(pc.code1)<<<pc.blocks_ac, kThreads, pc.smem_ac, ctx->stream>>>(it, pc.count, scr_warp);
     }
     if (nn_blocks) group_gemm_nn(ctx, f64, nn, n, nn_blocks);
@@ -483,7 +509,8 @@ void BatchEngine::run_filter() {
   }
   if (f64) fill_tables_t<double>();
   else fill_tables_t<float>();
-  const int per_step = 3 * (int)classes.size() + (cn_blocks ? 2 : 0) + (nn_blocks ? 1 : 0);
+  int per_step = (cn_blocks ? 2 : 0) + (nn_blocks ? 1 : 0);
+  for (const PassClass& pc : classes) per_step += pc.fcode ? 1 : 3;
   if (use_graph) {
     if (!gexec) {
       // Capture the filter launches once for this set of units; later iterations only rewrite

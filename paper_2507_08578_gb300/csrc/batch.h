@@ -22,6 +22,10 @@ struct PassClass {  // units whose FFT passes share one kernel instance
   size_t smem_bw;  // shared memory of the CTA-wide pass B form
   int wa, wb, wnt; // pass B schedule (autotuner): CTA-wide split wa x wb at wnt threads; wnt == 0:
                    // the per-warp form (split code code23)
+  int fcode = 0;   // single precision, small cubic box: the fused single-kernel instance (split code
+                   // A*32+B) runs the whole local part of the class in one persistent launch
+  int ftasks = 0;  // its (unit, band) tasks
+  size_t smem_f = 0;
 };
 struct Roles {
   int y, hy, free2;  // buffers holding Y, H Y, and the free one that receives the rotated X

@@ -1055,7 +1055,7 @@ Pencil<S> make_pencil(double2* A, int lda, double2* B, int ldb, double* w, int* 
 }
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per grid-barrier wait
-constexpr int kGridMinN = 160;  // pencils at least this large run on a cooperative grid
+constexpr int kGridMinN = 32;  // a single pencil at least this large runs on a cooperative grid
 
 // Dynamic shared memory: 3 n words of S for the tridiagonalisation's v_j, w and v_{j+1}, and, when
 // it fits in 200 KB, one column of n words of S per warp for the back-transformation.

@@ -62,6 +62,32 @@ def test_batch_matches_oracle_and_single(ctx, prec, tol):
             K.kss_sys_destroy(h)
 
 
+def test_batch_mixed_fused_and_slab_classes(ctx):
+    """Mixed batch whose units fall in several local-part classes: small cubic boxes (20^3, 24^3
+    twice, 25^3) that run the grouped single-kernel local part, and a 30^3 unit on the three-pass
+    slab path, solved together; eigenvalues against the oracle within 1e-6 Ha."""
+    systems = [
+        W.make_system("f20", 7.0, 5.0, 3, 8, seed=41, fft_box=(20, 20, 20), kpts=W.SHIFTED_222[:1]),
+        W.make_system("f24", 8.0, 6.0, 4, 12, seed=42, fft_box=(24, 24, 24)),
+        W.make_system("f24k", 8.0, 6.0, 3, 10, seed=43, fft_box=(24, 24, 24), kpts=W.SHIFTED_222[1:3]),
+        W.make_system("f25", 8.5, 6.0, 3, 9, seed=44, fft_box=(25, 25, 25)),
+        W.make_system("s30", 9.0, 7.0, 4, 11, seed=45, fft_box=(30, 30, 30)),
+    ]
+    handles = [setup(ctx, s) for s in systems]
+    try:
+        units = [(h, s, ik) for h, s in zip(handles, systems) for ik in range(len(s.kpts))]
+        opts = K.make_opts(prec=K.KSS_PREC_MIXED, seed=9)
+        ev, rs, st, status = K.kss_solve_batch(ctx, [u[0] for u in units], [u[2] for u in units],
+                                               [u[1].nband for u in units], opts)
+        assert status == K.KSS_OK
+        for (h, s, ik), e in zip(units, ev):
+            ref = oracle_levels(s, ik, s.nband)
+            assert np.max(np.abs(e - ref)) < 1e-6, (s.name, ik, np.max(np.abs(e - ref)))
+    finally:
+        for h in handles:
+            K.kss_sys_destroy(h)
+
+
 def submit(ctx, s, nband=None):
     return K.kss_server_submit(ctx, s.lattice, s.ecut, s.kpts, s.pos, s.D, nband or s.nband,
                                fft_box=s.fft_box or (0, 0, 0))

@@ -80,7 +80,7 @@ def run(ctx, pencils, real=False, lds=None):
     return info, out
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 17, 64, 159, 160, 301, 564])
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 31, 32, 64, 159, 160, 301, 564])
 def test_single_pencil(ctx, n):
     A, B = pencil(n, seed=n)
     info, [(w, X)] = run(ctx, [(A, B)])
@@ -112,10 +112,11 @@ def test_degenerate_clusters(ctx, n):
     check(A, B, w, X)
 
 
-@pytest.mark.parametrize("n", [1, 2, 24, 159, 160, 300, 700])
+@pytest.mark.parametrize("n", [1, 2, 24, 31, 32, 159, 300, 700])
 def test_real_symmetric(ctx, n):
-    """Real symmetric pencils (solved in real arithmetic): one CTA below order 160, the cooperative
-    grid from 160; imaginary parts planted in the inputs are ignored."""
+    """Real symmetric pencils (solved in real arithmetic): a single pencil runs on one CTA below
+    order 32 and on the cooperative grid from 32; imaginary parts planted in the inputs are
+    ignored."""
     A, B = pencil(n, seed=3 * n, real=True)
     rng = np.random.default_rng(n)
     junk = 1j * rng.standard_normal((n, n))
