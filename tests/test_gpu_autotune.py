@@ -9,6 +9,7 @@
 * The batch engine follows the table: the same batch with every entry pinned to the per-warp
   form gives the same eigenvalues.
 """
+import dataclasses
 import os
 import re
 
@@ -61,7 +62,9 @@ def _apply(sysh, c, prec, npw):
 
 CASES = [
     ("C1_24", lambda: W.config1(), K.KSS_PREC_FP64, 1e-10),
-    ("C1_24_mixed", lambda: W.config1(), K.KSS_PREC_MIXED, 2e-5),
+    # a cubic single-precision box of edge <= 25 takes the fused single-kernel local part, which has
+    # no pass-B schedule; the config-1 cell on a 25 x 24 x 24 box keeps the three-pass form
+    ("C1_25x24_mixed", lambda: dataclasses.replace(W.config1(), fft_box=(25, 24, 24)), K.KSS_PREC_MIXED, 2e-5),
     ("box30", lambda: W.tiny_system(a=8.0, ecut=6.0, natom=3, fft_box=(30, 30, 30)), K.KSS_PREC_FP64, 1e-10),
     ("box36_mixed", lambda: W.tiny_system(a=9.0, ecut=7.0, natom=3, fft_box=(36, 36, 36)), K.KSS_PREC_MIXED, 2e-5),
     ("box40", lambda: W.tiny_system(a=9.0, ecut=8.0, natom=2, fft_box=(40, 40, 40)), K.KSS_PREC_FP64, 1e-10),
@@ -103,6 +106,24 @@ def test_every_schedule_matches_oracle(ctx, name, mk, prec, tol):
         # all schedules agree with each other to rounding
         for o in outs[1:]:
             assert rel_err_rows(o, outs[0]) < (1e-13 if prec == K.KSS_PREC_FP64 else 1e-5)
+    finally:
+        K.kss_sys_destroy(sysh)
+        K.kss_autotune_clear()
+
+
+def test_fused_box_consults_no_schedule(ctx):
+    """The config-1 box (24^3) in single precision runs the fused local kernel: a tuned apply adds
+    no table entry and still matches the oracle."""
+    s = W.config1()
+    sysh = setup(ctx, s)
+    try:
+        p = O.build_problem(s, 0)
+        c = W.random_block(p.basis.npw, 5, seed=3)
+        K.kss_autotune_clear()
+        K.kss_autotune_set(ctx, 1)
+        out = _apply(sysh, c, K.KSS_PREC_MIXED, p.basis.npw)
+        assert K.kss_autotune_table() == []
+        assert rel_err_rows(out, p.apply(c)) < 2e-5
     finally:
         K.kss_sys_destroy(sysh)
         K.kss_autotune_clear()
