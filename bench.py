@@ -43,6 +43,16 @@ def bf16_peak():
         return 1700.0, "fallback (sustained BF16)"
 
 
+def hbm_peak():
+    """HBM copy bandwidth of this machine pool (GB/s): the measured figure when the measured-peaks
+    file is present, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -57,11 +67,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--nk", type=int, default=0, help="use only the first nk k-points (profiling)")
-    ap.add_argument("--workload", choices=["c2", "c2s", "c3", "c4", "c5", "density", "lobpcg", "gemm", "dense"],
+    ap.add_argument("--workload", choices=["c2", "c2s", "c3", "c4", "c5", "density", "lobpcg", "gemm", "dense",
+                                           "apply"],
                     default="c2",
                     help="c2: default FP64 ChebFi iterations; c3/c4/c5: mixed-precision full solves, "
                          "batched and served forms; gemm: the path's complex products at the C2 "
-                         "shapes; dense: the Rayleigh-Ritz eigensolve (auxiliary lines)")
+                         "shapes; dense: the Rayleigh-Ritz eigensolve; apply: H on a large band "
+                         "block of the config-1 cell (auxiliary lines)")
+    ap.add_argument("--bands", type=int, default=16384, help="apply: bands in the block")
     ap.add_argument("--requests", type=int, default=60, help="c5: number of requests")
     ap.add_argument("--no-extras", action="store_true",
                     help="c2 line without the full-solve, config-3 and served measurements")
@@ -834,6 +847,81 @@ def run_density(args):
                                   sorted(prof.items(), key=lambda kv: -kv[1][1])}}), flush=True)
 
 
+def run_apply(args):
+    """H applied to one large band block of the config-1 cell (a = 10 bohr, Ecut = 10 Ha, 24^3 box,
+    1503 plane waves): in the mixed form the local part is the fused single kernel (box held in
+    shared memory), in FP64 the three-pass pipeline.  The block (16384 bands by default: 197 MB
+    in complex64) is larger than L2, so every step reads psi from HBM."""
+    import torch
+    import workloads as W
+    import paper_2507_08578_gb300.kss as K
+    from paper_2507_08578_gb300 import build as B
+    B.build()
+    s = W.config1()
+    prec = K.KSS_PREC_FP64 if args.form == "fp64" else K.KSS_PREC_MIXED
+    cdt = torch.complex128 if prec == K.KSS_PREC_FP64 else torch.complex64
+    es = 16 if prec == K.KSS_PREC_FP64 else 8
+    ctx = K.kss_create(0, torch.cuda.current_stream().cuda_stream)
+    sysh = _setup(K, ctx, s)
+    npw = K.kss_sphere(sysh, 0).shape[0]
+    nb = args.bands
+    g = torch.Generator(device="cuda").manual_seed(77)
+    psi = torch.randn((nb, npw), dtype=cdt, device="cuda", generator=g)
+    hpsi = torch.empty_like(psi)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        K.kss_apply_H(sysh, 0, psi, hpsi, prec)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    K.kss_profile_enable(ctx, True)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        K.kss_apply_H(sysh, 0, psi, hpsi, prec)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    prof = K.profile_table(ctx)
+    _, launches = K.kss_profile_count(ctx)
+    K.kss_profile_enable(ctx, False)
+    bands = nb * args.steps
+    N = s.fft_box[0]
+    flops_band = 2 * 5.0 * N ** 3 * math.log2(N ** 3)  # dense 3D transforms, forward and inverse
+    fam = "local_fused<f32>" if "local_fused<f32>" in prof else (
+        "local_pass_b<f64>" if prec == K.KSS_PREC_FP64 else "local_pass_b<f32>")
+    roof = None
+    if fam in prof:
+        l, kms = prof[fam]
+        per_band = bands / l
+        if fam == "local_fused<f32>":
+            # the whole local part: psi in and H psi out once per band (2 npw complex64 words)
+            ach_gbs = per_band * 2 * npw * es / (kms / l / 1000.0) / 1e9
+            ach_tf = per_band * flops_band / (kms / l / 1000.0) / 1e12
+            roof = {"kernel": fam, "bound": "alu", "achieved": ach_tf, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach_tf / FP32_PEAK_TFLOPS, "traffic": None,
+                    "hbm_achieved_gbs": ach_gbs, "hbm_peak_gbs": hbm_peak()[0],
+                    "hbm_frac": ach_gbs / hbm_peak()[0],
+                    "note": "algorithmic bytes 2 npw x 8 B per band; FFT flops 2 x 5 N^3 log2 N^3 per band; "
+                            "FP32 peak derived (152 SMs x 128 lanes x 2 x 2070 MHz)",
+                    "launches": l, "avg_launch_ms": kms / l}
+    K.kss_sys_destroy(sysh)
+    K.kss_destroy(ctx)
+    print(json.dumps({"metric": "band H-applies/s", "value": bands / (ms / 1000.0), "unit": "band-applies/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+                      "ms_per_step": ms / args.steps, "higher_is_better": True,
+                      "dtype": "f64" if prec == K.KSS_PREC_FP64 else "c64 (split-BF16 projector products)",
+                      "data": "synthetic",
+                      "config": {"workload": f"H psi on the config-1 cell (a=10 bohr, Ecut=10 Ha, 24^3, {npw} "
+                                             f"plane waves, 16 projectors), one block of {nb} bands per step, "
+                                             f"inputs resident in HBM",
+                                 "l2": f"inputs larger than L2: {nb * npw * es / 1e6:.0f} MB block"},
+                      "gpu_launches": launches, "clocks": ck, "roofline": roof,
+                      "kernels": {k: {"launches": v[0], "ms": round(v[1], 2)} for k, v in
+                                  sorted(prof.items(), key=lambda kv: -kv[1][1])}}), flush=True)
+
+
 def run_lobpcg(args):
     """ChebFi against LOBPCG (the paper's two GPU eigensolvers) on one k-point of a config-4
     system (a = 11.6 bohr, Ecut = 19.3 Ha, 60 atoms, 120 bands, npw 6358, box 45^3), FP64 to
@@ -1040,7 +1128,7 @@ def run_dense(args):
 def main():
     args = parse()
     if args.workload not in ("c2", "c2s") and args.impl == "ours":
-        {"c3": run_c3, "c4": run_c4, "c5": run_c5, "density": run_density,
+        {"c3": run_c3, "c4": run_c4, "c5": run_c5, "density": run_density, "apply": run_apply,
          "lobpcg": run_lobpcg, "gemm": run_gemm, "dense": run_dense}[args.workload](args)
         return
     rank = int(os.environ.get("RANK", "0"))
