@@ -75,6 +75,9 @@ def parse():
                          "shapes; dense: the Rayleigh-Ritz eigensolve; apply: H on a large band "
                          "block of the config-1 cell (auxiliary lines)")
     ap.add_argument("--bands", type=int, default=16384, help="apply: bands in the block")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="c4/c5: issue the batch filter's launches directly instead of replaying a CUDA "
+                         "graph, so that the kernel table times every launch (profiling)")
     ap.add_argument("--requests", type=int, default=60, help="c5: number of requests")
     ap.add_argument("--no-extras", action="store_true",
                     help="c2 line without the full-solve, config-3 and served measurements")
@@ -727,7 +730,8 @@ def run_c4(args):
     need = sorted({all_units[u][0] for u in mine})
     handles = {j: _setup(K, ctx, systems[j]) for j in need}
     units = [(handles[all_units[u][0]], systems[all_units[u][0]], all_units[u][1]) for u in mine]
-    opts = K.make_opts(prec=K.KSS_PREC_MIXED, seed=7, degree=args.degree)
+    opts = K.make_opts(prec=K.KSS_PREC_MIXED, seed=7, degree=args.degree,
+                       flags=K.KSS_SOLVE_BATCH_NO_GRAPH if args.no_graph else 0)
     args_b = ([u[0] for u in units], [u[2] for u in units], [u[1].nband for u in units])
     for _ in range(args.warmup):
         K.kss_solve_batch(ctx, *args_b, opts)
@@ -763,8 +767,9 @@ def run_c4(args):
                       "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
                       "higher_is_better": True, "dtype": "c64+f64", "data": "synthetic",
                       "config": {"workload": f"C4: 48 systems, {len(all_units)} (system,k) units in one "
-                                             "lockstep batch (grouped launches, CUDA-graph filter), "
-                                             "mixed precision"},
+                                             "lockstep batch (grouped launches, " +
+                                             ("filter launched directly" if args.no_graph else "CUDA-graph filter") +
+                                             "), mixed precision"},
                       "units_per_s": len(all_units) * args.steps / dt, "band_applies_per_s": napply * args.steps / dt,
                       "max_residual_Ha": max_res, "scaling": "strong" if world > 1 else None,
                       "partition": "greedy longest-processing-time over (system, k) units" if world > 1 else None,
@@ -772,7 +777,7 @@ def run_c4(args):
                       "mean_iterations": sum(iters) / len(iters), "degree": args.degree,
                       "clocks": ck,
                       "kernels": {k: {"launches": v[0], "ms": round(v[1], 2)} for k, v in
-                                  sorted(prof.items(), key=lambda kv: -kv[1][1])[:12]}}), flush=True)
+                                  sorted(prof.items(), key=lambda kv: -kv[1][1])[:24]}}), flush=True)
 
 
 def run_density(args):

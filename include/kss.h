@@ -349,6 +349,13 @@ typedef struct {
  * ChebFi filter packs two bands per complex FFT (psi_a + i psi_b), halving the FFT work (the
  * time-reversal economy the paper notes for Gamma, §6).  This flag turns that off. */
 #define KSS_SOLVE_NO_GAMMA_REAL 1
+/* kss_solve_batch and the server: issue the filter's grouped launches directly instead of replaying
+ * them as a CUDA graph (same results; every launch is then timed by kss_profile_*, which sees a
+ * replayed graph as one entry). */
+#define KSS_SOLVE_BATCH_NO_GRAPH 2
+/* kss_solve_batch and the server, mixed form: the projector products of the batch on the FP32 CUDA
+ * cores (FP32 accumulation) instead of the split-BF16 tensor-core products. */
+#define KSS_SOLVE_BATCH_FP32_PROJ 4
 
 typedef struct {
   int iters;               /* filter iterations done */
@@ -564,27 +571,33 @@ kss_status kss_autotune_put(const kss_tune_entry* e);
 kss_status kss_autotune_clear(void);
 
 /* The tensor-core GEMMs (the projector products, Eq. ham-nl of §5.2; the Gram and rotation
- * products of Rayleigh-Ritz, §5.1) split K across CTAs when a product has few output tiles.  With
- * tuning on (kss_autotune_set), the first product of each (kind, shape) times the candidate splits
- * (no split, the closed-form plan, and the splits that fill the SMs in one, two or three waves) on
- * the device and keeps the fastest for the process; every split computes the same product (the
- * K ranges are added in a fixed order).  kind: 0 split-BF16 complex64 products, 1 FP64 digit
- * products, 2 the same with a complex64 result, 3 4-digit products of complex64 data.  Mr: real
- * rows of the product (twice the complex rows), Nr: columns, kblocks: K in k-blocks of the kernel. */
+ * products of Rayleigh-Ritz, §5.1) split K across CTAs when a product has few output tiles, and the
+ * split-BF16 products have three kernel forms: one CTA per 128 x 128 output tile (form 0), or
+ * persistent CTAs (one per SM) that walk the output tiles with two TMEM accumulators, so that the
+ * epilogue of one tile overlaps the MMAs of the next, on 128 x 128 (form 1) or 128 x 64 (form 2)
+ * tiles.  With tuning on (kss_autotune_set), the first product of each (kind, shape) times the
+ * candidate schedules (each form with no split, the closed-form plan, and the splits that fill the
+ * SMs in one, two or three waves) on the device and keeps the fastest for the process; every
+ * schedule computes the same product (the K ranges are added in a fixed order).  kind: 0
+ * split-BF16 complex64 products, 1 FP64 digit products, 2 the same with a complex64 result, 3
+ * 4-digit products of complex64 data.  Mr: real rows of the product (twice the complex rows), Nr:
+ * columns, kblocks: K in k-blocks of the kernel. */
 typedef struct {
   int device, kind, Mr, Nr, kblocks;
   int splits;  /* chosen K-split (CTAs along K) */
-  double ms;   /* time of one tuning run of the chosen split (0 for a pinned entry) */
+  double ms;   /* time of one tuning run of the chosen schedule (0 for a pinned entry) */
   int ncand;   /* candidates timed (0 for a pinned entry) */
+  int form;    /* kernel form (kind 0: 0, 1 or 2 as above; other kinds: 0) */
 } kss_gemm_tune_entry;
 
 /* Number of GEMM K-split table entries (process-wide).  Errors: KSS_EINVAL (n == NULL). */
 kss_status kss_autotune_gemm_count(int* n);
 /* Entry i (insertion order); KSS_EINVAL past the end or for a NULL out. */
 kss_status kss_autotune_gemm_get(int i, kss_gemm_tune_entry* out);
-/* Insert or replace the entry for (device, kind, Mr, Nr, kblocks): pins a split (clamped at use to
- * the kernel's minimum k-blocks per CTA).  ms and ncand are ignored.  Errors: KSS_EINVAL (NULL,
- * kind outside 0..3, sizes < 1, splits outside [1, kblocks]). */
+/* Insert or replace the entry for (device, kind, Mr, Nr, kblocks): pins a form and a split (the
+ * split clamped at use to the kernel's minimum k-blocks per CTA).  ms and ncand are ignored.
+ * Errors: KSS_EINVAL (NULL, kind outside 0..3, sizes < 1, splits outside [1, kblocks], form outside
+ * 0..2 for kind 0 or not 0 for the other kinds). */
 kss_status kss_autotune_gemm_put(const kss_gemm_tune_entry* e);
 
 #ifdef __cplusplus

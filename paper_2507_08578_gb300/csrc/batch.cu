@@ -113,6 +113,61 @@ __global__ void c128_ld_to_c64(const double2* __restrict__ in, int np, float2* _
   out[idx] = make_float2((float)v.x, (float)v.y);
 }
 
+// One unit of the grouped Rayleigh-Ritz epilogue (single precision): eigenvectors to complex64,
+// residual norms of the rotated block.
+struct RrItem {
+  const double2* Q;  // eigenvectors: leading nb x nb block, ld np
+  float2* Q32;       // complex64 copy, ld nb
+  const float2* X;   // rotated block and H times it, ld npw
+  const float2* HX;
+  const double* w;   // eigenvalues
+  double* r;         // residual norms |H x - lambda x|
+  int np, nb, npw;
+  long long q0, r0;  // first block of the unit in the conversion and residual launches
+};
+
+__device__ __forceinline__ int rr_find(const RrItem* it, int n, long long b, bool res) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if ((res ? it[mid].r0 : it[mid].q0) <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void rr_q_to_c64(const RrItem* __restrict__ items, int n) {
+  const RrItem& t = items[rr_find(items, n, blockIdx.x, false)];
+  const long long idx = (blockIdx.x - t.q0) * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)t.nb * t.nb) return;
+  const int i = (int)(idx % t.nb), j = (int)(idx / t.nb);
+  const double2 v = t.Q[(size_t)j * t.np + i];
+  t.Q32[idx] = make_float2((float)v.x, (float)v.y);
+}
+
+// One block per band: |H x_n - lambda_n x_n| with FP64 accumulation.
+__global__ void rr_residuals(const RrItem* __restrict__ items, int n) {
+  __shared__ double red[256];
+  const RrItem& t = items[rr_find(items, n, blockIdx.x, true)];
+  const int band = (int)(blockIdx.x - t.r0);
+  const double lam = t.w[band];
+  const float2* x = t.X + (size_t)band * t.npw;
+  const float2* h = t.HX + (size_t)band * t.npw;
+  double s = 0;
+  for (int g = threadIdx.x; g < t.npw; g += blockDim.x) {
+    const double dr = (double)h[g].x - lam * (double)x[g].x;
+    const double di = (double)h[g].y - lam * (double)x[g].y;
+    s += dr * dr + di * di;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) t.r[band] = sqrt(red[0]);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -121,6 +176,7 @@ __global__ void c128_ld_to_c64(const double2* __restrict__ in, int np, float2* _
 
 BatchEngine::~BatchEngine() {
   drop_graph();
+  if (hstage) cudaFreeHost(hstage);
   if (cap) cudaStreamDestroy((cudaStream_t)cap);
   for (auto w : workers) {
     cudaStreamSynchronize(w->stream);
@@ -166,6 +222,17 @@ void BatchEngine::rr_all(const std::vector<kss_solver_s*>& us, const std::vector
     KSS_CHECK_CUDA(cudaStreamWaitEvent(ctx->stream, (cudaEvent_t)wev[i], 0));
   }
   ctx->prof.launches += 0;
+}
+
+void* BatchEngine::stage(size_t bytes) {
+  if (bytes > hstage_bytes) {
+    if (hstage) KSS_CHECK_CUDA(cudaFreeHost(hstage));
+    hstage = nullptr;
+    hstage_bytes = 0;
+    KSS_CHECK_CUDA(cudaMallocHost(&hstage, bytes));
+    hstage_bytes = bytes;
+  }
+  return hstage;
 }
 
 void BatchEngine::drop_graph() {
@@ -306,6 +373,25 @@ void BatchEngine::prepare_t() {
   }
   for (const auto& kv : need)
     KSS_CHECK_CUDA(cudaFuncSetAttribute(kv.first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kv.second));
+  // Single precision: the projector products as grouped split-BF16 tensor-core products.
+  tc_on = false;
+  tc_i.assign(n, -1);
+  if (sizeof(T) == 4 && use_tc_gemm) {
+    std::vector<TcGroupSpec> cs, ns;
+    for (int u = 0; u < n; ++u) {
+      kss_solver_s* s = units[u];
+      kss_sys sy = s->sys;
+      const KData& kd = sy->k[s->ik];
+      if (!sy->nproj) continue;
+      tc_i[u] = (int)cs.size();
+      cs.push_back(TcGroupSpec{beta_split_cn(sy, s->ik), sy->nproj, s->nb, kd.npw, kd.npw, sy->nproj,
+                               sy->d_D32.as<float>()});
+      ns.push_back(TcGroupSpec{beta_split_nn(sy, s->ik), kd.npw, s->nb, sy->nproj, sy->nproj, kd.npw, nullptr});
+    }
+    tc_cn.build(ctx, cs, steps);
+    tc_nn.build(ctx, ns, steps);
+    tc_on = !cs.empty();
+  }
   prepared = true;
 }
 
@@ -333,6 +419,14 @@ void BatchEngine::fill_tables_t() {
     c[u] = cp.c;
     sigma[u] = cp.sigma1;
     tau[u] = 2.0 / cp.sigma1;
+  }
+  // Units whose FP64 check missed the tolerance with the split-BF16 products (proj32) take the
+  // FP32 CUDA-core products; the graph holds those launches only while such units exist.
+  bool need_simt = !tc_on;
+  for (auto* s : units) need_simt |= s->proj32 && s->sys->nproj;
+  if (need_simt != simt_on) {
+    simt_on = need_simt;
+    drop_graph();
   }
   // block offsets restart for every class (each class is its own launch)
   std::vector<int> off_ac(n), off_b(n);
@@ -413,7 +507,8 @@ void BatchEngine::fill_tables_t() {
       g = GemmItem{};
       GemmItem& h = nn[u];
       h = GemmItem{};
-      g.idle = h.idle = idle ? 1 : 0;
+      const bool on_tc = tc_on && tc_i[u] >= 0 && !s->proj32;
+      g.idle = h.idle = (idle || on_tc) ? 1 : 0;
       if (sy->nproj) {
         g.M = sy->nproj;
         g.N = s->nb;
@@ -438,6 +533,11 @@ void BatchEngine::fill_tables_t() {
         h.ldc = kd.npw;
         h.ar = 1.0;
         h.br = 1.0;
+        if (tc_on) {
+          void* cprj = (char*)ws.p + ws_off[u].cprj;
+          tc_cn.set(j, tc_i[u], psi, cprj, (float)al, 0.f, idle || !on_tc);
+          tc_nn.set(j, tc_i[u], cprj, out, 1.f, 1.f, idle || !on_tc);
+        }
       }
     }
     int b1, r1, b2, r2;
@@ -454,6 +554,10 @@ void BatchEngine::fill_tables_t() {
   KSS_CHECK_CUDA(cudaMemcpyAsync(d_local.p, h_local.data(), h_local.size(), cudaMemcpyHostToDevice, ctx->stream));
   KSS_CHECK_CUDA(cudaMemcpyAsync(d_cn.p, h_cn.data(), h_cn.size() * sizeof(GemmItem), cudaMemcpyHostToDevice, ctx->stream));
   KSS_CHECK_CUDA(cudaMemcpyAsync(d_nn.p, h_nn.data(), h_nn.size() * sizeof(GemmItem), cudaMemcpyHostToDevice, ctx->stream));
+  if (tc_on) {
+    tc_cn.upload(ctx->stream);
+    tc_nn.upload(ctx->stream);
+  }
 }
 
 template <typename T>
@@ -464,18 +568,26 @@ void BatchEngine::launch_filter_t() {
   for (int j = 0; j < steps; ++j) {
     const GemmItem* cn = d_cn.as<GemmItem>() + (size_t)j * n;
     const GemmItem* nn = d_nn.as<GemmItem>() + (size_t)j * n;
-    if (cn_blocks) group_gemm_cn(ctx, f64, cn, n, cn_blocks, cn_rblocks);
+    if (tc_on) tc_cn.launch(ctx, j, "cprj");
+    if (simt_on && cn_blocks) group_gemm_cn(ctx, f64, cn, n, cn_blocks, cn_rblocks);
+    static const int ida = prof_register(f64 ? "group_pass_a<f64>" : "group_pass_a<f32>");
+    static const int idb = prof_register(f64 ? "group_pass_b<f64>" : "group_pass_b<f32>");
+    static const int idc = prof_register(f64 ? "group_pass_c<f64>" : "group_pass_c<f32>");
     for (const PassClass& pc : classes) {
       const LocalItem<T>* it = dl + (size_t)j * n + pc.first;
       if (pc.fcode) {
+        static const int idf = prof_register("group_fused<f32>");
+        ProfScope ps(ctx, idf);
         if constexpr (sizeof(T) == 4) fused_group_launch(ctx, pc.fcode, it, pc.count, pc.ftasks, pc.smem_f);
         continue;
       }
+      ProfScope ps(ctx, ida);
       group_kernel<T, 0>(pc.code1)<<<pc.blocks_ac, kThreads, pc.smem_ac, ctx->stream>>>(it, pc.count, scr_warp);
     }
     for (const PassClass& pc : classes) {
       const LocalItem<T>* it = dl + (size_t)j * n + pc.first;
       if (pc.fcode) continue;
+      ProfScope ps(ctx, idb);
       if (pc.wnt)
         group_kernel_w<T>(pc.wa, pc.wb, pc.wnt)<<<pc.blocks_b, pc.wnt, pc.smem_bw, ctx->stream>>>(it, pc.count, scr_warp);
       else
@@ -484,9 +596,11 @@ void BatchEngine::launch_filter_t() {
     for (const PassClass& pc : classes) {
       const LocalItem<T>* it = dl + (size_t)j * n + pc.first;
       if (pc.fcode) continue;
+      ProfScope ps(ctx, idc);
       group_kernel<T, 2>(pc.code1)<<<pc.blocks_ac, kThreads, pc.smem_ac, ctx->stream>>>(it, pc.count, scr_warp);
     }
-    if (nn_blocks) group_gemm_nn(ctx, f64, nn, n, nn_blocks);
+    if (tc_on) tc_nn.launch(ctx, j, "nonlocal");
+    if (simt_on && nn_blocks) group_gemm_nn(ctx, f64, nn, n, nn_blocks);
   }
   KSS_CHECK_CUDA(cudaGetLastError());
 }
@@ -509,7 +623,8 @@ void BatchEngine::run_filter() {
   }
   if (f64) fill_tables_t<double>();
   else fill_tables_t<float>();
-  int per_step = (cn_blocks ? 2 : 0) + (nn_blocks ? 1 : 0);
+  int per_step = (tc_on ? 4 + (tc_cn.split() ? 1 : 0) + (tc_nn.split() ? 1 : 0) : 0) +
+                 (simt_on ? (cn_blocks ? 2 : 0) + (nn_blocks ? 1 : 0) : 0);
   for (const PassClass& pc : classes) per_step += pc.fcode ? 1 : 3;
   if (use_graph) {
     if (!gexec) {
@@ -637,6 +752,13 @@ void BatchEngine::decide(kss_solver_s* s) {
     if (r <= s->tol || stalled || s->iter >= s->o.max_iter) {
       refine_fp64(s);
       s->converged = max_wanted(s) <= s->tol;
+      // as in the single-system solver: a block that misses the tolerance in the FP64 check with
+      // the split-BF16 projector products continues with FP32 products
+      if (!s->converged && !s->proj32 && s->sys->nproj && s->iter < s->o.max_iter) {
+        s->proj32 = true;
+        s->hist.clear();
+        return;
+      }
       s->done = true;
     }
   }
@@ -657,6 +779,12 @@ void BatchEngine::rr_batched(const std::vector<kss_solver_s*>& us, const std::ve
   binfo.ensure((size_t)U * sizeof(int));
   double2* S = Sb.as<double2>();
   double2* H = Hb.as<double2>();
+  bool any64 = false;
+  for (auto* s : us) any64 |= s->f64;
+  if (!any64) {
+    rr_batched_grouped(us, y, hy, xo, hxo, np);
+    return;
+  }
   // Gram and projected-H matrices of every unit, into the leading nb x nb blocks.  The batch's
   // units are small (16-141 bands): one SIMT product per unit beats the tensor-core digit products,
   // whose operand preparation and 128 x 64 tiles do not pay at these sizes (measured).
@@ -717,6 +845,136 @@ void BatchEngine::rr_batched(const std::vector<kss_solver_s*>& us, const std::ve
   KSS_CHECK_CUDA(cudaGetLastError());
 }
 
+// Single precision: the Rayleigh-Ritz of every unit in a fixed number of grouped launches (the
+// Gram and projected-H products of all units in one SIMT launch with FP32 partial sums added in
+// FP64, the batched FP64 eigensolve, the eigenvectors to complex64, the rotations of all units in
+// one launch, the residuals of all bands in one launch) instead of about twenty launches per unit.
+void BatchEngine::rr_batched_grouped(const std::vector<kss_solver_s*>& us, const std::vector<int>& y,
+                                     const std::vector<int>& hy, const std::vector<int>& xo,
+                                     const std::vector<int>& hxo, int np) {
+  const int U = (int)us.size();
+  cudaStream_t st = ctx->stream;
+  const size_t mat = (size_t)np * np;
+  double2* S = Sb.as<double2>();
+  double2* H = Hb.as<double2>();
+  // Gram (Y^H Y) and projected H (Y^H HY) of every unit
+  std::vector<GemmItem> g(2 * (size_t)U);
+  for (int u = 0; u < U; ++u) {
+    kss_solver_s* s = us[u];
+    for (int k = 0; k < 2; ++k) {
+      GemmItem& e = g[2 * u + k];
+      e = GemmItem{};
+      e.M = e.N = s->nb;
+      e.K = s->npw;
+      e.A = s->blk[y[u]].p;
+      e.lda = s->npw;
+      e.B = k ? s->blk[hy[u]].p : s->blk[y[u]].p;
+      e.ldb = s->npw;
+      e.C = (k ? H : S) + u * mat;
+      e.ldc = np;
+      e.s = 1.0;
+    }
+  }
+  int gb = 0, grb = 0;
+  group_plan(ctx, g, true, &gb, &grb);
+  size_t part = 0;
+  for (auto& e : g) part += (size_t)e.splits * e.M * e.N;
+  rr_part.ensure(part * sizeof(float2));
+  part = 0;
+  for (auto& e : g) {
+    e.P = rr_part.as<float2>() + part;
+    part += (size_t)e.splits * e.M * e.N;
+  }
+  // rotations X = Y Q, HX = HY Q and the per-unit conversion / residual items
+  std::vector<GemmItem> rot(2 * (size_t)U);
+  std::vector<RrItem> it(U);
+  long long qb = 0, rb = 0;
+  for (int u = 0; u < U; ++u) {
+    kss_solver_s* s = us[u];
+    const int nb = s->nb, npw = s->npw;
+    s->Q32.ensure((size_t)nb * nb * sizeof(float2));
+    for (int k = 0; k < 2; ++k) {
+      GemmItem& e = rot[2 * u + k];
+      e = GemmItem{};
+      e.M = npw;
+      e.N = nb;
+      e.K = nb;
+      e.A = k ? s->blk[hy[u]].p : s->blk[y[u]].p;
+      e.lda = npw;
+      e.B = s->Q32.p;
+      e.ldb = nb;
+      e.C = k ? s->blk[hxo[u]].p : s->blk[xo[u]].p;
+      e.ldc = npw;
+      e.ar = 1.0;
+      e.br = 0.0;
+    }
+    RrItem& t = it[u];
+    t.Q = H + u * mat;
+    t.Q32 = s->Q32.as<float2>();
+    t.X = s->blk[xo[u]].as<float2>();
+    t.HX = s->blk[hxo[u]].as<float2>();
+    t.w = Wb.as<double>() + (size_t)u * np;
+    t.r = s->resid_d.as<double>();
+    t.np = np;
+    t.nb = nb;
+    t.npw = npw;
+    t.q0 = qb;
+    t.r0 = rb;
+    qb += ((long long)nb * nb + 255) / 256;
+    rb += nb;
+  }
+  int rotb = 0, rotrb = 0;
+  group_plan(ctx, rot, false, &rotb, &rotrb);
+  // tables through one pinned staging buffer (rewritten only after this call's synchronisation)
+  const size_t bg = g.size() * sizeof(GemmItem), br = rot.size() * sizeof(GemmItem), bi = it.size() * sizeof(RrItem);
+  unsigned char* h = (unsigned char*)stage(bg + br + bi);
+  std::memcpy(h, g.data(), bg);
+  std::memcpy(h + bg, rot.data(), br);
+  std::memcpy(h + bg + br, it.data(), bi);
+  d_rr_g.ensure(bg);
+  d_rr_rot.ensure(br);
+  d_rr_it.ensure(bi);
+  KSS_CHECK_CUDA(cudaMemcpyAsync(d_rr_g.p, h, bg, cudaMemcpyHostToDevice, st));
+  KSS_CHECK_CUDA(cudaMemcpyAsync(d_rr_rot.p, h + bg, br, cudaMemcpyHostToDevice, st));
+  KSS_CHECK_CUDA(cudaMemcpyAsync(d_rr_it.p, h + bg + br, bi, cudaMemcpyHostToDevice, st));
+  group_gemm_cn_c64_to_c128(ctx, d_rr_g.as<GemmItem>(), 2 * U, gb, grb);
+  // every unit's FP64 generalised eigensolve (H_s q = lambda S q) in one launch, one CTA per unit
+  int* dinfo = binfo.as<int>();
+  std::vector<HegvItem> items(U);
+  for (int u = 0; u < U; ++u)
+    items[u] = HegvItem{H + u * mat, S + u * mat, Wb.as<double>() + (size_t)u * np, dinfo + u, us[u]->nb, np, np, false};
+  hegv_batched(ctx, items);
+  {
+    static const int id = prof_register("group_q_to_c64");
+    ProfScope ps(ctx, id);
+    rr_q_to_c64<<<(unsigned)qb, 256, 0, st>>>(d_rr_it.as<RrItem>(), U);
+    KSS_CHECK_CUDA(cudaGetLastError());
+  }
+  group_gemm_nn(ctx, false, d_rr_rot.as<GemmItem>(), 2 * U, rotb);
+  {
+    static const int id = prof_register("group_residuals");
+    ProfScope ps(ctx, id);
+    rr_residuals<<<(unsigned)rb, 256, 0, st>>>(d_rr_it.as<RrItem>(), U);
+    KSS_CHECK_CUDA(cudaGetLastError());
+  }
+  for (int u = 0; u < U; ++u) {
+    kss_solver_s* s = us[u];
+    const int nb = s->nb;
+    const double* W = Wb.as<double>() + (size_t)u * np;
+    if (!s->hpin) KSS_CHECK_CUDA(cudaMallocHost((void**)&s->hpin, (2 * (size_t)nb + 1) * sizeof(double)));
+    KSS_CHECK_CUDA(cudaMemcpyAsync(s->hpin, W, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KSS_CHECK_CUDA(cudaMemcpyAsync(s->hpin + nb, s->resid_d.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  binfo_h.assign(U, 0);
+  KSS_CHECK_CUDA(cudaMemcpyAsync(binfo_h.data(), dinfo, U * sizeof(int), cudaMemcpyDeviceToHost, st));
+  KSS_CHECK_CUDA(cudaStreamSynchronize(st));
+  for (int u = 0; u < U; ++u) {
+    const int info = binfo_h[u];
+    std::memcpy(us[u]->hpin + 2 * us[u]->nb, &info, sizeof(int));
+  }
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
 }  // namespace kss
 
 using namespace kss;
@@ -747,6 +1005,8 @@ extern "C" kss_status kss_solve_batch(kss_ctx ctx, int n, const kss_sys* sys, co
     }
     BatchEngine eng;
     eng.ctx = ctx;
+    eng.use_graph = !(o.flags & KSS_SOLVE_BATCH_NO_GRAPH);
+    eng.use_tc_gemm = !(o.flags & KSS_SOLVE_BATCH_FP32_PROJ);
     eng.f64 = n ? made[0]->f64 : true;
     for (auto* s : made)
       KSS_REQUIRE(s->f64 == eng.f64 && s->o.degree == made[0]->o.degree,

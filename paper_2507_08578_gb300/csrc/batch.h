@@ -38,6 +38,7 @@ class BatchEngine {
   int degree = 10;
   bool use_graph = true;
   bool use_batched_rr = true;
+  bool use_tc_gemm = true;  // single precision: projector products on the tensor cores
 
   ~BatchEngine();
   // One lockstep iteration over every unit of `all` that is not done (fresh units get their
@@ -84,7 +85,25 @@ class BatchEngine {
   // triangular solves and Hermitian eigensolve (one call each for every unit).
   void rr_batched(const std::vector<kss_solver_s*>& us, const std::vector<int>& y,
                   const std::vector<int>& hy, const std::vector<int>& xo, const std::vector<int>& hxo);
+  // Single precision: the projector products of every unit as grouped split-BF16 products on the
+  // tensor cores (one persistent launch each for beta^H psi and beta C'); unit u is product tc_i[u]
+  // of both plans (-1: no projectors).
+  bool tc_on = false;
+  bool simt_on = true;  // the FP32 CUDA-core grouped products run (no tensor-core plan, or units with
+                        // proj32 set)
+  TcGroupPlan tc_cn, tc_nn;
+  std::vector<int> tc_i;
+  void rr_batched_grouped(const std::vector<kss_solver_s*>& us, const std::vector<int>& y,
+                          const std::vector<int>& hy, const std::vector<int>& xo, const std::vector<int>& hxo,
+                          int np);
   DevBuf Sb, Hb, Wb, binfo, q32;
+  // Grouped Rayleigh-Ritz of single-precision units: device tables (Gram and rotation products,
+  // per-unit conversion / residual items), split-K partial sums, and a pinned staging buffer for
+  // the tables (rewritten only after the stream synchronisation that ends every iteration).
+  DevBuf d_rr_g, d_rr_rot, d_rr_it, rr_part;
+  void* hstage = nullptr;
+  size_t hstage_bytes = 0;
+  void* stage(size_t bytes);
   std::vector<int> binfo_h;
   void* cap = nullptr;    // cudaStream_t used only to record the graph
 };

@@ -363,6 +363,25 @@ __global__ void gg_reduce(const GemmItem* __restrict__ items, int n) {
   ((C*)g.C)[(size_t)j * g.ldc + i] = out;
 }
 
+// The same reduction for complex64 products delivered in complex128 (the batched Gram matrices of
+// the mixed form): the FP32 partial sums of each K chunk added in FP64.
+__global__ void gg_reduce_c64_to_c128(const GemmItem* __restrict__ items, int n) {
+  const int it = find_item(items, n, blockIdx.x, true);
+  const GemmItem& g = items[it];
+  if (g.idle) return;
+  const long long idx = (long long)(blockIdx.x - g.rblk0) * blockDim.x + threadIdx.x;
+  if (idx >= (long long)g.M * g.N) return;
+  const int i = (int)(idx % g.M), j = (int)(idx / g.M);
+  double sr = 0, si = 0;
+  const float2* P = (const float2*)g.P;
+  for (int z = 0; z < g.splits; ++z) {
+    const float2 p = P[(size_t)z * g.M * g.N + idx];
+    sr += p.x;
+    si += p.y;
+  }
+  ((double2*)g.C)[(size_t)j * g.ldc + i] = make_double2(sr, si);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) gg_nn(const GemmItem* __restrict__ items, int n) {
   using C = typename CT<T>::C;
@@ -656,6 +675,20 @@ void group_gemm_cn(kss_ctx ctx, bool fp64, const GemmItem* d_items, int n, int b
     ProfScope ps(ctx, idr);
     if (fp64) gg_reduce<double><<<rblocks, 256, 0, ctx->stream>>>(d_items, n);
     else gg_reduce<float><<<rblocks, 256, 0, ctx->stream>>>(d_items, n);
+  }
+  KSS_CHECK_CUDA(cudaGetLastError());
+}
+
+void group_gemm_cn_c64_to_c128(kss_ctx ctx, const GemmItem* d_items, int n, int blocks, int rblocks) {
+  if (!n || !blocks) return;
+  static const int idp = prof_register("group_gemm_cn_partial:gram"), idr = prof_register("group_reduce64:gram");
+  {
+    ProfScope ps(ctx, idp);
+    gg_cn_partial<float><<<blocks, 256, 0, ctx->stream>>>(d_items, n);
+  }
+  {
+    ProfScope ps(ctx, idr);
+    gg_reduce_c64_to_c128<<<rblocks, 256, 0, ctx->stream>>>(d_items, n);
   }
   KSS_CHECK_CUDA(cudaGetLastError());
 }

@@ -191,6 +191,9 @@ struct kss_solver_s {
   bool gamma = false;        // Gamma point with real-space-real bands (packed FFTs, real RR)
   bool gram64 = false;       // mixed precision: Gram matrices accumulated in FP64 (after a failed
                              // Cholesky of the FP32-accumulated ones)
+  bool proj32 = false;       // mixed precision: projector products on the FP32 CUDA cores (after the
+                             // FP64 check of a block filtered with the split-BF16 products missed
+                             // the tolerance)
   ~kss_solver_s();
 };
 
@@ -249,6 +252,8 @@ void convert_f64_to_f32(const double* in, float* out, size_t n, cudaStream_t st)
 struct ChebCoef {
   double alpha, beta, gamma;
   bool packed = false;  // Gamma point, real-space-real bands: two bands per complex FFT
+  bool fp32_proj = false;  // mixed precision: projector products on the FP32 CUDA cores instead of
+                           // the split-BF16 tensor-core products
 };
 // out = alpha*(T psi + V psi + nonlocal psi) + beta*psi + gamma*psi_prev (psi_prev may be null)
 void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, void* out, int ld,
@@ -310,6 +315,43 @@ struct GemmItem {
 void group_plan(kss_ctx ctx, std::vector<GemmItem>& items, bool cn, int* blocks, int* rblocks);
 void group_gemm_cn(kss_ctx ctx, bool fp64, const GemmItem* d_items, int n, int blocks, int rblocks);
 void group_gemm_nn(kss_ctx ctx, bool fp64, const GemmItem* d_items, int n, int blocks);
+// Grouped complex64 A^H B products (d null, s = 1) delivered in complex128 at C (ldc): FP32 partial
+// sums per K chunk, added in FP64.
+void group_gemm_cn_c64_to_c128(kss_ctx ctx, const GemmItem* d_items, int n, int blocks, int rblocks);
+
+// Grouped split-BF16 complex64 products on the tensor cores (gemm_tc.cu), for the batch engine:
+// the same product of every unit in one persistent launch (plus one launch that splits the B
+// operands into BF16 hi/lo rows, and one that adds K-split partial sums when any product is split).
+// Product i: C_i = ar * rs[r] * op(A_i) B_i + br * C_i with A_i given in split form (tc_split_cn /
+// tc_split_nn: 2 M rows of 2 kpad(K) BF16) and B_i a K x N complex64 block (column j has K values
+// at Bsrc + j ldb).  Shapes and the A operands are fixed by build(); B sources, outputs,
+// coefficients and idle flags are per step (set(), uploaded with upload(), read by the launches,
+// so a CUDA graph of the launches follows later uploads).
+struct TcGroupSpec {
+  const void* Atc;
+  int M, N, K;
+  long long ldb, ldc;
+  const float* rs;  // real scale of output row i (null: 1)
+};
+class TcGroupPlan {
+ public:
+  void build(kss_ctx ctx, const std::vector<TcGroupSpec>& specs, int steps);
+  void set(int step, int i, const void* Bsrc, void* C, float ar, float br, bool idle);
+  void upload(cudaStream_t st);
+  void launch(kss_ctx ctx, int step, const char* tag) const;
+  int nprod() const { return n_; }
+  int tile_cols() const { return tnp_; }
+  int works() const { return nwork_; }
+  bool split() const { return any_split_; }
+
+ private:
+  int n_ = 0, steps_ = 0, tnp_ = 128, nwork_ = 0, prep_blocks_ = 0;
+  long long comb_blocks_ = 0;
+  bool any_split_ = false;
+  size_t prod_bytes_ = 0, prep_bytes_ = 0;
+  std::vector<unsigned char> h_prod_, h_prep_;
+  DevBuf d_maps_, d_prod_, d_prep_, d_btc_, d_part_;
+};
 
 // Complex64 GEMMs on the tensor cores (BF16 hi/lo split, FP32 accumulation in TMEM).
 void tc_gemm_cn(kss_ctx ctx, int M, int N, int K, const void* A, int lda, const void* B, int ldb,

@@ -852,6 +852,9 @@ void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, v
     if (f64)
       oz_gemm_cn(ctx, s->nproj, nb, kd.npw, kd.d_beta64.p, kd.npw, psi, ld, ctx->ws_cprj.p, s->nproj, 1.0, 0.0,
                  0.0, 0.0, "cprj", &beta_oz_cn(s, ik));
+    else if (c.fp32_proj)
+      gemm_cn(ctx, false, s->nproj, nb, kd.npw, kd.d_beta32.p, kd.npw, psi, ld, ctx->ws_cprj.p, s->nproj, 1.0, 0.0,
+              0.0, 0.0, "cprj");
     else
       tc_gemm_cn_split(ctx, s->nproj, nb, kd.npw, beta_split_cn(s, ik), psi, ld, ctx->ws_cprj.p, s->nproj,
                        1.0, 0.0, 0.0, 0.0, "cprj");
@@ -867,6 +870,9 @@ void apply_h(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, v
     if (f64)
       oz_gemm_nn(ctx, kd.npw, nb, s->nproj, kd.d_beta64.p, kd.npw, ctx->ws_cprj.p, s->nproj, out, ld, 1.0, 0.0,
                  1.0, 0.0, "nonlocal", &beta_oz_nn(s, ik));
+    else if (c.fp32_proj)
+      gemm_nn(ctx, false, kd.npw, nb, s->nproj, kd.d_beta32.p, kd.npw, ctx->ws_cprj.p, s->nproj, out, ld, 1.0, 0.0,
+              1.0, 0.0, "nonlocal");
     else
       tc_gemm_nn_split(ctx, kd.npw, nb, s->nproj, beta_split_nn(s, ik), ctx->ws_cprj.p, s->nproj, out, ld,
                        1.0, 0.0, 1.0, 0.0, "nonlocal");

@@ -293,6 +293,8 @@ kss_status kss_server_start(kss_ctx ctx, size_t hbm_budget_bytes, int max_slots,
     s->eng.ctx = ctx;
     s->eng.f64 = s->opts.prec == KSS_PREC_FP64;
     s->eng.degree = s->opts.degree;
+    s->eng.use_graph = !(s->opts.flags & KSS_SOLVE_BATCH_NO_GRAPH);
+    s->eng.use_tc_gemm = !(s->opts.flags & KSS_SOLVE_BATCH_FP32_PROJ);
     s->cache_cap = hbm_budget_bytes / 10;
     ctx->server = s.release();
   });

@@ -342,7 +342,7 @@ void gamma_fix(kss_solver_s* s, bool f64, void* X, void* HX) {
 }
 
 void apply_block(kss_solver_s* s, bool f64, const void* psi, void* out) {
-  apply_h(s->sys, s->ik, s->nb, psi, nullptr, out, s->npw, ChebCoef{1, 0, 0, s->gamma},
+  apply_h(s->sys, s->ik, s->nb, psi, nullptr, out, s->npw, ChebCoef{1, 0, 0, s->gamma, s->proj32},
           f64 ? KSS_PREC_FP64 : KSS_PREC_MIXED);
   s->napply += s->nb;
 }
@@ -392,7 +392,7 @@ int chebyshev_filter(kss_solver_s* s, int f1, int* prev_out) {
   {
     const double al = sigma1 / e;
     apply_filter_op(s->sys, s->ik, nb, s->blk[cur].p, nullptr, s->blk[prev].p, s->npw,
-                    ChebCoef{al, -al * c, 0.0, s->gamma}, p);
+                    ChebCoef{al, -al * c, 0.0, s->gamma, s->proj32}, p);
     s->napply += nb;
     std::swap(cur, prev);  // cur = Y_1, prev = X
   }
@@ -403,7 +403,7 @@ int chebyshev_filter(kss_solver_s* s, int f1, int* prev_out) {
     const double al = 2.0 * sn / e;
     // Y_j = (2 sn / e)(H - c) Y_{j-1} - sigma sn Y_{j-2}, written over Y_{j-2}
     apply_filter_op(s->sys, s->ik, nb, s->blk[cur].p, s->blk[prev].p, s->blk[prev].p, s->npw,
-                    ChebCoef{al, -al * c, -sigma * sn, s->gamma}, p);
+                    ChebCoef{al, -al * c, -sigma * sn, s->gamma, s->proj32}, p);
     s->napply += nb;
     std::swap(cur, prev);
     sigma = sn;
@@ -505,6 +505,13 @@ void after_iterate(kss_solver_s* s) {
     if (r <= s->tol || stalled || s->iter >= s->o.max_iter) {
       refine_fp64(s);
       s->converged = max_wanted(s) <= s->tol;
+      // The split-BF16 projector products bound the residual the single-precision filter can
+      // reach; a block that misses the tolerance in the FP64 check continues with FP32 products.
+      if (!s->converged && !s->proj32 && s->sys->nproj && s->iter < s->o.max_iter) {
+        s->proj32 = true;
+        s->hist.clear();
+        return;
+      }
       s->done = true;
     }
   }

@@ -408,6 +408,8 @@ def kss_apply_H_host(sys: System, ik: int, psi: np.ndarray, hpsi: np.ndarray,
 # eigensolver
 
 KSS_SOLVE_NO_GAMMA_REAL = 1
+KSS_SOLVE_BATCH_NO_GRAPH = 2
+KSS_SOLVE_BATCH_FP32_PROJ = 4
 
 
 def make_opts(degree=10, tol=0.0, max_iter=0, nbuffer=-1, prec=KSS_PREC_FP64, seed=1234,
@@ -633,7 +635,7 @@ def kss_dense_hegv_phase_ms(ctx) -> dict:
 
 class kss_gemm_tune_entry(ctypes.Structure):
     _fields_ = [("device", c_int), ("kind", c_int), ("Mr", c_int), ("Nr", c_int), ("kblocks", c_int),
-                ("splits", c_int), ("ms", c_double), ("ncand", c_int)]
+                ("splits", c_int), ("ms", c_double), ("ncand", c_int), ("form", c_int)]
 
 
 def kss_autotune_gemm_table():
@@ -648,9 +650,9 @@ def kss_autotune_gemm_table():
     return out
 
 
-def kss_autotune_gemm_put(device: int, kind: int, Mr: int, Nr: int, kblocks: int, splits: int):
-    """Pin the K-split of a (kind, shape) GEMM configuration."""
-    e = kss_gemm_tune_entry(device, kind, Mr, Nr, kblocks, splits, 0.0, 0)
+def kss_autotune_gemm_put(device: int, kind: int, Mr: int, Nr: int, kblocks: int, splits: int, form: int = 0):
+    """Pin the schedule (kernel form and K-split) of a (kind, shape) GEMM configuration."""
+    e = kss_gemm_tune_entry(device, kind, Mr, Nr, kblocks, splits, 0.0, 0, form)
     _check(lib().kss_autotune_gemm_put(byref(e)))
 
 

@@ -164,8 +164,45 @@ def test_gemm_split_autotuner_and_every_candidate(ctx, prec):
     assert len(entries) == 1 and entries[0]["ncand"] >= 2 and entries[0]["ms"] > 0
     e = entries[0]
     assert e["Mr"] == 2 * M
-    for sp in sorted({1, 2, 3, 5, e["splits"], max(1, e["kblocks"] // 24)}):
-        K.kss_autotune_gemm_put(e["device"], kind, e["Mr"], e["Nr"], e["kblocks"], sp)
-        assert run() < tol, sp
+    forms = (0, 1, 2) if kind == 0 else (0,)
+    if kind == 0:
+        assert e["ncand"] >= 6 and e["form"] in forms
+    for form in forms:
+        for sp in sorted({1, 2, 3, 5, e["splits"], max(1, e["kblocks"] // 24)}):
+            K.kss_autotune_gemm_put(e["device"], kind, e["Mr"], e["Nr"], e["kblocks"], sp, form)
+            assert run() < tol, (form, sp)
+    with pytest.raises(K.KssError):
+        K.kss_autotune_gemm_put(e["device"], kind, e["Mr"], e["Nr"], e["kblocks"], 1, 3)
     K.kss_autotune_clear()
     assert K.kss_autotune_gemm_table() == []
+
+
+@pytest.mark.parametrize("op,M,N,Kd", SHAPES)
+def test_split_bf16_every_form(ctx, op, M, N, Kd):
+    """Every kernel form of the split-BF16 products (one CTA per 128 x 128 tile; persistent CTAs
+    with two TMEM accumulators on 128- and 64-column tiles), with and without a K-split, pinned in
+    turn, gives the numpy product within 1e-4 (alpha and beta complex, ragged edges)."""
+    import torch
+    rng = np.random.default_rng(M * 5 + N * 11 + Kd + op)
+    A = crand(rng, (M, Kd)) if op == 0 else crand(rng, (Kd, M))
+    B = crand(rng, (N, Kd))
+    C0 = crand(rng, (N, M))
+    alpha, beta = 0.6 + 0.3j, -0.4 + 0.2j
+    Am = A.T
+    ref = alpha * ((Am.conj().T if op == 0 else Am) @ B.T) + beta * C0.T
+    tA, tB = (torch.from_numpy(x).to(torch.complex64).cuda() for x in (A, B))
+    kblocks = (2 * Kd + 63) // 64
+    K.kss_autotune_clear()
+    try:
+        for form in (0, 1, 2):
+            for sp in (1, 4):
+                sp = min(sp, max(1, kblocks // (8 if form == 0 else 4)))
+                K.kss_autotune_gemm_put(0, 0, 2 * M, N, kblocks, sp, form)
+                tC = torch.from_numpy(C0).to(torch.complex64).cuda()
+                K.kss_gemm(ctx, op, tA, tB, tC, alpha, beta, K.KSS_PREC_MIXED)
+                torch.cuda.synchronize()
+                got = tC.cpu().numpy().T
+                err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+                assert err < 1e-4, (form, sp, err)
+    finally:
+        K.kss_autotune_clear()
