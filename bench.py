@@ -29,7 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal); a CUDA-core FMA probe measured 1.19 at ~1990 MHz
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; 152 SMs x 2 FMA per clock x 2 x 2070 MHz = 1.26)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
 
 
@@ -247,6 +247,7 @@ def run_reference(args, rank: int):
 # null traffic when the autotuner picked another).
 PASS_B_DRAM_PER_BAND = {"fp64": (73.533824e6 + 7.281024e6) / 27, "mixed": (69.942784e6 + 6.154112e6) / 54}
 PASS_B_SCHEDULE = {"fp64": "8x12 @384", "mixed": "12x8 @384"}
+PASS_B_EXECUTED_PER_ALGORITHMIC = 6.7e7 / (4 * 5 * 96 ** 3 * math.log2(96))
 
 
 def algorithmic_work(s, npw, nb, degree, box, applies, rr_calls):
@@ -521,15 +522,26 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     dom = max(fam, key=lambda f: fam[f][1])
     dl, dms = fam[dom]
     peak = FP64_PEAK_TFLOPS if args.form == "fp64" else FP32_PEAK_TFLOPS
+    # the CUDA cores' FMA throughput measured on this device right after the timed region
+    probe = K.kss_peak_probe(ctx, 0 if args.form == "fp64" else 1)
     roof = None
     if dom in work and dms > 0:
         ach = work[dom] / (dms / 1000.0) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None,
-                "peak_note": ("FP64 CUDA-core rate, nominal 1.25 TFLOP/s (no FP64 figure in the "
-                              "measured peaks; FMA probe 1.19)" if args.form == "fp64" else
-                              "FP32 CUDA-core rate from 152 SMs x 128 lanes x 2 x 2070 MHz"),
+                "peak_note": ("FP64 CUDA-core rate derived from the unit counts and clock: 152 SMs x "
+                              "2 FP64 FMA per clock x 2 flops x 2070 MHz = 1.26, nominal 1.25"
+                              if args.form == "fp64" else
+                              "FP32 CUDA-core rate derived from 152 SMs x 128 lanes x 2 x 2070 MHz"),
+                "measured_peak": probe, "frac_of_measured": ach / probe,
+                "measured_note": "kss_peak_probe in this run: independent FMA chains, 8 CTAs per SM, "
+                                 "best of three launches",
                 "launches": dl, "avg_launch_ms": dms / dl}
+        if dom == "local_pass_b" and args.form == "fp64":
+            # FP64 instructions the pruned pass executes (ncu count: 6.7e7 flops per band, 2 per
+            # DFMA, 1 per DADD / DMUL) over the dense-transform count 4 x 5 N^3 log2 N
+            roof["executed_per_algorithmic"] = PASS_B_EXECUTED_PER_ALGORITHMIC
+            roof["executed_frac_of_measured"] = ach * PASS_B_EXECUTED_PER_ALGORITHMIC / probe
 
     # ---- the FP64 products on the tensor cores (FP64 form) ----
     fp64_gemm = None
@@ -640,7 +652,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                        "band_applies_per_step": applies / args.steps,
                        "k_points": "stepped together (kss_solver_step_many): the Rayleigh-Ritz of "
                                    "one k-point on a helper stream beside the filter of the next",
-                       "fft_schedule": sched},
+                       "fft_schedule": sched,
+                       "gemm_schedule": [f"kind {e['kind']} {e['Mr']}x{e['Nr']} x {e['kblocks']} k-blocks: form "
+                                         f"{e['form']}, {e['splits']} split(s)" for e in K.kss_autotune_gemm_table()]},
             "metric_family": "band H-applies/s & eigensolves/s at <=1e-6 Ha vs FP64 oracle; p50/p99 latency",
             "gpu_launches": launches,
             "clocks": ck,

@@ -310,6 +310,14 @@ kss_status kss_dense_hegv_phase_ms(kss_ctx ctx, double* ms);
  * KSS_EINVAL for a limit out of range. */
 kss_status kss_selftest_bounded_wait(kss_ctx ctx, double limit_ms);
 
+/* Measured fused multiply-add throughput of the CUDA cores on the context's device, the
+ * denominator of the ALU rooflines of the FFT passes (measurement support; the paper has no
+ * counterpart).  pipe 0: FP64, 1: FP32.  Every thread of a grid of 8 CTAs per SM runs 8
+ * independent FMA chains; *tflops is the best of three timed launches (2 flops per FMA, CUDA
+ * events on the context stream; synchronises it).  Errors: KSS_EINVAL (NULL, pipe not 0 or 1),
+ * KSS_ECUDA. */
+kss_status kss_peak_probe(kss_ctx ctx, int pipe, double* tflops);
+
 /* ------------------------------------------------------------------------------------------
  * Electron density after the solve (Eq. nandtau, §2)
  * ------------------------------------------------------------------------------------------ */

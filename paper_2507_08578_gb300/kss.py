@@ -128,6 +128,7 @@ def signatures() -> dict:
         "kss_gemm": ([P, c_int, c_int, c_int, c_int, P, c_int, P, c_int, P, c_int, c_double,
                       c_double, c_double, c_double, c_int], c_int),
         "kss_selftest_bounded_wait": ([P, c_double], c_int),
+        "kss_peak_probe": ([P, c_int, POINTER(c_double)], c_int),
         "kss_solve_batch": ([P, c_int, P, P, P, POINTER(kss_solve_opts), P, P, P], c_int),
         "kss_server_start": ([P, c_size_t, c_int, POINTER(kss_solve_opts)], c_int),
         "kss_server_submit": ([P, POINTER(kss_cell), POINTER(kss_atoms), c_int, POINTER(c_uint64)], c_int),
@@ -654,6 +655,13 @@ def kss_autotune_gemm_put(device: int, kind: int, Mr: int, Nr: int, kblocks: int
     """Pin the schedule (kernel form and K-split) of a (kind, shape) GEMM configuration."""
     e = kss_gemm_tune_entry(device, kind, Mr, Nr, kblocks, splits, 0.0, 0, form)
     _check(lib().kss_autotune_gemm_put(byref(e)))
+
+
+def kss_peak_probe(ctx, pipe: int) -> float:
+    """Measured FMA throughput (TFLOP/s) of the CUDA cores: pipe 0 FP64, 1 FP32."""
+    v = c_double()
+    _check(lib().kss_peak_probe(ctx, int(pipe), byref(v)), ctx)
+    return v.value
 
 
 def kss_selftest_bounded_wait(ctx, limit_ms: float = 50.0) -> int:
