@@ -79,6 +79,8 @@ def parse():
                     help="c4/c5: issue the batch filter's launches directly instead of replaying a CUDA "
                          "graph, so that the kernel table times every launch (profiling)")
     ap.add_argument("--requests", type=int, default=60, help="c5: number of requests")
+    ap.add_argument("--systems", type=int, default=48, help="c4: systems in the batch (48: config 4; "
+                                                                "fewer: a small case for profiling)")
     ap.add_argument("--no-extras", action="store_true",
                     help="c2 line without the full-solve, config-3 and served measurements")
     args = ap.parse_args()
@@ -734,7 +736,7 @@ def run_c4(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     B.build()
-    systems = W.config4(48)
+    systems = W.config4(48)[:max(1, min(48, args.systems))]
     # (system, k-point) units, split across ranks by a greedy longest-processing-time assignment
     all_units = [(j, ik) for j, s in enumerate(systems) for ik in range(len(s.kpts))]
     costs = [MR.unit_cost(int(MR.npw_estimate(abs(np.linalg.det(systems[j].lattice)), systems[j].ecut)),
@@ -780,7 +782,7 @@ def run_c4(args):
                       "unit": "systems solved/s", "n_gpus": world, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
                       "higher_is_better": True, "dtype": "c64+f64", "data": "synthetic",
-                      "config": {"workload": f"C4: 48 systems, {len(all_units)} (system,k) units in one "
+                      "config": {"workload": f"C4: {len(systems)} systems, {len(all_units)} (system,k) units in one "
                                              "lockstep batch (grouped launches, " +
                                              ("filter launched directly" if args.no_graph else "CUDA-graph filter") +
                                              "), mixed precision"},
