@@ -476,7 +476,8 @@ typedef struct {
   long long completed, rejected, warm_hits;
   double p50_ms, p99_ms, mean_ms;  /* latency submit -> done, over completed requests */
   double solves_per_s;             /* completed requests / (last completion - first submit) */
-  size_t peak_bytes, in_flight_bytes;  /* admission accounting (estimated footprints) */
+  size_t peak_bytes, in_flight_bytes;  /* admission accounting: device bytes of the admitted requests
+                                        (system tables + one solver footprint per k-point) */
 } kss_server_stats;
 
 /* Start a server on the context.  Requests are admitted in arrival order while the sum of their

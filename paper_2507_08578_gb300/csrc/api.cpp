@@ -685,6 +685,32 @@ kss_status kss_selftest_bounded_wait(kss_ctx ctx, double limit_ms) {
   });
 }
 
+}  // extern "C"
+
+namespace kss {
+// Device bytes held by a system's tables (V grids and views, twiddles, D, and every k-point's
+// sphere maps, kinetic energies and projector tables, including the lazily built split forms
+// present so far).
+size_t sys_device_bytes(kss_sys s) {
+  size_t b = s->d_V64.bytes + s->d_Vx64.bytes + s->d_Vx32.bytes + s->d_D64.bytes + s->d_D32.bytes +
+             s->d_Q64.bytes + s->d_Q32.bytes;
+  for (int i = 0; i < 3; ++i) b += s->d_tw64[i].bytes + s->d_tw32[i].bytes;
+  for (const auto& kv : s->vpi64) b += kv.second.bytes;
+  for (const auto& kv : s->vpi32) b += kv.second.bytes;
+  for (const auto& kv : s->vfused32) b += kv.second.bytes;
+  for (const KData& kd : s->k) {
+    const DevBuf* bufs[] = {&kd.d_miller, &kd.d_offset, &kd.d_tileidx, &kd.d_zstart, &kd.d_rowrange,
+                            &kd.d_kin64,  &kd.d_kin32,  &kd.d_beta64,  &kd.d_beta32, &kd.d_btc_cn,
+                            &kd.d_btc_nn, &kd.d_oz_cn,  &kd.d_oz_nn,   &kd.d_q,      &kd.d_mirror,
+                            &kd.d_G64,    &kd.d_G32,    &kd.d_W64,     &kd.d_W32};
+    for (const DevBuf* d : bufs) b += d->bytes;
+  }
+  return b;
+}
+}  // namespace kss
+
+extern "C" {
+
 kss_status kss_footprint(kss_sys sys, int nband, kss_precision prec, size_t* bytes) {
   if (!sys || !bytes || nband < 1) return KSS_EINVAL;
   size_t m = 0;

@@ -45,21 +45,20 @@ __global__ void __launch_bounds__(NT) pass_dw(LocalArgs<T> a, int m, int G, cons
   for (int r = 0; r < R; ++r)
 #pragma unroll
     for (int j = 0; j < B; ++j) acc[r][j] = 0;
+  const fftr::FastDiv dw2(W2), dw3(W3);
   for (int b = g; b < m; b += G) {
     __syncthreads();  // the previous band's reads of Q and Z are done
     for (int i = tid; i < W3 * QS; i += NT) Q[i] = C{0, 0};
     __syncthreads();
     const C* slab = a.work + ((size_t)b * a.N1 + x) * W3 * W2;
     for (int i = tid; i < W3 * W2; i += NT) {
-      const int u3 = i / W2, u2 = i - u3 * W2;
-      int y = (a.lo2 + u2) % N;
-      if (y < 0) y += N;
-      Q[u3 * QS + y] = slab[i];
+      const int u3 = dw2(i), u2 = i - u3 * W2;
+      Q[u3 * QS + fftr::wrap_add(a.lo2, u2, N)] = slab[i];
     }
     __syncthreads();
     // y inverse (two stages, in place; leaves position k2 + B k holding y = k + A k2)
     for (int t = tid; t < W3 * B; t += NT) {
-      const int r = t / W3, u = t - r * W3;  // rows fastest across lanes
+      const int r = dw3(t), u = t - r * W3;  // rows fastest across lanes
       C* row = Q + u * QS + r;
       C v[A];
 #pragma unroll
@@ -76,7 +75,7 @@ __global__ void __launch_bounds__(NT) pass_dw(LocalArgs<T> a, int m, int G, cons
     }
     __syncthreads();
     for (int t = tid; t < W3 * A; t += NT) {
-      const int k = t / W3, u = t - k * W3;
+      const int k = dw3(t), u = t - k * W3;
       C* row = Q + u * QS + B * k;
       C v[B];
 #pragma unroll

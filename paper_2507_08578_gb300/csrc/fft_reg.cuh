@@ -16,6 +16,23 @@
 namespace kss {
 namespace fftr {
 
+// floor(t / d) for 0 <= t < 2^22 and d >= 1 by one multiply with the float reciprocal of d (the
+// index arithmetic of the CTA-wide task loops, whose divisors are runtime window sizes): (t + 1/2)/d
+// lies at least 1/(2d) from an integer, and the roundings of the reciprocal and of the product
+// move it by at most 2^-23 (t + 1/2)/d < 1/(2d), so truncation gives the exact quotient.
+struct FastDiv {
+  float r;
+  __device__ __forceinline__ explicit FastDiv(int d) : r(1.0f / (float)d) {}
+  __device__ __forceinline__ int operator()(int t) const { return __float2int_rz(((float)t + 0.5f) * r); }
+};
+// (lo + u) mod n for lo in (-n, n) and 0 <= u < n (a window index to a box coordinate).
+__device__ __forceinline__ int wrap_add(int lo, int u, int n) {
+  int y = lo + u;
+  if (y < 0) y += n;
+  if (y >= n) y -= n;
+  return y;
+}
+
 // ---- compile-time trig: cos/sin(2 pi m / n) --------------------------------------------------
 __host__ __device__ constexpr double taylor_sin(double x) {
   double x2 = x * x, term = x, sum = x;

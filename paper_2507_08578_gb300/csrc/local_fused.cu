@@ -176,6 +176,7 @@ __device__ void fused_band(const FusedSmem& m, const FusedArgs& a, int n) {
   const int W2 = a.W2, W3 = a.W3;
   const int npx = W2 * W3;  // x pencils: (y, z) in the sphere window
   const int npy = N * W3;   // y pencils: (x position, z in the window)
+  const fftr::FastDiv dw2(W2), dnpx(npx), dnpy(npy), dn1p(a.N1p);
   const int g0 = zst[0], g1 = zst[W3];
   // slice of a sphere point: the last u3 with zst[u3] <= g
   auto slice_of = [&](int g) {
@@ -190,7 +191,7 @@ __device__ void fused_band(const FusedSmem& m, const FusedArgs& a, int n) {
   // ---- zero the window's x pencils, scatter the plane waves ----
   for (int i = tid; i < npx * N; i += NT) {
     const int p = i / N, x = i - p * N;
-    const int u3 = p / W2, u2 = p - u3 * W2;
+    const int u3 = dw2(p), u2 = p - u3 * W2;
     box[zwin[u3] * P2 + ywin[u2] * P1 + x] = make_float2(0.f, 0.f);
   }
   __syncthreads();
@@ -200,7 +201,7 @@ __device__ void fused_band(const FusedSmem& m, const FusedArgs& a, int n) {
     for (int g = g0 + tid; g < g1; g += NT) {
       const int u3 = slice_of(g);
       const int t = a.tileidx[g];
-      const int u2 = t / a.N1p, x = t - u2 * a.N1p;
+      const int u2 = dn1p(t), x = t - u2 * a.N1p;
       float2 v = pa[g];
       if (pb) {  // psi_2n + i psi_2n+1
         const float2 w = pb[g];
@@ -213,8 +214,8 @@ __device__ void fused_band(const FusedSmem& m, const FusedArgs& a, int n) {
   __syncthreads();
   // ---- x, inverse ----
   for (int t = tid; t < npx * B; t += NT) {
-    const int r = t / npx, p = t - r * npx;
-    const int u3 = p / W2, u2 = p - u3 * W2;
+    const int r = dnpx(t), p = t - r * npx;
+    const int u3 = dw2(p), u2 = p - u3 * W2;
     float2* row = box + zwin[u3] * P2 + ywin[u2] * P1;
     float2 v[A];
 #pragma unroll
@@ -227,8 +228,8 @@ __device__ void fused_band(const FusedSmem& m, const FusedArgs& a, int n) {
   }
   __syncthreads();
   for (int t = tid; t < npx * A; t += NT) {
-    const int k = t / npx, p = t - k * npx;
-    const int u3 = p / W2, u2 = p - u3 * W2;
+    const int k = dnpx(t), p = t - k * npx;
+    const int u3 = dw2(p), u2 = p - u3 * W2;
     float2* row = box + zwin[u3] * P2 + ywin[u2] * P1 + B * k;
     float2 v[B];
 #pragma unroll
@@ -240,7 +241,7 @@ __device__ void fused_band(const FusedSmem& m, const FusedArgs& a, int n) {
   __syncthreads();
   // ---- y, inverse (the W3 window planes; rows outside the y window read as zero) ----
   for (int t = tid; t < npy * B; t += NT) {
-    const int r = t / npy, p = t - r * npy;
+    const int r = dnpy(t), p = t - r * npy;
     const int u3 = p / N, x = p - u3 * N;
     float2* col = box + zwin[u3] * P2 + x;
     float2 v[A];
@@ -254,7 +255,7 @@ __device__ void fused_band(const FusedSmem& m, const FusedArgs& a, int n) {
   }
   __syncthreads();
   for (int t = tid; t < npy * A; t += NT) {
-    const int k = t / npy, p = t - k * npy;
+    const int k = dnpy(t), p = t - k * npy;
     const int u3 = p / N, x = p - u3 * N;
     float2* col = box + zwin[u3] * P2 + x + (B * k) * P1;
     float2 v[B];
@@ -316,7 +317,7 @@ __device__ void fused_band(const FusedSmem& m, const FusedArgs& a, int n) {
   __syncthreads();
   // ---- y, forward (window planes; only the window rows are kept) ----
   for (int t = tid; t < npy * A; t += NT) {
-    const int r = t / npy, p = t - r * npy;
+    const int r = dnpy(t), p = t - r * npy;
     const int u3 = p / N, x = p - u3 * N;
     float2* col = box + zwin[u3] * P2 + x + (B * r) * P1;
     float2 v[B];
@@ -330,7 +331,7 @@ __device__ void fused_band(const FusedSmem& m, const FusedArgs& a, int n) {
   }
   __syncthreads();
   for (int t = tid; t < npy * B; t += NT) {
-    const int q = t / npy, p = t - q * npy;
+    const int q = dnpy(t), p = t - q * npy;
     const int u3 = p / N, x = p - u3 * N;
     float2* col = box + zwin[u3] * P2 + x;
     float2 v[A];
@@ -344,8 +345,8 @@ __device__ void fused_band(const FusedSmem& m, const FusedArgs& a, int n) {
   __syncthreads();
   // ---- x, forward (window pencils) ----
   for (int t = tid; t < npx * A; t += NT) {
-    const int r = t / npx, p = t - r * npx;
-    const int u3 = p / W2, u2 = p - u3 * W2;
+    const int r = dnpx(t), p = t - r * npx;
+    const int u3 = dw2(p), u2 = p - u3 * W2;
     float2* row = box + zwin[u3] * P2 + ywin[u2] * P1 + B * r;
     float2 v[B];
 #pragma unroll
@@ -358,8 +359,8 @@ __device__ void fused_band(const FusedSmem& m, const FusedArgs& a, int n) {
   }
   __syncthreads();
   for (int t = tid; t < npx * B; t += NT) {
-    const int q = t / npx, p = t - q * npx;
-    const int u3 = p / W2, u2 = p - u3 * W2;
+    const int q = dnpx(t), p = t - q * npx;
+    const int u3 = dw2(p), u2 = p - u3 * W2;
     float2* row = box + zwin[u3] * P2 + ywin[u2] * P1;
     float2 v[A];
 #pragma unroll
@@ -380,7 +381,7 @@ __device__ void fused_band(const FusedSmem& m, const FusedArgs& a, int n) {
     for (int g = g0 + tid; g < g1; g += NT) {
       const int u3 = slice_of(g);
       const int t = a.tileidx[g];
-      const int u2 = t / a.N1p, x = t - u2 * a.N1p;
+      const int u2 = dn1p(t), x = t - u2 * a.N1p;
       const float2 v = box[zwin[u3] * P2 + ywin[u2] * P1 + x];
       if (a.packed) {  // raw transform of the pair; unpacked and finished by gamma_unpack
         po[g] = v;

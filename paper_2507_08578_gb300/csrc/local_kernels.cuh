@@ -341,8 +341,9 @@ __device__ __forceinline__ void pass_a_body(const LocalArgs<T>& a, const RegPlan
   __syncthreads();
   C* dst = a.work + ((size_t)nl * a.N1 * a.W3 + u3) * a.W2;
   const size_t xs = (size_t)a.W3 * a.W2;
+  const fftr::FastDiv dw2(a.W2);
   for (int i = threadIdx.x; i < a.N1 * a.W2; i += kThreads) {
-    const int x = i / a.W2, u2 = i - x * a.W2;
+    const int x = dw2(i), u2 = i - x * a.W2;
     dst[x * xs + u2] = tile[u2 * a.N1p + x];
   }
 }
@@ -368,11 +369,10 @@ __device__ __forceinline__ void pass_b_body(const LocalArgs<T>& a, const RegPlan
   for (int i = threadIdx.x; i < a.W3 * a.N2p; i += kThreads) Q[i] = C{0, 0};
   __syncthreads();
   C* slab = a.work + ((size_t)nl * a.N1 + x) * a.W3 * a.W2;
+  const fftr::FastDiv dw2(a.W2);
   for (int i = threadIdx.x; i < a.W3 * a.W2; i += kThreads) {
-    const int u3 = i / a.W2, u2 = i - u3 * a.W2;
-    int y = (a.lo2 + u2) % a.N2;
-    if (y < 0) y += a.N2;
-    Q[u3 * a.N2p + y] = slab[i];
+    const int u3 = dw2(i), u2 = i - u3 * a.W2;
+    Q[u3 * a.N2p + fftr::wrap_add(a.lo2, u2, a.N2)] = slab[i];
   }
   __syncthreads();
   const int N2p = a.N2p;
@@ -415,10 +415,8 @@ __device__ __forceinline__ void pass_b_body(const LocalArgs<T>& a, const RegPlan
   }
   __syncthreads();
   for (int i = threadIdx.x; i < a.W3 * a.W2; i += kThreads) {
-    const int u3 = i / a.W2, u2 = i - u3 * a.W2;
-    int y = (a.lo2 + u2) % a.N2;
-    if (y < 0) y += a.N2;
-    slab[i] = Q[u3 * a.N2p + y];
+    const int u3 = dw2(i), u2 = i - u3 * a.W2;
+    slab[i] = Q[u3 * a.N2p + fftr::wrap_add(a.lo2, u2, a.N2)];
   }
 }
 
@@ -437,8 +435,9 @@ __device__ __forceinline__ void pass_c_body(const LocalArgs<T>& a, const RegPlan
   const int nrows = r1 - r0 + 1;
   const C* src = a.work + ((size_t)nl * a.N1 * a.W3 + u3) * a.W2;
   const size_t xs = (size_t)a.W3 * a.W2;
+  const fftr::FastDiv dnr(nrows);
   for (int i = threadIdx.x; i < a.N1 * nrows; i += kThreads) {
-    const int x = i / nrows, u2 = r0 + (i - x * nrows);
+    const int x = dnr(i), u2 = r0 + (i - x * nrows);
     tile[u2 * a.N1p + x] = src[x * xs + u2];
   }
   __syncthreads();
@@ -528,16 +527,15 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   for (int i = tid; i < W3 * QS; i += NT) Q[i] = C{0, 0};
   __syncthreads();
   C* slab = a.work + ((size_t)nl * a.N1 + x) * W3 * W2;
+  const fftr::FastDiv dw2(W2), dw3(W3);
   for (int i = tid; i < W3 * W2; i += NT) {
-    const int u3 = i / W2, u2 = i - u3 * W2;
-    int y = (a.lo2 + u2) % N;
-    if (y < 0) y += N;
-    Q[u3 * QS + y] = slab[i];
+    const int u3 = dw2(i), u2 = i - u3 * W2;
+    Q[u3 * QS + fftr::wrap_add(a.lo2, u2, N)] = slab[i];
   }
   __syncthreads();
   // ---- y, inverse ----
   for (int t = tid; t < W3 * B; t += NT) {
-    const int r = t / W3, u = t - r * W3;  // rows fastest across lanes
+    const int r = dw3(t), u = t - r * W3;  // rows fastest across lanes
     C* row = Q + u * QS + r;
     C v[A];
 #pragma unroll
@@ -554,7 +552,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   }
   __syncthreads();
   for (int t = tid; t < W3 * A; t += NT) {
-    const int k = t / W3, u = t - k * W3;
+    const int k = dw3(t), u = t - k * W3;
     C* row = Q + u * QS + B * k;
     C v[B];
 #pragma unroll
@@ -626,7 +624,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   __syncthreads();
   // ---- y, forward ----
   for (int t = tid; t < W3 * A; t += NT) {
-    const int r = t / W3, u = t - r * W3;
+    const int r = dw3(t), u = t - r * W3;
     C* row = Q + u * QS + B * r;
     C v[B];
 #pragma unroll
@@ -639,7 +637,7 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   }
   __syncthreads();
   for (int t = tid; t < W3 * B; t += NT) {
-    const int q = t / W3, u = t - q * W3;
+    const int q = dw3(t), u = t - q * W3;
     C* row = Q + u * QS + q;
     C v[A];
 #pragma unroll
@@ -650,10 +648,8 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   }
   __syncthreads();
   for (int i = tid; i < W3 * W2; i += NT) {
-    const int u3 = i / W2, u2 = i - u3 * W2;
-    int y = (a.lo2 + u2) % N;
-    if (y < 0) y += N;
-    slab[i] = Q[u3 * QS + y];
+    const int u3 = dw2(i), u2 = i - u3 * W2;
+    slab[i] = Q[u3 * QS + fftr::wrap_add(a.lo2, u2, N)];
   }
 }
 

@@ -105,7 +105,7 @@ struct Server {
     while (!pending.empty()) {
       Request& r = reqs[pending.front()];
       const int nk = (int)(r.kpts.size() / 3);
-      const size_t need = estimate(r);
+      size_t need = estimate(r);
       const bool first = slots == 0 && used == 0;
       if (!first && (slots + nk > max_slots || used + need > budget)) break;
       pending.pop_front();
@@ -150,6 +150,11 @@ struct Server {
           lru.push_front(r.key);
         }
         r.admitted = true;
+        // Charged from here on: what the request holds, its system's tables plus one solver per
+        // k-point (kss_footprint: blocks, Rayleigh-Ritz matrices, workspaces, split projector
+        // tables); the estimate above only decided the admission.
+        size_t fp = 0;
+        if (kss_footprint(r.sys, r.nband, opts.prec, &fp) == KSS_OK) need = sys_device_bytes(r.sys) + (size_t)nk * fp;
         r.bytes = need;
         used += need;
         slots += nk;

@@ -176,6 +176,48 @@ def test_server_same_result_alone_and_in_mix_mixed_precision(ctx):
             assert np.max(np.abs(r[1][ik] - oracle_levels(s, ik, s.nband))) < 1e-6
 
 
+def test_server_charges_what_requests_hold(ctx):
+    """The server charges each admitted request the device bytes it holds (its system's tables plus
+    one solver footprint per k-point): during a served mix the device memory the process gained
+    stays within that accounting's peak plus the shared engine workspaces, the accounting never
+    exceeds the budget, and everything is released when the requests complete."""
+    import torch
+    opts = K.make_opts(seed=6, prec=K.KSS_PREC_MIXED)
+    reqs = W.config5(6, rate=200.0)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    budget = 150 << 30
+    K.kss_server_start(ctx, budget, 64, opts)
+    try:
+        tickets = [submit(ctx, r.system) for r in reqs]
+        shapes = [(len(r.system.kpts), r.system.nband) for r in reqs]
+        grown, charged = 0, 0
+        out = {}
+        import time
+        t0 = time.time()
+        while len(out) < len(tickets):
+            K.kss_server_pump(ctx, 50.0)
+            torch.cuda.synchronize()
+            grown = max(grown, free0 - torch.cuda.mem_get_info()[0])
+            st = K.kss_server_get_stats(ctx)
+            charged = max(charged, st["in_flight_bytes"])
+            assert st["in_flight_bytes"] <= budget
+            for t, (nk, nb) in zip(tickets, shapes):
+                if t not in out:
+                    r = K.kss_server_poll(ctx, t, nk, nb)
+                    if r is not None:
+                        out[t] = r
+            assert time.time() - t0 < 180.0
+        st = K.kss_server_get_stats(ctx)
+    finally:
+        K.kss_server_stop(ctx)
+    assert all(out[t][0] == K.KSS_OK for t in tickets)
+    assert st["in_flight_bytes"] == 0 and st["peak_bytes"] >= charged > 0
+    # engine workspaces (FFT slabs, split operands of the grouped products, CUDA graph) are shared
+    # by the batch and not charged per request: allow them, and the warm-start cache, on top
+    assert grown <= 2.0 * st["peak_bytes"] + (1 << 30), (grown, st["peak_bytes"])
+
+
 def test_server_admission_budget_and_busy(ctx):
     opts = K.make_opts(seed=4, prec=K.KSS_PREC_MIXED)  # default mixed tolerance (FP32 filter)
     systems = small_systems()
