@@ -545,7 +545,7 @@ kss_status kss_profile_entry(kss_ctx ctx, int i, const char** name, long long* l
  * The y/z transforms of one x-plane (the middle pass of the local-potential path) have several
  * kernel schedules for a box length N: a split N = A * B into two register codelets
  * (A, B <= 16, e.g. 96 = 8 x 12, 12 x 8, 6 x 16, 16 x 6), spread over 256 or 384 threads per
- * CTA, or a per-warp form.  With autotuning on, the first use of a (device, precision, box,
+ * CTA (also 128 in single precision), or a per-warp form.  With autotuning on, the first use of a (device, precision, box,
  * sphere window) configuration times every candidate on a scratch slab and keeps the fastest
  * for the rest of the process.  The candidates compute the same transform and differ only in
  * rounding order (results agree to a few ulps).  Tuning never runs inside a CUDA stream capture
@@ -573,7 +573,7 @@ kss_status kss_autotune_get(int i, kss_tune_entry* out);
  * A, B, threads as in kss_tune_entry (ms, ncand, W2 ignored).  A pinned schedule without a
  * kernel instance, or whose shared memory does not fit a configuration's window, falls back to
  * the per-warp form at use.  KSS_EINVAL for inconsistent fields (A * B != N, threads not in
- * {0, 256, 384}, W3 outside [1, N], unknown precision). */
+ * {0, 128, 256, 384}, W3 outside [1, N], unknown precision). */
 kss_status kss_autotune_put(const kss_tune_entry* e);
 /* Empty the tables of the FFT schedules and of the GEMM K-splits below (later configurations are
  * tuned again).  Cannot fail (returns KSS_OK). */

@@ -299,7 +299,7 @@ void BatchEngine::prepare_t() {
     if (bs[u].threads && (!group_kernel_w<T>(bs[u].A, bs[u].B, bs[u].threads) ||
                           wide_b_smem(au.N2, au.W3, es) > 227 * 1024 || au.N2 != au.N3))
       bs[u].threads = 0;
-    const long long k2 = bs[u].threads ? 10001 + (long long)(bs[u].A * 32 + bs[u].B) * 2 + (bs[u].threads == 384)
+    const long long k2 = bs[u].threads ? 10001 + (long long)(bs[u].A * 32 + bs[u].B) * 3 + bs[u].threads / 128 - 1
                                        : (long long)(c23 + 1);
     key[u] = {(long long)(c1 + 1) * 100000 + k2, u};
     if (sizeof(T) == 4 && fused_code(units[u]->sys)) key[u].first = -100000 + fused_code(units[u]->sys);

@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(NT) group_passw(const LocalItem<T>* __restrict
 template <typename T>
 using GroupKernel = void (*)(const LocalItem<T>*, int, int);
 
-// Grouped CTA-wide pass B for split (A, B) at nt threads (256 or 384); nullptr when no instance
+// Grouped CTA-wide pass B for split (A, B) at nt threads (128 in single precision, 256 or 384);
+// nullptr when no instance
 // exists.  Instances live in batch_wide_f32.cu / batch_wide_f64.cu.
 template <typename T>
 GroupKernel<T> group_kernel_w(int A, int B, int nt);

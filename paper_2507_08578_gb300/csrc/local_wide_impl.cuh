@@ -1,5 +1,5 @@
 // Kernel instances of the CTA-wide pass B (local_kernels.cuh, pass_bw_body) for one precision:
-// every split of KSS_WIDE_SPLITS at 256 and 384 threads per CTA.  Included by one translation
+// every split of KSS_WIDE_SPLITS at 256 and 384 threads per CTA (and 128 in single precision).  Included by one translation
 // unit per precision (local_wide_f32.cu, local_wide_f64.cu) so the build compiles them in parallel.
 #pragma once
 
@@ -26,14 +26,23 @@ bool launch_one(const LocalArgs<T>& a, int nbands, cudaStream_t st, bool dry) {
   return true;
 }
 
+// 128-thread instances in single precision only: for the small boxes of batched systems a stage's
+// tasks fill a 128-thread CTA better, and four-warp barriers idle fewer warps.
+template <typename T, int A, int B>
+bool launch_small(const LocalArgs<T>& a, int nbands, cudaStream_t st, bool dry) {
+  if constexpr (sizeof(T) == 4) return launch_one<T, A, B, 128>(a, nbands, st, dry);
+  else return false;
+}
+
 template <typename T>
 bool dispatch(const LocalArgs<T>& a, int A, int B, int nt, int nbands, cudaStream_t st, bool dry) {
-  if (a.N2 != a.N3 || A * B != a.N2 || (nt != 256 && nt != 384)) return false;
+  if (a.N2 != a.N3 || A * B != a.N2 || (nt != 128 && nt != 256 && nt != 384)) return false;
   switch (A * 32 + B) {
-#define KSS_CASE(x, y)                                                       \
-  case x * 32 + y:                                                           \
-    return nt == 256 ? launch_one<T, x, y, 256>(a, nbands, st, dry)          \
-                     : launch_one<T, x, y, 384>(a, nbands, st, dry);
+#define KSS_CASE(x, y)                                                                \
+  case x * 32 + y:                                                                    \
+    return nt == 128   ? launch_small<T, x, y>(a, nbands, st, dry)                    \
+           : nt == 256 ? launch_one<T, x, y, 256>(a, nbands, st, dry)                 \
+                       : launch_one<T, x, y, 384>(a, nbands, st, dry);
     KSS_WIDE_SPLITS(KSS_CASE)
 #undef KSS_CASE
     default:

@@ -1,6 +1,7 @@
 // Autotuner of the FFT radix schedule of pass B (the y/z transforms of the local-potential path,
 // §5.1 batched FFTs).  For a box length N = N2 = N3 the candidates are the CTA-wide form with
-// every compile-time split N = A * B at 256 and 384 threads per CTA, and the per-warp form.  Each
+// every compile-time split N = A * B at 256 and 384 threads per CTA (and 128 in single precision),
+// and the per-warp form.  Each
 // candidate runs one warm-up and three timed launches (the fastest counts) on a zero-filled
 // scratch slab of the same window and of the production chunk size (CUDA events on the context's
 // stream); the fastest candidate is kept for the process in a table keyed by device, precision,
@@ -62,7 +63,7 @@ PassBSched pass_b_schedule(kss_ctx ctx, const lk::LocalArgs<T>& a, const fftr::S
   std::vector<PassBSched> cand;
   if (a.N2 == a.N3)
     for (const auto& ab : wide_splits())
-      for (int nt : {256, 384})
+      for (int nt : {128, 256, 384})  // 128: single precision only (the dry check says which exist)
         if (ab.first * ab.second == a.N2 && wide_pass_b<T>(t, ab.first, ab.second, nt, 0, nullptr, true))
           cand.push_back(PassBSched{ab.first, ab.second, nt, 0, 0});
   cand.push_back(PassBSched{s2.A, s2.B, 0, 0, 0});
@@ -156,7 +157,7 @@ kss_status kss_autotune_get(int i, kss_tune_entry* out) {
 kss_status kss_autotune_put(const kss_tune_entry* e) {
   if (!e || e->N1 < 2 || e->N < 2 || e->W3 < 1 || e->W3 > e->N ||
       (e->precision != KSS_PREC_FP64 && e->precision != KSS_PREC_MIXED) ||
-      (e->threads != 0 && e->threads != 256 && e->threads != 384) || e->A * e->B != e->N)
+      (e->threads != 0 && e->threads != 128 && e->threads != 256 && e->threads != 384) || e->A * e->B != e->N)
     return KSS_EINVAL;
   const int bytes = e->precision == KSS_PREC_FP64 ? 8 : 4;
   const int W3b = std::min(e->N, (e->W3 + 7) / 8 * 8);

@@ -33,8 +33,9 @@ def wide_splits():
     return [(int(a), int(b)) for a, b in re.findall(r"X\((\d+),\s*(\d+)\)", m.group(1))]
 
 
-def candidates(N):
-    c = [(a, b, nt) for a, b in wide_splits() if a * b == N for nt in (256, 384)]
+def candidates(N, prec=K.KSS_PREC_FP64):
+    nts = (128, 256, 384) if prec == K.KSS_PREC_MIXED else (256, 384)
+    c = [(a, b, nt) for a, b in wide_splits() if a * b == N for nt in nts]
     return c + [(0, 0, 0)]
 
 
@@ -88,7 +89,7 @@ def test_every_schedule_matches_oracle(ctx, name, mk, prec, tol):
         assert len(tab) == 1
         e = tab[0]
         N = box[1]
-        cand = candidates(N)
+        cand = candidates(N, prec)
         assert e["N1"] == box[0] and e["N"] == N and e["ncand"] == len(cand)
         assert (e["A"], e["B"], e["threads"]) in [(a, b, t) for a, b, t in cand if t] or e["threads"] == 0
         assert rel_err_rows(tuned, ref) < tol
@@ -156,7 +157,7 @@ def test_put_rejects_inconsistent_entries(ctx):
     with pytest.raises(K.KssError):
         K.kss_autotune_put(0, K.KSS_PREC_FP64, 24, 24, 15, 5, 5, 256)   # 5 * 5 != 24
     with pytest.raises(K.KssError):
-        K.kss_autotune_put(0, K.KSS_PREC_FP64, 24, 24, 15, 4, 6, 128)   # threads
+        K.kss_autotune_put(0, K.KSS_PREC_FP64, 24, 24, 15, 4, 6, 64)    # threads
     with pytest.raises(K.KssError):
         K.kss_autotune_put(0, 7, 24, 24, 15, 4, 6, 256)                 # precision
     with pytest.raises(K.KssError):
