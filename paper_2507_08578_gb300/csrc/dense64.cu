@@ -5,8 +5,9 @@
 // column-major, lower triangles read), returning all eigenvalues ascending and B-orthonormal
 // eigenvectors, in five phases written out here:
 //
-//   1. Cholesky B = L L^H (right-looking, one rank-1 update of the trailing lower triangle per
-//      column with unscaled columns, then the columns scaled by 1/sqrt(pivot)).
+//   1. Cholesky B = L L^H (blocked right-looking: a 16-column panel at a time, its diagonal block
+//      factored in shared memory, the rows below solved against it, then a rank-16 update of the
+//      trailing lower triangle).
 //   2. Reduction to standard form C = L^{-1} A L^{-H}: two forward substitutions with n
 //      right-hand sides each (X = L^{-1} A, then C = L^{-1} X^H, using A = A^H).
 //   3. Householder tridiagonalisation C = Q T Q^H (unblocked, on the full Hermitian matrix):
@@ -29,7 +30,8 @@
 // column (the triangular solves, the reflector applications, the inverse iterations) needs no
 // team barrier: one warp owns a column and each lane owns the rows r = lane (mod 32), so values
 // written by one lane are read back only by that lane and everything else travels by shuffles.
-// The barrier count is about 3n per pencil (n Cholesky steps, 2n tridiagonalisation steps).
+// The barrier count is about n + n/8 per pencil (one per tridiagonalisation step, two per 16-column
+// Cholesky panel).
 //
 // Every grid-barrier wait gives up after a time limit; the kernel then raises the control
 // block's error word, sets the pencil's info to -1, and every thread leaves at its next barrier;
@@ -275,58 +277,123 @@ __device__ void finish(const Team&, const Pencil<double2>&) {}
 template <class S>
 __device__ __forceinline__ double* vrdiag(const Pencil<S>& P) { return P.vec + 8 * P.n; }
 
+// Panel width of the blocked Cholesky: 16 columns (one row of the panel lives in a thread's
+// registers while it is solved against the diagonal block).
+template <class S> __host__ __device__ constexpr int chol_panel() { return 16; }
+// Shared memory of the blocked Cholesky: the diagonal block (pitch panel + 1) and its 1 / L[j][j].
+template <class S> __host__ __device__ constexpr size_t chol_smem() {
+  return sizeof(S) * (size_t)chol_panel<S>() * (chol_panel<S>() + 1) + sizeof(double) * chol_panel<S>();
+}
+
+// Blocked right-looking Cholesky B = L L^H in panels of W columns, two team barriers per panel:
+//   1. every CTA factors the W x W diagonal block in its own shared memory (the same arithmetic
+//      in every CTA, so the copies agree bit for bit; the team's first CTA writes it back);
+//   2. the rows below it are solved against it, L21 = A21 L11^{-H} (one warp per 32 rows, one
+//      row per lane, its W entries in registers): no barrier between the rows;
+//   3. barrier; the trailing lower triangle is updated, A22 -= L21 L21^H (one warp per column,
+//      one row per lane, the column's W factors broadcast once); barrier.
 // Returns false when the solve stops (non-positive pivot: *info set; or an abandoned barrier).
 template <class Team, class S>
-__device__ bool cholesky(const Team& T, const Pencil<S>& P) {
+__device__ bool cholesky(const Team& T, const Pencil<S>& P, S* smem) {
+  constexpr int W = chol_panel<S>(), LP = W + 1;
   const int n = P.n, ld = P.ldb;
   S* B = P.B;
-  const int lane = threadIdx.x & 31;
-  for (int j = 0; j < n; ++j) {
-    const double d = re(B[j + (size_t)j * ld]);
-    if (!(d > 0.0) || !isfinite(d)) {
-      if (T.rank() == 0) *P.info = j + 1;
+  double* rd = vrdiag(P);
+  S* Lb = smem;  // diagonal block, column-major with pitch LP
+  double* rdb = reinterpret_cast<double*>(Lb + W * LP);
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool first_cta = T.rank() < (int)blockDim.x;
+  for (int p0 = 0; p0 < n; p0 += W) {
+    const int w = min(W, n - p0);
+    // 1. the diagonal block
+    for (int e = tid; e < W * W; e += blockDim.x) {
+      const int c = e / W, r = e - c * W;
+      Lb[c * LP + r] = (r < w && c < w && r >= c) ? B[(p0 + r) + (size_t)(p0 + c) * ld] : mk<S>(0.0, 0.0);
+    }
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    if (warp == 0) {  // unblocked right-looking on the block, lane = row
+      for (int j = 0; j < w; ++j) {
+        const double d = re(Lb[j * LP + j]);
+        if (!(d > 0.0) || !isfinite(d)) {
+          if (lane == 0) s_bad = p0 + j + 1;
+          break;
+        }
+        const double sd = sqrt(d), r = 1.0 / sd;
+        if (lane > j && lane < w) Lb[j * LP + lane] = cscale(Lb[j * LP + lane], r);
+        if (lane == j) {
+          Lb[j * LP + j] = mk<S>(sd, 0.0);
+          rdb[j] = r;
+        }
+        __syncwarp();
+        for (int k = j + 1; k < w; ++k) {
+          const S lkj = conjd(Lb[j * LP + k]);
+          if (lane >= k && lane < w) Lb[k * LP + lane] = cfms(Lb[j * LP + lane], lkj, Lb[k * LP + lane]);
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (s_bad) {
+      if (T.rank() == 0) *P.info = s_bad;
       return false;
     }
-    const S* __restrict__ cj = B + (size_t)j * ld;
-    bool have = false;
-    double dinv = 0.0;
-    for (int k = j + 1 + T.swrank(); k < n; k += T.wsize()) {
-      if (!have) {  // one division per warp, not per thread
-        dinv = __shfl_sync(0xffffffffu, lane == 0 ? 1.0 / d : 0.0, 0);
-        have = true;
+    if (first_cta) {
+      for (int e = tid; e < w * w; e += blockDim.x) {
+        const int c = e / w, r = e - c * w;
+        if (r >= c) B[(p0 + r) + (size_t)(p0 + c) * ld] = Lb[c * LP + r];
       }
-      const S f = cscale(conjd(cj[k]), dinv);
-      S* __restrict__ ck = B + (size_t)k * ld;
-      int i = k + lane;
-      // four rows per lane per pass, loads first (columns j and k never alias)
-      for (; i + 96 < n; i += 128) {
-        const S a0 = ck[i], a1 = ck[i + 32], a2 = ck[i + 64], a3 = ck[i + 96];
-        const S b0 = cj[i], b1 = cj[i + 32], b2 = cj[i + 64], b3 = cj[i + 96];
-        ck[i] = cfms(b0, f, a0);
-        ck[i + 32] = cfms(b1, f, a1);
-        ck[i + 64] = cfms(b2, f, a2);
-        ck[i + 96] = cfms(b3, f, a3);
+      for (int j = tid; j < w; j += blockDim.x) rd[p0 + j] = rdb[j];
+    }
+    // 2. the rows below: l_ij = (a_ij - sum_{k<j} l_ik conj(L11[j][k])) / L11[j][j]
+    for (int rb = p0 + w + 32 * T.swrank(); rb < n; rb += 32 * T.wsize()) {
+      const int i = rb + lane;
+      if (i < n) {
+        S row[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) row[j] = j < w ? B[i + (size_t)(p0 + j) * ld] : mk<S>(0.0, 0.0);
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+          S v = row[j];
+#pragma unroll
+          for (int k = 0; k < j; ++k) v = cfms(row[k], conjd(Lb[k * LP + j]), v);
+          row[j] = cscale(v, rdb[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+          if (j < w) B[i + (size_t)(p0 + j) * ld] = row[j];
       }
-      for (; i < n; i += 32) ck[i] = cfms(cj[i], f, ck[i]);
     }
     if (!T.sync()) return false;
-  }
-  // scale the columns: L[i][j] = B[i][j] / sqrt(d_j), L[j][j] = sqrt(d_j); keep 1/L[j][j]
-  double* rd = vrdiag(P);
-  for (int j = T.swrank(); j < n; j += T.wsize()) {
-    S* cj = B + (size_t)j * ld;
-    double s = 0.0, r = 0.0;
-    if (lane == 0) {
-      s = sqrt(re(cj[j]));
-      r = 1.0 / s;
-    }
-    s = __shfl_sync(0xffffffffu, s, 0);
-    r = __shfl_sync(0xffffffffu, r, 0);
-    for (int i = j + 1 + lane; i < n; i += 32) cj[i] = cscale(cj[i], r);
-    __syncwarp();
-    if (lane == 0) {
-      cj[j] = mk<S>(s, 0.0);
-      rd[j] = r;
+    // 3. the trailing lower triangle
+    if (p0 + w < n) {
+      for (int k = p0 + w + T.swrank(); k < n; k += T.wsize()) {
+        S f[W];
+        const S mine = lane < w ? conjd(B[k + (size_t)(p0 + lane) * ld]) : mk<S>(0.0, 0.0);
+#pragma unroll
+        for (int j = 0; j < W; ++j) f[j] = shfl_c(mine, j);
+        S* __restrict__ ck = B + (size_t)k * ld;
+        // two rows per lane and two partial sums per row: four independent accumulation chains
+        for (int i = k + lane; i < n; i += 64) {
+          const int i2 = i + 32;
+          S a0 = mk<S>(0.0, 0.0), a1 = a0, c0 = a0, c1 = a0;
+#pragma unroll
+          for (int j = 0; j < W; j += 2) {
+            const S* pj = B + (size_t)(p0 + j) * ld;
+            const S* pk = pj + ld;
+            if (j < w) a0 = cfma(pj[i], f[j], a0);
+            if (j + 1 < w) a1 = cfma(pk[i], f[j + 1], a1);
+            if (i2 < n) {
+              if (j < w) c0 = cfma(pj[i2], f[j], c0);
+              if (j + 1 < w) c1 = cfma(pk[i2], f[j + 1], c1);
+            }
+          }
+          ck[i] = csub(ck[i], cadd(a0, a1));
+          if (i2 < n) ck[i2] = csub(ck[i2], cadd(c0, c1));
+        }
+      }
+      if (!T.sync()) return false;
     }
   }
   return T.sync();
@@ -349,14 +416,33 @@ __device__ __forceinline__ void forward_subst(const S* __restrict__ L, const dou
       if (lane > i && lane < bn) xl = cfms(L[(size_t)(b0 + i) * ld + b0 + lane], xi, xl);
     }
     if (lane < bn) x[b0 + lane] = xl;
-    for (int r0 = b0 + bn; r0 < n; r0 += 32) {
-      const int r = r0 + lane;
-      S acc = mk<S>(0.0, 0.0);
-      for (int i = 0; i < bn; ++i) {
-        const S xi = shfl_c(xl, i);
-        if (r < n) acc = cfma(L[(size_t)(b0 + i) * ld + r], xi, acc);
+    // rows below, two 32-row blocks per pass and two partial sums per row (four independent
+    // accumulation chains per lane; every broadcast x_i serves both blocks)
+    for (int r0 = b0 + bn; r0 < n; r0 += 64) {
+      const int r = r0 + lane, r2 = r + 32;
+      S a0 = mk<S>(0.0, 0.0), a1 = a0, c0 = a0, c1 = a0;
+      int i = 0;
+      for (; i + 1 < bn; i += 2) {
+        const S xi = shfl_c(xl, i), xj = shfl_c(xl, i + 1);
+        const S* li = L + (size_t)(b0 + i) * ld;
+        const S* lj = li + ld;
+        if (r < n) {
+          a0 = cfma(li[r], xi, a0);
+          a1 = cfma(lj[r], xj, a1);
+        }
+        if (r2 < n) {
+          c0 = cfma(li[r2], xi, c0);
+          c1 = cfma(lj[r2], xj, c1);
+        }
       }
-      if (r < n) x[r] = csub(x[r], acc);
+      if (i < bn) {
+        const S xi = shfl_c(xl, i);
+        const S* li = L + (size_t)(b0 + i) * ld;
+        if (r < n) a0 = cfma(li[r], xi, a0);
+        if (r2 < n) c0 = cfma(li[r2], xi, c0);
+      }
+      if (r < n) x[r] = csub(x[r], cadd(a0, a1));
+      if (r2 < n) x[r2] = csub(x[r2], cadd(c0, c1));
     }
   }
 }
@@ -378,15 +464,31 @@ __device__ __forceinline__ void backward_subst_h(const S* __restrict__ L, const 
       if (lane < i) xl = csub(xl, cmulc(L[(size_t)(b0 + lane) * ld + b0 + i], xi));
     }
     if (lane < bn) x[b0 + lane] = xl;
-    for (int r0 = 0; r0 < b0; r0 += 32) {
-      const int r = r0 + lane;
-      S acc = mk<S>(0.0, 0.0);
+    // rows above, two 32-row blocks per pass and two partial sums per row
+    for (int r0 = 0; r0 < b0; r0 += 64) {
+      const int r = r0 + lane, r2 = r + 32;
+      S a0 = mk<S>(0.0, 0.0), a1 = a0, c0 = a0, c1 = a0;
       const S* lr = L + (size_t)r * ld + b0;
-      for (int t = 0; t < bn; ++t) {
-        const S xt = shfl_c(xl, t);
-        if (r < b0) acc = cfmac(lr[t], xt, acc);
+      const S* lr2 = lr + (size_t)32 * ld;
+      int t = 0;
+      for (; t + 1 < bn; t += 2) {
+        const S xt = shfl_c(xl, t), xu = shfl_c(xl, t + 1);
+        if (r < b0) {
+          a0 = cfmac(lr[t], xt, a0);
+          a1 = cfmac(lr[t + 1], xu, a1);
+        }
+        if (r2 < b0) {
+          c0 = cfmac(lr2[t], xt, c0);
+          c1 = cfmac(lr2[t + 1], xu, c1);
+        }
       }
-      if (r < b0) x[r] = csub(x[r], acc);
+      if (t < bn) {
+        const S xt = shfl_c(xl, t);
+        if (r < b0) a0 = cfmac(lr[t], xt, a0);
+        if (r2 < b0) c0 = cfmac(lr2[t], xt, c0);
+      }
+      if (r < b0) x[r] = csub(x[r], cadd(a0, a1));
+      if (r2 < b0) x[r2] = csub(x[r2], cadd(c0, c1));
     }
   }
 }
@@ -578,7 +680,7 @@ __device__ bool tridiagonalise(const Team& T, const Pencil<S>& P, S* sbuf) {
       for (int k = j + 2 + T.swrank(); k < n; k += T.wsize()) {
         const S cvk = conjd(sv[k]), cwk = conjd(sw[k]);
         S* __restrict__ ck = A + (size_t)k * la;
-        S acc = mk<S>(0.0, 0.0);
+        S acc = mk<S>(0.0, 0.0), acc2 = acc;  // two partial sums: shorter dependent chains
         int i = j + 2 + lane;
         for (; i + 96 < n; i += 128) {
           S a[4];
@@ -589,7 +691,8 @@ __device__ bool tridiagonalise(const Team& T, const Pencil<S>& P, S* sbuf) {
             const int r = i + 32 * u;
             a[u] = cfms(sw[r], cvk, cfms(sv[r], cwk, a[u]));
             ck[r] = a[u];
-            acc = cfmac(a[u], sn[r], acc);
+            if (u & 1) acc2 = cfmac(a[u], sn[r], acc2);
+            else acc = cfmac(a[u], sn[r], acc);
           }
         }
         for (; i < n; i += 32) {
@@ -597,7 +700,7 @@ __device__ bool tridiagonalise(const Team& T, const Pencil<S>& P, S* sbuf) {
           ck[i] = a;
           acc = cfmac(a, sn[i], acc);
         }
-        acc = warp_sum_c(acc);
+        acc = warp_sum_c(cadd(acc, acc2));
         if (lane == 0) pn[k] = cmul(tn, acc);
       }
       tau = tn;
@@ -704,7 +807,7 @@ __device__ bool tridiagonal_eig(const Team& T, const Pencil<S>& P) {
   gu += 2.0 * eps * tn + 2.0 * pivmin;
   if (!T.sync()) return false;
   // Eigenvalue k by multisection, one group of kSect lanes per eigenvalue (32 / kSect eigenvalues
-  // per warp): in every round the group's lanes count at kSect interior points of the bracket
+  // per warp, kSect = 8, 16 or 32): in every round the group's lanes count at kSect interior points of the bracket
   // [lo, hi] (count(lo) <= k < count(hi)) and the bracket shrinks to the 1/(kSect+1) between the
   // last point below eigenvalue k and the first above it.  The bracket is first narrowed with FP32
   // counts (about 64 times cheaper than FP64 on GB300) to 1e-6 |T|, widened by 2e-6 |T| and
@@ -714,10 +817,14 @@ __device__ bool tridiagonal_eig(const Team& T, const Pencil<S>& P) {
   // sequence about three times shorter.
   const float pivmin32 = 1e-30f * (float)fmax(1.0, emax2);
   const int lane = threadIdx.x & 31;
-  constexpr int kSect = 8, kGroups = 32 / kSect;
+  // lanes per eigenvalue: a 32-section shrinks the bracket by 33 per round, an 8-section by 9, at
+  // four times the Sturm counts per round; wider sections pay while they keep the busy warps at
+  // no more than half of the team's (beyond that the FP64 pipe, not the chain, is the limit)
+  const int kSect = T.wsize() >= 2 * n ? 32 : T.wsize() >= n ? 16 : 8;
+  const int kGroups = 32 / kSect;
   if (T.wsize() * kGroups >= n) {
     const int grp = lane / kSect, gi = lane % kSect;
-    const unsigned gmask = ((1u << kSect) - 1u) << (grp * kSect);
+    const unsigned gmask = kSect == 32 ? 0xffffffffu : ((1u << kSect) - 1u) << (grp * kSect);
     for (int k0 = T.swrank() * kGroups; k0 < n; k0 += T.wsize() * kGroups) {
       const int k = k0 + grp;
       const bool act = k < n;
@@ -984,7 +1091,7 @@ __device__ void solve_pencil(const Team& T, const Pencil<S>& P) {
   if (P.n <= 0) return;
   T.stamp(0);
   if (!prepare(T, P)) return;
-  if (!cholesky(T, P)) return;
+  if (!cholesky(T, P, smem)) return;
   T.stamp(1);
   if (!reduce_standard(T, P)) return;
   T.stamp(2);
@@ -1063,7 +1170,10 @@ size_t col_smem_bytes(int n, size_t ws) {
   const size_t b = (size_t)kWarps * (size_t)std::max(n, 1) * ws;
   return b <= 200u * 1024u ? b : 0;
 }
-size_t dyn_smem_bytes(int n, size_t ws) { return std::max(col_smem_bytes(n, ws), (size_t)3 * std::max(n, 1) * ws); }
+size_t dyn_smem_bytes(int n, size_t ws) {
+  const size_t chol = ws == 8 ? chol_smem<double>() : chol_smem<double2>();
+  return std::max({col_smem_bytes(n, ws), (size_t)3 * std::max(n, 1) * ws, chol});
+}
 constexpr int kMaxN = 4608;  // 3 n complex words must fit in shared memory (221 KB)
 
 template <class S>

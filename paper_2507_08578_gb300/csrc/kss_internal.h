@@ -275,6 +275,10 @@ void apply_s(kss_ctx ctx, kss_sys s, int ik, int nb, const void* psi, void* out,
 void apply_filter_op(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev, void* out, int ld,
                      ChebCoef c, kss_precision prec);
 size_t local_workspace_bytes(kss_sys s, int ik, int nb, kss_precision prec);
+// Bytes of y-z slab one launch of the local passes covers: small enough that the slab written by
+// pass A is still in L2 when passes B and C read it (with V, psi and the projector operands
+// streaming through the same L2).
+constexpr size_t kSlabChunkBytes = 64ull << 20;
 size_t sys_device_bytes(kss_sys s);  // device bytes of a system's tables (api.cpp)
 // Caller-provided workspace forms (used by the entry point that allocates nothing).
 size_t local_slab_bytes_per_band(kss_sys s, int ik, kss_precision prec);

@@ -418,7 +418,7 @@ size_t slab_elems(kss_sys s, int ik) {
 
 int chunk_bands(kss_sys s, int ik, int nb, size_t es) {
   const size_t per = slab_elems(s, ik) * es;
-  const size_t target = 64ull << 20;  // keep the slab chunk L2-resident
+  const size_t target = kSlabChunkBytes;  // keep the slab chunk L2-resident
   return (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, target / per));
 }
 

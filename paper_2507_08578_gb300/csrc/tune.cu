@@ -67,10 +67,10 @@ PassBSched pass_b_schedule(kss_ctx ctx, const lk::LocalArgs<T>& a, const fftr::S
         if (ab.first * ab.second == a.N2 && wide_pass_b<T>(t, ab.first, ab.second, nt, 0, nullptr, true))
           cand.push_back(PassBSched{ab.first, ab.second, nt, 0, 0});
   cand.push_back(PassBSched{s2.A, s2.B, 0, 0, 0});
-  // scratch slab of the production chunk size (the local passes keep about 64 MB of slab per
+  // scratch slab of the production chunk size (the local passes keep kSlabChunkBytes of slab per
   // launch), so that candidates are timed at the launch shape they will run at
   const size_t per_band = (size_t)t.N1 * t.W3 * t.W2 * sizeof(C);
-  const int nbt = (int)std::max<size_t>(1, std::min<size_t>(64, (64ull << 20) / per_band));
+  const int nbt = (int)std::max<size_t>(1, std::min<size_t>(64, kSlabChunkBytes / per_band));
   const size_t elems = (size_t)t.N1 * t.W3 * t.W2 * nbt;
   ctx->ws_tune.ensure(elems * sizeof(C));
   KSS_CHECK_CUDA(cudaMemsetAsync(ctx->ws_tune.p, 0, elems * sizeof(C), ctx->stream));
