@@ -247,8 +247,10 @@ def run_reference(args, rank: int):
 # pass_bw<double, 8, 12, 384> moved 73.53 + 7.28 MB per 27-band launch, pass_bw<float, 12, 8, 384>
 # 69.94 + 6.15 MB per 54-band launch.  Valid for that kernel and schedule only (the bench reports
 # null traffic when the autotuner picked another).
-PASS_B_DRAM_PER_BAND = {"fp64": (73.533824e6 + 7.281024e6) / 27, "mixed": (69.942784e6 + 6.154112e6) / 54}
-PASS_B_SCHEDULE = {"fp64": "8x12 @384", "mixed": "12x8 @384"}
+# ncu DRAM bytes per band of the middle pass with the L2 state the step leaves (--cache-control
+# none; second of two production launches each: profiles/c2_pass_b_dram_traffic.md)
+PASS_B_DRAM_PER_BAND = {"fp64": (17.314816e6 + 41.618944e6) / 27, "mixed": (1.820928e6 + 43.34976e6) / 54}
+PASS_B_SCHEDULE = {"fp64": "8x12 @384", "mixed": "16x6 @256"}
 PASS_B_EXECUTED_PER_ALGORITHMIC = 6.7e7 / (4 * 5 * 96 ** 3 * math.log2(96))
 
 
@@ -638,8 +640,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if roof is not None and roof["kernel"] == "local_pass_b" and args.workload == "c2" and \
             all(f"{e['A']}x{e['B']} @{e['threads']}" == PASS_B_SCHEDULE[args.form] for e in table):
         roof["traffic"] = PASS_B_DRAM_PER_BAND[args.form] * applies / roof["launches"]
-        roof["traffic_note"] = ("DRAM bytes per launch: ncu bytes per band of this kernel and schedule x the "
-                                "bands per launch of this run")
+        roof["traffic_note"] = ("DRAM bytes per launch: ncu bytes per band of this kernel and schedule (L2 as "
+                                "the step leaves it) x the bands per launch of this run")
 
     if rank == 0:
         line = {
