@@ -75,6 +75,9 @@ def parse():
                          "shapes; dense: the Rayleigh-Ritz eigensolve; apply: H on a large band "
                          "block of the config-1 cell (auxiliary lines)")
     ap.add_argument("--bands", type=int, default=16384, help="apply: bands in the block")
+    ap.add_argument("--pin-schedule", default=None, metavar="AxB@T",
+                    help="c2: pin the middle pass's schedule for the 96^3 box (split A x B at T threads) "
+                         "instead of tuning it (profiling runs that must see the production schedule)")
     ap.add_argument("--no-graph", action="store_true",
                     help="c4/c5: issue the batch filter's launches directly instead of replaying a CUDA "
                          "graph, so that the kernel table times every launch (profiling)")
@@ -468,6 +471,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     ctx = K.kss_create(local_rank, stream.cuda_stream)
     s = workload(args.workload)
     prec = K.KSS_PREC_FP64 if args.form == "fp64" else K.KSS_PREC_MIXED
+    if args.pin_schedule:
+        ab, nt = args.pin_schedule.split("@")
+        a_, b_ = (int(v) for v in ab.split("x"))
+        K.kss_autotune_put(local_rank, prec, 96, 96, 40, a_, b_, int(nt))
     if args.nk > 0:
         s.kpts = s.kpts[: args.nk]
     sysh = K.kss_setup(ctx, s.lattice, s.ecut, s.kpts, s.pos, s.D, fft_box=s.fft_box, Q=s.Q)

@@ -1179,6 +1179,9 @@ constexpr int kMaxN = 4608;  // 3 n complex words must fit in shared memory (221
 template <class S>
 void launch_cta(kss_ctx ctx, std::vector<Pencil<S>>& small, size_t items_offset, const char* name) {
   if (small.empty()) return;
+  // largest pencils first: the CTAs start in launch order, so the long solves begin on their own
+  // SMs and the short ones fill in behind them (each CTA reads its own self-contained item)
+  std::stable_sort(small.begin(), small.end(), [](const Pencil<S>& a, const Pencil<S>& b) { return a.n > b.n; });
   cudaStream_t st = ctx->stream;
   int nmax = 1;
   for (const auto& P : small) nmax = std::max(nmax, P.n);

@@ -210,6 +210,186 @@ __device__ __forceinline__ void rdft(C* v, T s) {
   else rdft_split<N>(v, s);
 }
 
+// ---- pruned transforms ---------------------------------------------------------------------------
+// rdft_m<N, MIN, MOUT>: y_q = sum_{t in MIN} v_t w^{s t q} for every q in MOUT (bit masks over
+// 0..N-1); inputs outside MIN are taken as zero (never read), outputs outside MOUT are left
+// unspecified.  The composite form follows rdft_split step for step (same factors, twiddles and
+// order), skipping the sub-transforms whose inputs are all zero, the twiddles and second-level
+// transforms no needed output depends on, and, in the base transforms, every term of a zero input
+// or an unneeded output; with full masks it performs exactly the operations of rdft.
+template <int N> __host__ __device__ constexpr unsigned full_mask() { return N >= 32 ? 0xffffffffu : ((1u << N) - 1u); }
+__host__ __device__ constexpr int popc(unsigned m) { int c = 0; for (; m; m &= m - 1) ++c; return c; }
+__host__ __device__ constexpr int lowbit(unsigned m) { int i = 0; while (!(m >> i & 1u)) ++i; return i; }
+
+// a * w^{E} with w = exp(s 2 pi i / N), compile-time E: the trivial factors without multiplies
+template <int E, int N, typename C, typename T>
+__device__ __forceinline__ C twiddle_c(C a, T s) {
+  constexpr int e = ((E % N) + N) % N;
+  if constexpr (e == 0) {
+    return a;
+  } else {
+    constexpr double wc = kcos(e, N), ws = ksin(e, N);
+    if constexpr (wc == 0.0 && (ws == 1.0 || ws == -1.0)) {
+      return muli(a, ws > 0.0 ? s : -s);
+    } else if constexpr (ws == 0.0 && wc == -1.0) {
+      C r;
+      r.x = -a.x;
+      r.y = -a.y;
+      return r;
+    } else {
+      C w;
+      w.x = (T)wc;
+      w.y = s > (T)0 ? (T)ws : -(T)ws;
+      return mul(a, w);
+    }
+  }
+}
+template <int E, int N> __host__ __device__ constexpr int twiddle_cost() {
+  constexpr int e = ((E % N) + N) % N;
+  if constexpr (e == 0) return 0;
+  else if constexpr ((kcos(e, N) == 0.0 && (ksin(e, N) == 1.0 || ksin(e, N) == -1.0)) ||
+                     (ksin(e, N) == 0.0 && kcos(e, N) == -1.0)) return 0;
+  else return 6;
+}
+// real operations of the direct sums of a masked base transform, and of the full codelet
+template <int N, unsigned MIN, unsigned MOUT> __host__ __device__ constexpr int direct_cost() {
+  int c = 0;
+  for (int q = 0; q < N; ++q) {
+    if (!(MOUT >> q & 1u)) continue;
+    int terms = 0;
+    for (int t = 0; t < N; ++t) {
+      if (!(MIN >> t & 1u)) continue;
+      const int e = (t * q) % N;
+      const bool triv = e == 0 || (kcos(e, N) == 0.0 && (ksin(e, N) == 1.0 || ksin(e, N) == -1.0)) ||
+                        (ksin(e, N) == 0.0 && kcos(e, N) == -1.0);
+      c += triv ? 0 : 6;
+      ++terms;
+    }
+    c += 2 * (terms - 1);
+  }
+  return c;
+}
+template <int N> __host__ __device__ constexpr int codelet_cost() {
+  return N == 2 ? 4 : N == 3 ? 16 : N == 4 ? 16 : N == 5 ? 44 : 1 << 20;
+}
+
+template <int N, unsigned MIN, unsigned MOUT, typename C, typename T>
+__device__ __forceinline__ void rdft_m(C* v, T s);
+
+template <int N, unsigned MIN, unsigned MOUT, typename C, typename T>
+__device__ __forceinline__ void rdft_direct(C* v, T s) {
+  constexpr int t0 = lowbit(MIN);
+  C in[N];
+  static_for<0, N>([&](auto tc) {
+    constexpr int t = decltype(tc)::value;
+    if constexpr (MIN >> t & 1u) in[t] = v[t];
+  });
+  static_for<0, N>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    if constexpr (MOUT >> q & 1u) {
+      C acc = twiddle_c<t0 * q, N>(in[t0], s);
+      static_for<t0 + 1, N>([&](auto tc) {
+        constexpr int t = decltype(tc)::value;
+        if constexpr (MIN >> t & 1u) acc = add(acc, twiddle_c<t * q, N>(in[t], s));
+      });
+      v[q] = acc;
+    }
+  });
+}
+
+template <int N, unsigned MIN, unsigned MOUT, typename C, typename T>
+__device__ __forceinline__ void rdft_split_m(C* v, T s) {
+  constexpr int P = first_factor(N);
+  constexpr int Q = N / P;
+  // first-level outputs k1 that some needed output k1 + P k2 depends on
+  constexpr unsigned need1 = [] {
+    unsigned m = 0;
+    for (int k1 = 0; k1 < P; ++k1)
+      for (int k2 = 0; k2 < Q; ++k2)
+        if (MOUT >> (k1 + P * k2) & 1u) m |= 1u << k1;
+    return m;
+  }();
+  // sub-transforms j with a nonzero input (the second level's input mask)
+  constexpr unsigned jm = [] {
+    unsigned m = 0;
+    for (int j = 0; j < Q; ++j)
+      for (int i = 0; i < P; ++i)
+        if (MIN >> (j + Q * i) & 1u) m |= 1u << j;
+    return m;
+  }();
+  C t[Q][P];
+  static_for<0, Q>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    constexpr unsigned mj = [] {
+      unsigned m = 0;
+      for (int i = 0; i < P; ++i)
+        if (MIN >> (j + Q * i) & 1u) m |= 1u << i;
+      return m;
+    }();
+    if constexpr (mj != 0u) {
+      static_for<0, P>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        if constexpr (mj >> i & 1u) t[j][i] = v[j + Q * i];
+      });
+      rdft_m<P, mj, need1>(t[j], s);
+      static_for<1, P>([&](auto kc) {
+        constexpr int k1 = decltype(kc)::value;
+        if constexpr ((need1 >> k1 & 1u) && (j * k1) % N != 0) t[j][k1] = twiddle_c<j * k1, N>(t[j][k1], s);
+      });
+    }
+  });
+  static_for<0, P>([&](auto kc) {
+    constexpr int k1 = decltype(kc)::value;
+    if constexpr (need1 >> k1 & 1u) {
+      constexpr unsigned mo2 = [] {
+        unsigned m = 0;
+        for (int k2 = 0; k2 < Q; ++k2)
+          if (MOUT >> (k1 + P * k2) & 1u) m |= 1u << k2;
+        return m;
+      }();
+      C u[Q];
+      static_for<0, Q>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        if constexpr (jm >> j & 1u) u[j] = t[j][k1];
+      });
+      rdft_m<Q, jm, mo2>(u, s);
+      static_for<0, Q>([&](auto qc) {
+        constexpr int k2 = decltype(qc)::value;
+        if constexpr (mo2 >> k2 & 1u) v[k1 + P * k2] = u[k2];
+      });
+    }
+  });
+}
+
+template <int N, unsigned MIN, unsigned MOUT, typename C, typename T>
+__device__ __forceinline__ void rdft_m(C* v, T s) {
+  static_assert(MIN != 0u && MOUT != 0u, "empty pruned transform");
+  constexpr unsigned F = full_mask<N>();
+  if constexpr (N == 1) {
+  } else if constexpr ((MIN & F) == F && (MOUT & F) == F) {
+    rdft<N>(v, s);
+  } else if constexpr (N <= 5) {
+    if constexpr (direct_cost<N, MIN, MOUT>() < codelet_cost<N>()) {
+      rdft_direct<N, MIN, MOUT>(v, s);
+    } else {
+      static_for<0, N>([&](auto tc) {  // the full codelet reads every input: zero the pruned ones
+        constexpr int t = decltype(tc)::value;
+        if constexpr (!(MIN >> t & 1u)) {
+          v[t].x = (T)0;
+          v[t].y = (T)0;
+        }
+      });
+      rdft_base<N>(v, s);
+    }
+  } else {
+    rdft_split_m<N, MIN, MOUT>(v, s);
+  }
+}
+// Mask of the window pattern of a pruned stage: the first C and the last C of N positions.
+template <int N, int C> __host__ __device__ constexpr unsigned edge_mask() {
+  return C <= 0 || 2 * C >= N ? full_mask<N>() : (((1u << C) - 1u) | (((1u << C) - 1u) << (N - C)));
+}
+
 // Runtime size dispatch over the codelet set {1,2,3,4,5,6,8,9,10,12,15,16}.
 template <typename C, typename T>
 __device__ __forceinline__ void rdft_rt(int n, C* v, T s) {

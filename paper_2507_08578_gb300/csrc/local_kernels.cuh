@@ -506,11 +506,18 @@ struct WideB {
   }
 };
 
-template <typename T, int A, int B, int NT = kWideThreads>
+// Pruned stages (CW > 0): the window rows of y and z (the sphere's extent, about 0.4 N) occupy,
+// in the strided index r + B i of a DFT-A stage, only the first CW and the last CW values of i, so
+// the first inverse stages read only those inputs (the others are zero) and the last forward
+// stages compute only those outputs (the others are discarded): fftr::rdft_m with the edge mask.
+// Valid when B CW exceeds the window's largest index and is at least its most negative index's
+// magnitude along both y and z (wide_prune_cw); CW = 0 is the full transform.
+template <typename T, int A, int B, int NT = kWideThreads, int CW = 0>
 __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int nl) {
   using C = typename CT<T>::C;
   using G = WideB<T, A, B>;
   constexpr int N = G::N, QS = G::QS, ZS = G::ZS;
+  constexpr unsigned MW = fftr::edge_mask<A, CW>(), MF = fftr::full_mask<A>();
   extern __shared__ __align__(16) unsigned char smraw[];
   C* tw = reinterpret_cast<C*>(smraw);  // e^{-2 pi i m / N}, m < N
   C* Q = tw + N;                        // W3 rows (z in the sphere window) x N (y)
@@ -538,9 +545,11 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
     const int r = dw3(t), u = t - r * W3;  // rows fastest across lanes
     C* row = Q + u * QS + r;
     C v[A];
-#pragma unroll
-    for (int i = 0; i < A; ++i) v[i] = row[B * i];
-    fftr::rdft<A>(v, (T)1);
+    fftr::static_for<0, A>([&](auto ic) {
+      constexpr int i = decltype(ic)::value;
+      if constexpr (MW >> i & 1u) v[i] = row[B * i];
+    });
+    fftr::rdft_m<A, MW, MF>(v, (T)1);
 #pragma unroll
     for (int k = 1; k < A; ++k) {
       C w = tw[r * k];
@@ -566,12 +575,14 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   for (int t = tid; t < N * B; t += NT) {
     const int r = t / N, p = t - r * N;
     C v[A];
-#pragma unroll
-    for (int i = 0; i < A; ++i) {
-      const int u = zmap[r + B * i];
-      v[i] = u >= 0 ? Q[u * QS + p] : C{0, 0};
-    }
-    fftr::rdft<A>(v, (T)1);
+    fftr::static_for<0, A>([&](auto ic) {
+      constexpr int i = decltype(ic)::value;
+      if constexpr (MW >> i & 1u) {
+        const int u = zmap[r + B * i];
+        v[i] = u >= 0 ? Q[u * QS + p] : C{0, 0};
+      }
+    });
+    fftr::rdft_m<A, MW, MF>(v, (T)1);
 #pragma unroll
     for (int k = 1; k < A; ++k) {
       C w = tw[r * k];
@@ -614,12 +625,14 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
     C v[A];
 #pragma unroll
     for (int m = 0; m < A; ++m) v[m] = col[B * m];
-    fftr::rdft<A>(v, (T)-1);
-#pragma unroll
-    for (int k = 0; k < A; ++k) {
-      const int u = zmap[q + B * k];
-      if (u >= 0) Q[u * QS + p] = v[k];
-    }
+    fftr::rdft_m<A, MF, MW>(v, (T)-1);
+    fftr::static_for<0, A>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      if constexpr (MW >> k & 1u) {
+        const int u = zmap[q + B * k];
+        if (u >= 0) Q[u * QS + p] = v[k];
+      }
+    });
   }
   __syncthreads();
   // ---- y, forward ----
@@ -642,15 +655,32 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
     C v[A];
 #pragma unroll
     for (int m = 0; m < A; ++m) v[m] = row[B * m];
-    fftr::rdft<A>(v, (T)-1);
-#pragma unroll
-    for (int k = 0; k < A; ++k) row[B * k] = v[k];
+    fftr::rdft_m<A, MF, MW>(v, (T)-1);
+    fftr::static_for<0, A>([&](auto kc) {  // rows outside the window are not read again
+      constexpr int k = decltype(kc)::value;
+      if constexpr (MW >> k & 1u) row[B * k] = v[k];
+    });
   }
   __syncthreads();
   for (int i = tid; i < W3 * W2; i += NT) {
     const int u3 = dw2(i), u2 = i - u3 * W2;
     slab[i] = Q[u3 * QS + fftr::wrap_add(a.lo2, u2, N)];
   }
+}
+
+// Pruning width of the CTA-wide pass for split N = A * B and the sphere windows of y (lo2, W2) and
+// z (lo3, W3): the smallest CW whose edge mask covers every window position of both axes in the
+// strided stages (B CW > largest index, B CW >= magnitude of the most negative one), or 0 when the
+// windows do not straddle 0 or leave nothing to prune (2 CW >= A).
+inline int wide_prune_cw(int A, int B, int lo2, int W2, int lo3, int W3) {
+  auto one = [&](int lo, int W) {
+    const int hi = lo + W - 1;
+    if (lo > 0 || hi < 0) return 1 << 20;
+    const int c1 = hi / B + 1, c2 = (-lo + B - 1) / B;
+    return c1 > c2 ? c1 : c2;
+  };
+  const int c = std::max(one(lo2, W2), one(lo3, W3));
+  return 2 * c < A ? c : 0;
 }
 
 // Best two-factor split N = A*B over the codelet sizes (fewest warp instructions per pencil).

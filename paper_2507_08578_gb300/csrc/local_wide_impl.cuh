@@ -11,9 +11,16 @@ namespace wide_detail {
 
 using namespace lk;
 
-template <typename T, int A, int B, int NT>
+template <typename T, int A, int B, int NT, int CW = 0>
 __global__ void __launch_bounds__(NT) pass_bw(LocalArgs<T> a) {
-  pass_bw_body<T, A, B, NT>(a, blockIdx.x, blockIdx.y);
+  pass_bw_body<T, A, B, NT, CW>(a, blockIdx.x, blockIdx.y);
+}
+
+// Splits with a pruned instance and its edge width: the 96-point splits, with the widths that the
+// sphere window of the config-2 box (|m| <= 20 along y and z) needs; a window that needs no more
+// than that width runs the pruned instance, any other the full one.
+constexpr int pruned_cw(int A, int B) {
+  return A == 8 && B == 12 ? 2 : A == 12 && B == 8 ? 3 : A == 6 && B == 16 ? 2 : A == 16 && B == 6 ? 4 : 0;
 }
 
 template <typename T, int A, int B, int NT>
@@ -21,6 +28,15 @@ bool launch_one(const LocalArgs<T>& a, int nbands, cudaStream_t st, bool dry) {
   const size_t sm = WideB<T, A, B>::smem(a.W3);
   if (sm > kWideSmemMax) return false;
   if (dry) return true;
+  constexpr int PC = pruned_cw(A, B);
+  if constexpr (PC > 0) {
+    const int cw = wide_prune_cw(A, B, a.lo2, a.W2, a.lo3, a.W3);
+    if (cw > 0 && cw <= PC) {
+      KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_bw<T, A, B, NT, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      pass_bw<T, A, B, NT, PC><<<dim3(a.N1, nbands), NT, sm, st>>>(a);
+      return true;
+    }
+  }
   KSS_CHECK_CUDA(cudaFuncSetAttribute(pass_bw<T, A, B, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   pass_bw<T, A, B, NT><<<dim3(a.N1, nbands), NT, sm, st>>>(a);
   return true;

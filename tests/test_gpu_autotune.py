@@ -1,9 +1,10 @@
 """The autotuner of the FFT pass-B schedule, on the GPU through the C ABI.
 
 * Every schedule the tuner can pick for a box length (the CTA-wide form with each compile-time
-  split N = A * B at 256 and 384 threads, and the per-warp form), pinned with kss_autotune_put,
-  gives H psi within 1e-10 relative (FP64) / 2e-5 (mixed) of the oracle, for the config-1 box
-  (24^3) and config-4 lengths (30^3, 36^3, 40^3).
+  split N = A * B at 256 and 384 threads, 128 too in single precision, and the per-warp form),
+  pinned with kss_autotune_put, gives H psi within 1e-10 relative (FP64) / 2e-5 (mixed) of the
+  oracle, for the config-1 cell (on a 25 x 24 x 24 box), config-4 lengths (30^3, 36^3, 40^3) and
+  the config-2 box (96^3, whose splits run pruned stages).
 * With tuning on, the first apply of a configuration adds one table entry whose choice was timed
   against every candidate; its result agrees with the built-in choice to rounding.
 * The batch engine follows the table: the same batch with every entry pinned to the per-warp
@@ -69,6 +70,10 @@ CASES = [
     ("box30", lambda: W.tiny_system(a=8.0, ecut=6.0, natom=3, fft_box=(30, 30, 30)), K.KSS_PREC_FP64, 1e-10),
     ("box36_mixed", lambda: W.tiny_system(a=9.0, ecut=7.0, natom=3, fft_box=(36, 36, 36)), K.KSS_PREC_MIXED, 2e-5),
     ("box40", lambda: W.tiny_system(a=9.0, ecut=8.0, natom=2, fft_box=(40, 40, 40)), K.KSS_PREC_FP64, 1e-10),
+    # the config-2 box (96^3, sphere |m| <= 20): every 96-point split has a pruned instance that
+    # skips the zero inputs and discarded outputs of its strided stages
+    ("C2_96", lambda: W.config2(), K.KSS_PREC_FP64, 1e-10),
+    ("C2_96_mixed", lambda: W.config2(), K.KSS_PREC_MIXED, 2e-5),
 ]
 
 
