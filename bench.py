@@ -250,11 +250,16 @@ def run_reference(args, rank: int):
 # pass_bw<double, 8, 12, 384> moved 73.53 + 7.28 MB per 27-band launch, pass_bw<float, 12, 8, 384>
 # 69.94 + 6.15 MB per 54-band launch.  Valid for that kernel and schedule only (the bench reports
 # null traffic when the autotuner picked another).
-# ncu DRAM bytes per band of the middle pass with the L2 state the step leaves (--cache-control
-# none; second of two production launches each: profiles/c2_pass_b_dram_traffic.md)
-PASS_B_DRAM_PER_BAND = {"fp64": (17.314816e6 + 41.618944e6) / 27, "mixed": (1.820928e6 + 43.34976e6) / 54}
-PASS_B_SCHEDULE = {"fp64": "8x12 @384", "mixed": "16x6 @256"}
-PASS_B_EXECUTED_PER_ALGORITHMIC = 6.7e7 / (4 * 5 * 96 ** 3 * math.log2(96))
+# ncu DRAM bytes per band of the middle pass (production schedule 12 x 8 at 384 threads, pruned
+# stages) with the L2 state the step leaves (--cache-control none; a full-chunk production launch:
+# profiles/c2_pass_b_dram_traffic.md)
+PASS_B_DRAM_PER_BAND = {"fp64": (19.000832e6 + 47.424256e6) / 27, "mixed": (9.314304e6 + 41.612032e6) / 54}
+PASS_B_SCHEDULE = {"fp64": "12x8 @384", "mixed": "12x8 @384"}
+# FP instructions the middle pass executes per band (ncu counts: 2 per FMA, 1 per add / multiply)
+# over the dense-transform count 4 x 5 N^3 log2 N, for the production schedule (12 x 8 at 384
+# threads with the pruned strided stages, CW = 3)
+PASS_B_EXECUTED_PER_ALGORITHMIC = {"fp64": (2 * 349526016 + 685449216 + 207194112) / 27 / (4 * 5 * 96 ** 3 * math.log2(96)),
+                                   "mixed": (2 * 707014656 + 1399762944 + 439271424) / 54 / (4 * 5 * 96 ** 3 * math.log2(96))}
 
 
 def algorithmic_work(s, npw, nb, degree, box, applies, rr_calls):
@@ -548,11 +553,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "measured_note": "kss_peak_probe in this run: independent FMA chains, 8 CTAs per SM, "
                                  "best of three launches",
                 "launches": dl, "avg_launch_ms": dms / dl}
-        if dom == "local_pass_b" and args.form == "fp64":
-            # FP64 instructions the pruned pass executes (ncu count: 6.7e7 flops per band, 2 per
-            # DFMA, 1 per DADD / DMUL) over the dense-transform count 4 x 5 N^3 log2 N
-            roof["executed_per_algorithmic"] = PASS_B_EXECUTED_PER_ALGORITHMIC
-            roof["executed_frac_of_measured"] = ach * PASS_B_EXECUTED_PER_ALGORITHMIC / probe
+        sched_now = [f"{e['A']}x{e['B']} @{e['threads']}" for e in K.kss_autotune_table() if e["N"] == 96]
+        if dom == "local_pass_b" and args.workload == "c2" and sched_now and \
+                all(x == PASS_B_SCHEDULE[args.form] for x in sched_now):
+            # FP instructions the pruned pass executes (ncu counts of this schedule) over the
+            # dense-transform count: the executed rate against the measured FMA throughput
+            roof["executed_per_algorithmic"] = PASS_B_EXECUTED_PER_ALGORITHMIC[args.form]
+            roof["executed_frac_of_measured"] = ach * PASS_B_EXECUTED_PER_ALGORITHMIC[args.form] / probe
 
     # ---- the FP64 products on the tensor cores (FP64 form) ----
     fp64_gemm = None
