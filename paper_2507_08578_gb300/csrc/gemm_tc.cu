@@ -13,7 +13,10 @@
 //   * split precision: every FP32 value x = hi + lo with hi = bf16(x), lo = bf16(x - hi); each
 //     operand row holds its hi copy followed by its lo copy, and for every k-block the kernel
 //     accumulates hi*hi + hi*lo + lo*hi in FP32 (TMEM) from the same four staged tiles.
-// The GEMM kernel: one CTA per 128 x 128 output tile (tiles with the same A rows adjacent in
+// Two kernel forms, chosen per shape by the autotuner (gemm_tune.cu): the persistent form (one CTA
+// per SM walking output tiles with two TMEM accumulators, described below at tc_persist_kernel,
+// also the grouped products of the batch engine), and the one-CTA-per-tile form:
+// one CTA per 128 x 128 output tile (tiles with the same A rows adjacent in
 // launch order, so A is fetched from HBM once and re-read from L2) and K split across CTAs so
 // that the grid fills the SMs in as few waves as possible; a TMA producer thread fills a 3-stage
 // ring, each stage holding the hi and lo 128B-swizzled 128 x 64 BF16 tiles of both operands; one
