@@ -62,6 +62,33 @@ def test_batch_matches_oracle_and_single(ctx, prec, tol):
             K.kss_sys_destroy(h)
 
 
+def test_batch_flags_direct_launch_and_fp32_products(ctx):
+    """The batch engine's options: without the CUDA graph (KSS_SOLVE_BATCH_NO_GRAPH) the filter
+    runs the same launches directly and gives the same eigenvalues to rounding; with FP32 CUDA-core
+    projector products (KSS_SOLVE_BATCH_FP32_PROJ) in place of the grouped split-BF16 tensor-core
+    products the batch converges to the same levels; both within 1e-6 Ha of the oracle."""
+    systems = small_systems()
+    handles = [setup(ctx, s) for s in systems]
+    try:
+        units = [(h, s, ik) for h, s in zip(handles, systems) for ik in range(len(s.kpts))]
+        args = ([u[0] for u in units], [u[2] for u in units], [u[1].nband for u in units])
+        runs = {}
+        for name, flags in (("graph", 0), ("direct", K.KSS_SOLVE_BATCH_NO_GRAPH),
+                            ("fp32", K.KSS_SOLVE_BATCH_FP32_PROJ)):
+            ev, rs, st, status = K.kss_solve_batch(ctx, *args, K.make_opts(prec=K.KSS_PREC_MIXED, seed=5,
+                                                                             flags=flags))
+            assert status == K.KSS_OK, name
+            runs[name] = ev
+        for i, (h, s, ik) in enumerate(units):
+            ref = oracle_levels(s, ik, s.nband)
+            assert np.max(np.abs(runs["graph"][i] - runs["direct"][i])) < 1e-10
+            for name in runs:
+                assert np.max(np.abs(runs[name][i] - ref)) < 1e-6, (name, s.name, ik)
+    finally:
+        for h in handles:
+            K.kss_sys_destroy(h)
+
+
 def test_batch_mixed_fused_and_slab_classes(ctx):
     """Mixed batch whose units fall in several local-part classes: small cubic boxes (20^3, 24^3
     twice, 25^3) that run the grouped single-kernel local part, and a 30^3 unit on the three-pass
