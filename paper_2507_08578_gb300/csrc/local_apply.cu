@@ -440,6 +440,8 @@ LocalArgs<T> local_args(kss_sys s, int ik, const void* psi, const void* psi_prev
   a.W3 = kd.W[2];
   a.lo2 = kd.lo[1];
   a.lo3 = kd.lo[2];
+  a.W1 = kd.W[0];
+  a.lo1 = kd.lo[0];
   a.d1 = s->dim[0];
   a.d2 = s->dim[1];
   a.d3 = s->dim[2];
@@ -535,6 +537,7 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
         kk.b<<<dim3(t.N1, m), kThreads, rb, ctx->stream>>>(t, rp, scr_warp);
       };
       const PassBSched sb = pass_b_schedule<T>(ctx, a, rp.s2, true);
+      const bool wx = wide_pass_x<T>(a, 0, 0, nullptr, true);
       if (sb.threads) a.Vpi = (const T*)vpi_view(s, sb.A, sb.B, f64);
       static const int ida = prof_register(f64 ? "local_pass_a<f64>" : "local_pass_a<f32>");
       static const int idb = prof_register(f64 ? "local_pass_b<f64>" : "local_pass_b<f32>");
@@ -556,7 +559,8 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
         a.n0 = n0;
         {
           ProfScope ps(ctx, ida);
-          kk.a<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
+          if (!(wx && wide_pass_x<T>(a, 0, m, ctx->stream, false)))
+            kk.a<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
         }
         {
           ProfScope ps(ctx, idb);
@@ -564,7 +568,8 @@ void run_local(kss_sys s, int ik, int nb, const void* psi, const void* psi_prev,
         }
         {
           ProfScope ps(ctx, idc);
-          kk.c<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
+          if (!(wx && wide_pass_x<T>(a, 1, m, ctx->stream, false)))
+            kk.c<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
         }
       }
       if (packed) gamma_finish<T>(s, ik, nb, psi, psi_prev, out, ld, c);
@@ -614,6 +619,8 @@ void run_local_ws(kss_sys s, int ik, int nb, const void* psi, void* out, int ld,
   a.W3 = kd.W[2];
   a.lo2 = kd.lo[1];
   a.lo3 = kd.lo[2];
+  a.W1 = kd.W[0];
+  a.lo1 = kd.lo[0];
   a.d1 = s->dim[0];
   a.d2 = s->dim[1];
   a.d3 = s->dim[2];
@@ -653,6 +660,7 @@ void run_local_ws(kss_sys s, int ik, int nb, const void* psi, void* out, int ld,
         kk.b<<<dim3(t.N1, m), kThreads, rb, ctx->stream>>>(t, rp, scr_warp);
       };
       PassBSched sb = pass_b_schedule<T>(ctx, a, rp.s2, false);  // no tuning here
+      const bool wx = wide_pass_x<T>(a, 0, 0, nullptr, true);
       // The CTA-wide form needs V in its split's layout; that view is built (allocated) by the
       // first ordinary application, and without it this path takes the per-warp form.
       if (sb.threads) {
@@ -664,9 +672,11 @@ void run_local_ws(kss_sys s, int ik, int nb, const void* psi, void* out, int ld,
       for (int n0 = 0; n0 < nb; n0 += nc) {
         const int m = std::min(nc, nb - n0);
         a.n0 = n0;
-        kk.a<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
+        if (!(wx && wide_pass_x<T>(a, 0, m, ctx->stream, false)))
+          kk.a<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
         if (!(sb.threads && wide_pass_b<T>(a, sb.A, sb.B, sb.threads, m, ctx->stream, false))) warp_b(a, m);
-        kk.c<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
+        if (!(wx && wide_pass_x<T>(a, 1, m, ctx->stream, false)))
+          kk.c<<<dim3(a.W3, m), kThreads, ra, ctx->stream>>>(a, rp, scr_warp);
       }
       KSS_CHECK_CUDA(cudaGetLastError());
       return;

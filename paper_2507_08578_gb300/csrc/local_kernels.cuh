@@ -24,6 +24,7 @@ struct LocalArgs {
   using C = typename CT<T>::C;
   int N1, N2, N3, N1p, N2p, N3p;
   int W2, W3, lo2, lo3;
+  int W1, lo1;    // the sphere's x window (0, 0 when unknown: no pruning of the x transforms)
   FftDim d1, d2, d3;
   int pw1, pw2, pw3;  // pencils per warp call along x, y, z
   const C* tw1;
@@ -296,6 +297,61 @@ struct CtPol {
   X(5, 8) X(8, 5) X(4, 10) X(10, 4) X(5, 9) X(9, 5) X(6, 8) X(8, 6) X(5, 10) X(10, 5) X(6, 9)     \
   X(9, 6) X(6, 10) X(10, 6) X(5, 12) X(12, 5) X(8, 12) X(12, 8) X(6, 16) X(16, 6)
 
+// Scatter of band n's sphere coefficients on z-plane u3 into the x-row tile (row u2 at u2 * N1p,
+// x in natural order, as the tile index table holds them).  Packed mode forms psi_2n + i psi_2n+1.
+template <int NT, typename T, typename C>
+__device__ __forceinline__ void scatter_plane(const LocalArgs<T>& a, C* tile, int u3, int n) {
+  const int g0 = a.zstart[u3], g1 = a.zstart[u3 + 1];
+  if (a.packed) {
+    const C* pa = a.psi + (size_t)(2 * n) * a.ld;
+    const C* pb = 2 * n + 1 < a.nbands ? pa + a.ld : nullptr;
+    for (int g = g0 + (int)threadIdx.x; g < g1; g += NT) {
+      C x = pa[g];
+      if (pb) {
+        const C y = pb[g];  // x + i y
+        x.x -= y.y;
+        x.y += y.x;
+      }
+      tile[a.tileidx[g]] = x;
+    }
+  } else {
+    const C* ps = a.psi + n * a.ld;
+    for (int g = g0 + (int)threadIdx.x; g < g1; g += NT) tile[a.tileidx[g]] = ps[g];
+  }
+}
+
+// Gather of z-plane u3 from the x-row tile and the epilogue of pass C: out = alpha (T psi + V
+// psi) + beta psi + gamma psi_prev (coefficients from device memory when coef is set).  Packed
+// mode stores the raw transform of the pair (unpacked and finished by gamma_unpack).
+template <int NT, typename T, typename C>
+__device__ __forceinline__ void gather_plane(const LocalArgs<T>& a, const C* tile, int u3, int n) {
+  const int g0 = a.zstart[u3], g1 = a.zstart[u3 + 1];
+  C* po = a.out + n * a.ld;
+  if (a.packed) {
+    for (int g = g0 + (int)threadIdx.x; g < g1; g += NT) po[g] = tile[a.tileidx[g]];
+    return;
+  }
+  const C* ps = a.psi + n * a.ld;
+  const C* pp = a.psi_prev ? a.psi_prev + n * a.ld : nullptr;
+  const T al = a.coef ? a.coef[0] : a.alpha;
+  const T be = a.coef ? a.coef[1] : a.beta;
+  const T ga = a.coef ? a.coef[2] : a.gamma;
+  for (int g = g0 + (int)threadIdx.x; g < g1; g += NT) {
+    const C v = tile[a.tileidx[g]];
+    const C p = ps[g];
+    const T t = a.kin[g];
+    C o;
+    o.x = al * (t * p.x + v.x) + be * p.x;
+    o.y = al * (t * p.y + v.y) + be * p.y;
+    if (pp) {
+      const C q = pp[g];
+      o.x += ga * q.x;
+      o.y += ga * q.y;
+    }
+    po[g] = o;
+  }
+}
+
 template <typename T, class Pol = RtPol>
 __device__ __forceinline__ void pass_a_body(const LocalArgs<T>& a, const RegPlan& rp, int scr_warp,
                                             int u3, int nl) {
@@ -310,23 +366,7 @@ __device__ __forceinline__ void pass_a_body(const LocalArgs<T>& a, const RegPlan
   const int tsz = a.W2 * a.N1p;
   for (int i = threadIdx.x; i < tsz; i += kThreads) tile[i] = C{0, 0};
   __syncthreads();
-  const int g0 = a.zstart[u3], g1 = a.zstart[u3 + 1];
-  if (a.packed) {
-    const C* pa = a.psi + (size_t)(2 * n) * a.ld;
-    const C* pb = 2 * n + 1 < a.nbands ? pa + a.ld : nullptr;
-    for (int g = g0 + threadIdx.x; g < g1; g += kThreads) {
-      C x = pa[g];
-      if (pb) {
-        const C y = pb[g];  // x + i y
-        x.x -= y.y;
-        x.y += y.x;
-      }
-      tile[a.tileidx[g]] = x;
-    }
-  } else {
-    const C* ps = a.psi + n * a.ld;
-    for (int g = g0 + threadIdx.x; g < g1; g += kThreads) tile[a.tileidx[g]] = ps[g];
-  }
+  scatter_plane<kThreads>(a, tile, u3, n);
   __syncthreads();
   const int r0 = a.rowrange[2 * u3], r1 = a.rowrange[2 * u3 + 1];
   const int nrows = r1 - r0 + 1;
@@ -450,32 +490,7 @@ __device__ __forceinline__ void pass_c_body(const LocalArgs<T>& a, const RegPlan
                      [&](int p, int e, C v) { rows[p * ld + e] = v; });
   }
   __syncthreads();
-  const int g0 = a.zstart[u3], g1 = a.zstart[u3 + 1];
-  if (a.packed) {  // raw transform of the pair; unpacked and finished by gamma_unpack
-    C* po = a.out + n * a.ld;
-    for (int g = g0 + threadIdx.x; g < g1; g += kThreads) po[g] = tile[a.tileidx[g]];
-    return;
-  }
-  const C* ps = a.psi + n * a.ld;
-  const C* pp = a.psi_prev ? a.psi_prev + n * a.ld : nullptr;
-  const T al = a.coef ? a.coef[0] : a.alpha;
-  const T be = a.coef ? a.coef[1] : a.beta;
-  const T ga = a.coef ? a.coef[2] : a.gamma;
-  C* po = a.out + n * a.ld;
-  for (int g = g0 + threadIdx.x; g < g1; g += kThreads) {
-    const C v = tile[a.tileidx[g]];
-    const C p = ps[g];
-    const T t = a.kin[g];
-    C o;
-    o.x = al * (t * p.x + v.x) + be * p.x;
-    o.y = al * (t * p.y + v.y) + be * p.y;
-    if (pp) {
-      const C q = pp[g];
-      o.x += ga * q.x;
-      o.y += ga * q.y;
-    }
-    po[g] = o;
-  }
+  gather_plane<kThreads>(a, tile, u3, n);
 }
 
 // Pass B with every transform stage spread over the whole CTA.  The per-warp pencil forms above
@@ -668,18 +683,161 @@ __device__ __forceinline__ void pass_bw_body(const LocalArgs<T>& a, int x, int n
   }
 }
 
-// Pruning width of the CTA-wide pass for split N = A * B and the sphere windows of y (lo2, W2) and
-// z (lo3, W3): the smallest CW whose edge mask covers every window position of both axes in the
-// strided stages (B CW > largest index, B CW >= magnitude of the most negative one), or 0 when the
-// windows do not straddle 0 or leave nothing to prune (2 CW >= A).
+// Passes A and C with the x transforms spread over the CTA, in the manner of pass_bw_body: each
+// stage is one loop over the (row, sub-transform) tasks of the rows r0..r1 of z-plane u3 that hold
+// sphere points, in place in the tile (rows fastest across lanes, odd pitch N + 1).  The tile
+// holds x in natural order for the scatter (pass A) and the gather (pass C); between the
+// transform stages and the slab it is in the stages' digit-reversed order, position x / A +
+// B (x % A) holding index x, so pass A's inverse ends and pass C's forward starts there, and the
+// slab keeps natural x order for pass B.  CW > 0: the sphere's x window occupies only the first
+// and last CW values of the strided index r + B i, so pass A's first stage reads only those
+// inputs and pass C's last stage computes only those outputs (fftr::rdft_m with the edge mask).
+// Requires N1 == A * B, even, so that the tile index table's pitch N1 + 1 is odd.
+template <typename T, int A, int B>
+struct WideX {
+  static constexpr int N = A * B, P = N + 1;
+  static_assert(N % 2 == 0, "the tile pitch N + 1 must be odd");
+  static size_t smem(int W2) { return sizeof(typename CT<T>::C) * ((size_t)N + (size_t)W2 * P); }
+  __device__ static int pos(int x) { return x / A + B * (x % A); }
+};
+
+template <typename T, int A, int B, int NT, int CW = 0>
+__device__ __forceinline__ void pass_aw_body(const LocalArgs<T>& a, int u3, int nl) {
+  using C = typename CT<T>::C;
+  using G = WideX<T, A, B>;
+  constexpr int N = G::N, P = G::P;
+  constexpr unsigned MW = fftr::edge_mask<A, CW>(), MF = fftr::full_mask<A>();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* tw = reinterpret_cast<C*>(smraw);  // e^{-2 pi i m / N}, m < N
+  C* tile = tw + N;                     // W2 rows (y in the sphere window) x N (x)
+  const int tid = threadIdx.x;
+  const int n = a.n0 + nl;
+  int r0 = a.rowrange[2 * u3];
+  const int r1 = a.rowrange[2 * u3 + 1];
+  const int nrows = r1 >= r0 ? r1 - r0 + 1 : 0;
+  if (!nrows) r0 = 0;
+  C* rows = tile + r0 * P;
+  for (int i = tid; i < N; i += NT) tw[i] = a.tw1[i];
+  for (int i = tid; i < nrows * P; i += NT) rows[i] = C{0, 0};
+  __syncthreads();
+  scatter_plane<NT>(a, tile, u3, n);
+  __syncthreads();
+  const fftr::FastDiv dnr(nrows > 0 ? nrows : 1);
+  // inverse, stage 1: task (row, r < B) on the elements r + B i
+  for (int t = tid; t < nrows * B; t += NT) {
+    const int r = dnr(t), u = t - r * nrows;
+    C* row = rows + u * P + r;
+    C v[A];
+    fftr::static_for<0, A>([&](auto ic) {
+      constexpr int i = decltype(ic)::value;
+      if constexpr (MW >> i & 1u) v[i] = row[B * i];
+    });
+    fftr::rdft_m<A, MW, MF>(v, (T)1);
+#pragma unroll
+    for (int k = 1; k < A; ++k) {
+      C w = tw[r * k];
+      w.y = -w.y;
+      v[k] = fftr::mul(v[k], w);
+    }
+#pragma unroll
+    for (int k = 0; k < A; ++k) row[B * k] = v[k];
+  }
+  __syncthreads();
+  // inverse, stage 2: task (row, k < A) on the B contiguous elements j + B k
+  for (int t = tid; t < nrows * A; t += NT) {
+    const int k = dnr(t), u = t - k * nrows;
+    C* row = rows + u * P + B * k;
+    C v[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) v[j] = row[j];
+    fftr::rdft<B>(v, (T)1);
+#pragma unroll
+    for (int j = 0; j < B; ++j) row[j] = v[j];
+  }
+  __syncthreads();
+  // slab [x][u3][u2] in natural x order; rows outside r0..r1 hold no sphere point (zero)
+  C* dst = a.work + ((size_t)nl * N * a.W3 + u3) * a.W2;
+  const size_t xs = (size_t)a.W3 * a.W2;
+  const fftr::FastDiv dw2(a.W2);
+  for (int i = tid; i < N * a.W2; i += NT) {
+    const int x = dw2(i), u2 = i - x * a.W2;
+    const int u = u2 - r0;
+    dst[x * xs + u2] = (u >= 0 && u < nrows) ? rows[u * P + G::pos(x)] : C{0, 0};
+  }
+}
+
+template <typename T, int A, int B, int NT, int CW = 0>
+__device__ __forceinline__ void pass_cw_body(const LocalArgs<T>& a, int u3, int nl) {
+  using C = typename CT<T>::C;
+  using G = WideX<T, A, B>;
+  constexpr int N = G::N, P = G::P;
+  constexpr unsigned MW = fftr::edge_mask<A, CW>(), MF = fftr::full_mask<A>();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* tw = reinterpret_cast<C*>(smraw);
+  C* tile = tw + N;
+  const int tid = threadIdx.x;
+  const int n = a.n0 + nl;
+  int r0 = a.rowrange[2 * u3];
+  const int r1 = a.rowrange[2 * u3 + 1];
+  const int nrows = r1 >= r0 ? r1 - r0 + 1 : 0;
+  if (!nrows) r0 = 0;
+  C* rows = tile + r0 * P;
+  for (int i = tid; i < N; i += NT) tw[i] = a.tw1[i];
+  const C* src = a.work + ((size_t)nl * N * a.W3 + u3) * a.W2;
+  const size_t xs = (size_t)a.W3 * a.W2;
+  const fftr::FastDiv dnr(nrows > 0 ? nrows : 1);
+  for (int i = tid; i < N * nrows; i += NT) {
+    const int x = dnr(i), u = i - x * nrows;
+    rows[u * P + G::pos(x)] = src[x * xs + r0 + u];
+  }
+  __syncthreads();
+  // forward, stage 1: task (row, r < A) on the B contiguous positions k2 + B r (index r + A k2)
+  for (int t = tid; t < nrows * A; t += NT) {
+    const int r = dnr(t), u = t - r * nrows;
+    C* row = rows + u * P + B * r;
+    C v[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) v[j] = row[j];
+    fftr::rdft<B>(v, (T)-1);
+#pragma unroll
+    for (int q = 1; q < B; ++q) v[q] = fftr::mul(v[q], tw[r * q]);
+#pragma unroll
+    for (int q = 0; q < B; ++q) row[q] = v[q];
+  }
+  __syncthreads();
+  // forward, stage 2: task (row, q < B) on the positions q + B m; index q + B k lands at
+  // position q + B k (natural order); only the window's outputs are formed
+  for (int t = tid; t < nrows * B; t += NT) {
+    const int q = dnr(t), u = t - q * nrows;
+    C* row = rows + u * P + q;
+    C v[A];
+#pragma unroll
+    for (int m = 0; m < A; ++m) v[m] = row[B * m];
+    fftr::rdft_m<A, MF, MW>(v, (T)-1);
+    fftr::static_for<0, A>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      if constexpr (MW >> k & 1u) row[B * k] = v[k];
+    });
+  }
+  __syncthreads();
+  gather_plane<NT>(a, tile, u3, n);
+}
+
+// Smallest edge width CW of split N = A * B whose strided index r + B i covers every position of
+// the window [lo, lo + W - 1] (B CW > largest index, B CW >= magnitude of the most negative one);
+// 1 << 20 when the window does not straddle 0.
+inline int axis_prune_cw(int B, int lo, int W) {
+  const int hi = lo + W - 1;
+  if (lo > 0 || hi < 0) return 1 << 20;
+  const int c1 = hi / B + 1, c2 = (-lo + B - 1) / B;
+  return c1 > c2 ? c1 : c2;
+}
+
+// Pruning width of the CTA-wide pass B for split N = A * B and the sphere windows of y (lo2, W2)
+// and z (lo3, W3): the width covering both axes, or 0 when the windows do not straddle 0 or leave
+// nothing to prune (2 CW >= A).
 inline int wide_prune_cw(int A, int B, int lo2, int W2, int lo3, int W3) {
-  auto one = [&](int lo, int W) {
-    const int hi = lo + W - 1;
-    if (lo > 0 || hi < 0) return 1 << 20;
-    const int c1 = hi / B + 1, c2 = (-lo + B - 1) / B;
-    return c1 > c2 ? c1 : c2;
-  };
-  const int c = std::max(one(lo2, W2), one(lo3, W3));
+  const int c = std::max(axis_prune_cw(B, lo2, W2), axis_prune_cw(B, lo3, W3));
   return 2 * c < A ? c : 0;
 }
 

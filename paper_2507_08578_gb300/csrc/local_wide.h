@@ -14,6 +14,13 @@ constexpr size_t kWideSmemMax = 227 * 1024;
 template <typename T>
 bool wide_pass_b(const lk::LocalArgs<T>& a, int A, int B, int nt, int nbands, cudaStream_t st, bool dry);
 
+// Launches pass A (which = 0) or pass C (which = 1) for nbands bands (grid W3 x nbands) with the
+// CTA-wide x transforms (lk::pass_aw_body, lk::pass_cw_body), pruned to the sphere's x window when
+// an instance covers it.  Returns false (and launches nothing) when no instance exists for N1 or
+// its shared memory does not fit; dry = true only checks availability.
+template <typename T>
+bool wide_pass_x(const lk::LocalArgs<T>& a, int which, int nbands, cudaStream_t st, bool dry);
+
 // The (A, B) pairs with instances, in KSS_WIDE_SPLITS order.
 inline const std::vector<std::pair<int, int>>& wide_splits() {
   static const std::vector<std::pair<int, int>> v = {

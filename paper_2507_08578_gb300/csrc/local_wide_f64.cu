@@ -9,4 +9,9 @@ bool wide_pass_b<double>(const lk::LocalArgs<double>& a, int A, int B, int nt, i
   return wide_detail::dispatch<double>(a, A, B, nt, nbands, st, dry);
 }
 
+template <>
+bool wide_pass_x<double>(const lk::LocalArgs<double>& a, int which, int nbands, cudaStream_t st, bool dry) {
+  return wide_detail::dispatch_x<double>(a, which, nbands, st, dry);
+}
+
 }  // namespace kss

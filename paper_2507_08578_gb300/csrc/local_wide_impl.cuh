@@ -1,6 +1,8 @@
-// Kernel instances of the CTA-wide pass B (local_kernels.cuh, pass_bw_body) for one precision:
-// every split of KSS_WIDE_SPLITS at 256 and 384 threads per CTA (and 128 in single precision).  Included by one translation
-// unit per precision (local_wide_f32.cu, local_wide_f64.cu) so the build compiles them in parallel.
+// Kernel instances of the CTA-wide passes (local_kernels.cuh) for one precision: pass B
+// (pass_bw_body) for every split of KSS_WIDE_SPLITS at 256 and 384 threads per CTA (and 128 in
+// single precision), passes A and C (pass_aw_body, pass_cw_body) for the x splits of
+// KSS_WIDEX_SPLITS.  Included by one translation unit per precision (local_wide_f32.cu,
+// local_wide_f64.cu) so the build compiles them in parallel.
 #pragma once
 
 #include "local_kernels.cuh"
@@ -60,6 +62,67 @@ bool dispatch(const LocalArgs<T>& a, int A, int B, int nt, int nbands, cudaStrea
            : nt == 256 ? launch_one<T, x, y, 256>(a, nbands, st, dry)                 \
                        : launch_one<T, x, y, 384>(a, nbands, st, dry);
     KSS_WIDE_SPLITS(KSS_CASE)
+#undef KSS_CASE
+    default:
+      return false;
+  }
+}
+
+// ---- passes A and C ----
+// x splits with CTA-wide instances (N1 = A * B even) for pass A and for pass C, and the edge width
+// of their pruned instances (the widths that the config-2 sphere's x window, |m| <= 20, needs).
+// Each pass puts the stage with the twiddle multiply on the 8-point transforms (pass A inverts
+// 8 x 12, pass C forwards 12 x 8): the 12-point stage then runs without the 11 twiddle values,
+// which keeps double precision at 64 / 80 registers (three CTAs per SM).  The slab between the
+// passes is in natural x order, so the two passes need not share a split.
+#define KSS_WIDEX_SPLITS(X) X(8, 12, 12, 8)
+constexpr int x_pruned_cw(int A, int B) { return A == 8 && B == 12 ? 2 : A == 12 && B == 8 ? 3 : 0; }
+constexpr int kWideXThreads = 256;
+
+template <typename T, int A, int B, int NT, int CW = 0>
+__global__ void __launch_bounds__(NT) pass_aw(LocalArgs<T> a) {
+  pass_aw_body<T, A, B, NT, CW>(a, blockIdx.x, blockIdx.y);
+}
+template <typename T, int A, int B, int NT, int CW = 0>
+__global__ void __launch_bounds__(NT) pass_cw(LocalArgs<T> a) {
+  pass_cw_body<T, A, B, NT, CW>(a, blockIdx.x, blockIdx.y);
+}
+
+template <typename T, int NT, class K>
+void launch_x1(K kern, const LocalArgs<T>& a, size_t sm, int nbands, cudaStream_t st) {
+  KSS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  kern<<<dim3(a.W3, nbands), NT, sm, st>>>(a);
+}
+
+// which = 0: pass A (inverse transforms), 1: pass C (forward transforms)
+template <typename T, int A, int B, int NT, int which>
+bool launch_x(const LocalArgs<T>& a, int nbands, cudaStream_t st, bool dry) {
+  using G = WideX<T, A, B>;
+  if (a.N1p != G::P) return false;  // the tile index table's pitch
+  const size_t sm = G::smem(a.W2);
+  if (sm > kWideSmemMax) return false;
+  if (dry) return true;
+  constexpr int PC = x_pruned_cw(A, B);
+  const bool pruned = PC > 0 && axis_prune_cw(B, a.lo1, a.W1) <= PC;
+  if constexpr (which == 0) {
+    if (pruned) launch_x1<T, NT>(pass_aw<T, A, B, NT, PC>, a, sm, nbands, st);
+    else launch_x1<T, NT>(pass_aw<T, A, B, NT>, a, sm, nbands, st);
+  } else {
+    if (pruned) launch_x1<T, NT>(pass_cw<T, A, B, NT, PC>, a, sm, nbands, st);
+    else launch_x1<T, NT>(pass_cw<T, A, B, NT>, a, sm, nbands, st);
+  }
+  return true;
+}
+
+template <typename T>
+bool dispatch_x(const LocalArgs<T>& a, int which, int nbands, cudaStream_t st, bool dry) {
+  switch (a.N1) {
+#define KSS_CASE(xa, ya, xc, yc)                                                           \
+  case xa * ya:                                                                            \
+    static_assert(xa * ya == xc * yc, "passes A and C split the same length");            \
+    return which == 0 ? launch_x<T, xa, ya, kWideXThreads, 0>(a, nbands, st, dry)          \
+                      : launch_x<T, xc, yc, kWideXThreads, 1>(a, nbands, st, dry);
+    KSS_WIDEX_SPLITS(KSS_CASE)
 #undef KSS_CASE
     default:
       return false;

@@ -131,6 +131,11 @@ APPLY_CASES = [
     ("box_72_cubic", lambda: W.tiny_system(a=10.0, ecut=6.0, natom=3, fft_box=(72, 72, 72)), 3, 0),
     ("box_32_64_72_k", lambda: W.tiny_system(a=10.0, ecut=6.0, natom=3, fft_box=(32, 64, 72),
                                              kpts=[(0.25, 0.0, -0.25)]), 6, 1),
+    # x edge 96: the CTA-wide x passes, pruned to a small sphere's x window here ...
+    ("box_96_48_48_k", lambda: W.tiny_system(a=10.0, ecut=6.0, natom=3, fft_box=(96, 48, 48),
+                                             kpts=[(0.25, 0.0, -0.25)]), 5, 1),
+    # ... and unpruned (|m| up to 28 along each axis: wider than the pruned instances cover)
+    ("box_96_wide_sphere", lambda: W.tiny_system(a=20.0, ecut=40.0, natom=3, fft_box=(96, 96, 96)), 3, 0),
 ]
 
 
@@ -140,7 +145,7 @@ def test_apply_fp64(ctx, name, mk, nb, pad):
     assert err < FP64_TOL, err
 
 
-MIXED_CASES = APPLY_CASES[:5] + APPLY_CASES[-4:]
+MIXED_CASES = APPLY_CASES[:5] + APPLY_CASES[-6:]
 
 
 @pytest.mark.parametrize("name,mk,nb,pad", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])

@@ -90,12 +90,20 @@ def symmetric_block(basis, nb, seed):
     return c
 
 
+GAMMA_APPLY_SYSTEMS = {
+    "C1": lambda: W.config1(),
+    # x edge 96: band pairs through the CTA-wide x passes
+    "box_96_48_48": lambda: W.tiny_system(a=10.0, ecut=6.0, natom=3, fft_box=(96, 48, 48)),
+}
+
+
 @pytest.mark.parametrize("prec,tol", [(K.KSS_PREC_FP64, 1e-10), (K.KSS_PREC_MIXED, 2e-5)])
 @pytest.mark.parametrize("nb", [6, 5])
-def test_apply_gamma_matches_oracle(ctx, prec, tol, nb):
+@pytest.mark.parametrize("system", list(GAMMA_APPLY_SYSTEMS))
+def test_apply_gamma_matches_oracle(ctx, prec, tol, nb, system):
     import torch
     from tests.kss_helpers import rel_err_rows
-    s = W.config1()
+    s = GAMMA_APPLY_SYSTEMS[system]()
     sysh = setup(ctx, s)
     try:
         p = O.build_problem(s, 0)
