@@ -19,8 +19,8 @@ __global__ void __launch_bounds__(NT) pass_bw(LocalArgs<T> a) {
 }
 
 // Splits with a pruned instance and its edge width: the 96-point splits, with the widths that the
-// sphere window of the config-2 box (|m| <= 20 along y and z) needs; a window that needs no more
-// than that width runs the pruned instance, any other the full one.
+// sphere window of a 96^3 box at a = 20 bohr, Ecut = 20 Ha (|m| <= 20 along y and z) needs; a
+// window that needs no more than that width runs the pruned instance, any other the full one.
 constexpr int pruned_cw(int A, int B) {
   return A == 8 && B == 12 ? 2 : A == 12 && B == 8 ? 3 : A == 6 && B == 16 ? 2 : A == 16 && B == 6 ? 4 : 0;
 }
@@ -70,7 +70,7 @@ bool dispatch(const LocalArgs<T>& a, int A, int B, int nt, int nbands, cudaStrea
 
 // ---- passes A and C ----
 // x splits with CTA-wide instances (N1 = A * B even) for pass A and for pass C, and the edge width
-// of their pruned instances (the widths that the config-2 sphere's x window, |m| <= 20, needs).
+// of their pruned instances (the widths that the x window of the same sphere, |m| <= 20, needs).
 // Each pass puts the stage with the twiddle multiply on the 8-point transforms (pass A inverts
 // 8 x 12, pass C forwards 12 x 8): the 12-point stage then runs without the 11 twiddle values,
 // which keeps double precision at 64 / 80 registers (three CTAs per SM).  The slab between the
