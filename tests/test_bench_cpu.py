@@ -60,6 +60,19 @@ def test_kernel_families():
     assert bench.family("residual_norms") == "residual_norms"
 
 
+def test_fft_path_hbm_figure():
+    # 1000 band-applies of 1000 plane waves in FP64 (2 x 1000 x 16 B per band) over 1.0 s of the
+    # three pass families: 32 MB/s; other families do not count
+    fam = {"local_pass_a": (10, 100.0), "local_pass_b": (10, 800.0), "local_pass_c": (10, 100.0),
+           "dense_hegv_grid": (1, 500.0)}
+    h = bench.fft_path_hbm(fam, 1000, 1000, 16, 6682.0)
+    assert h["algorithmic_bytes_per_band"] == 32000
+    assert h["achieved_gbs"] == pytest.approx(0.032)
+    assert h["frac"] == pytest.approx(0.032 / 6682.0)
+    assert h["kernels"] == "local_pass_a+local_pass_b+local_pass_c"
+    assert bench.fft_path_hbm({"dense_hegv_grid": (1, 5.0)}, 10, 10, 8, 6682.0) is None
+
+
 def test_algorithmic_work_counts():
     class S:
         nproj = 256
